@@ -1,0 +1,214 @@
+/*
+ * csff.h -- complex-contour multigrid far-field maps (C ABI).
+ *
+ * The method (Cools, Reps & Vanroose, "An efficient multigrid calculation of
+ * the Far Field map for Helmholtz and Schroedinger equations"):
+ *
+ *   1. Sec. 2.1, eq. (helmholtz_in) with Sec. 3.1, eq. (helmholtz_cc): the
+ *      scattered wave u solves, on the rotated grid z = x e^{i gamma},
+ *          -e^{-2i gamma} Lap_h u - k^2 (1 + chi(z)) u = k^2 chi(z) u_in(z),
+ *      u_in(z) = exp(i k eta.z), discretised per Sec. 3.2, eq. (csg), with the
+ *      stencil of Sec. 5.2 and homogeneous Dirichlet values on the box edge.
+ *   2. Sec. 4: the damped system is solved by geometric multigrid V-cycles
+ *      (omega-Jacobi or red-black Gauss-Seidel smoothing, full weighting,
+ *      bi/trilinear interpolation, direct solve on the coarsest grid).
+ *   3. eq. (FFmap) over the contour, eq. (I2complex):
+ *          F(alpha) = k^2 e^{i d gamma} h^d sum_j e^{-i k z_j.alpha}
+ *                     chi(z_j) (u_in(z_j) + u(z_j))
+ *      over the interior nodes (uniform weights; the paper allows any rule).
+ *
+ * Conventions shared by every call
+ *   - d = 2 or 3; n = 2^L + 1 nodes per side on [box_lo, box_hi]^d,
+ *     h = (box_hi - box_lo)/(n - 1).  Unknowns are the m^d interior nodes,
+ *     m = n - 2, stored x fastest: index ((iz*m + iy)*m + ix).
+ *   - Complex numbers are interleaved (re, im): "c128" = 2 x double (16 B),
+ *     "c64" = 2 x float (8 B).  Directions (eta, alpha) are real unit vectors
+ *     stored as d doubles per row, component 0 = x.
+ *   - Pointers named *_dev are device pointers (cudaMalloc'ed or any
+ *     device-accessible memory) owned by the caller; pointers named *_host are
+ *     ordinary host pointers.  The library never frees caller memory.
+ *   - All device work is enqueued on the plan's stream (set at creation or by
+ *     csff_plan_set_stream).  Calls returning results on the host
+ *     (csff_solve's info, csff_norm2) synchronise that stream.
+ *   - Errors are returned, never raised: no host exit, no device trap.  On any
+ *     CSFF_ERR_* the contents of output buffers are unspecified; the plan stays
+ *     usable unless the error is CSFF_ERR_CUDA from a sticky CUDA fault.
+ *     csff_last_error() gives a one-line description of the last failure in
+ *     the calling thread.
+ *   - A plan is not thread-safe; distinct plans are independent.
+ *   - chi must be analytic for the contour rotation to be valid (Sec. 2.3,
+ *     Sec. 3.1); the library takes chi as a sum of Gaussians and cannot check
+ *     analyticity of anything else.
+ */
+#ifndef CSFF_H
+#define CSFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum csff_status {
+  CSFF_OK = 0,
+  CSFF_ERR_INVALID_ARG = 1,   /* bad pointer, size, level or option */
+  CSFF_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  CSFF_ERR_OOM = 3,           /* device allocation failed */
+  CSFF_ERR_NOT_CONVERGED = 4, /* max_cycles reached above rel_tol */
+  CSFF_ERR_DIVERGED = 5,      /* residual grew for 3 cycles in a row */
+  CSFF_ERR_NONFINITE = 6,     /* a residual norm or input became Inf/NaN */
+  CSFF_ERR_TIMEOUT = 7,       /* a bounded device wait ran out */
+  CSFF_ERR_UNSUPPORTED = 8,   /* option combination not built */
+  CSFF_WARN_ILL_CONDITIONED = 100 /* result valid; far-field terms exceed
+                                     the FP64 range or kappa is large */
+} csff_status;
+
+/* One term A exp(-sum_c (z_c - center_c)^2 / width) of chi, A = amp_re + i amp_im.
+   Evaluated at complex z (analytic continuation, Sec. 3.1). */
+typedef struct csff_gauss {
+  double amp_re, amp_im;
+  double center[3];
+  double width;
+} csff_gauss;
+
+typedef struct csff_problem {
+  int dim;                 /* 2 or 3 */
+  int n;                   /* nodes per side, 2^L + 1, L >= 2 */
+  double box_lo, box_hi;   /* box [box_lo, box_hi]^dim */
+  double gamma;            /* rotation angle of the contour, radians, (0, pi/4) */
+  double k;                /* wavenumber k_0 > 0 */
+  int n_gauss;             /* 0..8 terms of chi */
+  const csff_gauss* gauss; /* host array of n_gauss terms (copied) */
+} csff_problem;
+
+enum { CSFF_SMOOTHER_JACOBI = 0, CSFF_SMOOTHER_RBGS = 1 };
+enum { CSFF_PREC_FP64 = 0, CSFF_PREC_MIXED = 1 };
+/* Arithmetic of the per-step calls below. */
+enum { CSFF_ARITH_FP64 = 0, CSFF_ARITH_FP32 = 1 };
+
+typedef struct csff_opts {
+  int smoother;       /* CSFF_SMOOTHER_* (Sec. 4) */
+  double omega;       /* Jacobi weight (2/3 in the paper); ignored by RBGS */
+  int nu1, nu2;       /* pre/post sweeps of V(nu1, nu2) */
+  int coarsest_n;     /* nodes per side of the coarsest grid (direct solve) */
+  double rel_tol;     /* stop when ||b - A u||_2 <= rel_tol ||b||_2 */
+  int max_cycles;     /* FP64: V-cycles; MIXED: total FP32 V-cycles */
+  int precision;      /* CSFF_PREC_FP64 or CSFF_PREC_MIXED */
+  int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1) */
+} csff_opts;
+
+#define CSFF_MAX_HISTORY 256
+
+/* Per-solve report.  history[i] = ||r_i|| / ||b|| after i finest-level
+   V-cycles (FP64) or i refinement steps (MIXED); history[0] = 1 for u0 = 0. */
+typedef struct csff_info {
+  int status;          /* csff_status of this right-hand side */
+  int cycles;          /* finest-level V-cycles run (FP64 or FP32) */
+  int refinements;     /* FP64 refinement steps (MIXED), else 0 */
+  double rel_res;      /* final ||r|| / ||b|| */
+  double conv_factor;  /* (||r_k|| / ||r_0||)^(1/k) per V-cycle */
+  int n_hist;
+  double history[CSFF_MAX_HISTORY];
+} csff_info;
+
+/* Read-only description of a plan's hierarchy. */
+typedef struct csff_plan_desc {
+  int n_levels;
+  int n[16];                 /* nodes per side of each level, finest first */
+  double h[16];
+  size_t device_bytes;       /* device memory held by the plan */
+  double log_rhs_max;        /* estimate of max log|chi u_in| over the box */
+  double log_ff_max;         /* estimate of max log|e^{-ikz.a} chi u_in| */
+  int ill_conditioned;       /* 1 if log_ff_max > 600 (beyond FP64 head-room) */
+  int below_min_gamma;       /* 1 if gamma < atan(0.5)/2, eq. (mingammajac) */
+} csff_plan_desc;
+
+typedef struct csff_plan csff_plan;
+
+/* ---- plan ------------------------------------------------------------ */
+
+/* Build the level hierarchy n, (n+1)/2, ..., coarsest_n; per level the
+   complex coefficients k^2(1 + chi) and 1/diag (FP64 and FP32 copies), the
+   dense inverse of the coarsest operator (FP64, from an LU with partial
+   pivoting), and work buffers.  stream: a cudaStream_t (NULL = legacy
+   default stream).  Sec. 3.2 eq. (csg); Sec. 4.
+   Errors: CSFF_ERR_INVALID_ARG for n != 2^j (coarsest_n - 1) + 1, dim not 2/3,
+   gamma outside (0, pi/4), k <= 0, n_gauss outside 0..8, bad opts;
+   CSFF_ERR_OOM; CSFF_ERR_CUDA. */
+csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, void* stream,
+                             csff_plan** out);
+void csff_plan_destroy(csff_plan* plan);
+csff_status csff_plan_set_stream(csff_plan* plan, void* stream);
+csff_status csff_plan_describe(const csff_plan* plan, csff_plan_desc* desc);
+
+/* ---- whole-path calls ------------------------------------------------ */
+
+/* b_dev (c128, n_rhs x m^d) = k^2 chi(z) u_in(z) for each incident direction
+   eta_host[r*dim ...] (Sec. 2.1). */
+csff_status csff_rhs(csff_plan* plan, int n_rhs, const double* eta_host, void* b_dev);
+
+/* Solve for the scattered wave of each incident direction.  u_dev (c128,
+   n_rhs x m^d) is read as the initial guess if use_guess != 0, else taken as 0,
+   and overwritten with the solution.  info_host: n_rhs reports or NULL.
+   Returns the worst status over the right-hand sides (CSFF_OK if all met
+   rel_tol).  FP64: V-cycles in FP64.  MIXED: FP64 residual r = b - A u, FP32
+   V-cycles on the power-of-two-scaled correction equation, FP64 update
+   (iterative refinement); the coarsest solve is FP64 in both. */
+csff_status csff_solve(csff_plan* plan, int n_rhs, const double* eta_host, void* u_dev,
+                       int use_guess, csff_info* info_host);
+
+/* Far-field map, eq. (FFmap) over the contour (eq. I2complex), for each
+   right-hand side r and outgoing direction a:
+     F[r*n_ang + a] = k^2 e^{i d gamma} h^d sum_j e^{-i k z_j.alpha_a}
+                      chi_j (u_in,r,j + u_r,j).
+   u_dev: c128 n_rhs x m^d (from csff_solve); alpha_host: n_ang x dim.
+   F_dev: c128 n_rhs x n_ang (device).  F_exp_dev: int32 n_rhs x n_ang
+   (device) or NULL.  With F_exp_dev the true value is F * 2^F_exp, which
+   keeps maps whose terms exceed the FP64 range finite; without it F is the
+   plain value (Inf where it does not fit) and the call returns
+   CSFF_WARN_ILL_CONDITIONED if any scale was needed.  Arithmetic: FP64. */
+csff_status csff_far_field(csff_plan* plan, int n_rhs, const double* eta_host, const void* u_dev,
+                           int n_ang, const double* alpha_host, void* F_dev, int32_t* F_exp_dev);
+
+/* ---- per-step calls (one kernel each; for verification and custom cycles) --
+   arith: CSFF_ARITH_FP64 (c128 buffers) or CSFF_ARITH_FP32 (c64 buffers).
+   level: 0 = finest.  All buffers are device pointers of m_level^d elements
+   unless stated.  Coefficients are the plan's (FP32 copies for FP32). */
+
+/* K1: r = b - A_l u (eq. csg with the Sec. 5.2 stencil). */
+csff_status csff_residual(csff_plan* plan, int level, int arith, const void* u_dev,
+                          const void* b_dev, void* r_dev);
+/* K2: `sweeps` sweeps of the plan's smoother on A_l u = b, in place on u_dev.
+   Jacobi: u <- u + omega D^{-1}(b - A u) (uses a plan buffer for the new
+   iterate).  RBGS: red points (even sum of node indices) then black. */
+csff_status csff_smooth(csff_plan* plan, int level, int arith, void* u_dev, const void* b_dev,
+                        int sweeps);
+/* K3: b_c (level+1) = full weighting of r_f (level). */
+csff_status csff_restrict(csff_plan* plan, int level, int arith, const void* r_fine_dev,
+                          void* b_coarse_dev);
+/* K4: u_f (level) += bi/trilinear interpolation of e_c (level+1). */
+csff_status csff_prolong_add(csff_plan* plan, int level, int arith, const void* e_coarse_dev,
+                             void* u_fine_dev);
+/* K5: u_c = A_c^{-1} b_c on the coarsest level (FP64 inverse, FP64 arithmetic;
+   buffers in the precision given by arith). */
+csff_status csff_coarse_solve(csff_plan* plan, int arith, const void* b_dev, void* u_dev);
+/* K6: ||v||_2 over m_level^d complex values, accumulated in FP64; result in
+   *out_host (synchronises the stream). */
+csff_status csff_norm2(csff_plan* plan, int level, int arith, const void* v_dev, double* out_host);
+/* One V(nu1, nu2) cycle on the finest level, in place on u_dev. */
+csff_status csff_vcycle(csff_plan* plan, int arith, void* u_dev, const void* b_dev);
+
+/* ---- helpers ------------------------------------------------------------ */
+
+/* eq. (thetagamma): gamma = atan(sin theta / (2 + cos theta)). */
+double csff_gamma_from_ecs(double theta_ecs);
+const char* csff_status_string(csff_status s);
+const char* csff_last_error(void);
+/* Number of CUDA kernel launches the library made in this process. */
+uint64_t csff_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSFF_H */

@@ -1,0 +1,272 @@
+"""csff: complex-contour multigrid far-field maps on GB300 (sm_103a CUDA).
+
+Thin ctypes binding over libcsff.so (declared in include/csff.h).  Every step
+of the method runs in the library's CUDA kernels; this module only marshals
+arguments (torch tensors -> device pointers, dicts -> C structs).  There is no
+CPU fallback: importing the package fails if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcsff.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libcsff.so not found at {LIB_PATH}; build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a). "
+        "There is no CPU fallback.")
+_lib = C.CDLL(LIB_PATH)
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_CUDA = 2
+ERR_OOM = 3
+ERR_NOT_CONVERGED = 4
+ERR_DIVERGED = 5
+ERR_NONFINITE = 6
+ERR_TIMEOUT = 7
+ERR_UNSUPPORTED = 8
+WARN_ILL_CONDITIONED = 100
+
+SMOOTHER = {"jacobi": 0, "rbgs": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+ARITH_FP64, ARITH_FP32 = 0, 1
+MAX_HISTORY = 256
+
+
+class Gauss(C.Structure):
+    _fields_ = [("amp_re", C.c_double), ("amp_im", C.c_double), ("center", C.c_double * 3),
+                ("width", C.c_double)]
+
+
+class ProblemC(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int), ("box_lo", C.c_double), ("box_hi", C.c_double),
+                ("gamma", C.c_double), ("k", C.c_double), ("n_gauss", C.c_int),
+                ("gauss", C.POINTER(Gauss))]
+
+
+class OptsC(C.Structure):
+    _fields_ = [("smoother", C.c_int), ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("coarsest_n", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
+                ("precision", C.c_int), ("inner_cycles", C.c_int)]
+
+
+class InfoC(C.Structure):
+    _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("refinements", C.c_int),
+                ("rel_res", C.c_double), ("conv_factor", C.c_double), ("n_hist", C.c_int),
+                ("history", C.c_double * MAX_HISTORY)]
+
+    def as_dict(self):
+        return {"status": self.status, "cycles": self.cycles, "refinements": self.refinements,
+                "rel_res": self.rel_res, "conv_factor": self.conv_factor,
+                "history": list(self.history[: self.n_hist])}
+
+
+class DescC(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("n", C.c_int * 16), ("h", C.c_double * 16),
+                ("device_bytes", C.c_size_t), ("log_rhs_max", C.c_double), ("log_ff_max", C.c_double),
+                ("ill_conditioned", C.c_int), ("below_min_gamma", C.c_int)]
+
+
+_vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
+_dp = C.POINTER(C.c_double)
+_SIGS = {
+    "csff_plan_create": (_i, [C.POINTER(ProblemC), C.POINTER(OptsC), _vp, C.POINTER(_vp)]),
+    "csff_plan_destroy": (None, [_vp]),
+    "csff_plan_set_stream": (_i, [_vp, _vp]),
+    "csff_plan_describe": (_i, [_vp, C.POINTER(DescC)]),
+    "csff_rhs": (_i, [_vp, _i, _dp, _vp]),
+    "csff_solve": (_i, [_vp, _i, _dp, _vp, _i, C.POINTER(InfoC)]),
+    "csff_far_field": (_i, [_vp, _i, _dp, _vp, _i, _dp, _vp, _vp]),
+    "csff_residual": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "csff_smooth": (_i, [_vp, _i, _i, _vp, _vp, _i]),
+    "csff_restrict": (_i, [_vp, _i, _i, _vp, _vp]),
+    "csff_prolong_add": (_i, [_vp, _i, _i, _vp, _vp]),
+    "csff_coarse_solve": (_i, [_vp, _i, _vp, _vp]),
+    "csff_norm2": (_i, [_vp, _i, _i, _vp, _dp]),
+    "csff_vcycle": (_i, [_vp, _i, _vp, _vp]),
+    "csff_gamma_from_ecs": (_d, [_d]),
+    "csff_status_string": (_cp, [_i]),
+    "csff_last_error": (_cp, []),
+    "csff_kernel_launches": (C.c_uint64, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTS = tuple(_SIGS)
+
+
+class CsffError(RuntimeError):
+    def __init__(self, status, where):
+        msg = _lib.csff_last_error().decode() or _lib.csff_status_string(status).decode()
+        super().__init__(f"{where}: {_lib.csff_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(st, where, ok=(OK,)):
+    if st not in ok:
+        raise CsffError(st, where)
+    return st
+
+
+def gamma_from_ecs(theta: float) -> float:
+    """eq. (thetagamma)."""
+    return _lib.csff_gamma_from_ecs(theta)
+
+
+def kernel_launches() -> int:
+    return int(_lib.csff_kernel_launches())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dbl(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _require(t, dtype, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+        raise ValueError(f"{name}: need contiguous {dtype} with >= {numel} elements, got {t.dtype} {tuple(t.shape)}")
+
+
+class Plan:
+    """A multigrid + far-field plan for one problem (csff_plan_create).
+
+    problem: {"dim", "n", "lo", "hi", "gamma", "k", "gaussians": [{"amp", "width", "center"}]}
+    opts:    {"smoother", "omega", "nu1", "nu2", "coarsest_n", "rel_tol", "max_cycles",
+              "precision" ("fp64" | "mixed"), "inner_cycles"}
+    """
+
+    def __init__(self, problem: dict, opts: dict, stream=None):
+        gs = problem.get("gaussians", [])
+        self._g = (Gauss * max(1, len(gs)))()
+        for i, g in enumerate(gs):
+            a = complex(g["amp"])
+            c = tuple(g.get("center", (0.0, 0.0, 0.0)))
+            self._g[i] = Gauss(a.real, a.imag, (C.c_double * 3)(*c), float(g["width"]))
+        self.dim = int(problem["dim"])
+        self.n = int(problem["n"])
+        self.m = self.n - 2
+        self.N = self.m ** self.dim
+        pc = ProblemC(self.dim, self.n, float(problem["lo"]), float(problem["hi"]), float(problem["gamma"]),
+                      float(problem["k"]), len(gs), self._g)
+        o = dict(opts)
+        oc = OptsC(SMOOTHER[o.get("smoother", "jacobi")], float(o.get("omega", 2.0 / 3.0)), int(o.get("nu1", 1)),
+                   int(o.get("nu2", 1)), int(o.get("coarsest_n", 5)), float(o.get("rel_tol", 1e-8)),
+                   int(o.get("max_cycles", 100)), PRECISION[o.get("precision", "fp64")],
+                   int(o.get("inner_cycles", 3)))
+        self._stream = stream
+        h = C.c_void_p()
+        _check(_lib.csff_plan_create(C.byref(pc), C.byref(oc), _stream_handle(stream), C.byref(h)), "plan_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.csff_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(_lib.csff_plan_set_stream(self._h, _stream_handle(stream)), "set_stream")
+
+    def describe(self) -> dict:
+        d = DescC()
+        _check(_lib.csff_plan_describe(self._h, C.byref(d)), "describe")
+        return {"levels": [d.n[i] for i in range(d.n_levels)], "h": [d.h[i] for i in range(d.n_levels)],
+                "device_bytes": d.device_bytes, "log_rhs_max": d.log_rhs_max, "log_ff_max": d.log_ff_max,
+                "ill_conditioned": bool(d.ill_conditioned), "below_min_gamma": bool(d.below_min_gamma)}
+
+    def level_size(self, level):
+        d = DescC()
+        _check(_lib.csff_plan_describe(self._h, C.byref(d)), "describe")
+        return (d.n[level] - 2) ** self.dim
+
+    # ---- whole path ------------------------------------------------------
+    def rhs(self, eta, b):
+        import torch
+        eta, ep = _dbl(eta)
+        nr = eta.shape[0]
+        _require(b, torch.complex128, nr * self.N, "b")
+        _check(_lib.csff_rhs(self._h, nr, ep, _ptr(b)), "rhs")
+
+    def solve(self, eta, u, use_guess=False, ok=(OK,)):
+        """Solve for each incident direction (rows of eta); u: complex128 CUDA
+        tensor of n_rhs * m^d.  Returns (status, [info dicts])."""
+        import torch
+        eta, ep = _dbl(eta)
+        nr = eta.shape[0]
+        _require(u, torch.complex128, nr * self.N, "u")
+        infos = (InfoC * max(1, nr))()
+        st = _lib.csff_solve(self._h, nr, ep, _ptr(u), int(bool(use_guess)), infos)
+        _check(st, "solve", ok)
+        return st, [infos[i].as_dict() for i in range(nr)]
+
+    def far_field(self, eta, u, alphas, F, F_exp=None, ok=(OK, WARN_ILL_CONDITIONED)):
+        import torch
+        eta, ep = _dbl(eta)
+        al, ap = _dbl(alphas)
+        nr, na = eta.shape[0], al.shape[0]
+        _require(u, torch.complex128, nr * self.N, "u")
+        _require(F, torch.complex128, nr * na, "F")
+        if F_exp is not None:
+            _require(F_exp, torch.int32, nr * na, "F_exp")
+        st = _lib.csff_far_field(self._h, nr, ep, _ptr(u), na, ap, _ptr(F), _ptr(F_exp))
+        return _check(st, "far_field", ok)
+
+    # ---- per-step calls ----------------------------------------------------
+    def _arith(self, t):
+        import torch
+        if t.dtype == torch.complex128:
+            return ARITH_FP64
+        if t.dtype == torch.complex64:
+            return ARITH_FP32
+        raise TypeError("buffers must be complex64 or complex128")
+
+    def residual(self, level, u, b, r):
+        _check(_lib.csff_residual(self._h, level, self._arith(u), _ptr(u), _ptr(b), _ptr(r)), "residual")
+
+    def smooth(self, level, u, b, sweeps=1):
+        _check(_lib.csff_smooth(self._h, level, self._arith(u), _ptr(u), _ptr(b), sweeps), "smooth")
+
+    def restrict(self, level, r_fine, b_coarse):
+        _check(_lib.csff_restrict(self._h, level, self._arith(r_fine), _ptr(r_fine), _ptr(b_coarse)), "restrict")
+
+    def prolong_add(self, level, e_coarse, u_fine):
+        _check(_lib.csff_prolong_add(self._h, level, self._arith(u_fine), _ptr(e_coarse), _ptr(u_fine)),
+               "prolong_add")
+
+    def coarse_solve(self, b, u):
+        _check(_lib.csff_coarse_solve(self._h, self._arith(u), _ptr(b), _ptr(u)), "coarse_solve")
+
+    def norm2(self, level, v) -> float:
+        out = C.c_double()
+        _check(_lib.csff_norm2(self._h, level, self._arith(v), _ptr(v), C.byref(out)), "norm2")
+        return out.value
+
+    def vcycle(self, u, b):
+        _check(_lib.csff_vcycle(self._h, self._arith(u), _ptr(u), _ptr(b)), "vcycle")

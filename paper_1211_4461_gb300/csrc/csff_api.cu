@@ -1,0 +1,651 @@
+// C ABI of libcsff: plan construction, the multigrid solve drivers (FP64 and
+// FP32-inner / FP64-refinement), the far-field call and the per-step calls.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "csff_internal.h"
+
+using csff::cx;
+using csff::Level;
+
+namespace csff {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& s) { t_last_error = s; }
+
+csff_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? CSFF_ERR_OOM : CSFF_ERR_CUDA;
+}
+
+}  // namespace csff
+
+namespace {
+
+using cd = std::complex<double>;
+
+#define CK(call, what)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return csff::cuda_fail(e_, what);        \
+  } while (0)
+
+#define CS(call)                                                    \
+  do {                                                              \
+    csff_status s_ = (call);                                        \
+    if (s_ != CSFF_OK) return s_;                                   \
+  } while (0)
+
+csff_status invalid(const std::string& s) {
+  csff::set_error(s);
+  return CSFF_ERR_INVALID_ARG;
+}
+
+template <typename P>
+csff_status dev_alloc(csff_plan* plan, P** p, size_t count) {
+  size_t bytes = sizeof(P) * (count ? count : 1);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return csff::cuda_fail(e, "cudaMalloc");
+  }
+  plan->bytes += bytes;
+  return CSFF_OK;
+}
+
+// chi per axis at the interior nodes of a grid with n nodes:
+// E_{g,c}(i) = exp(-(x_i e^{i gamma} - center_c)^2 / w), amplitude folded into c = 0.
+std::vector<double2> chi_tables(const csff_plan* P, int n) {
+  const int d = P->dim, m = n - 2, G = P->prob.n_gauss;
+  const double h = (P->prob.box_hi - P->prob.box_lo) / (n - 1);
+  const cd rot = std::polar(1.0, P->prob.gamma);
+  std::vector<double2> t((size_t)G * d * m);
+  for (int g = 0; g < G; ++g) {
+    const csff_gauss& q = P->gauss[g];
+    for (int c = 0; c < d; ++c)
+      for (int i = 0; i < m; ++i) {
+        double x = P->prob.box_lo + (i + 1) * h;
+        cd z = x * rot - q.center[c];
+        cd v = std::exp(-z * z / q.width);
+        if (c == 0) v *= cd(q.amp_re, q.amp_im);
+        t[((size_t)g * d + c) * m + i] = make_double2(v.real(), v.imag());
+      }
+  }
+  return t;
+}
+
+// Dense inverse of the coarsest operator by LU with partial pivoting.
+bool coarse_inverse(const csff_plan* P, const Level& L, std::vector<double2>& out) {
+  const int d = P->dim, m = L.m;
+  const int N = (d == 3) ? m * m * m : m * m;
+  std::vector<double2> tab = chi_tables(P, L.n);
+  const int G = P->prob.n_gauss;
+  const double k2 = P->prob.k * P->prob.k;
+  const cd c(L.c.x, L.c.y);
+  std::vector<cd> A((size_t)N * N, cd(0, 0));
+  auto id = [&](int ix, int iy, int iz) { return (iz * m + iy) * m + ix; };
+  for (int iz = 0; iz < (d == 3 ? m : 1); ++iz)
+    for (int iy = 0; iy < m; ++iy)
+      for (int ix = 0; ix < m; ++ix) {
+        cd chi(0, 0);
+        for (int g = 0; g < G; ++g) {
+          const double2* t = &tab[(size_t)g * d * m];
+          cd v = cd(t[ix].x, t[ix].y) * cd(t[m + iy].x, t[m + iy].y);
+          if (d == 3) v *= cd(t[2 * m + iz].x, t[2 * m + iz].y);
+          chi += v;
+        }
+        int r = id(ix, iy, iz);
+        A[(size_t)r * N + r] = 2.0 * d * c - k2 * (1.0 + chi);
+        int nb[6][3] = {{ix - 1, iy, iz}, {ix + 1, iy, iz}, {ix, iy - 1, iz},
+                        {ix, iy + 1, iz}, {ix, iy, iz - 1}, {ix, iy, iz + 1}};
+        for (int q = 0; q < 2 * d; ++q) {
+          int a = nb[q][0], b = nb[q][1], e = nb[q][2];
+          if (a < 0 || a >= m || b < 0 || b >= m || e < 0 || e >= (d == 3 ? m : 1)) continue;
+          A[(size_t)r * N + id(a, b, e)] = -c;
+        }
+      }
+  // Gauss-Jordan on [A | I] with partial pivoting
+  std::vector<cd> I((size_t)N * N, cd(0, 0));
+  for (int i = 0; i < N; ++i) I[(size_t)i * N + i] = 1.0;
+  for (int col = 0; col < N; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < N; ++r)
+      if (std::abs(A[(size_t)r * N + col]) > std::abs(A[(size_t)piv * N + col])) piv = r;
+    if (std::abs(A[(size_t)piv * N + col]) == 0.0) return false;
+    if (piv != col)
+      for (int j = 0; j < N; ++j) {
+        std::swap(A[(size_t)piv * N + j], A[(size_t)col * N + j]);
+        std::swap(I[(size_t)piv * N + j], I[(size_t)col * N + j]);
+      }
+    cd inv = 1.0 / A[(size_t)col * N + col];
+    for (int j = 0; j < N; ++j) {
+      A[(size_t)col * N + j] *= inv;
+      I[(size_t)col * N + j] *= inv;
+    }
+    for (int r = 0; r < N; ++r) {
+      if (r == col) continue;
+      cd f = A[(size_t)r * N + col];
+      if (f == cd(0, 0)) continue;
+      for (int j = 0; j < N; ++j) {
+        A[(size_t)r * N + j] -= f * A[(size_t)col * N + j];
+        I[(size_t)r * N + j] -= f * I[(size_t)col * N + j];
+      }
+    }
+  }
+  out.resize((size_t)N * N);
+  for (size_t i = 0; i < out.size(); ++i) out[i] = make_double2(I[i].real(), I[i].imag());
+  return true;
+}
+
+// Incident-wave tables U_c(i) = exp(i k eta_c x_i e^{i gamma}) on the finest grid.
+csff_status upload_uinc(csff_plan* P, const double* eta) {
+  const Level& L = P->lv[0];
+  const int d = P->dim, m = L.m;
+  std::vector<double2> ut((size_t)d * m);
+  const cd ik(0.0, P->prob.k), rot = std::polar(1.0, P->prob.gamma);
+  for (int c = 0; c < d; ++c)
+    for (int i = 0; i < m; ++i) {
+      double x = P->prob.box_lo + (i + 1) * L.h;
+      cd v = std::exp(ik * eta[c] * x * rot);
+      ut[(size_t)c * m + i] = make_double2(v.real(), v.imag());
+    }
+  CK(cudaMemcpyAsync(P->uinc_tab, ut.data(), sizeof(double2) * ut.size(), cudaMemcpyHostToDevice, P->stream),
+     "upload incident tables");
+  return CSFF_OK;
+}
+
+// ---- per-precision buffer access ------------------------------------------------
+template <typename T> cx<T>* ubuf(Level& L);
+template <> double2* ubuf<double>(Level& L) { return L.u64; }
+template <> float2* ubuf<float>(Level& L) { return L.u32; }
+template <typename T> cx<T>* tbuf(Level& L);
+template <> double2* tbuf<double>(Level& L) { return L.t64; }
+template <> float2* tbuf<float>(Level& L) { return L.t32; }
+template <typename T> cx<T>* bbuf(Level& L);
+template <> double2* bbuf<double>(Level& L) { return L.b64; }
+template <> float2* bbuf<float>(Level& L) { return L.b32; }
+template <typename T> cx<T>* rbuf(Level& L);
+template <> double2* rbuf<double>(Level& L) { return L.r64; }
+template <> float2* rbuf<float>(Level& L) { return L.r32; }
+
+template <typename T>
+csff_status smooth(csff_plan* P, int l, cx<T>* u, const cx<T>* b, int sweeps) {
+  Level& L = P->lv[l];
+  cudaStream_t s = P->stream;
+  if (P->opts.smoother == CSFF_SMOOTHER_RBGS) {
+    for (int i = 0; i < sweeps; ++i) CK(csff::launch_rbgs<T>(P->dim, L, u, b, s), "rbgs");
+    return CSFF_OK;
+  }
+  cx<T>* t = tbuf<T>(L);
+  int i = 0;
+  for (; i + 1 < sweeps; i += 2) {
+    CK(csff::launch_jacobi<T>(P->dim, L, P->opts.omega, u, b, t, s), "jacobi");
+    CK(csff::launch_jacobi<T>(P->dim, L, P->opts.omega, t, b, u, s), "jacobi");
+  }
+  if (i < sweeps) {
+    CK(csff::launch_jacobi<T>(P->dim, L, P->opts.omega, u, b, t, s), "jacobi");
+    CK(cudaMemcpyAsync(u, t, sizeof(cx<T>) * (size_t)L.N, cudaMemcpyDeviceToDevice, s), "copy");
+  }
+  return CSFF_OK;
+}
+
+// One V(nu1, nu2) cycle on level l for A_l u = b (Sec. 4).
+template <typename T>
+csff_status vcycle(csff_plan* P, int l, cx<T>* u, const cx<T>* b) {
+  const int nl = (int)P->lv.size();
+  cudaStream_t s = P->stream;
+  if (l == nl - 1) {
+    CK(csff::launch_coarse_solve<T>(P->coarse_inv, P->coarse_N, b, u, s), "coarse solve");
+    return CSFF_OK;
+  }
+  Level& L = P->lv[l];
+  Level& C = P->lv[l + 1];
+  CS(smooth<T>(P, l, u, b, P->opts.nu1));
+  CK(csff::launch_residual<T>(P->dim, L, u, b, rbuf<T>(L), s), "residual");
+  CK(csff::launch_restrict<T>(P->dim, L, C, rbuf<T>(L), bbuf<T>(C), s), "restrict");
+  if (l + 1 < nl - 1) CK(csff::launch_zero<T>(ubuf<T>(C), C.N, s), "zero");
+  CS(vcycle<T>(P, l + 1, ubuf<T>(C), bbuf<T>(C)));
+  CK(csff::launch_prolong_add<T>(P->dim, L, C, ubuf<T>(C), u, s), "prolong");
+  CS(smooth<T>(P, l, u, b, P->opts.nu2));
+  return CSFF_OK;
+}
+
+// norm of a level-0 FP64 vector into red_out[slot] (device), scaled by 2^-e.
+csff_status norm64(csff_plan* P, const double2* v, int e, int slot) {
+  CK(csff::launch_norm2<double>(v, P->lv[0].N, e, P->red, P->red_blocks, P->red_out + slot, P->stream),
+     "norm");
+  return CSFF_OK;
+}
+
+csff_status read_scalars(csff_plan* P, int count) {
+  CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double) * count, cudaMemcpyDeviceToHost, P->stream),
+     "read norms");
+  CK(cudaStreamSynchronize(P->stream), "sync");
+  return CSFF_OK;
+}
+
+struct Tracker {
+  csff_info* info;
+  double prev = 0;
+  int rises = 0;
+  void start(csff_info* in) {
+    info = in;
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->history[0] = 1.0;
+      info->n_hist = 1;
+    }
+    prev = 1.0;
+    rises = 0;
+  }
+  // returns status if the iteration must stop
+  int push(double rel, int cycles, int refinements, double tol, int max_cycles) {
+    if (info) {
+      if (info->n_hist < CSFF_MAX_HISTORY) info->history[info->n_hist++] = rel;
+      info->cycles = cycles;
+      info->refinements = refinements;
+      info->rel_res = rel;
+      info->conv_factor = cycles > 0 ? std::pow(rel, 1.0 / cycles) : 0.0;
+    }
+    if (!std::isfinite(rel)) return CSFF_ERR_NONFINITE;
+    if (rel <= tol) return CSFF_OK;
+    rises = rel > prev ? rises + 1 : 0;
+    prev = rel;
+    if (rises >= 3) return CSFF_ERR_DIVERGED;
+    if (cycles >= max_cycles) return CSFF_ERR_NOT_CONVERGED;
+    return -1;
+  }
+};
+
+// FP64 V-cycles on the finest level: u (c128, N) solves A u = b64 (level-0 plan buffer).
+csff_status solve_fp64(csff_plan* P, double2* u, int eb, double nb, csff_info* info) {
+  Level& L = P->lv[0];
+  Tracker tr;
+  tr.start(info);
+  int cycles = 0;
+  for (;;) {
+    CS(vcycle<double>(P, 0, u, L.b64));
+    ++cycles;
+    CK(csff::launch_residual<double>(P->dim, L, u, L.b64, L.r64, P->stream), "residual");
+    CS(norm64(P, L.r64, eb, 0));
+    CS(read_scalars(P, 1));
+    int st = tr.push(P->red_host[0] / nb, cycles, 0, P->opts.rel_tol, P->opts.max_cycles);
+    if (st >= 0) return (csff_status)st;
+  }
+}
+
+// FP64 residual, FP32 V-cycles on the scaled correction equation, FP64 update.
+csff_status solve_mixed(csff_plan* P, double2* u, int eb, double nb, csff_info* info) {
+  Level& L = P->lv[0];
+  cudaStream_t s = P->stream;
+  int* ex = reinterpret_cast<int*>(P->red_out + 4);
+  Tracker tr;
+  tr.start(info);
+  int cycles = 0, refinements = 0;
+  const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
+  CK(csff::launch_residual<double>(P->dim, L, u, L.b64, L.r64, s), "residual");
+  CS(norm64(P, L.r64, eb, 0));
+  for (;;) {
+    CK(csff::launch_to32_scaled(L.r64, L.N, P->red_out, L.b32, ex, s), "scale");
+    CK(csff::launch_zero<float>(L.u32, L.N, s), "zero");
+    for (int c = 0; c < inner; ++c) CS(vcycle<float>(P, 0, L.u32, L.b32));
+    cycles += inner;
+    ++refinements;
+    CK(csff::launch_update64(u, L.u32, L.N, ex, s), "update");
+    CK(csff::launch_residual<double>(P->dim, L, u, L.b64, L.r64, s), "residual");
+    CS(norm64(P, L.r64, eb, 0));
+    CS(read_scalars(P, 1));
+    int st = tr.push(P->red_host[0] / nb, cycles, refinements, P->opts.rel_tol, P->opts.max_cycles);
+    if (st >= 0) return (csff_status)st;
+  }
+}
+
+csff_status check_level(const csff_plan* P, int level, int arith) {
+  if (!P) return invalid("plan is NULL");
+  if (level < 0 || level >= (int)P->lv.size()) return invalid("level out of range");
+  if (arith != CSFF_ARITH_FP64 && arith != CSFF_ARITH_FP32) return invalid("arith must be FP64 or FP32");
+  return CSFF_OK;
+}
+
+int worse(int a, int b) {
+  auto rank = [](int s) { return s == CSFF_OK ? 0 : (s == CSFF_WARN_ILL_CONDITIONED ? 1 : 2 + s); };
+  return rank(b) > rank(a) ? b : a;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+double csff_gamma_from_ecs(double theta) { return std::atan(std::sin(theta) / (2.0 + std::cos(theta))); }
+
+const char* csff_status_string(csff_status s) {
+  switch (s) {
+    case CSFF_OK: return "ok";
+    case CSFF_ERR_INVALID_ARG: return "invalid argument";
+    case CSFF_ERR_CUDA: return "CUDA error";
+    case CSFF_ERR_OOM: return "out of device memory";
+    case CSFF_ERR_NOT_CONVERGED: return "not converged";
+    case CSFF_ERR_DIVERGED: return "diverged";
+    case CSFF_ERR_NONFINITE: return "non-finite value";
+    case CSFF_ERR_TIMEOUT: return "device wait timed out";
+    case CSFF_ERR_UNSUPPORTED: return "unsupported";
+    case CSFF_WARN_ILL_CONDITIONED: return "ill-conditioned (result valid)";
+  }
+  return "unknown status";
+}
+
+const char* csff_last_error(void) { return csff::t_last_error.c_str(); }
+
+uint64_t csff_kernel_launches(void) { return csff::g_launches.load(); }
+
+void csff_plan_destroy(csff_plan* P) {
+  if (!P) return;
+  for (Level& L : P->lv)
+    for (void* p : {(void*)L.q64, (void*)L.dinv64, (void*)L.q32, (void*)L.dinv32, (void*)L.u64, (void*)L.t64,
+                    (void*)L.b64, (void*)L.r64, (void*)L.u32, (void*)L.t32, (void*)L.b32, (void*)L.r32})
+      if (p) cudaFree(p);
+  for (double2* p : P->chi_tab)
+    if (p) cudaFree(p);
+  if (P->coarse_inv) cudaFree(P->coarse_inv);
+  if (P->uinc_tab) cudaFree(P->uinc_tab);
+  if (P->red) cudaFree(P->red);
+  if (P->red_out) cudaFree(P->red_out);
+  if (P->red_host) cudaFreeHost(P->red_host);
+  csff::free_ff_buffers(P);
+  delete P;
+}
+
+csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, void* stream, csff_plan** out) {
+  if (!out) return invalid("out is NULL");
+  *out = nullptr;
+  if (!prob || !opts) return invalid("problem/opts is NULL");
+  if (prob->dim != 2 && prob->dim != 3) return invalid("dim must be 2 or 3");
+  if (!(prob->gamma > 0.0 && prob->gamma < 0.78539816339744830962)) return invalid("gamma must lie in (0, pi/4)");
+  if (!(prob->k > 0.0) || !std::isfinite(prob->k)) return invalid("k must be positive");
+  if (!(prob->box_hi > prob->box_lo)) return invalid("empty box");
+  if (prob->n_gauss < 0 || prob->n_gauss > 8 || (prob->n_gauss > 0 && !prob->gauss))
+    return invalid("n_gauss must be 0..8 with a non-NULL array");
+  for (int g = 0; g < prob->n_gauss; ++g)
+    if (!(prob->gauss[g].width > 0.0)) return invalid("Gaussian width must be positive");
+  if (opts->smoother != CSFF_SMOOTHER_JACOBI && opts->smoother != CSFF_SMOOTHER_RBGS)
+    return invalid("unknown smoother");
+  if (opts->nu1 < 0 || opts->nu2 < 0 || opts->nu1 + opts->nu2 == 0) return invalid("need nu1 + nu2 > 0");
+  if (opts->precision != CSFF_PREC_FP64 && opts->precision != CSFF_PREC_MIXED) return invalid("bad precision");
+  if (!(opts->rel_tol > 0.0) || opts->max_cycles < 1) return invalid("need rel_tol > 0 and max_cycles >= 1");
+  if (opts->smoother == CSFF_SMOOTHER_JACOBI && !(opts->omega > 0.0 && opts->omega < 2.0))
+    return invalid("omega must lie in (0, 2)");
+  if (opts->coarsest_n < 3) return invalid("coarsest_n must be >= 3");
+  std::vector<int> ns;
+  for (int n = prob->n;; n = (n + 1) / 2) {
+    ns.push_back(n);
+    if (n == opts->coarsest_n) break;
+    if (n < opts->coarsest_n || (n - 1) % 2 != 0 || ns.size() > 15)
+      return invalid("n must equal 2^j (coarsest_n - 1) + 1 with at most 16 levels");
+  }
+  const int d = prob->dim;
+  long long nc = 1;
+  for (int i = 0; i < d; ++i) nc *= (opts->coarsest_n - 2);
+  if (nc > 4096) return invalid("coarsest grid too large for the dense direct solve");
+
+  csff_plan* P = new csff_plan();
+  P->prob = *prob;
+  P->gauss.assign(prob->gauss, prob->gauss + prob->n_gauss);
+  P->prob.gauss = P->gauss.data();
+  P->opts = *opts;
+  P->dim = d;
+  P->stream = (cudaStream_t)stream;
+  auto fail = [&](csff_status s) {
+    csff_plan_destroy(P);
+    return s;
+  };
+  const double k2 = prob->k * prob->k;
+  const std::complex<double> e2 = std::polar(1.0, -2.0 * prob->gamma);
+  for (size_t l = 0; l < ns.size(); ++l) {
+    Level L;
+    L.n = ns[l];
+    L.m = L.n - 2;
+    L.N = 1;
+    for (int i = 0; i < d; ++i) L.N *= L.m;
+    L.h = (prob->box_hi - prob->box_lo) / (L.n - 1);
+    std::complex<double> c = e2 / (L.h * L.h);
+    L.c = make_double2(c.real(), c.imag());
+    P->lv.push_back(L);
+  }
+  for (size_t l = 0; l < P->lv.size(); ++l) {
+    Level& L = P->lv[l];
+    csff_status s;
+    if ((s = dev_alloc(P, &L.q64, L.N)) || (s = dev_alloc(P, &L.dinv64, L.N)) || (s = dev_alloc(P, &L.q32, L.N)) ||
+        (s = dev_alloc(P, &L.dinv32, L.N)) || (s = dev_alloc(P, &L.u64, L.N)) || (s = dev_alloc(P, &L.t64, L.N)) ||
+        (s = dev_alloc(P, &L.b64, L.N)) || (s = dev_alloc(P, &L.r64, L.N)) || (s = dev_alloc(P, &L.u32, L.N)) ||
+        (s = dev_alloc(P, &L.t32, L.N)) || (s = dev_alloc(P, &L.b32, L.N)) || (s = dev_alloc(P, &L.r32, L.N)))
+      return fail(s);
+    std::vector<double2> tab = chi_tables(P, L.n);
+    double2* dtab = nullptr;
+    if ((s = dev_alloc(P, &dtab, tab.size()))) return fail(s);
+    P->chi_tab.push_back(dtab);
+    cudaError_t e = cudaMemcpy(dtab, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(csff::cuda_fail(e, "upload chi tables"));
+    std::vector<const double2*> per_g(P->prob.n_gauss);
+    for (int g = 0; g < P->prob.n_gauss; ++g) per_g[g] = dtab + (size_t)g * d * L.m;
+    e = csff::launch_coefs(d, L, per_g.data(), P->prob.n_gauss, k2, P->stream);
+    if (e != cudaSuccess) return fail(csff::cuda_fail(e, "coefficients"));
+  }
+  // the chi tables are kept per level; finest-level tables are used by rhs/far field
+  std::vector<double2> inv;
+  if (!coarse_inverse(P, P->lv.back(), inv)) return fail(invalid("coarsest operator is singular"));
+  P->coarse_N = (int)std::lround(std::sqrt((double)inv.size()));
+  {
+    csff_status s;
+    if ((s = dev_alloc(P, &P->coarse_inv, inv.size()))) return fail(s);
+    cudaError_t e = cudaMemcpy(P->coarse_inv, inv.data(), sizeof(double2) * inv.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(csff::cuda_fail(e, "upload coarse inverse"));
+    P->red_blocks = 152 * 8;
+    if ((s = dev_alloc(P, &P->red, P->red_blocks)) || (s = dev_alloc(P, &P->red_out, 16)) ||
+        (s = dev_alloc(P, &P->uinc_tab, (size_t)d * P->lv[0].m)))
+      return fail(s);
+    e = cudaMallocHost((void**)&P->red_host, 16 * sizeof(double));
+    if (e != cudaSuccess) return fail(csff::cuda_fail(e, "pinned host buffer"));
+  }
+  // conditioning estimates (single Gaussian on the axis of eta, Sec. 3.3's
+  // warning about products of growing and decaying factors)
+  {
+    const double sg = std::sin(prob->gamma), c2 = std::cos(2 * prob->gamma);
+    const double R = std::max(std::fabs(prob->box_lo), std::fabs(prob->box_hi));
+    double lr = -1e300, lf = -1e300;
+    for (int g = 0; g < prob->n_gauss; ++g) {
+      double w = prob->gauss[g].width, la = std::log(std::hypot(prob->gauss[g].amp_re, prob->gauss[g].amp_im));
+      double t = std::min(prob->k * sg * w / (2 * c2), R);
+      lr = std::max(lr, la + prob->k * sg * t - c2 * t * t / w);
+      double t2 = std::min(prob->k * sg * w / c2, R);
+      lf = std::max(lf, la + 2 * prob->k * sg * t2 - c2 * t2 * t2 / w);
+    }
+    P->log_rhs_max = lr;
+    P->log_ff_max = lf;
+  }
+  cudaError_t e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return fail(csff::cuda_fail(e, "plan setup"));
+  *out = P;
+  return CSFF_OK;
+}
+
+csff_status csff_plan_set_stream(csff_plan* P, void* stream) {
+  if (!P) return invalid("plan is NULL");
+  P->stream = (cudaStream_t)stream;
+  return CSFF_OK;
+}
+
+csff_status csff_plan_describe(const csff_plan* P, csff_plan_desc* d) {
+  if (!P || !d) return invalid("NULL argument");
+  std::memset(d, 0, sizeof(*d));
+  d->n_levels = (int)P->lv.size();
+  for (int l = 0; l < d->n_levels; ++l) {
+    d->n[l] = P->lv[l].n;
+    d->h[l] = P->lv[l].h;
+  }
+  d->device_bytes = P->bytes;
+  d->log_rhs_max = P->log_rhs_max;
+  d->log_ff_max = P->log_ff_max;
+  d->ill_conditioned = P->log_ff_max > 600.0;
+  d->below_min_gamma = P->prob.gamma < std::atan(0.5) / 2.0;
+  return CSFF_OK;
+}
+
+csff_status csff_rhs(csff_plan* P, int n_rhs, const double* eta, void* b_dev) {
+  if (!P || !eta || !b_dev || n_rhs < 0) return invalid("bad rhs arguments");
+  Level& L = P->lv[0];
+  std::vector<const double2*> per_g(P->prob.n_gauss);
+  for (int g = 0; g < P->prob.n_gauss; ++g) per_g[g] = P->chi_tab[0] + (size_t)g * P->dim * L.m;
+  for (int r = 0; r < n_rhs; ++r) {
+    CS(upload_uinc(P, eta + (size_t)r * P->dim));
+    CK(csff::launch_rhs(P->dim, L.m, per_g.data(), P->prob.n_gauss, P->uinc_tab, P->prob.k * P->prob.k,
+                        (double2*)b_dev + (size_t)r * L.N, P->stream),
+       "rhs");
+  }
+  return CSFF_OK;
+}
+
+csff_status csff_solve(csff_plan* P, int n_rhs, const double* eta, void* u_dev, int use_guess, csff_info* info) {
+  if (!P || !eta || !u_dev || n_rhs < 0) return invalid("bad solve arguments");
+  Level& L = P->lv[0];
+  int worst = CSFF_OK;
+  for (int r = 0; r < n_rhs; ++r) {
+    double2* u = (double2*)u_dev + (size_t)r * L.N;
+    csff_info* in = info ? info + r : nullptr;
+    CS(csff_rhs(P, 1, eta + (size_t)r * P->dim, L.b64));
+    if (!use_guess) CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
+    // ||b|| with a power-of-two prescale taken from max |b|
+    int* ex = reinterpret_cast<int*>(P->red_out + 4);
+    CK(csff::launch_max_exp(L.b64, L.N, ex, P->stream), "max exponent");
+    int eb = 0;
+    CK(cudaMemcpyAsync(&eb, ex, sizeof(int), cudaMemcpyDeviceToHost, P->stream), "read exponent");
+    CK(cudaStreamSynchronize(P->stream), "sync");
+    if (eb >= 4000) {
+      csff::set_error("right-hand side is not finite");
+      if (in) { std::memset(in, 0, sizeof(*in)); in->status = CSFF_ERR_NONFINITE; }
+      worst = worse(worst, CSFF_ERR_NONFINITE);
+      continue;
+    }
+    if (eb <= -2000) eb = 0;
+    CS(norm64(P, L.b64, eb, 1));
+    CS(read_scalars(P, 2));
+    double nb = P->red_host[1];
+    csff_status st;
+    if (nb == 0.0) {
+      CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
+      if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
+      st = CSFF_OK;
+    } else if (P->opts.precision == CSFF_PREC_FP64) {
+      st = solve_fp64(P, u, eb, nb, in);
+    } else {
+      st = solve_mixed(P, u, eb, nb, in);
+    }
+    if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;
+    if (in) in->status = st;
+    worst = worse(worst, st);
+  }
+  return (csff_status)worst;
+}
+
+csff_status csff_far_field(csff_plan* P, int n_rhs, const double* eta, const void* u_dev, int n_ang,
+                           const double* alpha, void* F_dev, int32_t* F_exp_dev) {
+  if (!P || !eta || !u_dev || !alpha || !F_dev || n_rhs < 0 || n_ang < 0) return invalid("bad far-field arguments");
+  if (n_ang == 0 || n_rhs == 0) return CSFF_OK;
+  Level& L = P->lv[0];
+  bool any_scaled = false;
+  for (int r = 0; r < n_rhs; ++r) {
+    bool scaled = false;
+    CS(csff::far_field_one(P, eta + (size_t)r * P->dim, (const double2*)u_dev + (size_t)r * L.N, n_ang, alpha,
+                           (double2*)F_dev + (size_t)r * n_ang, F_exp_dev ? F_exp_dev + (size_t)r * n_ang : nullptr,
+                           F_exp_dev ? nullptr : &scaled));
+    any_scaled |= scaled;
+  }
+  return any_scaled ? CSFF_WARN_ILL_CONDITIONED : CSFF_OK;
+}
+
+csff_status csff_residual(csff_plan* P, int level, int arith, const void* u, const void* b, void* r) {
+  CS(check_level(P, level, arith));
+  if (!u || !b || !r) return invalid("NULL buffer");
+  Level& L = P->lv[level];
+  if (arith == CSFF_ARITH_FP64)
+    CK(csff::launch_residual<double>(P->dim, L, (const double2*)u, (const double2*)b, (double2*)r, P->stream), "residual");
+  else
+    CK(csff::launch_residual<float>(P->dim, L, (const float2*)u, (const float2*)b, (float2*)r, P->stream), "residual");
+  return CSFF_OK;
+}
+
+csff_status csff_smooth(csff_plan* P, int level, int arith, void* u, const void* b, int sweeps) {
+  CS(check_level(P, level, arith));
+  if (!u || !b || sweeps < 0) return invalid("bad smoother arguments");
+  if (arith == CSFF_ARITH_FP64) return smooth<double>(P, level, (double2*)u, (const double2*)b, sweeps);
+  return smooth<float>(P, level, (float2*)u, (const float2*)b, sweeps);
+}
+
+csff_status csff_restrict(csff_plan* P, int level, int arith, const void* rf, void* bc) {
+  CS(check_level(P, level, arith));
+  if (level + 1 >= (int)P->lv.size()) return invalid("no coarser level");
+  if (!rf || !bc) return invalid("NULL buffer");
+  Level& F = P->lv[level];
+  Level& C = P->lv[level + 1];
+  if (arith == CSFF_ARITH_FP64)
+    CK(csff::launch_restrict<double>(P->dim, F, C, (const double2*)rf, (double2*)bc, P->stream), "restrict");
+  else
+    CK(csff::launch_restrict<float>(P->dim, F, C, (const float2*)rf, (float2*)bc, P->stream), "restrict");
+  return CSFF_OK;
+}
+
+csff_status csff_prolong_add(csff_plan* P, int level, int arith, const void* ec, void* uf) {
+  CS(check_level(P, level, arith));
+  if (level + 1 >= (int)P->lv.size()) return invalid("no coarser level");
+  if (!ec || !uf) return invalid("NULL buffer");
+  Level& F = P->lv[level];
+  Level& C = P->lv[level + 1];
+  if (arith == CSFF_ARITH_FP64)
+    CK(csff::launch_prolong_add<double>(P->dim, F, C, (const double2*)ec, (double2*)uf, P->stream), "prolong");
+  else
+    CK(csff::launch_prolong_add<float>(P->dim, F, C, (const float2*)ec, (float2*)uf, P->stream), "prolong");
+  return CSFF_OK;
+}
+
+csff_status csff_coarse_solve(csff_plan* P, int arith, const void* b, void* u) {
+  CS(check_level(P, 0, arith));
+  if (!b || !u) return invalid("NULL buffer");
+  if (arith == CSFF_ARITH_FP64)
+    CK(csff::launch_coarse_solve<double>(P->coarse_inv, P->coarse_N, (const double2*)b, (double2*)u, P->stream),
+       "coarse");
+  else
+    CK(csff::launch_coarse_solve<float>(P->coarse_inv, P->coarse_N, (const float2*)b, (float2*)u, P->stream),
+       "coarse");
+  return CSFF_OK;
+}
+
+csff_status csff_norm2(csff_plan* P, int level, int arith, const void* v, double* out) {
+  CS(check_level(P, level, arith));
+  if (!v || !out) return invalid("NULL argument");
+  Level& L = P->lv[level];
+  if (arith == CSFF_ARITH_FP64)
+    CK(csff::launch_norm2<double>((const double2*)v, L.N, 0, P->red, P->red_blocks, P->red_out + 2, P->stream),
+       "norm");
+  else
+    CK(csff::launch_norm2<float>((const float2*)v, L.N, 0, P->red, P->red_blocks, P->red_out + 2, P->stream),
+       "norm");
+  CS(read_scalars(P, 3));
+  *out = P->red_host[2];
+  return CSFF_OK;
+}
+
+csff_status csff_vcycle(csff_plan* P, int arith, void* u, const void* b) {
+  CS(check_level(P, 0, arith));
+  if (!u || !b) return invalid("NULL buffer");
+  if (arith == CSFF_ARITH_FP64) return vcycle<double>(P, 0, (double2*)u, (const double2*)b);
+  return vcycle<float>(P, 0, (float2*)u, (const float2*)b);
+}
+
+}  // extern "C"

@@ -1,0 +1,136 @@
+// Internal declarations shared by the CUDA translation units of libcsff.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/csff.h"
+
+namespace csff {
+
+// ---------------------------------------------------------------------------
+// complex helpers (interleaved re/im in CUDA vector types)
+// ---------------------------------------------------------------------------
+template <typename T> struct CxT;
+template <> struct CxT<double> { using type = double2; };
+template <> struct CxT<float> { using type = float2; };
+template <typename T> using cx = typename CxT<T>::type;
+
+template <typename C> __host__ __device__ __forceinline__ C mk(decltype(C{}.x) a, decltype(C{}.x) b) {
+  C r; r.x = a; r.y = b; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C a, S s) {
+  return mk<C>(a.x * s, a.y * s);
+}
+
+// ---------------------------------------------------------------------------
+// plan internals
+// ---------------------------------------------------------------------------
+struct Level {
+  int n = 0, m = 0;
+  long long N = 0;       // m^d
+  double h = 0;
+  double2 c{};           // e^{-2i gamma} / h^2
+  // per-point coefficients
+  double2* q64 = nullptr;     // k^2 (1 + chi)
+  double2* dinv64 = nullptr;  // 1 / (2d c - q)
+  float2* q32 = nullptr;
+  float2* dinv32 = nullptr;
+  // work buffers
+  double2 *u64 = nullptr, *t64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+  float2 *u32 = nullptr, *t32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+};
+
+// Far-field scratch (grown on demand): g = chi (u_in + u); x/y/z phase
+// tables; stage-1 sums T; angle data; per-row exponents; misc[0] = max
+// exponent of |g|, misc[1] = "a scale was applied" flag.
+struct FFBuffers {
+  size_t g = 0, xt = 0, yt = 0, zt = 0, T = 0, al = 0, ux = 0, xr = 0, s1 = 0;
+  double2 *dg = nullptr, *dxt = nullptr, *dyt = nullptr, *dzt = nullptr, *dT = nullptr;
+  double *dal = nullptr, *dux = nullptr;
+  int *dxr = nullptr, *ds1 = nullptr, *dmisc = nullptr;
+};
+
+}  // namespace csff
+
+struct csff_plan {
+  csff_problem prob{};
+  std::vector<csff_gauss> gauss;
+  csff_opts opts{};
+  cudaStream_t stream = nullptr;
+  int dim = 2;
+  std::vector<csff::Level> lv;
+  // separable tables of chi per level: [n_gauss][dim][m_l] (amplitude folded
+  // into axis 0), FP64 on the device
+  std::vector<double2*> chi_tab;
+  double2* coarse_inv = nullptr;  // dense inverse of the coarsest operator
+  int coarse_N = 0;
+  // per-solve data
+  double2* uinc_tab = nullptr;    // [dim][m] for the current eta
+  double* red = nullptr;          // reduction partials
+  double* red_out = nullptr;      // device scalars (norms)
+  double* red_host = nullptr;     // pinned host mirror
+  int red_blocks = 0;
+  csff::FFBuffers ff;
+  size_t bytes = 0;
+  double log_rhs_max = 0, log_ff_max = 0;
+};
+
+namespace csff {
+
+// error reporting (thread-local last error)
+void set_error(const std::string& s);
+csff_status cuda_fail(cudaError_t e, const char* what);
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// ---- multigrid kernel launchers (mg_kernels.cu) ----------------------------
+template <typename T>
+cudaError_t launch_residual(int dim, const Level& L, const cx<T>* u, const cx<T>* b, cx<T>* r,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi(int dim, const Level& L, double omega, const cx<T>* u, const cx<T>* b,
+                          cx<T>* u_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rbgs(int dim, const Level& L, cx<T>* u, const cx<T>* b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(int dim, const Level& F, const Level& C, const cx<T>* r, cx<T>* bc,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx<T>* ec, cx<T>* u,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(const double2* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s);
+// ||v||_2 * 2^{-e_scale}... computed as sqrt(sum |v 2^-e|^2) * 2^e; result to out (device)
+template <typename T>
+cudaError_t launch_norm2(const cx<T>* v, long long N, int exp_scale, double* partial, int nblk,
+                         double* out, cudaStream_t s);
+// max exponent (frexp) of |v| over N values -> *out (device int)
+cudaError_t launch_max_exp(const double2* v, long long N, int* out, cudaStream_t s);
+cudaError_t launch_coefs(int dim, const Level& L, const double2* const* chi_tab, int n_gauss,
+                         double k2, cudaStream_t s);
+cudaError_t launch_rhs(int dim, int m, const double2* const* chi_tab, int n_gauss,
+                       const double2* uinc_tab, double k2, double2* b, cudaStream_t s);
+// mixed precision helpers
+cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
+                               int* exp_out, cudaStream_t s);
+cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
+
+// ---- far field (farfield.cu) -----------------------------------------------
+void free_ff_buffers(csff_plan* P);
+csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u, int n_ang,
+                          const double* alpha_host, double2* F, int32_t* F_exp, bool* scaled);
+
+}  // namespace csff

@@ -1,0 +1,333 @@
+// Far-field map over the rotated contour (eq. (FFmap) with eq. (I2complex)):
+//   F(a) = k^2 e^{i d gamma} h^d sum_j P(a, j) g_j,
+//   g_j = chi(z_j) (u_in(z_j) + u_j),  P(a, j) = prod_c exp(-i k e^{i gamma} alpha_{a,c} x_{j,c}).
+//
+// The phase factorises over the axes, so the sum is computed in two stages:
+//   stage 1  T[k][rho] = sum_ix P_x(k, ix) g[rho][ix]       (rho = row index (iz, iy))
+//   stage 2  F[a]      = sum_rho P_y(a, iy) [P_z(a, iz)] T[xrow(a)][rho]
+// where k runs over the distinct x-components of the outgoing directions
+// (mirror-image directions share them).  Arithmetic is FP64 throughout.
+//
+// Range: with a rotated contour |P| grows like e^{k sin(gamma) alpha.x} and
+// |g| like e^{k sin(gamma) |x|} at the upstream edge; for large k R the terms
+// leave the FP64 range.  Stage 1 folds a power of two 2^-s1 into the x-table
+// when an a-priori bound on |T| exceeds 2^1020, stage 2 picks 2^-s2 from the
+// largest term of its own sum; the result is returned as F' with exponent
+// s1 + s2 (F = F' 2^(s1+s2)).
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "csff_internal.h"
+
+namespace csff {
+namespace {
+
+__device__ __forceinline__ int exp2_of(double a) {
+  if (a == 0.0) return -4000;
+  int e;
+  frexp(a, &e);
+  return e;
+}
+
+__device__ __forceinline__ int cexp2(double2 v) { return exp2_of(fmax(fabs(v.x), fabs(v.y))) + 1; }
+
+// g = chi (u_in + u) at every interior node.
+struct Tabs8 { const double2* p[8]; };
+
+template <int D>
+__global__ void k_gfield(Tabs8 tabs, int n_gauss, const double2* __restrict__ uinc,
+                         const double2* __restrict__ u, int m, double2* __restrict__ g) {
+  int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
+  int iz = (D == 3) ? (int)blockIdx.z : 0;
+  if (ix >= m || iy >= m) return;
+  long long idx = ((long long)iz * m + iy) * m + ix;
+  double2 chi = make_double2(0, 0);
+  for (int q = 0; q < n_gauss; ++q) {
+    double2 v = cmul(tabs.p[q][ix], tabs.p[q][m + iy]);
+    if (D == 3) v = cmul(v, tabs.p[q][2 * m + iz]);
+    chi = cadd(chi, v);
+  }
+  double2 ui = cmul(uinc[ix], uinc[m + iy]);
+  if (D == 3) ui = cmul(ui, uinc[2 * m + iz]);
+  g[idx] = cmul(chi, cadd(ui, u[idx]));
+}
+
+// Phase tables.  x-table rows k < n_ux: P_x(k, i) 2^-s1[k]; y/z tables for
+// every angle: ytab[a][i], ztab[a][i] (unscaled).  x_i = lo + (i + 1) h.
+// s1[k] = max(0, bound_exp(P_x row) + gmax + ceil(log2 m) + 2 - 1020).
+__global__ void k_phase_tables(const double* __restrict__ ux, int n_ux, const double* __restrict__ alpha,
+                               int n_ang, int dim, int m, double lo, double h, double k, double sg,
+                               double cg, const int* __restrict__ gmax, double2* __restrict__ xtab,
+                               double2* __restrict__ ytab, double2* __restrict__ ztab,
+                               int* __restrict__ s1, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = blockIdx.y;
+  if (i >= m) return;
+  const double LN2 = 0.69314718055994530942;
+  double x = lo + (double)(i + 1) * h;
+  if (row < n_ux) {
+    double a = ux[row];
+    double xmax = fmax(a * (lo + h), a * (lo + (double)m * h));   // max_i a x_i
+    int bx = (int)ceil(k * sg * xmax / LN2) + 1;
+    int lm = 0;
+    while ((1 << lm) < m) ++lm;
+    int s = bx + *gmax + lm + 2 - 1020;
+    s = s > 0 ? s : 0;
+    if (i == 0) { s1[row] = s; if (s > 0) atomicOr(flag, 1); }
+    double mag = exp(k * sg * a * x - (double)s * LN2);
+    double sn, cs;
+    sincos(k * cg * a * x, &sn, &cs);
+    xtab[(long long)row * m + i] = make_double2(mag * cs, -mag * sn);
+  } else {
+    int ar = row - n_ux;                 // y (and z) tables for angle ar
+    if (ar >= n_ang) return;
+    for (int c = 1; c < dim; ++c) {
+      double a = alpha[(long long)ar * dim + c];
+      double mag = exp(k * sg * a * x);
+      double sn, cs;
+      sincos(k * cg * a * x, &sn, &cs);
+      double2 v = make_double2(mag * cs, -mag * sn);
+      if (c == 1) ytab[(long long)ar * m + i] = v;
+      else ztab[(long long)ar * m + i] = v;
+    }
+  }
+}
+
+// Stage 1: T[k][rho] = sum_i X[k][i] G[rho][i]   (complex, FP64).
+// Block tile 32 (k) x 64 (rho), K step 16; 256 threads, 2 x 4 outputs each.
+constexpr int S1_BM = 32, S1_BN = 64, S1_BK = 16;
+
+__global__ void __launch_bounds__(256) k_ff_stage1(const double2* __restrict__ X, int M,
+                                                   const double2* __restrict__ G, int N, int K,
+                                                   double2* __restrict__ T) {
+  __shared__ double2 As[S1_BK][S1_BM];
+  __shared__ double2 Bs[S1_BK][S1_BN];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;     // tx: rho group (4), ty: k group (2)
+  const int m0 = blockIdx.y * S1_BM, n0 = blockIdx.x * S1_BN;
+  double2 acc[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0, 0);
+
+  for (int k0 = 0; k0 < K; k0 += S1_BK) {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {          // A tile: 32 x 16
+      int e = tid + l * 256;
+      int r = e >> 4, kk = e & 15;
+      int gm = m0 + r, gk = k0 + kk;
+      As[kk][r] = (gm < M && gk < K) ? X[(long long)gm * K + gk] : make_double2(0, 0);
+    }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {          // B tile: 64 x 16
+      int e = tid + l * 256;
+      int r = e >> 4, kk = e & 15;
+      int gn = n0 + r, gk = k0 + kk;
+      Bs[kk][r] = (gn < N && gk < K) ? G[(long long)gn * K + gk] : make_double2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < S1_BK; ++kk) {
+      double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        double2 bv = Bs[kk][tx * 4 + b];
+        acc[0][b].x = fma(a0.x, bv.x, fma(-a0.y, bv.y, acc[0][b].x));
+        acc[0][b].y = fma(a0.x, bv.y, fma(a0.y, bv.x, acc[0][b].y));
+        acc[1][b].x = fma(a1.x, bv.x, fma(-a1.y, bv.y, acc[1][b].x));
+        acc[1][b].y = fma(a1.x, bv.y, fma(a1.y, bv.x, acc[1][b].y));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    int gm = m0 + ty * 2 + a;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int gn = n0 + tx * 4 + b;
+      if (gn < N) T[(long long)gm * N + gn] = acc[a][b];
+    }
+  }
+}
+
+template <typename V, typename Op>
+__device__ __forceinline__ V bred(V v, Op op, V* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  v = sh[0];
+  for (int j = 1; j < (int)(blockDim.x >> 5); ++j) v = op(v, sh[j]);
+  return v;
+}
+struct MaxI { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
+struct AddD { __device__ double operator()(double a, double b) const { return a + b; } };
+
+// Stage 2: one block per angle.
+template <int D>
+__global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict__ xrow,
+                            const int* __restrict__ s1, const double2* __restrict__ ytab,
+                            const double2* __restrict__ ztab, int m, double2 pref,
+                            double2* __restrict__ F, int* __restrict__ Fexp, int write_exp,
+                            int* __restrict__ flag) {
+  __shared__ int shi[32];
+  __shared__ double shd[32];
+  const int a = blockIdx.x;
+  const int kx = xrow[a];
+  const long long R = (D == 3) ? (long long)m * m : m;
+  const double2* Tr = T + (long long)kx * R;
+  const double2* yr = ytab + (long long)a * m;
+  const double2* zr = ztab + (long long)a * m;
+  int emax = -4000;
+  for (long long r = threadIdx.x; r < R; r += blockDim.x) {
+    int iy = (int)(r % m), iz = (int)(r / m);
+    int e = cexp2(Tr[r]) + cexp2(yr[iy]) + ((D == 3) ? cexp2(zr[iz]) : 0);
+    emax = e > emax ? e : emax;
+  }
+  emax = bred(emax, MaxI(), shi);
+  int lr = 0;
+  while ((1ll << lr) < R) ++lr;
+  int s2 = emax + lr + 2 - 1020;
+  s2 = s2 > 0 ? s2 : 0;
+  double sc = ldexp(1.0, -s2);
+  double ax = 0, ay = 0;
+  for (long long r = threadIdx.x; r < R; r += blockDim.x) {
+    int iy = (int)(r % m), iz = (int)(r / m);
+    double2 w = cscale(yr[iy], sc);
+    if (D == 3) w = cmul(w, zr[iz]);
+    double2 t = Tr[r];
+    ax = fma(w.x, t.x, fma(-w.y, t.y, ax));
+    ay = fma(w.x, t.y, fma(w.y, t.x, ay));
+  }
+  ax = bred(ax, AddD(), shd);
+  ay = bred(ay, AddD(), shd);
+  if (threadIdx.x == 0) {
+    double2 f = cmul(pref, make_double2(ax, ay));
+    int e = s1[kx] + s2;
+    if (s2 > 0) atomicOr(flag, 1);
+    if (write_exp) {
+      F[a] = f;
+      Fexp[a] = e;
+    } else {
+      F[a] = make_double2(ldexp(f.x, e), ldexp(f.y, e));
+    }
+  }
+}
+
+}  // namespace
+
+static cudaError_t ensure(void** p, size_t& cap, size_t need, csff_plan* P) {
+  if (cap >= need && *p) return cudaSuccess;
+  if (*p) { cudaFree(*p); P->bytes -= cap; *p = nullptr; cap = 0; }
+  cudaError_t e = cudaMalloc(p, need);
+  if (e == cudaSuccess) { cap = need; P->bytes += need; }
+  return e;
+}
+
+void free_ff_buffers(csff_plan* P) {
+  FFBuffers& b = P->ff;
+  for (void* p : {(void*)b.dg, (void*)b.dxt, (void*)b.dyt, (void*)b.dzt, (void*)b.dT, (void*)b.dal,
+                  (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc})
+    if (p) cudaFree(p);
+  b = FFBuffers{};
+}
+
+csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u, int n_ang,
+                          const double* alpha_host, double2* F, int32_t* F_exp, bool* scaled) {
+  const int d = P->dim;
+  const Level& L = P->lv[0];
+  const int m = L.m;
+  cudaStream_t s = P->stream;
+  FFBuffers& B = P->ff;
+  cudaError_t e;
+  // distinct x-components (bitwise) -> rows of the x-table
+  std::vector<double> ux;
+  std::vector<int> xr(n_ang);
+  std::map<double, int> seen;
+  for (int a = 0; a < n_ang; ++a) {
+    double v = alpha_host[(size_t)a * d];
+    auto it = seen.find(v);
+    if (it == seen.end()) { it = seen.emplace(v, (int)ux.size()).first; ux.push_back(v); }
+    xr[a] = it->second;
+  }
+  const int n_ux = (int)ux.size();
+  const long long R = (d == 3) ? (long long)m * m : m;
+  if ((e = ensure((void**)&B.dg, B.g, sizeof(double2) * (size_t)L.N, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dxt, B.xt, sizeof(double2) * (size_t)n_ux * m, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dyt, B.yt, sizeof(double2) * (size_t)n_ang * m, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dzt, B.zt, sizeof(double2) * (size_t)n_ang * m, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dT, B.T, sizeof(double2) * (size_t)n_ux * R, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dal, B.al, sizeof(double) * (size_t)n_ang * d, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dux, B.ux, sizeof(double) * (size_t)n_ux, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dxr, B.xr, sizeof(int) * (size_t)n_ang, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.ds1, B.s1, sizeof(int) * (size_t)n_ux, P)) != cudaSuccess) {
+    return e == cudaErrorMemoryAllocation ? (set_error("far field: device allocation failed"), CSFF_ERR_OOM)
+                                          : cuda_fail(e, "far field scratch");
+  }
+  if (!B.dmisc) {
+    if ((e = cudaMalloc((void**)&B.dmisc, 4 * sizeof(int))) != cudaSuccess) return cuda_fail(e, "malloc");
+  }
+  // incident-wave tables for eta: U_c[i] = exp(i k eta_c z_i)
+  {
+    std::vector<double2> ut((size_t)d * m);
+    const double cg = std::cos(P->prob.gamma), sg = std::sin(P->prob.gamma);
+    for (int c = 0; c < d; ++c)
+      for (int i = 0; i < m; ++i) {
+        double x = P->prob.box_lo + (double)(i + 1) * L.h;
+        double t = P->prob.k * eta_host[c] * x;   // i k eta_c x e^{i g} = -k sg t + i k cg t
+        double mag = std::exp(-sg * t);
+        ut[(size_t)c * m + i] = make_double2(mag * std::cos(cg * t), mag * std::sin(cg * t));
+      }
+    if ((e = cudaMemcpyAsync(P->uinc_tab, ut.data(), sizeof(double2) * ut.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return cuda_fail(e, "upload incident tables");
+  }
+  if ((e = cudaMemcpyAsync(B.dal, alpha_host, sizeof(double) * (size_t)n_ang * d, cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(B.dux, ux.data(), sizeof(double) * n_ux, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(B.dxr, xr.data(), sizeof(int) * n_ang, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(B.dmisc + 1, 0, sizeof(int), s)) != cudaSuccess)
+    return cuda_fail(e, "upload angles");
+
+  Tabs8 t{};
+  for (int q = 0; q < P->prob.n_gauss; ++q) t.p[q] = P->chi_tab[0] + (size_t)q * d * m;   // finest level
+  dim3 gg((m + 31) / 32, (m + 7) / 8, d == 3 ? m : 1), gb(32, 8);
+  if (d == 2) k_gfield<2><<<gg, gb, 0, s>>>(t, P->prob.n_gauss, P->uinc_tab, u, m, B.dg);
+  else k_gfield<3><<<gg, gb, 0, s>>>(t, P->prob.n_gauss, P->uinc_tab, u, m, B.dg);
+  count_launch();
+  if ((e = launch_max_exp(B.dg, L.N, B.dmisc, s)) != cudaSuccess) return cuda_fail(e, "max exponent");
+  const double sg = std::sin(P->prob.gamma), cg = std::cos(P->prob.gamma);
+  dim3 tg((m + 127) / 128, n_ux + n_ang);
+  k_phase_tables<<<tg, 128, 0, s>>>(B.dux, n_ux, B.dal, n_ang, d, m, P->prob.box_lo, L.h, P->prob.k, sg, cg,
+                                    B.dmisc, B.dxt, B.dyt, B.dzt, B.ds1, B.dmisc + 1);
+  count_launch();
+  dim3 g1((unsigned)((R + S1_BN - 1) / S1_BN), (n_ux + S1_BM - 1) / S1_BM);
+  k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT);
+  count_launch();
+  const double hd = std::pow(L.h, d);
+  const double k2 = P->prob.k * P->prob.k;
+  double2 pref = make_double2(k2 * hd * std::cos(d * P->prob.gamma), k2 * hd * std::sin(d * P->prob.gamma));
+  if (d == 2)
+    k_ff_stage2<2><<<n_ang, 256, 0, s>>>(B.dT, B.dxr, B.ds1, B.dyt, B.dzt, m, pref, F, F_exp, F_exp != nullptr,
+                                         B.dmisc + 1);
+  else
+    k_ff_stage2<3><<<n_ang, 256, 0, s>>>(B.dT, B.dxr, B.ds1, B.dyt, B.dzt, m, pref, F, F_exp, F_exp != nullptr,
+                                         B.dmisc + 1);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "far field kernels");
+  if (scaled) {
+    int flag = 0;
+    if ((e = cudaMemcpyAsync(&flag, B.dmisc + 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "far field flag");
+    *scaled = flag != 0;
+  }
+  return CSFF_OK;
+}
+
+}  // namespace csff

@@ -1,0 +1,458 @@
+// Multigrid kernels on the rotated grid (Sec. 3.2 eq. (csg) with the Sec. 5.2
+// stencil; Sec. 4 V-cycle components).  Templated on the real type (double for
+// the plain and refinement path, float for the inner cycles of the mixed
+// path) and on the dimension.
+//
+// Layout: m^d interior unknowns, x fastest, interleaved complex.  Boundary
+// nodes are not stored (homogeneous Dirichlet).  Grid mapping: block (32, 8)
+// over (x, y), blockIdx.z = z plane in 3D.
+#include "csff_internal.h"
+
+namespace csff {
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+template <int D>
+__device__ __forceinline__ bool thread_point(int m, int& ix, int& iy, int& iz, long long& idx) {
+  ix = blockIdx.x * BX + threadIdx.x;
+  iy = blockIdx.y * BY + threadIdx.y;
+  iz = (D == 3) ? (int)blockIdx.z : 0;
+  if (ix >= m || iy >= m) return false;
+  idx = ((long long)iz * m + iy) * m + ix;
+  return true;
+}
+
+// (A u)_j = c (2d u_j - sum_nbr u) - q_j u_j ; neighbours outside the
+// interior are zero.
+template <typename T, int D>
+__device__ __forceinline__ cx<T> apply_point(const cx<T>* __restrict__ u, cx<T> uj, cx<T> qj, cx<T> c,
+                                             int m, int ix, int iy, int iz, long long idx) {
+  using C = cx<T>;
+  C s = mk<C>(0, 0);
+  if (ix > 0) s = cadd(s, u[idx - 1]);
+  if (ix < m - 1) s = cadd(s, u[idx + 1]);
+  if (iy > 0) s = cadd(s, u[idx - m]);
+  if (iy < m - 1) s = cadd(s, u[idx + m]);
+  if (D == 3) {
+    long long p = (long long)m * m;
+    if (iz > 0) s = cadd(s, u[idx - p]);
+    if (iz < m - 1) s = cadd(s, u[idx + p]);
+  }
+  C t = csub(cscale(uj, (T)(2 * D)), s);
+  return csub(cmul(c, t), cmul(qj, uj));
+}
+
+template <typename T, int D>
+__global__ void k_residual(const cx<T>* __restrict__ u, const cx<T>* __restrict__ b,
+                           const cx<T>* __restrict__ q, cx<T> c, int m, cx<T>* __restrict__ r) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
+  cx<T> au = apply_point<T, D>(u, u[idx], q[idx], c, m, ix, iy, iz, idx);
+  r[idx] = csub(b[idx], au);
+}
+
+template <typename T, int D>
+__global__ void k_jacobi(const cx<T>* __restrict__ u, const cx<T>* __restrict__ b,
+                         const cx<T>* __restrict__ q, const cx<T>* __restrict__ dinv, cx<T> c, T omega,
+                         int m, cx<T>* __restrict__ u_out) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
+  cx<T> uj = u[idx];
+  cx<T> rj = csub(b[idx], apply_point<T, D>(u, uj, q[idx], c, m, ix, iy, iz, idx));
+  u_out[idx] = cadd(uj, cscale(cmul(dinv[idx], rj), omega));
+}
+
+// One colour of red-black Gauss-Seidel, in place.  colour 0 (red) = even sum
+// of node indices (interior index + 1 per axis).
+template <typename T, int D>
+__global__ void k_rbgs(cx<T>* u, const cx<T>* __restrict__ b, const cx<T>* __restrict__ q,
+                       const cx<T>* __restrict__ dinv, cx<T> c, int m, int colour) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
+  if (((ix + iy + iz + D) & 1) != colour) return;
+  cx<T> uj = u[idx];
+  cx<T> rj = csub(b[idx], apply_point<T, D>(u, uj, q[idx], c, m, ix, iy, iz, idx));
+  u[idx] = cadd(uj, cmul(dinv[idx], rj));
+}
+
+// Full weighting: coarse interior P <- sum over offsets o in {-1,0,1}^d of
+// prod(1/2 if o = 0 else 1/4) * r_f[2P + 1 + o].
+template <typename T, int D>
+__global__ void k_restrict(const cx<T>* __restrict__ rf, int mf, cx<T>* __restrict__ bc, int mc) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(mc, ix, iy, iz, idx)) return;
+  using C = cx<T>;
+  C acc = mk<C>(0, 0);
+  const int fx = 2 * ix + 1, fy = 2 * iy + 1, fz = (D == 3) ? 2 * iz + 1 : 0;
+  const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
+#pragma unroll
+  for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz) {
+#pragma unroll
+    for (int oy = -1; oy <= 1; ++oy) {
+      C row = mk<C>(0, 0);
+      long long base = ((long long)(fz + oz) * mf + (fy + oy)) * mf + fx;
+#pragma unroll
+      for (int ox = -1; ox <= 1; ++ox) row = cadd(row, cscale(rf[base + ox], w1[ox + 1]));
+      T wz = (D == 3) ? w1[oz + 1] : (T)1;
+      acc = cadd(acc, cscale(row, w1[oy + 1] * wz));
+    }
+  }
+  bc[idx] = acc;
+}
+
+// Linear interpolation weights of fine interior index p along one axis: node
+// i = p + 1; even i sits on coarse node i/2 (weight 1), odd i between coarse
+// nodes (i-1)/2 and (i+1)/2 (weights 1/2).  Returns the number of coarse
+// interior neighbours (coarse interior index = coarse node - 1).
+template <typename T>
+__device__ __forceinline__ int interp_1d(int p, int mc, int* ci, T* w) {
+  int i = p + 1, n = 0;
+  if ((i & 1) == 0) {
+    int I = i >> 1;
+    if (I >= 1 && I <= mc) { ci[n] = I - 1; w[n] = (T)1; ++n; }
+  } else {
+    int I0 = (i - 1) >> 1, I1 = I0 + 1;
+    if (I0 >= 1 && I0 <= mc) { ci[n] = I0 - 1; w[n] = (T)0.5; ++n; }
+    if (I1 >= 1 && I1 <= mc) { ci[n] = I1 - 1; w[n] = (T)0.5; ++n; }
+  }
+  return n;
+}
+
+template <typename T, int D>
+__global__ void k_prolong_add(const cx<T>* __restrict__ ec, int mc, cx<T>* __restrict__ uf, int mf) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(mf, ix, iy, iz, idx)) return;
+  using C = cx<T>;
+  int cxi[2], cyi[2], czi[2] = {0, 0};
+  T wx[2], wy[2], wz[2] = {(T)1, (T)0};
+  int nx = interp_1d<T>(ix, mc, cxi, wx);
+  int ny = interp_1d<T>(iy, mc, cyi, wy);
+  int nz = (D == 3) ? interp_1d<T>(iz, mc, czi, wz) : 1;
+  C acc = mk<C>(0, 0);
+  for (int a = 0; a < nz; ++a)
+    for (int bq = 0; bq < ny; ++bq) {
+      long long base = ((long long)czi[a] * mc + cyi[bq]) * mc;
+      for (int cq = 0; cq < nx; ++cq) acc = cadd(acc, cscale(ec[base + cxi[cq]], wx[cq] * wy[bq] * wz[a]));
+    }
+  uf[idx] = cadd(uf[idx], acc);
+}
+
+// Coarsest level: u = A_c^{-1} b with the FP64 dense inverse; one CTA.
+template <typename T>
+__global__ void k_coarse_solve(const double2* __restrict__ inv, int N, const cx<T>* __restrict__ b,
+                               cx<T>* __restrict__ u) {
+  extern __shared__ double2 sb[];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = make_double2((double)b[j].x, (double)b[j].y);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double2 acc = make_double2(0, 0);
+    const double2* row = inv + (long long)i * N;
+    for (int j = 0; j < N; ++j) acc = cadd(acc, cmul(row[j], sb[j]));
+    u[i] = mk<cx<T>>((T)acc.x, (T)acc.y);
+  }
+}
+
+// ---- reductions ------------------------------------------------------------
+// Block-wide reduction; the result is valid in thread 0.
+template <typename V, typename Op>
+__device__ __forceinline__ V block_reduce(V v, Op op, V* sh, V identity) {
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  if (w == 0) {
+    v = (l < nw) ? sh[l] : identity;
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+struct AddOp { __device__ double operator()(double a, double b) const { return a + b; } };
+struct MaxIOp { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
+
+constexpr int RED_THREADS = 256;
+
+template <typename T>
+__global__ void k_norm_partial(const cx<T>* __restrict__ v, long long N, double scale,
+                               double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double a = (double)v[i].x * scale, b = (double)v[i].y * scale;
+    acc = fma(a, a, fma(b, b, acc));
+  }
+  acc = block_reduce(acc, AddOp(), sh, 0.0);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void k_norm_finish(const double* __restrict__ partial, int nblk, double inv_scale,
+                              double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += partial[i];
+  acc = block_reduce(acc, AddOp(), sh, 0.0);
+  if (threadIdx.x == 0) *out = sqrt(acc) * inv_scale;
+}
+
+__device__ __forceinline__ int exp_of(double a) {
+  if (a == 0.0) return -2000;
+  if (!isfinite(a)) return 4000;
+  int e;
+  frexp(a, &e);
+  return e;
+}
+
+__global__ void k_max_exp(const double2* __restrict__ v, long long N, int* __restrict__ out) {
+  __shared__ int sh[32];
+  int mx = -2000;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double a = fmax(fabs(v[i].x), fabs(v[i].y));
+    int e = exp_of(a);
+    mx = e > mx ? e : mx;
+  }
+  mx = block_reduce(mx, MaxIOp(), sh, -2000);
+  if (threadIdx.x == 0) atomicMax(out, mx);
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+// ---- coefficients and right-hand side ----------------------------------------
+template <int D>
+__device__ __forceinline__ double2 chi_point(const double2* const* tabs, int n_gauss, int m, int ix,
+                                             int iy, int iz) {
+  double2 chi = make_double2(0, 0);
+  for (int g = 0; g < n_gauss; ++g) {
+    const double2* t = tabs[g];
+    double2 v = cmul(t[ix], t[m + iy]);
+    if (D == 3) v = cmul(v, t[2 * m + iz]);
+    chi = cadd(chi, v);
+  }
+  return chi;
+}
+
+struct TabPtrs { const double2* p[8]; };
+
+template <int D>
+__global__ void k_coefs(TabPtrs tabs, int n_gauss, int m, double k2, double2 c, double2* q64,
+                        double2* dinv64, float2* q32, float2* dinv32) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
+  double2 chi = chi_point<D>(tabs.p, n_gauss, m, ix, iy, iz);
+  double2 q = make_double2(k2 * (1.0 + chi.x), k2 * chi.y);
+  double2 dg = make_double2(2 * D * c.x - q.x, 2 * D * c.y - q.y);
+  double den = dg.x * dg.x + dg.y * dg.y;
+  double2 di = make_double2(dg.x / den, -dg.y / den);
+  q64[idx] = q;
+  dinv64[idx] = di;
+  q32[idx] = make_float2((float)q.x, (float)q.y);
+  dinv32[idx] = make_float2((float)di.x, (float)di.y);
+}
+
+template <int D>
+__global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uinc, int m, double k2,
+                      double2* __restrict__ b) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
+  double2 chi = chi_point<D>(tabs.p, n_gauss, m, ix, iy, iz);
+  double2 ui = cmul(uinc[ix], uinc[m + iy]);
+  if (D == 3) ui = cmul(ui, uinc[2 * m + iz]);
+  b[idx] = cscale(cmul(chi, ui), k2);
+}
+
+// ---- mixed precision ----------------------------------------------------------
+// r32 = r64 * 2^-e with e = exponent of ||r64||_2 (so |r32| < 1 elementwise).
+__global__ void k_to32_scaled(const double2* __restrict__ r, long long N, const double* __restrict__ nrm,
+                              float2* __restrict__ r32, int* __restrict__ exp_out) {
+  int e;
+  frexp(*nrm, &e);
+  double s = ldexp(1.0, -e);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = e;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    r32[i] = make_float2((float)(r[i].x * s), (float)(r[i].y * s));
+}
+
+__global__ void k_update64(double2* __restrict__ u, const float2* __restrict__ e, long long N,
+                           const int* __restrict__ exp_in) {
+  double s = ldexp(1.0, *exp_in);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    u[i].x = fma((double)e[i].x, s, u[i].x);
+    u[i].y = fma((double)e[i].y, s, u[i].y);
+  }
+}
+
+template <typename T>
+__global__ void k_zero(cx<T>* v, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    v[i] = mk<cx<T>>(0, 0);
+}
+
+inline dim3 grid_of(int dim, int m) {
+  return dim3((m + BX - 1) / BX, (m + BY - 1) / BY, dim == 3 ? m : 1);
+}
+inline int flat_blocks(long long N) {
+  long long b = (N + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+#define CSFF_DIM_DISPATCH(dim, KERNEL, ...)                                   \
+  do {                                                                        \
+    if ((dim) == 2) KERNEL<T, 2><<<g, blk, 0, s>>>(__VA_ARGS__);              \
+    else KERNEL<T, 3><<<g, blk, 0, s>>>(__VA_ARGS__);                         \
+  } while (0)
+
+template <typename T> static const cx<T>* qtab(const Level& L);
+template <> const double2* qtab<double>(const Level& L) { return L.q64; }
+template <> const float2* qtab<float>(const Level& L) { return L.q32; }
+template <typename T> static const cx<T>* dtab(const Level& L);
+template <> const double2* dtab<double>(const Level& L) { return L.dinv64; }
+template <> const float2* dtab<float>(const Level& L) { return L.dinv32; }
+
+template <typename T>
+cudaError_t launch_residual(int dim, const Level& L, const cx<T>* u, const cx<T>* b, cx<T>* r,
+                            cudaStream_t s) {
+  dim3 g = grid_of(dim, L.m), blk(BX, BY);
+  cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
+  CSFF_DIM_DISPATCH(dim, k_residual, u, b, qtab<T>(L), c, L.m, r);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jacobi(int dim, const Level& L, double omega, const cx<T>* u, const cx<T>* b,
+                          cx<T>* u_out, cudaStream_t s) {
+  dim3 g = grid_of(dim, L.m), blk(BX, BY);
+  cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
+  CSFF_DIM_DISPATCH(dim, k_jacobi, u, b, qtab<T>(L), dtab<T>(L), c, (T)omega, L.m, u_out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rbgs(int dim, const Level& L, cx<T>* u, const cx<T>* b, cudaStream_t s) {
+  dim3 g = grid_of(dim, L.m), blk(BX, BY);
+  cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
+  CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 0);
+  CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 1);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(int dim, const Level& F, const Level& C, const cx<T>* r, cx<T>* bc,
+                            cudaStream_t s) {
+  dim3 g = grid_of(dim, C.m), blk(BX, BY);
+  CSFF_DIM_DISPATCH(dim, k_restrict, r, F.m, bc, C.m);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx<T>* ec, cx<T>* u,
+                               cudaStream_t s) {
+  dim3 g = grid_of(dim, F.m), blk(BX, BY);
+  CSFF_DIM_DISPATCH(dim, k_prolong_add, ec, C.m, u, F.m);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(const double2* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s) {
+  k_coarse_solve<T><<<1, 256, (size_t)N * sizeof(double2), s>>>(inv, N, b, u);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_norm2(const cx<T>* v, long long N, int exp_scale, double* partial, int nblk,
+                         double* out, cudaStream_t s) {
+  long long need = (N + RED_THREADS - 1) / RED_THREADS;
+  int nb = (int)(need < nblk ? (need < 1 ? 1 : need) : nblk);
+  k_norm_partial<T><<<nb, RED_THREADS, 0, s>>>(v, N, ldexp(1.0, -exp_scale), partial);
+  k_norm_finish<<<1, RED_THREADS, 0, s>>>(partial, nb, ldexp(1.0, exp_scale), out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_exp(const double2* v, long long N, int* out, cudaStream_t s) {
+  k_set_int<<<1, 1, 0, s>>>(out, -2000);
+  k_max_exp<<<flat_blocks(N), RED_THREADS, 0, s>>>(v, N, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coefs(int dim, const Level& L, const double2* const* chi_tab, int n_gauss,
+                         double k2, cudaStream_t s) {
+  TabPtrs t{};
+  for (int i = 0; i < n_gauss; ++i) t.p[i] = chi_tab[i];
+  dim3 g = grid_of(dim, L.m), blk(BX, BY);
+  if (dim == 2)
+    k_coefs<2><<<g, blk, 0, s>>>(t, n_gauss, L.m, k2, L.c, L.q64, L.dinv64, L.q32, L.dinv32);
+  else
+    k_coefs<3><<<g, blk, 0, s>>>(t, n_gauss, L.m, k2, L.c, L.q64, L.dinv64, L.q32, L.dinv32);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(int dim, int m, const double2* const* chi_tab, int n_gauss,
+                       const double2* uinc_tab, double k2, double2* b, cudaStream_t s) {
+  TabPtrs t{};
+  for (int i = 0; i < n_gauss; ++i) t.p[i] = chi_tab[i];
+  dim3 g = grid_of(dim, m), blk(BX, BY);
+  if (dim == 2) k_rhs<2><<<g, blk, 0, s>>>(t, n_gauss, uinc_tab, m, k2, b);
+  else k_rhs<3><<<g, blk, 0, s>>>(t, n_gauss, uinc_tab, m, k2, b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
+                               int* exp_out, cudaStream_t s) {
+  k_to32_scaled<<<flat_blocks(N), 256, 0, s>>>(r, N, norm_dev, r32, exp_out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,
+                            cudaStream_t s) {
+  k_update64<<<flat_blocks(N), 256, 0, s>>>(u, e, N, exp_in);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s) {
+  k_zero<T><<<flat_blocks(N), 256, 0, s>>>(v, N);
+  count_launch();
+  return cudaGetLastError();
+}
+
+#define CSFF_INST(T)                                                                                   \
+  template cudaError_t launch_residual<T>(int, const Level&, const cx<T>*, const cx<T>*, cx<T>*,       \
+                                          cudaStream_t);                                               \
+  template cudaError_t launch_jacobi<T>(int, const Level&, double, const cx<T>*, const cx<T>*, cx<T>*, \
+                                        cudaStream_t);                                                 \
+  template cudaError_t launch_rbgs<T>(int, const Level&, cx<T>*, const cx<T>*, cudaStream_t);         \
+  template cudaError_t launch_restrict<T>(int, const Level&, const Level&, const cx<T>*, cx<T>*,       \
+                                          cudaStream_t);                                               \
+  template cudaError_t launch_prolong_add<T>(int, const Level&, const Level&, const cx<T>*, cx<T>*,    \
+                                             cudaStream_t);                                            \
+  template cudaError_t launch_coarse_solve<T>(const double2*, int, const cx<T>*, cx<T>*, cudaStream_t); \
+  template cudaError_t launch_norm2<T>(const cx<T>*, long long, int, double*, int, double*,            \
+                                       cudaStream_t);                                                  \
+  template cudaError_t launch_zero<T>(cx<T>*, long long, cudaStream_t);
+
+CSFF_INST(double)
+CSFF_INST(float)
+
+}  // namespace csff
