@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Far-field maps/s at 1e-8 relative residual on the 2D 1025x1025 workload.
+
+Workload (one "step"): four far-field maps on [-20,20]^2, rotation pi/6,
+chi = -exp(-|x|^2/4), k in {5, 10, 20, 40}, eta = +x: for each k the
+scattered wave is solved to ||b - A u|| <= 1e-8 ||b|| (FP32 red-black
+Gauss-Seidel V(1,1) cycles inside FP64 iterative refinement, 8 levels, 9x9
+coarsest grid) and its far field evaluated at 720 equispaced outgoing angles.
+Inputs are synthetic (analytic potential and plane waves).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+KS = W.MIXED_2D_KS
+METRIC = "far-field maps/s at 1e-8 residual"
+UNIT = "maps/s"
+WORKLOAD = "2D 1025x1025 on [-20,20]^2, rotation pi/6, chi=-exp(-|x|^2/4), k in {5,10,20,40}, 720 angles"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 FMA throughput of this part, measured with an FMA-loop kernel
+# (0.599e12 DFMA/s over 152 SMs; 2 flops per FMA).
+FP64_PEAK_TFLOPS = 1.198
+
+
+def _cases(precision):
+    out = []
+    for k in KS:
+        c = W.mixed_2d(k)
+        c["opts"]["precision"] = precision
+        c["opts"]["inner_cycles"] = 3
+        out.append(c)
+    return out
+
+
+def _config(args, extra=None):
+    cfg = {"workload": WORKLOAD, "maps_per_step": len(KS), "n": 1025, "levels": 8, "angles": 720,
+           "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
+           "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.result = None
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[2:6]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            self.result = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                           "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(n_angles_sample=18):
+    """One k=5 map: full oracle V-cycle solve to 1e-8 plus the far field at
+    n_angles_sample of the 720 angles; returns seconds per full map (far-field
+    time scaled to 720 angles) and the thread count used."""
+    from oracle import csff_oracle as O
+    c = W.mixed_2d(5.0)
+    p = O.problem_from_dict(c["problem"])
+    o = O.opts_from_dict(c["opts"])
+    t0 = time.perf_counter()
+    res = O.mg_solve(p, O.rhs(p, c["eta"][0]), o)
+    t1 = time.perf_counter()
+    stride = len(c["alphas"]) // n_angles_sample
+    O.far_field(p, res.u, c["eta"][0], c["alphas"][::stride][:n_angles_sample])
+    t2 = time.perf_counter()
+    per_map = (t1 - t0) + (t2 - t1) * len(c["alphas"]) / n_angles_sample
+    return per_map, {"solve_s": t1 - t0, "ff_sample_s": t2 - t1, "cycles": res.cycles}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sample = "one k=5 map: oracle RB-GS V(1,1) solve to 1e-8 + far field at 18 of 720 angles (scaled to 720)"
+    for _ in range(args.warmup):
+        oracle_sample()
+    times = []
+    for _ in range(args.steps):
+        t, _info = oracle_sample()
+        times.append(t)
+    per_map = sum(times) / len(times)
+    value = 1.0 / per_map
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_map * 1e3 * len(KS),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args, {"precision": "fp64 (oracle)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1211_4461_gb300 as csff
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    cases = _cases(args.precision)
+    t0 = time.perf_counter()
+    plans = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in cases]
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    N = plans[0].N
+    us = [torch.zeros(N, dtype=torch.complex128, device=dev) for _ in cases]
+    Fs = [torch.zeros(720, dtype=torch.complex128, device=dev) for _ in cases]
+    Fe = [torch.zeros(720, dtype=torch.int32, device=dev) for _ in cases]
+    # host-side inputs/outputs for the end-to-end measurement, in pinned memory
+    eta_h = [torch.from_numpy(np.ascontiguousarray(c["eta"])).pin_memory() for c in cases]
+    al_h = [torch.from_numpy(np.ascontiguousarray(c["alphas"])).pin_memory() for c in cases]
+    F_h = [torch.zeros(720, dtype=torch.complex128).pin_memory() for _ in cases]
+    Fe_h = [torch.zeros(720, dtype=torch.int32).pin_memory() for _ in cases]
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    infos = {}
+
+    def step(e2e=False):
+        for i, (p, c) in enumerate(zip(plans, cases)):
+            eta = eta_h[i].numpy() if e2e else c["eta"]
+            al = al_h[i].numpy() if e2e else c["alphas"]
+            st, info = p.solve(eta, us[i], ok=(csff.OK,))
+            infos[i] = info[0]
+            p.far_field(eta, us[i], al, Fs[i], Fe[i])
+            if e2e:
+                F_h[i].copy_(Fs[i], non_blocking=True)
+                Fe_h[i].copy_(Fe[i], non_blocking=True)
+        if e2e:
+            torch.cuda.current_stream().synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the launching stream) ----
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = csff.kernel_launches()
+    csff.prof_begin(csff.PROF_FF_CONTRACT)
+    step_ms = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    prof_timed = csff.prof_end()
+    launches = csff.kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = len(KS) * args.steps * world / (total_ms / 1e3)
+
+    # ---- per-family breakdown (one extra profiled step) -----------------------
+    flush.zero_()
+    torch.cuda.synchronize()
+    csff.prof_begin(csff.PROF_FF_CONTRACT | csff.PROF_MG32 | csff.PROF_MG64)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    breakdown = csff.prof_end()
+    breakdown_step_ms = e0.elapsed_time(e1)
+
+    # ---- end to end through the public API with host buffers ----------------
+    for _ in range(2):
+        step(e2e=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(e2e=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = len(KS) * args.steps * world / e2e_s
+    h2d = sum(int(eta_h[i].numel() * 8 + al_h[i].numel() * 8) for i in range(len(cases)))
+    d2h = sum(int(F_h[i].numel() * 16 + Fe_h[i].numel() * 4) for i in range(len(cases)))
+
+    if rank != 0:
+        return
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    ff = prof_timed["ff_contract"]
+    ff_avg_ms = ff["ms"] / max(1, ff["launches"])
+    ff_flops = ff["alg_flops"] / max(1, ff["launches"])
+    achieved_tf = ff_flops / (ff_avg_ms * 1e-3) / 1e12 if ff_avg_ms > 0 else 0.0
+    roofline = {"kernel": "k_ff_stage1 (FP64 far-field contraction)", "bound": "alu",
+                "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA-loop measurement on this GB300 (no FP64 entry in MEASURED_PEAKS.json)",
+                "avg_launch_ms": ff_avg_ms, "launches": ff["launches"],
+                "alg_flops_per_launch": ff_flops}
+    mg32, mg64 = breakdown["mg32"], breakdown["mg64"]
+    cycles = sum(infos[i]["cycles"] for i in infos)
+    vc = {"fp32_kernels_ms": mg32["ms"], "fp32_alg_bytes": mg32["alg_bytes"],
+          "fp32_achieved_gbs": mg32["alg_bytes"] / (mg32["ms"] * 1e-3) / 1e9 if mg32["ms"] else 0.0,
+          "fp64_kernels_ms": mg64["ms"],
+          "fp64_achieved_gbs": mg64["alg_bytes"] / (mg64["ms"] * 1e-3) / 1e9 if mg64["ms"] else 0.0,
+          "hbm_peak_gbs": hbm, "fp32_vcycles_per_step": cycles,
+          "step_ms_profiled": breakdown_step_ms, "ff_contract_ms": breakdown["ff_contract"]["ms"]}
+    vc["fp32_hbm_frac"] = vc["fp32_achieved_gbs"] / hbm
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": _config(args, {"plan_ms": plan_ms}),
+            "roofline": roofline, "vcycle": vc,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk.result,
+            "solve": {str(KS[i]): {"cycles": infos[i]["cycles"], "refinements": infos[i]["refinements"],
+                                   "rel_res": infos[i]["rel_res"]} for i in infos}}
+    if args.cpu_baseline and world == 1:
+        per_map, info = oracle_sample()
+        line["cpu_baseline"] = {"value": 1.0 / per_map, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one k=5 map: oracle RB-GS V(1,1) solve to 1e-8 + far field at 18 "
+                                          "of 720 angles (scaled to 720); numpy, single thread",
+                                "detail": info}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -199,6 +199,30 @@ csff_status csff_norm2(csff_plan* plan, int level, int arith, const void* v_dev,
 /* One V(nu1, nu2) cycle on the finest level, in place on u_dev. */
 csff_status csff_vcycle(csff_plan* plan, int arith, void* u_dev, const void* b_dev);
 
+/* ---- measurement --------------------------------------------------------
+   While recording, the library brackets every launch of the selected kernel
+   families with a pair of CUDA events on the launching stream and adds up
+   the algorithmic bytes (arrays each kernel must read and write; per-point
+   coefficient tables excluded, since they can be rebuilt from O(n) tables)
+   and flops of those launches.  Global to the process, not thread-safe. */
+enum {
+  CSFF_PROF_FF_CONTRACT = 1, /* far-field stage-1 contraction (FP64) */
+  CSFF_PROF_MG32 = 2,        /* multigrid kernels in FP32 */
+  CSFF_PROF_MG64 = 4,        /* multigrid kernels in FP64 (incl. refinement residuals) */
+  CSFF_PROF_FF_OTHER = 8     /* far-field tables, g field, stage 2 */
+};
+#define CSFF_PROF_FAMILIES 4
+typedef struct csff_prof_stats {
+  int launches;
+  double ms;          /* summed event time of the launches */
+  double alg_bytes;   /* summed algorithmic bytes */
+  double alg_flops;   /* summed algorithmic real flops */
+} csff_prof_stats;
+csff_status csff_prof_begin(unsigned family_mask);
+/* Stop recording, wait for the recorded events, write one entry per family
+   (index log2 of the family bit) to out_host[CSFF_PROF_FAMILIES]. */
+csff_status csff_prof_end(csff_prof_stats* out_host);
+
 /* ---- helpers ------------------------------------------------------------ */
 
 /* eq. (thetagamma): gamma = atan(sin theta / (2 + cos theta)). */

@@ -73,6 +73,13 @@ class DescC(C.Structure):
                 ("ill_conditioned", C.c_int), ("below_min_gamma", C.c_int)]
 
 
+class ProfStatsC(C.Structure):
+    _fields_ = [("launches", C.c_int), ("ms", C.c_double), ("alg_bytes", C.c_double), ("alg_flops", C.c_double)]
+
+
+PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER = 1, 2, 4, 8
+PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other")
+
 _vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
 _dp = C.POINTER(C.c_double)
 _SIGS = {
@@ -94,6 +101,8 @@ _SIGS = {
     "csff_status_string": (_cp, [_i]),
     "csff_last_error": (_cp, []),
     "csff_kernel_launches": (C.c_uint64, []),
+    "csff_prof_begin": (_i, [C.c_uint]),
+    "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -123,6 +132,18 @@ def gamma_from_ecs(theta: float) -> float:
 
 def kernel_launches() -> int:
     return int(_lib.csff_kernel_launches())
+
+
+def prof_begin(mask: int) -> None:
+    """Start event-timing the selected kernel families (csff_prof_begin)."""
+    _check(_lib.csff_prof_begin(mask), "prof_begin")
+
+
+def prof_end() -> dict:
+    out = (ProfStatsC * 4)()
+    _check(_lib.csff_prof_end(out), "prof_end")
+    return {PROF_NAMES[i]: {"launches": out[i].launches, "ms": out[i].ms, "alg_bytes": out[i].alg_bytes,
+                            "alg_flops": out[i].alg_flops} for i in range(4)}
 
 
 def _ptr(t):

@@ -23,6 +23,44 @@ csff_status cuda_fail(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? CSFF_ERR_OOM : CSFF_ERR_CUDA;
 }
 
+// ---- kernel-family timing (csff_prof_begin / csff_prof_end) -------------------
+namespace {
+struct ProfRec {
+  int family;
+  cudaEvent_t a, b;
+  double bytes, flops;
+};
+struct ProfState {
+  unsigned mask = 0;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+ProfState g_prof;
+}  // namespace
+
+ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops) : stream(s) {
+  if (!(g_prof.mask & (1u << family))) return;
+  ProfRec r{family, g_prof.get(), g_prof.get(), bytes, flops};
+  if (!r.a || !r.b) return;
+  cudaEventRecord(r.a, s);
+  slot = (int)g_prof.recs.size();
+  g_prof.recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot >= 0) cudaEventRecord(g_prof.recs[slot].b, stream);
+}
+
 }  // namespace csff
 
 namespace {
@@ -345,6 +383,33 @@ const char* csff_status_string(csff_status s) {
 const char* csff_last_error(void) { return csff::t_last_error.c_str(); }
 
 uint64_t csff_kernel_launches(void) { return csff::g_launches.load(); }
+
+csff_status csff_prof_begin(unsigned family_mask) {
+  for (auto& r : csff::g_prof.recs) {
+    csff::g_prof.pool.push_back(r.a);
+    csff::g_prof.pool.push_back(r.b);
+  }
+  csff::g_prof.recs.clear();
+  csff::g_prof.mask = family_mask;
+  return CSFF_OK;
+}
+
+csff_status csff_prof_end(csff_prof_stats* out) {
+  if (!out) return invalid("NULL output");
+  csff::g_prof.mask = 0;
+  std::memset(out, 0, sizeof(csff_prof_stats) * CSFF_PROF_FAMILIES);
+  for (auto& r : csff::g_prof.recs) {
+    CK(cudaEventSynchronize(r.b), "profiling event");
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b), "profiling elapsed time");
+    csff_prof_stats& o = out[r.family];
+    o.launches += 1;
+    o.ms += ms;
+    o.alg_bytes += r.bytes;
+    o.alg_flops += r.flops;
+  }
+  return CSFF_OK;
+}
 
 void csff_plan_destroy(csff_plan* P) {
   if (!P) return;

@@ -93,6 +93,16 @@ csff_status cuda_fail(cudaError_t e, const char* what);
 extern std::atomic<uint64_t> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// Event bracket around the launches of one kernel family (see csff_prof_begin).
+enum ProfFamily { PF_FF_CONTRACT = 0, PF_MG32 = 1, PF_MG64 = 2, PF_FF_OTHER = 3 };
+struct ProfScope {
+  int slot = -1;
+  cudaStream_t stream = nullptr;
+  ProfScope(int family, cudaStream_t s, double bytes, double flops);
+  ~ProfScope();
+};
+template <typename T> constexpr int mg_family() { return sizeof(T) == 8 ? PF_MG64 : PF_MG32; }
+
 // ---- multigrid kernel launchers (mg_kernels.cu) ----------------------------
 template <typename T>
 cudaError_t launch_residual(int dim, const Level& L, const cx<T>* u, const cx<T>* b, cx<T>* r,

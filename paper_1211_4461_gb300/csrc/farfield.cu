@@ -307,7 +307,11 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
                                     B.dmisc, B.dxt, B.dyt, B.dzt, B.ds1, B.dmisc + 1);
   count_launch();
   dim3 g1((unsigned)((R + S1_BN - 1) / S1_BN), (n_ux + S1_BM - 1) / S1_BM);
-  k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT);
+  {
+    ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_ux * m + (double)R * m + (double)n_ux * R),
+                 8.0 * (double)n_ux * (double)R * m);
+    k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT);
+  }
   count_launch();
   const double hd = std::pow(L.h, d);
   const double k2 = P->prob.k * P->prob.k;

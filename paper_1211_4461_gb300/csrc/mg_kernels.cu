@@ -324,6 +324,7 @@ cudaError_t launch_residual(int dim, const Level& L, const cx<T>* u, const cx<T>
                             cudaStream_t s) {
   dim3 g = grid_of(dim, L.m), blk(BX, BY);
   cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
+  ProfScope ps(mg_family<T>(), s, 3.0 * sizeof(cx<T>) * L.N, 0);
   CSFF_DIM_DISPATCH(dim, k_residual, u, b, qtab<T>(L), c, L.m, r);
   count_launch();
   return cudaGetLastError();
@@ -334,6 +335,7 @@ cudaError_t launch_jacobi(int dim, const Level& L, double omega, const cx<T>* u,
                           cx<T>* u_out, cudaStream_t s) {
   dim3 g = grid_of(dim, L.m), blk(BX, BY);
   cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
+  ProfScope ps(mg_family<T>(), s, 3.0 * sizeof(cx<T>) * L.N, 0);
   CSFF_DIM_DISPATCH(dim, k_jacobi, u, b, qtab<T>(L), dtab<T>(L), c, (T)omega, L.m, u_out);
   count_launch();
   return cudaGetLastError();
@@ -343,6 +345,7 @@ template <typename T>
 cudaError_t launch_rbgs(int dim, const Level& L, cx<T>* u, const cx<T>* b, cudaStream_t s) {
   dim3 g = grid_of(dim, L.m), blk(BX, BY);
   cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
+  ProfScope ps(mg_family<T>(), s, 3.0 * sizeof(cx<T>) * L.N, 0);
   CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 0);
   CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 1);
   count_launch(2);
@@ -353,6 +356,7 @@ template <typename T>
 cudaError_t launch_restrict(int dim, const Level& F, const Level& C, const cx<T>* r, cx<T>* bc,
                             cudaStream_t s) {
   dim3 g = grid_of(dim, C.m), blk(BX, BY);
+  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (F.N + C.N), 0);
   CSFF_DIM_DISPATCH(dim, k_restrict, r, F.m, bc, C.m);
   count_launch();
   return cudaGetLastError();
@@ -362,6 +366,7 @@ template <typename T>
 cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx<T>* ec, cx<T>* u,
                                cudaStream_t s) {
   dim3 g = grid_of(dim, F.m), blk(BX, BY);
+  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (2.0 * F.N + C.N), 0);
   CSFF_DIM_DISPATCH(dim, k_prolong_add, ec, C.m, u, F.m);
   count_launch();
   return cudaGetLastError();
@@ -369,6 +374,7 @@ cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx
 
 template <typename T>
 cudaError_t launch_coarse_solve(const double2* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s) {
+  ProfScope ps(mg_family<T>(), s, 2.0 * sizeof(cx<T>) * N + 16.0 * N * N, 8.0 * N * N);
   k_coarse_solve<T><<<1, 256, (size_t)N * sizeof(double2), s>>>(inv, N, b, u);
   count_launch();
   return cudaGetLastError();
@@ -379,6 +385,7 @@ cudaError_t launch_norm2(const cx<T>* v, long long N, int exp_scale, double* par
                          double* out, cudaStream_t s) {
   long long need = (N + RED_THREADS - 1) / RED_THREADS;
   int nb = (int)(need < nblk ? (need < 1 ? 1 : need) : nblk);
+  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * N, 0);
   k_norm_partial<T><<<nb, RED_THREADS, 0, s>>>(v, N, ldexp(1.0, -exp_scale), partial);
   k_norm_finish<<<1, RED_THREADS, 0, s>>>(partial, nb, ldexp(1.0, exp_scale), out);
   count_launch(2);
@@ -418,6 +425,7 @@ cudaError_t launch_rhs(int dim, int m, const double2* const* chi_tab, int n_gaus
 
 cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
                                int* exp_out, cudaStream_t s) {
+  ProfScope ps(PF_MG64, s, 24.0 * N, 0);
   k_to32_scaled<<<flat_blocks(N), 256, 0, s>>>(r, N, norm_dev, r32, exp_out);
   count_launch();
   return cudaGetLastError();
@@ -425,6 +433,7 @@ cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm
 
 cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,
                             cudaStream_t s) {
+  ProfScope ps(PF_MG64, s, 40.0 * N, 0);
   k_update64<<<flat_blocks(N), 256, 0, s>>>(u, e, N, exp_in);
   count_launch();
   return cudaGetLastError();
@@ -432,6 +441,7 @@ cudaError_t launch_update64(double2* u, const float2* e, long long N, const int*
 
 template <typename T>
 cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s) {
+  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * N, 0);
   k_zero<T><<<flat_blocks(N), 256, 0, s>>>(v, N);
   count_launch();
   return cudaGetLastError();
