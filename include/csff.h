@@ -199,6 +199,27 @@ csff_status csff_norm2(csff_plan* plan, int level, int arith, const void* v_dev,
 /* One V(nu1, nu2) cycle on the finest level, in place on u_dev. */
 csff_status csff_vcycle(csff_plan* plan, int arith, void* u_dev, const void* b_dev);
 
+/* Allocation-free Euclidean norm.  The paper has no counterpart: this is a
+   service for callers that cannot allocate device memory (memory owned by
+   another allocator, or loops that must not pay cudaMalloc's implicit device
+   synchronisation).  Needs no plan and calls no cudaMalloc/cudaFree.
+     *out_dev (device double) = 2^exp_scale * sqrt(sum |v_j 2^-exp_scale|^2)
+   over n complex values v_dev (c128 for CSFF_ARITH_FP64, c64 for FP32),
+   accumulated in FP64; enqueued on `stream` (a cudaStream_t, NULL = legacy
+   default), nothing is synchronised.  exp_scale in [-1000, 1000] guards the
+   squares against overflow (pass 0 for ordinary magnitudes).
+   Scratch: a fixed 32 KiB device array inside the library (4096 per-block
+   partial sums), held by every GPU that loads the library until exit;
+   n is limited to 33554432 (2^25) values, larger n returns
+   CSFF_ERR_INVALID_ARG with a message.  All calls share that array: calls
+   whose work overlaps on the GPU (different streams, or different host
+   threads on one device) race and give wrong results; serialise them.
+   The first call on each device looks up the array's device address
+   (cudaGetSymbolAddress, with that device current); make that first call
+   before any stream capture. */
+csff_status csff_norm2_noalloc(int arith, const void* v_dev, long long n, int exp_scale, double* out_dev,
+                               void* stream);
+
 /* ---- measurement --------------------------------------------------------
    While recording, the library brackets every launch of the selected kernel
    families with a pair of CUDA events on the launching stream and adds up

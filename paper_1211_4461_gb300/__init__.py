@@ -101,6 +101,7 @@ _SIGS = {
     "csff_status_string": (_cp, [_i]),
     "csff_last_error": (_cp, []),
     "csff_kernel_launches": (C.c_uint64, []),
+    "csff_norm2_noalloc": (_i, [_i, _vp, C.c_longlong, _i, _vp, _vp]),
     "csff_prof_begin": (_i, [C.c_uint]),
     "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
 }
@@ -144,6 +145,18 @@ def prof_end() -> dict:
     _check(_lib.csff_prof_end(out), "prof_end")
     return {PROF_NAMES[i]: {"launches": out[i].launches, "ms": out[i].ms, "alg_bytes": out[i].alg_bytes,
                             "alg_flops": out[i].alg_flops} for i in range(4)}
+
+
+NOALLOC_MAX_N = 1 << 25
+
+
+def norm2_noalloc(v, out, exp_scale=0, stream=None) -> None:
+    """csff_norm2_noalloc: ||v||_2 into the device double `out` without any
+    device allocation (fixed scratch inside the library; see include/csff.h)."""
+    import torch
+    arith = ARITH_FP64 if v.dtype == torch.complex128 else ARITH_FP32
+    _check(_lib.csff_norm2_noalloc(arith, _ptr(v), v.numel(), int(exp_scale), _ptr(out), _stream_handle(stream)),
+           "norm2_noalloc")
 
 
 def _ptr(t):
