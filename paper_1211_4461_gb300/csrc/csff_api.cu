@@ -48,8 +48,11 @@ struct ProfState {
 ProfState g_prof;
 }  // namespace
 
+bool g_capturing = false;
+unsigned prof_mask() { return g_prof.mask; }
+
 ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops) : stream(s) {
-  if (!(g_prof.mask & (1u << family))) return;
+  if (g_capturing || !(g_prof.mask & (1u << family))) return;
   ProfRec r{family, g_prof.get(), g_prof.get(), bytes, flops};
   if (!r.a || !r.b) return;
   cudaEventRecord(r.a, s);
@@ -300,44 +303,128 @@ struct Tracker {
   }
 };
 
-// FP64 V-cycles on the finest level: u (c128, N) solves A u = b64 (level-0 plan buffer).
-csff_status solve_fp64(csff_plan* P, double2* u, int eb, double nb, csff_info* info) {
+// One V-cycle at the finest level: the fused 2D V(1,1) RB-GS kernels when the
+// plan qualifies, else the general per-step kernels.  zero_init: the iterate
+// enters as zero (the correction equation of a refinement step).
+template <typename T>
+csff_status run_vcycle(csff_plan* P, cx<T>* u, const cx<T>* b, bool zero_init) {
+  cudaStream_t s = P->stream;
+  const int lc = P->fused_lc;
+  if (lc < 1) {
+    if (zero_init) CK(csff::launch_zero<T>(u, P->lv[0].N, s), "zero");
+    return vcycle<T>(P, 0, u, b);
+  }
+  for (int l = 0; l < lc; ++l) {
+    Level& F = P->lv[l];
+    Level& C = P->lv[l + 1];
+    const cx<T>* in = (l == 0) ? u : ubuf<T>(F);
+    const cx<T>* bl = (l == 0) ? b : bbuf<T>(F);
+    CK(csff::launch_down2<T>(F, C, in, zero_init || l > 0, bl, tbuf<T>(F), bbuf<T>(C), s), "fused down");
+  }
+  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, P->coarse_inv, bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
+     "coarse levels");
+  for (int l = lc - 1; l >= 0; --l) {
+    Level& F = P->lv[l];
+    Level& C = P->lv[l + 1];
+    cx<T>* out = (l == 0) ? u : ubuf<T>(F);
+    const cx<T>* bl = (l == 0) ? b : bbuf<T>(F);
+    CK(csff::launch_up2<T>(F, C, tbuf<T>(F), ubuf<T>(C), bl, out, s), "fused up");
+  }
+  return CSFF_OK;
+}
+
+// Body of one solver step on P->stream (eagerly or under capture): the
+// finest-level norm of the new residual ends in red_host[0].
+csff_status step_fp64(csff_plan* P, int eb) {
   Level& L = P->lv[0];
+  CS(run_vcycle<double>(P, L.u64, L.b64, false));
+  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, P->stream), "residual");
+  CS(norm64(P, L.r64, eb, 0));
+  CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, P->stream), "read norm");
+  return CSFF_OK;
+}
+
+csff_status step_mixed(csff_plan* P, int eb) {
+  Level& L = P->lv[0];
+  cudaStream_t s = P->stream;
+  int* ex = reinterpret_cast<int*>(P->red_out + 4);
+  const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
+  CK(csff::launch_to32_scaled(L.r64, L.N, P->red_out, L.b32, ex, s), "scale");
+  for (int c = 0; c < inner; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
+  CK(csff::launch_update64(L.u64, L.u32, L.N, ex, s), "update");
+  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
+  CS(norm64(P, L.r64, eb, 0));
+  CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s), "read norm");
+  return CSFF_OK;
+}
+
+// Run one step: replay the captured graph (capturing it first if the key
+// changed), or eagerly while kernel families of the solver are being timed.
+csff_status run_step(csff_plan* P, long long key, csff_status (*body)(csff_plan*, int), int eb) {
+  const unsigned mg_bits = CSFF_PROF_MG32 | CSFF_PROF_MG64;
+  if (!P->use_graphs || !P->gstream || (csff::prof_mask() & mg_bits)) {
+    CS(body(P, eb));
+    CK(cudaStreamSynchronize(P->stream), "sync");
+    return CSFF_OK;
+  }
+  if (!P->gexec || P->gkey != key) {
+    if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+    CK(cudaStreamBeginCapture(P->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    const uint64_t before = csff::g_launches.load();
+    cudaStream_t saved = P->stream;
+    P->stream = P->gstream;
+    csff::g_capturing = true;
+    csff_status st = body(P, eb);
+    csff::g_capturing = false;
+    P->stream = saved;
+    // kernels recorded in the graph: counted again on every replay below
+    P->gkernels = csff::g_launches.load() - before;
+    csff::g_launches.fetch_sub(P->gkernels);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(P->gstream, &graph);
+    if (st != CSFF_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return csff::cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&P->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { P->gexec = nullptr; return csff::cuda_fail(e, "instantiate graph"); }
+    P->gkey = key;
+  }
+  CK(cudaEventRecord(P->gev, P->stream), "event");
+  CK(cudaStreamWaitEvent(P->gstream, P->gev, 0), "wait event");
+  CK(cudaGraphLaunch(P->gexec, P->gstream), "graph launch");
+  csff::count_launch((int)P->gkernels);
+  CK(cudaStreamSynchronize(P->gstream), "sync");
+  return CSFF_OK;
+}
+
+// FP64 V-cycles on the finest level (iterate in the plan's u64, rhs in b64).
+csff_status solve_fp64(csff_plan* P, int eb, double nb, csff_info* info) {
   Tracker tr;
   tr.start(info);
   int cycles = 0;
+  const long long key = (1ll << 40) + (long long)(eb + 8192);
   for (;;) {
-    CS(vcycle<double>(P, 0, u, L.b64));
+    CS(run_step(P, key, step_fp64, eb));
     ++cycles;
-    CK(csff::launch_residual<double>(P->dim, L, u, L.b64, L.r64, P->stream), "residual");
-    CS(norm64(P, L.r64, eb, 0));
-    CS(read_scalars(P, 1));
     int st = tr.push(P->red_host[0] / nb, cycles, 0, P->opts.rel_tol, P->opts.max_cycles);
     if (st >= 0) return (csff_status)st;
   }
 }
 
 // FP64 residual, FP32 V-cycles on the scaled correction equation, FP64 update.
-csff_status solve_mixed(csff_plan* P, double2* u, int eb, double nb, csff_info* info) {
+csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
   Level& L = P->lv[0];
-  cudaStream_t s = P->stream;
-  int* ex = reinterpret_cast<int*>(P->red_out + 4);
   Tracker tr;
   tr.start(info);
   int cycles = 0, refinements = 0;
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
-  CK(csff::launch_residual<double>(P->dim, L, u, L.b64, L.r64, s), "residual");
+  const long long key = (2ll << 40) + (long long)(eb + 8192) * 64 + inner;
+  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, P->stream), "residual");
   CS(norm64(P, L.r64, eb, 0));
   for (;;) {
-    CK(csff::launch_to32_scaled(L.r64, L.N, P->red_out, L.b32, ex, s), "scale");
-    CK(csff::launch_zero<float>(L.u32, L.N, s), "zero");
-    for (int c = 0; c < inner; ++c) CS(vcycle<float>(P, 0, L.u32, L.b32));
+    CS(run_step(P, key, step_mixed, eb));
     cycles += inner;
     ++refinements;
-    CK(csff::launch_update64(u, L.u32, L.N, ex, s), "update");
-    CK(csff::launch_residual<double>(P->dim, L, u, L.b64, L.r64, s), "residual");
-    CS(norm64(P, L.r64, eb, 0));
-    CS(read_scalars(P, 1));
     int st = tr.push(P->red_host[0] / nb, cycles, refinements, P->opts.rel_tol, P->opts.max_cycles);
     if (st >= 0) return (csff_status)st;
   }
@@ -425,6 +512,9 @@ void csff_plan_destroy(csff_plan* P) {
   if (P->red_out) cudaFree(P->red_out);
   if (P->red_host) cudaFreeHost(P->red_host);
   csff::free_ff_buffers(P);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->gstream) cudaStreamDestroy(P->gstream);
+  if (P->gev) cudaEventDestroy(P->gev);
   delete P;
 }
 
@@ -519,6 +609,24 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
     e = cudaMallocHost((void**)&P->red_host, 16 * sizeof(double));
     if (e != cudaSuccess) return fail(csff::cuda_fail(e, "pinned host buffer"));
   }
+  // fused V(1,1) RB-GS path (2D): the levels from the first with n <= 33 run in
+  // one CTA; at least one fused fine level is needed
+  if (d == 2 && opts->smoother == CSFF_SMOOTHER_RBGS && opts->nu1 == 1 && opts->nu2 == 1) {
+    int lc = -1;
+    for (int l = 0; l < (int)P->lv.size(); ++l)
+      if (P->lv[l].n <= 33) { lc = l; break; }
+    if (lc < 0) lc = (int)P->lv.size() - 1;
+    if (lc >= 1 && csff::coarse_levels_smem(d, P->lv, lc, 8) <= 200 * 1024) {
+      cudaError_t e = csff::prepare_fused(d, P->lv, lc);
+      if (e != cudaSuccess) return fail(csff::cuda_fail(e, "fused kernel attributes"));
+      P->fused_lc = lc;
+    }
+  }
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->gev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(csff::cuda_fail(e, "graph stream"));
+  }
   // conditioning estimates (single Gaussian on the axis of eta, Sec. 3.3's
   // warning about products of growing and decaying factors)
   {
@@ -607,10 +715,14 @@ csff_status csff_solve(csff_plan* P, int n_rhs, const double* eta, void* u_dev, 
       CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
       if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
       st = CSFF_OK;
-    } else if (P->opts.precision == CSFF_PREC_FP64) {
-      st = solve_fp64(P, u, eb, nb, in);
     } else {
-      st = solve_mixed(P, u, eb, nb, in);
+      if (use_guess)
+        CK(cudaMemcpyAsync(L.u64, u, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
+      else
+        CK(csff::launch_zero<double>(L.u64, L.N, P->stream), "zero");
+      st = (P->opts.precision == CSFF_PREC_FP64) ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in);
+      if (st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)
+        CK(cudaMemcpyAsync(u, L.u64, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
     }
     if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;
     if (in) in->status = st;
@@ -709,8 +821,8 @@ csff_status csff_norm2(csff_plan* P, int level, int arith, const void* v, double
 csff_status csff_vcycle(csff_plan* P, int arith, void* u, const void* b) {
   CS(check_level(P, 0, arith));
   if (!u || !b) return invalid("NULL buffer");
-  if (arith == CSFF_ARITH_FP64) return vcycle<double>(P, 0, (double2*)u, (const double2*)b);
-  return vcycle<float>(P, 0, (float2*)u, (const float2*)b);
+  if (arith == CSFF_ARITH_FP64) return run_vcycle<double>(P, (double2*)u, (const double2*)b, false);
+  return run_vcycle<float>(P, (float2*)u, (const float2*)b, false);
 }
 
 }  // extern "C"

@@ -83,6 +83,16 @@ struct csff_plan {
   csff::FFBuffers ff;
   size_t bytes = 0;
   double log_rhs_max = 0, log_ff_max = 0;
+  // fused V(1,1) RB-GS path (2D): levels >= fused_lc run in one CTA; -1 = unfused
+  int fused_lc = -1;
+  // CUDA graph of one solver step (FP64 cycle or mixed refinement step),
+  // captured on an internal stream; re-captured when its key changes
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long gkey = 0;
+  uint64_t gkernels = 0;          // kernel nodes in the captured graph
+  bool use_graphs = true;
 };
 
 namespace csff {
@@ -137,6 +147,26 @@ cudaError_t launch_update64(double2* u, const float2* e, long long N, const int*
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
+
+// ---- fused 2D V(1,1) RB-GS kernels (mg_fused.cu) ----------------------------
+size_t fused_down_smem(int real_bytes);
+size_t fused_up_smem(int real_bytes);
+size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int real_bytes);
+template <typename T>
+cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, bool zero_init, const cx<T>* b,
+                         cx<T>* u_out, cx<T>* bc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
+                       cx<T>* u_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const double2* inv, const cx<T>* b,
+                                 cx<T>* u, cudaStream_t s);
+// dynamic shared-memory opt-in of the fused kernels on the current device
+cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc);
+// true while a graph is being captured (profiling brackets are suppressed)
+extern bool g_capturing;
+// kernel families currently timed (csff_prof_begin mask)
+unsigned prof_mask();
 
 // ---- far field (farfield.cu) -----------------------------------------------
 void free_ff_buffers(csff_plan* P);

@@ -95,33 +95,28 @@ __global__ void k_phase_tables(const double* __restrict__ ux, int n_ux, const do
 }
 
 // Stage 1: T[k][rho] = sum_i X[k][i] G[rho][i]   (complex, FP64).
-// Block tile 32 (k) x 64 (rho), K step 16; 256 threads, 2 x 4 outputs each.
-constexpr int S1_BM = 32, S1_BN = 64, S1_BK = 16;
+// FP64 FMA throughput (about 2 per SM per clock) bounds this kernel, so the
+// tiles are small (16 rows x 32 columns, K step 16; 2 outputs per thread) to
+// give several CTAs per SM and a short last wave.
+constexpr int S1_BM = 16, S1_BN = 32, S1_BK = 16;
 
 __global__ void __launch_bounds__(256) k_ff_stage1(const double2* __restrict__ X, int M,
                                                    const double2* __restrict__ G, int N, int K,
                                                    double2* __restrict__ T) {
   __shared__ double2 As[S1_BK][S1_BM];
-  __shared__ double2 Bs[S1_BK][S1_BN];
+  __shared__ double2 Bs[S1_BK][S1_BN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;     // tx: rho group (4), ty: k group (2)
+  const int tx = tid & 15, ty = tid >> 4;     // tx: column pair, ty: row
   const int m0 = blockIdx.y * S1_BM, n0 = blockIdx.x * S1_BN;
-  double2 acc[2][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = make_double2(0, 0);
-
+  double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
   for (int k0 = 0; k0 < K; k0 += S1_BK) {
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {          // A tile: 32 x 16
-      int e = tid + l * 256;
-      int r = e >> 4, kk = e & 15;
+    {                                        // A tile: 16 x 16
+      int r = tid >> 4, kk = tid & 15;
       int gm = m0 + r, gk = k0 + kk;
       As[kk][r] = (gm < M && gk < K) ? X[(long long)gm * K + gk] : make_double2(0, 0);
     }
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {          // B tile: 64 x 16
+    for (int l = 0; l < 2; ++l) {            // B tile: 32 x 16
       int e = tid + l * 256;
       int r = e >> 4, kk = e & 15;
       int gn = n0 + r, gk = k0 + kk;
@@ -130,27 +125,20 @@ __global__ void __launch_bounds__(256) k_ff_stage1(const double2* __restrict__ X
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < S1_BK; ++kk) {
-      double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        double2 bv = Bs[kk][tx * 4 + b];
-        acc[0][b].x = fma(a0.x, bv.x, fma(-a0.y, bv.y, acc[0][b].x));
-        acc[0][b].y = fma(a0.x, bv.y, fma(a0.y, bv.x, acc[0][b].y));
-        acc[1][b].x = fma(a1.x, bv.x, fma(-a1.y, bv.y, acc[1][b].x));
-        acc[1][b].y = fma(a1.x, bv.y, fma(a1.y, bv.x, acc[1][b].y));
-      }
+      double2 a = As[kk][ty];
+      double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc0.x = fma(a.x, b0.x, fma(-a.y, b0.y, acc0.x));
+      acc0.y = fma(a.x, b0.y, fma(a.y, b0.x, acc0.y));
+      acc1.x = fma(a.x, b1.x, fma(-a.y, b1.y, acc1.x));
+      acc1.y = fma(a.x, b1.y, fma(a.y, b1.x, acc1.y));
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    int gm = m0 + ty * 2 + a;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int gn = n0 + tx * 4 + b;
-      if (gn < N) T[(long long)gm * N + gn] = acc[a][b];
-    }
+  int gm = m0 + ty;
+  if (gm < M) {
+    int gn = n0 + tx * 2;
+    if (gn < N) T[(long long)gm * N + gn] = acc0;
+    if (gn + 1 < N) T[(long long)gm * N + gn + 1] = acc1;
   }
 }
 
@@ -245,7 +233,10 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   cudaStream_t s = P->stream;
   FFBuffers& B = P->ff;
   cudaError_t e;
-  // distinct x-components (bitwise) -> rows of the x-table
+  // distinct x-components (bitwise) -> rows of the x-table.  (Pairing +a
+  // with -a through even/odd parts of g would halve the work but multiplies
+  // e^{+k sin(gamma) a |x|} with the large upstream g; the cross terms exceed
+  // the sum by up to e^{2 k sin(gamma) a R}, so the plain form is kept.)
   std::vector<double> ux;
   std::vector<int> xr(n_ang);
   std::map<double, int> seen;
@@ -256,16 +247,17 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
     xr[a] = it->second;
   }
   const int n_ux = (int)ux.size();
+  const int n_trow = n_ux;
   const long long R = (d == 3) ? (long long)m * m : m;
   if ((e = ensure((void**)&B.dg, B.g, sizeof(double2) * (size_t)L.N, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dxt, B.xt, sizeof(double2) * (size_t)n_ux * m, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dyt, B.yt, sizeof(double2) * (size_t)n_ang * m, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dzt, B.zt, sizeof(double2) * (size_t)n_ang * m, P)) != cudaSuccess ||
-      (e = ensure((void**)&B.dT, B.T, sizeof(double2) * (size_t)n_ux * R, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dT, B.T, sizeof(double2) * (size_t)n_trow * R, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dal, B.al, sizeof(double) * (size_t)n_ang * d, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dux, B.ux, sizeof(double) * (size_t)n_ux, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dxr, B.xr, sizeof(int) * (size_t)n_ang, P)) != cudaSuccess ||
-      (e = ensure((void**)&B.ds1, B.s1, sizeof(int) * (size_t)n_ux, P)) != cudaSuccess) {
+      (e = ensure((void**)&B.ds1, B.s1, sizeof(int) * (size_t)n_trow, P)) != cudaSuccess) {
     return e == cudaErrorMemoryAllocation ? (set_error("far field: device allocation failed"), CSFF_ERR_OOM)
                                           : cuda_fail(e, "far field scratch");
   }

@@ -44,7 +44,13 @@ def cases():
     c2b = W.small_2d(n=65)
     c2b["problem"]["gaussians"] = [W.gauss(-0.3 - 0.05j, 2.0, (0.5, -0.3, 0.0)), W.gauss(-0.2, 1.0, (-0.5, 0.5, 0.0))]
     c2b["name"] = "2d-n65-two-gaussians"
-    return [c2, c2b, c3]
+    # red-black V(1,1) in 2D runs the fused kernels (levels >= 33^2 in one CTA)
+    c2r = W.mixed_2d(5.0, n=129)
+    c2r["problem"]["hi"], c2r["problem"]["lo"] = 12.0, -12.0
+    c2r["opts"].update(coarsest_n=5, rel_tol=1e-10)
+    c2r["name"] = "2d-n129-rbgs-fused"
+    c2s = dict(c2r, name="2d-n65-rbgs-fused", problem=dict(c2r["problem"], n=65))
+    return [c2, c2b, c3, c2r, c2s]
 
 
 CASES = cases()
@@ -166,6 +172,20 @@ def test_vcycle_fp64(setup):
     assert np.abs(host(ut, shp) - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
+def test_vcycle_fp32(setup):
+    """FP32 V-cycle against the FP64 oracle cycle from the same FP32-rounded inputs."""
+    c, plan, p, levels = setup
+    oo = O.opts_from_dict(c["opts"])
+    lu = O.coarse_factor(levels[-1])
+    shp = (levels[0].m,) * p.dim
+    u0 = W.rand_complex(shp, 902).astype(np.complex64).astype(np.complex128)
+    b = W.rand_complex(shp, 903, scale=20.0).astype(np.complex64).astype(np.complex128)
+    ut = dev(u0, torch.complex64)
+    plan.vcycle(ut, dev(b, torch.complex64))
+    ref = O.vcycle(levels, lu, 0, u0, b, oo)
+    assert np.abs(host(ut, shp) - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
 def test_solve_fp64_history_and_far_field(setup):
     """Per-cycle residual history, cycle count, solution and far-field map."""
     c, plan, p, levels = setup
@@ -186,6 +206,26 @@ def test_solve_fp64_history_and_far_field(setup):
     # far field from the same solution: rounding-level agreement
     Fs = O.far_field_value(*O.far_field(p, ug, eta[0], al))
     assert np.linalg.norm(F.cpu().numpy() - Fs) <= 1e-12 * np.linalg.norm(Fs)
+
+
+@pytest.mark.parametrize("lo,hi", [(-10.0, 10.0), (-9.0, 11.0)], ids=["symmetric-box", "shifted-box"])
+def test_far_field_on_symmetric_and_shifted_boxes(csff, lo, hi):
+    """Far field on a box symmetric about 0 and on a shifted one against the
+    oracle on the same solution, with outgoing directions that include
+    unpaired x-components."""
+    c = W.small_2d(n=65)
+    c["problem"]["lo"], c["problem"]["hi"] = lo, hi
+    plan = csff.Plan(c["problem"], c["opts"])
+    p = O.problem_from_dict(c["problem"])
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    plan.solve(c["eta"], u)
+    ug = host(u, (p.m,) * 2)
+    al = np.vstack([c["alphas"][::7], W.angle_set_2d(13)])
+    F = torch.zeros(len(al), dtype=torch.complex128, device="cuda")
+    plan.far_field(c["eta"], u, al, F)
+    m, e2, tn = O.far_field(p, ug, c["eta"][0], al, return_terms_norm=True)
+    Fo = O.far_field_value(m, e2)
+    assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-13 * (tn * 2.0 ** e2).max()
 
 
 def test_rhs(setup):

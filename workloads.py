@@ -27,18 +27,29 @@ def problem(dim, n, R, gamma, k, gaussians):
 
 
 def angle_set_2d(n_ang):
-    """alpha_a = (cos t_a, sin t_a), t_a = 2 pi a / n_ang."""
-    t = 2 * np.pi * np.arange(n_ang) / n_ang
-    return np.ascontiguousarray(np.stack([np.cos(t), np.sin(t)], axis=1))
+    """alpha_a = (cos t_a, sin t_a), t_a = 2 pi a / n_ang, generated so that
+    mirror images t and 2 pi - t are exact (same cosine bit for bit, sines of
+    opposite sign)."""
+    a = np.arange(n_ang)
+    mirror = a > n_ang // 2
+    j = np.where(mirror, n_ang - a, a)
+    t = 2 * np.pi * j / n_ang
+    s = np.where(mirror, -np.sin(t), np.sin(t))
+    return np.ascontiguousarray(np.stack([np.cos(t), s], axis=1))
 
 
 def angle_set_3d(n_phi, n_theta):
     """phi_i = 2 pi i / n_phi, theta_j = pi (j + 1/2) / n_theta (midpoints, no
     poles); row a = j * n_phi + i."""
-    ph = 2 * np.pi * np.arange(n_phi) / n_phi
+    i = np.arange(n_phi)
+    mirror = i > n_phi // 2
+    j = np.where(mirror, n_phi - i, i)
+    ph = 2 * np.pi * j / n_phi                 # phi and 2 pi - phi exact mirror images
+    sgn = np.where(mirror, -1.0, 1.0)
     th = np.pi * (np.arange(n_theta) + 0.5) / n_theta
     T, P = np.meshgrid(th, ph, indexing="ij")
-    out = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], axis=-1)
+    S = np.broadcast_to(sgn, T.shape)
+    out = np.stack([np.sin(T) * np.cos(P), S * np.sin(T) * np.sin(P), np.cos(T)], axis=-1)
     return np.ascontiguousarray(out.reshape(-1, 3))
 
 
