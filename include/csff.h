@@ -199,6 +199,47 @@ csff_status csff_norm2(csff_plan* plan, int level, int arith, const void* v_dev,
 /* One V(nu1, nu2) cycle on the finest level, in place on u_dev. */
 csff_status csff_vcycle(csff_plan* plan, int arith, void* u_dev, const void* b_dev);
 
+/* ---- batched solve: many uneven 2D problems in one persistent launch ----
+   Each instance is solved as by csff_solve with CSFF_PREC_MIXED (FP64
+   residual, FP32 V(1,1) red-black cycles on the scaled correction, FP64
+   update; Sec. 4 with the refinement loop), but all instances advance inside
+   one cooperative kernel whose phases are separated by grid barriers; the
+   tiles of every active instance are shared out among the CTAs, convergence
+   is decided per instance on the device.  The solve is captured once as a
+   CUDA graph and replayed.  Barrier waits are bounded: a wait that runs out
+   ends the kernel with CSFF_ERR_TIMEOUT (no trap, no hang).
+   Requirements: dim = 2, red-black GS, nu1 = nu2 = 1, precision MIXED,
+   n >= 65, at most 12 levels; otherwise CSFF_ERR_UNSUPPORTED. */
+typedef struct csff_batch csff_batch;
+/* probs: n_inst problems (host, copied); opts: shared by all instances. */
+csff_status csff_batch_create(int n_inst, const csff_problem* probs, const csff_opts* opts, void* stream,
+                              csff_batch** out);
+void csff_batch_destroy(csff_batch* batch);
+/* eta_host: n_inst x 2 incident directions; infos_host: n_inst reports or NULL.
+   Synchronises.  Returns the worst instance status. */
+csff_status csff_batch_solve(csff_batch* batch, const double* eta_host, csff_info* infos_host);
+/* Device pointer (c128, m_i^2) to instance i's solution of the last solve;
+   owned by the batch, valid until the next solve. */
+csff_status csff_batch_solution(const csff_batch* batch, int i, const void** u_dev);
+/* Copy of instance i's solution into the caller's u_out_dev (c128, m_i^2);
+   synchronises the batch's stream. */
+csff_status csff_batch_copy_solution(const csff_batch* batch, int i, void* u_out_dev);
+/* Far-field map of every instance (as csff_far_field): n_ang[i] directions
+   alpha_host[i] (host, n_ang[i] x 2) into F_dev[i] (c128) and, if F_exp_dev
+   is not NULL, the exponents F_exp_dev[i] (int32). */
+csff_status csff_batch_far_field(csff_batch* batch, const double* eta_host, const int* n_ang,
+                                 const double* const* alpha_host, void* const* F_dev, int32_t* const* F_exp_dev);
+/* Autotuner: times the persistent solve for each tile size of the large
+   levels (16 or 8 coarse points per tile side) and each CTA count per SM the
+   occupancy allows, keeps the fastest; chosen values returned if non-NULL. */
+csff_status csff_batch_autotune(csff_batch* batch, const double* eta_host, int* tc_big_out, int* ctas_per_sm_out);
+
+/* Test hook for the bounded barrier: extra_arrivals = 1 makes every grid
+   barrier of the next solves wait for one CTA that does not exist, so each
+   wait runs out after spin_limit polls (0 = the default limit of 2^26 polls
+   of ~64 ns) and the solve returns CSFF_ERR_TIMEOUT; 0 restores normal runs. */
+csff_status csff_batch_debug_barrier(csff_batch* batch, int extra_arrivals, long long spin_limit);
+
 /* Allocation-free Euclidean norm.  The paper has no counterpart: this is a
    service for callers that cannot allocate device memory (memory owned by
    another allocator, or loops that must not pay cudaMalloc's implicit device

@@ -102,6 +102,14 @@ _SIGS = {
     "csff_last_error": (_cp, []),
     "csff_kernel_launches": (C.c_uint64, []),
     "csff_norm2_noalloc": (_i, [_i, _vp, C.c_longlong, _i, _vp, _vp]),
+    "csff_batch_create": (_i, [_i, C.POINTER(ProblemC), C.POINTER(OptsC), _vp, C.POINTER(_vp)]),
+    "csff_batch_destroy": (None, [_vp]),
+    "csff_batch_solve": (_i, [_vp, _dp, C.POINTER(InfoC)]),
+    "csff_batch_solution": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "csff_batch_copy_solution": (_i, [_vp, _i, _vp]),
+    "csff_batch_far_field": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_dp), C.POINTER(_vp), C.POINTER(_vp)]),
+    "csff_batch_autotune": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_i)]),
+    "csff_batch_debug_barrier": (_i, [_vp, _i, C.c_longlong]),
     "csff_prof_begin": (_i, [C.c_uint]),
     "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
 }
@@ -180,6 +188,83 @@ def _require(t, dtype, numel, name):
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
         raise ValueError(f"{name}: need contiguous {dtype} with >= {numel} elements, got {t.dtype} {tuple(t.shape)}")
+
+
+def _problem_c(problem):
+    gs = problem.get("gaussians", [])
+    garr = (Gauss * max(1, len(gs)))()
+    for i, g in enumerate(gs):
+        a = complex(g["amp"])
+        c = tuple(g.get("center", (0.0, 0.0, 0.0)))
+        garr[i] = Gauss(a.real, a.imag, (C.c_double * 3)(*c), float(g["width"]))
+    pc = ProblemC(int(problem["dim"]), int(problem["n"]), float(problem["lo"]), float(problem["hi"]),
+                  float(problem["gamma"]), float(problem["k"]), len(gs), garr)
+    return pc, garr
+
+
+def _opts_c(o):
+    return OptsC(SMOOTHER[o.get("smoother", "jacobi")], float(o.get("omega", 2.0 / 3.0)), int(o.get("nu1", 1)),
+                 int(o.get("nu2", 1)), int(o.get("coarsest_n", 5)), float(o.get("rel_tol", 1e-8)),
+                 int(o.get("max_cycles", 100)), PRECISION[o.get("precision", "fp64")],
+                 int(o.get("inner_cycles", 3)))
+
+
+class Batch:
+    """Many uneven 2D problems solved together in one persistent launch
+    (csff_batch_create / csff_batch_solve)."""
+
+    def __init__(self, problems, opts: dict, stream=None):
+        self._keep = [_problem_c(p) for p in problems]
+        arr = (ProblemC * len(problems))(*[k[0] for k in self._keep])
+        self.n = len(problems)
+        self.sizes = [(int(p["n"]) - 2) ** 2 for p in problems]
+        oc = _opts_c(dict(opts, precision="mixed"))
+        h = C.c_void_p()
+        _check(_lib.csff_batch_create(self.n, arr, C.byref(oc), _stream_handle(stream), C.byref(h)), "batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.csff_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, eta, ok=(OK,)):
+        eta, ep = _dbl(eta)
+        infos = (InfoC * self.n)()
+        st = _lib.csff_batch_solve(self._h, ep, infos)
+        _check(st, "batch_solve", ok)
+        return st, [infos[i].as_dict() for i in range(self.n)]
+
+    def solution(self, i):
+        """Copy of instance i's solution (complex128 CUDA tensor of m_i^2)."""
+        import torch
+        out = torch.empty(self.sizes[i], dtype=torch.complex128, device="cuda")
+        _check(_lib.csff_batch_copy_solution(self._h, i, _ptr(out)), "batch_copy_solution")
+        return out
+
+    def far_field(self, eta, alphas, F, F_exp=None):
+        eta, ep = _dbl(eta)
+        al = [np.ascontiguousarray(a, dtype=np.float64) for a in alphas]
+        n_ang = (C.c_int * self.n)(*[a.shape[0] for a in al])
+        aptr = (_dp * self.n)(*[a.ctypes.data_as(_dp) for a in al])
+        fptr = (C.c_void_p * self.n)(*[f.data_ptr() for f in F])
+        eptr = (C.c_void_p * self.n)(*[e.data_ptr() for e in F_exp]) if F_exp is not None else None
+        _check(_lib.csff_batch_far_field(self._h, ep, n_ang, aptr, fptr, eptr), "batch_far_field")
+
+    def autotune(self, eta):
+        eta, ep = _dbl(eta)
+        tc, per = C.c_int(), C.c_int()
+        _check(_lib.csff_batch_autotune(self._h, ep, C.byref(tc), C.byref(per)), "batch_autotune")
+        return tc.value, per.value
+
+    def debug_barrier(self, extra_arrivals, spin_limit=0):
+        _check(_lib.csff_batch_debug_barrier(self._h, int(extra_arrivals), int(spin_limit)), "batch_debug_barrier")
 
 
 class Plan:

@@ -138,18 +138,24 @@ __global__ void k_prolong_add(const cx<T>* __restrict__ ec, int mc, cx<T>* __res
   uf[idx] = cadd(uf[idx], acc);
 }
 
-// Coarsest level: u = A_c^{-1} b with the FP64 dense inverse; one CTA.
+// Coarsest level: u = A_c^{-1} b with the FP64 dense inverse; one CTA, one
+// warp per row (lanes split the columns, shuffle reduction).
 template <typename T>
 __global__ void k_coarse_solve(const double2* __restrict__ inv, int N, const cx<T>* __restrict__ b,
                                cx<T>* __restrict__ u) {
   extern __shared__ double2 sb[];
   for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = make_double2((double)b[j].x, (double)b[j].y);
   __syncthreads();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < N; i += nw) {
     double2 acc = make_double2(0, 0);
     const double2* row = inv + (long long)i * N;
-    for (int j = 0; j < N; ++j) acc = cadd(acc, cmul(row[j], sb[j]));
-    u[i] = mk<cx<T>>((T)acc.x, (T)acc.y);
+    for (int j = lane; j < N; j += 32) acc = cadd(acc, cmul(row[j], sb[j]));
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) u[i] = mk<cx<T>>((T)acc.x, (T)acc.y);
   }
 }
 
