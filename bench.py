@@ -46,11 +46,15 @@ def _peaks():
 # FP64 FMA throughput of this part, measured with an FMA-loop kernel
 # (0.599e12 DFMA/s over 152 SMs; 2 flops per FMA).
 FP64_PEAK_TFLOPS = 1.198
+# DRAM bytes (read + write) of one k_ff_stage1 launch on this workload, from the
+# ncu capture summarised in profiles/ff_stage1_2d_n1025.md (None once the kernel
+# changes).
+FF_STAGE1_DRAM_BYTES = 22668288
 
 
-def _cases(precision):
+def _cases(precision, ks=None):
     out = []
-    for k in KS:
+    for k in (ks or KS):
         c = W.mixed_2d(k)
         c["opts"]["precision"] = precision
         c["opts"]["inner_cycles"] = 3
@@ -170,7 +174,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
     stream = torch.cuda.current_stream()
-    cases = _cases(args.precision)
+    ks = tuple(float(k) for k in args.ks.split(",")) if args.ks else KS
+    cases = _cases(args.precision, ks)
     t0 = time.perf_counter()
     plans = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in cases]
     torch.cuda.synchronize()
@@ -231,7 +236,7 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = len(KS) * args.steps * world / (total_ms / 1e3)
+    value = len(cases) * args.steps * world / (total_ms / 1e3)
 
     # ---- per-family breakdown (one extra profiled step) -----------------------
     flush.zero_()
@@ -261,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_val = len(KS) * args.steps * world / e2e_s
+    e2e_val = len(cases) * args.steps * world / e2e_s
     h2d = sum(int(eta_h[i].numel() * 8 + al_h[i].numel() * 8) for i in range(len(cases)))
     d2h = sum(int(F_h[i].numel() * 16 + Fe_h[i].numel() * 4) for i in range(len(cases)))
 
@@ -275,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
     achieved_tf = ff_flops / (ff_avg_ms * 1e-3) / 1e12 if ff_avg_ms > 0 else 0.0
     roofline = {"kernel": "k_ff_stage1 (FP64 far-field contraction)", "bound": "alu",
                 "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": FF_STAGE1_DRAM_BYTES,
                 "peak_source": "FP64 FMA-loop measurement on this GB300 (no FP64 entry in MEASURED_PEAKS.json)",
                 "avg_launch_ms": ff_avg_ms, "launches": ff["launches"],
                 "alg_flops_per_launch": ff_flops}
@@ -296,8 +301,10 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk.result,
-            "solve": {str(KS[i]): {"cycles": infos[i]["cycles"], "refinements": infos[i]["refinements"],
+            "solve": {str(ks[i]): {"cycles": infos[i]["cycles"], "refinements": infos[i]["refinements"],
                                    "rel_res": infos[i]["rel_res"]} for i in infos}}
+    if args.variants:
+        line["variants"] = measure_variants(csff, torch, dev, stream, flush)
     if args.cpu_baseline and world == 1:
         per_map, info = oracle_sample()
         line["cpu_baseline"] = {"value": 1.0 / per_map, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -305,6 +312,94 @@ def run_ours(args, rank, world, local_rank):
                                           "of 720 angles (scaled to 720); numpy, single thread",
                                 "detail": info}
     print(json.dumps(line), flush=True)
+
+
+def _time_events(torch, stream, fn, flush, reps):
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return sum(ms) / len(ms)
+
+
+def measure_variants(csff, torch, dev, stream, flush):
+    """The same four maps in plain FP64 (V-cycles in FP64), and the 64-instance
+    uneven batch solved in one persistent launch against the same instances
+    solved one after the other through the single-problem mixed path."""
+    out = {}
+    cases = _cases("fp64")
+    plans = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in cases]
+    N = plans[0].N
+    us = [torch.zeros(N, dtype=torch.complex128, device=dev) for _ in cases]
+    Fs = [torch.zeros(720, dtype=torch.complex128, device=dev) for _ in cases]
+    Fe = [torch.zeros(720, dtype=torch.int32, device=dev) for _ in cases]
+    cyc = {}
+
+    def step64():
+        for i, (p, c) in enumerate(zip(plans, cases)):
+            _, info = p.solve(c["eta"], us[i])
+            cyc[i] = info[0]["cycles"]
+            p.far_field(c["eta"], us[i], c["alphas"], Fs[i], Fe[i])
+
+    step64()
+    ms = _time_events(torch, stream, step64, flush, 2)
+    out["fp64_plain"] = {"value": len(cases) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                         "cycles": [cyc[i] for i in range(len(cases))]}
+    for p in plans:
+        p.close()
+    del us, Fs, Fe
+    # ---- 64 uneven instances
+    bc = W.batch_2d(64, seed=4461)
+    for c in bc:
+        c["opts"].update(precision="mixed", inner_cycles=3, coarsest_n=5)
+    eta = np.vstack([c["eta"] for c in bc])
+    al = [c["alphas"] for c in bc]
+    b = csff.Batch([c["problem"] for c in bc], bc[0]["opts"], stream=stream)
+    tc, per = b.autotune(eta)
+    Fb = [torch.zeros(720, dtype=torch.complex128, device=dev) for _ in bc]
+    Eb = [torch.zeros(720, dtype=torch.int32, device=dev) for _ in bc]
+    binfo = {}
+
+    def batch_step():
+        _, inf = b.solve(eta)
+        binfo["inf"] = inf
+        b.far_field(eta, al, Fb, Eb)
+
+    batch_step()
+    ms_b = _time_events(torch, stream, batch_step, flush, 3)
+    ms_bs = _time_events(torch, stream, lambda: b.solve(eta), flush, 3)
+    sizes = {}
+    for c in bc:
+        sizes[c["problem"]["n"]] = sizes.get(c["problem"]["n"], 0) + 1
+    out["batched_64"] = {"value": len(bc) / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b,
+                         "solve_ms": ms_bs, "autotuned": {"tile_coarse_points": tc, "ctas_per_sm": per},
+                         "sizes": {str(k): v for k, v in sorted(sizes.items())},
+                         "all_converged": all(x["rel_res"] <= 1e-8 for x in binfo["inf"]),
+                         "cycles_total": int(sum(x["cycles"] for x in binfo["inf"]))}
+    b.close()
+    # the same instances, one plan at a time (single-problem mixed path)
+    sp = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in bc]
+    su = [torch.zeros(p.N, dtype=torch.complex128, device=dev) for p in sp]
+
+    def seq_step():
+        for i, (p, c) in enumerate(zip(sp, bc)):
+            p.solve(c["eta"], su[i])
+            p.far_field(c["eta"], su[i], c["alphas"], Fb[i], Eb[i])
+
+    seq_step()
+    ms_s = _time_events(torch, stream, seq_step, flush, 2)
+    out["sequential_64"] = {"value": len(bc) / (ms_s / 1e3), "unit": UNIT, "ms_per_step": ms_s}
+    out["batched_speedup_vs_sequential"] = ms_s / ms_b
+    for p in sp:
+        p.close()
+    return out
 
 
 def main():
@@ -315,6 +410,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="skip the plain-FP64 and batched comparison runs")
+    ap.add_argument("--ks", default="", help="comma-separated subset of the wavenumbers (profiling runs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
