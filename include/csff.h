@@ -110,6 +110,8 @@ typedef struct csff_info {
   double conv_factor;  /* (||r_k|| / ||r_0||)^(1/k) per V-cycle */
   int n_hist;
   double history[CSFF_MAX_HISTORY];
+  int flags;           /* bit 0: a learned smoother was attached; bit 1: it fell
+                          back to plain red-black sweeps during this solve */
 } csff_info;
 
 /* Read-only description of a plan's hierarchy. */
@@ -198,6 +200,44 @@ csff_status csff_coarse_solve(csff_plan* plan, int arith, const void* b_dev, voi
 csff_status csff_norm2(csff_plan* plan, int level, int arith, const void* v_dev, double* out_host);
 /* One V(nu1, nu2) cycle on the finest level, in place on u_dev. */
 csff_status csff_vcycle(csff_plan* plan, int arith, void* u_dev, const void* b_dev);
+
+/* ---- learned smoother --------------------------------------------------
+   Not in the paper: a bias-free 3x3 convolutional network N (2 -> 16 -> 16 ->
+   2 channels, ReLU between layers) on the two real channels of a residual,
+   used as u <- u + N(b - A u) after each red-black sweep of the FP32 cycles on
+   the finest levels.  Weights and activations BF16, FP32 accumulation, FP32
+   master weights.  Weight layout: flat (out, in, a, b) per layer, layers 1, 2,
+   3 (288 + 2304 + 288 = 2880 values).  Convolutions are 3x3
+   cross-correlations with zero padding.  Training (all on the GPU): loss
+   L = mean over patches of sum_mask |r - A N(r)|^2 / sum_mask |r|^2, A the
+   level's operator with per-pixel q = k^2(1 + chi) and constant c (eq. csg),
+   mask = interior minus a margin; Adam (beta 0.9/0.999, eps 1e-8). */
+typedef struct csff_net csff_net;
+int csff_net_num_params(void);
+/* w_host: 2880 FP32 weights (copied). */
+csff_status csff_net_create(const float* w_host, csff_net** out);
+void csff_net_destroy(csff_net* net);
+csff_status csff_net_set_weights(csff_net* net, const float* w_host);   /* resets Adam state */
+csff_status csff_net_get_weights(const csff_net* net, float* w_host);
+/* y_dev = N(r_dev) for B patches of H x W (c64 each, device). */
+csff_status csff_net_forward(csff_net* net, int B, int H, int W, const void* r_dev, void* y_dev, void* stream);
+/* Loss and FP32 weight gradient of a batch: r_dev, q_dev c64 [B][H][W];
+   c_host: B complex constants (re, im); grad_host: 2880 floats or NULL. */
+csff_status csff_net_loss_grad(csff_net* net, int B, int H, int W, const void* r_dev, const void* q_dev,
+                               const double* c_host, int margin, float* loss_host, float* grad_host, void* stream);
+/* One Adam step on a batch (loss before the step in *loss_host if non-NULL). */
+csff_status csff_net_train_step(csff_net* net, int B, int H, int W, const void* r_dev, const void* q_dev,
+                                const double* c_host, int margin, float lr, float* loss_host, void* stream);
+/* Attach (net != NULL) or detach the learned step on levels 0..levels-1 of a
+   red-black plan's FP32 cycles.  A mixed-precision refinement step that
+   reduces the residual by less than the factor `guard` turns the learned step
+   off for the rest of that solve (csff_info.flags bit 1).  The plan keeps a
+   pointer to the net; the net must outlive the attachment. */
+csff_status csff_plan_set_learned(csff_plan* plan, csff_net* net, int levels, double guard);
+/* FP32 copy of a level's q = k^2(1 + chi) (c64, m_l^d, device) and its
+   constant c = e^{-2i gamma}/h_l^2 (2 doubles, host): the operator the learned
+   step is trained against. */
+csff_status csff_plan_copy_coefficients(const csff_plan* plan, int level, void* q32_dev, double* c_host);
 
 /* ---- batched solve: many uneven 2D problems in one persistent launch ----
    Each instance is solved as by csff_solve with CSFF_PREC_MIXED (FP64

@@ -59,12 +59,12 @@ class OptsC(C.Structure):
 class InfoC(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("refinements", C.c_int),
                 ("rel_res", C.c_double), ("conv_factor", C.c_double), ("n_hist", C.c_int),
-                ("history", C.c_double * MAX_HISTORY)]
+                ("history", C.c_double * MAX_HISTORY), ("flags", C.c_int)]
 
     def as_dict(self):
         return {"status": self.status, "cycles": self.cycles, "refinements": self.refinements,
                 "rel_res": self.rel_res, "conv_factor": self.conv_factor,
-                "history": list(self.history[: self.n_hist])}
+                "history": list(self.history[: self.n_hist]), "flags": self.flags}
 
 
 class DescC(C.Structure):
@@ -82,6 +82,7 @@ PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other")
 
 _vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
 _dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
 _SIGS = {
     "csff_plan_create": (_i, [C.POINTER(ProblemC), C.POINTER(OptsC), _vp, C.POINTER(_vp)]),
     "csff_plan_destroy": (None, [_vp]),
@@ -110,6 +111,16 @@ _SIGS = {
     "csff_batch_far_field": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_dp), C.POINTER(_vp), C.POINTER(_vp)]),
     "csff_batch_autotune": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_i)]),
     "csff_batch_debug_barrier": (_i, [_vp, _i, C.c_longlong]),
+    "csff_net_num_params": (_i, []),
+    "csff_net_create": (_i, [_fp, C.POINTER(_vp)]),
+    "csff_net_destroy": (None, [_vp]),
+    "csff_net_set_weights": (_i, [_vp, _fp]),
+    "csff_net_get_weights": (_i, [_vp, _fp]),
+    "csff_net_forward": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
+    "csff_net_loss_grad": (_i, [_vp, _i, _i, _i, _vp, _vp, _dp, _i, _fp, _fp, _vp]),
+    "csff_net_train_step": (_i, [_vp, _i, _i, _i, _vp, _vp, _dp, _i, C.c_float, _fp, _vp]),
+    "csff_plan_set_learned": (_i, [_vp, _vp, _i, _d]),
+    "csff_plan_copy_coefficients": (_i, [_vp, _i, _vp, _dp]),
     "csff_prof_begin": (_i, [C.c_uint]),
     "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
 }
@@ -267,6 +278,62 @@ class Batch:
         _check(_lib.csff_batch_debug_barrier(self._h, int(extra_arrivals), int(spin_limit)), "batch_debug_barrier")
 
 
+class Net:
+    """The learned smoother's network on the GPU (csff_net_*).  Weights are a
+    flat FP32 vector of 2880 values, (out, in, a, b) per layer."""
+
+    def __init__(self, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        if w.size != _lib.csff_net_num_params():
+            raise ValueError("need %d weights" % _lib.csff_net_num_params())
+        h = C.c_void_p()
+        _check(_lib.csff_net_create(w.ctypes.data_as(_fp), C.byref(h)), "net_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.csff_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def weights(self):
+        w = np.empty(_lib.csff_net_num_params(), np.float32)
+        _check(_lib.csff_net_get_weights(self._h, w.ctypes.data_as(_fp)), "net_get_weights")
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(_lib.csff_net_set_weights(self._h, w.ctypes.data_as(_fp)), "net_set_weights")
+
+    def forward(self, r, y, stream=None):
+        """r, y: complex64 CUDA tensors of shape (B, H, W)."""
+        B, H, W = r.shape
+        _check(_lib.csff_net_forward(self._h, B, H, W, _ptr(r), _ptr(y), _stream_handle(stream)), "net_forward")
+
+    def loss_grad(self, r, q, c, margin=4, stream=None):
+        B, H, W = r.shape
+        cc, cp = _dbl(np.stack([np.real(c), np.imag(c)], axis=1).ravel())
+        loss = C.c_float()
+        g = np.empty(_lib.csff_net_num_params(), np.float32)
+        _check(_lib.csff_net_loss_grad(self._h, B, H, W, _ptr(r), _ptr(q), cp, int(margin), C.byref(loss),
+                                       g.ctypes.data_as(_fp), _stream_handle(stream)), "net_loss_grad")
+        return loss.value, g
+
+    def train_step(self, r, q, c, lr, margin=4, stream=None):
+        B, H, W = r.shape
+        cc, cp = _dbl(np.stack([np.real(c), np.imag(c)], axis=1).ravel())
+        loss = C.c_float()
+        _check(_lib.csff_net_train_step(self._h, B, H, W, _ptr(r), _ptr(q), cp, int(margin), float(lr),
+                                        C.byref(loss), _stream_handle(stream)), "net_train_step")
+        return loss.value
+
+
 class Plan:
     """A multigrid + far-field plan for one problem (csff_plan_create).
 
@@ -312,6 +379,21 @@ class Plan:
     def set_stream(self, stream):
         self._stream = stream
         _check(_lib.csff_plan_set_stream(self._h, _stream_handle(stream)), "set_stream")
+
+    def set_learned(self, net, levels=1, guard=0.5):
+        """Attach (net) or detach (None) the learned step on the finest levels."""
+        _check(_lib.csff_plan_set_learned(self._h, net._h if net is not None else None, int(levels), float(guard)),
+               "plan_set_learned")
+        self._net = net
+
+    def coefficients(self, level):
+        """(q, c): FP32 q = k^2(1+chi) of a level (complex64 CUDA tensor) and c."""
+        import torch
+        n = self.level_size(level)
+        q = torch.empty(n, dtype=torch.complex64, device="cuda")
+        cbuf = (C.c_double * 2)()
+        _check(_lib.csff_plan_copy_coefficients(self._h, level, _ptr(q), cbuf), "plan_copy_coefficients")
+        return q, complex(cbuf[0], cbuf[1])
 
     def describe(self) -> dict:
         d = DescC()

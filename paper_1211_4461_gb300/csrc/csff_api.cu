@@ -219,7 +219,12 @@ csff_status smooth(csff_plan* P, int l, cx<T>* u, const cx<T>* b, int sweeps) {
   Level& L = P->lv[l];
   cudaStream_t s = P->stream;
   if (P->opts.smoother == CSFF_SMOOTHER_RBGS) {
-    for (int i = 0; i < sweeps; ++i) CK(csff::launch_rbgs<T>(P->dim, L, u, b, s), "rbgs");
+    for (int i = 0; i < sweeps; ++i) {
+      CK(csff::launch_rbgs<T>(P->dim, L, u, b, s), "rbgs");
+      if constexpr (sizeof(T) == 4) {
+        if (P->net && !P->learned_off && l < P->learned_levels) CS(csff::learned_step(P, P->dim, L, u, b, s));
+      }
+    }
     return CSFF_OK;
   }
   cx<T>* t = tbuf<T>(L);
@@ -418,14 +423,27 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
   tr.start(info);
   int cycles = 0, refinements = 0;
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
-  const long long key = (2ll << 40) + (long long)(eb + 8192) * 64 + inner;
+  const long long key0 = (2ll << 40) + (long long)(eb + 8192) * 64 + inner;
+  P->learned_off = false;
+  bool fell_back = false;
+  double prev = 1.0;
   CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, P->stream), "residual");
   CS(norm64(P, L.r64, eb, 0));
   for (;;) {
-    CS(run_step(P, key, step_mixed, eb));
+    const bool learned = P->net && !P->learned_off;
+    CS(run_step(P, key0 + (learned ? (1ll << 38) : 0), step_mixed, eb));
     cycles += inner;
     ++refinements;
-    int st = tr.push(P->red_host[0] / nb, cycles, refinements, P->opts.rel_tol, P->opts.max_cycles);
+    const double rel = P->red_host[0] / nb;
+    // a learned step that fails to cut the residual by the guard factor hands
+    // the rest of the solve back to plain red-black sweeps
+    if (learned && rel > P->learned_guard * prev) {
+      P->learned_off = true;
+      fell_back = true;
+    }
+    prev = rel;
+    int st = tr.push(rel, cycles, refinements, P->opts.rel_tol, P->opts.max_cycles);
+    if (info) info->flags = (P->net ? 1 : 0) | (fell_back ? 2 : 0);
     if (st >= 0) return (csff_status)st;
   }
 }
@@ -646,6 +664,33 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
   cudaError_t e = cudaStreamSynchronize(P->stream);
   if (e != cudaSuccess) return fail(csff::cuda_fail(e, "plan setup"));
   *out = P;
+  return CSFF_OK;
+}
+
+csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, double guard) {
+  if (!P) return invalid("plan is NULL");
+  if (net && (levels < 1 || levels > (int)P->lv.size() - 1 || !(guard > 0.0))) return invalid("bad learned settings");
+  if (net && P->opts.smoother != CSFF_SMOOTHER_RBGS) {
+    csff::set_error("the learned step follows red-black sweeps");
+    return CSFF_ERR_UNSUPPORTED;
+  }
+  if (net) CS(csff::net_reserve(net, P->lv[0].N));
+  if (net && !P->net) P->fused_saved = P->fused_lc;
+  P->net = net;
+  P->learned_levels = net ? levels : 0;
+  P->learned_guard = guard;
+  P->fused_lc = net ? -1 : P->fused_saved;   // the learned step runs in the per-level path
+  if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+  return CSFF_OK;
+}
+
+csff_status csff_plan_copy_coefficients(const csff_plan* P, int level, void* q32_dev, double* c_host) {
+  if (!P || level < 0 || level >= (int)P->lv.size() || !q32_dev || !c_host) return invalid("bad arguments");
+  const Level& L = P->lv[level];
+  CK(cudaMemcpyAsync(q32_dev, L.q32, sizeof(float2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy q");
+  CK(cudaStreamSynchronize(P->stream), "sync");
+  c_host[0] = L.c.x;
+  c_host[1] = L.c.y;
   return CSFF_OK;
 }
 

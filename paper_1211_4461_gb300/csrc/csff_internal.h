@@ -93,6 +93,13 @@ struct csff_plan {
   long long gkey = 0;
   uint64_t gkernels = 0;          // kernel nodes in the captured graph
   bool use_graphs = true;
+  // learned smoother (csff_plan_set_learned): RB-GS sweep followed by
+  // u += N(r) on levels < learned_levels of the FP32 cycles
+  csff_net* net = nullptr;
+  int learned_levels = 0;
+  double learned_guard = 0.5;
+  bool learned_off = false;       // per-solve fallback to plain RB-GS
+  int fused_saved = -1;
 };
 
 namespace csff {
@@ -167,6 +174,10 @@ cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc);
 extern bool g_capturing;
 // kernel families currently timed (csff_prof_begin mask)
 unsigned prof_mask();
+
+// ---- learned smoother (learned.cu) ------------------------------------------
+csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s);
+csff_status net_reserve(csff_net* N, long long npix);
 
 // ---- far field (farfield.cu) -----------------------------------------------
 void free_ff_buffers(csff_plan* P);

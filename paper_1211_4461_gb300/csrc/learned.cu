@@ -1,0 +1,538 @@
+// Learned smoother: a bias-free 3x3 convolutional network N (2 -> 16 -> 16 -> 2
+// channels, ReLU between layers) applied as u <- u + N(r) after a red-black
+// sweep on the finest levels.  Complex values are two real channels.  The
+// paper has no such component; it is an addition built around the method's
+// own operator: the training loss is the relative residual after the learned
+// step, ||r - A N(r)||^2 / ||r||^2, with A the level's rotated-grid operator.
+//
+// Precision: weights and activations are stored in BF16, every convolution
+// accumulates in FP32, the master weights and the Adam moments are FP32.
+//
+// Layout: patches [B][H][W]; the residual and the output are complex FP32
+// (float2); hidden activations are channels-last BF16 [B][H][W][16].
+// Convolution: out[o, i, j] = sum_c sum_{a,b} w[o][c][a][b] x[c][i+a-1][j+b-1],
+// zero outside the patch.  Weights are stored flat in (out, in, a, b) order,
+// layer 1 then 2 then 3 (288 + 2304 + 288 values).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "csff_internal.h"
+
+namespace csff {
+namespace {
+
+constexpr int NP1 = 16 * 2 * 9, NP2 = 16 * 16 * 9, NP3 = 2 * 16 * 9;
+constexpr int NPARAM = NP1 + NP2 + NP3;
+constexpr int NTH = 256;
+
+__device__ __forceinline__ float bf(float x) { return __bfloat162float(__float2bfloat16(x)); }
+
+struct Geom {
+  int B, H, W;
+  __host__ __device__ __forceinline__ long long npix() const { return (long long)B * H * W; }
+};
+
+// neighbour (i + a - 1, j + b - 1) of pixel p inside its patch, or -1
+__device__ __forceinline__ long long nbr(const Geom& g, long long p, int a, int b) {
+  int j = (int)(p % g.W);
+  long long t = p / g.W;
+  int i = (int)(t % g.H);
+  int ii = i + a - 1, jj = j + b - 1;
+  if (ii < 0 || ii >= g.H || jj < 0 || jj >= g.W) return -1;
+  return p + (long long)(a - 1) * g.W + (b - 1);
+}
+
+// layer 1: x0 = bf16(r) (2 channels) -> h1 = bf16(relu(conv)) (16 channels)
+__global__ void k_conv1(Geom g, const float2* __restrict__ r, const __nv_bfloat16* __restrict__ w1,
+                        __nv_bfloat16* __restrict__ h1) {
+  __shared__ float ws[NP1];
+  for (int i = threadIdx.x; i < NP1; i += blockDim.x) ws[i] = __bfloat162float(w1[i]);
+  __syncthreads();
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  float acc[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) acc[o] = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      long long q = nbr(g, p, a, b);
+      if (q < 0) continue;
+      float2 v = r[q];
+      float x0 = bf(v.x), x1 = bf(v.y);
+#pragma unroll
+      for (int o = 0; o < 16; ++o)
+        acc[o] = fmaf(ws[(o * 2 + 0) * 9 + a * 3 + b], x0, fmaf(ws[(o * 2 + 1) * 9 + a * 3 + b], x1, acc[o]));
+    }
+#pragma unroll
+  for (int o = 0; o < 16; ++o) h1[p * 16 + o] = __float2bfloat16(fmaxf(acc[o], 0.f));
+}
+
+// layer 2: h1 (16) -> h2 = bf16(relu(conv)) (16)
+__global__ void k_conv2(Geom g, const __nv_bfloat16* __restrict__ h1, const __nv_bfloat16* __restrict__ w2,
+                        __nv_bfloat16* __restrict__ h2) {
+  __shared__ float ws[NP2];
+  for (int i = threadIdx.x; i < NP2; i += blockDim.x) ws[i] = __bfloat162float(w2[i]);
+  __syncthreads();
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  float acc[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) acc[o] = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      long long q = nbr(g, p, a, b);
+      if (q < 0) continue;
+      const __nv_bfloat16* x = h1 + q * 16;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        float xc = __bfloat162float(x[c]);
+#pragma unroll
+        for (int o = 0; o < 16; ++o) acc[o] = fmaf(ws[(o * 16 + c) * 9 + a * 3 + b], xc, acc[o]);
+      }
+    }
+#pragma unroll
+  for (int o = 0; o < 16; ++o) h2[p * 16 + o] = __float2bfloat16(fmaxf(acc[o], 0.f));
+}
+
+// layer 3: h2 (16) -> y (2, FP32); mode 0: y = out, mode 1: y += out (u <- u + N(r))
+__global__ void k_conv3(Geom g, const __nv_bfloat16* __restrict__ h2, const __nv_bfloat16* __restrict__ w3,
+                        float2* __restrict__ y, int accumulate) {
+  __shared__ float ws[NP3];
+  for (int i = threadIdx.x; i < NP3; i += blockDim.x) ws[i] = __bfloat162float(w3[i]);
+  __syncthreads();
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  float a0 = 0.f, a1 = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      long long q = nbr(g, p, a, b);
+      if (q < 0) continue;
+      const __nv_bfloat16* x = h2 + q * 16;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        float xc = __bfloat162float(x[c]);
+        a0 = fmaf(ws[(0 * 16 + c) * 9 + a * 3 + b], xc, a0);
+        a1 = fmaf(ws[(1 * 16 + c) * 9 + a * 3 + b], xc, a1);
+      }
+    }
+  if (accumulate) {
+    float2 u = y[p];
+    y[p] = make_float2(u.x + a0, u.y + a1);
+  } else {
+    y[p] = make_float2(a0, a1);
+  }
+}
+
+// ---- loss: E = mask (r - A y); per-patch sums |E|^2 and |r|^2 over the mask
+__device__ __forceinline__ bool in_mask(const Geom& g, long long p, int margin) {
+  int j = (int)(p % g.W);
+  int i = (int)((p / g.W) % g.H);
+  return i >= margin && i < g.H - margin && j >= margin && j < g.W - margin;
+}
+
+__device__ __forceinline__ float2 apply_A_patch(const Geom& g, const float2* v, long long p, float2 q, float2 c,
+                                                bool conj_in) {
+  auto ld = [&](long long k) {
+    float2 x = v[k];
+    return conj_in ? make_float2(x.x, -x.y) : x;
+  };
+  float2 s = make_float2(0.f, 0.f);
+  for (int t = 0; t < 4; ++t) {
+    int a = (t == 0) ? 0 : (t == 1) ? 2 : 1;
+    int b = (t == 2) ? 0 : (t == 3) ? 2 : 1;
+    long long k = nbr(g, p, a, b);
+    if (k >= 0) s = cadd(s, ld(k));
+  }
+  float2 vj = ld(p);
+  float2 t = csub(cscale(vj, 4.f), s);
+  return csub(cmul(c, t), cmul(q, vj));
+}
+
+__global__ void k_loss1(Geom g, const float2* __restrict__ y, const float2* __restrict__ r,
+                        const float2* __restrict__ q, const float2* __restrict__ cpatch, int margin,
+                        float2* __restrict__ E, double* __restrict__ sums /* [B][2]: |E|^2, |r|^2 */) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  int bpatch = (int)(p / ((long long)g.H * g.W));
+  float2 e = make_float2(0.f, 0.f);
+  if (in_mask(g, p, margin)) {
+    float2 rv = r[p];
+    e = csub(rv, apply_A_patch(g, y, p, q[p], cpatch[bpatch], false));
+    atomicAdd(&sums[2 * bpatch + 0], (double)e.x * e.x + (double)e.y * e.y);
+    atomicAdd(&sums[2 * bpatch + 1], (double)rv.x * rv.x + (double)rv.y * rv.y);
+  }
+  E[p] = e;
+}
+
+// dy = -conj(A conj(G)), G = 2 E / (S_r B)   (A is complex symmetric)
+__global__ void k_loss2(Geom g, const float2* __restrict__ E, const double* __restrict__ sums,
+                        const float2* __restrict__ q, const float2* __restrict__ cpatch, float2* __restrict__ G,
+                        float2* __restrict__ dy, int phase) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  int bpatch = (int)(p / ((long long)g.H * g.W));
+  if (phase == 0) {
+    double sr = sums[2 * bpatch + 1];
+    float sc = sr > 0 ? (float)(2.0 / (sr * g.B)) : 0.f;
+    G[p] = cscale(E[p], sc);
+  } else {
+    float2 a = apply_A_patch(g, G, p, q[p], cpatch[bpatch], true);
+    dy[p] = make_float2(-a.x, a.y);     // -conj(a)
+  }
+}
+
+// input gradient of layer 3: dh2[c] = sum_o sum_ab w3[o][c][a][b] dy[o](p - (a-1, b-1)), masked by h2 > 0
+__global__ void k_bwd3(Geom g, const float2* __restrict__ dy, const __nv_bfloat16* __restrict__ w3,
+                       const __nv_bfloat16* __restrict__ h2, float* __restrict__ dh2) {
+  __shared__ float ws[NP3];
+  for (int i = threadIdx.x; i < NP3; i += blockDim.x) ws[i] = __bfloat162float(w3[i]);
+  __syncthreads();
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      long long q = nbr(g, p, 2 - a, 2 - b);      // out pixel p - (a-1, b-1)
+      if (q < 0) continue;
+      float2 d = dy[q];
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        acc[c] = fmaf(ws[(0 * 16 + c) * 9 + a * 3 + b], d.x, fmaf(ws[(1 * 16 + c) * 9 + a * 3 + b], d.y, acc[c]));
+    }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) dh2[p * 16 + c] = __bfloat162float(h2[p * 16 + c]) > 0.f ? acc[c] : 0.f;
+}
+
+// input gradient of layer 2, masked by h1 > 0
+__global__ void k_bwd2(Geom g, const float* __restrict__ dh2, const __nv_bfloat16* __restrict__ w2,
+                       const __nv_bfloat16* __restrict__ h1, float* __restrict__ dh1) {
+  __shared__ float ws[NP2];
+  for (int i = threadIdx.x; i < NP2; i += blockDim.x) ws[i] = __bfloat162float(w2[i]);
+  __syncthreads();
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      long long q = nbr(g, p, 2 - a, 2 - b);
+      if (q < 0) continue;
+      const float* d = dh2 + q * 16;
+#pragma unroll
+      for (int o = 0; o < 16; ++o) {
+        float dv = d[o];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = fmaf(ws[(o * 16 + c) * 9 + a * 3 + b], dv, acc[c]);
+      }
+    }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) dh1[p * 16 + c] = __bfloat162float(h1[p * 16 + c]) > 0.f ? acc[c] : 0.f;
+}
+
+// weight gradient: dw[o][c][a][b] += sum_p dout[p][o] in[c](p + (a-1, b-1)).
+// INKIND 0: input is bf16(r) (2 channels from float2); 1: bf16 activations.
+// DKIND 0: dout is float2 (2 channels); 1: float[16].
+template <int CIN, int COUT, int INKIND, int DKIND>
+__global__ void k_wgrad(Geom g, const void* __restrict__ in, const void* __restrict__ dout, float* __restrict__ dw) {
+  constexpr int NPAR = COUT * CIN * 9;
+  constexpr int TP = 128;                          // pixels per block
+  __shared__ float sd[TP * COUT];
+  const long long p0 = (long long)blockIdx.x * TP;
+  for (int i = threadIdx.x; i < TP * COUT; i += blockDim.x) {
+    long long p = p0 + i / COUT;
+    int o = i % COUT;
+    float v = 0.f;
+    if (p < g.npix()) {
+      if (DKIND == 0) {
+        float2 d = reinterpret_cast<const float2*>(dout)[p];
+        v = (o == 0) ? d.x : d.y;
+      } else {
+        v = reinterpret_cast<const float*>(dout)[p * COUT + o];
+      }
+    }
+    sd[i] = v;
+  }
+  __syncthreads();
+  for (int par = threadIdx.x; par < NPAR; par += blockDim.x) {
+    int o = par / (CIN * 9), rem = par % (CIN * 9), c = rem / 9, ab = rem % 9, a = ab / 3, b = ab % 3;
+    float acc = 0.f;
+    for (int t = 0; t < TP; ++t) {
+      long long p = p0 + t;
+      if (p >= g.npix()) break;
+      long long q = nbr(g, p, a, b);
+      if (q < 0) continue;
+      float x;
+      if (INKIND == 0) {
+        float2 v = reinterpret_cast<const float2*>(in)[q];
+        x = bf(c == 0 ? v.x : v.y);
+      } else {
+        x = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(in)[q * CIN + c]);
+      }
+      acc = fmaf(sd[t * COUT + o], x, acc);
+    }
+    atomicAdd(&dw[par], acc);
+  }
+}
+
+__global__ void k_adam(float* w, float* m, float* v, const float* gr, __nv_bfloat16* wb, int n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = gr[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  w[i] = wi;
+  wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) wb[i] = __float2bfloat16(w[i]);
+}
+
+inline int nblk(long long n) { return (int)((n + NTH - 1) / NTH); }
+
+}  // namespace
+}  // namespace csff
+
+struct csff_net {
+  float* w = nullptr;            // FP32 master [NPARAM]
+  float* m = nullptr;            // Adam moments
+  float* v = nullptr;
+  float* grad = nullptr;
+  __nv_bfloat16* wb = nullptr;   // BF16 copy used by the kernels
+  int step = 0;
+  // scratch, grown on demand (pixels)
+  long long cap = 0;
+  __nv_bfloat16 *h1 = nullptr, *h2 = nullptr;
+  float *dh1 = nullptr, *dh2 = nullptr;
+  float2 *y = nullptr, *E = nullptr, *G = nullptr, *dy = nullptr;
+  double* sums = nullptr;
+  int cap_b = 0;
+  float2* cpatch = nullptr;
+};
+
+namespace {
+
+#define NK(call, what)                                                   \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return csff::cuda_fail(e_, what);             \
+  } while (0)
+
+csff_status ninvalid(const char* s) {
+  csff::set_error(s);
+  return CSFF_ERR_INVALID_ARG;
+}
+
+csff_status ensure_scratch(csff_net* N, long long npix, int B, bool train) {
+  if (npix > N->cap || (train && !N->dh1)) {
+    for (void* p : {(void*)N->h1, (void*)N->h2, (void*)N->dh1, (void*)N->dh2, (void*)N->y, (void*)N->E,
+                    (void*)N->G, (void*)N->dy})
+      if (p) cudaFree(p);
+    N->h1 = N->h2 = nullptr;
+    N->dh1 = N->dh2 = nullptr;
+    N->y = N->E = N->G = N->dy = nullptr;
+    long long cap = std::max(npix, N->cap);
+    NK(cudaMalloc((void**)&N->h1, sizeof(__nv_bfloat16) * 16 * cap), "net scratch");
+    NK(cudaMalloc((void**)&N->h2, sizeof(__nv_bfloat16) * 16 * cap), "net scratch");
+    NK(cudaMalloc((void**)&N->y, sizeof(float2) * cap), "net scratch");
+    if (train) {
+      NK(cudaMalloc((void**)&N->dh1, sizeof(float) * 16 * cap), "net scratch");
+      NK(cudaMalloc((void**)&N->dh2, sizeof(float) * 16 * cap), "net scratch");
+      NK(cudaMalloc((void**)&N->E, sizeof(float2) * cap), "net scratch");
+      NK(cudaMalloc((void**)&N->G, sizeof(float2) * cap), "net scratch");
+      NK(cudaMalloc((void**)&N->dy, sizeof(float2) * cap), "net scratch");
+    }
+    N->cap = cap;
+  }
+  if (B > N->cap_b) {
+    if (N->sums) cudaFree(N->sums);
+    if (N->cpatch) cudaFree(N->cpatch);
+    NK(cudaMalloc((void**)&N->sums, sizeof(double) * 2 * B), "net sums");
+    NK(cudaMalloc((void**)&N->cpatch, sizeof(float2) * B), "net patch constants");
+    N->cap_b = B;
+  }
+  return CSFF_OK;
+}
+
+csff_status forward(csff_net* N, csff::Geom g, const float2* r, float2* y, int accumulate, cudaStream_t s) {
+  using namespace csff;
+  const long long np = g.npix();
+  const __nv_bfloat16* w1 = N->wb;
+  const __nv_bfloat16* w2 = N->wb + NP1;
+  const __nv_bfloat16* w3 = N->wb + NP1 + NP2;
+  {
+    ProfScope ps(PF_MG32, s, 8.0 * np + 2.0 * 32 * np + 8.0 * np, 2.0 * 9 * (2 * 16 + 16 * 16 + 16 * 2) * np);
+    k_conv1<<<nblk(np), NTH, 0, s>>>(g, r, w1, N->h1);
+    k_conv2<<<nblk(np), NTH, 0, s>>>(g, N->h1, w2, N->h2);
+    k_conv3<<<nblk(np), NTH, 0, s>>>(g, N->h2, w3, y, accumulate);
+  }
+  count_launch(3);
+  NK(cudaGetLastError(), "net forward");
+  return CSFF_OK;
+}
+
+// loss and weight gradient (into N->grad) for a batch of patches
+csff_status loss_grad(csff_net* N, csff::Geom g, const float2* r, const float2* q, const double* c_host, int margin,
+                      float* loss_host, cudaStream_t s) {
+  using namespace csff;
+  const long long np = g.npix();
+  csff_status st = ensure_scratch(N, np, g.B, true);
+  if (st != CSFF_OK) return st;
+  std::vector<float2> cp(g.B);
+  for (int b = 0; b < g.B; ++b) cp[b] = make_float2((float)c_host[2 * b], (float)c_host[2 * b + 1]);
+  NK(cudaMemcpyAsync(N->cpatch, cp.data(), sizeof(float2) * g.B, cudaMemcpyHostToDevice, s), "patch constants");
+  NK(cudaMemsetAsync(N->sums, 0, sizeof(double) * 2 * g.B, s), "sums");
+  NK(cudaMemsetAsync(N->grad, 0, sizeof(float) * NPARAM, s), "grad");
+  st = forward(N, g, r, N->y, 0, s);
+  if (st != CSFF_OK) return st;
+  const __nv_bfloat16* w2 = N->wb + NP1;
+  const __nv_bfloat16* w3 = N->wb + NP1 + NP2;
+  k_loss1<<<nblk(np), NTH, 0, s>>>(g, N->y, r, q, N->cpatch, margin, N->E, N->sums);
+  k_loss2<<<nblk(np), NTH, 0, s>>>(g, N->E, N->sums, q, N->cpatch, N->G, N->dy, 0);
+  k_loss2<<<nblk(np), NTH, 0, s>>>(g, N->E, N->sums, q, N->cpatch, N->G, N->dy, 1);
+  k_bwd3<<<nblk(np), NTH, 0, s>>>(g, N->dy, w3, N->h2, N->dh2);
+  k_bwd2<<<nblk(np), NTH, 0, s>>>(g, N->dh2, w2, N->h1, N->dh1);
+  const int wb_blocks = (int)((np + 127) / 128);
+  k_wgrad<16, 2, 1, 0><<<wb_blocks, NTH, 0, s>>>(g, N->h2, N->dy, N->grad + NP1 + NP2);
+  k_wgrad<16, 16, 1, 1><<<wb_blocks, NTH, 0, s>>>(g, N->h1, N->dh2, N->grad + NP1);
+  k_wgrad<2, 16, 0, 1><<<wb_blocks, NTH, 0, s>>>(g, r, N->dh1, N->grad);
+  count_launch(8);
+  NK(cudaGetLastError(), "net backward");
+  if (loss_host) {
+    std::vector<double> sums(2 * g.B);
+    NK(cudaMemcpyAsync(sums.data(), N->sums, sizeof(double) * 2 * g.B, cudaMemcpyDeviceToHost, s), "loss");
+    NK(cudaStreamSynchronize(s), "sync");
+    double L = 0;
+    for (int b = 0; b < g.B; ++b) L += sums[2 * b + 1] > 0 ? sums[2 * b] / sums[2 * b + 1] : 0.0;
+    *loss_host = (float)(L / g.B);
+  }
+  return CSFF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+csff_status csff_net_create(const float* w_host, csff_net** out) {
+  if (!out) return ninvalid("out is NULL");
+  *out = nullptr;
+  csff_net* N = new csff_net();
+  auto fail = [&](csff_status s) {
+    csff_net_destroy(N);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc((void**)&N->w, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->m, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->v, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->grad, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->wb, sizeof(__nv_bfloat16) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMemset(N->m, 0, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMemset(N->v, 0, sizeof(float) * csff::NPARAM)) != cudaSuccess)
+    return fail(csff::cuda_fail(e, "net allocation"));
+  csff_status s = csff_net_set_weights(N, w_host);
+  if (s != CSFF_OK) return fail(s);
+  *out = N;
+  return CSFF_OK;
+}
+
+void csff_net_destroy(csff_net* N) {
+  if (!N) return;
+  for (void* p : {(void*)N->w, (void*)N->m, (void*)N->v, (void*)N->grad, (void*)N->wb, (void*)N->h1, (void*)N->h2,
+                  (void*)N->dh1, (void*)N->dh2, (void*)N->y, (void*)N->E, (void*)N->G, (void*)N->dy,
+                  (void*)N->sums, (void*)N->cpatch})
+    if (p) cudaFree(p);
+  delete N;
+}
+
+int csff_net_num_params(void) { return csff::NPARAM; }
+
+csff_status csff_net_set_weights(csff_net* N, const float* w_host) {
+  if (!N || !w_host) return ninvalid("NULL argument");
+  for (int i = 0; i < csff::NPARAM; ++i)
+    if (!std::isfinite(w_host[i])) return ninvalid("non-finite weight");
+  NK(cudaMemcpy(N->w, w_host, sizeof(float) * csff::NPARAM, cudaMemcpyHostToDevice), "set weights");
+  csff::k_to_bf16<<<(csff::NPARAM + 255) / 256, 256>>>(N->w, N->wb, csff::NPARAM);
+  csff::count_launch();
+  NK(cudaMemset(N->m, 0, sizeof(float) * csff::NPARAM), "reset moments");
+  NK(cudaMemset(N->v, 0, sizeof(float) * csff::NPARAM), "reset moments");
+  N->step = 0;
+  NK(cudaDeviceSynchronize(), "set weights");
+  return CSFF_OK;
+}
+
+csff_status csff_net_get_weights(const csff_net* N, float* w_host) {
+  if (!N || !w_host) return ninvalid("NULL argument");
+  NK(cudaMemcpy(w_host, N->w, sizeof(float) * csff::NPARAM, cudaMemcpyDeviceToHost), "get weights");
+  return CSFF_OK;
+}
+
+csff_status csff_net_forward(csff_net* N, int B, int H, int W, const void* r_dev, void* y_dev, void* stream) {
+  if (!N || !r_dev || !y_dev || B < 1 || H < 1 || W < 1) return ninvalid("bad forward arguments");
+  csff::Geom g{B, H, W};
+  csff_status s = ensure_scratch(N, g.npix(), B, false);
+  if (s != CSFF_OK) return s;
+  return forward(N, g, (const float2*)r_dev, (float2*)y_dev, 0, (cudaStream_t)stream);
+}
+
+csff_status csff_net_loss_grad(csff_net* N, int B, int H, int W, const void* r_dev, const void* q_dev,
+                               const double* c_host, int margin, float* loss_host, float* grad_host, void* stream) {
+  if (!N || !r_dev || !q_dev || !c_host || B < 1 || H < 2 * margin + 1 || W < 2 * margin + 1 || margin < 0)
+    return ninvalid("bad loss arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  csff_status st = loss_grad(N, csff::Geom{B, H, W}, (const float2*)r_dev, (const float2*)q_dev, c_host, margin,
+                             loss_host, s);
+  if (st != CSFF_OK) return st;
+  if (grad_host) {
+    NK(cudaMemcpyAsync(grad_host, N->grad, sizeof(float) * csff::NPARAM, cudaMemcpyDeviceToHost, s), "grad");
+    NK(cudaStreamSynchronize(s), "sync");
+  }
+  return CSFF_OK;
+}
+
+csff_status csff_net_train_step(csff_net* N, int B, int H, int W, const void* r_dev, const void* q_dev,
+                                const double* c_host, int margin, float lr, float* loss_host, void* stream) {
+  if (!(lr > 0.f)) return ninvalid("learning rate must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  csff_status st = csff_net_loss_grad(N, B, H, W, r_dev, q_dev, c_host, margin, loss_host, nullptr, stream);
+  if (st != CSFF_OK) return st;
+  N->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  float c1 = 1.f - std::pow(b1, (float)N->step), c2 = 1.f - std::pow(b2, (float)N->step);
+  csff::k_adam<<<(csff::NPARAM + 255) / 256, 256, 0, s>>>(N->w, N->m, N->v, N->grad, N->wb, csff::NPARAM, lr, b1,
+                                                          b2, 1e-8f, c1, c2);
+  csff::count_launch();
+  NK(cudaGetLastError(), "adam");
+  return CSFF_OK;
+}
+
+}  // extern "C"
+
+namespace csff {
+
+// scratch for a single patch of npix pixels (reserved before graph capture)
+csff_status net_reserve(csff_net* N, long long npix) { return ensure_scratch(N, npix, 1, false); }
+
+// u <- u + N(b - A u) on level L (FP32), the learned step of the smoother
+csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s) {
+  csff_net* N = P->net;
+  Geom g{1, L.m, L.m};
+  csff_status st = ensure_scratch(N, g.npix(), 1, false);
+  if (st != CSFF_OK) return st;
+  cudaError_t e = launch_residual<float>(dim, L, u, b, L.r32, s);
+  if (e != cudaSuccess) return cuda_fail(e, "learned step residual");
+  return forward(N, g, L.r32, u, 1, s);
+}
+
+}  // namespace csff
