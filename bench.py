@@ -399,6 +399,91 @@ def measure_variants(csff, torch, dev, stream, flush):
     out["batched_speedup_vs_sequential"] = ms_s / ms_b
     for p in sp:
         p.close()
+    del su
+    out["3d_257_16dirs"] = measure_3d(csff, torch, dev, stream, flush)
+    out["learned_2049"] = measure_learned(csff, torch, dev, stream, flush)
+    return out
+
+
+def measure_3d(csff, torch, dev, stream, flush):
+    """257^3 on [-15,15]^3, k = 4, 16 incident directions, 64 x 32 angles,
+    FP32-inner / FP64-refinement, sum-factorised FP64 far field."""
+    c = W.big_3d(n=257, n_rhs=16)
+    c["opts"]["precision"] = "mixed"
+    plan = csff.Plan(c["problem"], c["opts"], stream=stream)
+    nr, na = c["eta"].shape[0], c["alphas"].shape[0]
+    u = torch.zeros(nr * plan.N, dtype=torch.complex128, device=dev)
+    F = torch.zeros(nr * na, dtype=torch.complex128, device=dev)
+    Fe = torch.zeros(nr * na, dtype=torch.int32, device=dev)
+    info = {}
+
+    def step():
+        _, inf = plan.solve(c["eta"], u)
+        info["inf"] = inf
+        plan.far_field(c["eta"], u, c["alphas"], F, Fe)
+
+    step()
+    ms = _time_events(torch, stream, step, flush, 2)
+    csff.prof_begin(csff.PROF_FF_CONTRACT)
+    plan.far_field(c["eta"], u, c["alphas"], F, Fe)
+    torch.cuda.synchronize()
+    ff = csff.prof_end()["ff_contract"]
+    plan.close()
+    return {"value": nr / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "maps_per_step": nr,
+            "cycles": [i["cycles"] for i in info["inf"]],
+            "all_converged": all(i["rel_res"] <= 1e-8 for i in info["inf"]),
+            "ff_stageA_ms_per_map": ff["ms"] / max(1, nr),
+            "ff_stageA_tflops": ff["alg_flops"] / (ff["ms"] * 1e-3) / 1e12 if ff["ms"] else 0.0}
+
+
+def measure_learned(csff, torch, dev, stream, flush):
+    """2049^2 on [-20,20]^2, k = 60 (k h = 1.17 on the finest level): plain
+    red-black V(1,1) cycles against red-black + learned step on the finest
+    level.  The network is trained on the GPU on residual patches from 257^2
+    problems with the same k h (k = 7.5), chi drawn from the batch ranges."""
+    from paper_1211_4461_gb300 import learned as LR
+    import math as _m
+    opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
+            "max_cycles": 400, "inner_cycles": 3}
+    probs = []
+    rng = np.random.Generator(np.random.PCG64(5))
+    for i in range(32):
+        n = 257
+        amp = float(rng.uniform(-2.0, -0.2))
+        w = float(rng.uniform(1.0, 6.0))
+        t = float(rng.uniform(0, 2 * _m.pi))
+        probs.append((W.problem(2, n, 20.0, _m.pi / 6, 7.5, [W.gauss(amp, w)]), np.array([_m.cos(t), _m.sin(t)])))
+    t0 = time.perf_counter()
+    data = LR.collect_patches(probs, opts, n_cycles=5, patch=64, per_field=6, seed=1)
+    net = csff.Net(LR.init_weights(7))
+    hist = LR.train(net, data, steps=1000, batch=32, lr=2e-3, margin=4, seed=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    case = W.mixed_2d(60.0, n=2049)
+    case["opts"].update(precision="mixed", inner_cycles=3, max_cycles=400)
+    plan = csff.Plan(case["problem"], case["opts"], stream=stream)
+    u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
+    F = torch.zeros(720, dtype=torch.complex128, device=dev)
+    Fe = torch.zeros(720, dtype=torch.int32, device=dev)
+    out = {"train_s": train_s, "train_patches": int(data[0].shape[0]),
+           "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:]))}
+    for name, levels in (("classical", 0), ("learned", 1)):
+        plan.set_learned(net if levels else None, levels=max(levels, 1))
+        info = {}
+
+        def step():
+            _, inf = plan.solve(case["eta"], u)
+            info["inf"] = inf[0]
+            plan.far_field(case["eta"], u, case["alphas"], F, Fe)
+
+        step()
+        ms = _time_events(torch, stream, step, flush, 2)
+        out[name] = {"value": 1.0 / (ms / 1e3), "unit": UNIT, "ms_per_map": ms, "cycles": info["inf"]["cycles"],
+                     "rel_res": info["inf"]["rel_res"], "flags": info["inf"]["flags"]}
+    out["cycle_ratio_learned_vs_classical"] = out["learned"]["cycles"] / max(1, out["classical"]["cycles"])
+    out["speedup_learned_vs_classical"] = out["classical"]["ms_per_map"] / out["learned"]["ms_per_map"]
+    plan.close()
+    net.close()
     return out
 
 

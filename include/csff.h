@@ -229,10 +229,12 @@ csff_status csff_net_loss_grad(csff_net* net, int B, int H, int W, const void* r
 csff_status csff_net_train_step(csff_net* net, int B, int H, int W, const void* r_dev, const void* q_dev,
                                 const double* c_host, int margin, float lr, float* loss_host, void* stream);
 /* Attach (net != NULL) or detach the learned step on levels 0..levels-1 of a
-   red-black plan's FP32 cycles.  A mixed-precision refinement step that
-   reduces the residual by less than the factor `guard` turns the learned step
-   off for the rest of that solve (csff_info.flags bit 1).  The plan keeps a
-   pointer to the net; the net must outlive the attachment. */
+   red-black plan's FP32 cycles (mixed-precision solves).  The first two
+   refinement steps of each solve run plain red-black sweeps; the second sets
+   the reference reduction factor f = min(its factor, guard); a later learned step
+   that reduces the residual by less than f turns the learned step off for the
+   rest of that solve (csff_info.flags bit 1).  The plan keeps a pointer to
+   the net; the net must outlive the attachment. */
 csff_status csff_plan_set_learned(csff_plan* plan, csff_net* net, int levels, double guard);
 /* FP32 copy of a level's q = k^2(1 + chi) (c64, m_l^d, device) and its
    constant c = e^{-2i gamma}/h_l^2 (2 doubles, host): the operator the learned

@@ -148,9 +148,29 @@ def u_incident(prob: Problem, eta, n: int | None = None) -> np.ndarray:
     return np.exp(1j * prob.k * rot * ph) * np.ones((n - 2,) * prob.dim)
 
 
+def chi_u_incident(prob: Problem, eta, n: int | None = None) -> np.ndarray:
+    """chi(z) u_in(z) = sum_g A_g exp(-sum_c (z_c - c_c)^2 / w_g + i k eta.z),
+    each term one exponential of its summed exponent: the factors alone can
+    exceed the FP64 range (|u_in| = e^{k sin(gamma) |eta.x|}) where the product
+    does not."""
+    n = prob.n if n is None else n
+    rot = np.exp(1j * prob.gamma)
+    X = _axis_coords(prob.dim, n, prob.lo, prob.hi)
+    ph = 0.0
+    for c in range(prob.dim):
+        ph = ph + eta[c] * X[c]
+    out = np.zeros((n - 2,) * prob.dim, dtype=np.complex128)
+    for g in prob.gaussians:
+        s = 0.0
+        for c in range(prob.dim):
+            s = s + (rot * X[c] - g.center[c]) ** 2
+        out = out + complex(g.amp) * np.exp(-s / g.width + 1j * prob.k * rot * ph)
+    return out
+
+
 def rhs(prob: Problem, eta) -> np.ndarray:
     """b = k^2 chi(z) u_in(z), the source of eq. (helmholtz_cc)."""
-    return prob.k ** 2 * chi_at_nodes(prob) * u_incident(prob, eta)
+    return prob.k ** 2 * chi_u_incident(prob, eta)
 
 
 # ---------------------------------------------------------------------------
@@ -423,7 +443,7 @@ def far_field(prob: Problem, u: np.ndarray, eta, alphas, return_terms_norm=False
     alphas = np.atleast_2d(np.asarray(alphas, dtype=np.float64))
     rot = np.exp(1j * prob.gamma)
     X = _axis_coords(prob.dim, prob.n, prob.lo, prob.hi)
-    g = chi_at_nodes(prob) * (u_incident(prob, eta) + u)
+    g = chi_u_incident(prob, eta) + chi_at_nodes(prob) * u
     with np.errstate(divide="ignore"):
         lg = np.log(np.abs(g))
     ag = np.angle(g)

@@ -143,12 +143,12 @@ __device__ void ph_rhs(const BInst& I, BState* st, int i, int t) {
   int mx = -2000;
   for (long long j = (long long)t * PT + threadIdx.x; j < min((long long)(t + 1) * PT, I.N); j += blockDim.x) {
     int ix = (int)(j % m), iy = (int)(j / m);
-    double2 chi = make_double2(0, 0);
+    double2 cu = make_double2(0, 0);      // chi u_in, axis factors paired first
     for (int g = 0; g < I.n_gauss; ++g) {
       const double2* tb = I.chi + (size_t)g * 2 * m;
-      chi = cadd(chi, cmul(tb[ix], tb[m + iy]));
+      cu = cadd(cu, cmul(cmul(tb[ix], I.uinc[ix]), cmul(tb[m + iy], I.uinc[m + iy])));
     }
-    double2 bj = cscale(cmul(chi, cmul(I.uinc[ix], I.uinc[m + iy])), I.k2);
+    double2 bj = cscale(cu, I.k2);
     I.b64[j] = bj;
     I.r64[j] = bj;
     I.u64[0][j] = make_double2(0, 0);

@@ -424,9 +424,13 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
   int cycles = 0, refinements = 0;
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
   const long long key0 = (2ll << 40) + (long long)(eb + 8192) * 64 + inner;
-  P->learned_off = false;
+  // with a learned smoother the first two refinement steps run plain
+  // red-black sweeps and the second sets the reference factor; a later learned
+  // step that reduces the residual less than min(reference, guard) hands the
+  // rest of the solve back to plain sweeps
+  P->learned_off = P->net != nullptr;
   bool fell_back = false;
-  double prev = 1.0;
+  double prev = 1.0, ref_factor = P->learned_guard;
   CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, P->stream), "residual");
   CS(norm64(P, L.r64, eb, 0));
   for (;;) {
@@ -435,9 +439,14 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
     cycles += inner;
     ++refinements;
     const double rel = P->red_host[0] / nb;
-    // a learned step that fails to cut the residual by the guard factor hands
-    // the rest of the solve back to plain red-black sweeps
-    if (learned && rel > P->learned_guard * prev) {
+    const double factor = rel / prev;
+    if (P->net && refinements <= 2) {
+      // two plain steps: the second one's factor is the reference
+      if (refinements == 2) {
+        ref_factor = std::min(factor, P->learned_guard);
+        P->learned_off = false;
+      }
+    } else if (learned && factor > ref_factor) {
       P->learned_off = true;
       fell_back = true;
     }
@@ -675,11 +684,12 @@ csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, doubl
     return CSFF_ERR_UNSUPPORTED;
   }
   if (net) CS(csff::net_reserve(net, P->lv[0].N));
-  if (net && !P->net) P->fused_saved = P->fused_lc;
+  if (net && !P->net) P->fused_saved = P->fused_lc;      // attach: remember the fused split
+  if (!net && P->net) P->fused_lc = P->fused_saved;      // detach: restore it
+  if (net) P->fused_lc = -1;                             // the learned step runs in the per-level path
   P->net = net;
   P->learned_levels = net ? levels : 0;
   P->learned_guard = guard;
-  P->fused_lc = net ? -1 : P->fused_saved;   // the learned step runs in the per-level path
   if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
   return CSFF_OK;
 }

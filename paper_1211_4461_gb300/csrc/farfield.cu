@@ -42,15 +42,21 @@ __global__ void k_gfield(Tabs8 tabs, int n_gauss, const double2* __restrict__ ui
   int iz = (D == 3) ? (int)blockIdx.z : 0;
   if (ix >= m || iy >= m) return;
   long long idx = ((long long)iz * m + iy) * m + ix;
-  double2 chi = make_double2(0, 0);
+  // g = chi u_in + chi u; chi u_in with each axis' Gaussian factor paired with
+  // its incident-wave factor first (no partial product beyond the FP64 range)
+  double2 chi = make_double2(0, 0), cu = make_double2(0, 0);
   for (int q = 0; q < n_gauss; ++q) {
-    double2 v = cmul(tabs.p[q][ix], tabs.p[q][m + iy]);
-    if (D == 3) v = cmul(v, tabs.p[q][2 * m + iz]);
+    const double2* t = tabs.p[q];
+    double2 v = cmul(t[ix], t[m + iy]);
+    double2 w = cmul(cmul(t[ix], uinc[ix]), cmul(t[m + iy], uinc[m + iy]));
+    if (D == 3) {
+      v = cmul(v, t[2 * m + iz]);
+      w = cmul(w, cmul(t[2 * m + iz], uinc[2 * m + iz]));
+    }
     chi = cadd(chi, v);
+    cu = cadd(cu, w);
   }
-  double2 ui = cmul(uinc[ix], uinc[m + iy]);
-  if (D == 3) ui = cmul(ui, uinc[2 * m + iz]);
-  g[idx] = cmul(chi, cadd(ui, u[idx]));
+  g[idx] = cadd(cu, cmul(chi, u[idx]));
 }
 
 // Phase tables.  x-table rows k < n_ux: P_x(k, i) 2^-s1[k]; y/z tables for
@@ -207,6 +213,90 @@ __global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict
   }
 }
 
+// ---- 3D sum-factorised contraction --------------------------------------------
+// stage A: T1[t][col] = sum_iz Pz[t][iz] g[iz][col] for a group of TB distinct
+// z-components t (col = iy m + ix); each thread keeps TB sums in registers so
+// g is streamed once per group.
+template <int TB>
+__global__ void __launch_bounds__(256) k_ff3_stageA(const double2* __restrict__ zt, int T, int t0,
+                                                    const double2* __restrict__ g, int m, long long ncol,
+                                                    double2* __restrict__ T1) {
+  __shared__ double2 zs[TB][32];
+  const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double2 acc[TB];
+#pragma unroll
+  for (int t = 0; t < TB; ++t) acc[t] = make_double2(0, 0);
+  for (int k0 = 0; k0 < m; k0 += 32) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < TB * 32; i += blockDim.x) {
+      int t = i / 32, kk = i % 32;
+      zs[t][kk] = (t0 + t < T && k0 + kk < m) ? zt[(long long)(t0 + t) * m + k0 + kk] : make_double2(0, 0);
+    }
+    __syncthreads();
+    if (col < ncol) {
+      const int kend = min(32, m - k0);
+      for (int kk = 0; kk < kend; ++kk) {
+        double2 gv = g[(long long)(k0 + kk) * ncol + col];
+#pragma unroll
+        for (int t = 0; t < TB; ++t) {
+          double2 z = zs[t][kk];
+          acc[t].x = fma(z.x, gv.x, fma(-z.y, gv.y, acc[t].x));
+          acc[t].y = fma(z.x, gv.y, fma(z.y, gv.x, acc[t].y));
+        }
+      }
+    }
+  }
+  if (col >= ncol) return;
+#pragma unroll
+  for (int t = 0; t < TB; ++t)
+    if (t0 + t < T) T1[(long long)(t0 + t) * ncol + col] = acc[t];
+}
+
+// stage B: T2[a][ix] = sum_iy Py[a][iy] T1[t(a)][iy m + ix]
+__global__ void __launch_bounds__(128) k_ff3_stageB(const double2* __restrict__ yt, const int* __restrict__ trow,
+                                                    const double2* __restrict__ T1, int m,
+                                                    double2* __restrict__ T2) {
+  extern __shared__ double2 ys[];
+  const int a = blockIdx.y;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) ys[i] = yt[(long long)a * m + i];
+  __syncthreads();
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= m) return;
+  const double2* base = T1 + (long long)trow[a] * m * m + ix;
+  double2 acc = make_double2(0, 0);
+  for (int iy = 0; iy < m; ++iy) {
+    double2 y = ys[iy], t = base[(long long)iy * m];
+    acc.x = fma(y.x, t.x, fma(-y.y, t.y, acc.x));
+    acc.y = fma(y.x, t.y, fma(y.y, t.x, acc.y));
+  }
+  T2[(long long)a * m + ix] = acc;
+}
+
+// per-angle tables for the 3D path: ztab over distinct z-components, y and x
+// tables per angle: P_c(a, i) = exp(-i k e^{i gamma} alpha_c x_i)
+__global__ void k_phase_tables3(const double* __restrict__ uz, int n_uz, const double* __restrict__ alpha,
+                                int n_ang, int m, double lo, double h, double k, double sg, double cg,
+                                double2* __restrict__ ztab, double2* __restrict__ ytab, double2* __restrict__ xtab) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int row = blockIdx.y;
+  if (i >= m) return;
+  double x = lo + (double)(i + 1) * h;
+  auto ph = [&](double a) {
+    double mag = exp(k * sg * a * x);
+    double sn, cs;
+    sincos(k * cg * a * x, &sn, &cs);
+    return make_double2(mag * cs, -mag * sn);
+  };
+  if (row < n_uz) {
+    ztab[(long long)row * m + i] = ph(uz[row]);
+  } else {
+    int a = row - n_uz;
+    if (a >= n_ang) return;
+    ytab[(long long)a * m + i] = ph(alpha[(long long)a * 3 + 1]);
+    xtab[(long long)a * m + i] = ph(alpha[(long long)a * 3 + 0]);
+  }
+}
+
 }  // namespace
 
 static cudaError_t ensure(void** p, size_t& cap, size_t need, csff_plan* P) {
@@ -253,7 +343,6 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
       (e = ensure((void**)&B.dxt, B.xt, sizeof(double2) * (size_t)n_ux * m, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dyt, B.yt, sizeof(double2) * (size_t)n_ang * m, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dzt, B.zt, sizeof(double2) * (size_t)n_ang * m, P)) != cudaSuccess ||
-      (e = ensure((void**)&B.dT, B.T, sizeof(double2) * (size_t)n_trow * R, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dal, B.al, sizeof(double) * (size_t)n_ang * d, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dux, B.ux, sizeof(double) * (size_t)n_ux, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dxr, B.xr, sizeof(int) * (size_t)n_ang, P)) != cudaSuccess ||
@@ -294,6 +383,76 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   count_launch();
   if ((e = launch_max_exp(B.dg, L.N, B.dmisc, s)) != cudaSuccess) return cuda_fail(e, "max exponent");
   const double sg = std::sin(P->prob.gamma), cg = std::cos(P->prob.gamma);
+  if (d == 3) {
+    // sum-factorised path when no intermediate can leave the FP64 range:
+    // |T1| <= m max|Pz| max|g|, |T2| <= m max|Py| |T1|, terms of stage C
+    // scaled from their own maximum
+    int gmax = 0;
+    if ((e = cudaMemcpyAsync(&gmax, B.dmisc, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "far field range");
+    const double R = std::max(std::fabs(P->prob.box_lo), std::fabs(P->prob.box_hi));
+    const double lp = P->prob.k * sg * R / std::log(2.0);
+    const double bound = gmax + 2 * lp + 2 * std::log2((double)m) + 4;
+    if (bound < 1000.0 && gmax < 2000) {
+      std::vector<double> uz;
+      std::vector<int> tr(n_ang);
+      std::map<double, int> zseen;
+      for (int a = 0; a < n_ang; ++a) {
+        double v = alpha_host[(size_t)a * 3 + 2];
+        auto it = zseen.find(v);
+        if (it == zseen.end()) { it = zseen.emplace(v, (int)uz.size()).first; uz.push_back(v); }
+        tr[a] = it->second;
+      }
+      const int n_uz = (int)uz.size();
+      const long long ncol = (long long)m * m;
+      // scratch: ztab in dxt, y/x tables in dyt/dzt, T1 in dT, T2 after T1, rows in dxr, zero s1
+      if ((e = ensure((void**)&B.dxt, B.xt, sizeof(double2) * (size_t)std::max(n_uz, 1) * m, P)) != cudaSuccess ||
+          (e = ensure((void**)&B.dT, B.T, sizeof(double2) * ((size_t)n_uz * ncol + (size_t)n_ang * m), P)) !=
+              cudaSuccess ||
+          (e = ensure((void**)&B.dux, B.ux, sizeof(double) * (size_t)std::max(n_uz, 1), P)) != cudaSuccess ||
+          (e = ensure((void**)&B.ds1, B.s1, sizeof(int) * (size_t)n_ang, P)) != cudaSuccess)
+        return cuda_fail(e, "far field scratch");
+      std::vector<int> ident(n_ang);
+      for (int a = 0; a < n_ang; ++a) ident[a] = a;
+      if ((e = cudaMemcpyAsync(B.dux, uz.data(), sizeof(double) * n_uz, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(B.dxr, tr.data(), sizeof(int) * n_ang, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+          (e = cudaMemsetAsync(B.ds1, 0, sizeof(int) * n_ang, s)) != cudaSuccess)
+        return cuda_fail(e, "far field tables");
+      dim3 tg3((m + 127) / 128, n_uz + n_ang);
+      k_phase_tables3<<<tg3, 128, 0, s>>>(B.dux, n_uz, B.dal, n_ang, m, P->prob.box_lo, L.h, P->prob.k, sg, cg,
+                                          B.dxt, B.dyt, B.dzt);
+      double2* T1 = B.dT;
+      double2* T2 = B.dT + (size_t)n_uz * ncol;
+      {
+        ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_uz * m + (double)ncol * m + (double)n_uz * ncol),
+                     8.0 * (double)n_uz * (double)ncol * m);
+        for (int t0 = 0; t0 < n_uz; t0 += 16)
+          k_ff3_stageA<16><<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(B.dxt, n_uz, t0, B.dg, m, ncol, T1);
+      }
+      k_ff3_stageB<<<dim3((m + 127) / 128, n_ang), 128, sizeof(double2) * m, s>>>(B.dyt, B.dxr, T1, m, T2);
+      // stage C: F[a] = pref sum_ix Px[a][ix] T2[a][ix]  (the 2D stage-2 kernel on rows a)
+      if ((e = cudaMemcpyAsync(B.dxr, ident.data(), sizeof(int) * n_ang, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "far field rows");
+      const double hd = std::pow(L.h, 3);
+      const double k2 = P->prob.k * P->prob.k;
+      double2 pref = make_double2(k2 * hd * std::cos(3 * P->prob.gamma), k2 * hd * std::sin(3 * P->prob.gamma));
+      k_ff_stage2<2><<<n_ang, 256, 0, s>>>(T2, B.dxr, B.ds1, B.dzt, B.dzt, m, pref, F, F_exp, F_exp != nullptr,
+                                           B.dmisc + 1);
+      count_launch(3 + (n_uz + 15) / 16);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "far field 3D kernels");
+      if (scaled) {
+        int flag = 0;
+        if ((e = cudaMemcpyAsync(&flag, B.dmisc + 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+          return cuda_fail(e, "far field flag");
+        *scaled = flag != 0;
+      }
+      return CSFF_OK;
+    }
+  }
+  if ((e = ensure((void**)&B.dT, B.T, sizeof(double2) * (size_t)n_trow * R, P)) != cudaSuccess)
+    return cuda_fail(e, "far field scratch");
   dim3 tg((m + 127) / 128, n_ux + n_ang);
   k_phase_tables<<<tg, 128, 0, s>>>(B.dux, n_ux, B.dal, n_ang, d, m, P->prob.box_lo, L.h, P->prob.k, sg, cg,
                                     B.dmisc, B.dxt, B.dyt, B.dzt, B.ds1, B.dmisc + 1);

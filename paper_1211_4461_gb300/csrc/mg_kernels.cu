@@ -263,10 +263,17 @@ __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uin
                       double2* __restrict__ b) {
   int ix, iy, iz; long long idx;
   if (!thread_point<D>(m, ix, iy, iz, idx)) return;
-  double2 chi = chi_point<D>(tabs.p, n_gauss, m, ix, iy, iz);
-  double2 ui = cmul(uinc[ix], uinc[m + iy]);
-  if (D == 3) ui = cmul(ui, uinc[2 * m + iz]);
-  b[idx] = cscale(cmul(chi, ui), k2);
+  // chi u_in = sum_g prod_c (E_{g,c} U_c): each axis' Gaussian factor is paired
+  // with its incident-wave factor first, so no partial product leaves the
+  // FP64 range when chi u_in itself does not
+  double2 acc = make_double2(0, 0);
+  for (int g = 0; g < n_gauss; ++g) {
+    const double2* t = tabs.p[g];
+    double2 v = cmul(cmul(t[ix], uinc[ix]), cmul(t[m + iy], uinc[m + iy]));
+    if (D == 3) v = cmul(v, cmul(t[2 * m + iz], uinc[2 * m + iz]));
+    acc = cadd(acc, v);
+  }
+  b[idx] = cscale(acc, k2);
 }
 
 // ---- mixed precision ----------------------------------------------------------

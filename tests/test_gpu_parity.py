@@ -228,6 +228,23 @@ def test_far_field_on_symmetric_and_shifted_boxes(csff, lo, hi):
     assert np.abs(F.cpu().numpy() - Fo).max() <= 1e-13 * (tn * 2.0 ** e2).max()
 
 
+def test_rhs_with_factor_overflow(csff):
+    """45-degree incidence, k = 52, w = 1 on [-20,20]^2: the incident wave alone
+    exceeds the FP64 range at the upstream corner, chi u_in does not; the
+    device source matches the oracle's."""
+    c = W.mixed_2d(52.0, n=65)
+    c["problem"]["gaussians"] = [W.gauss(-1.0, 1.0)]
+    c["opts"]["coarsest_n"] = 5
+    plan = csff.Plan(c["problem"], c["opts"])
+    eta = np.array([[math.sqrt(0.5), math.sqrt(0.5)]])
+    b = torch.empty(plan.N, dtype=torch.complex128, device="cuda")
+    plan.rhs(eta, b)
+    ref = O.rhs(O.problem_from_dict(c["problem"]), eta[0]).ravel()
+    got = b.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
 def test_rhs(setup):
     c, plan, p, levels = setup
     eta = np.vstack([c["eta"], -c["eta"]])

@@ -348,3 +348,23 @@ def test_far_field_extended_range():
         P = np.exp(-1j * p.k * np.exp(1j * p.gamma) * (alpha[0] * X[0] + alpha[1] * X[1]))
         ref = p.k ** 2 * np.exp(2j * p.gamma) * p.h ** 2 * np.sum(P * g)
         assert abs(F[a] - ref) <= 1e-12 * np.sum(np.abs(P * g)) * p.k ** 2 * p.h ** 2
+
+
+def test_rhs_stays_finite_for_oblique_incidence_at_large_k():
+    """k = 52, w = 1 on [-20,20]^2 with eta at 45 degrees: |u_in| alone reaches
+    e^{k sin(g) R sqrt 2} = e^{735} (beyond FP64) at the upstream corner, while
+    chi u_in peaks at e^{338} (t* = k sin(g) w / (2 cos 2g) = 26 along -eta);
+    the source is evaluated without overflow and equals the product of the two
+    factors wherever those fit."""
+    p = O.Problem(2, 65, -20.0, 20.0, math.pi / 6, 52.0, [O.Gaussian(-1.0, 1.0)])
+    eta = [math.sqrt(0.5), math.sqrt(0.5)]
+    b = O.rhs(p, eta)
+    assert np.all(np.isfinite(b))
+    assert np.log(np.abs(b).max() / p.k ** 2) <= 338.5
+    with np.errstate(over="ignore", invalid="ignore"):
+        prod = p.k ** 2 * O.chi_at_nodes(p) * O.u_incident(p, eta)
+    fin = np.isfinite(prod)
+    assert fin.sum() > 0.5 * fin.size and not fin.all()
+    # exponents up to ~340 and phases up to ~1500 rad: both evaluations round
+    # them at ~1e-16 relative, i.e. ~1e-13 relative in the values
+    assert np.all(np.abs(b[fin] - prod[fin]) <= 1e-10 * np.abs(prod[fin]) + 1e-14 * np.abs(b).max())
