@@ -484,7 +484,45 @@ def measure_learned(csff, torch, dev, stream, flush):
     out["speedup_learned_vs_classical"] = out["classical"]["ms_per_map"] / out["learned"]["ms_per_map"]
     plan.close()
     net.close()
+    out["small_grid_129"] = measure_learned_small(csff, torch, dev, stream)
     return out
+
+
+def measure_learned_small(csff, torch, dev, stream):
+    """129^2 on [-20,20]^2, k ~ U[3,5] (k h 0.9-1.6): trained on 24 seeded
+    problems, evaluated on 4 held-out seeds (V-cycles to 1e-8)."""
+    from paper_1211_4461_gb300 import learned as LR
+    import math as _m
+    opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
+            "max_cycles": 300, "inner_cycles": 3}
+
+    def probs(seeds):
+        out = []
+        for s in seeds:
+            rng = np.random.Generator(np.random.PCG64(1000 + s))
+            k = float(rng.uniform(3.0, 5.0))
+            amp = float(rng.uniform(-1.5, -0.5))
+            w = float(rng.uniform(2.0, 5.0))
+            t = float(rng.uniform(0, 2 * _m.pi))
+            out.append((W.problem(2, 129, 20.0, _m.pi / 6, k, [W.gauss(amp, w)]),
+                        np.array([_m.cos(t), _m.sin(t)])))
+        return out
+
+    data = LR.collect_patches(probs(range(24)), opts, n_cycles=5, patch=48, per_field=6, seed=1)
+    net = csff.Net(LR.init_weights(7))
+    hist = LR.train(net, data, steps=800, batch=32, lr=2e-3, margin=4, seed=2)
+    rows = []
+    for prob, eta in probs([100, 101, 102, 103]):
+        plan = csff.Plan(prob, dict(opts, precision="mixed"), stream=stream)
+        u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
+        _, b = plan.solve(np.atleast_2d(eta), u)
+        plan.set_learned(net, levels=1)
+        _, l = plan.solve(np.atleast_2d(eta), u)
+        rows.append({"classical": b[0]["cycles"], "learned": l[0]["cycles"], "flags": l[0]["flags"]})
+        plan.close()
+    net.close()
+    return {"loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:])), "held_out": rows,
+            "cycle_ratio": sum(r["learned"] for r in rows) / max(1, sum(r["classical"] for r in rows))}
 
 
 def main():
