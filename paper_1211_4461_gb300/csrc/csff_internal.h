@@ -58,6 +58,10 @@ struct FFBuffers {
   double2 *dg = nullptr, *dxt = nullptr, *dyt = nullptr, *dzt = nullptr, *dT = nullptr;
   double *dal = nullptr, *dux = nullptr;
   int *dxr = nullptr, *ds1 = nullptr, *dmisc = nullptr;
+  // double-float stage 1: split operands, block exponents, spread flags [2]
+  size_t xdf = 0, gdf = 0, exs = 0, egs = 0;
+  float4 *dxdf = nullptr, *dgdf = nullptr;
+  int *dex = nullptr, *deg = nullptr, *dspread = nullptr;
 };
 
 }  // namespace csff

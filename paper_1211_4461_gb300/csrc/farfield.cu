@@ -106,9 +106,24 @@ __global__ void k_phase_tables(const double* __restrict__ ux, int n_ux, const do
 // give several CTAs per SM and a short last wave.
 constexpr int S1_BM = 16, S1_BN = 32, S1_BK = 16;
 
+// Choice between the two stage-1 kernels, taken on the device from the block
+// spreads (max - min exponent inside one block of one row) of the two operands.
+// With x' = 2^-ex x and g' = 2^-eg g every block holds a node where |x'| >= 1/2
+// and one where |g'| >= 1/2, so the largest scaled product of a block is at
+// least 2^-(min(sx, sg) + 2); products flushed below FP32's subnormal range
+// (2^-149) then cost at most 2^-149 * DKB absolute, far under the double-float
+// rounding (2^-47 relative) of that largest product when min(sx, sg) <= 90.
+constexpr int DF_SPREAD_LIMIT = 90;       // bits
+constexpr int DF_NONFINITE = 100000;      // spread written for a block with a NaN/Inf
+__device__ __forceinline__ bool df_selected(const int* __restrict__ spread) {
+  const int sx = spread[0], sg = spread[1];
+  return sx < DF_NONFINITE && sg < DF_NONFINITE && min(sx, sg) <= DF_SPREAD_LIMIT;
+}
+
 __global__ void __launch_bounds__(256) k_ff_stage1(const double2* __restrict__ X, int M,
                                                    const double2* __restrict__ G, int N, int K,
-                                                   double2* __restrict__ T) {
+                                                   double2* __restrict__ T, const int* __restrict__ skip_if_df) {
+  if (skip_if_df && df_selected(skip_if_df)) return;   // the double-float kernel ran
   __shared__ double2 As[S1_BK][S1_BM];
   __shared__ double2 Bs[S1_BK][S1_BN + 1];
   const int tid = threadIdx.x;
@@ -213,6 +228,170 @@ __global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict
   }
 }
 
+// ---- stage 1 in double-float arithmetic -------------------------------------
+// FP64 runs at 1/61 of the FP32 rate on this part, so stage 1 can also run in
+// double-float arithmetic (value = hi + lo, two FP32 numbers, ~48-bit
+// significand) on the FP32 pipes: products by Dekker's splitting with FMA
+// (TwoProd), sums by Knuth's TwoSum.  Both operands are cut into blocks of
+// DKB consecutive x-nodes; inside a block every row of P_x and every row of g
+// is scaled by a power of two (ex, eg: exponent of the block maximum), so all
+// block sums (|.| <= 2 DKB) are formed in double-float and merged into a
+// running double-float sum that carries its own power-of-two exponent:
+//   T[k][rho] = sum_b 2^(ex[k][b] + eg[rho][b]) sum_{i in b} P'_x(k, i) g'[rho][i].
+// The kernel runs only when df_selected() holds for the measured spreads,
+// else the FP64 kernel does.
+constexpr int DKB = 32;
+
+struct df { float hi, lo; };
+
+// split x (|x| <= 2) into hi + lo
+__device__ __forceinline__ df df_of(double x) {
+  float h = (float)x;
+  return df{h, (float)(x - (double)h)};
+}
+
+// s += a * b  (double-float; s kept unnormalised: hi via TwoSum, lo collects errors)
+__device__ __forceinline__ void df_mac(df& s, df a, df b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);          // exact error of the leading product
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float t = s.hi + p;                      // TwoSum(s.hi, p)
+  float v = t - s.hi;
+  float err = (s.hi - (t - v)) + (p - v);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+__device__ __forceinline__ int ilog2_up(double a) {   // exponent e with a < 2^e (a > 0)
+  int e;
+  frexp(a, &e);
+  return e;
+}
+
+// one warp per (row, block): block exponent of |v| (upper bound), scaled
+// double-float split, and the row-block spread (max - min exponent) into *spread
+__global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, float4* __restrict__ vdf,
+                             int* __restrict__ ev, int* __restrict__ spread) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nb = (m + DKB - 1) / DKB;
+  if (warp >= nrows * nb) return;
+  const int row = warp / nb, b = warp % nb;
+  const int i = b * DKB + lane;
+  double2 x = (i < m) ? v[(long long)row * m + i] : make_double2(0, 0);
+  double a = fmax(fabs(x.x), fabs(x.y));
+  int e = (a > 0.0 && isfinite(a)) ? ilog2_up(a) : -100000;
+  int emin = (a > 0.0 && isfinite(a)) ? e : 100000;
+  for (int o = 16; o > 0; o >>= 1) {
+    e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  }
+  const bool bad = __any_sync(0xffffffffu, !isfinite(a));   // non-finite: the FP64 kernel runs
+  const int eb = (e == -100000 || bad) ? 0 : e;
+  if (lane == 0) {
+    ev[(long long)row * nb + b] = eb;
+    int sp = bad ? DF_NONFINITE : ((e == -100000) ? 0 : e - emin);
+    atomicMax(spread, sp);
+  }
+  // ldexp on the value itself: 2^-eb alone overflows for subnormal blocks
+  const bool zero = e == -100000 || bad;
+  df re = df_of(zero ? 0.0 : ldexp(x.x, -eb)), im = df_of(zero ? 0.0 : ldexp(x.y, -eb));
+  vdf[(long long)row * nb * DKB + b * DKB + lane] = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// 2^d as a float for d <= 0 (0 below the subnormal range): exact power of two
+__device__ __forceinline__ float pow2f_neg(int d) {
+  if (d >= -126) return __int_as_float((d + 127) << 23);
+  if (d >= -149) return __int_as_float(1 << (d + 149));
+  return 0.f;
+}
+
+// running double-float sum with its own power-of-two exponent:
+// value = (hi + lo) 2^E; merging a block sum s 2^Es rescales the smaller of the
+// two exactly (powers of two) and adds with TwoSum, all in FP32
+struct dfacc { float hi, lo; int E; };
+
+__device__ __forceinline__ void dfacc_merge2(dfacc& re, dfacc& im, df sr, df si, int Es) {
+  if (sr.hi == 0.f && si.hi == 0.f && sr.lo == 0.f && si.lo == 0.f) return;
+  const int En = max(re.E, Es);                    // re.E == im.E always
+  const float fa = pow2f_neg(re.E - En), fs = pow2f_neg(Es - En);
+  auto add = [&](dfacc& a, df x) {
+    float ah = a.hi * fa, al = a.lo * fa, xh = x.hi * fs, xl = x.lo * fs;
+    float t = ah + xh, v = t - ah;
+    float err = (ah - (t - v)) + (xh - v);
+    float lo = al + xl + err;
+    float h = t + lo;                              // renormalise (fast TwoSum)
+    a.lo = lo - (h - t);
+    a.hi = h;
+    a.E = En;
+  };
+  add(re, sr);
+  add(im, si);
+}
+
+// T[k][rho] over blocks; 16 (k) x 64 (rho) output tile, 1 x 4 outputs per thread
+constexpr int DF_BM = 16, DF_BN = 64;
+
+__global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__ X, const int* __restrict__ ex, int M,
+                                                      const float4* __restrict__ G, const int* __restrict__ eg, int N,
+                                                      int nb, const int* __restrict__ spread,
+                                                      double2* __restrict__ T) {
+  if (!df_selected(spread)) return;      // the FP64 kernel takes this launch
+  __shared__ float4 As[DF_BM][DKB + 1];
+  __shared__ float4 Bs[DF_BN][DKB + 1];
+  __shared__ int eA[DF_BM], eB[DF_BN];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
+  dfacc accr[4], acci[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    accr[j] = dfacc{0.f, 0.f, -100000};
+    acci[j] = dfacc{0.f, 0.f, -100000};
+  }
+  for (int b = 0; b < nb; ++b) {
+    for (int i = tid; i < DF_BM * DKB; i += 256) {
+      int r = i / DKB, kk = i % DKB, gm = m0 + r;
+      As[r][kk] = (gm < M) ? X[((long long)gm * nb + b) * DKB + kk] : make_float4(0, 0, 0, 0);
+    }
+    for (int i = tid; i < DF_BN * DKB; i += 256) {
+      int r = i / DKB, kk = i % DKB, gn = n0 + r;
+      Bs[r][kk] = (gn < N) ? G[((long long)gn * nb + b) * DKB + kk] : make_float4(0, 0, 0, 0);
+    }
+    if (tid < DF_BM) eA[tid] = (m0 + tid < M) ? ex[(long long)(m0 + tid) * nb + b] : 0;
+    if (tid >= 64 && tid < 64 + DF_BN) eB[tid - 64] = (n0 + tid - 64 < N) ? eg[(long long)(n0 + tid - 64) * nb + b] : 0;
+    __syncthreads();
+    df sr[4], si[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { sr[j] = df{0.f, 0.f}; si[j] = df{0.f, 0.f}; }
+#pragma unroll 2
+    for (int kk = 0; kk < DKB; ++kk) {
+      float4 a = As[ty][kk];
+      df ar{a.x, a.y}, ai{a.z, a.w}, nai{-a.z, -a.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float4 bb = Bs[tx + 16 * j][kk];
+        df br{bb.x, bb.y}, bi{bb.z, bb.w};
+        df_mac(sr[j], ar, br);
+        df_mac(sr[j], nai, bi);
+        df_mac(si[j], ar, bi);
+        df_mac(si[j], ai, br);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dfacc_merge2(accr[j], acci[j], sr[j], si[j], eA[ty] + eB[tx + 16 * j]);
+    __syncthreads();
+  }
+  const int gm = m0 + ty;
+  if (gm >= M) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int gn = n0 + tx + 16 * j;
+    if (gn >= N) continue;
+    T[(long long)gm * N + gn] = make_double2(ldexp((double)accr[j].hi + (double)accr[j].lo, accr[j].E),
+                                             ldexp((double)acci[j].hi + (double)acci[j].lo, acci[j].E));
+  }
+}
+
 // ---- 3D sum-factorised contraction --------------------------------------------
 // stage A: T1[t][col] = sum_iz Pz[t][iz] g[iz][col] for a group of TB distinct
 // z-components t (col = iy m + ix); each thread keeps TB sums in registers so
@@ -310,7 +489,8 @@ static cudaError_t ensure(void** p, size_t& cap, size_t need, csff_plan* P) {
 void free_ff_buffers(csff_plan* P) {
   FFBuffers& b = P->ff;
   for (void* p : {(void*)b.dg, (void*)b.dxt, (void*)b.dyt, (void*)b.dzt, (void*)b.dT, (void*)b.dal,
-                  (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc})
+                  (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc, (void*)b.dxdf, (void*)b.dgdf,
+                  (void*)b.dex, (void*)b.deg, (void*)b.dspread})
     if (p) cudaFree(p);
   b = FFBuffers{};
 }
@@ -457,13 +637,32 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   k_phase_tables<<<tg, 128, 0, s>>>(B.dux, n_ux, B.dal, n_ang, d, m, P->prob.box_lo, L.h, P->prob.k, sg, cg,
                                     B.dmisc, B.dxt, B.dyt, B.dzt, B.ds1, B.dmisc + 1);
   count_launch();
+  // operands of the double-float contraction
+  const int nbk = (m + DKB - 1) / DKB;
+  if ((e = ensure((void**)&B.dxdf, B.xdf, sizeof(float4) * (size_t)n_ux * nbk * DKB, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dgdf, B.gdf, sizeof(float4) * (size_t)R * nbk * DKB, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dex, B.exs, sizeof(int) * (size_t)n_ux * nbk, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.deg, B.egs, sizeof(int) * (size_t)R * nbk, P)) != cudaSuccess)
+    return cuda_fail(e, "far field scratch");
+  if (!B.dspread && (e = cudaMalloc((void**)&B.dspread, 2 * sizeof(int))) != cudaSuccess)
+    return cuda_fail(e, "far field scratch");
+  if ((e = cudaMemsetAsync(B.dspread, 0, 2 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
+  {
+    const long long wx = (long long)n_ux * nbk, wg = (long long)R * nbk;
+    k_split_rows<<<(unsigned)((wx * 32 + 255) / 256), 256, 0, s>>>(B.dxt, m, n_ux, B.dxdf, B.dex, B.dspread);
+    k_split_rows<<<(unsigned)((wg * 32 + 255) / 256), 256, 0, s>>>(B.dg, m, (int)R, B.dgdf, B.deg, B.dspread + 1);
+    count_launch(2);
+  }
   dim3 g1((unsigned)((R + S1_BN - 1) / S1_BN), (n_ux + S1_BM - 1) / S1_BM);
+  dim3 gdf((unsigned)((R + DF_BN - 1) / DF_BN), (n_ux + DF_BM - 1) / DF_BM);
   {
     ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_ux * m + (double)R * m + (double)n_ux * R),
                  8.0 * (double)n_ux * (double)R * m);
-    k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT);
+    // exactly one of the two writes T (device-side range check on the spreads)
+    k_ff_stage1_df<<<gdf, 256, 0, s>>>(B.dxdf, B.dex, n_ux, B.dgdf, B.deg, (int)R, nbk, B.dspread, B.dT);
+    k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT, B.dspread);
   }
-  count_launch();
+  count_launch(2);
   const double hd = std::pow(L.h, d);
   const double k2 = P->prob.k * P->prob.k;
   double2 pref = make_double2(k2 * hd * std::cos(d * P->prob.gamma), k2 * hd * std::sin(d * P->prob.gamma));
