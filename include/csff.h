@@ -156,7 +156,9 @@ csff_status csff_rhs(csff_plan* plan, int n_rhs, const double* eta_host, void* b
    Returns the worst status over the right-hand sides (CSFF_OK if all met
    rel_tol).  FP64: V-cycles in FP64.  MIXED: FP64 residual r = b - A u, FP32
    V-cycles on the power-of-two-scaled correction equation, FP64 update
-   (iterative refinement); the coarsest solve is FP64 in both. */
+   (iterative refinement).  The coarsest-grid inverse is formed in FP64 in
+   both; FP32 cycles apply its FP32 rounding in FP32, since their coarse
+   solution is stored in FP32 (an FP64 product would be rounded anyway). */
 csff_status csff_solve(csff_plan* plan, int n_rhs, const double* eta_host, void* u_dev,
                        int use_guess, csff_info* info_host);
 
@@ -192,8 +194,9 @@ csff_status csff_restrict(csff_plan* plan, int level, int arith, const void* r_f
 /* K4: u_f (level) += bi/trilinear interpolation of e_c (level+1). */
 csff_status csff_prolong_add(csff_plan* plan, int level, int arith, const void* e_coarse_dev,
                              void* u_fine_dev);
-/* K5: u_c = A_c^{-1} b_c on the coarsest level (FP64 inverse, FP64 arithmetic;
-   buffers in the precision given by arith). */
+/* K5: u_c = A_c^{-1} b_c on the coarsest level.  The inverse is formed in
+   FP64; FP64: FP64 product; FP32: the inverse rounded to FP32, FP32 product.
+   Buffers in the precision given by arith. */
 csff_status csff_coarse_solve(csff_plan* plan, int arith, const void* b_dev, void* u_dev);
 /* K6: ||v||_2 over m_level^d complex values, accumulated in FP64; result in
    *out_host (synchronises the stream). */

@@ -41,7 +41,7 @@ struct BInst {
   long long N;
   BLevel L[MAXL];
   tiles::CoarseLevels cl;
-  const double2* inv;
+  const float2* inv;
   double2 c64;
   const double2* q64;
   double2* u64[2];                  // current iterate alternates between these
@@ -461,7 +461,7 @@ csff_status upload_descriptors(csff_batch* B) {
       I.cl.dinv[l] = L.dinv32;
       I.cl.c[l] = L.c;
     }
-    I.inv = P->coarse_inv;
+    I.inv = P->coarse_inv32;
     I.c64 = P->lv[0].c;
     I.q64 = P->lv[0].q64;
     I.u64[0] = P->lv[0].u64;

@@ -207,6 +207,9 @@ template <> float2* ubuf<float>(Level& L) { return L.u32; }
 template <typename T> cx<T>* tbuf(Level& L);
 template <> double2* tbuf<double>(Level& L) { return L.t64; }
 template <> float2* tbuf<float>(Level& L) { return L.t32; }
+template <typename T> const cx<T>* cinv(const csff_plan* P);
+template <> const double2* cinv<double>(const csff_plan* P) { return P->coarse_inv; }
+template <> const float2* cinv<float>(const csff_plan* P) { return P->coarse_inv32; }
 template <typename T> cx<T>* bbuf(Level& L);
 template <> double2* bbuf<double>(Level& L) { return L.b64; }
 template <> float2* bbuf<float>(Level& L) { return L.b32; }
@@ -246,7 +249,7 @@ csff_status vcycle(csff_plan* P, int l, cx<T>* u, const cx<T>* b) {
   const int nl = (int)P->lv.size();
   cudaStream_t s = P->stream;
   if (l == nl - 1) {
-    CK(csff::launch_coarse_solve<T>(P->coarse_inv, P->coarse_N, b, u, s), "coarse solve");
+    CK(csff::launch_coarse_solve<T>(cinv<T>(P), P->coarse_N, b, u, s), "coarse solve");
     return CSFF_OK;
   }
   Level& L = P->lv[l];
@@ -326,7 +329,7 @@ csff_status run_vcycle(csff_plan* P, cx<T>* u, const cx<T>* b, bool zero_init) {
     const cx<T>* bl = (l == 0) ? b : bbuf<T>(F);
     CK(csff::launch_down2<T>(F, C, in, zero_init || l > 0, bl, tbuf<T>(F), bbuf<T>(C), s), "fused down");
   }
-  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, P->coarse_inv, bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
+  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, cinv<T>(P), bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
      "coarse levels");
   for (int l = lc - 1; l >= 0; --l) {
     Level& F = P->lv[l];
@@ -534,6 +537,7 @@ void csff_plan_destroy(csff_plan* P) {
   for (double2* p : P->chi_tab)
     if (p) cudaFree(p);
   if (P->coarse_inv) cudaFree(P->coarse_inv);
+  if (P->coarse_inv32) cudaFree(P->coarse_inv32);
   if (P->uinc_tab) cudaFree(P->uinc_tab);
   if (P->red) cudaFree(P->red);
   if (P->red_out) cudaFree(P->red_out);
@@ -626,8 +630,13 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
   P->coarse_N = (int)std::lround(std::sqrt((double)inv.size()));
   {
     csff_status s;
-    if ((s = dev_alloc(P, &P->coarse_inv, inv.size()))) return fail(s);
+    std::vector<float2> inv32(inv.size());
+    for (size_t i = 0; i < inv.size(); ++i) inv32[i] = make_float2((float)inv[i].x, (float)inv[i].y);
+    if ((s = dev_alloc(P, &P->coarse_inv, inv.size())) || (s = dev_alloc(P, &P->coarse_inv32, inv.size())))
+      return fail(s);
     cudaError_t e = cudaMemcpy(P->coarse_inv, inv.data(), sizeof(double2) * inv.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P->coarse_inv32, inv32.data(), sizeof(float2) * inv32.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(csff::cuda_fail(e, "upload coarse inverse"));
     P->red_blocks = 152 * 8;
     if ((s = dev_alloc(P, &P->red, P->red_blocks)) || (s = dev_alloc(P, &P->red_out, 16)) ||
@@ -853,7 +862,7 @@ csff_status csff_coarse_solve(csff_plan* P, int arith, const void* b, void* u) {
     CK(csff::launch_coarse_solve<double>(P->coarse_inv, P->coarse_N, (const double2*)b, (double2*)u, P->stream),
        "coarse");
   else
-    CK(csff::launch_coarse_solve<float>(P->coarse_inv, P->coarse_N, (const float2*)b, (float2*)u, P->stream),
+    CK(csff::launch_coarse_solve<float>(P->coarse_inv32, P->coarse_N, (const float2*)b, (float2*)u, P->stream),
        "coarse");
   return CSFF_OK;
 }

@@ -76,7 +76,8 @@ struct csff_plan {
   // separable tables of chi per level: [n_gauss][dim][m_l] (amplitude folded
   // into axis 0), FP64 on the device
   std::vector<double2*> chi_tab;
-  double2* coarse_inv = nullptr;  // dense inverse of the coarsest operator
+  double2* coarse_inv = nullptr;  // dense inverse of the coarsest operator (FP64 Gauss-Jordan)
+  float2* coarse_inv32 = nullptr;  // the same inverse rounded to FP32, applied in FP32 cycles
   int coarse_N = 0;
   // per-solve data
   double2* uinc_tab = nullptr;    // [dim][m] for the current eta
@@ -140,7 +141,7 @@ template <typename T>
 cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx<T>* ec, cx<T>* u,
                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_coarse_solve(const double2* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s);
+cudaError_t launch_coarse_solve(const cx<T>* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s);
 // ||v||_2 * 2^{-e_scale}... computed as sqrt(sum |v 2^-e|^2) * 2^e; result to out (device)
 template <typename T>
 cudaError_t launch_norm2(const cx<T>* v, long long N, int exp_scale, double* partial, int nblk,
@@ -170,7 +171,7 @@ template <typename T>
 cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
                        cx<T>* u_out, cudaStream_t s);
 template <typename T>
-cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const double2* inv, const cx<T>* b,
+cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const cx<T>* inv, const cx<T>* b,
                                  cx<T>* u, cudaStream_t s);
 // dynamic shared-memory opt-in of the fused kernels on the current device
 cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc);

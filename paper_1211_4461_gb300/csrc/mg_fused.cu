@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(NT) k_up2(const cx<T>* __restrict__ u_in, cons
 
 template <typename T, int D>
 __global__ void __launch_bounds__(1024) k_coarse_levels(CoarseLevels L, const cx<T>* __restrict__ b_top,
-                                                        cx<T>* __restrict__ u_top, const double2* __restrict__ inv) {
+                                                        cx<T>* __restrict__ u_top, const cx<T>* __restrict__ inv) {
   extern __shared__ unsigned char smem_raw[];
   tiles::coarse_levels_block<T, D, false>(L, b_top, u_top, inv, smem_raw);
 }
@@ -102,7 +102,7 @@ size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int rea
 }
 
 template <typename T>
-cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const double2* inv, const cx<T>* b,
+cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const cx<T>* inv, const cx<T>* b,
                                  cx<T>* u, cudaStream_t s) {
   CoarseLevels L{};
   L.nl = (int)lv.size() - lc;
@@ -154,7 +154,7 @@ cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc) {
                                        cx<T>*, cudaStream_t);                                              \
   template cudaError_t launch_up2<T>(const Level&, const Level&, const cx<T>*, const cx<T>*, const cx<T>*,   \
                                      cx<T>*, cudaStream_t);                                                \
-  template cudaError_t launch_coarse_levels<T>(int, const std::vector<Level>&, int, const double2*,         \
+  template cudaError_t launch_coarse_levels<T>(int, const std::vector<Level>&, int, const cx<T>*,           \
                                                const cx<T>*, cx<T>*, cudaStream_t);
 CSFF_FUSED_INST(double)
 CSFF_FUSED_INST(float)

@@ -141,21 +141,22 @@ __global__ void k_prolong_add(const cx<T>* __restrict__ ec, int mc, cx<T>* __res
 // Coarsest level: u = A_c^{-1} b with the FP64 dense inverse; one CTA, one
 // warp per row (lanes split the columns, shuffle reduction).
 template <typename T>
-__global__ void k_coarse_solve(const double2* __restrict__ inv, int N, const cx<T>* __restrict__ b,
+__global__ void k_coarse_solve(const cx<T>* __restrict__ inv, int N, const cx<T>* __restrict__ b,
                                cx<T>* __restrict__ u) {
-  extern __shared__ double2 sb[];
-  for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = make_double2((double)b[j].x, (double)b[j].y);
+  extern __shared__ unsigned char sb_raw[];
+  cx<T>* sb = reinterpret_cast<cx<T>*>(sb_raw);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = b[j];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < N; i += nw) {
-    double2 acc = make_double2(0, 0);
-    const double2* row = inv + (long long)i * N;
+    cx<T> acc = mk<cx<T>>((T)0, (T)0);
+    const cx<T>* row = inv + (long long)i * N;
     for (int j = lane; j < N; j += 32) acc = cadd(acc, cmul(row[j], sb[j]));
     for (int o = 16; o > 0; o >>= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    if (lane == 0) u[i] = mk<cx<T>>((T)acc.x, (T)acc.y);
+    if (lane == 0) u[i] = acc;
   }
 }
 
@@ -386,9 +387,9 @@ cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx
 }
 
 template <typename T>
-cudaError_t launch_coarse_solve(const double2* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s) {
-  ProfScope ps(mg_family<T>(), s, 2.0 * sizeof(cx<T>) * N + 16.0 * N * N, 8.0 * N * N);
-  k_coarse_solve<T><<<1, 256, (size_t)N * sizeof(double2), s>>>(inv, N, b, u);
+cudaError_t launch_coarse_solve(const cx<T>* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s) {
+  ProfScope ps(mg_family<T>(), s, sizeof(cx<T>) * (2.0 * N + (double)N * N), 8.0 * N * N);
+  k_coarse_solve<T><<<1, 256, (size_t)N * sizeof(cx<T>), s>>>(inv, N, b, u);
   count_launch();
   return cudaGetLastError();
 }
@@ -470,7 +471,7 @@ cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s) {
                                           cudaStream_t);                                               \
   template cudaError_t launch_prolong_add<T>(int, const Level&, const Level&, const cx<T>*, cx<T>*,    \
                                              cudaStream_t);                                            \
-  template cudaError_t launch_coarse_solve<T>(const double2*, int, const cx<T>*, cx<T>*, cudaStream_t); \
+  template cudaError_t launch_coarse_solve<T>(const cx<T>*, int, const cx<T>*, cx<T>*, cudaStream_t);     \
   template cudaError_t launch_norm2<T>(const cx<T>*, long long, int, double*, int, double*,            \
                                        cudaStream_t);                                                  \
   template cudaError_t launch_zero<T>(cx<T>*, long long, cudaStream_t);

@@ -270,7 +270,7 @@ inline size_t coarse_levels_elems(const std::vector<Level>& lv, int lc) {
 
 template <typename T, int D, bool COH>
 __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, cx<T>* u_top,
-                                    const double2* __restrict__ inv, unsigned char* smem_raw) {
+                                    const cx<T>* __restrict__ inv, unsigned char* smem_raw) {
   using C = cx<T>;
   C* base = reinterpret_cast<C*>(smem_raw);
   C* U[8];
@@ -335,20 +335,20 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
     }
     __syncthreads();
   }
-  // coarsest: u = inv b (FP64), one warp per row, lanes split the columns
+  // coarsest: u = inv b in the cycle's precision (the inverse itself comes from
+  // FP64 Gauss-Jordan), one warp per row, lanes split the columns
   {
     const int n = N[last];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = warp; i < n; i += nw) {
-      double2 acc = make_double2(0, 0);
-      const double2* row = inv + (long long)i * n;
-      for (int j = lane; j < n; j += 32)
-        acc = cadd(acc, cmul(row[j], make_double2((double)B[last][j].x, (double)B[last][j].y)));
+      C acc = zero_c<T>();
+      const C* row = inv + (long long)i * n;
+      for (int j = lane; j < n; j += 32) acc = cadd(acc, cmul(row[j], B[last][j]));
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
-      if (lane == 0) U[last][i] = mk<C>((T)acc.x, (T)acc.y);
+      if (lane == 0) U[last][i] = acc;
     }
     __syncthreads();
   }
