@@ -31,8 +31,7 @@ constexpr long long BAR_SPIN_LIMIT = 1ll << 26;
 struct BLevel {
   int m, tc, ntx;                   // interior size, tile size (as fine level), tiles per side
   float2 c;
-  const float2* q;
-  const float2* dinv;
+  tiles::LevelCoef<float> K;        // formed coefficients (separable factors)
   float2 *u, *t, *b;
 };
 
@@ -275,9 +274,9 @@ __device__ void ph_down(const BInst& I, int l, int t, bool zero_init, unsigned c
   const float2* in = (l == 0) ? F.u : nullptr;
   bool zi = zero_init || l > 0;
   if (F.tc == 16)
-    tiles::down_tile<float, 16, true>(tx * 16, ty * 16, in, zi, F.b, F.q, F.dinv, F.c, F.m, C.m, F.t, C.b, smem);
+    tiles::down_tile<float, 16, true>(tx * 16, ty * 16, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
   else
-    tiles::down_tile<float, 8, true>(tx * 8, ty * 8, in, zi, F.b, F.q, F.dinv, F.c, F.m, C.m, F.t, C.b, smem);
+    tiles::down_tile<float, 8, true>(tx * 8, ty * 8, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
 }
 
 __device__ void ph_up(const BInst& I, int l, int t, unsigned char* smem) {
@@ -285,13 +284,13 @@ __device__ void ph_up(const BInst& I, int l, int t, unsigned char* smem) {
   const BLevel& C = I.L[l + 1];
   const int tx = t % F.ntx, ty = t / F.ntx;
   if (F.tc == 16)
-    tiles::up_tile<float, 16, true>(tx * 16, ty * 16, F.t, C.u, F.b, F.q, F.dinv, F.c, F.m, C.m, F.u, smem);
+    tiles::up_tile<float, 16, true>(tx * 16, ty * 16, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
   else
-    tiles::up_tile<float, 8, true>(tx * 8, ty * 8, F.t, C.u, F.b, F.q, F.dinv, F.c, F.m, C.m, F.u, smem);
+    tiles::up_tile<float, 8, true>(tx * 8, ty * 8, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
 }
 
 __global__ void __launch_bounds__(256) k_batch_solve(BArgs A) {
-  extern __shared__ unsigned char smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double shd[8];
   const int n = A.n_inst;
   const int npts = A.off_pts[n];
@@ -363,7 +362,9 @@ __global__ void k_batch_init(BState* st, int n, unsigned* bar, int* err) {
 }
 
 size_t batch_smem(const std::vector<csff_plan*>& plans) {
-  size_t s = std::max(tiles::down_smem_elems<16>(), tiles::up_smem_elems<16>());
+  int ng = 0;
+  for (csff_plan* P : plans) ng = std::max(ng, P->prob.n_gauss);
+  size_t s = std::max(tiles::down_smem_elems<16>(ng, false), tiles::up_smem_elems<16>(ng, false));
   for (csff_plan* P : plans) {
     int lc = P->fused_lc;
     s = std::max(s, tiles::coarse_levels_elems(P->lv, lc));
@@ -447,8 +448,10 @@ csff_status upload_descriptors(csff_batch* B) {
       b.tc = (mc >= 64) ? B->tc_big : 8;
       b.ntx = (mc + b.tc - 1) / b.tc;
       b.c = make_float2((float)L.c.x, (float)L.c.y);
-      b.q = L.q32;
-      b.dinv = L.dinv32;
+      b.K = csff::tiles::LevelCoef<float>{};
+      b.K.fac = L.fac32;
+      b.K.ng = L.ng;
+      b.K.k2 = (float)L.k2;
       b.u = L.u32;
       b.t = L.t32;
       b.b = L.b32;

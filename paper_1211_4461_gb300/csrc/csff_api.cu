@@ -120,6 +120,33 @@ std::vector<double2> chi_tables(const csff_plan* P, int n) {
   return t;
 }
 
+// FP32 factors of q for the fused 2D tiles: per Gaussian X = k^2 t_x (t_x
+// carries the amplitude), Y = t_y, rescaled by 2^-s and 2^s so that the two
+// factors' largest magnitudes agree (the product is unchanged; neither factor
+// leaves FP32's range unless q itself does).
+std::vector<float2> fp32_factors(const csff_plan* P, const std::vector<double2>& tab, int m) {
+  const int G = P->prob.n_gauss;
+  const double k2 = P->prob.k * P->prob.k;
+  std::vector<float2> out((size_t)G * 2 * m);
+  for (int g = 0; g < G; ++g) {
+    const double2* tx = &tab[((size_t)g * 2) * m];
+    const double2* ty = &tab[((size_t)g * 2 + 1) * m];
+    double mx = 0, my = 0;
+    for (int i = 0; i < m; ++i) {
+      mx = std::max(mx, k2 * std::hypot(tx[i].x, tx[i].y));
+      my = std::max(my, std::hypot(ty[i].x, ty[i].y));
+    }
+    int sh = 0;
+    if (mx > 0 && my > 0) sh = (int)std::lround(0.5 * (std::log2(mx) - std::log2(my)));
+    for (int i = 0; i < m; ++i) {
+      out[((size_t)g * 2) * m + i] =
+          make_float2((float)std::ldexp(k2 * tx[i].x, -sh), (float)std::ldexp(k2 * tx[i].y, -sh));
+      out[((size_t)g * 2 + 1) * m + i] = make_float2((float)std::ldexp(ty[i].x, sh), (float)std::ldexp(ty[i].y, sh));
+    }
+  }
+  return out;
+}
+
 // Dense inverse of the coarsest operator by LU with partial pivoting.
 bool coarse_inverse(const csff_plan* P, const Level& L, std::vector<double2>& out) {
   const int d = P->dim, m = L.m;
@@ -532,7 +559,8 @@ void csff_plan_destroy(csff_plan* P) {
   if (!P) return;
   for (Level& L : P->lv)
     for (void* p : {(void*)L.q64, (void*)L.dinv64, (void*)L.q32, (void*)L.dinv32, (void*)L.u64, (void*)L.t64,
-                    (void*)L.b64, (void*)L.r64, (void*)L.u32, (void*)L.t32, (void*)L.b32, (void*)L.r32})
+                    (void*)L.b64, (void*)L.r64, (void*)L.u32, (void*)L.t32, (void*)L.b32, (void*)L.r32,
+                    (void*)L.fac32})
       if (p) cudaFree(p);
   for (double2* p : P->chi_tab)
     if (p) cudaFree(p);
@@ -619,6 +647,16 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
     P->chi_tab.push_back(dtab);
     cudaError_t e = cudaMemcpy(dtab, tab.data(), sizeof(double2) * tab.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(csff::cuda_fail(e, "upload chi tables"));
+    if (d == 2) {
+      std::vector<float2> fac = fp32_factors(P, tab, L.m);
+      L.ng = P->prob.n_gauss;
+      L.k2 = P->prob.k * P->prob.k;
+      if (!fac.empty()) {
+        if ((s = dev_alloc(P, &L.fac32, fac.size()))) return fail(s);
+        e = cudaMemcpy(L.fac32, fac.data(), sizeof(float2) * fac.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(csff::cuda_fail(e, "upload factors"));
+      }
+    }
     std::vector<const double2*> per_g(P->prob.n_gauss);
     for (int g = 0; g < P->prob.n_gauss; ++g) per_g[g] = dtab + (size_t)g * d * L.m;
     e = csff::launch_coefs(d, L, per_g.data(), P->prob.n_gauss, k2, P->stream);

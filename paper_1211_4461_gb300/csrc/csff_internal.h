@@ -45,6 +45,11 @@ struct Level {
   double2* dinv64 = nullptr;  // 1 / (2d c - q)
   float2* q32 = nullptr;
   float2* dinv32 = nullptr;
+  // separable factors of q for the FP32 fused tiles: [n_gauss][2][m],
+  // X_g = 2^-s_g k^2 A_g e^{-(z_x-c_gx)^2/w_g}, Y_g = 2^s_g e^{-(z_y-c_gy)^2/w_g}
+  float2* fac32 = nullptr;
+  int ng = 0;
+  double k2 = 0;
   // work buffers
   double2 *u64 = nullptr, *t64 = nullptr, *b64 = nullptr, *r64 = nullptr;
   float2 *u32 = nullptr, *t32 = nullptr, *b32 = nullptr, *r32 = nullptr;
@@ -161,8 +166,6 @@ template <typename T>
 cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
 
 // ---- fused 2D V(1,1) RB-GS kernels (mg_fused.cu) ----------------------------
-size_t fused_down_smem(int real_bytes);
-size_t fused_up_smem(int real_bytes);
 size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int real_bytes);
 template <typename T>
 cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, bool zero_init, const cx<T>* b,

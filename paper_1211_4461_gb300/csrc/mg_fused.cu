@@ -22,22 +22,20 @@ using tiles::NT;
 using tiles::CoarseLevels;
 
 template <typename T, int TC>
-__global__ void __launch_bounds__(NT) k_down2(const cx<T>* __restrict__ u_in, int zero_init,
-                                              const cx<T>* __restrict__ b, const cx<T>* __restrict__ q,
-                                              const cx<T>* __restrict__ dinv, cx<T> c, int m, int mc,
-                                              cx<T>* __restrict__ u_out, cx<T>* __restrict__ bc) {
-  extern __shared__ unsigned char smem_raw[];
-  tiles::down_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, zero_init, b, q, dinv, c, m, mc, u_out, bc,
+__global__ void __launch_bounds__(NT, 8) k_down2(const cx<T>* __restrict__ u_in, int zero_init,
+                                              const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
+                                              int m, int mc, cx<T>* __restrict__ u_out, cx<T>* __restrict__ bc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tiles::down_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, zero_init, b, K, c, m, mc, u_out, bc,
                                  smem_raw);
 }
 
 template <typename T, int TC>
-__global__ void __launch_bounds__(NT) k_up2(const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
-                                            const cx<T>* __restrict__ b, const cx<T>* __restrict__ q,
-                                            const cx<T>* __restrict__ dinv, cx<T> c, int m, int mc,
-                                            cx<T>* __restrict__ u_out) {
-  extern __shared__ unsigned char smem_raw[];
-  tiles::up_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, q, dinv, c, m, mc, u_out, smem_raw);
+__global__ void __launch_bounds__(NT, 8) k_up2(const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
+                                            const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
+                                            int m, int mc, cx<T>* __restrict__ u_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tiles::up_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, K, c, m, mc, u_out, smem_raw);
 }
 
 template <typename T, int D>
@@ -54,12 +52,27 @@ template <typename T> const cx<T>* dt(const Level& L);
 template <> const double2* dt<double>(const Level& L) { return L.dinv64; }
 template <> const float2* dt<float>(const Level& L) { return L.dinv32; }
 
+// the tiles' view of a level's coefficients (formed from factors in FP32)
+template <typename T> tiles::LevelCoef<T> level_coef(const Level& L);
+template <> tiles::LevelCoef<double> level_coef<double>(const Level& L) {
+  tiles::LevelCoef<double> K;
+  K.q = L.q64;
+  K.dinv = L.dinv64;
+  return K;
+}
+template <> tiles::LevelCoef<float> level_coef<float>(const Level& L) {
+  tiles::LevelCoef<float> K;
+  K.fac = L.fac32;
+  K.ng = L.ng;
+  K.k2 = (float)L.k2;
+  return K;
+}
+template <typename T> int coef_ng(const Level& L) { return tiles::formed_coef<T>() ? L.ng : 0; }
+
 }  // namespace
 
-template <int TC> size_t down_smem(int rb) { return tiles::down_smem_elems<TC>() * 2 * rb; }
-template <int TC> size_t up_smem(int rb) { return tiles::up_smem_elems<TC>() * 2 * rb; }
-size_t fused_down_smem(int real_bytes) { return down_smem<16>(real_bytes); }
-size_t fused_up_smem(int real_bytes) { return up_smem<16>(real_bytes); }
+template <int TC> size_t down_smem(int rb, int ng) { return tiles::down_smem_elems<TC>(ng, rb == 8) * 2 * rb; }
+template <int TC> size_t up_smem(int rb, int ng) { return tiles::up_smem_elems<TC>(ng, rb == 8) * 2 * rb; }
 // tiles of 16 coarse points unless that leaves fewer CTAs than SMs
 static bool small_tiles(int mc) { return ((mc + 15) / 16) * ((mc + 15) / 16) < 152; }
 
@@ -68,14 +81,16 @@ cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, boo
                          cx<T>* u_out, cx<T>* bc, cudaStream_t s) {
   cx<T> c = mk<cx<T>>((T)F.c.x, (T)F.c.y);
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0);
+  const tiles::LevelCoef<T> K = level_coef<T>(F);
+  const int ng = coef_ng<T>(F);
   if (small_tiles(Cl.m)) {
     dim3 g((Cl.m + 7) / 8, (Cl.m + 7) / 8);
-    k_down2<T, 8><<<g, NT, down_smem<8>(sizeof(T)), s>>>(u_in, zero_init ? 1 : 0, b, qt<T>(F), dt<T>(F), c, F.m,
-                                                           Cl.m, u_out, bc);
+    k_down2<T, 8><<<g, NT, down_smem<8>(sizeof(T), ng), s>>>(u_in, zero_init ? 1 : 0, b, K, c, F.m, Cl.m, u_out,
+                                                               bc);
   } else {
     dim3 g((Cl.m + 15) / 16, (Cl.m + 15) / 16);
-    k_down2<T, 16><<<g, NT, down_smem<16>(sizeof(T)), s>>>(u_in, zero_init ? 1 : 0, b, qt<T>(F), dt<T>(F), c,
-                                                             F.m, Cl.m, u_out, bc);
+    k_down2<T, 16><<<g, NT, down_smem<16>(sizeof(T), ng), s>>>(u_in, zero_init ? 1 : 0, b, K, c, F.m, Cl.m, u_out,
+                                                                 bc);
   }
   count_launch();
   return cudaGetLastError();
@@ -86,12 +101,14 @@ cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const
                        cx<T>* u_out, cudaStream_t s) {
   cx<T> c = mk<cx<T>>((T)F.c.x, (T)F.c.y);
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0);
+  const tiles::LevelCoef<T> K = level_coef<T>(F);
+  const int ng = coef_ng<T>(F);
   if (small_tiles(Cl.m)) {
     dim3 g((Cl.m + 7) / 8, (Cl.m + 7) / 8);
-    k_up2<T, 8><<<g, NT, up_smem<8>(sizeof(T)), s>>>(u_in, ec, b, qt<T>(F), dt<T>(F), c, F.m, Cl.m, u_out);
+    k_up2<T, 8><<<g, NT, up_smem<8>(sizeof(T), ng), s>>>(u_in, ec, b, K, c, F.m, Cl.m, u_out);
   } else {
     dim3 g((Cl.m + 15) / 16, (Cl.m + 15) / 16);
-    k_up2<T, 16><<<g, NT, up_smem<16>(sizeof(T)), s>>>(u_in, ec, b, qt<T>(F), dt<T>(F), c, F.m, Cl.m, u_out);
+    k_up2<T, 16><<<g, NT, up_smem<16>(sizeof(T), ng), s>>>(u_in, ec, b, K, c, F.m, Cl.m, u_out);
   }
   count_launch();
   return cudaGetLastError();
@@ -128,13 +145,18 @@ cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, 
 cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc) {
   const int kMax = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_down2<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)down_smem<16>(4))) ||
-      (e = cudaFuncSetAttribute(k_down2<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)down_smem<16>(8))) ||
-      (e = cudaFuncSetAttribute(k_up2<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)up_smem<16>(4))) ||
-      (e = cudaFuncSetAttribute(k_up2<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)up_smem<16>(8))) ||
-      (e = cudaFuncSetAttribute(k_down2<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)down_smem<8>(8))) ||
-      (e = cudaFuncSetAttribute(k_up2<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)up_smem<8>(8))))
+  // the tiles stay below the default 48 KB (FP64: no factor windows; FP32:
+  // at most 8 Gaussians)
+  if ((e = cudaFuncSetAttribute(k_down2<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)down_smem<16>(8, 0))) ||
+      (e = cudaFuncSetAttribute(k_up2<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)up_smem<16>(8, 0))))
     return e;
+  static_assert(tiles::down_smem_elems<16>(8, false) * 8 <= 48 * 1024 &&
+                    tiles::up_smem_elems<16>(8, false) * 8 <= 48 * 1024 &&
+                    tiles::down_smem_elems<8>(0, true) * 16 <= 48 * 1024 &&
+                    tiles::up_smem_elems<8>(0, true) * 16 <= 48 * 1024,
+                "fused tile shared memory");
   size_t s8 = coarse_levels_smem(dim, lv, lc, 8);
   if (s8 > (size_t)kMax) return cudaErrorInvalidValue;
   if (dim == 2) {

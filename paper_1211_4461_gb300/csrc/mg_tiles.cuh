@@ -28,15 +28,52 @@ template <int TC> struct Geo {
 };
 constexpr int NT = 256;
 
-template <int TC> __host__ __device__ constexpr size_t down_smem_elems() {
-  return (size_t)(4 * Geo<TC>::DW * Geo<TC>::DW + (Geo<TC>::FT + 1) * (Geo<TC>::FT + 1));
+// Coefficients of one fine level as the tile bodies see them: the diagonal
+// d = 2D c - q and its inverse.  FP64 cycles read the plan's FP64 tables
+// (q, dinv); FP32 cycles form them from separable per-axis factors,
+//   q(z) = k^2 + sum_g X_g[ix] Y_g[iy],
+//   X_g = 2^-s_g k^2 A_g e^{-(z_x - c_gx)^2 / w_g},  Y_g = 2^s_g e^{-(z_y - c_gy)^2 / w_g}
+// (s_g balances the two factors' ranges), which leaves the RHS and the iterate
+// as the only per-point streams of an FP32 tile.
+template <typename T> struct LevelCoef {
+  const cx<T>* q = nullptr;      // stored q (FP64 cycles)
+  const cx<T>* dinv = nullptr;   // stored 1/d (FP64 cycles)
+  const cx<T>* fac = nullptr;    // [ng][2][m] factors X_g, Y_g (FP32 cycles)
+  int ng = 0;
+  T k2 = 0;
+};
+template <typename T> constexpr bool formed_coef() { return sizeof(T) == 4; }
+
+template <int TC> __host__ __device__ constexpr int down_window() { return Geo<TC>::DW * Geo<TC>::DW; }
+template <int TC> __host__ __device__ constexpr int up_window() { return Geo<TC>::UW * Geo<TC>::UW; }
+// shared-memory elements (complex values) of one tile: iterate and RHS
+// windows, then FP32 factor windows (ng pairs) or the FP64 1/d window
+template <int TC> __host__ __device__ constexpr size_t down_smem_elems(int ng, bool fp64) {
+  return (size_t)(fp64 ? 3 : 2) * down_window<TC>() + (fp64 ? 0 : 2 * ng * Geo<TC>::DW);
 }
-template <int TC> __host__ __device__ constexpr size_t up_smem_elems() {
-  return (size_t)(4 * Geo<TC>::UW * Geo<TC>::UW + Geo<TC>::EW * Geo<TC>::EW);
+template <int TC> __host__ __device__ constexpr size_t up_smem_elems(int ng, bool fp64) {
+  return (size_t)(fp64 ? 3 : 2) * up_window<TC>() + Geo<TC>::EW * Geo<TC>::EW + (fp64 ? 0 : 2 * ng * Geo<TC>::UW);
 }
 
 template <typename T>
 __device__ __forceinline__ cx<T> zero_c() { return mk<cx<T>>((T)0, (T)0); }
+
+// Complex arithmetic of the tiles with every rounding spelled out (round-to-
+// nearest intrinsics are never contracted or reassociated by the compiler), so
+// the per-level kernels and the persistent batched kernel, which inline the
+// same tile bodies into different code, produce identical bits.
+__device__ __forceinline__ float2 xadd(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ double2 xadd(double2 a, double2 b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 xsub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ double2 xsub(double2 a, double2 b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 xmul(float2 a, float2 b) {
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ double2 xmul(double2 a, double2 b) {
+  return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 xscale(float2 a, float s) { return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
+__device__ __forceinline__ double2 xscale(double2 a, double s) { return make_double2(__dmul_rn(a.x, s), __dmul_rn(a.y, s)); }
 
 template <bool COH, typename C>
 __device__ __forceinline__ C ld(const C* p) {
@@ -44,68 +81,120 @@ __device__ __forceinline__ C ld(const C* p) {
   else return *p;
 }
 
-// A u at window point (wy, wx) of a row-major window of width W (values
-// outside the domain are stored as zero).  Neighbour order x-1, x+1, y-1, y+1
-// as in the unfused kernels.
+// sum of the four neighbours of window point i (row width W); values outside
+// the domain are stored as zero.  Order x-1, x+1, y-1, y+1.
+template <typename C>
+__device__ __forceinline__ C nbr_sum(const C* U, int W, int i) {
+  return xadd(xadd(xadd(U[i - 1], U[i + 1]), U[i - W]), U[i + W]);
+}
+
+// 1/d for the smoother: reciprocal of |d|^2 by the hardware approximation
+// (__fdividef, about 2 ulp), enough for an inverse diagonal that only scales
+// the correction
+__device__ __forceinline__ float2 crecip(float2 d) {
+  const float r = __fdividef(1.f, __fmaf_rn(d.x, d.x, __fmul_rn(d.y, d.y)));
+  return make_float2(__fmul_rn(d.x, r), -__fmul_rn(d.y, r));
+}
+
+// Window of W x W fine points with origin (ox, oy): iterate -> U, RHS -> B,
+// and the coefficient windows (FP32: X_g, Y_g along the two axes; FP64: 1/d).
+// Points outside the interior are zero.
+template <typename T, bool COH>
+__device__ __forceinline__ void load_window(int ox, int oy, int W, int m, const cx<T>* u_in, bool zero_u,
+                                            const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
+                                            cx<T>* X) {
+  for (int i = threadIdx.x; i < W * W; i += NT) {
+    const int wy = i / W, wx = i - wy * W;
+    const int fx = ox + wx, fy = oy + wy;
+    const bool in = fx >= 0 && fx < m && fy >= 0 && fy < m;
+    const long long g = (long long)fy * m + fx;
+    U[i] = (in && !zero_u) ? ld<COH>(u_in + g) : zero_c<T>();
+    B[i] = in ? ld<COH>(b + g) : zero_c<T>();
+    if constexpr (!formed_coef<T>()) X[i] = in ? K.dinv[g] : zero_c<T>();
+  }
+  if constexpr (formed_coef<T>()) {
+    cx<T>* FY = X + K.ng * W;
+    for (int i = threadIdx.x; i < K.ng * W; i += NT) {
+      const int g = i / W, w = i - g * W;
+      const int fx = ox + w, fy = oy + w;
+      X[i] = (fx >= 0 && fx < m) ? K.fac[((size_t)g * 2) * m + fx] : zero_c<T>();
+      FY[i] = (fy >= 0 && fy < m) ? K.fac[((size_t)g * 2 + 1) * m + fy] : zero_c<T>();
+    }
+  }
+}
+
+// d = 4c - q at window point (wx, wy) from the factor windows
+__device__ __forceinline__ float2 formed_diag(const LevelCoef<float>& K, float2 c, const float2* X, int W, int wx,
+                                              int wy) {
+  const float2* FY = X + K.ng * W;
+  float2 q = make_float2(K.k2, 0.f);
+  for (int g = 0; g < K.ng; ++g) q = xadd(q, xmul(X[g * W + wx], FY[g * W + wy]));
+  return make_float2(__fmaf_rn(4.f, c.x, -q.x), __fmaf_rn(4.f, c.y, -q.y));
+}
+
+// One red-black Gauss-Seidel half sweep over window points [lo, hi]^2 of the
+// given colour, in the form
+//   u_j <- d_j^{-1} (b_j + c sum_nbr u),
+// which equals u_j + d_j^{-1} (b_j - (A u)_j) for A u = d u - c sum_nbr u.
 template <typename T>
-__device__ __forceinline__ cx<T> apply_w(const cx<T>* U, int W, int wy, int wx, cx<T> q, cx<T> c) {
-  using C = cx<T>;
-  C uj = U[wy * W + wx];
-  C s = cadd(cadd(cadd(U[wy * W + wx - 1], U[wy * W + wx + 1]), U[(wy - 1) * W + wx]), U[(wy + 1) * W + wx]);
-  C t = csub(cscale(uj, (T)4), s);
-  return csub(cmul(c, t), cmul(q, uj));
+__device__ __forceinline__ void rb_half(int ox, int oy, int W, int m, int colour, const LevelCoef<T>& K, cx<T> c,
+                                        cx<T>* U, const cx<T>* B, const cx<T>* X) {
+  const int lo = 1 + colour, hi = W - 2 - colour;
+  const int R = hi - lo + 1, HW = (R + 1) >> 1;
+  // only the points of this colour: in window row wy they start at lo or
+  // lo + 1, whichever gives (fx + fy) of the colour's parity, and step by 2
+  for (int t = threadIdx.x; t < R * HW; t += NT) {
+    const int r = t / HW, j = t - r * HW;
+    const int wy = lo + r;
+    const int wx = lo + ((colour ^ (ox + oy + wy + lo)) & 1) + 2 * j;
+    const int fx = ox + wx, fy = oy + wy;
+    if (wx > hi || fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
+    const int i = wy * W + wx;
+    cx<T> di;
+    if constexpr (formed_coef<T>()) di = crecip(formed_diag(K, c, X, W, wx, wy));
+    else di = X[i];
+    U[i] = xmul(di, xadd(B[i], xmul(c, nbr_sum(U, W, i))));
+  }
 }
 
 // down tile (P0x, P0y in coarse points).  u_in is ignored when zero_init.
 template <typename T, int TC, bool COH>
 __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, const cx<T>* b,
-                          const cx<T>* __restrict__ q, const cx<T>* __restrict__ dinv, cx<T> c, int m, int mc,
-                          cx<T>* u_out, cx<T>* bc, unsigned char* smem_raw) {
+                          const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, cx<T>* bc,
+                          unsigned char* smem_raw) {
   using C = cx<T>;
-  constexpr int FT = Geo<TC>::FT, DW = Geo<TC>::DW;
+  constexpr int FT = Geo<TC>::FT, DW = Geo<TC>::DW, NW = DW * DW;
   C* U = reinterpret_cast<C*>(smem_raw);
-  C* B = U + DW * DW;
-  C* Q = B + DW * DW;
-  C* Dv = Q + DW * DW;
-  C* R = Dv + DW * DW;                   // residual on fine [2P0, 2P0+2TC], (FT+1)^2
+  C* B = U + NW;                              // RHS, then the residual in place
+  C* X = B + NW;                              // coefficient windows
   const int ox = 2 * P0x - 3, oy = 2 * P0y - 3;   // window origin (fine interior index)
-  for (int i = threadIdx.x; i < DW * DW; i += NT) {
-    int wy = i / DW, wx = i - wy * DW;
-    int fx = ox + wx, fy = oy + wy;
-    bool in = fx >= 0 && fx < m && fy >= 0 && fy < m;
-    long long g = (long long)fy * m + fx;
-    U[i] = (in && !zero_init) ? ld<COH>(u_in + g) : zero_c<T>();
-    B[i] = in ? ld<COH>(b + g) : zero_c<T>();
-    Q[i] = in ? q[g] : zero_c<T>();
-    Dv[i] = in ? dinv[g] : zero_c<T>();
-  }
+  load_window<T, COH>(ox, oy, DW, m, u_in, zero_init != 0, b, K, U, B, X);
   __syncthreads();
-  // red on window [1, DW-2], black on [2, DW-3]; colour from the node-index sum
+  // red on window [1, DW-2], black on [2, DW-3]
   for (int colour = 0; colour < 2; ++colour) {
-    const int lo = 1 + colour, hi = DW - 2 - colour;
-    for (int i = threadIdx.x; i < DW * DW; i += NT) {
-      int wy = i / DW, wx = i - wy * DW;
-      if (wx < lo || wx > hi || wy < lo || wy > hi) continue;
-      int fx = ox + wx, fy = oy + wy;
-      if (fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
-      if (((fx + fy) & 1) != colour) continue;
-      C rj = csub(B[i], apply_w<T>(U, DW, wy, wx, Q[i], c));
-      U[i] = cadd(U[i], cmul(Dv[i], rj));
-    }
+    rb_half<T>(ox, oy, DW, m, colour, K, c, U, B, X);
     __syncthreads();
   }
-  // owned fine points: [2P0, 2P0+FT) per axis, the last tile also the final index
+  // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final
+  // index); residual on [2P0, 2P0+FT] written over the RHS (each point reads
+  // only its own RHS value)
   {
     const int ex = (P0x + TC >= mc) ? m : 2 * P0x + FT;
     const int ey = (P0y + TC >= mc) ? m : 2 * P0y + FT;
     for (int i = threadIdx.x; i < (FT + 1) * (FT + 1); i += NT) {
-      int ly = i / (FT + 1), lx = i - ly * (FT + 1);
-      int fx = 2 * P0x + lx, fy = 2 * P0y + ly;
-      int wx = lx + 3, wy = ly + 3;
-      if (fx < ex && fy < ey && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[wy * DW + wx];
+      const int ly = i / (FT + 1), lx = i - ly * (FT + 1);
+      const int fx = 2 * P0x + lx, fy = 2 * P0y + ly;
+      const int w = (ly + 3) * DW + lx + 3;
+      const long long g = (long long)fy * m + fx;
+      if (fx < ex && fy < ey && fx < m && fy < m) u_out[g] = U[w];
       C rv = zero_c<T>();
-      if (fx < m && fy < m) rv = csub(B[wy * DW + wx], apply_w<T>(U, DW, wy, wx, Q[wy * DW + wx], c));
-      R[i] = rv;
+      if (fx < m && fy < m) {
+        C d;
+        if constexpr (formed_coef<T>()) d = formed_diag(K, c, X, DW, lx + 3, ly + 3);
+        else d = xsub(xscale(c, (T)4), K.q[g]);
+        rv = xsub(B[w], xsub(xmul(d, U[w]), xmul(c, nbr_sum(U, DW, w))));
+      }
+      B[w] = rv;
     }
   }
   __syncthreads();
@@ -118,10 +207,10 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
 #pragma unroll
     for (int oy2 = -1; oy2 <= 1; ++oy2) {
       C row = zero_c<T>();
-      int ry = 2 * py + 1 + oy2;
+      int ry = 2 * py + 4 + oy2;          // window row of fine 2P0y + 2py + 1 + oy2
 #pragma unroll
-      for (int ox2 = -1; ox2 <= 1; ++ox2) row = cadd(row, cscale(R[ry * (FT + 1) + 2 * px + 1 + ox2], w1[ox2 + 1]));
-      acc = cadd(acc, cscale(row, w1[oy2 + 1]));
+      for (int ox2 = -1; ox2 <= 1; ++ox2) row = xadd(row, xscale(B[ry * DW + 2 * px + 4 + ox2], w1[ox2 + 1]));
+      acc = xadd(acc, xscale(row, w1[oy2 + 1]));
     }
     bc[(long long)Py * mc + Px] = acc;
   }
@@ -147,15 +236,13 @@ __device__ __forceinline__ int interp_w(int p, int e0, int mc, int* ci, T* w) {
 // up tile: u = u_in + P e_c, one RB-GS sweep, write owned points.
 template <typename T, int TC, bool COH>
 __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
-                        const cx<T>* __restrict__ q, const cx<T>* __restrict__ dinv, cx<T> c, int m, int mc,
-                        cx<T>* u_out, unsigned char* smem_raw) {
+                        const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, unsigned char* smem_raw) {
   using C = cx<T>;
-  constexpr int FT = Geo<TC>::FT, UW = Geo<TC>::UW, EW = Geo<TC>::EW;
+  constexpr int FT = Geo<TC>::FT, UW = Geo<TC>::UW, EW = Geo<TC>::EW, NW = UW * UW;
   C* U = reinterpret_cast<C*>(smem_raw);
-  C* B = U + UW * UW;
-  C* Q = B + UW * UW;
-  C* Dv = Q + UW * UW;
-  C* E = Dv + UW * UW;                   // EW x EW coarse window
+  C* B = U + NW;
+  C* E = B + NW;                         // EW x EW coarse window
+  C* X = E + EW * EW;                    // coefficient windows
   const int ox = 2 * P0x - 2, oy = 2 * P0y - 2;
   const int ex0 = P0x - 2, ey0 = P0y - 2;
   for (int i = threadIdx.x; i < EW * EW; i += NT) {
@@ -163,42 +250,27 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
     int cxp = ex0 + wx, cyp = ey0 + wy;
     E[i] = (cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc) ? ld<COH>(ec + (long long)cyp * mc + cxp) : zero_c<T>();
   }
-  for (int i = threadIdx.x; i < UW * UW; i += NT) {
-    int wy = i / UW, wx = i - wy * UW;
-    int fx = ox + wx, fy = oy + wy;
-    bool in = fx >= 0 && fx < m && fy >= 0 && fy < m;
-    long long g = (long long)fy * m + fx;
-    U[i] = in ? ld<COH>(u_in + g) : zero_c<T>();
-    B[i] = in ? ld<COH>(b + g) : zero_c<T>();
-    Q[i] = in ? q[g] : zero_c<T>();
-    Dv[i] = in ? dinv[g] : zero_c<T>();
-  }
+  load_window<T, COH>(ox, oy, UW, m, u_in, false, b, K, U, B, X);
   __syncthreads();
-  for (int i = threadIdx.x; i < UW * UW; i += NT) {
-    int wy = i / UW, wx = i - wy * UW;
-    int fx = ox + wx, fy = oy + wy;
+  // bilinear interpolation: node index i = f + 1 lies on coarse node i/2 (even
+  // i, weight 1) or between (i-1)/2 and (i+1)/2 (odd i, 1/2 each); the coarse
+  // window is zero outside the coarse interior, so no range tests are needed
+  for (int i = threadIdx.x; i < NW; i += NT) {
+    const int wy = i / UW, wx = i - wy * UW;
+    const int fx = ox + wx, fy = oy + wy;
     if (fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
-    int cxi[2], cyi[2];
-    T wxs[2], wys[2];
-    int nx = interp_w<T>(fx, ex0, mc, cxi, wxs);
-    int ny = interp_w<T>(fy, ey0, mc, cyi, wys);
-    C acc = zero_c<T>();
-    for (int a = 0; a < ny; ++a)
-      for (int bb = 0; bb < nx; ++bb) acc = cadd(acc, cscale(E[cyi[a] * EW + cxi[bb]], wxs[bb] * wys[a]));
-    U[i] = cadd(U[i], acc);
+    const int ix = fx + 1, iy = fy + 1;
+    const int cx0 = (ix >> 1) - 1 - ex0, cy0 = (iy >> 1) - 1 - ey0;
+    const int cx1 = cx0 + (ix & 1), cy1 = cy0 + (iy & 1);
+    const T wx0 = (ix & 1) ? (T)0.5 : (T)1, wx1 = (ix & 1) ? (T)0.5 : (T)0;
+    const T wy0 = (iy & 1) ? (T)0.5 : (T)1, wy1 = (iy & 1) ? (T)0.5 : (T)0;
+    const C r0 = xadd(xscale(E[cy0 * EW + cx0], wx0), xscale(E[cy0 * EW + cx1], wx1));
+    const C r1 = xadd(xscale(E[cy1 * EW + cx0], wx0), xscale(E[cy1 * EW + cx1], wx1));
+    U[i] = xadd(U[i], xadd(xscale(r0, wy0), xscale(r1, wy1)));
   }
   __syncthreads();
   for (int colour = 0; colour < 2; ++colour) {
-    const int lo = 1 + colour, hi = UW - 2 - colour;
-    for (int i = threadIdx.x; i < UW * UW; i += NT) {
-      int wy = i / UW, wx = i - wy * UW;
-      if (wx < lo || wx > hi || wy < lo || wy > hi) continue;
-      int fx = ox + wx, fy = oy + wy;
-      if (fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
-      if (((fx + fy) & 1) != colour) continue;
-      C rj = csub(B[i], apply_w<T>(U, UW, wy, wx, Q[i], c));
-      U[i] = cadd(U[i], cmul(Dv[i], rj));
-    }
+    rb_half<T>(ox, oy, UW, m, colour, K, c, U, B, X);
     __syncthreads();
   }
   const int exx = (P0x + TC >= mc) ? m : 2 * P0x + FT;
@@ -228,17 +300,17 @@ __device__ __forceinline__ cx<T> apply_s(const cx<T>* u, int m, int ix, int iy, 
                                          cx<T> c) {
   using C = cx<T>;
   C s = zero_c<T>();
-  if (ix > 0) s = cadd(s, u[idx - 1]);
-  if (ix < m - 1) s = cadd(s, u[idx + 1]);
-  if (iy > 0) s = cadd(s, u[idx - m]);
-  if (iy < m - 1) s = cadd(s, u[idx + m]);
+  if (ix > 0) s = xadd(s, u[idx - 1]);
+  if (ix < m - 1) s = xadd(s, u[idx + 1]);
+  if (iy > 0) s = xadd(s, u[idx - m]);
+  if (iy < m - 1) s = xadd(s, u[idx + m]);
   if (D == 3) {
-    if (iz > 0) s = cadd(s, u[idx - m * m]);
-    if (iz < m - 1) s = cadd(s, u[idx + m * m]);
+    if (iz > 0) s = xadd(s, u[idx - m * m]);
+    if (iz < m - 1) s = xadd(s, u[idx + m * m]);
   }
   C uj = u[idx];
-  C t = csub(cscale(uj, (T)(2 * D)), s);
-  return csub(cmul(c, t), cmul(q, uj));
+  C t = xsub(xscale(uj, (T)(2 * D)), s);
+  return xsub(xmul(c, t), xmul(q, uj));
 }
 
 template <int D>
@@ -255,8 +327,8 @@ __device__ void rbgs_s(cx<T>* u, const cx<T>* b, const cx<T>* q, const cx<T>* di
       int ix, iy, iz;
       decode<D>(i, m, ix, iy, iz);
       if (((ix + iy + iz + D) & 1) != colour) continue;
-      cx<T> rj = csub(b[i], apply_s<T, D>(u, m, ix, iy, iz, i, q[i], c));
-      u[i] = cadd(u[i], cmul(dinv[i], rj));
+      cx<T> rj = xsub(b[i], apply_s<T, D>(u, m, ix, iy, iz, i, q[i], c));
+      u[i] = xadd(u[i], xmul(dinv[i], rj));
     }
     __syncthreads();
   }
@@ -317,7 +389,7 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
     for (int i = threadIdx.x; i < N[l]; i += blockDim.x) {
       int ix, iy, iz;
       decode<D>(i, m, ix, iy, iz);
-      R[l][i] = csub(B[l][i], apply_s<T, D>(U[l], m, ix, iy, iz, i, Qs[l][i], c));
+      R[l][i] = xsub(B[l][i], apply_s<T, D>(U[l], m, ix, iy, iz, i, Qs[l][i], c));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < N[l + 1]; i += blockDim.x) {
@@ -329,7 +401,7 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
           for (int ox = -1; ox <= 1; ++ox) {
             int fx = 2 * px + 1 + ox, fy = 2 * py + 1 + oy, fz = (D == 3) ? 2 * pz + 1 + oz : 0;
             T w = w1[ox + 1] * w1[oy + 1] * ((D == 3) ? w1[oz + 1] : (T)1);
-            acc = cadd(acc, cscale(R[l][(fz * m + fy) * m + fx], w));
+            acc = xadd(acc, xscale(R[l][(fz * m + fy) * m + fx], w));
           }
       B[l + 1][i] = acc;
     }
@@ -343,7 +415,7 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
     for (int i = warp; i < n; i += nw) {
       C acc = zero_c<T>();
       const C* row = inv + (long long)i * n;
-      for (int j = lane; j < n; j += 32) acc = cadd(acc, cmul(row[j], B[last][j]));
+      for (int j = lane; j < n; j += 32) acc = xadd(acc, xmul(row[j], B[last][j]));
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
@@ -367,8 +439,8 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
       for (int a = 0; a < nz; ++a)
         for (int bq = 0; bq < ny; ++bq)
           for (int cq = 0; cq < nx; ++cq)
-            acc = cadd(acc, cscale(U[l + 1][(czi[a] * mc + cyi[bq]) * mc + cxi[cq]], wx[cq] * wy[bq] * wz[a]));
-      U[l][i] = cadd(U[l][i], acc);
+            acc = xadd(acc, xscale(U[l + 1][(czi[a] * mc + cyi[bq]) * mc + cxi[cq]], wx[cq] * wy[bq] * wz[a]));
+      U[l][i] = xadd(U[l][i], acc);
     }
     __syncthreads();
     rbgs_s<T, D>(U[l], B[l], Qs[l], Ds[l], c, m, N[l]);
