@@ -46,10 +46,18 @@ def _peaks():
 # FP64 FMA throughput of this part, measured with an FMA-loop kernel
 # (0.599e12 DFMA/s over 152 SMs; 2 flops per FMA).
 FP64_PEAK_TFLOPS = 1.198
-# DRAM bytes (read + write) of one k_ff_stage1 launch on this workload, from the
-# ncu capture summarised in profiles/ff_stage1_2d_n1025.md (None once the kernel
-# changes).
-FF_STAGE1_DRAM_BYTES = 22668288
+# FP32 instruction rate derived from unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2.07 GHz.  The double-float contraction spends 48 FP32 instructions
+# (4 double-float multiply-adds of 12) per complex multiply-add, i.e. 6 per
+# FP64-equivalent flop, so its arithmetic ceiling in FP64-equivalent flops is
+# that rate / 6.
+FP32_INSTR_PER_S = 152 * 128 * 2.07e9
+DF_INSTR_PER_FLOP = 6.0
+DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
+# DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload, from
+# the ncu capture summarised in profiles/ff_stage1_df_2d_n1025.md (None once
+# the kernel changes).
+FF_DF_DRAM_BYTES = 22876160
 
 
 def _cases(precision, ks=None):
@@ -278,10 +286,11 @@ def run_ours(args, rank, world, local_rank):
     ff_avg_ms = ff["ms"] / max(1, ff["launches"])
     ff_flops = ff["alg_flops"] / max(1, ff["launches"])
     achieved_tf = ff_flops / (ff_avg_ms * 1e-3) / 1e12 if ff_avg_ms > 0 else 0.0
-    roofline = {"kernel": "k_ff_stage1 (FP64 far-field contraction)", "bound": "alu",
-                "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": FF_STAGE1_DRAM_BYTES,
-                "peak_source": "FP64 FMA-loop measurement on this GB300 (no FP64 entry in MEASURED_PEAKS.json)",
+    roofline = {"kernel": "k_ff_stage1_df (double-float far-field contraction)", "bound": "alu",
+                "achieved": achieved_tf, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / DF_PEAK_TFLOPS, "traffic": FF_DF_DRAM_BYTES,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 6 FP32 instructions per "
+                               "FP64-equivalent flop (48 per complex multiply-add in double-float)",
                 "avg_launch_ms": ff_avg_ms, "launches": ff["launches"],
                 "alg_flops_per_launch": ff_flops}
     mg32, mg64 = breakdown["mg32"], breakdown["mg64"]
@@ -433,7 +442,9 @@ def measure_3d(csff, torch, dev, stream, flush):
             "cycles": [i["cycles"] for i in info["inf"]],
             "all_converged": all(i["rel_res"] <= 1e-8 for i in info["inf"]),
             "ff_stageA_ms_per_map": ff["ms"] / max(1, nr),
-            "ff_stageA_tflops": ff["alg_flops"] / (ff["ms"] * 1e-3) / 1e12 if ff["ms"] else 0.0}
+            "ff_stageA_tflops": ff["alg_flops"] / (ff["ms"] * 1e-3) / 1e12 if ff["ms"] else 0.0,
+            "ff_stageA_fp64_frac": (ff["alg_flops"] / (ff["ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
+                                    if ff["ms"] else 0.0)}
 
 
 def measure_learned(csff, torch, dev, stream, flush):
