@@ -175,6 +175,22 @@ csff_status csff_solve(csff_plan* plan, int n_rhs, const double* eta_host, void*
 csff_status csff_far_field(csff_plan* plan, int n_rhs, const double* eta_host, const void* u_dev,
                            int n_ang, const double* alpha_host, void* F_dev, int32_t* F_exp_dev);
 
+/* Arithmetic of the far-field contraction (eq. FFmap; the paper leaves the
+   quadrature's arithmetic open, Sec. 4).
+   CSFF_FF_FP64 (default): FP64-class throughout (2D stage 1 in double-float
+     arithmetic on the FP32 pipes, FP64 where the operand ranges need it).
+   CSFF_FF_TC_BF16X3: 3D plans evaluate the z-contraction (the largest stage)
+     on the tensor cores: operands rounded to FP32, split into three BF16 terms,
+     six products accumulated in FP32; relative error per term about 2^-22 of
+     its magnitude, so F carries an absolute error of that order times
+     sum_j |term_j| per angle.  The library falls back to FP64 on the device
+     when an operand is not finite or its exponent range is too wide.  2D plans
+     are unaffected.  A wait inside the tensor-core kernel that runs out makes
+     csff_far_field return CSFF_ERR_TIMEOUT.
+   Errors: CSFF_ERR_INVALID_ARG for an unknown mode. */
+enum { CSFF_FF_FP64 = 0, CSFF_FF_TC_BF16X3 = 1 };
+csff_status csff_plan_set_far_field_mode(csff_plan* plan, int mode);
+
 /* ---- per-step calls (one kernel each; for verification and custom cycles) --
    arith: CSFF_ARITH_FP64 (c128 buffers) or CSFF_ARITH_FP32 (c64 buffers).
    level: 0 = finest.  All buffers are device pointers of m_level^d elements

@@ -78,6 +78,7 @@ class ProfStatsC(C.Structure):
 
 
 PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER = 1, 2, 4, 8
+FF_FP64, FF_TC_BF16X3 = 0, 1
 PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other")
 
 _vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
@@ -91,6 +92,7 @@ _SIGS = {
     "csff_rhs": (_i, [_vp, _i, _dp, _vp]),
     "csff_solve": (_i, [_vp, _i, _dp, _vp, _i, C.POINTER(InfoC)]),
     "csff_far_field": (_i, [_vp, _i, _dp, _vp, _i, _dp, _vp, _vp]),
+    "csff_plan_set_far_field_mode": (_i, [_vp, _i]),
     "csff_residual": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "csff_smooth": (_i, [_vp, _i, _i, _vp, _vp, _i]),
     "csff_restrict": (_i, [_vp, _i, _i, _vp, _vp]),
@@ -379,6 +381,10 @@ class Plan:
     def set_stream(self, stream):
         self._stream = stream
         _check(_lib.csff_plan_set_stream(self._h, _stream_handle(stream)), "set_stream")
+
+    def set_far_field_mode(self, mode):
+        """FF_FP64 (default) or FF_TC_BF16X3 (3D z-contraction on the tensor cores)."""
+        _check(_lib.csff_plan_set_far_field_mode(self._h, int(mode)), "plan_set_far_field_mode")
 
     def set_learned(self, net, levels=1, guard=0.5):
         """Attach (net) or detach (None) the learned step on the finest levels."""

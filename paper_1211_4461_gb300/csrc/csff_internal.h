@@ -67,12 +67,18 @@ struct FFBuffers {
   size_t xdf = 0, gdf = 0, exs = 0, egs = 0;
   float4 *dxdf = nullptr, *dgdf = nullptr;
   int *dex = nullptr, *deg = nullptr, *dspread = nullptr;
+  // tensor-core 3D stage A: pre-swizzled split phase operand, per-column and
+  // per-row exponents, [spread_g, spread_P, error word]
+  size_t tcb = 0, tce = 0;
+  unsigned char* dtcb = nullptr;
+  int *dtce = nullptr, *dtcflag = nullptr;
 };
 
 }  // namespace csff
 
 struct csff_plan {
   csff_problem prob{};
+  int ff_mode = 0;          // CSFF_FF_FP64 or CSFF_FF_TC_BF16X3
   std::vector<csff_gauss> gauss;
   csff_opts opts{};
   cudaStream_t stream = nullptr;

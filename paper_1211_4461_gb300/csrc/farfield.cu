@@ -14,6 +14,8 @@
 // when an a-priori bound on |T| exceeds 2^1020, stage 2 picks 2^-s2 from the
 // largest term of its own sum; the result is returned as F' with exponent
 // s1 + s2 (F = F' 2^(s1+s2)).
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <map>
 #include <vector>
@@ -392,6 +394,325 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
   }
 }
 
+// ---- 3D stage A on the tensor cores ------------------------------------------
+// T1[t][col] = sum_iz Pz[t][iz] g[iz][col] as a real GEMM D[col][j] = sum_k
+// A[col][k] B[j][k] with k = 2 iz + (re, im):
+//   A[col] = (g_re(iz), g_im(iz))_iz,  B[t]    = (P_re, -P_im)_iz  (Re T_t),
+//                                      B[32+t] = (P_im,  P_re)_iz  (Im T_t).
+// Each operand row is scaled by a power of two (per column of g, per z-row of
+// P), rounded to FP32 and split into three BF16 terms v = v0 + v1 + v2 (24
+// significant bits); the six products with i + j <= 2 run as tcgen05.mma
+// (kind::f16, BF16 inputs, FP32 accumulation in tensor memory), the (0,0)
+// product in its own accumulator.  The epilogue adds the two accumulators in
+// FP64 and applies the exponents.  Operands sit in shared memory in the
+// 128-byte-swizzled K-major layout (8-row atoms of 1024 B, 16-byte chunk index
+// XOR row mod 8): A is split and stored by the CTA's threads from g, B is
+// pre-split and pre-swizzled in global memory.  Two pipeline stages; the MMAs
+// of one stage run while the threads fill the other.
+namespace tc {
+constexpr int TM = 128;                       // GEMM rows (columns of g) per CTA
+constexpr int TT = 32;                        // z-rows of P per launch (GEMM N = 2 TT = 64)
+constexpr int KZ = 32;                        // z-nodes per K chunk (64 BF16 = one 128-byte row)
+constexpr int NTHR = 256;
+constexpr int A_SPLIT = TM * 128;             // bytes of one split of an A chunk
+constexpr int B_SPLIT = 2 * TT * 128;         // bytes of one split of a B chunk
+constexpr int STAGE = 3 * A_SPLIT + 3 * B_SPLIT;
+constexpr int SMEM = 2 * STAGE + 1024 + 64;
+constexpr int SPREAD_LIMIT = 90;              // bits, see tc_selected
+constexpr int NONFINITE = 100000;
+constexpr long long WAIT_LIMIT = 1ll << 26;   // polls of an mbarrier before giving up
+constexpr int ERR_TIMEOUT = 1;
+}  // namespace tc
+
+// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled K-major tile
+__device__ __forceinline__ int sw128(int r, int c) { return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 B apart (leading offset unused for this layout), sm_100-family version
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// v (|v| < 1 after scaling) as three BF16 terms
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(v);
+  const float r1 = __fsub_rn(v, __bfloat162float(a));
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b)));
+}
+
+// e with |v| < 2^e from the biased exponent bits (v != 0; subnormals as -1022)
+__device__ __forceinline__ int exp_bound(double v) {
+  const int E = (__double2hiint(v) >> 20) & 0x7FF;
+  return (E == 0 ? 1 : E) - 1022;
+}
+
+// float(v * 2^-e), round to nearest even, from the bit fields alone (no FP64
+// arithmetic: this part runs FP64 at 1/61 of the FP32 rate).  Results below
+// FP32's normal range become zero; v must be finite with |v| 2^-e < 2^127.
+__device__ __forceinline__ float d2f_scaled(double v, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const int E = (int)((hi >> 20) & 0x7FF);
+  const int Ef = E - e - 1023 + 127;
+  if (E == 0 || Ef <= 0) return 0.f;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  unsigned int f = ((unsigned int)Ef << 23) + (unsigned int)(mant >> 29);
+  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull), halfway = 0x10000000u;
+  f += (rem > halfway || (rem == halfway && (f & 1u))) ? 1u : 0u;   // a carry into the exponent is exact
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// 2^e as a double (e clamped to the normal range -1022..1023)
+__device__ __forceinline__ double pow2d(int e) {
+  e = max(-1022, min(e, 1023));
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// The tensor-core kernel runs when both operands are finite and the smaller
+// of the two exponent spreads (max - min inside one scaled row) is at most
+// SPREAD_LIMIT: every row then holds a product within 2^-(min spread + 2) of
+// the row scales, so terms flushed below FP32's range cost at most 2^-126
+// relative to it, far under the 2^-24 rounding of the split.
+__device__ __forceinline__ bool tc_selected(const int* __restrict__ f) {
+  return f[0] < tc::NONFINITE && f[1] < tc::NONFINITE && min(f[0], f[1]) <= tc::SPREAD_LIMIT;
+}
+
+// per column of g: exponent bound over z (of max(|re|, |im|) per node) and the
+// spread -> flag[0]; a block covers 32 columns x 8 groups of z, reduced in
+// shared memory
+constexpr int GX_COLS = 32, GX_ZG = 8;
+__global__ void __launch_bounds__(GX_COLS * GX_ZG) k_tc_gexp(const double2* __restrict__ g, int m, long long ncol,
+                                                             int* __restrict__ ecol, int* __restrict__ flag) {
+  __shared__ int smax[GX_ZG][GX_COLS], smin[GX_ZG][GX_COLS], sbad[GX_ZG][GX_COLS];
+  const int cl = threadIdx.x % GX_COLS, zg = threadIdx.x / GX_COLS;
+  const long long col = blockIdx.x * (long long)GX_COLS + cl;
+  int emax = -100000, emin = 100000, bad = 0;
+  if (col < ncol)
+    for (int iz = zg; iz < m; iz += GX_ZG) {
+      const double2 v = g[(long long)iz * ncol + col];
+      const double a = fmax(fabs(v.x), fabs(v.y));
+      bad |= !isfinite(a);
+      if (a != 0.0) { const int e = exp_bound(a); emax = max(emax, e); emin = min(emin, e); }
+    }
+  smax[zg][cl] = emax;
+  smin[zg][cl] = emin;
+  sbad[zg][cl] = bad;
+  __syncthreads();
+  if (zg == 0) {
+    for (int j = 1; j < GX_ZG; ++j) {
+      emax = max(emax, smax[j][cl]);
+      emin = min(emin, smin[j][cl]);
+      bad |= sbad[j][cl];
+    }
+    int sp = 0;
+    if (col < ncol) {
+      ecol[col] = (emax == -100000) ? 0 : emax;
+      sp = bad ? tc::NONFINITE : (emax == -100000 ? 0 : emax - emin);
+    }
+    for (int o = 16; o > 0; o >>= 1) sp = max(sp, __shfl_xor_sync(0xffffffffu, sp, o));
+    if (cl == 0 && sp > 0) atomicMax(flag, sp);
+  }
+}
+
+// per z-row of P: exponent bound and spread -> flag[1] (one warp per row)
+__global__ void k_tc_pexp(const double2* __restrict__ zt, int T, int t0, int m, int* __restrict__ erow,
+                          int* __restrict__ flag) {
+  const int t = blockIdx.x, lane = threadIdx.x;
+  int emax = -100000, emin = 100000;
+  bool bad = false;
+  if (t0 + t < T)
+    for (int iz = lane; iz < m; iz += 32) {
+      const double2 v = zt[(long long)(t0 + t) * m + iz];
+      const double a = fmax(fabs(v.x), fabs(v.y));
+      bad |= !isfinite(a);
+      if (a != 0.0) { const int e = exp_bound(a); emax = max(emax, e); emin = min(emin, e); }
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    erow[t] = (emax == -100000) ? 0 : emax;
+    atomicMax(flag + 1, bad ? tc::NONFINITE : (emax == -100000 ? 0 : emax - emin));
+  }
+}
+
+// B operand: per K chunk c and split s, 64 rows x 128 B, pre-swizzled; one
+// thread per (chunk, row, 16-byte chunk)
+__global__ void k_tc_psplit(const double2* __restrict__ zt, int T, int t0, int m, int nkc,
+                            const int* __restrict__ erow, unsigned char* __restrict__ Bg) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= nkc * 2 * tc::TT * 8) return;
+  const int q = id & 7, j = (id >> 3) % (2 * tc::TT), c = id / (2 * tc::TT * 8);
+  const int t = j % tc::TT, im_row = j / tc::TT;
+  __align__(16) __nv_bfloat16 v[3][8];
+  const int er = erow[t];
+  for (int e = 0; e < 8; ++e) {
+    const int k = q * 8 + e, iz = c * tc::KZ + (k >> 1);
+    double x = 0.0;
+    if (t0 + t < T && iz < m) {
+      const double2 p = zt[(long long)(t0 + t) * m + iz];
+      // Re rows (P_re, -P_im), Im rows (P_im, P_re)
+      x = im_row ? ((k & 1) ? p.x : p.y) : ((k & 1) ? -p.y : p.x);
+    }
+    split3(d2f_scaled(x, er), v[0][e], v[1][e], v[2][e]);
+  }
+  for (int sidx = 0; sidx < 3; ++sidx) {
+    unsigned char* dst = Bg + ((size_t)c * 3 + sidx) * tc::B_SPLIT + sw128(j, q);
+    *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v[sidx]);
+  }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < tc::WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(tc::NTHR, 1)
+    k_ff3_stageA_tc(const double2* __restrict__ g, int m, long long ncol, int T, int t0, int nkc,
+                    const unsigned char* __restrict__ Bg, const int* __restrict__ ecol,
+                    const int* __restrict__ erow, int* __restrict__ flag, double2* __restrict__ T1) {
+  if (!tc_selected(flag)) return;                  // the FP64 kernel takes this launch
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 2 * tc::STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(base + 2 * tc::STAGE + 32);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long col0 = (long long)blockIdx.x * tc::TM;
+  const int rl = tid & (tc::TM - 1), half = tid >> 7;     // row of A and z half-chunk of this thread
+  const long long col = col0 + rl;
+  const bool colv = col < ncol;
+  const int ecl = colv ? ecol[col] : 0;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  // instruction descriptor: FP32 accumulator, BF16 A and B, K-major, N = 64, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * tc::TT >> 3) << 17) |
+                         ((uint32_t)(tc::TM >> 4) << 24);
+  bool ok = true;
+  for (int c = 0; c < nkc; ++c) {
+    const int st = c & 1;
+    unsigned char* sA = base + st * tc::STAGE;
+    unsigned char* sB = sA + 3 * tc::A_SPLIT;
+    // the MMAs of chunk c - 2 read this stage
+    if (c >= 2) ok &= mbar_wait(smem_addr(&mbar[st]), (uint32_t)(((c - 2) >> 1) & 1));
+    // A: 16 z-nodes of this thread's column, 4 at a time -> one 16-byte chunk per split
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const int izl = half * 16 + qq * 4;
+      __align__(16) __nv_bfloat16 v[3][8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int iz = c * tc::KZ + izl + e;
+        double2 x = make_double2(0.0, 0.0);
+        if (colv && iz < m) x = g[(long long)iz * ncol + col];
+        split3(d2f_scaled(x.x, ecl), v[0][2 * e], v[1][2 * e], v[2][2 * e]);
+        split3(d2f_scaled(x.y, ecl), v[0][2 * e + 1], v[1][2 * e + 1], v[2][2 * e + 1]);
+      }
+      const int off = sw128(rl, half * 4 + qq);
+#pragma unroll
+      for (int sidx = 0; sidx < 3; ++sidx)
+        *reinterpret_cast<uint4*>(sA + sidx * tc::A_SPLIT + off) = *reinterpret_cast<const uint4*>(v[sidx]);
+    }
+    // B: copy the pre-swizzled chunk
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(Bg + (size_t)c * 3 * tc::B_SPLIT);
+      uint4* dst = reinterpret_cast<uint4*>(sB);
+      for (int i = tid; i < 3 * tc::B_SPLIT / 16; i += tc::NTHR) dst[i] = src[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const uint32_t dacc = tmem + (p == 0 ? 0u : (uint32_t)(2 * tc::TT));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = sw128_desc(smem_addr(sA + pa[p] * tc::A_SPLIT) + 32 * kk);
+          const uint64_t bd = sw128_desc(smem_addr(sB + pb[p] * tc::B_SPLIT) + 32 * kk);
+          const uint32_t acc = (c > 0 || kk > 0 || p > 1) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(dacc),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&mbar[st]))
+                   : "memory");
+    }
+  }
+  // the last commit covers every MMA issued before it
+  const int cl = nkc - 1;
+  ok &= mbar_wait(smem_addr(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1));
+  if (!ok) {
+    atomicOr(flag + 2, tc::ERR_TIMEOUT);
+    mbar_wait(smem_addr(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    // warp w reads lanes 32 (w % 4).. (rows) and z-rows [16 (w / 4), +16)
+    const int lg = warp & 3, th = warp >> 2;
+    const uint32_t ta = tmem + ((uint32_t)(32 * lg) << 16);
+    uint32_t r0[16], i0[16], r1[16], i1[16];
+#define TC_LD16(dst, colo)                                                                                   \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+               : "=r"(dst[0]), "=r"(dst[1]), "=r"(dst[2]), "=r"(dst[3]), "=r"(dst[4]), "=r"(dst[5]),          \
+                 "=r"(dst[6]), "=r"(dst[7]), "=r"(dst[8]), "=r"(dst[9]), "=r"(dst[10]), "=r"(dst[11]),          \
+                 "=r"(dst[12]), "=r"(dst[13]), "=r"(dst[14]), "=r"(dst[15])                                     \
+               : "r"(ta + (uint32_t)(colo)))
+    TC_LD16(r0, 16 * th);
+    TC_LD16(i0, tc::TT + 16 * th);
+    TC_LD16(r1, 2 * tc::TT + 16 * th);
+    TC_LD16(i1, 3 * tc::TT + 16 * th);
+#undef TC_LD16
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const long long ocol = col0 + 32 * lg + lane;
+    if (ocol < ncol) {
+      const int ec = ecol[ocol];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int t = 16 * th + j;
+        if (t0 + t >= T) continue;
+        const int e = ec + erow[t];
+        const double re = (double)__uint_as_float(r0[j]) + (double)__uint_as_float(r1[j]);
+        const double im = (double)__uint_as_float(i0[j]) + (double)__uint_as_float(i1[j]);
+        T1[(long long)(t0 + t) * ncol + ocol] =
+            (e >= -1022 && e <= 1023) ? make_double2(re * pow2d(e), im * pow2d(e)) : make_double2(ldexp(re, e), ldexp(im, e));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+}
+
 // ---- 3D sum-factorised contraction --------------------------------------------
 // stage A: T1[t][col] = sum_iz Pz[t][iz] g[iz][col] for a group of TB distinct
 // z-components t (col = iy m + ix); each thread keeps TB sums in registers so
@@ -399,7 +720,8 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
 template <int TB>
 __global__ void __launch_bounds__(256) k_ff3_stageA(const double2* __restrict__ zt, int T, int t0,
                                                     const double2* __restrict__ g, int m, long long ncol,
-                                                    double2* __restrict__ T1) {
+                                                    double2* __restrict__ T1, const int* __restrict__ skip_if_tc) {
+  if (skip_if_tc && tc_selected(skip_if_tc)) return;   // the tensor-core kernel wrote T1
   __shared__ double2 zs[TB][32];
   const long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double2 acc[TB];
@@ -490,7 +812,7 @@ void free_ff_buffers(csff_plan* P) {
   FFBuffers& b = P->ff;
   for (void* p : {(void*)b.dg, (void*)b.dxt, (void*)b.dyt, (void*)b.dzt, (void*)b.dT, (void*)b.dal,
                   (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc, (void*)b.dxdf, (void*)b.dgdf,
-                  (void*)b.dex, (void*)b.deg, (void*)b.dspread})
+                  (void*)b.dex, (void*)b.deg, (void*)b.dspread, (void*)b.dtcb, (void*)b.dtce, (void*)b.dtcflag})
     if (p) cudaFree(p);
   b = FFBuffers{};
 }
@@ -604,11 +926,49 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
                                           B.dxt, B.dyt, B.dzt);
       double2* T1 = B.dT;
       double2* T2 = B.dT + (size_t)n_uz * ncol;
+      const bool use_tc = P->ff_mode == CSFF_FF_TC_BF16X3;
+      const int nkc = (m + tc::KZ - 1) / tc::KZ;
+      if (use_tc) {
+        if ((e = ensure((void**)&B.dtcb, B.tcb, (size_t)nkc * 3 * tc::B_SPLIT, P)) != cudaSuccess ||
+            (e = ensure((void**)&B.dtce, B.tce, sizeof(int) * ((size_t)ncol + tc::TT), P)) != cudaSuccess)
+          return cuda_fail(e, "far field scratch");
+        if (!B.dtcflag && (e = cudaMalloc((void**)&B.dtcflag, 3 * sizeof(int))) != cudaSuccess)
+          return cuda_fail(e, "far field scratch");
+        if ((e = cudaFuncSetAttribute(k_ff3_stageA_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM)) !=
+                cudaSuccess ||
+            (e = cudaMemsetAsync(B.dtcflag, 0, 3 * sizeof(int), s)) != cudaSuccess)
+          return cuda_fail(e, "far field tensor-core set-up");
+        k_tc_gexp<<<(unsigned)((ncol + GX_COLS - 1) / GX_COLS), GX_COLS * GX_ZG, 0, s>>>(B.dg, m, ncol, B.dtce,
+                                                                                         B.dtcflag);
+        count_launch();
+      }
       {
         ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_uz * m + (double)ncol * m + (double)n_uz * ncol),
                      8.0 * (double)n_uz * (double)ncol * m);
-        for (int t0 = 0; t0 < n_uz; t0 += 16)
-          k_ff3_stageA<16><<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(B.dxt, n_uz, t0, B.dg, m, ncol, T1);
+        if (use_tc) {
+          // per group of 32 z-rows: exponents and split phases, the tensor-core
+          // kernel, and the FP64 kernel, which returns at once unless the range
+          // check turned the tensor-core kernel away
+          for (int t0 = 0; t0 < n_uz; t0 += tc::TT) {
+            int* erow = B.dtce + ncol;
+            if ((e = cudaMemsetAsync(B.dtcflag + 1, 0, sizeof(int), s)) != cudaSuccess)
+              return cuda_fail(e, "memset");
+            k_tc_pexp<<<tc::TT, 32, 0, s>>>(B.dxt, n_uz, t0, m, erow, B.dtcflag);
+            const int nth = nkc * 2 * tc::TT * 8;
+            k_tc_psplit<<<(nth + 255) / 256, 256, 0, s>>>(B.dxt, n_uz, t0, m, nkc, erow, B.dtcb);
+            k_ff3_stageA_tc<<<(unsigned)((ncol + tc::TM - 1) / tc::TM), tc::NTHR, tc::SMEM, s>>>(
+                B.dg, m, ncol, n_uz, t0, nkc, B.dtcb, B.dtce, erow, B.dtcflag, T1);
+            for (int tb = t0; tb < std::min(n_uz, t0 + tc::TT); tb += 16)
+              k_ff3_stageA<16><<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(B.dxt, n_uz, tb, B.dg, m, ncol, T1,
+                                                                              B.dtcflag);
+            count_launch(3 + (std::min(n_uz, t0 + tc::TT) - t0 + 15) / 16);
+          }
+        } else {
+          for (int t0 = 0; t0 < n_uz; t0 += 16)
+            k_ff3_stageA<16><<<(unsigned)((ncol + 255) / 256), 256, 0, s>>>(B.dxt, n_uz, t0, B.dg, m, ncol, T1,
+                                                                            nullptr);
+          count_launch((n_uz + 15) / 16);
+        }
       }
       k_ff3_stageB<<<dim3((m + 127) / 128, n_ang), 128, sizeof(double2) * m, s>>>(B.dyt, B.dxr, T1, m, T2);
       // stage C: F[a] = pref sum_ix Px[a][ix] T2[a][ix]  (the 2D stage-2 kernel on rows a)
@@ -619,8 +979,18 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
       double2 pref = make_double2(k2 * hd * std::cos(3 * P->prob.gamma), k2 * hd * std::sin(3 * P->prob.gamma));
       k_ff_stage2<2><<<n_ang, 256, 0, s>>>(T2, B.dxr, B.ds1, B.dzt, B.dzt, m, pref, F, F_exp, F_exp != nullptr,
                                            B.dmisc + 1);
-      count_launch(3 + (n_uz + 15) / 16);
+      count_launch(3);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "far field 3D kernels");
+      if (use_tc) {
+        int fl[3] = {0, 0, 0};
+        if ((e = cudaMemcpyAsync(fl, B.dtcflag, sizeof(fl), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+          return cuda_fail(e, "far field tensor-core status");
+        if (fl[2] & tc::ERR_TIMEOUT) {
+          set_error("tensor-core far field: an mbarrier wait ran out");
+          return CSFF_ERR_TIMEOUT;
+        }
+      }
       if (scaled) {
         int flag = 0;
         if ((e = cudaMemcpyAsync(&flag, B.dmisc + 1, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
