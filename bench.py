@@ -416,7 +416,9 @@ def measure_variants(csff, torch, dev, stream, flush):
 
 def measure_3d(csff, torch, dev, stream, flush):
     """257^3 on [-15,15]^3, k = 4, 16 incident directions, 64 x 32 angles,
-    FP32-inner / FP64-refinement, sum-factorised FP64 far field."""
+    FP32-inner / FP64-refinement; the step with the FP64-class sum-factorised
+    far field, then the far field alone in both modes (FP64 and the
+    tensor-core z-contraction) and the relative L2 distance of their maps."""
     c = W.big_3d(n=257, n_rhs=16)
     c["opts"]["precision"] = "mixed"
     plan = csff.Plan(c["problem"], c["opts"], stream=stream)
@@ -431,20 +433,35 @@ def measure_3d(csff, torch, dev, stream, flush):
         info["inf"] = inf
         plan.far_field(c["eta"], u, c["alphas"], F, Fe)
 
+    def ff():
+        plan.far_field(c["eta"], u, c["alphas"], F, Fe)
+
     step()
     ms = _time_events(torch, stream, step, flush, 2)
-    csff.prof_begin(csff.PROF_FF_CONTRACT)
-    plan.far_field(c["eta"], u, c["alphas"], F, Fe)
-    torch.cuda.synchronize()
-    ff = csff.prof_end()["ff_contract"]
+    out = {"value": nr / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "maps_per_step": nr,
+           "cycles": [i["cycles"] for i in info["inf"]],
+           "all_converged": all(i["rel_res"] <= 1e-8 for i in info["inf"])}
+    maps = {}
+    for mode, name in ((csff.FF_FP64, "fp64"), (csff.FF_TC_BF16X3, "tc_bf16x3")):
+        plan.set_far_field_mode(mode)
+        ff()
+        ff_ms = _time_events(torch, stream, ff, flush, 3)
+        csff.prof_begin(csff.PROF_FF_CONTRACT)
+        ff()
+        torch.cuda.synchronize()
+        prof = csff.prof_end()["ff_contract"]
+        maps[name] = (F.cpu().numpy() * 2.0 ** Fe.cpu().numpy().astype(np.float64)).reshape(nr, na)
+        out[f"ff_{name}_ms_per_16_maps"] = ff_ms
+        out[f"ff_{name}_stageA_ms_per_map"] = prof["ms"] / max(1, nr)
+        out[f"ff_{name}_stageA_tflops"] = prof["alg_flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] else 0.0
+    out["ff_fp64_stageA_fp64_frac"] = out["ff_fp64_stageA_tflops"] / FP64_PEAK_TFLOPS
+    rel = np.linalg.norm(maps["tc_bf16x3"] - maps["fp64"], axis=1) / np.linalg.norm(maps["fp64"], axis=1)
+    out["tc_vs_fp64_rel_l2"] = {"max": float(rel.max()), "median": float(np.median(rel)),
+                                "maps_below_1e-5": int((rel <= 1e-5).sum())}
+    out["step_ms_with_tc_far_field"] = ms - out["ff_fp64_ms_per_16_maps"] + out["ff_tc_bf16x3_ms_per_16_maps"]
+    plan.set_far_field_mode(csff.FF_FP64)
     plan.close()
-    return {"value": nr / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "maps_per_step": nr,
-            "cycles": [i["cycles"] for i in info["inf"]],
-            "all_converged": all(i["rel_res"] <= 1e-8 for i in info["inf"]),
-            "ff_stageA_ms_per_map": ff["ms"] / max(1, nr),
-            "ff_stageA_tflops": ff["alg_flops"] / (ff["ms"] * 1e-3) / 1e12 if ff["ms"] else 0.0,
-            "ff_stageA_fp64_frac": (ff["alg_flops"] / (ff["ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS
-                                    if ff["ms"] else 0.0)}
+    return out
 
 
 def measure_learned(csff, torch, dev, stream, flush):

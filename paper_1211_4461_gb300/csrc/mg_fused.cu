@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(NT, 8) k_down2(const cx<T>* __restrict__ u_in,
                                               const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
                                               int m, int mc, cx<T>* __restrict__ u_out, cx<T>* __restrict__ bc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_prologue();
   tiles::down_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, zero_init, b, K, c, m, mc, u_out, bc,
                                  smem_raw);
 }
@@ -35,6 +36,7 @@ __global__ void __launch_bounds__(NT, 8) k_up2(const cx<T>* __restrict__ u_in, c
                                             const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
                                             int m, int mc, cx<T>* __restrict__ u_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_prologue();
   tiles::up_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, K, c, m, mc, u_out, smem_raw);
 }
 
@@ -42,6 +44,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(1024) k_coarse_levels(CoarseLevels L, const cx<T>* __restrict__ b_top,
                                                         cx<T>* __restrict__ u_top, const cx<T>* __restrict__ inv) {
   extern __shared__ unsigned char smem_raw[];
+  pdl_prologue();
   tiles::coarse_levels_block<T, D, false>(L, b_top, u_top, inv, smem_raw);
 }
 
@@ -83,17 +86,18 @@ cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, boo
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0);
   const tiles::LevelCoef<T> K = level_coef<T>(F);
   const int ng = coef_ng<T>(F);
+  cudaError_t e;
   if (small_tiles(Cl.m)) {
     dim3 g((Cl.m + 7) / 8, (Cl.m + 7) / 8);
-    k_down2<T, 8><<<g, NT, down_smem<8>(sizeof(T), ng), s>>>(u_in, zero_init ? 1 : 0, b, K, c, F.m, Cl.m, u_out,
-                                                               bc);
+    e = launch_pdl(k_down2<T, 8>, g, dim3(NT), down_smem<8>(sizeof(T), ng), s, u_in, zero_init ? 1 : 0, b, K, c,
+                   F.m, Cl.m, u_out, bc);
   } else {
     dim3 g((Cl.m + 15) / 16, (Cl.m + 15) / 16);
-    k_down2<T, 16><<<g, NT, down_smem<16>(sizeof(T), ng), s>>>(u_in, zero_init ? 1 : 0, b, K, c, F.m, Cl.m, u_out,
-                                                                 bc);
+    e = launch_pdl(k_down2<T, 16>, g, dim3(NT), down_smem<16>(sizeof(T), ng), s, u_in, zero_init ? 1 : 0, b, K,
+                   c, F.m, Cl.m, u_out, bc);
   }
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -103,15 +107,16 @@ cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0);
   const tiles::LevelCoef<T> K = level_coef<T>(F);
   const int ng = coef_ng<T>(F);
+  cudaError_t e;
   if (small_tiles(Cl.m)) {
     dim3 g((Cl.m + 7) / 8, (Cl.m + 7) / 8);
-    k_up2<T, 8><<<g, NT, up_smem<8>(sizeof(T), ng), s>>>(u_in, ec, b, K, c, F.m, Cl.m, u_out);
+    e = launch_pdl(k_up2<T, 8>, g, dim3(NT), up_smem<8>(sizeof(T), ng), s, u_in, ec, b, K, c, F.m, Cl.m, u_out);
   } else {
     dim3 g((Cl.m + 15) / 16, (Cl.m + 15) / 16);
-    k_up2<T, 16><<<g, NT, up_smem<16>(sizeof(T), ng), s>>>(u_in, ec, b, K, c, F.m, Cl.m, u_out);
+    e = launch_pdl(k_up2<T, 16>, g, dim3(NT), up_smem<16>(sizeof(T), ng), s, u_in, ec, b, K, c, F.m, Cl.m, u_out);
   }
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int real_bytes) {
@@ -133,10 +138,10 @@ cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, 
   }
   size_t sm = coarse_levels_smem(dim, lv, lc, sizeof(T));
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * 2.0 * lv[lc].N, 0);
-  if (dim == 2) k_coarse_levels<T, 2><<<1, 1024, sm, s>>>(L, b, u, inv);
-  else k_coarse_levels<T, 3><<<1, 1024, sm, s>>>(L, b, u, inv);
+  cudaError_t e = (dim == 2) ? launch_pdl(k_coarse_levels<T, 2>, dim3(1), dim3(1024), sm, s, L, b, u, inv)
+                             : launch_pdl(k_coarse_levels<T, 3>, dim3(1), dim3(1024), sm, s, L, b, u, inv);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Opt the fused kernels into the dynamic shared memory they need (done at plan

@@ -46,6 +46,7 @@ __device__ __forceinline__ cx<T> apply_point(const cx<T>* __restrict__ u, cx<T> 
 template <typename T, int D>
 __global__ void k_residual(const cx<T>* __restrict__ u, const cx<T>* __restrict__ b,
                            const cx<T>* __restrict__ q, cx<T> c, int m, cx<T>* __restrict__ r) {
+  pdl_prologue();
   int ix, iy, iz; long long idx;
   if (!thread_point<D>(m, ix, iy, iz, idx)) return;
   cx<T> au = apply_point<T, D>(u, u[idx], q[idx], c, m, ix, iy, iz, idx);
@@ -184,6 +185,7 @@ constexpr int RED_THREADS = 256;
 template <typename T>
 __global__ void k_norm_partial(const cx<T>* __restrict__ v, long long N, double scale,
                                double* __restrict__ partial) {
+  pdl_prologue();
   __shared__ double sh[32];
   double acc = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -197,6 +199,7 @@ __global__ void k_norm_partial(const cx<T>* __restrict__ v, long long N, double 
 
 __global__ void k_norm_finish(const double* __restrict__ partial, int nblk, double inv_scale,
                               double* __restrict__ out) {
+  pdl_prologue();
   __shared__ double sh[32];
   double acc = 0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += partial[i];
@@ -279,24 +282,57 @@ __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uin
 
 // ---- mixed precision ----------------------------------------------------------
 // r32 = r64 * 2^-e with e = exponent of ||r64||_2 (so |r32| < 1 elementwise).
+// The scaling and the rounding to FP32 (to nearest) work on the bit fields,
+// keeping the pass off the FP64 pipe (1/61 of the FP32 rate on this part);
+// values below FP32's normal range, 2^-126 ||r|| and less, become zero.
+__device__ __forceinline__ float d2f_pow2(double v, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const int E = (int)((hi >> 20) & 0x7FF);
+  const int Ef = E - e - 1023 + 127;
+  if (E == 0 || Ef <= 0) return 0.f;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  unsigned int f = ((unsigned int)Ef << 23) + (unsigned int)(mant >> 29);
+  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull), halfway = 0x10000000u;
+  f += (rem > halfway || (rem == halfway && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 __global__ void k_to32_scaled(const double2* __restrict__ r, long long N, const double* __restrict__ nrm,
                               float2* __restrict__ r32, int* __restrict__ exp_out) {
+  pdl_prologue();
   int e;
   frexp(*nrm, &e);
-  double s = ldexp(1.0, -e);
   if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = e;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x)
-    r32[i] = make_float2((float)(r[i].x * s), (float)(r[i].y * s));
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = r[i];
+    r32[i] = make_float2(d2f_pow2(v.x, e), d2f_pow2(v.y, e));
+  }
+}
+
+// FP32 value times 2^s as a double, exactly, from the bit fields (zero,
+// subnormal input, or a result outside the normal FP64 range take ldexp)
+__device__ __forceinline__ double f2d_pow2(float v, int s) {
+  const unsigned int b = __float_as_uint(v);
+  const int E = (int)((b >> 23) & 0xFFu), Ed = E + 896 + s;
+  if (E == 0 || Ed < 1 || Ed > 2046) return ldexp((double)v, s);
+  const long long bits = ((long long)(b >> 31) << 63) | ((long long)Ed << 52) |
+                         ((long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double(bits);
 }
 
 __global__ void k_update64(double2* __restrict__ u, const float2* __restrict__ e, long long N,
                            const int* __restrict__ exp_in) {
-  double s = ldexp(1.0, *exp_in);
+  pdl_prologue();
+  const int s = *exp_in;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    u[i].x = fma((double)e[i].x, s, u[i].x);
-    u[i].y = fma((double)e[i].y, s, u[i].y);
+    const float2 c = e[i];
+    double2 v = u[i];
+    v.x += f2d_pow2(c.x, s);
+    v.y += f2d_pow2(c.y, s);
+    u[i] = v;
   }
 }
 
@@ -339,9 +375,10 @@ cudaError_t launch_residual(int dim, const Level& L, const cx<T>* u, const cx<T>
   dim3 g = grid_of(dim, L.m), blk(BX, BY);
   cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
   ProfScope ps(mg_family<T>(), s, 3.0 * sizeof(cx<T>) * L.N, 0);
-  CSFF_DIM_DISPATCH(dim, k_residual, u, b, qtab<T>(L), c, L.m, r);
+  cudaError_t e = (dim == 2) ? launch_pdl(k_residual<T, 2>, g, blk, 0, s, u, b, qtab<T>(L), c, L.m, r)
+                             : launch_pdl(k_residual<T, 3>, g, blk, 0, s, u, b, qtab<T>(L), c, L.m, r);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -400,10 +437,13 @@ cudaError_t launch_norm2(const cx<T>* v, long long N, int exp_scale, double* par
   long long need = (N + RED_THREADS - 1) / RED_THREADS;
   int nb = (int)(need < nblk ? (need < 1 ? 1 : need) : nblk);
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * N, 0);
-  k_norm_partial<T><<<nb, RED_THREADS, 0, s>>>(v, N, ldexp(1.0, -exp_scale), partial);
-  k_norm_finish<<<1, RED_THREADS, 0, s>>>(partial, nb, ldexp(1.0, exp_scale), out);
+  cudaError_t e = launch_pdl(k_norm_partial<T>, dim3(nb), dim3(RED_THREADS), 0, s, v, N, ldexp(1.0, -exp_scale),
+                             partial);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_norm_finish, dim3(1), dim3(RED_THREADS), 0, s, (const double*)partial, nb,
+                   ldexp(1.0, exp_scale), out);
   count_launch(2);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_max_exp(const double2* v, long long N, int* out, cudaStream_t s) {
@@ -440,17 +480,17 @@ cudaError_t launch_rhs(int dim, int m, const double2* const* chi_tab, int n_gaus
 cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
                                int* exp_out, cudaStream_t s) {
   ProfScope ps(PF_MG64, s, 24.0 * N, 0);
-  k_to32_scaled<<<flat_blocks(N), 256, 0, s>>>(r, N, norm_dev, r32, exp_out);
+  cudaError_t e = launch_pdl(k_to32_scaled, dim3(flat_blocks(N)), dim3(256), 0, s, r, N, norm_dev, r32, exp_out);
   count_launch();
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,
                             cudaStream_t s) {
   ProfScope ps(PF_MG64, s, 40.0 * N, 0);
-  k_update64<<<flat_blocks(N), 256, 0, s>>>(u, e, N, exp_in);
+  cudaError_t err = launch_pdl(k_update64, dim3(flat_blocks(N)), dim3(256), 0, s, u, e, N, exp_in);
   count_launch();
-  return cudaGetLastError();
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 template <typename T>
