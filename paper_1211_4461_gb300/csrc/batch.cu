@@ -463,6 +463,7 @@ csff_status upload_descriptors(csff_batch* B) {
       I.cl.q[l] = L.q32;
       I.cl.dinv[l] = L.dinv32;
       I.cl.c[l] = L.c;
+      I.cl.c32[l] = make_float2((float)L.c.x, (float)L.c.y);
     }
     I.inv = P->coarse_inv32;
     I.c64 = P->lv[0].c;

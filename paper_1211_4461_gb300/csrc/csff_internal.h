@@ -36,8 +36,8 @@ template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C
 // Programmatic dependent launch: a kernel launched with launch_pdl is set up
 // while its predecessor in the stream runs, and starts as the predecessor's
 // CTAs retire (each CTA triggers its dependents implicitly when it exits; an
-// explicit early trigger measured slower here, since waiting dependents then
-// hold SM slots).  Every such kernel begins with pdl_prologue(), which waits
+// explicit trigger at kernel start measured slower on the 1025^2 solves).
+// Every such kernel begins with pdl_prologue(), which waits
 // until the predecessor has completed and its writes are visible; launched
 // the ordinary way, the wait is a no-op.
 // ---------------------------------------------------------------------------

@@ -331,8 +331,10 @@ __device__ __forceinline__ void dfacc_merge2(dfacc& re, dfacc& im, df sr, df si,
   add(im, si);
 }
 
-// T[k][rho] over blocks; 16 (k) x 64 (rho) output tile, 1 x 4 outputs per thread
-constexpr int DF_BM = 16, DF_BN = 64;
+// T[k][rho] over blocks; 16 (k) x 16 DF_J (rho) output tile, 1 x DF_J outputs per thread (small
+// tiles: the 736 CTAs of the 1025^2 maps spread over the 152 SMs more evenly than 368 larger ones)
+constexpr int DF_J = 2;                       // outputs per thread along rho
+constexpr int DF_BM = 16, DF_BN = 16 * DF_J;
 
 __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__ X, const int* __restrict__ ex, int M,
                                                       const float4* __restrict__ G, const int* __restrict__ eg, int N,
@@ -344,9 +346,9 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
   __shared__ int eA[DF_BM], eB[DF_BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
-  dfacc accr[4], acci[4];
+  dfacc accr[DF_J], acci[DF_J];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < DF_J; ++j) {
     accr[j] = dfacc{0.f, 0.f, -100000};
     acci[j] = dfacc{0.f, 0.f, -100000};
   }
@@ -362,15 +364,15 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
     if (tid < DF_BM) eA[tid] = (m0 + tid < M) ? ex[(long long)(m0 + tid) * nb + b] : 0;
     if (tid >= 64 && tid < 64 + DF_BN) eB[tid - 64] = (n0 + tid - 64 < N) ? eg[(long long)(n0 + tid - 64) * nb + b] : 0;
     __syncthreads();
-    df sr[4], si[4];
+    df sr[DF_J], si[DF_J];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) { sr[j] = df{0.f, 0.f}; si[j] = df{0.f, 0.f}; }
+    for (int j = 0; j < DF_J; ++j) { sr[j] = df{0.f, 0.f}; si[j] = df{0.f, 0.f}; }
 #pragma unroll 2
     for (int kk = 0; kk < DKB; ++kk) {
       float4 a = As[ty][kk];
       df ar{a.x, a.y}, ai{a.z, a.w}, nai{-a.z, -a.w};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < DF_J; ++j) {
         float4 bb = Bs[tx + 16 * j][kk];
         df br{bb.x, bb.y}, bi{bb.z, bb.w};
         df_mac(sr[j], ar, br);
@@ -380,13 +382,13 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) dfacc_merge2(accr[j], acci[j], sr[j], si[j], eA[ty] + eB[tx + 16 * j]);
+    for (int j = 0; j < DF_J; ++j) dfacc_merge2(accr[j], acci[j], sr[j], si[j], eA[ty] + eB[tx + 16 * j]);
     __syncthreads();
   }
   const int gm = m0 + ty;
   if (gm >= M) return;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < DF_J; ++j) {
     const int gn = n0 + tx + 16 * j;
     if (gn >= N) continue;
     T[(long long)gm * N + gn] = make_double2(ldexp((double)accr[j].hi + (double)accr[j].lo, accr[j].E),

@@ -135,6 +135,7 @@ cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, 
     L.q[i] = qt<T>(v);
     L.dinv[i] = dt<T>(v);
     L.c[i] = v.c;
+    L.c32[i] = make_float2((float)v.c.x, (float)v.c.y);
   }
   size_t sm = coarse_levels_smem(dim, lv, lc, sizeof(T));
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * 2.0 * lv[lc].N, 0);

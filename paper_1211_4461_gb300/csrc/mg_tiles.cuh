@@ -293,7 +293,12 @@ struct CoarseLevels {
   const void* q[8];
   const void* dinv[8];
   double2 c[8];
+  float2 c32[8];                // c rounded to FP32 (FP32 cycles)
 };
+
+template <typename T> __device__ __forceinline__ cx<T> level_c(const CoarseLevels& L, int l);
+template <> __device__ __forceinline__ double2 level_c<double>(const CoarseLevels& L, int l) { return L.c[l]; }
+template <> __device__ __forceinline__ float2 level_c<float>(const CoarseLevels& L, int l) { return L.c32[l]; }
 
 template <typename T, int D>
 __device__ __forceinline__ cx<T> apply_s(const cx<T>* u, int m, int ix, int iy, int iz, int idx, cx<T> q,
@@ -362,17 +367,40 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
       Ds[l] = p; p += N[l];
     }
   }
-  // every global read up front (independent loads in flight together); the
-  // phases below touch shared memory only
+  // every global read up front; the phases below touch shared memory only.
+  // The first point of each level per thread is loaded into registers for
+  // all levels before any store, so those loads are in flight together
+  // (in 2D every level handled here has at most one point per thread).
+  {
+    const int t = threadIdx.x;
+    C qv[8], dv[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+      if (l < L.nl && t < N[l]) {
+        qv[l] = reinterpret_cast<const C*>(L.q[l])[t];
+        dv[l] = reinterpret_cast<const C*>(L.dinv[l])[t];
+      }
+    const C bv = (t < N[0]) ? ld<COH>(b_top + t) : zero_c<T>();
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+      if (l < L.nl && t < N[l]) {
+        Qs[l][t] = qv[l];
+        Ds[l][t] = dv[l];
+      }
+    if (t < N[0]) {
+      B[0][t] = bv;
+      U[0][t] = zero_c<T>();
+    }
+  }
   for (int l = 0; l < L.nl; ++l) {
     const C* q = reinterpret_cast<const C*>(L.q[l]);
     const C* dv = reinterpret_cast<const C*>(L.dinv[l]);
-    for (int i = threadIdx.x; i < N[l]; i += blockDim.x) {
+    for (int i = threadIdx.x + blockDim.x; i < N[l]; i += blockDim.x) {
       Qs[l][i] = q[i];
       Ds[l][i] = dv[i];
     }
   }
-  for (int i = threadIdx.x; i < N[0]; i += blockDim.x) {
+  for (int i = threadIdx.x + blockDim.x; i < N[0]; i += blockDim.x) {
     B[0][i] = ld<COH>(b_top + i);
     U[0][i] = zero_c<T>();
   }
@@ -381,7 +409,7 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
   const int last = L.nl - 1;
   for (int l = 0; l < last; ++l) {
     const int m = L.m[l], mc = L.m[l + 1];
-    C c = mk<C>((T)L.c[l].x, (T)L.c[l].y);
+    const C c = level_c<T>(L, l);
     if (l > 0)
       for (int i = threadIdx.x; i < N[l]; i += blockDim.x) U[l][i] = zero_c<T>();
     __syncthreads();
@@ -426,7 +454,7 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
   }
   for (int l = last - 1; l >= 0; --l) {
     const int m = L.m[l], mc = L.m[l + 1];
-    C c = mk<C>((T)L.c[l].x, (T)L.c[l].y);
+    const C c = level_c<T>(L, l);
     for (int i = threadIdx.x; i < N[l]; i += blockDim.x) {
       int ix, iy, iz;
       decode<D>(i, m, ix, iy, iz);
