@@ -368,9 +368,8 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
     }
   }
   // every global read up front; the phases below touch shared memory only.
-  // The first point of each level per thread is loaded into registers for
-  // all levels before any store, so those loads are in flight together
-  // (in 2D every level handled here has at most one point per thread).
+  // Each thread's first point of every level is loaded into registers before
+  // any store, so those loads are in flight together; the rest follow.
   {
     const int t = threadIdx.x;
     C qv[8], dv[8];
