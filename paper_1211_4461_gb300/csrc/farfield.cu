@@ -61,44 +61,70 @@ __global__ void k_gfield(Tabs8 tabs, int n_gauss, const double2* __restrict__ ui
   g[idx] = cadd(cu, cmul(chi, u[idx]));
 }
 
-// Phase tables.  x-table rows k < n_ux: P_x(k, i) 2^-s1[k]; y/z tables for
-// every angle: ytab[a][i], ztab[a][i] (unscaled).  x_i = lo + (i + 1) h.
-// s1[k] = max(0, bound_exp(P_x row) + gmax + ceil(log2 m) + 2 - 1020).
-__global__ void k_phase_tables(const double* __restrict__ ux, int n_ux, const double* __restrict__ alpha,
-                               int n_ang, int dim, int m, double lo, double h, double k, double sg,
-                               double cg, const int* __restrict__ gmax, double2* __restrict__ xtab,
-                               double2* __restrict__ ytab, double2* __restrict__ ztab,
-                               int* __restrict__ s1, int* __restrict__ flag) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int row = blockIdx.y;
-  if (i >= m) return;
+// Phase tables P(a, x_i) = exp(-i k e^{i gamma} a x_i) = exp(k a x_i (sin g - i cos g)):
+// one CTA per row (a distinct alpha_x; or an angle, whose y (and z) rows it
+// fills).  The exponentials are evaluated exactly only at every PT_B-th node
+// and for the PT_B offsets r h; each entry is then one complex product
+// P(x_{jB + r}) = P(x_{jB}) P(r h), with two roundings more than a direct
+// evaluation and a sixteenth of its FP64 transcendentals.  x rows carry the
+// stage-1 range scale 2^-s1 (chosen from the a-priori bound on |T|).
+constexpr int PT_B = 32;
+size_t phase_tables_smem(int m) { return sizeof(double2) * 2 * ((m + PT_B - 1) / PT_B + PT_B); }
+
+__global__ void __launch_bounds__(256) k_phase_tables(const double* __restrict__ ux, int n_ux,
+                                                      const double* __restrict__ alpha, int n_ang, int dim, int m,
+                                                      double lo, double h, double k, double sg, double cg,
+                                                      const int* __restrict__ gmax, double2* __restrict__ xtab,
+                                                      double2* __restrict__ ytab, double2* __restrict__ ztab,
+                                                      int* __restrict__ s1, int* __restrict__ flag) {
+  extern __shared__ double2 ptab[];        // per table: nb block values, then PT_B offset values
+  const int row = blockIdx.x;
+  const int nb = (m + PT_B - 1) / PT_B, W = nb + PT_B;
   const double LN2 = 0.69314718055994530942;
-  double x = lo + (double)(i + 1) * h;
+  int ntab, s = 0;
+  double av[2] = {0.0, 0.0};
+  double2* out[2] = {nullptr, nullptr};
   if (row < n_ux) {
-    double a = ux[row];
-    double xmax = fmax(a * (lo + h), a * (lo + (double)m * h));   // max_i a x_i
-    int bx = (int)ceil(k * sg * xmax / LN2) + 1;
+    ntab = 1;
+    av[0] = ux[row];
+    out[0] = xtab + (long long)row * m;
+    const double xmax = fmax(av[0] * (lo + h), av[0] * (lo + (double)m * h));   // max_i a x_i
+    const int bx = (int)ceil(k * sg * xmax / LN2) + 1;
     int lm = 0;
     while ((1 << lm) < m) ++lm;
-    int s = bx + *gmax + lm + 2 - 1020;
+    s = bx + *gmax + lm + 2 - 1020;
     s = s > 0 ? s : 0;
-    if (i == 0) { s1[row] = s; if (s > 0) atomicOr(flag, 1); }
-    double mag = exp(k * sg * a * x - (double)s * LN2);
+    if (threadIdx.x == 0) {
+      s1[row] = s;
+      if (s > 0) atomicOr(flag, 1);
+    }
+  } else {
+    const int ar = row - n_ux;
+    if (ar >= n_ang) return;
+    ntab = dim - 1;
+    for (int c = 1; c < dim; ++c) av[c - 1] = alpha[(long long)ar * dim + c];
+    out[0] = ytab + (long long)ar * m;
+    out[1] = ztab + (long long)ar * m;
+  }
+  for (int q = threadIdx.x; q < ntab * W; q += blockDim.x) {
+    const int tb = q / W, j = q - tb * W;
+    const double a = av[tb];
+    double x, sub = 0.0;
+    if (j < nb) {
+      x = lo + (double)(j * PT_B + 1) * h;
+      sub = (double)s * LN2;
+    } else {
+      x = (double)(j - nb) * h;
+    }
+    const double mag = exp(k * sg * a * x - sub);
     double sn, cs;
     sincos(k * cg * a * x, &sn, &cs);
-    xtab[(long long)row * m + i] = make_double2(mag * cs, -mag * sn);
-  } else {
-    int ar = row - n_ux;                 // y (and z) tables for angle ar
-    if (ar >= n_ang) return;
-    for (int c = 1; c < dim; ++c) {
-      double a = alpha[(long long)ar * dim + c];
-      double mag = exp(k * sg * a * x);
-      double sn, cs;
-      sincos(k * cg * a * x, &sn, &cs);
-      double2 v = make_double2(mag * cs, -mag * sn);
-      if (c == 1) ytab[(long long)ar * m + i] = v;
-      else ztab[(long long)ar * m + i] = v;
-    }
+    ptab[q] = make_double2(mag * cs, -mag * sn);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < ntab * m; q += blockDim.x) {
+    const int tb = q / m, i = q - tb * m;
+    out[tb][i] = cmul(ptab[tb * W + i / PT_B], ptab[tb * W + nb + i % PT_B]);
   }
 }
 
@@ -1005,9 +1031,9 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   }
   if ((e = ensure((void**)&B.dT, B.T, sizeof(double2) * (size_t)n_trow * R, P)) != cudaSuccess)
     return cuda_fail(e, "far field scratch");
-  dim3 tg((m + 127) / 128, n_ux + n_ang);
-  k_phase_tables<<<tg, 128, 0, s>>>(B.dux, n_ux, B.dal, n_ang, d, m, P->prob.box_lo, L.h, P->prob.k, sg, cg,
-                                    B.dmisc, B.dxt, B.dyt, B.dzt, B.ds1, B.dmisc + 1);
+  k_phase_tables<<<n_ux + n_ang, 256, phase_tables_smem(m), s>>>(B.dux, n_ux, B.dal, n_ang, d, m, P->prob.box_lo,
+                                                                 L.h, P->prob.k, sg, cg, B.dmisc, B.dxt, B.dyt,
+                                                                 B.dzt, B.ds1, B.dmisc + 1);
   count_launch();
   // operands of the double-float contraction
   const int nbk = (m + DKB - 1) / DKB;
