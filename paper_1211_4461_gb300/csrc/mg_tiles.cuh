@@ -103,10 +103,11 @@ template <typename T, bool COH>
 __device__ __forceinline__ void load_window(int ox, int oy, int W, int m, const cx<T>* u_in, bool zero_u,
                                             const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
                                             cx<T>* X) {
+  const bool inner = ox >= 0 && oy >= 0 && ox + W <= m && oy + W <= m;
   for (int i = threadIdx.x; i < W * W; i += NT) {
     const int wy = i / W, wx = i - wy * W;
     const int fx = ox + wx, fy = oy + wy;
-    const bool in = fx >= 0 && fx < m && fy >= 0 && fy < m;
+    const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
     const long long g = (long long)fy * m + fx;
     U[i] = (in && !zero_u) ? ld<COH>(u_in + g) : zero_c<T>();
     B[i] = in ? ld<COH>(b + g) : zero_c<T>();
@@ -136,19 +137,25 @@ __device__ __forceinline__ float2 formed_diag(const LevelCoef<float>& K, float2 
 // given colour, in the form
 //   u_j <- d_j^{-1} (b_j + c sum_nbr u),
 // which equals u_j + d_j^{-1} (b_j - (A u)_j) for A u = d u - c sum_nbr u.
-template <typename T>
-__device__ __forceinline__ void rb_half(int ox, int oy, int W, int m, int colour, const LevelCoef<T>& K, cx<T> c,
-                                        cx<T>* U, const cx<T>* B, const cx<T>* X) {
-  const int lo = 1 + colour, hi = W - 2 - colour;
-  const int R = hi - lo + 1, HW = (R + 1) >> 1;
+template <typename T, int W, int COLOUR>
+__device__ __forceinline__ void rb_half(int ox, int oy, int m, const LevelCoef<T>& K, cx<T> c, cx<T>* U,
+                                        const cx<T>* B, const cx<T>* X) {
+  constexpr int lo = 1 + COLOUR, hi = W - 2 - COLOUR;
+  constexpr int R = hi - lo + 1, HW = (R + 1) >> 1;
   // only the points of this colour: in window row wy they start at lo or
-  // lo + 1, whichever gives (fx + fy) of the colour's parity, and step by 2
+  // lo + 1, whichever gives (fx + fy) of the colour's parity, and step by 2;
+  // tiles away from the domain edge skip the range tests
+  const bool inner = ox + lo >= 0 && oy + lo >= 0 && ox + hi < m && oy + hi < m;
+  const int par = (COLOUR ^ (ox + oy)) & 1;        // (fx + fy) parity = colour
   for (int t = threadIdx.x; t < R * HW; t += NT) {
     const int r = t / HW, j = t - r * HW;
     const int wy = lo + r;
-    const int wx = lo + ((colour ^ (ox + oy + wy + lo)) & 1) + 2 * j;
-    const int fx = ox + wx, fy = oy + wy;
-    if (wx > hi || fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
+    const int wx = lo + ((par ^ r) & 1) + 2 * j;
+    if (wx > hi) continue;
+    if (!inner) {
+      const int fx = ox + wx, fy = oy + wy;
+      if (fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
+    }
     const int i = wy * W + wx;
     cx<T> di;
     if constexpr (formed_coef<T>()) di = crecip(formed_diag(K, c, X, W, wx, wy));
@@ -171,10 +178,10 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
   load_window<T, COH>(ox, oy, DW, m, u_in, zero_init != 0, b, K, U, B, X);
   __syncthreads();
   // red on window [1, DW-2], black on [2, DW-3]
-  for (int colour = 0; colour < 2; ++colour) {
-    rb_half<T>(ox, oy, DW, m, colour, K, c, U, B, X);
-    __syncthreads();
-  }
+  rb_half<T, DW, 0>(ox, oy, m, K, c, U, B, X);
+  __syncthreads();
+  rb_half<T, DW, 1>(ox, oy, m, K, c, U, B, X);
+  __syncthreads();
   // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final
   // index); residual on [2P0, 2P0+FT] written over the RHS (each point reads
   // only its own RHS value)
@@ -269,10 +276,10 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
     U[i] = xadd(U[i], xadd(xscale(r0, wy0), xscale(r1, wy1)));
   }
   __syncthreads();
-  for (int colour = 0; colour < 2; ++colour) {
-    rb_half<T>(ox, oy, UW, m, colour, K, c, U, B, X);
-    __syncthreads();
-  }
+  rb_half<T, UW, 0>(ox, oy, m, K, c, U, B, X);
+  __syncthreads();
+  rb_half<T, UW, 1>(ox, oy, m, K, c, U, B, X);
+  __syncthreads();
   const int exx = (P0x + TC >= mc) ? m : 2 * P0x + FT;
   const int eyy = (P0y + TC >= mc) ? m : 2 * P0y + FT;
   for (int i = threadIdx.x; i < (FT + 1) * (FT + 1); i += NT) {
