@@ -60,12 +60,19 @@ DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 FF_DF_DRAM_BYTES = 22876160
 
 
+# FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of
+# 3, 4, 5, 6, 8 on the four 1025^2 solves gave 12.8, 11.8, 11.5, 10.9 and
+# 11.3 ms: each refinement step costs about as much as a V-cycle, and
+# stopping only after a step wastes about half a step's cycles on average.
+INNER_CYCLES = 6
+
+
 def _cases(precision, ks=None):
     out = []
     for k in (ks or KS):
         c = W.mixed_2d(k)
         c["opts"]["precision"] = precision
-        c["opts"]["inner_cycles"] = 3
+        c["opts"]["inner_cycles"] = INNER_CYCLES
         out.append(c)
     return out
 
@@ -73,6 +80,7 @@ def _cases(precision, ks=None):
 def _config(args, extra=None):
     cfg = {"workload": WORKLOAD, "maps_per_step": len(KS), "n": 1025, "levels": 8, "angles": 720,
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
+           "inner_cycles": INNER_CYCLES if args.precision == "mixed" else None,
            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
     if extra:
         cfg.update(extra)
