@@ -248,7 +248,9 @@ csff_status csff_net_loss_grad(csff_net* net, int B, int H, int W, const void* r
 csff_status csff_net_train_step(csff_net* net, int B, int H, int W, const void* r_dev, const void* q_dev,
                                 const double* c_host, int margin, float lr, float* loss_host, void* stream);
 /* Attach (net != NULL) or detach the learned step on levels 0..levels-1 of a
-   red-black plan's FP32 cycles (mixed-precision solves).  The first two
+   red-black plan's FP32 cycles (mixed-precision solves): after the red-black
+   pre-sweep, u <- u + N(h_l^2 r) with r the level's residual (so the network
+   sees the operator in units of h^2, O(1) on every grid).  The first two
    refinement steps of each solve run plain red-black sweeps; the second sets
    the reference reduction factor f = min(its factor, guard); a later learned step
    that reduces the residual by less than f turns the learned step off for the

@@ -2,8 +2,10 @@
 
 The learned smoother is not in the paper; it is a small convolutional network
 N that maps the residual r of a multigrid level to a correction, used as
-u <- u + N(r) after a red-black sweep on the finest levels.  Complex values are
-two real channels (re, im).
+u <- u + N(h^2 r) = u + h^2 N(r) after a red-black sweep on the finest levels
+(N is positively homogeneous; the loss below then takes the operator in units
+of h^2, c = e^{-2i gamma} and q = (kh)^2 (1 + chi)).  Complex values are two
+real channels (re, im).
 
     h1 = relu(conv(x0, w1)),  h2 = relu(conv(h1, w2)),  y = conv(h2, w3)
     x0 = (Re r, Im r),  w1: 16x2x3x3, w2: 16x16x3x3, w3: 2x16x3x3, no biases

@@ -338,34 +338,77 @@ struct Tracker {
   }
 };
 
+// V-cycle from level l0 (u, b: that level's iterate and right-hand side) with
+// the fused 2D V(1,1) RB-GS kernels down to the coarse-level block.
+template <typename T>
+csff_status run_fused_from(csff_plan* P, int l0, cx<T>* u, const cx<T>* b, bool zero_init) {
+  cudaStream_t s = P->stream;
+  const int lc = P->fused_lc;
+  for (int l = l0; l < lc; ++l) {
+    Level& F = P->lv[l];
+    Level& C = P->lv[l + 1];
+    const cx<T>* in = (l == l0) ? u : ubuf<T>(F);
+    const cx<T>* bl = (l == l0) ? b : bbuf<T>(F);
+    CK(csff::launch_down2<T>(F, C, in, zero_init || l > l0, bl, tbuf<T>(F), bbuf<T>(C), s), "fused down");
+  }
+  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, cinv<T>(P), bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
+     "coarse levels");
+  for (int l = lc - 1; l >= l0; --l) {
+    Level& F = P->lv[l];
+    Level& C = P->lv[l + 1];
+    cx<T>* out = (l == l0) ? u : ubuf<T>(F);
+    const cx<T>* bl = (l == l0) ? b : bbuf<T>(F);
+    CK(csff::launch_up2<T>(F, C, tbuf<T>(F), ubuf<T>(C), bl, out, s), "fused up");
+  }
+  return CSFF_OK;
+}
+
+// With the learned step active: levels below learned_levels run the per-level
+// kernels (red-black sweep, learned step, residual, full weighting; then
+// prolongation, sweep, learned step), the levels below them the fused kernels.
+csff_status run_vcycle_learned(csff_plan* P, float2* u, const float2* b, bool zero_init) {
+  cudaStream_t s = P->stream;
+  const int ll = P->learned_levels;
+  for (int l = 0; l < ll; ++l) {
+    Level& L = P->lv[l];
+    Level& C = P->lv[l + 1];
+    float2* ul = (l == 0) ? u : L.u32;
+    const float2* bl = (l == 0) ? b : L.b32;
+    if (l > 0 || zero_init) CK(csff::launch_zero<float>(ul, L.N, s), "zero");
+    CS(smooth<float>(P, l, ul, bl, 1));
+    CK(csff::launch_residual<float>(P->dim, L, ul, bl, L.r32, s), "residual");
+    CK(csff::launch_restrict<float>(P->dim, L, C, L.r32, C.b32, s), "restrict");
+  }
+  CS(run_fused_from<float>(P, ll, P->lv[ll].u32, P->lv[ll].b32, true));
+  for (int l = ll - 1; l >= 0; --l) {
+    Level& L = P->lv[l];
+    Level& C = P->lv[l + 1];
+    float2* ul = (l == 0) ? u : L.u32;
+    const float2* bl = (l == 0) ? b : L.b32;
+    CK(csff::launch_prolong_add<float>(P->dim, L, C, C.u32, ul, s), "prolong");
+    CS(smooth<float>(P, l, ul, bl, 1));
+  }
+  return CSFF_OK;
+}
+
 // One V-cycle at the finest level: the fused 2D V(1,1) RB-GS kernels when the
 // plan qualifies, else the general per-step kernels.  zero_init: the iterate
 // enters as zero (the correction equation of a refinement step).
 template <typename T>
 csff_status run_vcycle(csff_plan* P, cx<T>* u, const cx<T>* b, bool zero_init) {
-  cudaStream_t s = P->stream;
   const int lc = P->fused_lc;
+  if constexpr (sizeof(T) == 4) {
+    if (P->net && !P->learned_off) {
+      if (lc > P->learned_levels) return run_vcycle_learned(P, u, b, zero_init);
+      if (zero_init) CK(csff::launch_zero<T>(u, P->lv[0].N, P->stream), "zero");
+      return vcycle<T>(P, 0, u, b);
+    }
+  }
   if (lc < 1) {
-    if (zero_init) CK(csff::launch_zero<T>(u, P->lv[0].N, s), "zero");
+    if (zero_init) CK(csff::launch_zero<T>(u, P->lv[0].N, P->stream), "zero");
     return vcycle<T>(P, 0, u, b);
   }
-  for (int l = 0; l < lc; ++l) {
-    Level& F = P->lv[l];
-    Level& C = P->lv[l + 1];
-    const cx<T>* in = (l == 0) ? u : ubuf<T>(F);
-    const cx<T>* bl = (l == 0) ? b : bbuf<T>(F);
-    CK(csff::launch_down2<T>(F, C, in, zero_init || l > 0, bl, tbuf<T>(F), bbuf<T>(C), s), "fused down");
-  }
-  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, cinv<T>(P), bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
-     "coarse levels");
-  for (int l = lc - 1; l >= 0; --l) {
-    Level& F = P->lv[l];
-    Level& C = P->lv[l + 1];
-    cx<T>* out = (l == 0) ? u : ubuf<T>(F);
-    const cx<T>* bl = (l == 0) ? b : bbuf<T>(F);
-    CK(csff::launch_up2<T>(F, C, tbuf<T>(F), ubuf<T>(C), bl, out, s), "fused up");
-  }
-  return CSFF_OK;
+  return run_fused_from<T>(P, 0, u, b, zero_init);
 }
 
 // Body of one solver step on P->stream (eagerly or under capture): the
@@ -731,9 +774,6 @@ csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, doubl
     return CSFF_ERR_UNSUPPORTED;
   }
   if (net) CS(csff::net_reserve(net, P->lv[0].N));
-  if (net && !P->net) P->fused_saved = P->fused_lc;      // attach: remember the fused split
-  if (!net && P->net) P->fused_lc = P->fused_saved;      // detach: restore it
-  if (net) P->fused_lc = -1;                             // the learned step runs in the per-level path
   P->net = net;
   P->learned_levels = net ? levels : 0;
   P->learned_guard = guard;

@@ -143,7 +143,6 @@ struct csff_plan {
   int learned_levels = 0;
   double learned_guard = 0.5;
   bool learned_off = false;       // per-solve fallback to plain RB-GS
-  int fused_saved = -1;
 };
 
 namespace csff {

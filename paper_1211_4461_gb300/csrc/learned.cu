@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "csff_internal.h"
@@ -294,6 +295,12 @@ __global__ void k_adam(float* w, float* m, float* v, const float* gr, __nv_bfloa
   wb[i] = __float2bfloat16(wi);
 }
 
+// v *= s (the learned step's input scaling by h^2)
+__global__ void k_scale_c64(float2* v, long long n, float s) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    v[i] = make_float2(v[i].x * s, v[i].y * s);
+}
+
 __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) wb[i] = __float2bfloat16(w[i]);
@@ -532,6 +539,13 @@ csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const
   if (st != CSFF_OK) return st;
   cudaError_t e = launch_residual<float>(dim, L, u, b, L.r32, s);
   if (e != cudaSuccess) return cuda_fail(e, "learned step residual");
+  // u += N(h^2 r) = h^2 N(r): the network is positively homogeneous, and in
+  // units of h^2 the level's operator e^{-2i gamma}(4 - shift) - (kh)^2 (1 + chi)
+  // is O(1) on every grid, so one net serves levels with the same k h
+  const long long n = (long long)L.m * L.m;
+  k_scale_c64<<<(unsigned)std::min<long long>((n + 255) / 256, 152 * 16), 256, 0, s>>>(L.r32, n, (float)(L.h * L.h));
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "learned step scaling");
   return forward(N, g, L.r32, u, 1, s);
 }
 

@@ -25,8 +25,10 @@ def collect_patches(problems, opts, n_cycles=5, patch=64, per_field=4, seed=0):
     """Residual patches as the learned step sees them: in FP32 from u = 0 on
     A u = b (b the scaled right-hand side), after each red-black sweep that
     starts a V-cycle.  Returns (r, q, c): complex64 CUDA tensors (B, P, P) of
-    residuals normalised to unit RMS, the matching q = k^2(1+chi) windows, and
-    the per-patch operator constants."""
+    residuals normalised to unit RMS, the matching windows of h^2 q =
+    (kh)^2(1+chi), and the per-patch constants h^2 c = e^{-2i gamma}: the
+    operator in the units in which the plan applies the network,
+    u <- u + N(h^2 r)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     rs, qs, cs = [], [], []
     for prob, eta in problems:
@@ -38,6 +40,8 @@ def collect_patches(problems, opts, n_cycles=5, patch=64, per_field=4, seed=0):
         u = torch.zeros(plan.N, dtype=torch.complex64, device="cuda")
         r = torch.empty_like(u)
         q, c = plan.coefficients(0)
+        h2 = plan.describe()["h"][0] ** 2
+        q, c = q * h2, c * h2
         for _ in range(n_cycles):
             plan.smooth(0, u, b, 1)
             plan.residual(0, u, b, r)
