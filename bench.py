@@ -474,9 +474,10 @@ def measure_3d(csff, torch, dev, stream, flush):
 
 def measure_learned(csff, torch, dev, stream, flush):
     """2049^2 on [-20,20]^2, k = 60 (k h = 1.17 on the finest level): plain
-    red-black V(1,1) cycles against red-black + learned step on the finest
-    level.  The network is trained on the GPU on residual patches from 257^2
-    problems with the same k h (k = 7.5), chi drawn from the batch ranges."""
+    red-black V(1,1) cycles against red-black + learned step u += N(h^2 r) on
+    the finest level.  The network is trained on the GPU on residual patches
+    from 257^2 problems with the same k h (k = 7.5), chi drawn from the batch
+    ranges; in units of h^2 the operator is the same on both grids."""
     from paper_1211_4461_gb300 import learned as LR
     import math as _m
     opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
@@ -503,6 +504,7 @@ def measure_learned(csff, torch, dev, stream, flush):
     Fe = torch.zeros(720, dtype=torch.int32, device=dev)
     out = {"train_s": train_s, "train_patches": int(data[0].shape[0]),
            "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:]))}
+    maps = {}
     for name, levels in (("classical", 0), ("learned", 1)):
         plan.set_learned(net if levels else None, levels=max(levels, 1))
         info = {}
@@ -514,8 +516,14 @@ def measure_learned(csff, torch, dev, stream, flush):
 
         step()
         ms = _time_events(torch, stream, step, flush, 2)
+        maps[name] = F.cpu().numpy() * 2.0 ** Fe.cpu().numpy().astype(np.float64)
         out[name] = {"value": 1.0 / (ms / 1e3), "unit": UNIT, "ms_per_map": ms, "cycles": info["inf"]["cycles"],
                      "rel_res": info["inf"]["rel_res"], "flags": info["inf"]["flags"]}
+    # both solves reach 1e-8; the learned map against the classical one (the
+    # FP64-class far field of each solution; the oracle is pinned to that path
+    # on smaller grids)
+    out["far_field_rel_l2_learned_vs_classical"] = float(
+        np.linalg.norm(maps["learned"] - maps["classical"]) / np.linalg.norm(maps["classical"]))
     out["cycle_ratio_learned_vs_classical"] = out["learned"]["cycles"] / max(1, out["classical"]["cycles"])
     out["speedup_learned_vs_classical"] = out["classical"]["ms_per_map"] / out["learned"]["ms_per_map"]
     plan.close()

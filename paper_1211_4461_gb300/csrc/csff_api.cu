@@ -863,6 +863,10 @@ csff_status csff_solve(csff_plan* P, int n_rhs, const double* eta, void* u_dev, 
       else
         CK(csff::launch_zero<double>(L.u64, L.N, P->stream), "zero");
       st = (P->opts.precision == CSFF_PREC_FP64) ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in);
+      if (P->net && P->opts.precision != CSFF_PREC_FP64) {
+        const csff_status nst = csff::net_check(P->net);
+        if (nst != CSFF_OK) st = nst;
+      }
       if (st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)
         CK(cudaMemcpyAsync(u, L.u64, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
     }

@@ -219,6 +219,7 @@ unsigned prof_mask();
 // ---- learned smoother (learned.cu) ------------------------------------------
 csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s);
 csff_status net_reserve(csff_net* N, long long npix);
+csff_status net_check(csff_net* N);
 
 // ---- far field (farfield.cu) -----------------------------------------------
 void free_ff_buffers(csff_plan* P);

@@ -36,14 +36,23 @@ struct Geom {
   __host__ __device__ __forceinline__ long long npix() const { return (long long)B * H * W; }
 };
 
-// neighbour (i + a - 1, j + b - 1) of pixel p inside its patch, or -1
-__device__ __forceinline__ long long nbr(const Geom& g, long long p, int a, int b) {
-  int j = (int)(p % g.W);
-  long long t = p / g.W;
-  int i = (int)(t % g.H);
-  int ii = i + a - 1, jj = j + b - 1;
+// row and column of pixel p inside its patch (32-bit: the API keeps B H W
+// below 2^31)
+struct Pix { int i, j; };
+__device__ __forceinline__ Pix pix_of(const Geom& g, long long p) {
+  const int q = (int)p;
+  const int t = q / g.W;
+  return Pix{t % g.H, q - t * g.W};
+}
+
+// neighbour (i + a - 1, j + b - 1) of pixel p (at c) inside its patch, or -1
+__device__ __forceinline__ long long nbr_at(const Geom& g, Pix c, long long p, int a, int b) {
+  const int ii = c.i + a - 1, jj = c.j + b - 1;
   if (ii < 0 || ii >= g.H || jj < 0 || jj >= g.W) return -1;
   return p + (long long)(a - 1) * g.W + (b - 1);
+}
+__device__ __forceinline__ long long nbr(const Geom& g, long long p, int a, int b) {
+  return nbr_at(g, pix_of(g, p), p, a, b);
 }
 
 // layer 1: x0 = bf16(r) (2 channels) -> h1 = bf16(relu(conv)) (16 channels)
@@ -57,9 +66,12 @@ __global__ void k_conv1(Geom g, const float2* __restrict__ r, const __nv_bfloat1
   float acc[16];
 #pragma unroll
   for (int o = 0; o < 16; ++o) acc[o] = 0.f;
+  const Pix pc = pix_of(g, p);
+#pragma unroll
   for (int a = 0; a < 3; ++a)
+#pragma unroll
     for (int b = 0; b < 3; ++b) {
-      long long q = nbr(g, p, a, b);
+      long long q = nbr_at(g, pc, p, a, b);
       if (q < 0) continue;
       float2 v = r[q];
       float x0 = bf(v.x), x1 = bf(v.y);
@@ -67,64 +79,198 @@ __global__ void k_conv1(Geom g, const float2* __restrict__ r, const __nv_bfloat1
       for (int o = 0; o < 16; ++o)
         acc[o] = fmaf(ws[(o * 2 + 0) * 9 + a * 3 + b], x0, fmaf(ws[(o * 2 + 1) * 9 + a * 3 + b], x1, acc[o]));
     }
+  __align__(16) __nv_bfloat16 hv[16];
 #pragma unroll
-  for (int o = 0; o < 16; ++o) h1[p * 16 + o] = __float2bfloat16(fmaxf(acc[o], 0.f));
+  for (int o = 0; o < 16; ++o) hv[o] = __float2bfloat16(fmaxf(acc[o], 0.f));
+  uint4* dst = reinterpret_cast<uint4*>(h1 + p * 16);          // 32 bytes per pixel, two vector stores
+  dst[0] = *reinterpret_cast<const uint4*>(hv);
+  dst[1] = *reinterpret_cast<const uint4*>(hv + 8);
 }
 
-// layer 2: h1 (16) -> h2 = bf16(relu(conv)) (16)
-__global__ void k_conv2(Geom g, const __nv_bfloat16* __restrict__ h1, const __nv_bfloat16* __restrict__ w2,
-                        __nv_bfloat16* __restrict__ h2) {
-  __shared__ float ws[NP2];
-  for (int i = threadIdx.x; i < NP2; i += blockDim.x) ws[i] = __bfloat162float(w2[i]);
-  __syncthreads();
-  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= g.npix()) return;
-  float acc[16];
-#pragma unroll
-  for (int o = 0; o < 16; ++o) acc[o] = 0.f;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      long long q = nbr(g, p, a, b);
-      if (q < 0) continue;
-      const __nv_bfloat16* x = h1 + q * 16;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        float xc = __bfloat162float(x[c]);
-#pragma unroll
-        for (int o = 0; o < 16; ++o) acc[o] = fmaf(ws[(o * 16 + c) * 9 + a * 3 + b], xc, acc[o]);
-      }
-    }
-#pragma unroll
-  for (int o = 0; o < 16; ++o) h2[p * 16 + o] = __float2bfloat16(fmaxf(acc[o], 0.f));
+// Layers 2 and 3 on the tensor cores (implicit GEMM): for 128 consecutive pixels
+//   D[p][o] = sum_{t = 3a + b} sum_c h[nbr(p, a, b)][c] w[o][c][a][b],
+// a GEMM D[128 x 16] = A[128 x 144] B[16 x 144]^T with k = 16 t + c.  A is
+// gathered into shared memory (one 16-channel, 32-byte vector per pixel and
+// tap; zero outside the patch) in the 128-byte-swizzled K-major layout (taps
+// 0-3, 4-7 and 8 in three 64-wide chunks); B holds the weights in the same
+// layout (layer 3: rows 0-1, the rest zero).  Nine tcgen05.mma (kind::f16,
+// BF16 in, FP32 accumulator in tensor memory, M = 128, N = 16, K = 16 each),
+// one per tap.  Epilogue: layer 2 ReLU and BF16 rounding as the CUDA-core
+// layers; layer 3 the two output channels into y (stored or added).
+// Persistent: a CTA builds B and allocates tensor memory once and walks the
+// pixel tiles; each tile's MMAs complete on an mbarrier (bounded wait).
+namespace ctc {
+constexpr int TM = 128;
+constexpr int A_CHUNK = TM * 128;            // bytes of one 64-wide K chunk of A
+constexpr int B_CHUNK = 16 * 128;            // bytes of one 64-wide K chunk of B
+constexpr int SMEM = 3 * A_CHUNK + 3 * B_CHUNK + 1024 + 64;
+constexpr int CTAS_PER_SM = 4;
+constexpr long long WAIT_LIMIT = 1ll << 26;
+}  // namespace ctc
+
+__device__ __forceinline__ int c_sw128(int r, int c) { return (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4); }
+__device__ __forceinline__ uint32_t c_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t c_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// layer 3: h2 (16) -> y (2, FP32); mode 0: y = out, mode 1: y += out (u <- u + N(r))
-__global__ void k_conv3(Geom g, const __nv_bfloat16* __restrict__ h2, const __nv_bfloat16* __restrict__ w3,
-                        float2* __restrict__ y, int accumulate) {
-  __shared__ float ws[NP3];
-  for (int i = threadIdx.x; i < NP3; i += blockDim.x) ws[i] = __bfloat162float(w3[i]);
-  __syncthreads();
-  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= g.npix()) return;
-  float a0 = 0.f, a1 = 0.f;
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) {
-      long long q = nbr(g, p, a, b);
-      if (q < 0) continue;
-      const __nv_bfloat16* x = h2 + q * 16;
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        float xc = __bfloat162float(x[c]);
-        a0 = fmaf(ws[(0 * 16 + c) * 9 + a * 3 + b], xc, a0);
-        a1 = fmaf(ws[(1 * 16 + c) * 9 + a * 3 + b], xc, a1);
-      }
-    }
-  if (accumulate) {
-    float2 u = y[p];
-    y[p] = make_float2(u.x + a0, u.y + a1);
-  } else {
-    y[p] = make_float2(a0, a1);
+// LAYER 2: h -> out_h = bf16(relu(conv)) (16 channels); LAYER 3: h -> y (2
+// channels, FP32; accumulate: y += conv)
+template <int LAYER>
+__global__ void __launch_bounds__(128) k_conv_tc(Geom g, const __nv_bfloat16* __restrict__ h,
+                                                 const __nv_bfloat16* __restrict__ w,
+                                                 __nv_bfloat16* __restrict__ out_h, float2* __restrict__ y,
+                                                 int accumulate, int* __restrict__ err) {
+  constexpr int COUT = (LAYER == 2) ? 16 : 2;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (c_saddr(smem_raw) & 1023)) & 1023);
+  unsigned char* sA = base;
+  unsigned char* sB = base + 3 * ctc::A_CHUNK;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 3 * ctc::B_CHUNK);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sB + 3 * ctc::B_CHUNK + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long np = g.npix();
+  const long long ntiles = (np + ctc::TM - 1) / ctc::TM;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(c_saddr(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(c_saddr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // B: row o, k = 16 t + c  <-  w[(o 16 + c) 9 + t]; 8 values per 16-byte chunk
+  for (int q = tid; q < 16 * 24; q += blockDim.x) {
+    const int o = q / 24, kc = q % 24;          // kc: 16-byte chunk along k (18..23 padding)
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = kc * 8 + e, t = k >> 4, c = k & 15;
+      v[e] = (t < 9 && o < COUT) ? w[(o * 16 + c) * 9 + t] : __float2bfloat16(0.f);
+    }
+    *reinterpret_cast<uint4*>(sB + (kc >> 3) * ctc::B_CHUNK + c_sw128(o, kc & 7)) =
+        *reinterpret_cast<const uint4*>(v);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) |
+                         ((uint32_t)(ctc::TM >> 4) << 24);
+  uint32_t phase = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
+    const long long p0 = tile * ctc::TM;
+    // A: this thread's pixel row, all nine taps (32 bytes each)
+    {
+      const int r = tid;
+      const long long p = p0 + r;
+      const bool pv = p < np;
+      const Pix pc = pv ? pix_of(g, p) : Pix{0, 0};
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
+        const long long nq = pv ? nbr_at(g, pc, p, t / 3, t % 3) : -1;
+        if (nq >= 0) {
+          const uint4* src = reinterpret_cast<const uint4*>(h + nq * 16);
+          x0 = src[0];
+          x1 = src[1];
+        }
+        unsigned char* dst = sA + (t >> 2) * ctc::A_CHUNK;
+        const int c0 = (t & 3) * 2;
+        *reinterpret_cast<uint4*>(dst + c_sw128(r, c0)) = x0;
+        *reinterpret_cast<uint4*>(dst + c_sw128(r, c0 + 1)) = x1;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const uint64_t ad = c_desc(c_saddr(sA + (t >> 2) * ctc::A_CHUNK) + 32 * (t & 3));
+        const uint64_t bd = c_desc(c_saddr(sB + (t >> 2) * ctc::B_CHUNK) + 32 * (t & 3));
+        const uint32_t acc = t > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       c_saddr(mbar))
+                   : "memory");
+    }
+    bool done = false;
+    for (long long it = 0; it < ctc::WAIT_LIMIT && !done; ++it) {
+      uint32_t d;
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(d)
+          : "r"(c_saddr(mbar)), "r"(phase)
+          : "memory");
+      done = d != 0;
+    }
+    // one decision for the whole CTA (every thread polls the same barrier)
+    if (!__syncthreads_and(done ? 1 : 0)) {
+      if (tid == 0) atomicExch(err, 1);
+      // the MMAs may still be in flight: wait once more (bounded) before the
+      // tensor memory is freed
+      for (long long it = 0; it < ctc::WAIT_LIMIT; ++it) {
+        uint32_t d;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(d)
+            : "r"(c_saddr(mbar)), "r"(phase)
+            : "memory");
+        if (d) break;
+      }
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+      const long long p = p0 + 32 * warp + lane;
+      if constexpr (LAYER == 2) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (p < np) {
+          __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) o[j] = __float2bfloat16(fmaxf(__uint_as_float(v[j]), 0.f));
+          uint4* dst = reinterpret_cast<uint4*>(out_h + p * 16);
+          dst[0] = *reinterpret_cast<const uint4*>(o);
+          dst[1] = *reinterpret_cast<const uint4*>(o + 8);
+        }
+      } else {
+        uint32_t v[2];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+                     : "=r"(v[0]), "=r"(v[1])
+                     : "r"(tmem + ((uint32_t)(32 * warp) << 16)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (p < np) {
+          const float a0 = __uint_as_float(v[0]), a1 = __uint_as_float(v[1]);
+          if (accumulate) {
+            const float2 u = y[p];
+            y[p] = make_float2(u.x + a0, u.y + a1);
+          } else {
+            y[p] = make_float2(a0, a1);
+          }
+        }
+      }
+    }
+    // every thread is done with shared memory and tensor memory before the
+    // next tile is gathered and its MMAs overwrite the accumulator
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem));
 }
 
 // ---- loss: E = mask (r - A y); per-patch sums |E|^2 and |r|^2 over the mask
@@ -326,6 +472,7 @@ struct csff_net {
   double* sums = nullptr;
   int cap_b = 0;
   float2* cpatch = nullptr;
+  int* tcerr = nullptr;          // set when a tensor-core layer's wait ran out
 };
 
 namespace {
@@ -342,6 +489,7 @@ csff_status ninvalid(const char* s) {
 }
 
 csff_status ensure_scratch(csff_net* N, long long npix, int B, bool train) {
+  if (npix >= (1ll << 31)) return ninvalid("more than 2^31 pixels");
   if (npix > N->cap || (train && !N->dh1)) {
     for (void* p : {(void*)N->h1, (void*)N->h2, (void*)N->dh1, (void*)N->dh2, (void*)N->y, (void*)N->E,
                     (void*)N->G, (void*)N->dy})
@@ -381,8 +529,12 @@ csff_status forward(csff_net* N, csff::Geom g, const float2* r, float2* y, int a
   {
     ProfScope ps(PF_MG32, s, 8.0 * np + 2.0 * 32 * np + 8.0 * np, 2.0 * 9 * (2 * 16 + 16 * 16 + 16 * 2) * np);
     k_conv1<<<nblk(np), NTH, 0, s>>>(g, r, w1, N->h1);
-    k_conv2<<<nblk(np), NTH, 0, s>>>(g, N->h1, w2, N->h2);
-    k_conv3<<<nblk(np), NTH, 0, s>>>(g, N->h2, w3, y, accumulate);
+    NK(cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctc::SMEM), "conv attribute");
+    NK(cudaFuncSetAttribute(k_conv_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, ctc::SMEM), "conv attribute");
+    const long long tiles = (np + ctc::TM - 1) / ctc::TM;
+    const unsigned grid = (unsigned)std::min<long long>(tiles, 152 * ctc::CTAS_PER_SM);
+    k_conv_tc<2><<<grid, 128, ctc::SMEM, s>>>(g, N->h1, w2, N->h2, nullptr, 0, N->tcerr);
+    k_conv_tc<3><<<grid, 128, ctc::SMEM, s>>>(g, N->h2, w3, nullptr, y, accumulate, N->tcerr);
   }
   count_launch(3);
   NK(cudaGetLastError(), "net forward");
@@ -445,6 +597,8 @@ csff_status csff_net_create(const float* w_host, csff_net** out) {
       (e = cudaMalloc((void**)&N->v, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
       (e = cudaMalloc((void**)&N->grad, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
       (e = cudaMalloc((void**)&N->wb, sizeof(__nv_bfloat16) * csff::NPARAM)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->tcerr, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(N->tcerr, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(N->m, 0, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
       (e = cudaMemset(N->v, 0, sizeof(float) * csff::NPARAM)) != cudaSuccess)
     return fail(csff::cuda_fail(e, "net allocation"));
@@ -458,12 +612,14 @@ void csff_net_destroy(csff_net* N) {
   if (!N) return;
   for (void* p : {(void*)N->w, (void*)N->m, (void*)N->v, (void*)N->grad, (void*)N->wb, (void*)N->h1, (void*)N->h2,
                   (void*)N->dh1, (void*)N->dh2, (void*)N->y, (void*)N->E, (void*)N->G, (void*)N->dy,
-                  (void*)N->sums, (void*)N->cpatch})
+                  (void*)N->sums, (void*)N->cpatch, (void*)N->tcerr})
     if (p) cudaFree(p);
   delete N;
 }
 
 int csff_net_num_params(void) { return csff::NPARAM; }
+
+
 
 csff_status csff_net_set_weights(csff_net* N, const float* w_host) {
   if (!N || !w_host) return ninvalid("NULL argument");
@@ -490,7 +646,10 @@ csff_status csff_net_forward(csff_net* N, int B, int H, int W, const void* r_dev
   csff::Geom g{B, H, W};
   csff_status s = ensure_scratch(N, g.npix(), B, false);
   if (s != CSFF_OK) return s;
-  return forward(N, g, (const float2*)r_dev, (float2*)y_dev, 0, (cudaStream_t)stream);
+  s = forward(N, g, (const float2*)r_dev, (float2*)y_dev, 0, (cudaStream_t)stream);
+  if (s != CSFF_OK) return s;
+  NK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
+  return csff::net_check(N);
 }
 
 csff_status csff_net_loss_grad(csff_net* N, int B, int H, int W, const void* r_dev, const void* q_dev,
@@ -532,6 +691,19 @@ namespace csff {
 csff_status net_reserve(csff_net* N, long long npix) { return ensure_scratch(N, npix, 1, false); }
 
 // u <- u + N(b - A u) on level L (FP32), the learned step of the smoother
+// status of the tensor-core layer since the last check (synchronises)
+csff_status net_check(csff_net* N) {
+  int err = 0;
+  cudaError_t e = cudaMemcpy(&err, N->tcerr, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "net status");
+  if (err) {
+    cudaMemset(N->tcerr, 0, sizeof(int));
+    set_error("learned smoother: a tensor-core wait ran out");
+    return CSFF_ERR_TIMEOUT;
+  }
+  return CSFF_OK;
+}
+
 csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s) {
   csff_net* N = P->net;
   Geom g{1, L.m, L.m};
