@@ -158,29 +158,37 @@ __global__ void __launch_bounds__(128) k_conv_tc(Geom g, const __nv_bfloat16* __
   const uint32_t tmem = *tslot;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) |
                          ((uint32_t)(ctc::TM >> 4) << 24);
+  // A rows are gathered into registers one tile ahead: the loads of tile n+1
+  // are in flight while the tensor core and the epilogue work on tile n
+  uint4 xa[9][2];
+  auto gather = [&](long long tile) {
+    const long long p = tile * ctc::TM + tid;
+    const bool pv = tile < ntiles && p < np;
+    const Pix pc = pv ? pix_of(g, p) : Pix{0, 0};
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const long long nq = pv ? nbr_at(g, pc, p, t / 3, t % 3) : -1;
+      if (nq >= 0) {
+        const uint4* src = reinterpret_cast<const uint4*>(h + nq * 16);
+        xa[t][0] = src[0];
+        xa[t][1] = src[1];
+      } else {
+        xa[t][0] = make_uint4(0, 0, 0, 0);
+        xa[t][1] = make_uint4(0, 0, 0, 0);
+      }
+    }
+  };
+  gather(blockIdx.x);
   uint32_t phase = 0;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, phase ^= 1u) {
     const long long p0 = tile * ctc::TM;
     // A: this thread's pixel row, all nine taps (32 bytes each)
-    {
-      const int r = tid;
-      const long long p = p0 + r;
-      const bool pv = p < np;
-      const Pix pc = pv ? pix_of(g, p) : Pix{0, 0};
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
-        const long long nq = pv ? nbr_at(g, pc, p, t / 3, t % 3) : -1;
-        if (nq >= 0) {
-          const uint4* src = reinterpret_cast<const uint4*>(h + nq * 16);
-          x0 = src[0];
-          x1 = src[1];
-        }
-        unsigned char* dst = sA + (t >> 2) * ctc::A_CHUNK;
-        const int c0 = (t & 3) * 2;
-        *reinterpret_cast<uint4*>(dst + c_sw128(r, c0)) = x0;
-        *reinterpret_cast<uint4*>(dst + c_sw128(r, c0 + 1)) = x1;
-      }
+    for (int t = 0; t < 9; ++t) {
+      unsigned char* dst = sA + (t >> 2) * ctc::A_CHUNK;
+      const int c0 = (t & 3) * 2;
+      *reinterpret_cast<uint4*>(dst + c_sw128(tid, c0)) = xa[t][0];
+      *reinterpret_cast<uint4*>(dst + c_sw128(tid, c0 + 1)) = xa[t][1];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -201,6 +209,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(Geom g, const __nv_bfloat16* __
                        c_saddr(mbar))
                    : "memory");
     }
+    gather(tile + gridDim.x);
     bool done = false;
     for (long long it = 0; it < ctc::WAIT_LIMIT && !done; ++it) {
       uint32_t d;
