@@ -375,7 +375,7 @@ def measure_variants(csff, torch, dev, stream, flush):
     # ---- 64 uneven instances
     bc = W.batch_2d(64, seed=4461)
     for c in bc:
-        c["opts"].update(precision="mixed", inner_cycles=3, coarsest_n=5)
+        c["opts"].update(precision="mixed", inner_cycles=INNER_CYCLES, coarsest_n=5)
     eta = np.vstack([c["eta"] for c in bc])
     al = [c["alphas"] for c in bc]
     b = csff.Batch([c["problem"] for c in bc], bc[0]["opts"], stream=stream)
