@@ -516,14 +516,16 @@ def measure_learned(csff, torch, dev, stream, flush):
 
         step()
         ms = _time_events(torch, stream, step, flush, 2)
-        maps[name] = F.cpu().numpy() * 2.0 ** Fe.cpu().numpy().astype(np.float64)
+        maps[name] = (F.cpu().numpy(), Fe.cpu().numpy().astype(np.int64))
         out[name] = {"value": 1.0 / (ms / 1e3), "unit": UNIT, "ms_per_map": ms, "cycles": info["inf"]["cycles"],
                      "rel_res": info["inf"]["rel_res"], "flags": info["inf"]["flags"]}
-    # both solves reach 1e-8; the learned map against the classical one (the
-    # FP64-class far field of each solution; the oracle is pinned to that path
-    # on smaller grids)
-    out["far_field_rel_l2_learned_vs_classical"] = float(
-        np.linalg.norm(maps["learned"] - maps["classical"]) / np.linalg.norm(maps["classical"]))
+    # both solves reach 1e-8; the learned map against the classical one, angle
+    # by angle (mantissa and power-of-two exponent, since the map's terms pass
+    # the FP64 range at this k; the oracle is pinned to this far-field path on
+    # smaller grids)
+    (f0, e0), (f1, e1) = maps["classical"], maps["learned"]
+    d = np.abs(f1 * 2.0 ** (e1 - e0).astype(np.float64) - f0) / np.abs(f0)
+    out["far_field_learned_vs_classical"] = {"median_rel_diff": float(np.median(d)), "max_rel_diff": float(d.max())}
     out["cycle_ratio_learned_vs_classical"] = out["learned"]["cycles"] / max(1, out["classical"]["cycles"])
     out["speedup_learned_vs_classical"] = out["classical"]["ms_per_map"] / out["learned"]["ms_per_map"]
     plan.close()
