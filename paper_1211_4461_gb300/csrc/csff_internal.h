@@ -92,8 +92,9 @@ struct FFBuffers {
   double *dal = nullptr, *dux = nullptr;
   int *dxr = nullptr, *ds1 = nullptr, *dmisc = nullptr;
   // double-float stage 1: split operands, block exponents, spread flags [2]
-  size_t xdf = 0, gdf = 0, exs = 0, egs = 0;
+  size_t xdf = 0, gdf = 0, exs = 0, egs = 0, xsm = 0, gsm = 0;
   float4 *dxdf = nullptr, *dgdf = nullptr;
+  float2 *dxsm = nullptr, *dgsm = nullptr;   // re + im of the split operands
   int *dex = nullptr, *deg = nullptr, *dspread = nullptr;
   // tensor-core 3D stage A: pre-swizzled split phase operand, per-column and
   // per-row exponents, [spread_g, spread_P, error word]

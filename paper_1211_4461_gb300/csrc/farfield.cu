@@ -300,7 +300,7 @@ __device__ __forceinline__ int ilog2_up(double a) {   // exponent e with a < 2^e
 // one warp per (row, block): block exponent of |v| (upper bound), scaled
 // double-float split, and the row-block spread (max - min exponent) into *spread
 __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, float4* __restrict__ vdf,
-                             int* __restrict__ ev, int* __restrict__ spread) {
+                             float2* __restrict__ vsum, int* __restrict__ ev, int* __restrict__ spread) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nb = (m + DKB - 1) / DKB;
   if (warp >= nrows * nb) return;
@@ -323,8 +323,11 @@ __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, fl
   }
   // ldexp on the value itself: 2^-eb alone overflows for subnormal blocks
   const bool zero = e == -100000 || bad;
-  df re = df_of(zero ? 0.0 : ldexp(x.x, -eb)), im = df_of(zero ? 0.0 : ldexp(x.y, -eb));
-  vdf[(long long)row * nb * DKB + b * DKB + lane] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  const double xr = zero ? 0.0 : ldexp(x.x, -eb), xi = zero ? 0.0 : ldexp(x.y, -eb);
+  df re = df_of(xr), im = df_of(xi), sm = df_of(xr + xi);
+  const long long o = (long long)row * nb * DKB + b * DKB + lane;
+  vdf[o] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  vsum[o] = make_float2(sm.hi, sm.lo);      // re + im for Gauss's three-product complex multiply
 }
 
 // 2^d as a float for d <= 0 (0 below the subnormal range): exact power of two
@@ -357,58 +360,92 @@ __device__ __forceinline__ void dfacc_merge2(dfacc& re, dfacc& im, df sr, df si,
   add(im, si);
 }
 
+__device__ __forceinline__ void dfacc_merge3(dfacc& a1, dfacc& a2, dfacc& a3, df s1, df s2, df s3, int Es) {
+  if (s1.hi == 0.f && s2.hi == 0.f && s3.hi == 0.f && s1.lo == 0.f && s2.lo == 0.f && s3.lo == 0.f) return;
+  const int En = max(a1.E, Es);                    // the three share one exponent
+  const float fa = pow2f_neg(a1.E - En), fs = pow2f_neg(Es - En);
+  auto add = [&](dfacc& a, df x) {
+    float ah = a.hi * fa, al = a.lo * fa, xh = x.hi * fs, xl = x.lo * fs;
+    float t = ah + xh, v = t - ah;
+    float err = (ah - (t - v)) + (xh - v);
+    float lo = al + xl + err;
+    float h = t + lo;                              // renormalise (fast TwoSum)
+    a.lo = lo - (h - t);
+    a.hi = h;
+    a.E = En;
+  };
+  add(a1, s1);
+  add(a2, s2);
+  add(a3, s3);
+}
+
 // T[k][rho] over blocks; 16 (k) x 16 DF_J (rho) output tile, 1 x DF_J outputs per thread (small
 // tiles: the 736 CTAs of the 1025^2 maps spread over the 152 SMs more evenly than 368 larger ones)
 constexpr int DF_J = 2;                       // outputs per thread along rho
 constexpr int DF_BM = 16, DF_BN = 16 * DF_J;
 
-__global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__ X, const int* __restrict__ ex, int M,
-                                                      const float4* __restrict__ G, const int* __restrict__ eg, int N,
-                                                      int nb, const int* __restrict__ spread,
-                                                      double2* __restrict__ T) {
+// Complex products by Gauss's three multiplications: with p1 = ar br,
+// p2 = ai bi, p3 = (ar + ai)(br + bi) summed separately, Re = S1 - S2 and
+// Im = S3 - S1 - S2 (formed in FP64 at the end).  Three double-float
+// multiply-adds per complex term instead of four; the rounding of each sum
+// stays relative to the sum of its terms' magnitudes, all bounded by
+// (|ar| + |ai|)(|br| + |bi|), so the error is still double-float-small
+// against the sum of the terms' magnitudes.
+__global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__ X, const float2* __restrict__ Xs,
+                                                      const int* __restrict__ ex, int M,
+                                                      const float4* __restrict__ G, const float2* __restrict__ Gs,
+                                                      const int* __restrict__ eg, int N, int nb,
+                                                      const int* __restrict__ spread, double2* __restrict__ T) {
   if (!df_selected(spread)) return;      // the FP64 kernel takes this launch
   __shared__ float4 As[DF_BM][DKB + 1];
+  __shared__ float2 As2[DF_BM][DKB + 1];
   __shared__ float4 Bs[DF_BN][DKB + 1];
+  __shared__ float2 Bs2[DF_BN][DKB + 1];
   __shared__ int eA[DF_BM], eB[DF_BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
-  dfacc accr[DF_J], acci[DF_J];
+  dfacc acc1[DF_J], acc2[DF_J], acc3[DF_J];
 #pragma unroll
   for (int j = 0; j < DF_J; ++j) {
-    accr[j] = dfacc{0.f, 0.f, -100000};
-    acci[j] = dfacc{0.f, 0.f, -100000};
+    acc1[j] = dfacc{0.f, 0.f, -100000};
+    acc2[j] = dfacc{0.f, 0.f, -100000};
+    acc3[j] = dfacc{0.f, 0.f, -100000};
   }
   for (int b = 0; b < nb; ++b) {
     for (int i = tid; i < DF_BM * DKB; i += 256) {
       int r = i / DKB, kk = i % DKB, gm = m0 + r;
-      As[r][kk] = (gm < M) ? X[((long long)gm * nb + b) * DKB + kk] : make_float4(0, 0, 0, 0);
+      const long long o = ((long long)gm * nb + b) * DKB + kk;
+      As[r][kk] = (gm < M) ? X[o] : make_float4(0, 0, 0, 0);
+      As2[r][kk] = (gm < M) ? Xs[o] : make_float2(0, 0);
     }
     for (int i = tid; i < DF_BN * DKB; i += 256) {
       int r = i / DKB, kk = i % DKB, gn = n0 + r;
-      Bs[r][kk] = (gn < N) ? G[((long long)gn * nb + b) * DKB + kk] : make_float4(0, 0, 0, 0);
+      const long long o = ((long long)gn * nb + b) * DKB + kk;
+      Bs[r][kk] = (gn < N) ? G[o] : make_float4(0, 0, 0, 0);
+      Bs2[r][kk] = (gn < N) ? Gs[o] : make_float2(0, 0);
     }
     if (tid < DF_BM) eA[tid] = (m0 + tid < M) ? ex[(long long)(m0 + tid) * nb + b] : 0;
     if (tid >= 64 && tid < 64 + DF_BN) eB[tid - 64] = (n0 + tid - 64 < N) ? eg[(long long)(n0 + tid - 64) * nb + b] : 0;
     __syncthreads();
-    df sr[DF_J], si[DF_J];
+    df s1[DF_J], s2[DF_J], s3[DF_J];
 #pragma unroll
-    for (int j = 0; j < DF_J; ++j) { sr[j] = df{0.f, 0.f}; si[j] = df{0.f, 0.f}; }
+    for (int j = 0; j < DF_J; ++j) { s1[j] = df{0.f, 0.f}; s2[j] = df{0.f, 0.f}; s3[j] = df{0.f, 0.f}; }
 #pragma unroll 2
     for (int kk = 0; kk < DKB; ++kk) {
-      float4 a = As[ty][kk];
-      df ar{a.x, a.y}, ai{a.z, a.w}, nai{-a.z, -a.w};
+      const float4 a = As[ty][kk];
+      const float2 a2 = As2[ty][kk];
+      const df ar{a.x, a.y}, ai{a.z, a.w}, as{a2.x, a2.y};
 #pragma unroll
       for (int j = 0; j < DF_J; ++j) {
-        float4 bb = Bs[tx + 16 * j][kk];
-        df br{bb.x, bb.y}, bi{bb.z, bb.w};
-        df_mac(sr[j], ar, br);
-        df_mac(sr[j], nai, bi);
-        df_mac(si[j], ar, bi);
-        df_mac(si[j], ai, br);
+        const float4 bb = Bs[tx + 16 * j][kk];
+        const float2 b2 = Bs2[tx + 16 * j][kk];
+        df_mac(s1[j], ar, df{bb.x, bb.y});
+        df_mac(s2[j], ai, df{bb.z, bb.w});
+        df_mac(s3[j], as, df{b2.x, b2.y});
       }
     }
 #pragma unroll
-    for (int j = 0; j < DF_J; ++j) dfacc_merge2(accr[j], acci[j], sr[j], si[j], eA[ty] + eB[tx + 16 * j]);
+    for (int j = 0; j < DF_J; ++j) dfacc_merge3(acc1[j], acc2[j], acc3[j], s1[j], s2[j], s3[j], eA[ty] + eB[tx + 16 * j]);
     __syncthreads();
   }
   const int gm = m0 + ty;
@@ -417,8 +454,9 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
   for (int j = 0; j < DF_J; ++j) {
     const int gn = n0 + tx + 16 * j;
     if (gn >= N) continue;
-    T[(long long)gm * N + gn] = make_double2(ldexp((double)accr[j].hi + (double)accr[j].lo, accr[j].E),
-                                             ldexp((double)acci[j].hi + (double)acci[j].lo, acci[j].E));
+    const double S1 = (double)acc1[j].hi + (double)acc1[j].lo, S2 = (double)acc2[j].hi + (double)acc2[j].lo;
+    const double S3 = (double)acc3[j].hi + (double)acc3[j].lo;
+    T[(long long)gm * N + gn] = make_double2(ldexp(S1 - S2, acc1[j].E), ldexp(S3 - S1 - S2, acc1[j].E));
   }
 }
 
@@ -839,7 +877,7 @@ static cudaError_t ensure(void** p, size_t& cap, size_t need, csff_plan* P) {
 void free_ff_buffers(csff_plan* P) {
   FFBuffers& b = P->ff;
   for (void* p : {(void*)b.dg, (void*)b.dxt, (void*)b.dyt, (void*)b.dzt, (void*)b.dT, (void*)b.dal,
-                  (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc, (void*)b.dxdf, (void*)b.dgdf,
+                  (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc, (void*)b.dxdf, (void*)b.dgdf, (void*)b.dxsm, (void*)b.dgsm,
                   (void*)b.dex, (void*)b.deg, (void*)b.dspread, (void*)b.dtcb, (void*)b.dtce, (void*)b.dtcflag})
     if (p) cudaFree(p);
   b = FFBuffers{};
@@ -1039,6 +1077,8 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   const int nbk = (m + DKB - 1) / DKB;
   if ((e = ensure((void**)&B.dxdf, B.xdf, sizeof(float4) * (size_t)n_ux * nbk * DKB, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dgdf, B.gdf, sizeof(float4) * (size_t)R * nbk * DKB, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dxsm, B.xsm, sizeof(float2) * (size_t)n_ux * nbk * DKB, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dgsm, B.gsm, sizeof(float2) * (size_t)R * nbk * DKB, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dex, B.exs, sizeof(int) * (size_t)n_ux * nbk, P)) != cudaSuccess ||
       (e = ensure((void**)&B.deg, B.egs, sizeof(int) * (size_t)R * nbk, P)) != cudaSuccess)
     return cuda_fail(e, "far field scratch");
@@ -1047,8 +1087,10 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   if ((e = cudaMemsetAsync(B.dspread, 0, 2 * sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
   {
     const long long wx = (long long)n_ux * nbk, wg = (long long)R * nbk;
-    k_split_rows<<<(unsigned)((wx * 32 + 255) / 256), 256, 0, s>>>(B.dxt, m, n_ux, B.dxdf, B.dex, B.dspread);
-    k_split_rows<<<(unsigned)((wg * 32 + 255) / 256), 256, 0, s>>>(B.dg, m, (int)R, B.dgdf, B.deg, B.dspread + 1);
+    k_split_rows<<<(unsigned)((wx * 32 + 255) / 256), 256, 0, s>>>(B.dxt, m, n_ux, B.dxdf, B.dxsm, B.dex,
+                                                                   B.dspread);
+    k_split_rows<<<(unsigned)((wg * 32 + 255) / 256), 256, 0, s>>>(B.dg, m, (int)R, B.dgdf, B.dgsm, B.deg,
+                                                                   B.dspread + 1);
     count_launch(2);
   }
   dim3 g1((unsigned)((R + S1_BN - 1) / S1_BN), (n_ux + S1_BM - 1) / S1_BM);
@@ -1057,7 +1099,8 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
     ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_ux * m + (double)R * m + (double)n_ux * R),
                  8.0 * (double)n_ux * (double)R * m);
     // exactly one of the two writes T (device-side range check on the spreads)
-    k_ff_stage1_df<<<gdf, 256, 0, s>>>(B.dxdf, B.dex, n_ux, B.dgdf, B.deg, (int)R, nbk, B.dspread, B.dT);
+    k_ff_stage1_df<<<gdf, 256, 0, s>>>(B.dxdf, B.dxsm, B.dex, n_ux, B.dgdf, B.dgsm, B.deg, (int)R, nbk, B.dspread,
+                                       B.dT);
     k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT, B.dspread);
   }
   count_launch(2);
