@@ -47,17 +47,18 @@ def _peaks():
 # (0.599e12 DFMA/s over 152 SMs; 2 flops per FMA).
 FP64_PEAK_TFLOPS = 1.198
 # FP32 instruction rate derived from unit counts and clock: 152 SMs x 128 FP32
-# lanes x 2.07 GHz.  The double-float contraction spends 48 FP32 instructions
-# (4 double-float multiply-adds of 12) per complex multiply-add, i.e. 6 per
-# FP64-equivalent flop, so its arithmetic ceiling in FP64-equivalent flops is
-# that rate / 6.
+# lanes x 2.07 GHz.  The double-float contraction spends 36 FP32 instructions
+# (three double-float multiply-adds of 12, Gauss's complex product) per complex
+# multiply-add, i.e. 4.5 per FP64-equivalent flop (8 per complex
+# multiply-add), so its arithmetic ceiling in FP64-equivalent flops is that
+# rate / 4.5.
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
-DF_INSTR_PER_FLOP = 6.0
+DF_INSTR_PER_FLOP = 36.0 / 8.0
 DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 # DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload, from
 # the ncu capture summarised in profiles/ff_stage1_df_2d_n1025.md (None once
 # the kernel changes).
-FF_DF_DRAM_BYTES = 22876160
+FF_DF_DRAM_BYTES = 34205696 + 18944
 
 
 # FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of
@@ -297,8 +298,9 @@ def run_ours(args, rank, world, local_rank):
     roofline = {"kernel": "k_ff_stage1_df (double-float far-field contraction)", "bound": "alu",
                 "achieved": achieved_tf, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / DF_PEAK_TFLOPS, "traffic": FF_DF_DRAM_BYTES,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 6 FP32 instructions per "
-                               "FP64-equivalent flop (48 per complex multiply-add in double-float)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 4.5 FP32 instructions per "
+                               "FP64-equivalent flop (36 per complex multiply-add: three double-float "
+                               "multiply-adds, Gauss's product)",
                 "avg_launch_ms": ff_avg_ms, "launches": ff["launches"],
                 "alg_flops_per_launch": ff_flops}
     mg32, mg64 = breakdown["mg32"], breakdown["mg64"]
