@@ -420,6 +420,7 @@ def measure_variants(csff, torch, dev, stream, flush):
         p.close()
     del su
     out["3d_257_16dirs"] = measure_3d(csff, torch, dev, stream, flush)
+    out["vcycle_4097"] = measure_vcycle_bandwidth(csff, torch, dev, stream, flush)
     out["learned_2049"] = measure_learned(csff, torch, dev, stream, flush)
     return out
 
@@ -470,6 +471,38 @@ def measure_3d(csff, torch, dev, stream, flush):
                                 "maps_below_1e-5": int((rel <= 1e-5).sum())}
     out["step_ms_with_tc_far_field"] = ms - out["ff_fp64_ms_per_16_maps"] + out["ff_tc_bf16x3_ms_per_16_maps"]
     plan.set_far_field_mode(csff.FF_FP64)
+    plan.close()
+    return out
+
+
+def measure_vcycle_bandwidth(csff, torch, dev, stream, flush):
+    """Fused V(1,1) cycles on a grid whose FP32 arrays exceed the 129 MB L2
+    (4097^2 on [-20,20]^2, k = 40, 10 levels, 9^2 coarsest; 134 MB per FP32
+    array): algorithmic bytes of the multigrid kernels (u and b read and u
+    written per tile pass, plus the next level's right-hand side) over their
+    CUDA-event time, against the measured HBM copy bandwidth; the same for
+    the FP64 cycle."""
+    c = W.mixed_2d(40.0, n=4097)
+    c["opts"].update(coarsest_n=9, precision="mixed")
+    plan = csff.Plan(c["problem"], c["opts"], stream=stream)
+    out = {"grid": "4097^2, 10 levels", "fp32_array_mb": plan.N * 8 / 1e6}
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    for name, dt, mask in (("fp32", torch.complex64, csff.PROF_MG32), ("fp64", torch.complex128, csff.PROF_MG64)):
+        u = torch.zeros(plan.N, dtype=dt, device=dev)
+        b = torch.randn(plan.N, dtype=dt, device=dev)
+        plan.vcycle(u, b)
+        torch.cuda.synchronize()
+        reps = 10 if name == "fp32" else 3
+        csff.prof_begin(mask)
+        for _ in range(reps):
+            plan.vcycle(u, b)
+        torch.cuda.synchronize()
+        st = csff.prof_end()["mg32" if name == "fp32" else "mg64"]
+        gbs = st["alg_bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else 0.0
+        out[name] = {"ms_per_cycle": st["ms"] / reps, "alg_gb_per_cycle": st["alg_bytes"] / reps / 1e9,
+                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+        del u, b
     plan.close()
     return out
 

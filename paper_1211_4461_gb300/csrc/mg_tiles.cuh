@@ -96,6 +96,18 @@ __device__ __forceinline__ float2 crecip(float2 d) {
   return make_float2(__fmul_rn(d.x, r), -__fmul_rn(d.y, r));
 }
 
+// Asynchronous global -> shared copy of BYTES (4, 8 or 16), zero-filled when
+// !valid (no bytes are read then).  Per-level kernels only: data written by
+// other CTAs of the same launch (the persistent kernel) is read through L2.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void* smem_dst, const void* gsrc, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(gsrc), "n"(BYTES),
+               "r"(valid ? BYTES : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Window of W x W fine points with origin (ox, oy): iterate -> U, RHS -> B,
 // and the coefficient windows (FP32: X_g, Y_g along the two axes; FP64: 1/d).
 // Points outside the interior are zero.
@@ -104,14 +116,28 @@ __device__ __forceinline__ void load_window(int ox, int oy, int W, int m, const 
                                             const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
                                             cx<T>* X) {
   const bool inner = ox >= 0 && oy >= 0 && ox + W <= m && oy + W <= m;
-  for (int i = threadIdx.x; i < W * W; i += NT) {
-    const int wy = i / W, wx = i - wy * W;
-    const int fx = ox + wx, fy = oy + wy;
-    const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
-    const long long g = (long long)fy * m + fx;
-    U[i] = (in && !zero_u) ? ld<COH>(u_in + g) : zero_c<T>();
-    B[i] = in ? ld<COH>(b + g) : zero_c<T>();
-    if constexpr (!formed_coef<T>()) X[i] = in ? K.dinv[g] : zero_c<T>();
+  if constexpr (COH) {
+    for (int i = threadIdx.x; i < W * W; i += NT) {
+      const int wy = i / W, wx = i - wy * W;
+      const int fx = ox + wx, fy = oy + wy;
+      const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
+      const long long g = (long long)fy * m + fx;
+      U[i] = (in && !zero_u) ? ld<COH>(u_in + g) : zero_c<T>();
+      B[i] = in ? ld<COH>(b + g) : zero_c<T>();
+      if constexpr (!formed_coef<T>()) X[i] = in ? K.dinv[g] : zero_c<T>();
+    }
+  } else {
+    // every copy of this thread in flight at once (one round trip per tile)
+    for (int i = threadIdx.x; i < W * W; i += NT) {
+      const int wy = i / W, wx = i - wy * W;
+      const int fx = ox + wx, fy = oy + wy;
+      const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
+      const long long g = in ? (long long)fy * m + fx : 0;
+      if (zero_u) U[i] = zero_c<T>();
+      else cp_async_zfill<sizeof(cx<T>)>(U + i, u_in + g, in);
+      cp_async_zfill<sizeof(cx<T>)>(B + i, b + g, in);
+      if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + i, K.dinv + g, in);
+    }
   }
   if constexpr (formed_coef<T>()) {
     cx<T>* FY = X + K.ng * W;
@@ -122,6 +148,7 @@ __device__ __forceinline__ void load_window(int ox, int oy, int W, int m, const 
       FY[i] = (fy >= 0 && fy < m) ? K.fac[((size_t)g * 2 + 1) * m + fy] : zero_c<T>();
     }
   }
+  if constexpr (!COH) cp_async_wait_all();
 }
 
 // d = 4c - q at window point (wx, wy) from the factor windows
