@@ -3,6 +3,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -48,11 +49,15 @@ struct ProfState {
 ProfState g_prof;
 }  // namespace
 
-bool g_capturing = false;
+thread_local bool g_capturing = false;   // this thread is capturing a graph (plans may run on several threads)
 unsigned prof_mask() { return g_prof.mask; }
+
+// the record list is shared by every thread that launches while profiling is on
+std::mutex g_prof_mu;
 
 ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops) : stream(s) {
   if (g_capturing || !(g_prof.mask & (1u << family))) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
   ProfRec r{family, g_prof.get(), g_prof.get(), bytes, flops};
   if (!r.a || !r.b) return;
   cudaEventRecord(r.a, s);
@@ -61,7 +66,9 @@ ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops) : s
 }
 
 ProfScope::~ProfScope() {
-  if (slot >= 0) cudaEventRecord(g_prof.recs[slot].b, stream);
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_prof.recs[slot].b, stream);
 }
 
 }  // namespace csff

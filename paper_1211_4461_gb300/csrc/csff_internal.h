@@ -213,7 +213,7 @@ cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, 
 // dynamic shared-memory opt-in of the fused kernels on the current device
 cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc);
 // true while a graph is being captured (profiling brackets are suppressed)
-extern bool g_capturing;
+extern thread_local bool g_capturing;
 // kernel families currently timed (csff_prof_begin mask)
 unsigned prof_mask();
 
