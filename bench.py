@@ -19,6 +19,7 @@ import math
 import os
 import statistics
 import subprocess
+import threading
 import sys
 import time
 
@@ -82,7 +83,8 @@ def _config(args, extra=None):
     cfg = {"workload": WORKLOAD, "maps_per_step": len(KS), "n": 1025, "levels": 8, "angles": 720,
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
            "inner_cycles": INNER_CYCLES if args.precision == "mixed" else None,
-           "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+           "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
+           "concurrency": "the maps of a step solved concurrently: one host thread and one CUDA stream per map"}
     if extra:
         cfg.update(extra)
     return cfg
@@ -193,8 +195,11 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     ks = tuple(float(k) for k in args.ks.split(",")) if args.ks else KS
     cases = _cases(args.precision, ks)
+    # one stream and one host thread per map: the four solves are independent
+    # and each alone leaves most SMs idle on its coarse levels
+    streams = [torch.cuda.Stream(device=dev) for _ in cases]
     t0 = time.perf_counter()
-    plans = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in cases]
+    plans = [csff.Plan(c["problem"], c["opts"], stream=st) for c, st in zip(cases, streams)]
     torch.cuda.synchronize()
     plan_ms = (time.perf_counter() - t0) * 1e3
     N = plans[0].N
@@ -209,8 +214,9 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     infos = {}
 
-    def step(e2e=False):
-        for i, (p, c) in enumerate(zip(plans, cases)):
+    def one_map(i, e2e):
+        p, c = plans[i], cases[i]
+        with torch.cuda.stream(streams[i]):
             eta = eta_h[i].numpy() if e2e else c["eta"]
             al = al_h[i].numpy() if e2e else c["alphas"]
             st, info = p.solve(eta, us[i], ok=(csff.OK,))
@@ -219,8 +225,25 @@ def run_ours(args, rank, world, local_rank):
             if e2e:
                 F_h[i].copy_(Fs[i], non_blocking=True)
                 Fe_h[i].copy_(Fe[i], non_blocking=True)
+
+    def step(e2e=False, concurrent=True):
+        start = torch.cuda.Event()
+        start.record(stream)
+        for st in streams:
+            st.wait_event(start)
+        if concurrent:
+            th = [threading.Thread(target=one_map, args=(i, e2e)) for i in range(len(plans))]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+        else:
+            for i in range(len(plans)):
+                one_map(i, e2e)
+        for st in streams:
+            stream.wait_stream(st)
         if e2e:
-            torch.cuda.current_stream().synchronize()
+            stream.synchronize()
 
     for _ in range(args.warmup):
         step()
@@ -231,7 +254,6 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = csff.kernel_launches()
-    csff.prof_begin(csff.PROF_FF_CONTRACT)
     step_ms = []
     with ClockSampler(local_rank) as clk:
         for _ in range(args.steps):
@@ -244,7 +266,6 @@ def run_ours(args, rank, world, local_rank):
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
-    prof_timed = csff.prof_end()
     launches = csff.kernel_launches() - launches0
     if dist:
         dist.barrier()
@@ -255,14 +276,23 @@ def run_ours(args, rank, world, local_rank):
         total_ms = float(t.item())
     value = len(cases) * args.steps * world / (total_ms / 1e3)
 
-    # ---- per-family breakdown (one extra profiled step) -----------------------
+    # ---- the dominant kernel alone: one sequential step timing only the
+    # far-field contraction launches (CUDA events on each launch's stream) ----
+    flush.zero_()
+    torch.cuda.synchronize()
+    csff.prof_begin(csff.PROF_FF_CONTRACT)
+    step(concurrent=False)
+    torch.cuda.synchronize()
+    prof_timed = csff.prof_end()
+
+    # ---- per-family breakdown (one extra sequential profiled step) ----------
     flush.zero_()
     torch.cuda.synchronize()
     csff.prof_begin(csff.PROF_FF_CONTRACT | csff.PROF_MG32 | csff.PROF_MG64)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    step()
+    step(concurrent=False)
     e1.record(stream)
     torch.cuda.synchronize()
     breakdown = csff.prof_end()
@@ -354,18 +384,34 @@ def measure_variants(csff, torch, dev, stream, flush):
     solved one after the other through the single-problem mixed path."""
     out = {}
     cases = _cases("fp64")
-    plans = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in cases]
+    streams = [torch.cuda.Stream(device=dev) for _ in cases]
+    plans = [csff.Plan(c["problem"], c["opts"], stream=st) for c, st in zip(cases, streams)]
     N = plans[0].N
     us = [torch.zeros(N, dtype=torch.complex128, device=dev) for _ in cases]
     Fs = [torch.zeros(720, dtype=torch.complex128, device=dev) for _ in cases]
     Fe = [torch.zeros(720, dtype=torch.int32, device=dev) for _ in cases]
     cyc = {}
 
-    def step64():
-        for i, (p, c) in enumerate(zip(plans, cases)):
+    def one64(i):
+        p, c = plans[i], cases[i]
+        with torch.cuda.stream(streams[i]):
             _, info = p.solve(c["eta"], us[i])
             cyc[i] = info[0]["cycles"]
             p.far_field(c["eta"], us[i], c["alphas"], Fs[i], Fe[i])
+
+    def step64():
+        # scheduled as the headline step: one host thread and stream per map
+        start = torch.cuda.Event()
+        start.record(stream)
+        for st in streams:
+            st.wait_event(start)
+        th = [threading.Thread(target=one64, args=(i,)) for i in range(len(plans))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for st in streams:
+            stream.wait_stream(st)
 
     step64()
     ms = _time_events(torch, stream, step64, flush, 2)
