@@ -84,7 +84,8 @@ def _config(args, extra=None):
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
            "inner_cycles": INNER_CYCLES if args.precision == "mixed" else None,
            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
-           "concurrency": "the maps of a step solved concurrently: one host thread and one CUDA stream per map"}
+           "concurrency": ("the maps of a step solved one after another" if args.sequential else
+                           "the maps of a step solved concurrently: one host thread and one CUDA stream per map")}
     if extra:
         cfg.update(extra)
     return cfg
@@ -226,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
                 F_h[i].copy_(Fs[i], non_blocking=True)
                 Fe_h[i].copy_(Fe[i], non_blocking=True)
 
-    def step(e2e=False, concurrent=True):
+    def step(e2e=False, concurrent=not args.sequential):
         start = torch.cuda.Event()
         start.record(stream)
         for st in streams:
@@ -663,6 +664,9 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the plain-FP64 and batched comparison runs")
     ap.add_argument("--ks", default="", help="comma-separated subset of the wavenumbers (profiling runs)")
+    ap.add_argument("--sequential", action="store_true",
+                    help="solve the maps of a step one after another on one host thread (for profilers, "
+                         "which serialise kernels anyway and do not follow several capturing threads)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
