@@ -551,6 +551,27 @@ def measure_vcycle_bandwidth(csff, torch, dev, stream, flush):
                      "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
         del u, b
     plan.close()
+    # the 3D workload's grid (257^3, 66 MB per FP32 array): per-level kernels
+    c3 = W.big_3d(n=257, n_rhs=1)
+    c3["opts"]["precision"] = "mixed"
+    p3 = csff.Plan(c3["problem"], c3["opts"], stream=stream)
+    for name, dt, mask in (("fp32_3d_257", torch.complex64, csff.PROF_MG32),
+                           ("fp64_3d_257", torch.complex128, csff.PROF_MG64)):
+        u = torch.zeros(p3.N, dtype=dt, device=dev)
+        b = torch.randn(p3.N, dtype=dt, device=dev)
+        p3.vcycle(u, b)
+        torch.cuda.synchronize()
+        reps = 5
+        csff.prof_begin(mask)
+        for _ in range(reps):
+            p3.vcycle(u, b)
+        torch.cuda.synchronize()
+        st = csff.prof_end()["mg32" if "fp32" in name else "mg64"]
+        gbs = st["alg_bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else 0.0
+        out[name] = {"ms_per_cycle": st["ms"] / reps, "alg_gb_per_cycle": st["alg_bytes"] / reps / 1e9,
+                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+        del u, b
+    p3.close()
     return out
 
 
