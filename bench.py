@@ -59,7 +59,7 @@ DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 # DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload, from
 # the ncu capture summarised in profiles/ff_stage1_df_2d_n1025.md (None once
 # the kernel changes).
-FF_DF_DRAM_BYTES = 34205696 + 18944
+FF_DF_DRAM_BYTES = None
 
 
 # FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of

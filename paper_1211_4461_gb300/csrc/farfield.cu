@@ -379,10 +379,10 @@ __device__ __forceinline__ void dfacc_merge3(dfacc& a1, dfacc& a2, dfacc& a3, df
   add(a3, s3);
 }
 
-// T[k][rho] over blocks; 16 (k) x 16 DF_J (rho) output tile, 1 x DF_J outputs per thread (small
-// tiles: the 736 CTAs of the 1025^2 maps spread over the 152 SMs more evenly than 368 larger ones)
-constexpr int DF_J = 2;                       // outputs per thread along rho
-constexpr int DF_BM = 16, DF_BN = 16 * DF_J;
+// T[k][rho] over blocks; 16 (k) x 32 (rho) output tile per CTA of 128 threads,
+// 2 x 2 outputs per thread (each operand value loaded from shared memory
+// serves two outputs); the 736 CTAs of the 1025^2 maps fit one wave at 5 per SM.
+constexpr int DF_BM = 16, DF_BN = 32, DF_NT = 128;
 
 // Complex products by Gauss's three multiplications: with p1 = ar br,
 // p2 = ai bi, p3 = (ar + ai)(br + bi) summed separately, Re = S1 - S2 and
@@ -391,34 +391,36 @@ constexpr int DF_BM = 16, DF_BN = 16 * DF_J;
 // stays relative to the sum of its terms' magnitudes, all bounded by
 // (|ar| + |ai|)(|br| + |bi|), so the error is still double-float-small
 // against the sum of the terms' magnitudes.
-__global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__ X, const float2* __restrict__ Xs,
-                                                      const int* __restrict__ ex, int M,
-                                                      const float4* __restrict__ G, const float2* __restrict__ Gs,
-                                                      const int* __restrict__ eg, int N, int nb,
-                                                      const int* __restrict__ spread, double2* __restrict__ T) {
+__global__ void __launch_bounds__(DF_NT) k_ff_stage1_df(const float4* __restrict__ X, const float2* __restrict__ Xs,
+                                                        const int* __restrict__ ex, int M,
+                                                        const float4* __restrict__ G, const float2* __restrict__ Gs,
+                                                        const int* __restrict__ eg, int N, int nb,
+                                                        const int* __restrict__ spread, double2* __restrict__ T) {
   if (!df_selected(spread)) return;      // the FP64 kernel takes this launch
   __shared__ float4 As[DF_BM][DKB + 1];
   __shared__ float2 As2[DF_BM][DKB + 1];
   __shared__ float4 Bs[DF_BN][DKB + 1];
   __shared__ float2 Bs2[DF_BN][DKB + 1];
   __shared__ int eA[DF_BM], eB[DF_BN];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // ty: 0..7, rows 2 ty and 2 ty + 1
   const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
-  dfacc acc1[DF_J], acc2[DF_J], acc3[DF_J];
+  dfacc acc1[2][2], acc2[2][2], acc3[2][2];
 #pragma unroll
-  for (int j = 0; j < DF_J; ++j) {
-    acc1[j] = dfacc{0.f, 0.f, -100000};
-    acc2[j] = dfacc{0.f, 0.f, -100000};
-    acc3[j] = dfacc{0.f, 0.f, -100000};
-  }
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      acc1[i][j] = dfacc{0.f, 0.f, -100000};
+      acc2[i][j] = dfacc{0.f, 0.f, -100000};
+      acc3[i][j] = dfacc{0.f, 0.f, -100000};
+    }
   for (int b = 0; b < nb; ++b) {
-    for (int i = tid; i < DF_BM * DKB; i += 256) {
+    for (int i = tid; i < DF_BM * DKB; i += DF_NT) {
       int r = i / DKB, kk = i % DKB, gm = m0 + r;
       const long long o = ((long long)gm * nb + b) * DKB + kk;
       As[r][kk] = (gm < M) ? X[o] : make_float4(0, 0, 0, 0);
       As2[r][kk] = (gm < M) ? Xs[o] : make_float2(0, 0);
     }
-    for (int i = tid; i < DF_BN * DKB; i += 256) {
+    for (int i = tid; i < DF_BN * DKB; i += DF_NT) {
       int r = i / DKB, kk = i % DKB, gn = n0 + r;
       const long long o = ((long long)gn * nb + b) * DKB + kk;
       Bs[r][kk] = (gn < N) ? G[o] : make_float4(0, 0, 0, 0);
@@ -427,36 +429,57 @@ __global__ void __launch_bounds__(256) k_ff_stage1_df(const float4* __restrict__
     if (tid < DF_BM) eA[tid] = (m0 + tid < M) ? ex[(long long)(m0 + tid) * nb + b] : 0;
     if (tid >= 64 && tid < 64 + DF_BN) eB[tid - 64] = (n0 + tid - 64 < N) ? eg[(long long)(n0 + tid - 64) * nb + b] : 0;
     __syncthreads();
-    df s1[DF_J], s2[DF_J], s3[DF_J];
+    df s1[2][2], s2[2][2], s3[2][2];
 #pragma unroll
-    for (int j = 0; j < DF_J; ++j) { s1[j] = df{0.f, 0.f}; s2[j] = df{0.f, 0.f}; s3[j] = df{0.f, 0.f}; }
-#pragma unroll 2
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) { s1[i][j] = df{0.f, 0.f}; s2[i][j] = df{0.f, 0.f}; s3[i][j] = df{0.f, 0.f}; }
+#pragma unroll 4
     for (int kk = 0; kk < DKB; ++kk) {
-      const float4 a = As[ty][kk];
-      const float2 a2 = As2[ty][kk];
-      const df ar{a.x, a.y}, ai{a.z, a.w}, as{a2.x, a2.y};
+      df ar[2], ai[2], as[2], br[2], bi[2], bs[2];
 #pragma unroll
-      for (int j = 0; j < DF_J; ++j) {
-        const float4 bb = Bs[tx + 16 * j][kk];
-        const float2 b2 = Bs2[tx + 16 * j][kk];
-        df_mac(s1[j], ar, df{bb.x, bb.y});
-        df_mac(s2[j], ai, df{bb.z, bb.w});
-        df_mac(s3[j], as, df{b2.x, b2.y});
+      for (int i = 0; i < 2; ++i) {
+        const float4 a = As[2 * ty + i][kk];
+        const float2 a2 = As2[2 * ty + i][kk];
+        ar[i] = df{a.x, a.y};
+        ai[i] = df{a.z, a.w};
+        as[i] = df{a2.x, a2.y};
+        const float4 bb = Bs[tx + 16 * i][kk];
+        const float2 b2 = Bs2[tx + 16 * i][kk];
+        br[i] = df{bb.x, bb.y};
+        bi[i] = df{bb.z, bb.w};
+        bs[i] = df{b2.x, b2.y};
       }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          df_mac(s1[i][j], ar[i], br[j]);
+          df_mac(s2[i][j], ai[i], bi[j]);
+          df_mac(s3[i][j], as[i], bs[j]);
+        }
     }
 #pragma unroll
-    for (int j = 0; j < DF_J; ++j) dfacc_merge3(acc1[j], acc2[j], acc3[j], s1[j], s2[j], s3[j], eA[ty] + eB[tx + 16 * j]);
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        dfacc_merge3(acc1[i][j], acc2[i][j], acc3[i][j], s1[i][j], s2[i][j], s3[i][j],
+                     eA[2 * ty + i] + eB[tx + 16 * j]);
     __syncthreads();
   }
-  const int gm = m0 + ty;
-  if (gm >= M) return;
 #pragma unroll
-  for (int j = 0; j < DF_J; ++j) {
-    const int gn = n0 + tx + 16 * j;
-    if (gn >= N) continue;
-    const double S1 = (double)acc1[j].hi + (double)acc1[j].lo, S2 = (double)acc2[j].hi + (double)acc2[j].lo;
-    const double S3 = (double)acc3[j].hi + (double)acc3[j].lo;
-    T[(long long)gm * N + gn] = make_double2(ldexp(S1 - S2, acc1[j].E), ldexp(S3 - S1 - S2, acc1[j].E));
+  for (int i = 0; i < 2; ++i) {
+    const int gm = m0 + 2 * ty + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      const double S1 = (double)acc1[i][j].hi + (double)acc1[i][j].lo;
+      const double S2 = (double)acc2[i][j].hi + (double)acc2[i][j].lo;
+      const double S3 = (double)acc3[i][j].hi + (double)acc3[i][j].lo;
+      T[(long long)gm * N + gn] = make_double2(ldexp(S1 - S2, acc1[i][j].E), ldexp(S3 - S1 - S2, acc1[i][j].E));
+    }
   }
 }
 
@@ -1099,8 +1122,8 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
     ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_ux * m + (double)R * m + (double)n_ux * R),
                  8.0 * (double)n_ux * (double)R * m);
     // exactly one of the two writes T (device-side range check on the spreads)
-    k_ff_stage1_df<<<gdf, 256, 0, s>>>(B.dxdf, B.dxsm, B.dex, n_ux, B.dgdf, B.dgsm, B.deg, (int)R, nbk, B.dspread,
-                                       B.dT);
+    k_ff_stage1_df<<<gdf, DF_NT, 0, s>>>(B.dxdf, B.dxsm, B.dex, n_ux, B.dgdf, B.dgsm, B.deg, (int)R, nbk, B.dspread,
+                                         B.dT);
     k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT, B.dspread);
   }
   count_launch(2);
