@@ -273,23 +273,33 @@ __device__ void ph_down(const BInst& I, int l, int t, bool zero_init, unsigned c
   const int tx = t % F.ntx, ty = t / F.ntx;
   const float2* in = (l == 0) ? F.u : nullptr;
   bool zi = zero_init || l > 0;
-  if (F.tc == 16)
-    tiles::down_tile<float, 16, true>(tx * 16, ty * 16, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
-  else
-    tiles::down_tile<float, 8, true>(tx * 8, ty * 8, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
+  const bool g1 = F.K.ng == 1;
+  if (F.tc == 16) {
+    if (g1) tiles::down_tile<float, 16, true, true>(tx * 16, ty * 16, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
+    else tiles::down_tile<float, 16, true, false>(tx * 16, ty * 16, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
+  } else {
+    if (g1) tiles::down_tile<float, 8, true, true>(tx * 8, ty * 8, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
+    else tiles::down_tile<float, 8, true, false>(tx * 8, ty * 8, in, zi, F.b, F.K, F.c, F.m, C.m, F.t, C.b, smem);
+  }
 }
 
 __device__ void ph_up(const BInst& I, int l, int t, unsigned char* smem) {
   const BLevel& F = I.L[l];
   const BLevel& C = I.L[l + 1];
   const int tx = t % F.ntx, ty = t / F.ntx;
-  if (F.tc == 16)
-    tiles::up_tile<float, 16, true>(tx * 16, ty * 16, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
-  else
-    tiles::up_tile<float, 8, true>(tx * 8, ty * 8, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
+  const bool g1 = F.K.ng == 1;
+  if (F.tc == 16) {
+    if (g1) tiles::up_tile<float, 16, true, true>(tx * 16, ty * 16, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
+    else tiles::up_tile<float, 16, true, false>(tx * 16, ty * 16, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
+  } else {
+    if (g1) tiles::up_tile<float, 8, true, true>(tx * 8, ty * 8, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
+    else tiles::up_tile<float, 8, true, false>(tx * 8, ty * 8, F.t, C.u, F.b, F.K, F.c, F.m, C.m, F.u, smem);
+  }
 }
 
-__global__ void __launch_bounds__(256) k_batch_solve(BArgs A) {
+// at most 85 registers a thread, so that three CTAs fit on an SM (the
+// autotuner picks between one and the occupancy maximum)
+__global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double shd[8];
   const int n = A.n_inst;

@@ -21,23 +21,26 @@ using tiles::Geo;
 using tiles::NT;
 using tiles::CoarseLevels;
 
-template <typename T, int TC>
-__global__ void __launch_bounds__(NT, 8) k_down2(const cx<T>* __restrict__ u_in, int zero_init,
+// FP64 16-point tiles need 75 KB of shared memory (three CTAs per SM)
+template <typename T, int TC> constexpr int tile_min_ctas() { return (sizeof(T) == 8 && TC == 16) ? 3 : 8; }
+
+template <typename T, int TC, bool G1>
+__global__ void __launch_bounds__(NT, tile_min_ctas<T, TC>()) k_down2(const cx<T>* __restrict__ u_in, int zero_init,
                                               const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
                                               int m, int mc, cx<T>* __restrict__ u_out, cx<T>* __restrict__ bc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_prologue();
-  tiles::down_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, zero_init, b, K, c, m, mc, u_out, bc,
+  tiles::down_tile<T, TC, false, G1>(blockIdx.x * TC, blockIdx.y * TC, u_in, zero_init, b, K, c, m, mc, u_out, bc,
                                  smem_raw);
 }
 
-template <typename T, int TC>
-__global__ void __launch_bounds__(NT, 8) k_up2(const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
+template <typename T, int TC, bool G1>
+__global__ void __launch_bounds__(NT, tile_min_ctas<T, TC>()) k_up2(const cx<T>* __restrict__ u_in, const cx<T>* __restrict__ ec,
                                             const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
                                             int m, int mc, cx<T>* __restrict__ u_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_prologue();
-  tiles::up_tile<T, TC, false>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, K, c, m, mc, u_out, smem_raw);
+  tiles::up_tile<T, TC, false, G1>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, K, c, m, mc, u_out, smem_raw);
 }
 
 template <typename T, int D>
@@ -80,6 +83,23 @@ template <int TC> size_t up_smem(int rb, int ng) { return tiles::up_smem_elems<T
 // 513^2 level then runs 1024 tiles of 8 instead of 256 of 16: 3-5 % faster)
 static bool small_tiles(int mc) { return ((mc + 15) / 16) * ((mc + 15) / 16) < 2 * 152; }
 
+// the down and up kernels for a tile size, specialised for a single Gaussian
+// in FP32 (its x factors then stay in registers)
+template <typename T, int TC>
+cudaError_t down2_tc(dim3 g, size_t smem, bool g1, cudaStream_t s, const cx<T>* u_in, int zi, const cx<T>* b,
+                     const tiles::LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, cx<T>* bc) {
+  if constexpr (tiles::formed_coef<T>())
+    if (g1) return launch_pdl(k_down2<T, TC, true>, g, dim3(NT), smem, s, u_in, zi, b, K, c, m, mc, u_out, bc);
+  return launch_pdl(k_down2<T, TC, false>, g, dim3(NT), smem, s, u_in, zi, b, K, c, m, mc, u_out, bc);
+}
+template <typename T, int TC>
+cudaError_t up2_tc(dim3 g, size_t smem, bool g1, cudaStream_t s, const cx<T>* u_in, const cx<T>* ec,
+                   const cx<T>* b, const tiles::LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out) {
+  if constexpr (tiles::formed_coef<T>())
+    if (g1) return launch_pdl(k_up2<T, TC, true>, g, dim3(NT), smem, s, u_in, ec, b, K, c, m, mc, u_out);
+  return launch_pdl(k_up2<T, TC, false>, g, dim3(NT), smem, s, u_in, ec, b, K, c, m, mc, u_out);
+}
+
 template <typename T>
 cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, bool zero_init, const cx<T>* b,
                          cx<T>* u_out, cx<T>* bc, cudaStream_t s) {
@@ -90,12 +110,12 @@ cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, boo
   cudaError_t e;
   if (small_tiles(Cl.m)) {
     dim3 g((Cl.m + 7) / 8, (Cl.m + 7) / 8);
-    e = launch_pdl(k_down2<T, 8>, g, dim3(NT), down_smem<8>(sizeof(T), ng), s, u_in, zero_init ? 1 : 0, b, K, c,
-                   F.m, Cl.m, u_out, bc);
+    e = down2_tc<T, 8>(g, down_smem<8>(sizeof(T), ng), ng == 1, s, u_in, zero_init ? 1 : 0, b, K, c, F.m, Cl.m,
+                       u_out, bc);
   } else {
     dim3 g((Cl.m + 15) / 16, (Cl.m + 15) / 16);
-    e = launch_pdl(k_down2<T, 16>, g, dim3(NT), down_smem<16>(sizeof(T), ng), s, u_in, zero_init ? 1 : 0, b, K,
-                   c, F.m, Cl.m, u_out, bc);
+    e = down2_tc<T, 16>(g, down_smem<16>(sizeof(T), ng), ng == 1, s, u_in, zero_init ? 1 : 0, b, K, c, F.m,
+                        Cl.m, u_out, bc);
   }
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -111,10 +131,10 @@ cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const
   cudaError_t e;
   if (small_tiles(Cl.m)) {
     dim3 g((Cl.m + 7) / 8, (Cl.m + 7) / 8);
-    e = launch_pdl(k_up2<T, 8>, g, dim3(NT), up_smem<8>(sizeof(T), ng), s, u_in, ec, b, K, c, F.m, Cl.m, u_out);
+    e = up2_tc<T, 8>(g, up_smem<8>(sizeof(T), ng), ng == 1, s, u_in, ec, b, K, c, F.m, Cl.m, u_out);
   } else {
     dim3 g((Cl.m + 15) / 16, (Cl.m + 15) / 16);
-    e = launch_pdl(k_up2<T, 16>, g, dim3(NT), up_smem<16>(sizeof(T), ng), s, u_in, ec, b, K, c, F.m, Cl.m, u_out);
+    e = up2_tc<T, 16>(g, up_smem<16>(sizeof(T), ng), ng == 1, s, u_in, ec, b, K, c, F.m, Cl.m, u_out);
   }
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
@@ -154,9 +174,9 @@ cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc) {
   cudaError_t e;
   // the tiles stay below the default 48 KB (FP64: no factor windows; FP32:
   // at most 8 Gaussians)
-  if ((e = cudaFuncSetAttribute(k_down2<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_down2<double, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)down_smem<16>(8, 0))) ||
-      (e = cudaFuncSetAttribute(k_up2<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (e = cudaFuncSetAttribute(k_up2<double, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)up_smem<16>(8, 0))))
     return e;
   static_assert(tiles::down_smem_elems<16>(8, false) * 8 <= 48 * 1024 &&

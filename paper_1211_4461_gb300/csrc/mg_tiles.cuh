@@ -44,15 +44,33 @@ template <typename T> struct LevelCoef {
 };
 template <typename T> constexpr bool formed_coef() { return sizeof(T) == 4; }
 
-template <int TC> __host__ __device__ constexpr int down_window() { return Geo<TC>::DW * Geo<TC>::DW; }
-template <int TC> __host__ __device__ constexpr int up_window() { return Geo<TC>::UW * Geo<TC>::UW; }
+// Shared-memory windows are stored split by colour: window point (wx, wy)
+// sits in plane (wx + wy) & 1, row wy, slot wx >> 1, with HS = (W + 1) / 2
+// slots a row.  A point in slot j of its row (wx = 2 j + o) finds its four
+// neighbours in the other plane: slots j + o - 1 and j + o of the same row and
+// slot j of the rows above and below, so a warp working along a row touches
+// consecutive words.
+template <int W> struct RB {
+  static constexpr int HS = (W + 1) / 2;
+  static constexpr int PLANE = W * HS;
+  static constexpr int ELEMS = 2 * PLANE;
+  // factor windows of one Gaussian: X_g split by the parity of wx (2 HS), Y_g (W)
+  static constexpr int FACTOR = 2 * HS + W;
+};
+template <int W> __device__ __forceinline__ int rbi(int wx, int wy) {
+  return (((wx + wy) & 1) * W + wy) * RB<W>::HS + (wx >> 1);
+}
+
+template <int TC> __host__ __device__ constexpr int down_window() { return RB<Geo<TC>::DW>::ELEMS; }
+template <int TC> __host__ __device__ constexpr int up_window() { return RB<Geo<TC>::UW>::ELEMS; }
 // shared-memory elements (complex values) of one tile: iterate and RHS
-// windows, then FP32 factor windows (ng pairs) or the FP64 1/d window
+// windows, then FP32 factor windows (ng Gaussians) or the FP64 1/d window
 template <int TC> __host__ __device__ constexpr size_t down_smem_elems(int ng, bool fp64) {
-  return (size_t)(fp64 ? 3 : 2) * down_window<TC>() + (fp64 ? 0 : 2 * ng * Geo<TC>::DW);
+  return (size_t)(fp64 ? 3 : 2) * down_window<TC>() + (fp64 ? 0 : (size_t)ng * RB<Geo<TC>::DW>::FACTOR);
 }
 template <int TC> __host__ __device__ constexpr size_t up_smem_elems(int ng, bool fp64) {
-  return (size_t)(fp64 ? 3 : 2) * up_window<TC>() + Geo<TC>::EW * Geo<TC>::EW + (fp64 ? 0 : 2 * ng * Geo<TC>::UW);
+  return (size_t)(fp64 ? 3 : 2) * up_window<TC>() + Geo<TC>::EW * Geo<TC>::EW +
+         (fp64 ? 0 : (size_t)ng * RB<Geo<TC>::UW>::FACTOR);
 }
 
 template <typename T>
@@ -81,13 +99,6 @@ __device__ __forceinline__ C ld(const C* p) {
   else return *p;
 }
 
-// sum of the four neighbours of window point i (row width W); values outside
-// the domain are stored as zero.  Order x-1, x+1, y-1, y+1.
-template <typename C>
-__device__ __forceinline__ C nbr_sum(const C* U, int W, int i) {
-  return xadd(xadd(xadd(U[i - 1], U[i + 1]), U[i - W]), U[i + W]);
-}
-
 // 1/d for the smoother: reciprocal of |d|^2 by the hardware approximation
 // (__fdividef, about 2 ulp), enough for an inverse diagonal that only scales
 // the correction
@@ -108,145 +119,215 @@ __device__ __forceinline__ void cp_async_zfill(void* smem_dst, const void* gsrc,
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Window of W x W fine points with origin (ox, oy): iterate -> U, RHS -> B,
-// and the coefficient windows (FP32: X_g, Y_g along the two axes; FP64: 1/d).
-// Points outside the interior are zero.
-template <typename T, bool COH>
-__device__ __forceinline__ void load_window(int ox, int oy, int W, int m, const cx<T>* u_in, bool zero_u,
+// Window of W x W fine points with origin (ox, oy) in the colour-split layout.
+//  - Iterate: the black points (window colour 1) only.  A red-black sweep
+//    never reads a red point's own old value, and the red half sweep computes
+//    every red value read afterwards, so red slots are only set to zero where
+//    they lie outside the domain (Dirichlet neighbours of black edge points).
+//  - RHS (FP64: and 1/d) on window [1, W-2]^2, the points the sweeps update.
+//  - FP32: per Gaussian X_g at wx = 2 j + o in slot o HS + j, then Y_g along wy.
+// Points outside the interior read as zero.
+template <typename T, int W, bool COH>
+__device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* u_in, bool zero_u,
                                             const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
                                             cx<T>* X) {
+  constexpr int HS = RB<W>::HS, PL = RB<W>::PLANE, WI = W - 2;
   const bool inner = ox >= 0 && oy >= 0 && ox + W <= m && oy + W <= m;
-  if constexpr (COH) {
-    for (int i = threadIdx.x; i < W * W; i += NT) {
-      const int wy = i / W, wx = i - wy * W;
-      const int fx = ox + wx, fy = oy + wy;
-      const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
-      const long long g = (long long)fy * m + fx;
-      U[i] = (in && !zero_u) ? ld<COH>(u_in + g) : zero_c<T>();
-      B[i] = in ? ld<COH>(b + g) : zero_c<T>();
-      if constexpr (!formed_coef<T>()) X[i] = in ? K.dinv[g] : zero_c<T>();
+  // per-level kernels: every copy of this thread in flight at once (one round
+  // trip per tile); the persistent kernel reads data written by other CTAs of
+  // the same launch through L2
+  for (int i = threadIdx.x; i < W * HS; i += NT) {         // black plane: wx = 2 j + (~wy & 1)
+    const int wy = i / HS, j = i - wy * HS;
+    const int wx = 2 * j + ((wy & 1) ^ 1);
+    if (wx >= W) continue;
+    const int fx = ox + wx, fy = oy + wy;
+    const bool in = !zero_u && (inner || (fx >= 0 && fx < m && fy >= 0 && fy < m));
+    const long long g = in ? (long long)fy * m + fx : 0;
+    if constexpr (COH) U[PL + i] = in ? ld<COH>(u_in + g) : zero_c<T>();
+    else cp_async_zfill<sizeof(cx<T>)>(U + PL + i, u_in + g, in);
+  }
+  if (!inner)
+    for (int i = threadIdx.x; i < W * HS; i += NT) {       // red plane: wx = 2 j + (wy & 1)
+      const int wy = i / HS, j = i - wy * HS;
+      const int fx = ox + 2 * j + (wy & 1), fy = oy + wy;
+      if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[i] = zero_c<T>();
     }
-  } else {
-    // every copy of this thread in flight at once (one round trip per tile)
-    for (int i = threadIdx.x; i < W * W; i += NT) {
-      const int wy = i / W, wx = i - wy * W;
-      const int fx = ox + wx, fy = oy + wy;
-      const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
-      const long long g = in ? (long long)fy * m + fx : 0;
-      if (zero_u) U[i] = zero_c<T>();
-      else cp_async_zfill<sizeof(cx<T>)>(U + i, u_in + g, in);
-      cp_async_zfill<sizeof(cx<T>)>(B + i, b + g, in);
-      if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + i, K.dinv + g, in);
+  for (int i = threadIdx.x; i < WI * WI; i += NT) {
+    const int r = i / WI;
+    const int wy = 1 + r, wx = 1 + i - r * WI;
+    const int fx = ox + wx, fy = oy + wy;
+    const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
+    const int d = rbi<W>(wx, wy);
+    const long long g = in ? (long long)fy * m + fx : 0;
+    if constexpr (COH) {
+      B[d] = in ? ld<COH>(b + g) : zero_c<T>();
+      if constexpr (!formed_coef<T>()) X[d] = in ? K.dinv[g] : zero_c<T>();
+    } else {
+      cp_async_zfill<sizeof(cx<T>)>(B + d, b + g, in);
+      if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + d, K.dinv + g, in);
     }
   }
   if constexpr (formed_coef<T>()) {
-    cx<T>* FY = X + K.ng * W;
-    for (int i = threadIdx.x; i < K.ng * W; i += NT) {
-      const int g = i / W, w = i - g * W;
-      const int fx = ox + w, fy = oy + w;
-      X[i] = (fx >= 0 && fx < m) ? K.fac[((size_t)g * 2) * m + fx] : zero_c<T>();
-      FY[i] = (fy >= 0 && fy < m) ? K.fac[((size_t)g * 2 + 1) * m + fy] : zero_c<T>();
+    constexpr int FW = RB<W>::FACTOR;
+    for (int i = threadIdx.x; i < K.ng * FW; i += NT) {
+      const int g = i / FW, r = i - g * FW;
+      cx<T> v = zero_c<T>();
+      if (r < 2 * HS) {
+        const int o = r >= HS ? 1 : 0;
+        const int fx = ox + 2 * (r - o * HS) + o;
+        if (fx >= 0 && fx < m) v = K.fac[((size_t)g * 2) * m + fx];
+      } else {
+        const int fy = oy + r - 2 * HS;
+        if (fy >= 0 && fy < m) v = K.fac[((size_t)g * 2 + 1) * m + fy];
+      }
+      X[i] = v;
     }
   }
   if constexpr (!COH) cp_async_wait_all();
 }
 
-// d = 4c - q at window point (wx, wy) from the factor windows
-__device__ __forceinline__ float2 formed_diag(const LevelCoef<float>& K, float2 c, const float2* X, int W, int wx,
+// d = 4c - q at the point in slot j (wx = 2 j + o) of window row wy, from the
+// factor windows
+template <int W>
+__device__ __forceinline__ float2 formed_diag(const LevelCoef<float>& K, float2 c, const float2* X, int o, int j,
                                               int wy) {
-  const float2* FY = X + K.ng * W;
+  constexpr int HS = RB<W>::HS, FW = RB<W>::FACTOR;
   float2 q = make_float2(K.k2, 0.f);
-  for (int g = 0; g < K.ng; ++g) q = xadd(q, xmul(X[g * W + wx], FY[g * W + wy]));
+  for (int g = 0; g < K.ng; ++g) q = xadd(q, xmul(X[g * FW + o * HS + j], X[g * FW + 2 * HS + wy]));
   return make_float2(__fmaf_rn(4.f, c.x, -q.x), __fmaf_rn(4.f, c.y, -q.y));
 }
 
-// One red-black Gauss-Seidel half sweep over window points [lo, hi]^2 of the
-// given colour, in the form
+// Work split of a pass over R window rows: each thread takes slot column j of
+// a segment of RS consecutive rows.  RS is even, so every segment starts on a
+// row of LO's parity and the slot parity o of each row of the segment is a
+// compile-time constant.
+template <int W, int R> struct Seg {
+  static constexpr int HS = RB<W>::HS;
+  static constexpr int RS0 = (R + NT / HS - 1) / (NT / HS);
+  static constexpr int RS = RS0 + (RS0 & 1);
+  static constexpr int NSEG = (R + RS - 1) / RS;
+  static_assert(NSEG * HS <= NT, "one segment per thread");
+};
+
+// One pass over the points of window colour COLOUR in window rows and columns
+// [LO, HI] that lie inside the domain: a red-black Gauss-Seidel half sweep
 //   u_j <- d_j^{-1} (b_j + c sum_nbr u),
-// which equals u_j + d_j^{-1} (b_j - (A u)_j) for A u = d u - c sum_nbr u.
-template <typename T, int W, int COLOUR>
-__device__ __forceinline__ void rb_half(int ox, int oy, int m, const LevelCoef<T>& K, cx<T> c, cx<T>* U,
-                                        const cx<T>* B, const cx<T>* X) {
-  constexpr int lo = 1 + COLOUR, hi = W - 2 - COLOUR;
-  constexpr int R = hi - lo + 1, HW = (R + 1) >> 1;
-  // only the points of this colour: in window row wy they start at lo or
-  // lo + 1, whichever gives (fx + fy) of the colour's parity, and step by 2;
-  // tiles away from the domain edge skip the range tests
-  const bool inner = ox + lo >= 0 && oy + lo >= 0 && ox + hi < m && oy + hi < m;
-  const int par = (COLOUR ^ (ox + oy)) & 1;        // (fx + fy) parity = colour
-  for (int t = threadIdx.x; t < R * HW; t += NT) {
-    const int r = t / HW, j = t - r * HW;
-    const int wy = lo + r;
-    const int wx = lo + ((par ^ r) & 1) + 2 * j;
-    if (wx > hi) continue;
-    if (!inner) {
-      const int fx = ox + wx, fy = oy + wy;
-      if (fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
+// which equals u_j + d_j^{-1} (b_j - (A u)_j) for A u = d u - c sum_nbr u, or,
+// with RESID, the residual r_j = b_j - (d_j u_j - c sum_nbr u) written over
+// b_j.  The thread carries the other colour's slot-j values from row to row in
+// registers (three loads and a store per point, all on consecutive words of a
+// row).  Neighbour order of the sum: x-1, x+1, y-1, y+1.  G1: the level has a
+// single Gaussian, whose x factors for the thread's two slot parities stay in
+// registers.
+template <typename T, int W, int COLOUR, int LO, int HI, bool RESID, bool G1>
+__device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T>& K, cx<T> c, cx<T>* U,
+                                        cx<T>* B, const cx<T>* X) {
+  using C = cx<T>;
+  using S = Seg<W, HI - LO + 1>;
+  constexpr int HS = S::HS, PL = RB<W>::PLANE, RS = S::RS;
+  constexpr int OA = (COLOUR ^ LO) & 1;          // slot parity of the segment's even rows
+  static_assert(LO >= 1 && HI <= W - 2, "neighbours inside the window");
+  const int t = threadIdx.x;
+  if (t >= S::NSEG * HS) return;
+  const int seg = t / HS, j = t - seg * HS;
+  const int y0 = LO + seg * RS;
+  const int nrows = min(RS, HI + 1 - y0);
+  const int wxA = 2 * j + OA, wxB = 2 * j + (OA ^ 1);
+  const bool okA = wxA >= LO && wxA <= HI && ox + wxA >= 0 && ox + wxA < m;
+  const bool okB = wxB >= LO && wxB <= HI && ox + wxB >= 0 && ox + wxB < m;
+  const bool rows_in = oy + y0 >= 0 && oy + y0 + nrows <= m;
+  const C* po = U + (1 - COLOUR) * PL + y0 * HS + j;
+  C* pc = U + COLOUR * PL + y0 * HS + j;
+  C* pb = B + COLOUR * PL + y0 * HS + j;
+  C xA = zero_c<T>(), xB = zero_c<T>();
+  if constexpr (G1 && formed_coef<T>()) {
+    xA = X[OA * HS + j];
+    xB = X[(OA ^ 1) * HS + j];
+  }
+  C up = po[-HS], mid = po[0];
+#pragma unroll
+  for (int r = 0; r < RS; ++r) {
+    if (r >= nrows) break;
+    const C dn = po[(r + 1) * HS];
+    const int o = OA ^ (r & 1);
+    bool ok = (r & 1) ? okB : okA;
+    if (!rows_in) ok = ok && oy + y0 + r >= 0 && oy + y0 + r < m;
+    if (ok) {
+      const C side = po[r * HS + 2 * o - 1];
+      const C s = xadd(xadd(xadd(o ? mid : side, o ? side : mid), up), dn);
+      C d;
+      if constexpr (formed_coef<T>()) {
+        if constexpr (G1) {
+          const C q = xadd(make_float2(K.k2, 0.f), xmul((r & 1) ? xB : xA, X[2 * HS + y0 + r]));
+          d = make_float2(__fmaf_rn(4.f, c.x, -q.x), __fmaf_rn(4.f, c.y, -q.y));
+        } else {
+          d = formed_diag<W>(K, c, X, o, j, y0 + r);
+        }
+      }
+      if constexpr (RESID) {
+        if constexpr (!formed_coef<T>()) d = xsub(xscale(c, (T)4), K.q[(long long)(oy + y0 + r) * m + ox + 2 * j + o]);
+        pb[r * HS] = xsub(pb[r * HS], xsub(xmul(d, pc[r * HS]), xmul(c, s)));
+      } else {
+        C di;
+        if constexpr (formed_coef<T>()) di = crecip(d);
+        else di = X[COLOUR * PL + (y0 + r) * HS + j];
+        pc[r * HS] = xmul(di, xadd(pb[r * HS], xmul(c, s)));
+      }
     }
-    const int i = wy * W + wx;
-    cx<T> di;
-    if constexpr (formed_coef<T>()) di = crecip(formed_diag(K, c, X, W, wx, wy));
-    else di = X[i];
-    U[i] = xmul(di, xadd(B[i], xmul(c, nbr_sum(U, W, i))));
+    up = mid;
+    mid = dn;
   }
 }
 
 // down tile (P0x, P0y in coarse points).  u_in is ignored when zero_init.
-template <typename T, int TC, bool COH>
+// The window origin has ox + oy even, so window colour 0 is red ((fx + fy) even).
+template <typename T, int TC, bool COH, bool G1>
 __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, const cx<T>* b,
                           const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, cx<T>* bc,
                           unsigned char* smem_raw) {
   using C = cx<T>;
-  constexpr int FT = Geo<TC>::FT, DW = Geo<TC>::DW, NW = DW * DW;
+  constexpr int FT = Geo<TC>::FT, DW = Geo<TC>::DW, HS = RB<DW>::HS, NW = RB<DW>::ELEMS;
   C* U = reinterpret_cast<C*>(smem_raw);
-  C* B = U + NW;                              // RHS, then the residual in place
+  C* B = U + NW;                              // RHS, then the red residual in place
   C* X = B + NW;                              // coefficient windows
   const int ox = 2 * P0x - 3, oy = 2 * P0y - 3;   // window origin (fine interior index)
-  load_window<T, COH>(ox, oy, DW, m, u_in, zero_init != 0, b, K, U, B, X);
+  load_window<T, DW, COH>(ox, oy, m, u_in, zero_init != 0, b, K, U, B, X);
   __syncthreads();
   // red on window [1, DW-2], black on [2, DW-3]
-  rb_half<T, DW, 0>(ox, oy, m, K, c, U, B, X);
+  rb_pass<T, DW, 0, 1, DW - 2, false, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
-  rb_half<T, DW, 1>(ox, oy, m, K, c, U, B, X);
+  rb_pass<T, DW, 1, 2, DW - 3, false, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
-  // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final
-  // index); residual on [2P0, 2P0+FT] written over the RHS (each point reads
-  // only its own RHS value)
+  // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final index)
   {
     const int ex = (P0x + TC >= mc) ? m : 2 * P0x + FT;
     const int ey = (P0y + TC >= mc) ? m : 2 * P0y + FT;
     for (int i = threadIdx.x; i < (FT + 1) * (FT + 1); i += NT) {
       const int ly = i / (FT + 1), lx = i - ly * (FT + 1);
       const int fx = 2 * P0x + lx, fy = 2 * P0y + ly;
-      const int w = (ly + 3) * DW + lx + 3;
-      const long long g = (long long)fy * m + fx;
-      if (fx < ex && fy < ey && fx < m && fy < m) u_out[g] = U[w];
-      C rv = zero_c<T>();
-      if (fx < m && fy < m) {
-        C d;
-        if constexpr (formed_coef<T>()) d = formed_diag(K, c, X, DW, lx + 3, ly + 3);
-        else d = xsub(xscale(c, (T)4), K.q[g]);
-        rv = xsub(B[w], xsub(xmul(d, U[w]), xmul(c, nbr_sum(U, DW, w))));
-      }
-      B[w] = rv;
+      if (fx < ex && fy < ey && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[rbi<DW>(lx + 3, ly + 3)];
     }
   }
+  // residual at the red points of [2P0, 2P0+FT]^2 (window [3, 3+FT]).  At the
+  // black points it is zero: the black half sweep has just solved their
+  // equations with the final red values.
+  rb_pass<T, DW, 0, 3, 3 + FT, true, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
-  const T w1[3] = {(T)0.25, (T)0.5, (T)0.25};
+  // full weighting: coarse P has its centre fine point 2P+1 at window
+  // (2p+4, 2p+4) and corners at (2p+3 | 2p+5, 2p+3 | 2p+5), all red (slots
+  // p+2 and p+1, p+2); the four edge points are black, with zero residual
+  const C* R0 = B;
   for (int i = threadIdx.x; i < TC * TC; i += NT) {
-    int py = i / TC, px = i - py * TC;
-    int Px = P0x + px, Py = P0y + py;
+    const int py = i / TC, px = i - py * TC;
+    const int Px = P0x + px, Py = P0y + py;
     if (Px >= mc || Py >= mc) continue;
-    C acc = zero_c<T>();
-#pragma unroll
-    for (int oy2 = -1; oy2 <= 1; ++oy2) {
-      C row = zero_c<T>();
-      int ry = 2 * py + 4 + oy2;          // window row of fine 2P0y + 2py + 1 + oy2
-#pragma unroll
-      for (int ox2 = -1; ox2 <= 1; ++ox2) row = xadd(row, xscale(B[ry * DW + 2 * px + 4 + ox2], w1[ox2 + 1]));
-      acc = xadd(acc, xscale(row, w1[oy2 + 1]));
-    }
-    bc[(long long)Py * mc + Px] = acc;
+    const C* r3 = R0 + (2 * py + 3) * HS + px;
+    const C* r4 = r3 + HS;
+    const C* r5 = r4 + HS;
+    const C top = xadd(xscale(r3[1], (T)0.25), xscale(r3[2], (T)0.25));
+    const C cen = xscale(r4[2], (T)0.5);
+    const C bot = xadd(xscale(r5[1], (T)0.25), xscale(r5[2], (T)0.25));
+    bc[(long long)Py * mc + Px] = xadd(xadd(xscale(top, (T)0.25), xscale(cen, (T)0.5)), xscale(bot, (T)0.25));
   }
   __syncthreads();   // shared memory is reused by the next tile
 }
@@ -267,12 +348,13 @@ __device__ __forceinline__ int interp_w(int p, int e0, int mc, int* ci, T* w) {
   return n;
 }
 
-// up tile: u = u_in + P e_c, one RB-GS sweep, write owned points.
-template <typename T, int TC, bool COH>
+// up tile: u = u_in + P e_c, one RB-GS sweep, write owned points.  Window
+// colour 0 is red (ox + oy even).
+template <typename T, int TC, bool COH, bool G1>
 __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
                         const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, unsigned char* smem_raw) {
   using C = cx<T>;
-  constexpr int FT = Geo<TC>::FT, UW = Geo<TC>::UW, EW = Geo<TC>::EW, NW = UW * UW;
+  constexpr int FT = Geo<TC>::FT, UW = Geo<TC>::UW, EW = Geo<TC>::EW, NW = RB<UW>::ELEMS;
   C* U = reinterpret_cast<C*>(smem_raw);
   C* B = U + NW;
   C* E = B + NW;                         // EW x EW coarse window
@@ -284,35 +366,35 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
     int cxp = ex0 + wx, cyp = ey0 + wy;
     E[i] = (cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc) ? ld<COH>(ec + (long long)cyp * mc + cxp) : zero_c<T>();
   }
-  load_window<T, COH>(ox, oy, UW, m, u_in, false, b, K, U, B, X);
+  load_window<T, UW, COH>(ox, oy, m, u_in, false, b, K, U, B, X);
   __syncthreads();
-  // bilinear interpolation: node index i = f + 1 lies on coarse node i/2 (even
-  // i, weight 1) or between (i-1)/2 and (i+1)/2 (odd i, 1/2 each); the coarse
-  // window is zero outside the coarse interior, so no range tests are needed
-  for (int i = threadIdx.x; i < NW; i += NT) {
-    const int wy = i / UW, wx = i - wy * UW;
-    const int fx = ox + wx, fy = oy + wy;
-    if (fx < 0 || fx >= m || fy < 0 || fy >= m) continue;
-    const int ix = fx + 1, iy = fy + 1;
-    const int cx0 = (ix >> 1) - 1 - ex0, cy0 = (iy >> 1) - 1 - ey0;
-    const int cx1 = cx0 + (ix & 1), cy1 = cy0 + (iy & 1);
-    const T wx0 = (ix & 1) ? (T)0.5 : (T)1, wx1 = (ix & 1) ? (T)0.5 : (T)0;
-    const T wy0 = (iy & 1) ? (T)0.5 : (T)1, wy1 = (iy & 1) ? (T)0.5 : (T)0;
-    const C r0 = xadd(xscale(E[cy0 * EW + cx0], wx0), xscale(E[cy0 * EW + cx1], wx1));
-    const C r1 = xadd(xscale(E[cy1 * EW + cx0], wx0), xscale(E[cy1 * EW + cx1], wx1));
-    U[i] = xadd(U[i], xadd(xscale(r0, wy0), xscale(r1, wy1)));
+  // prolongation at the black points only: the red half sweep overwrites the
+  // red ones without reading them.  With node index i = f + 1, a black fine
+  // point has one odd and one even index: in odd window rows (iy even) it lies
+  // between coarse-window columns j and j+1 of row (wy+1)/2, in even rows (iy
+  // odd) between rows wy/2 and wy/2+1 of column j+1.  The coarse window is
+  // zero outside the coarse interior, so points outside the domain stay zero.
+  {
+    constexpr int HS = RB<UW>::HS, PL = RB<UW>::PLANE;
+    for (int i = threadIdx.x; i < UW * HS; i += NT) {
+      const int wy = i / HS, j = i - wy * HS;
+      if (2 * j + ((wy & 1) ^ 1) >= UW) continue;
+      const C* e = (wy & 1) ? E + ((wy + 1) >> 1) * EW + j : E + (wy >> 1) * EW + j + 1;
+      const C e1 = (wy & 1) ? e[1] : e[EW];
+      U[PL + i] = xadd(U[PL + i], xadd(xscale(e[0], (T)0.5), xscale(e1, (T)0.5)));
+    }
   }
   __syncthreads();
-  rb_half<T, UW, 0>(ox, oy, m, K, c, U, B, X);
+  rb_pass<T, UW, 0, 1, UW - 2, false, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
-  rb_half<T, UW, 1>(ox, oy, m, K, c, U, B, X);
+  rb_pass<T, UW, 1, 2, UW - 3, false, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
   const int exx = (P0x + TC >= mc) ? m : 2 * P0x + FT;
   const int eyy = (P0y + TC >= mc) ? m : 2 * P0y + FT;
   for (int i = threadIdx.x; i < (FT + 1) * (FT + 1); i += NT) {
     int ly = i / (FT + 1), lx = i - ly * (FT + 1);
     int fx = 2 * P0x + lx, fy = 2 * P0y + ly;
-    if (fx < exx && fy < eyy && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[(ly + 2) * UW + lx + 2];
+    if (fx < exx && fy < eyy && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[rbi<UW>(lx + 2, ly + 2)];
   }
   __syncthreads();
 }
