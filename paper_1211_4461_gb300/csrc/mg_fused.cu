@@ -10,8 +10,10 @@
 // residual on the tile; halo 2 for up), so one level costs two passes over
 // its arrays instead of eight kernels.  The smoothed iterate of down(l) goes to
 // a second buffer (the halos of neighbouring tiles must see the old values);
-// up(l) reads it and writes the final iterate back.  The tile bodies live in
-// mg_tiles.cuh (shared with the persistent batched kernel).
+// up(l) reads it and writes the final iterate back.  Since a red update never
+// reads the red point's own old value, both kernels read only the black
+// points of the incoming iterate, and down(l) writes only those.  The tile
+// bodies live in mg_tiles.cuh (shared with the persistent batched kernel).
 #include "mg_tiles.cuh"
 
 namespace csff {

@@ -92,6 +92,19 @@ __device__ __forceinline__ double2 xmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ float2 xscale(float2 a, float s) { return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
 __device__ __forceinline__ double2 xscale(double2 a, double s) { return make_double2(__dmul_rn(a.x, s), __dmul_rn(a.y, s)); }
+// a + b c and a - b c as chains of fused multiply-adds (one rounding each)
+__device__ __forceinline__ float2 xfma(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(b.x, c.x, __fmaf_rn(-b.y, c.y, a.x)), __fmaf_rn(b.x, c.y, __fmaf_rn(b.y, c.x, a.y)));
+}
+__device__ __forceinline__ double2 xfma(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(b.x, c.x, __fma_rn(-b.y, c.y, a.x)), __fma_rn(b.x, c.y, __fma_rn(b.y, c.x, a.y)));
+}
+__device__ __forceinline__ float2 xfms(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(-b.x, c.x, __fmaf_rn(b.y, c.y, a.x)), __fmaf_rn(-b.x, c.y, __fmaf_rn(-b.y, c.x, a.y)));
+}
+__device__ __forceinline__ double2 xfms(double2 a, double2 b, double2 c) {
+  return make_double2(__fma_rn(-b.x, c.x, __fma_rn(b.y, c.y, a.x)), __fma_rn(-b.x, c.y, __fma_rn(-b.y, c.x, a.y)));
+}
 
 template <bool COH, typename C>
 __device__ __forceinline__ C ld(const C* p) {
@@ -186,15 +199,15 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
   if constexpr (!COH) cp_async_wait_all();
 }
 
-// d = 4c - q at the point in slot j (wx = 2 j + o) of window row wy, from the
-// factor windows
+// d = 4c - q = D0 - sum_g X_g Y_g (D0 = 4c - k^2) at the point in slot j
+// (wx = 2 j + o) of window row wy, from the factor windows
 template <int W>
-__device__ __forceinline__ float2 formed_diag(const LevelCoef<float>& K, float2 c, const float2* X, int o, int j,
+__device__ __forceinline__ float2 formed_diag(const LevelCoef<float>& K, float2 D0, const float2* X, int o, int j,
                                               int wy) {
   constexpr int HS = RB<W>::HS, FW = RB<W>::FACTOR;
-  float2 q = make_float2(K.k2, 0.f);
-  for (int g = 0; g < K.ng; ++g) q = xadd(q, xmul(X[g * FW + o * HS + j], X[g * FW + 2 * HS + wy]));
-  return make_float2(__fmaf_rn(4.f, c.x, -q.x), __fmaf_rn(4.f, c.y, -q.y));
+  float2 d = D0;
+  for (int g = 0; g < K.ng; ++g) d = xfms(d, X[g * FW + o * HS + j], X[g * FW + 2 * HS + wy]);
+  return d;
 }
 
 // Work split of a pass over R window rows: each thread takes slot column j of
@@ -244,6 +257,9 @@ __device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T
     xA = X[OA * HS + j];
     xB = X[(OA ^ 1) * HS + j];
   }
+  // formed diagonal: D0 = 4c - k^2
+  C D0 = zero_c<T>();
+  if constexpr (formed_coef<T>()) D0 = make_float2(__fmaf_rn(4.f, c.x, -K.k2), __fmul_rn(4.f, c.y));
   C up = po[-HS], mid = po[0];
 #pragma unroll
   for (int r = 0; r < RS; ++r) {
@@ -257,21 +273,17 @@ __device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T
       const C s = xadd(xadd(xadd(o ? mid : side, o ? side : mid), up), dn);
       C d;
       if constexpr (formed_coef<T>()) {
-        if constexpr (G1) {
-          const C q = xadd(make_float2(K.k2, 0.f), xmul((r & 1) ? xB : xA, X[2 * HS + y0 + r]));
-          d = make_float2(__fmaf_rn(4.f, c.x, -q.x), __fmaf_rn(4.f, c.y, -q.y));
-        } else {
-          d = formed_diag<W>(K, c, X, o, j, y0 + r);
-        }
+        if constexpr (G1) d = xfms(D0, (r & 1) ? xB : xA, X[2 * HS + y0 + r]);
+        else d = formed_diag<W>(K, D0, X, o, j, y0 + r);
       }
       if constexpr (RESID) {
         if constexpr (!formed_coef<T>()) d = xsub(xscale(c, (T)4), K.q[(long long)(oy + y0 + r) * m + ox + 2 * j + o]);
-        pb[r * HS] = xsub(pb[r * HS], xsub(xmul(d, pc[r * HS]), xmul(c, s)));
+        pb[r * HS] = xfma(xfms(pb[r * HS], d, pc[r * HS]), c, s);       // b - d u + c s
       } else {
         C di;
         if constexpr (formed_coef<T>()) di = crecip(d);
         else di = X[COLOUR * PL + (y0 + r) * HS + j];
-        pc[r * HS] = xmul(di, xadd(pb[r * HS], xmul(c, s)));
+        pc[r * HS] = xmul(di, xfma(pb[r * HS], c, s));                  // d^{-1} (b + c s)
       }
     }
     up = mid;
@@ -298,14 +310,17 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
   __syncthreads();
   rb_pass<T, DW, 1, 2, DW - 3, false, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
-  // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final index)
+  // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final
+  // index), the black ones only: the up tile of this level reads no red value
   {
+    constexpr int PL = RB<DW>::PLANE;
     const int ex = (P0x + TC >= mc) ? m : 2 * P0x + FT;
     const int ey = (P0y + TC >= mc) ? m : 2 * P0y + FT;
-    for (int i = threadIdx.x; i < (FT + 1) * (FT + 1); i += NT) {
-      const int ly = i / (FT + 1), lx = i - ly * (FT + 1);
-      const int fx = 2 * P0x + lx, fy = 2 * P0y + ly;
-      if (fx < ex && fy < ey && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[rbi<DW>(lx + 3, ly + 3)];
+    for (int i = threadIdx.x; i < (FT + 1) * HS; i += NT) {
+      const int ly = i / HS, j = i - ly * HS;
+      const int wy = ly + 3, wx = 2 * j + ((wy & 1) ^ 1);
+      const int fx = ox + wx, fy = oy + wy;
+      if (wx >= 3 && fx < ex && fy < ey && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[PL + wy * HS + j];
     }
   }
   // residual at the red points of [2P0, 2P0+FT]^2 (window [3, 3+FT]).  At the
