@@ -368,3 +368,91 @@ def test_rhs_stays_finite_for_oblique_incidence_at_large_k():
     # exponents up to ~340 and phases up to ~1500 rad: both evaluations round
     # them at ~1e-16 relative, i.e. ~1e-13 relative in the values
     assert np.all(np.abs(b[fin] - prod[fin]) <= 1e-10 * np.abs(prod[fin]) + 1e-14 * np.abs(b).max())
+
+
+# ---------------------------------------------------------------------------
+# GMRES(m) smoothing step (Sec. 3.3, Tables 2-3): pinned by what GMRES is --
+# the minimiser of the residual over the shifted Krylov space -- computed here
+# by brute force, by the full-space case and by the m = 1 closed form
+# ---------------------------------------------------------------------------
+def _gmres_level(n=17, dim=2):
+    c = W.paper_gmres(dim=dim, k=1.0, n=n)
+    p = O.problem_from_dict(c["problem"])
+    return O.make_hierarchy(p, 5)[0]
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4])
+def test_gmres_step_is_the_krylov_least_squares_minimiser(m):
+    lv = _gmres_level(17)
+    shp = (lv.m,) * 2
+    u = W.rand_complex(shp, 41)
+    b = W.rand_complex(shp, 42)
+    r0 = O.residual(lv, u, b)
+    # Krylov basis r0, A r0, ..., A^{m-1} r0 (unorthogonalised) and the dense
+    # least-squares problem min_c || r0 - A K c ||
+    K = [r0]
+    for _ in range(m - 1):
+        K.append(O.apply_A(lv, K[-1]))
+    AK = np.stack([O.apply_A(lv, v).ravel() for v in K], axis=1)
+    cvec = np.linalg.lstsq(AK, r0.ravel(), rcond=None)[0]
+    x_bf = u + sum(ci * v for ci, v in zip(cvec, K))
+    x = O.gmres_smooth(lv, u, b, m)
+    assert np.abs(x - x_bf).max() <= 1e-9 * np.abs(x_bf - u).max()
+    # and its residual is no larger than that of any other point of the space
+    rng = np.random.default_rng(7)
+    rx = O.norm2(O.residual(lv, x, b))
+    for _ in range(5):
+        pert = cvec + 1e-3 * (rng.standard_normal(m) + 1j * rng.standard_normal(m)) * np.abs(cvec).max()
+        xp = u + sum(ci * v for ci, v in zip(pert, K))
+        assert rx <= O.norm2(O.residual(lv, xp, b)) * (1 + 1e-12)
+
+
+def test_gmres_over_the_whole_space_is_the_direct_solve():
+    # 9 unknowns: GMRES(9) spans the whole space, so one step solves exactly
+    c = W.paper_gmres(dim=2, k=1.0, n=5)
+    p = O.problem_from_dict(c["problem"])
+    lv = O.make_hierarchy(p, 5)[0]
+    b = W.rand_complex((3, 3), 43)
+    u0 = W.rand_complex((3, 3), 44)
+    A = O.assemble_matrix(lv).toarray()
+    x_ref = np.linalg.solve(A, b.ravel()).reshape(3, 3)
+    x = O.gmres_smooth(lv, u0, b, 9)
+    assert np.abs(x - x_ref).max() <= 1e-10 * np.abs(x_ref).max()
+
+
+def test_gmres1_is_the_minimal_residual_step():
+    # m = 1: u + a r with a = (A r, r) / (A r, A r), the one-dimensional minimiser
+    lv = _gmres_level(17)
+    shp = (lv.m,) * 2
+    u = W.rand_complex(shp, 45)
+    b = W.rand_complex(shp, 46)
+    r = O.residual(lv, u, b)
+    Ar = O.apply_A(lv, r)
+    a = np.vdot(Ar, r) / np.vdot(Ar, Ar)
+    x = O.gmres_smooth(lv, u, b, 1)
+    assert np.abs(x - (u + a * r)).max() <= 1e-12 * np.abs(a * r).max()
+
+
+def test_gmres_leaves_an_exact_solution_alone():
+    lv = _gmres_level(9)
+    x = W.rand_complex((lv.m, lv.m), 47)
+    b = O.apply_A(lv, x)
+    out = O.gmres_smooth(lv, x, b, 3)
+    assert np.abs(out - x).max() <= 1e-12 * np.abs(x).max()
+
+
+def test_gmres_vcycle_stable_where_gauss_seidel_is_not():
+    # Sec. 3.3: with omega-Jacobi / Gauss-Seidel smoothing the rotation must be
+    # at least about 13 degrees; with GMRES(m) about 10 degrees suffices.  On
+    # eq. (chi2D) at 9.9 degrees the red-black V(1,1) cycle diverges and the
+    # GMRES(3) V(1,1) cycle converges with factors in the range the paper
+    # reports for its V(1,1)/GMRES(3) runs (Table 2: 0.01-0.33).
+    c = W.paper_gmres(dim=2, k=1.0, n=65)
+    p = O.problem_from_dict(c["problem"])
+    b = O.rhs(p, c["eta"][0])
+    og = O.opts_from_dict(c["opts"])
+    rg = O.mg_solve(p, b, og)
+    assert rg.converged and rg.cycles <= 15 and rg.conv_factor <= 0.35
+    orb = O.opts_from_dict(dict(c["opts"], smoother="rbgs", max_cycles=12))
+    rr = O.mg_solve(p, b, orb)
+    assert not rr.converged and rr.history[-1] > 1.0

@@ -160,6 +160,24 @@ def paper_2d(gamma=14.6 * PI / 180, n=257):
     }
 
 
+def paper_gmres(dim=2, k=1.0, n=129):
+    """The paper's GMRES(3)-smoothed configuration (Tables 2-3): eq. (chi2D) or
+    (chi3D), k0^2 chi = -1/5 (e^{-(x^2+(y-4)^2[+z^2])} + e^{-(x^2+(y+4)^2[+z^2])}),
+    on [-20,20]^d, rotation 9.9 degrees (Table 1's value for the ECS angle
+    pi/6), eta = +x, V(1,1) cycles with GMRES(3) smoothing, 5^d coarsest grid,
+    residual reduction 1e-6."""
+    amp = -0.2 / k ** 2
+    return {
+        "name": f"paper-gmres-{dim}d-n{n}-k{k:g}",
+        "problem": problem(dim, n, 20.0, 9.9 * PI / 180, k,
+                           [gauss(amp, 1.0, (0.0, 4.0, 0.0)), gauss(amp, 1.0, (0.0, -4.0, 0.0))]),
+        "opts": {"smoother": "gmres", "krylov_m": 3, "nu1": 1, "nu2": 1, "coarsest_n": 5,
+                 "rel_tol": 1e-6, "max_cycles": 60},
+        "eta": np.array([[1.0, 0.0] if dim == 2 else [1.0, 0.0, 0.0]]),
+        "alphas": angle_set_2d(360) if dim == 2 else angle_set_3d(16, 8),
+    }
+
+
 # ---------------------------------------------------------------------------
 # Seeded random arrays
 # ---------------------------------------------------------------------------
