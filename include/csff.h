@@ -82,7 +82,9 @@ typedef struct csff_problem {
   const csff_gauss* gauss; /* host array of n_gauss terms (copied) */
 } csff_problem;
 
-enum { CSFF_SMOOTHER_JACOBI = 0, CSFF_SMOOTHER_RBGS = 1 };
+/* Smoothers (Sec. 4; GMRES(m) cycles: Sec. 3.3, Tables 2-3, for rotation
+   angles near 10 degrees where the stationary smoothers diverge). */
+enum { CSFF_SMOOTHER_JACOBI = 0, CSFF_SMOOTHER_RBGS = 1, CSFF_SMOOTHER_GMRES = 2 };
 enum { CSFF_PREC_FP64 = 0, CSFF_PREC_MIXED = 1 };
 /* Arithmetic of the per-step calls below. */
 enum { CSFF_ARITH_FP64 = 0, CSFF_ARITH_FP32 = 1 };
@@ -96,6 +98,9 @@ typedef struct csff_opts {
   int max_cycles;     /* FP64: V-cycles; MIXED: total FP32 V-cycles */
   int precision;      /* CSFF_PREC_FP64 or CSFF_PREC_MIXED */
   int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1) */
+  int krylov_m;       /* GMRES smoother: Krylov dimension m of each GMRES(m)
+                         smoothing step, 1..4 (0 selects 3); nu1 / nu2 count
+                         GMRES(m) steps.  Ignored by the other smoothers. */
 } csff_opts;
 
 #define CSFF_MAX_HISTORY 256

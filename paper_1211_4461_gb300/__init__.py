@@ -33,7 +33,7 @@ ERR_TIMEOUT = 7
 ERR_UNSUPPORTED = 8
 WARN_ILL_CONDITIONED = 100
 
-SMOOTHER = {"jacobi": 0, "rbgs": 1}
+SMOOTHER = {"jacobi": 0, "rbgs": 1, "gmres": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 ARITH_FP64, ARITH_FP32 = 0, 1
 MAX_HISTORY = 256
@@ -53,7 +53,7 @@ class ProblemC(C.Structure):
 class OptsC(C.Structure):
     _fields_ = [("smoother", C.c_int), ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarsest_n", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
-                ("precision", C.c_int), ("inner_cycles", C.c_int)]
+                ("precision", C.c_int), ("inner_cycles", C.c_int), ("krylov_m", C.c_int)]
 
 
 class InfoC(C.Structure):
@@ -219,7 +219,7 @@ def _opts_c(o):
     return OptsC(SMOOTHER[o.get("smoother", "jacobi")], float(o.get("omega", 2.0 / 3.0)), int(o.get("nu1", 1)),
                  int(o.get("nu2", 1)), int(o.get("coarsest_n", 5)), float(o.get("rel_tol", 1e-8)),
                  int(o.get("max_cycles", 100)), PRECISION[o.get("precision", "fp64")],
-                 int(o.get("inner_cycles", 3)))
+                 int(o.get("inner_cycles", 3)), int(o.get("krylov_m", 0)))
 
 
 class Batch:
@@ -340,8 +340,8 @@ class Plan:
     """A multigrid + far-field plan for one problem (csff_plan_create).
 
     problem: {"dim", "n", "lo", "hi", "gamma", "k", "gaussians": [{"amp", "width", "center"}]}
-    opts:    {"smoother", "omega", "nu1", "nu2", "coarsest_n", "rel_tol", "max_cycles",
-              "precision" ("fp64" | "mixed"), "inner_cycles"}
+    opts:    {"smoother" ("jacobi" | "rbgs" | "gmres"), "omega", "nu1", "nu2", "krylov_m",
+              "coarsest_n", "rel_tol", "max_cycles", "precision" ("fp64" | "mixed"), "inner_cycles"}
     """
 
     def __init__(self, problem: dict, opts: dict, stream=None):
@@ -358,10 +358,7 @@ class Plan:
         pc = ProblemC(self.dim, self.n, float(problem["lo"]), float(problem["hi"]), float(problem["gamma"]),
                       float(problem["k"]), len(gs), self._g)
         o = dict(opts)
-        oc = OptsC(SMOOTHER[o.get("smoother", "jacobi")], float(o.get("omega", 2.0 / 3.0)), int(o.get("nu1", 1)),
-                   int(o.get("nu2", 1)), int(o.get("coarsest_n", 5)), float(o.get("rel_tol", 1e-8)),
-                   int(o.get("max_cycles", 100)), PRECISION[o.get("precision", "fp64")],
-                   int(o.get("inner_cycles", 3)))
+        oc = _opts_c(o)
         self._stream = stream
         h = C.c_void_p()
         _check(_lib.csff_plan_create(C.byref(pc), C.byref(oc), _stream_handle(stream), C.byref(h)), "plan_create")

@@ -255,6 +255,13 @@ template <typename T>
 csff_status smooth(csff_plan* P, int l, cx<T>* u, const cx<T>* b, int sweeps) {
   Level& L = P->lv[l];
   cudaStream_t s = P->stream;
+  if (P->opts.smoother == CSFF_SMOOTHER_GMRES) {
+    for (int i = 0; i < sweeps; ++i)
+      CK(csff::launch_gmres_step<T>(P->dim, L, P->opts.krylov_m, u, b, reinterpret_cast<cx<T>*>(P->gm_v),
+                                    P->gm_part, P->red_blocks, P->gm, s),
+         "gmres");
+    return CSFF_OK;
+  }
   if (P->opts.smoother == CSFF_SMOOTHER_RBGS) {
     for (int i = 0; i < sweeps; ++i) {
       CK(csff::launch_rbgs<T>(P->dim, L, u, b, s), "rbgs");
@@ -620,6 +627,8 @@ void csff_plan_destroy(csff_plan* P) {
   if (P->red) cudaFree(P->red);
   if (P->red_out) cudaFree(P->red_out);
   if (P->red_host) cudaFreeHost(P->red_host);
+  for (void* p : {P->gm_v, (void*)P->gm_part, (void*)P->gm})
+    if (p) cudaFree(p);
   csff::free_ff_buffers(P);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->gstream) cudaStreamDestroy(P->gstream);
@@ -639,8 +648,11 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
     return invalid("n_gauss must be 0..8 with a non-NULL array");
   for (int g = 0; g < prob->n_gauss; ++g)
     if (!(prob->gauss[g].width > 0.0)) return invalid("Gaussian width must be positive");
-  if (opts->smoother != CSFF_SMOOTHER_JACOBI && opts->smoother != CSFF_SMOOTHER_RBGS)
+  if (opts->smoother != CSFF_SMOOTHER_JACOBI && opts->smoother != CSFF_SMOOTHER_RBGS &&
+      opts->smoother != CSFF_SMOOTHER_GMRES)
     return invalid("unknown smoother");
+  if (opts->smoother == CSFF_SMOOTHER_GMRES && (opts->krylov_m < 0 || opts->krylov_m > csff::GM_MAX))
+    return invalid("krylov_m must be 0..4 (0 selects 3)");
   if (opts->nu1 < 0 || opts->nu2 < 0 || opts->nu1 + opts->nu2 == 0) return invalid("need nu1 + nu2 > 0");
   if (opts->precision != CSFF_PREC_FP64 && opts->precision != CSFF_PREC_MIXED) return invalid("bad precision");
   if (!(opts->rel_tol > 0.0) || opts->max_cycles < 1) return invalid("need rel_tol > 0 and max_cycles >= 1");
@@ -664,6 +676,7 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
   P->gauss.assign(prob->gauss, prob->gauss + prob->n_gauss);
   P->prob.gauss = P->gauss.data();
   P->opts = *opts;
+  if (P->opts.smoother == CSFF_SMOOTHER_GMRES && P->opts.krylov_m == 0) P->opts.krylov_m = 3;
   P->dim = d;
   P->stream = (cudaStream_t)stream;
   auto fail = [&](csff_status s) {
@@ -732,6 +745,15 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
       return fail(s);
     e = cudaMallocHost((void**)&P->red_host, 16 * sizeof(double));
     if (e != cudaSuccess) return fail(csff::cuda_fail(e, "pinned host buffer"));
+    if (P->opts.smoother == CSFF_SMOOTHER_GMRES) {
+      double2* v = nullptr;
+      if ((s = dev_alloc(P, &v, (size_t)(P->opts.krylov_m + 1) * P->lv[0].N)) ||
+          (s = dev_alloc(P, &P->gm_part, P->red_blocks)) || (s = dev_alloc(P, &P->gm, 1))) {
+        if (v) cudaFree(v);
+        return fail(s);
+      }
+      P->gm_v = v;
+    }
   }
   // fused V(1,1) RB-GS path (2D): the levels from the first with n <= 33 run in
   // one CTA; at least one fused fine level is needed

@@ -103,6 +103,18 @@ struct FFBuffers {
   int *dtce = nullptr, *dtcflag = nullptr;
 };
 
+// Device state of one GMRES(m) smoothing step (gmres.cu): the (m+1) x m
+// Hessenberg matrix, the norms beta = nrm[0] and h_{j+1,j} = nrm[j+1] with their
+// inverses, the least-squares solution y and the number k of columns used.
+constexpr int GM_MAX = 4;
+struct GmState {
+  double2 H[GM_MAX + 1][GM_MAX];
+  double nrm[GM_MAX + 1];
+  double inv[GM_MAX + 1];
+  double2 y[GM_MAX];
+  int k;
+};
+
 }  // namespace csff
 
 struct csff_plan {
@@ -144,6 +156,11 @@ struct csff_plan {
   int learned_levels = 0;
   double learned_guard = 0.5;
   bool learned_off = false;       // per-solve fallback to plain RB-GS
+  // GMRES(m) smoother: m+1 basis vectors of the finest level (sized for FP64,
+  // shared by every level and both precisions), reduction partials, state
+  void* gm_v = nullptr;
+  double2* gm_part = nullptr;
+  csff::GmState* gm = nullptr;
 };
 
 namespace csff {
@@ -198,6 +215,13 @@ cudaError_t launch_update64(double2* u, const float2* e, long long N, const int*
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
+
+// ---- GMRES(m) smoothing step (gmres.cu) ----------------------------------------
+// u += V y for the GMRES(m) minimiser from u; V holds m+1 vectors of L.N
+// values, part at least part_cap double2 partial sums, S the step's state.
+template <typename T>
+cudaError_t launch_gmres_step(int dim, const Level& L, int m, cx<T>* u, const cx<T>* b, cx<T>* V,
+                              double2* part, int part_cap, GmState* S, cudaStream_t s);
 
 // ---- fused 2D V(1,1) RB-GS kernels (mg_fused.cu) ----------------------------
 size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int real_bytes);

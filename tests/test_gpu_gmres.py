@@ -1,0 +1,131 @@
+"""GMRES(m) smoothing (Sec. 3.3, Tables 2-3) on the GPU against the oracle.
+
+The smoothing step is compared element by element with the oracle's GMRES(m)
+cycle on the same inputs (FP64 to 1e-11 of the update, FP32 to 1e-4); the
+V(1,1)/GMRES(3) solve at 9.9 degrees is compared by residual history and
+solution, in 2D and 3D, plain FP64 and FP32-inner / FP64-refinement; and the
+red-black cycle at the same angle is shown to fail on the GPU as well."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.csff_oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def csff():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1211_4461_gb300 as m
+    return m
+
+
+def dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a).ravel()).to("cuda").to(dtype)
+
+
+def host(t, shape):
+    return t.cpu().numpy().astype(np.complex128).reshape(shape)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 33), (2, 65), (3, 17)])
+@pytest.mark.parametrize("m", [1, 3, 4])
+@pytest.mark.parametrize("dt", [torch.complex128, torch.complex64], ids=["fp64", "fp32"])
+def test_gmres_step_matches_oracle(csff, dim, n, m, dt):
+    c = W.paper_gmres(dim=dim, k=1.0, n=n)
+    c["opts"]["krylov_m"] = m
+    plan = csff.Plan(c["problem"], c["opts"])
+    p = O.problem_from_dict(c["problem"])
+    levels = O.make_hierarchy(p, 5)
+    for l in (0, 1):
+        lv = levels[l]
+        shp = (lv.m,) * dim
+        u0 = W.rand_complex(shp, 500 + l)
+        b = W.rand_complex(shp, 510 + l, scale=3.0)
+        if dt == torch.complex64:
+            u0 = u0.astype(np.complex64).astype(np.complex128)
+            b = b.astype(np.complex64).astype(np.complex128)
+        ut = dev(u0, dt)
+        plan.smooth(l, ut, dev(b, dt), sweeps=1)
+        torch.cuda.synchronize()
+        ref = O.gmres_smooth(lv, u0, b, m)
+        tol = 1e-11 if dt == torch.complex128 else 1e-4
+        assert np.abs(host(ut, shp) - ref).max() <= tol * np.abs(ref - u0).max(), (l, m)
+    plan.close()
+
+
+def test_gmres_step_with_zero_residual_is_a_no_op(csff):
+    c = W.paper_gmres(dim=2, k=1.0, n=33)
+    plan = csff.Plan(c["problem"], c["opts"])
+    u = dev(np.zeros(31 * 31))
+    plan.smooth(0, u, dev(np.zeros(31 * 31)), sweeps=2)
+    assert torch.count_nonzero(u).item() == 0
+    plan.close()
+
+
+def _solve(csff, c):
+    plan = csff.Plan(c["problem"], c["opts"])
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    st, info = plan.solve(c["eta"], u, ok=(csff.OK, csff.ERR_NOT_CONVERGED, csff.ERR_DIVERGED))
+    out = u.cpu().numpy()
+    plan.close()
+    return st, info[0], out
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, 65, 1.0), (2, 129, 2.0), (3, 33, 1.0)])
+def test_gmres_vcycle_solve_matches_oracle(csff, dim, n, k):
+    c = W.paper_gmres(dim=dim, k=k, n=n)
+    c["opts"]["rel_tol"] = 1e-9
+    st, info, u = _solve(csff, c)
+    p = O.problem_from_dict(c["problem"])
+    b = O.rhs(p, c["eta"][0])
+    res = O.mg_solve(p, b, O.opts_from_dict(c["opts"]))
+    assert st == csff.OK and res.converged
+    assert info["cycles"] == res.cycles
+    np.testing.assert_allclose(info["history"], res.history, rtol=1e-6, atol=1e-15)
+    ref = res.u.ravel()
+    assert np.linalg.norm(u - ref) <= 1e-8 * np.linalg.norm(ref)
+    # the factors of Table 2's V(1,1)/GMRES(3) runs lie in 0.01-0.33
+    assert info["conv_factor"] <= 0.35
+
+
+def test_gmres_mixed_precision_solve(csff):
+    c = W.paper_gmres(dim=2, k=2.0, n=129)
+    c["opts"].update(precision="mixed", inner_cycles=2, rel_tol=1e-8)
+    st, info, u = _solve(csff, c)
+    assert st == csff.OK and info["rel_res"] <= 1e-8
+    p = O.problem_from_dict(c["problem"])
+    b = O.rhs(p, c["eta"][0])
+    ref = O.mg_solve(p, b, O.opts_from_dict(dict(c["opts"], rel_tol=1e-11))).u.ravel()
+    assert np.linalg.norm(u - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_red_black_cycle_fails_at_the_ecs_angle_on_the_gpu(csff):
+    c = W.paper_gmres(dim=2, k=1.0, n=65)
+    c["opts"].update(smoother="rbgs", max_cycles=20)
+    st, info, _ = _solve(csff, c)
+    assert st in (csff.ERR_DIVERGED, csff.ERR_NOT_CONVERGED, csff.ERR_NONFINITE)
+    assert info["rel_res"] > 1.0 or not math.isfinite(info["rel_res"])
+
+
+def test_gmres_far_field_of_the_paper_configuration(csff):
+    c = W.paper_gmres(dim=2, k=1.0, n=129)
+    plan = csff.Plan(c["problem"], c["opts"])
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    st, info = plan.solve(c["eta"], u)
+    al = c["alphas"]
+    F = torch.zeros(len(al), dtype=torch.complex128, device="cuda")
+    E = torch.zeros(len(al), dtype=torch.int32, device="cuda")
+    plan.far_field(c["eta"], u, al, F, E)
+    got = F.cpu().numpy() * 2.0 ** E.cpu().numpy().astype(np.float64)
+    p = O.problem_from_dict(c["problem"])
+    mant, e2, tn = O.far_field(p, u.cpu().numpy().reshape(127, 127), c["eta"][0], al, return_terms_norm=True)
+    ref = O.far_field_value(mant, e2)
+    assert np.abs(got - ref).max() <= 1e-12 * (tn * 2.0 ** e2).max()
+    plan.close()
