@@ -456,3 +456,26 @@ def test_gmres_vcycle_stable_where_gauss_seidel_is_not():
     orb = O.opts_from_dict(dict(c["opts"], smoother="rbgs", max_cycles=12))
     rr = O.mg_solve(p, b, orb)
     assert not rr.converged and rr.history[-1] > 1.0
+
+
+def _table2():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table2_vcycle_gmres3.txt"))
+            if l.strip() and not l.startswith("#")]
+    return [(float(k), int(n), int(c), float(f)) for k, n, c, f in rows]
+
+
+@pytest.mark.parametrize("pts", [16, 32])
+def test_gmres_vcycle_reproduces_table2(pts):
+    # Table 2's V(1,1)/GMRES(3) cycle counts and factors on the 16^3 and 32^3
+    # grids (eq. chi3D, 9.9 degrees, 1e-6): the oracle's cycle counts agree to
+    # within two cycles and its factors to within 0.07 for every k0
+    rows = [r for r in _table2() if r[1] == pts]
+    assert len(rows) == 5
+    for k, n, cyc, fac in rows:
+        c = W.paper_gmres(dim=3, k=k, n=n + 1)
+        p = O.problem_from_dict(c["problem"])
+        b = O.rhs(p, c["eta"][0])
+        r = O.mg_solve(p, b, O.opts_from_dict(c["opts"]))
+        assert r.converged
+        assert abs(r.cycles - cyc) <= 2, (k, n, r.cycles, cyc)
+        assert abs(r.conv_factor - fac) <= 0.07, (k, n, r.conv_factor, fac)
