@@ -59,7 +59,7 @@ DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 # DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload, from
 # the ncu capture summarised in profiles/ff_stage1_df_2d_n1025.md (None once
 # the kernel changes).
-FF_DF_DRAM_BYTES = None
+FF_DF_DRAM_BYTES = 34220032 + 768
 
 
 # FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of
@@ -469,6 +469,7 @@ def measure_variants(csff, torch, dev, stream, flush):
     out["3d_257_16dirs"] = measure_3d(csff, torch, dev, stream, flush)
     out["vcycle_4097"] = measure_vcycle_bandwidth(csff, torch, dev, stream, flush)
     out["learned_2049"] = measure_learned(csff, torch, dev, stream, flush)
+    out["gmres3_table2"] = measure_gmres_table2(csff, torch, dev, stream, flush)
     return out
 
 
@@ -672,6 +673,45 @@ def measure_learned_small(csff, torch, dev, stream):
     net.close()
     return {"loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:])), "held_out": rows,
             "cycle_ratio": sum(r["learned"] for r in rows) / max(1, sum(r["classical"] for r in rows))}
+
+
+def measure_gmres_table2(csff, torch, dev, stream, flush):
+    """The paper's V(1,1)/GMRES(3) configuration of Table 2 (eq. chi3D on
+    [-20,20]^3, rotation 9.9 degrees, residual reduction 1e-6, FP64) on the
+    64^3, 128^3 and 256^3 grids for k0 = 1/4 ... 4: V-cycles, average
+    convergence factor and time per solve, beside the values Table 2 prints
+    (tests/golden/table2_vcycle_gmres3.txt).  At this angle the red-black
+    V-cycle diverges (checked in the tests)."""
+    gold = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "table2_vcycle_gmres3.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, pts, cyc, fac = line.split()
+            gold[(float(k), int(pts))] = (int(cyc), float(fac))
+    out = {}
+    for pts in (64, 128, 256):
+        rows = []
+        for k in (0.25, 0.5, 1.0, 2.0, 4.0):
+            c = W.paper_gmres(dim=3, k=k, n=pts + 1)
+            plan = csff.Plan(c["problem"], c["opts"], stream=stream)
+            u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
+            info = {}
+
+            def solve():
+                _, inf = plan.solve(c["eta"], u)
+                info["i"] = inf[0]
+
+            solve()
+            ms = _time_events(torch, stream, solve, flush, 2)
+            i = info["i"]
+            pc, pf = gold[(k, pts)]
+            rows.append({"k0": k, "cycles": i["cycles"], "conv_factor": round(i["conv_factor"], 3),
+                         "paper_cycles": pc, "paper_factor": pf, "ms_per_solve": ms,
+                         "converged": i["rel_res"] <= c["opts"]["rel_tol"]})
+            plan.close()
+            del u
+        out[f"{pts}^3"] = rows
+    return out
 
 
 def main():

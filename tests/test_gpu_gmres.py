@@ -129,3 +129,19 @@ def test_gmres_far_field_of_the_paper_configuration(csff):
     ref = O.far_field_value(mant, e2)
     assert np.abs(got - ref).max() <= 1e-12 * (tn * 2.0 ** e2).max()
     plan.close()
+
+
+def test_gmres_vcycle_on_the_64_cubed_grid_against_table2(csff):
+    # Table 2's 64^3 column (eq. chi3D, 9.9 degrees, 1e-6): cycle counts within
+    # two and factors within 0.07 of the printed values for every k0
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_vcycle_gmres3.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    rows = [(float(k), int(n), int(c), float(f)) for k, n, c, f in rows if int(n) == 64]
+    assert len(rows) == 5
+    for k, n, cyc, fac in rows:
+        c = W.paper_gmres(dim=3, k=k, n=n + 1)
+        st, info, _ = _solve(csff, c)
+        assert st == csff.OK
+        assert abs(info["cycles"] - cyc) <= 2, (k, info["cycles"], cyc)
+        assert abs(info["conv_factor"] - fac) <= 0.07, (k, info["conv_factor"], fac)
