@@ -178,6 +178,30 @@ def paper_gmres(dim=2, k=1.0, n=129):
     }
 
 
+def partial_wave(E, n=257, R=15.0, gamma=8.5 * PI / 180):
+    """Sec. 5.2-5.3 partial-wave model along the rotated contour: V1(x) =
+    -4.5 e^{-x^2}, V2(y) = -4.5 e^{-y^2}, V12 = 2 e^{-(x+y)^2}, phi =
+    e^{-3(x+y)^2} on [0, R]^2 (R = 15), rotation 8.5 degrees, energy E.
+    Samples at the interior nodes z = i h e^{i gamma} (x fastest): q = 2E -
+    2(V1 + V2 + V12), the right-hand side 2 phi, phi, V12 and V1 along one
+    axis; plan options for V(1,1) cycles with GMRES(3) smoothing."""
+    h = R / (n - 1)
+    z = np.arange(1, n - 1) * h * np.exp(1j * gamma)
+    zy, zx = np.meshgrid(z, z, indexing="ij")
+    v_one = -4.5 * np.exp(-z * z)
+    w12 = 2.0 * np.exp(-(zx + zy) ** 2)
+    V = -4.5 * np.exp(-zx * zx) - 4.5 * np.exp(-zy * zy) + w12
+    ph = np.exp(-3.0 * (zx + zy) ** 2)
+    return {
+        "name": f"partial-wave-n{n}-E{E:g}",
+        "problem": problem(2, n, R, gamma, 1.0, []) | {"lo": 0.0, "hi": float(R)},
+        "opts": {"smoother": "gmres", "krylov_m": 3, "nu1": 1, "nu2": 1, "coarsest_n": 5,
+                 "rel_tol": 1e-10, "max_cycles": 200},
+        "h": h, "gamma": gamma, "E": E,
+        "q": 2.0 * E - 2.0 * V, "b": 2.0 * ph, "f": ph, "w": w12, "v1": v_one,
+    }
+
+
 # ---------------------------------------------------------------------------
 # Seeded random arrays
 # ---------------------------------------------------------------------------
