@@ -196,6 +196,66 @@ csff_status csff_far_field(csff_plan* plan, int n_rhs, const double* eta_host, c
 enum { CSFF_FF_FP64 = 0, CSFF_FF_TC_BF16X3 = 1 };
 csff_status csff_plan_set_far_field_mode(csff_plan* plan, int mode);
 
+/* ---- user coefficients and right-hand sides (Sec. 5.2-5.3) ---------------
+   The partial-wave Schroedinger problem (-1/2 Delta + V - E) u = phi along the
+   rotated contour is, times 2, the plan's operator A u = c (2d u - sum_nbr u)
+   - q u with q = 2E - 2V and right-hand side 2 phi; its potentials are not
+   Gaussians of the kind csff_problem describes, so they are given as samples. */
+
+/* Replace the plan's q = k^2 (1 + chi) by samples of q at the finest level's
+   interior nodes (q_dev: device, complex128, m^d values, x fastest; read
+   during the call).  Coarser levels take q at their nodes (injection: coarse
+   nodes are fine nodes), 1/d and the FP32 copies are rebuilt and the coarsest
+   inverse is formed again (FP64 Gauss-Jordan on the host).  From then on
+   V-cycles use the per-level kernels (the fused FP32 tiles form q from the
+   Gaussian factors).  csff_rhs / csff_solve keep forming the Gaussian
+   right-hand side; use csff_solve_rhs.  Errors: CSFF_ERR_INVALID_ARG for NULL
+   arguments or a singular coarsest operator, CSFF_ERR_CUDA. */
+csff_status csff_plan_set_potential(csff_plan* plan, const void* q_dev);
+
+/* Solve A u = b for one right-hand side b_dev (device, complex128, m^d
+   values, read only) into u_dev (device, complex128, m^d; the initial guess
+   when use_guess != 0, else ignored), with the plan's smoother, precision and
+   tolerance; info (host, may be NULL) as for csff_solve.  Returns the solve's
+   status (CSFF_ERR_NOT_CONVERGED, CSFF_ERR_DIVERGED, CSFF_ERR_NONFINITE are
+   reported with u holding the last iterate). */
+csff_status csff_solve_rhs(csff_plan* plan, const void* b_dev, void* u_dev, int use_guess, csff_info* info);
+
+/* One-dimensional functions along the contour z_i = i h e^{i gamma},
+   i = 1 .. m (zero at i = 0 and i = m + 1), with the three-point stencil of
+   -1/2 d^2/dz^2; v (host, 2m doubles, interleaved re/im) holds V(z_i).
+
+   Bound state of eq. (boundstate), (-1/2 d^2/dz^2 + V) phi = lambda phi: the
+   eigenpair nearest lambda_guess, by inverse iteration with the fixed shift
+   followed by Rayleigh-quotient updates (bilinear form, no conjugate: the
+   contour operator is complex symmetric).  phi (host, 2m doubles) is scaled
+   so that sum_i phi_i^2 h e^{i gamma} = 1 and its largest entry has a
+   non-negative real part; lambda (host, 2 doubles).  Errors:
+   CSFF_ERR_INVALID_ARG, CSFF_ERR_NOT_CONVERGED after 200 steps. */
+csff_status csff_contour_bound_state(int m, double h, double gamma, const double* v, double lambda_guess,
+                                     double* lambda, double* phi);
+
+/* Regular solution of eq. (testfunction), (-1/2 d^2/dz^2 + V - k^2/2) phi = 0
+   with phi = 0 at z = 0, by the recurrence of the discrete equation, scaled
+   to sin(kappa z + delta) / sqrt(k) where |V| < tail (kappa: the discrete
+   wavenumber, cos(kappa h e^{i gamma}) = 1 - (k h e^{i gamma})^2 / 2; the
+   scale is fitted at the first two such nodes).  phi: host, 2m doubles.
+   Errors: CSFF_ERR_INVALID_ARG (also when |V| never falls below tail). */
+csff_status csff_contour_regular_solution(int m, double h, double gamma, const double* v, double k, double tail,
+                                          double* phi);
+
+/* Separable contour integrals of eqs. (single-ionization) and
+   (double-ionization) on a 2D plan:
+     out[r] = e^{2 i gamma} h^2 sum_{j,i} X[r][i] Y[r][j] (f - w u)[j][i],
+   r < n_rows, i the x index and j the y index of the finest level's interior
+   nodes.  X, Y: device, complex128, n_rows x m, row-major; f, w, u: device,
+   complex128, m x m (x fastest); w and u both NULL means the integrand f;
+   out: device, complex128, n_rows.  Runs on the plan's stream (FP64).
+   Errors: CSFF_ERR_INVALID_ARG (3D plan, NULL buffers, only one of w, u),
+   CSFF_ERR_CUDA. */
+csff_status csff_separable_sum(csff_plan* plan, int n_rows, const void* X, const void* Y, const void* f,
+                               const void* w, const void* u, void* out);
+
 /* ---- per-step calls (one kernel each; for verification and custom cycles) --
    arith: CSFF_ARITH_FP64 (c128 buffers) or CSFF_ARITH_FP32 (c64 buffers).
    level: 0 = finest.  All buffers are device pointers of m_level^d elements

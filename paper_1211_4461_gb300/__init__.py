@@ -125,6 +125,11 @@ _SIGS = {
     "csff_plan_copy_coefficients": (_i, [_vp, _i, _vp, _dp]),
     "csff_prof_begin": (_i, [C.c_uint]),
     "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
+    "csff_plan_set_potential": (_i, [_vp, _vp]),
+    "csff_solve_rhs": (_i, [_vp, _vp, _vp, _i, C.POINTER(InfoC)]),
+    "csff_contour_bound_state": (_i, [_i, _d, _d, _dp, _d, _dp, _dp]),
+    "csff_contour_regular_solution": (_i, [_i, _d, _d, _dp, _d, _d, _dp]),
+    "csff_separable_sum": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -336,6 +341,32 @@ class Net:
         return loss.value
 
 
+def contour_bound_state(v, h, gamma, lambda_guess):
+    """Bound state nearest lambda_guess of -1/2 d^2/dz^2 + V along the contour
+    (csff_contour_bound_state); v: complex samples V(z_i), i = 1..m.
+    Returns (lambda, phi) as (complex, complex128 numpy array)."""
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.complex128))
+    m = v.shape[0]
+    lam = np.zeros(2)
+    phi = np.zeros(2 * m)
+    _check(_lib.csff_contour_bound_state(m, float(h), float(gamma), v.view(np.float64).ctypes.data_as(_dp),
+                                         float(lambda_guess), lam.ctypes.data_as(_dp), phi.ctypes.data_as(_dp)),
+           "contour_bound_state")
+    return complex(lam[0], lam[1]), phi.view(np.complex128)
+
+
+def contour_regular_solution(v, h, gamma, k, tail=1e-15):
+    """Regular solution of (-1/2 d^2/dz^2 + V - k^2/2) phi = 0 along the contour,
+    scaled to sin(kappa z + delta)/sqrt(k) (csff_contour_regular_solution)."""
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.complex128))
+    m = v.shape[0]
+    phi = np.zeros(2 * m)
+    _check(_lib.csff_contour_regular_solution(m, float(h), float(gamma), v.view(np.float64).ctypes.data_as(_dp),
+                                              float(k), float(tail), phi.ctypes.data_as(_dp)),
+           "contour_regular_solution")
+    return phi.view(np.complex128)
+
+
 class Plan:
     """A multigrid + far-field plan for one problem (csff_plan_create).
 
@@ -474,3 +505,31 @@ class Plan:
 
     def vcycle(self, u, b):
         _check(_lib.csff_vcycle(self._h, self._arith(u), _ptr(u), _ptr(b)), "vcycle")
+
+    def set_potential(self, q):
+        """q: complex128 CUDA tensor of m^d samples of q (csff_plan_set_potential)."""
+        import torch
+        _require(q, torch.complex128, self.N, "q")
+        _check(_lib.csff_plan_set_potential(self._h, _ptr(q)), "plan_set_potential")
+
+    def solve_rhs(self, b, u, use_guess=False, ok=(OK,)):
+        """Solve A u = b (complex128 CUDA tensors of m^d); returns (status, info)."""
+        import torch
+        _require(b, torch.complex128, self.N, "b")
+        _require(u, torch.complex128, self.N, "u")
+        info = InfoC()
+        st = _lib.csff_solve_rhs(self._h, _ptr(b), _ptr(u), int(bool(use_guess)), C.byref(info))
+        _check(st, "solve_rhs", ok)
+        return st, info.as_dict()
+
+    def separable_sum(self, X, Y, f, w=None, u=None, out=None):
+        """out[r] = e^{2 i gamma} h^2 sum X[r,i] Y[r,j] (f - w u)[j,i] (csff_separable_sum);
+        X, Y: complex128 CUDA (n_rows, m); f, w, u: complex128 CUDA m^2."""
+        import torch
+        n = X.shape[0]
+        if out is None:
+            out = torch.empty(n, dtype=torch.complex128, device=X.device)
+        _check(_lib.csff_separable_sum(self._h, n, _ptr(X), _ptr(Y), _ptr(f),
+                                       _ptr(w) if w is not None else None, _ptr(u) if u is not None else None,
+                                       _ptr(out)), "separable_sum")
+        return out

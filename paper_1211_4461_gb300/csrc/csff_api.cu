@@ -155,7 +155,9 @@ std::vector<float2> fp32_factors(const csff_plan* P, const std::vector<double2>&
 }
 
 // Dense inverse of the coarsest operator by LU with partial pivoting.
-bool coarse_inverse(const csff_plan* P, const Level& L, std::vector<double2>& out) {
+// qv: the coarsest level's q from user samples (else formed from the Gaussians)
+bool coarse_inverse(const csff_plan* P, const Level& L, std::vector<double2>& out,
+                    const std::vector<double2>* qv = nullptr) {
   const int d = P->dim, m = L.m;
   const int N = (d == 3) ? m * m * m : m * m;
   std::vector<double2> tab = chi_tables(P, L.n);
@@ -175,7 +177,7 @@ bool coarse_inverse(const csff_plan* P, const Level& L, std::vector<double2>& ou
           chi += v;
         }
         int r = id(ix, iy, iz);
-        A[(size_t)r * N + r] = 2.0 * d * c - k2 * (1.0 + chi);
+        A[(size_t)r * N + r] = qv ? 2.0 * d * c - cd((*qv)[r].x, (*qv)[r].y) : 2.0 * d * c - k2 * (1.0 + chi);
         int nb[6][3] = {{ix - 1, iy, iz}, {ix + 1, iy, iz}, {ix, iy - 1, iz},
                         {ix, iy + 1, iz}, {ix, iy, iz - 1}, {ix, iy, iz + 1}};
         for (int q = 0; q < 2 * d; ++q) {
@@ -627,7 +629,7 @@ void csff_plan_destroy(csff_plan* P) {
   if (P->red) cudaFree(P->red);
   if (P->red_out) cudaFree(P->red_out);
   if (P->red_host) cudaFreeHost(P->red_host);
-  for (void* p : {P->gm_v, (void*)P->gm_part, (void*)P->gm})
+  for (void* p : {P->gm_v, (void*)P->gm_part, (void*)P->gm, (void*)P->sep_T})
     if (p) cudaFree(p);
   csff::free_ff_buffers(P);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
@@ -856,6 +858,8 @@ csff_status csff_rhs(csff_plan* P, int n_rhs, const double* eta, void* b_dev) {
   return CSFF_OK;
 }
 
+static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_info* in);
+
 csff_status csff_solve(csff_plan* P, int n_rhs, const double* eta, void* u_dev, int use_guess, csff_info* info) {
   if (!P || !eta || !u_dev || n_rhs < 0) return invalid("bad solve arguments");
   Level& L = P->lv[0];
@@ -864,46 +868,86 @@ csff_status csff_solve(csff_plan* P, int n_rhs, const double* eta, void* u_dev, 
     double2* u = (double2*)u_dev + (size_t)r * L.N;
     csff_info* in = info ? info + r : nullptr;
     CS(csff_rhs(P, 1, eta + (size_t)r * P->dim, L.b64));
-    if (!use_guess) CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
-    // ||b|| with a power-of-two prescale taken from max |b|
-    int* ex = reinterpret_cast<int*>(P->red_out + 4);
-    CK(csff::launch_max_exp(L.b64, L.N, ex, P->stream), "max exponent");
-    int eb = 0;
-    CK(cudaMemcpyAsync(&eb, ex, sizeof(int), cudaMemcpyDeviceToHost, P->stream), "read exponent");
-    CK(cudaStreamSynchronize(P->stream), "sync");
-    if (eb >= 4000) {
-      csff::set_error("right-hand side is not finite");
-      if (in) { std::memset(in, 0, sizeof(*in)); in->status = CSFF_ERR_NONFINITE; }
-      worst = worse(worst, CSFF_ERR_NONFINITE);
-      continue;
-    }
-    if (eb <= -2000) eb = 0;
-    CS(norm64(P, L.b64, eb, 1));
-    CS(read_scalars(P, 2));
-    double nb = P->red_host[1];
-    csff_status st;
-    if (nb == 0.0) {
-      CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
-      if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
-      st = CSFF_OK;
-    } else {
-      if (use_guess)
-        CK(cudaMemcpyAsync(L.u64, u, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
-      else
-        CK(csff::launch_zero<double>(L.u64, L.N, P->stream), "zero");
-      st = (P->opts.precision == CSFF_PREC_FP64) ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in);
-      if (P->net && P->opts.precision != CSFF_PREC_FP64) {
-        const csff_status nst = csff::net_check(P->net);
-        if (nst != CSFF_OK) st = nst;
-      }
-      if (st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)
-        CK(cudaMemcpyAsync(u, L.u64, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
-    }
+    const csff_status st = solve_loaded(P, u, use_guess, in);
     if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;
-    if (in) in->status = st;
     worst = worse(worst, st);
   }
   return (csff_status)worst;
+}
+
+// Solve A u = b for the right-hand side already in level 0's b64; u (the
+// caller's buffer) holds the guess when use_guess and receives the solution.
+static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_info* in) {
+  Level& L = P->lv[0];
+  if (!use_guess) CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
+  // ||b|| with a power-of-two prescale taken from max |b|
+  int* ex = reinterpret_cast<int*>(P->red_out + 4);
+  CK(csff::launch_max_exp(L.b64, L.N, ex, P->stream), "max exponent");
+  int eb = 0;
+  CK(cudaMemcpyAsync(&eb, ex, sizeof(int), cudaMemcpyDeviceToHost, P->stream), "read exponent");
+  CK(cudaStreamSynchronize(P->stream), "sync");
+  if (eb >= 4000) {
+    csff::set_error("right-hand side is not finite");
+    if (in) { std::memset(in, 0, sizeof(*in)); in->status = CSFF_ERR_NONFINITE; }
+    return CSFF_ERR_NONFINITE;
+  }
+  if (eb <= -2000) eb = 0;
+  CS(norm64(P, L.b64, eb, 1));
+  CS(read_scalars(P, 2));
+  double nb = P->red_host[1];
+  csff_status st;
+  if (nb == 0.0) {
+    CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
+    if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
+    st = CSFF_OK;
+  } else {
+    if (use_guess)
+      CK(cudaMemcpyAsync(L.u64, u, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
+    else
+      CK(csff::launch_zero<double>(L.u64, L.N, P->stream), "zero");
+    st = (P->opts.precision == CSFF_PREC_FP64) ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in);
+    if (P->net && P->opts.precision != CSFF_PREC_FP64) {
+      const csff_status nst = csff::net_check(P->net);
+      if (nst != CSFF_OK) st = nst;
+    }
+    if (st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)
+      CK(cudaMemcpyAsync(u, L.u64, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
+  }
+  if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;
+  if (in) in->status = st;
+  return st;
+}
+
+csff_status csff_solve_rhs(csff_plan* P, const void* b_dev, void* u_dev, int use_guess, csff_info* info) {
+  if (!P || !b_dev || !u_dev) return invalid("bad solve arguments");
+  Level& L = P->lv[0];
+  CK(cudaMemcpyAsync(L.b64, b_dev, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy rhs");
+  return solve_loaded(P, (double2*)u_dev, use_guess, info);
+}
+
+csff_status csff_plan_set_potential(csff_plan* P, const void* q_dev) {
+  if (!P || !q_dev) return invalid("bad potential arguments");
+  cudaStream_t s = P->stream;
+  CK(cudaMemcpyAsync(P->lv[0].q64, q_dev, sizeof(double2) * (size_t)P->lv[0].N, cudaMemcpyDeviceToDevice, s),
+     "copy potential");
+  for (size_t l = 1; l < P->lv.size(); ++l) CK(csff::launch_inject_q(P->dim, P->lv[l - 1], P->lv[l], s), "inject q");
+  for (const Level& L : P->lv) CK(csff::launch_coefs_from_q(P->dim, L, s), "coefficients");
+  const Level& Lc = P->lv.back();
+  std::vector<double2> qc((size_t)Lc.N);
+  CK(cudaMemcpyAsync(qc.data(), Lc.q64, sizeof(double2) * qc.size(), cudaMemcpyDeviceToHost, s), "read q");
+  CK(cudaStreamSynchronize(s), "sync");
+  std::vector<double2> inv;
+  if (!coarse_inverse(P, Lc, inv, &qc)) return invalid("coarsest operator is singular");
+  std::vector<float2> inv32(inv.size());
+  for (size_t i = 0; i < inv.size(); ++i) inv32[i] = make_float2((float)inv[i].x, (float)inv[i].y);
+  CK(cudaMemcpy(P->coarse_inv, inv.data(), sizeof(double2) * inv.size(), cudaMemcpyHostToDevice), "upload inverse");
+  CK(cudaMemcpy(P->coarse_inv32, inv32.data(), sizeof(float2) * inv32.size(), cudaMemcpyHostToDevice),
+     "upload inverse");
+  // the fused FP32 tiles form q from the Gaussian factors: per-level kernels from now on
+  P->fused_lc = -1;
+  P->user_q = true;
+  if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+  return CSFF_OK;
 }
 
 csff_status csff_far_field(csff_plan* P, int n_rhs, const double* eta, const void* u_dev, int n_ang,

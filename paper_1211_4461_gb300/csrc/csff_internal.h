@@ -161,6 +161,11 @@ struct csff_plan {
   void* gm_v = nullptr;
   double2* gm_part = nullptr;
   csff::GmState* gm = nullptr;
+  // coefficients from user samples (csff_plan_set_potential) and the scratch
+  // of csff_separable_sum
+  bool user_q = false;
+  double2* sep_T = nullptr;
+  size_t sep_cap = 0;
 };
 
 namespace csff {
@@ -215,6 +220,11 @@ cudaError_t launch_update64(double2* u, const float2* e, long long N, const int*
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
+
+// q_c = q_f at the coarse nodes (injection), then 1/d, q and 1/d in FP32 from
+// each level's q64 (csff_plan_set_potential)
+cudaError_t launch_inject_q(int dim, const Level& F, const Level& C, cudaStream_t s);
+cudaError_t launch_coefs_from_q(int dim, const Level& L, cudaStream_t s);
 
 // ---- GMRES(m) smoothing step (gmres.cu) ----------------------------------------
 // u += V y for the GMRES(m) minimiser from u; V holds m+1 vectors of L.N

@@ -262,6 +262,30 @@ __global__ void k_coefs(TabPtrs tabs, int n_gauss, int m, double k2, double2 c, 
   dinv32[idx] = make_float2((float)di.x, (float)di.y);
 }
 
+// coarse q at the coarse nodes, which are fine nodes 2 I + 1 per axis
+template <int D>
+__global__ void k_inject_q(const double2* __restrict__ qf, int mf, double2* __restrict__ qc, int mc) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(mc, ix, iy, iz, idx)) return;
+  const long long f = ((long long)(D == 3 ? 2 * iz + 1 : 0) * mf + 2 * iy + 1) * mf + 2 * ix + 1;
+  qc[idx] = qf[f];
+}
+
+// 1/d = 1/(2d c - q) and the FP32 copies from a level's q64
+template <int D>
+__global__ void k_coefs_from_q(const double2* __restrict__ q64, int m, double2 c, double2* dinv64, float2* q32,
+                               float2* dinv32) {
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
+  const double2 q = q64[idx];
+  const double2 dg = make_double2(2 * D * c.x - q.x, 2 * D * c.y - q.y);
+  const double den = dg.x * dg.x + dg.y * dg.y;
+  const double2 di = make_double2(dg.x / den, -dg.y / den);
+  dinv64[idx] = di;
+  q32[idx] = make_float2((float)q.x, (float)q.y);
+  dinv32[idx] = make_float2((float)di.x, (float)di.y);
+}
+
 template <int D>
 __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uinc, int m, double k2,
                       double2* __restrict__ b) {
@@ -491,6 +515,22 @@ cudaError_t launch_update64(double2* u, const float2* e, long long N, const int*
   cudaError_t err = launch_pdl(k_update64, dim3(flat_blocks(N)), dim3(256), 0, s, u, e, N, exp_in);
   count_launch();
   return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+cudaError_t launch_inject_q(int dim, const Level& F, const Level& C, cudaStream_t s) {
+  dim3 g = grid_of(dim, C.m), blk(BX, BY);
+  if (dim == 2) k_inject_q<2><<<g, blk, 0, s>>>(F.q64, F.m, C.q64, C.m);
+  else k_inject_q<3><<<g, blk, 0, s>>>(F.q64, F.m, C.q64, C.m);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coefs_from_q(int dim, const Level& L, cudaStream_t s) {
+  dim3 g = grid_of(dim, L.m), blk(BX, BY);
+  if (dim == 2) k_coefs_from_q<2><<<g, blk, 0, s>>>(L.q64, L.m, L.c, L.dinv64, L.q32, L.dinv32);
+  else k_coefs_from_q<3><<<g, blk, 0, s>>>(L.q64, L.m, L.c, L.dinv64, L.q32, L.dinv32);
+  count_launch();
+  return cudaGetLastError();
 }
 
 template <typename T>
