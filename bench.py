@@ -470,6 +470,7 @@ def measure_variants(csff, torch, dev, stream, flush):
     out["vcycle_4097"] = measure_vcycle_bandwidth(csff, torch, dev, stream, flush)
     out["learned_2049"] = measure_learned(csff, torch, dev, stream, flush)
     out["gmres3_table2"] = measure_gmres_table2(csff, torch, dev, stream, flush)
+    out["partial_wave_fig8"] = measure_partial_wave(csff, torch, dev, stream, flush)
     return out
 
 
@@ -711,6 +712,74 @@ def measure_gmres_table2(csff, torch, dev, stream, flush):
             plan.close()
             del u
         out[f"{pts}^3"] = rows
+    return out
+
+
+def measure_partial_wave(csff, torch, dev, stream, flush):
+    """Fig. 8's cross-section curve along the contour (Sec. 5.2-5.3): for each
+    energy of the figure's contour points above the threshold, the 2D
+    partial-wave problem on [0,15]^2 (513^2 nodes, rotation 8.5 degrees) is
+    solved by V(1,1)/GMRES(3) cycles (FP64, 1e-10; an energy whose cycles
+    diverge is reported as such, as Fig. 9 reports for -1 < E < 0) with its potential and
+    right-hand side given as samples, the 1D bound state and regular
+    solutions come from the library, and the single and double ionization
+    integrals (1 + 32 angles) run on the device.  Reports the time per energy
+    and the cross sections beside the printed ones (readings: single 4|s_0|^2,
+    double (4/pi) int |f|^2 k1 k2 da)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "fig8_cross_sections_contour.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    rows = [(float(a), float(b), float(c)) for a, b, c in rows][1:]
+    n, n_al = 513, 32
+    m = n - 2
+    al = (np.arange(n_al) + 0.5) * (math.pi / 2) / n_al
+    out = {"grid": f"{n}^2 on [0,15]^2, rotation 8.5 deg", "energies": []}
+    t_all = 0.0
+    for E, ps, pd in rows:
+        c = W.partial_wave(E, n=n)
+        c["opts"].update(rel_tol=1e-10, max_cycles=100)
+        plan = csff.Plan(c["problem"], c["opts"], stream=stream)
+        q, b, f, w = (torch.from_numpy(np.ascontiguousarray(x).ravel()).to(dev) for x in (c["q"], c["b"], c["f"], c["w"]))
+        u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
+        res = {}
+
+        def run():
+            plan.set_potential(q)
+            st, info = plan.solve_rhs(b, u, ok=(csff.OK, csff.ERR_DIVERGED, csff.ERR_NOT_CONVERGED))
+            g = c["gamma"]
+            lam, phi0 = csff.contour_bound_state(c["v1"], c["h"], g, -1.0)
+            kn = math.sqrt(2.0 * (E - lam.real))
+            X = [csff.contour_regular_solution(c["v1"], c["h"], g, kn)]
+            Y = [phi0]
+            if E > 0:
+                k = math.sqrt(2.0 * E)
+                for a in al:
+                    X.append(csff.contour_regular_solution(c["v1"], c["h"], g, k * math.sin(a)))
+                    Y.append(csff.contour_regular_solution(c["v1"], c["h"], g, k * math.cos(a)))
+            Xd = torch.from_numpy(np.ascontiguousarray(np.stack(X))).to(dev)
+            Yd = torch.from_numpy(np.ascontiguousarray(np.stack(Y))).to(dev)
+            amp = plan.separable_sum(Xd, Yd, f, w, u).cpu().numpy()
+            res.update(st=st, info=info, amp=amp)
+
+        run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        t_all += dt
+        amp = res["amp"]
+        single = 4.0 * abs(amp[0]) ** 2
+        double = 0.0
+        if E > 0:
+            k2 = 2.0 * E
+            double = (4.0 / math.pi) * float(np.sum(np.abs(amp[1:]) ** 2 * k2 * np.sin(al) * np.cos(al))) \
+                * (math.pi / 2) / n_al
+        out["energies"].append({"E": E, "cycles": res["info"]["cycles"], "conv_factor": round(res["info"]["conv_factor"], 3),
+                                "converged": res["st"] == csff.OK, "single": single, "paper_single": ps,
+                                "double": double, "paper_double": pd, "ms": dt * 1e3})
+        plan.close()
+    out["s_per_curve"] = t_all
     return out
 
 
