@@ -38,7 +38,8 @@
  *   - A plan is not thread-safe; distinct plans are independent.
  *   - chi must be analytic for the contour rotation to be valid (Sec. 2.3,
  *     Sec. 3.1); the library takes chi as a sum of Gaussians and cannot check
- *     analyticity of anything else.
+ *     analyticity of anything else (coefficients given as samples through
+ *     csff_plan_set_potential are the caller's responsibility).
  */
 #ifndef CSFF_H
 #define CSFF_H
@@ -195,6 +196,16 @@ csff_status csff_far_field(csff_plan* plan, int n_rhs, const double* eta_host, c
    Errors: CSFF_ERR_INVALID_ARG for an unknown mode. */
 enum { CSFF_FF_FP64 = 0, CSFF_FF_TC_BF16X3 = 1 };
 csff_status csff_plan_set_far_field_mode(csff_plan* plan, int mode);
+
+/* The 2D far field's stage-1 contraction skips the 32-node blocks whose
+   terms, bounded through per-block exponents, stay below 2^-55 of the sum of
+   the magnitudes of each far-field value's terms (Sec. 3.3: on the rotated
+   contour the terms span hundreds of orders of magnitude, so most blocks of a
+   large-k map are negligible).  *executed (host) receives the fraction of the
+   contraction's work the plan's last 2D far field carried out (1 for 3D
+   plans, for the FP64 range-fallback kernel, or before any far field).
+   Synchronises the plan's stream.  Errors: CSFF_ERR_INVALID_ARG, CSFF_ERR_CUDA. */
+csff_status csff_far_field_work(csff_plan* plan, double* executed);
 
 /* ---- user coefficients and right-hand sides (Sec. 5.2-5.3) ---------------
    The partial-wave Schroedinger problem (-1/2 Delta + V - E) u = phi along the

@@ -126,6 +126,7 @@ _SIGS = {
     "csff_prof_begin": (_i, [C.c_uint]),
     "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
     "csff_plan_set_potential": (_i, [_vp, _vp]),
+    "csff_far_field_work": (_i, [_vp, _dp]),
     "csff_solve_rhs": (_i, [_vp, _vp, _vp, _i, C.POINTER(InfoC)]),
     "csff_contour_bound_state": (_i, [_i, _d, _d, _dp, _d, _dp, _dp]),
     "csff_contour_regular_solution": (_i, [_i, _d, _d, _dp, _d, _d, _dp]),
@@ -505,6 +506,13 @@ class Plan:
 
     def vcycle(self, u, b):
         _check(_lib.csff_vcycle(self._h, self._arith(u), _ptr(u), _ptr(b)), "vcycle")
+
+    def far_field_work(self) -> float:
+        """Fraction of the 2D far-field contraction the last far field computed
+        (csff_far_field_work; the rest was negligible and skipped)."""
+        out = C.c_double()
+        _check(_lib.csff_far_field_work(self._h, C.byref(out)), "far_field_work")
+        return out.value
 
     def set_potential(self, q):
         """q: complex128 CUDA tensor of m^d samples of q (csff_plan_set_potential)."""

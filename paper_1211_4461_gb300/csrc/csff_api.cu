@@ -966,6 +966,11 @@ csff_status csff_far_field(csff_plan* P, int n_rhs, const double* eta, const voi
   return any_scaled ? CSFF_WARN_ILL_CONDITIONED : CSFF_OK;
 }
 
+csff_status csff_far_field_work(csff_plan* P, double* executed) {
+  if (!P || !executed) return invalid("bad far-field work arguments");
+  return csff::far_field_executed(P, executed);
+}
+
 csff_status csff_plan_set_far_field_mode(csff_plan* P, int mode) {
   if (!P || (mode != CSFF_FF_FP64 && mode != CSFF_FF_TC_BF16X3)) return invalid("bad far-field mode");
   P->ff_mode = mode;

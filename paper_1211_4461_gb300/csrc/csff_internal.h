@@ -96,6 +96,11 @@ struct FFBuffers {
   float4 *dxdf = nullptr, *dgdf = nullptr;
   float2 *dxsm = nullptr, *dgsm = nullptr;   // re + im of the split operands
   int *dex = nullptr, *deg = nullptr, *dspread = nullptr;
+  // block bounds for skipping negligible blocks and the per-tile skip flags
+  size_t xlo = 0, ghi = 0, skip = 0;
+  int *dxlo = nullptr, *dghi = nullptr;
+  unsigned char* dskip = nullptr;
+  size_t skip_used = 0;       // flags written by the last 2D far field
   // tensor-core 3D stage A: pre-swizzled split phase operand, per-column and
   // per-row exponents, [spread_g, spread_P, error word]
   size_t tcb = 0, tce = 0;
@@ -258,6 +263,7 @@ csff_status net_check(csff_net* N);
 
 // ---- far field (farfield.cu) -----------------------------------------------
 void free_ff_buffers(csff_plan* P);
+csff_status far_field_executed(csff_plan* P, double* executed);
 csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u, int n_ang,
                           const double* alpha_host, double2* F, int32_t* F_exp, bool* scaled);
 

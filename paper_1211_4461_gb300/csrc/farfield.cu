@@ -298,9 +298,14 @@ __device__ __forceinline__ int ilog2_up(double a) {   // exponent e with a < 2^e
 }
 
 // one warp per (row, block): block exponent of |v| (upper bound), scaled
-// double-float split, and the row-block spread (max - min exponent) into *spread
+// double-float split, and the row-block spread (max - min exponent) into *spread.
+// elo (block bounds for skipping negligible blocks, see k_ff_df_skip):
+// lo_min != 0 writes the smallest exponent of the block's entries inside the
+// grid (-100000 if one is zero: max(|re|, |im|) >= 2^(e-1) for every entry),
+// else the largest (-100000 for an all-zero block: some entry reaches 2^(e-1)).
 __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, float4* __restrict__ vdf,
-                             float2* __restrict__ vsum, int* __restrict__ ev, int* __restrict__ spread) {
+                             float2* __restrict__ vsum, int* __restrict__ ev, int* __restrict__ spread,
+                             int* __restrict__ elo, int lo_min) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nb = (m + DKB - 1) / DKB;
   if (warp >= nrows * nb) return;
@@ -310,14 +315,17 @@ __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, fl
   double a = fmax(fabs(x.x), fabs(x.y));
   int e = (a > 0.0 && isfinite(a)) ? ilog2_up(a) : -100000;
   int emin = (a > 0.0 && isfinite(a)) ? e : 100000;
+  int elow = (i < m) ? e : 100000;               // -100000 for a zero entry; padding lanes ignored
   for (int o = 16; o > 0; o >>= 1) {
     e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
     emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    elow = min(elow, __shfl_xor_sync(0xffffffffu, elow, o));
   }
   const bool bad = __any_sync(0xffffffffu, !isfinite(a));   // non-finite: the FP64 kernel runs
   const int eb = (e == -100000 || bad) ? 0 : e;
   if (lane == 0) {
     ev[(long long)row * nb + b] = eb;
+    if (elo) elo[(long long)row * nb + b] = lo_min ? elow : e;
     int sp = bad ? DF_NONFINITE : ((e == -100000) ? 0 : e - emin);
     atomicMax(spread, sp);
   }
@@ -391,11 +399,62 @@ constexpr int DF_BM = 16, DF_BN = 32, DF_NT = 128;
 // stays relative to the sum of its terms' magnitudes, all bounded by
 // (|ar| + |ai|)(|br| + |bi|), so the error is still double-float-small
 // against the sum of the terms' magnitudes.
-__global__ void __launch_bounds__(DF_NT) k_ff_stage1_df(const float4* __restrict__ X, const float2* __restrict__ Xs,
+// Negligible blocks of the contraction.  For an output T[k][rho] the sum of
+// its terms' magnitudes is at least
+//   2^L,  L = max_b (xlo[k][b] + ghi[rho][b] - 2)
+// (xlo: smallest exponent of X's entries in block b, ghi: largest of g's), and
+// block b adds at most 32 * 2 * 2^(ex[k][b] + eg[rho][b]) (ex, eg: the block
+// exponents the split scales by).  A block whose bound lies 60 binades under
+// L for every (k, rho) of a contraction tile is skipped by that tile: per
+// angle the skipped terms of the far field stay below 2^-55 of the sum of the
+// magnitudes of all its terms (the factor Y[alpha][rho] of stage 2 is common
+// to both sides), far below the double-float rounding.  All-zero g blocks add
+// nothing and set no constraint.  One CTA per tile of k_ff_stage1_df.
+constexpr int DF_SKIP_MARGIN = 60;
+__global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__ xlo, int M,
+                             const int* __restrict__ eg, const int* __restrict__ ghi, int N, int nb,
+                             unsigned char* __restrict__ skip) {
+  __shared__ int Ls[DF_BM * DF_BN];
+  const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
+  constexpr int OUTSIDE = -(1 << 30);    // pair outside the output range: no constraint
+  constexpr int UNKNOWN = -(1 << 29);    // no lower bound for the pair: nothing may be skipped
+  for (int p = threadIdx.x; p < DF_BM * DF_BN; p += blockDim.x) {
+    const int k = m0 + p / DF_BN, r = n0 + p % DF_BN;
+    int L = OUTSIDE;
+    if (k < M && r < N) {
+      L = UNKNOWN;
+      for (int b = 0; b < nb; ++b) {
+        const int a = xlo[(long long)k * nb + b], g = ghi[(long long)r * nb + b];
+        if (a > -100000 && g > -100000) L = max(L, a + g - 2);
+      }
+    }
+    Ls[p] = L;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long tile = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+  for (int b = warp; b < nb; b += nw) {
+    int worst = OUTSIDE;                                // max over pairs of bound - L
+    for (int p = lane; p < DF_BM * DF_BN; p += 32) {
+      const int L = Ls[p];
+      if (L == OUTSIDE) continue;
+      const int k = m0 + p / DF_BN, r = n0 + p % DF_BN;
+      if (ghi[(long long)r * nb + b] <= -100000) continue;   // zero block of g: adds nothing
+      if (L == UNKNOWN) { worst = 1 << 20; continue; }
+      worst = max(worst, ex[(long long)k * nb + b] + eg[(long long)r * nb + b] + 6 - L);
+    }
+    for (int o = 16; o > 0; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    if (lane == 0) skip[tile * nb + b] = worst < -DF_SKIP_MARGIN ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(DF_NT, 5) k_ff_stage1_df(const float4* __restrict__ X, const float2* __restrict__ Xs,
                                                         const int* __restrict__ ex, int M,
                                                         const float4* __restrict__ G, const float2* __restrict__ Gs,
                                                         const int* __restrict__ eg, int N, int nb,
-                                                        const int* __restrict__ spread, double2* __restrict__ T) {
+                                                        const int* __restrict__ spread,
+                                                        const unsigned char* __restrict__ skip,
+                                                        double2* __restrict__ T) {
   if (!df_selected(spread)) return;      // the FP64 kernel takes this launch
   __shared__ float4 As[DF_BM][DKB + 1];
   __shared__ float2 As2[DF_BM][DKB + 1];
@@ -413,7 +472,9 @@ __global__ void __launch_bounds__(DF_NT) k_ff_stage1_df(const float4* __restrict
       acc2[i][j] = dfacc{0.f, 0.f, -100000};
       acc3[i][j] = dfacc{0.f, 0.f, -100000};
     }
+  const unsigned char* tskip = skip + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * nb;
   for (int b = 0; b < nb; ++b) {
+    if (tskip[b]) continue;              // negligible for every output of the tile (uniform)
     for (int i = tid; i < DF_BM * DKB; i += DF_NT) {
       int r = i / DKB, kk = i % DKB, gm = m0 + r;
       const long long o = ((long long)gm * nb + b) * DKB + kk;
@@ -897,11 +958,32 @@ static cudaError_t ensure(void** p, size_t& cap, size_t need, csff_plan* P) {
   return e;
 }
 
+// fraction of the double-float contraction's (tile, block) pairs that the last
+// 2D far field computed (1 when the FP64 kernel ran or nothing was skipped)
+csff_status far_field_executed(csff_plan* P, double* executed) {
+  FFBuffers& B = P->ff;
+  *executed = 1.0;
+  if (!B.dskip || !B.dspread || B.skip_used == 0) return CSFF_OK;
+  std::vector<unsigned char> h(B.skip_used);
+  int sp[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h.data(), B.dskip, h.size(), cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sp, B.dspread, sizeof(sp), cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "far-field work");
+  const bool df = sp[0] < DF_NONFINITE && sp[1] < DF_NONFINITE && std::min(sp[0], sp[1]) <= DF_SPREAD_LIMIT;
+  if (!df) return CSFF_OK;
+  size_t run = 0;
+  for (unsigned char c : h) run += c == 0;
+  *executed = (double)run / (double)h.size();
+  return CSFF_OK;
+}
+
 void free_ff_buffers(csff_plan* P) {
   FFBuffers& b = P->ff;
   for (void* p : {(void*)b.dg, (void*)b.dxt, (void*)b.dyt, (void*)b.dzt, (void*)b.dT, (void*)b.dal,
                   (void*)b.dux, (void*)b.dxr, (void*)b.ds1, (void*)b.dmisc, (void*)b.dxdf, (void*)b.dgdf, (void*)b.dxsm, (void*)b.dgsm,
-                  (void*)b.dex, (void*)b.deg, (void*)b.dspread, (void*)b.dtcb, (void*)b.dtce, (void*)b.dtcflag})
+                  (void*)b.dex, (void*)b.deg, (void*)b.dspread, (void*)b.dtcb, (void*)b.dtce, (void*)b.dtcflag,
+                  (void*)b.dxlo, (void*)b.dghi, (void*)b.dskip})
     if (p) cudaFree(p);
   b = FFBuffers{};
 }
@@ -1103,7 +1185,9 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
       (e = ensure((void**)&B.dxsm, B.xsm, sizeof(float2) * (size_t)n_ux * nbk * DKB, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dgsm, B.gsm, sizeof(float2) * (size_t)R * nbk * DKB, P)) != cudaSuccess ||
       (e = ensure((void**)&B.dex, B.exs, sizeof(int) * (size_t)n_ux * nbk, P)) != cudaSuccess ||
-      (e = ensure((void**)&B.deg, B.egs, sizeof(int) * (size_t)R * nbk, P)) != cudaSuccess)
+      (e = ensure((void**)&B.deg, B.egs, sizeof(int) * (size_t)R * nbk, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dxlo, B.xlo, sizeof(int) * (size_t)n_ux * nbk, P)) != cudaSuccess ||
+      (e = ensure((void**)&B.dghi, B.ghi, sizeof(int) * (size_t)R * nbk, P)) != cudaSuccess)
     return cuda_fail(e, "far field scratch");
   if (!B.dspread && (e = cudaMalloc((void**)&B.dspread, 2 * sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "far field scratch");
@@ -1111,19 +1195,25 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   {
     const long long wx = (long long)n_ux * nbk, wg = (long long)R * nbk;
     k_split_rows<<<(unsigned)((wx * 32 + 255) / 256), 256, 0, s>>>(B.dxt, m, n_ux, B.dxdf, B.dxsm, B.dex,
-                                                                   B.dspread);
+                                                                   B.dspread, B.dxlo, 1);
     k_split_rows<<<(unsigned)((wg * 32 + 255) / 256), 256, 0, s>>>(B.dg, m, (int)R, B.dgdf, B.dgsm, B.deg,
-                                                                   B.dspread + 1);
+                                                                   B.dspread + 1, B.dghi, 0);
     count_launch(2);
   }
   dim3 g1((unsigned)((R + S1_BN - 1) / S1_BN), (n_ux + S1_BM - 1) / S1_BM);
   dim3 gdf((unsigned)((R + DF_BN - 1) / DF_BN), (n_ux + DF_BM - 1) / DF_BM);
+  if ((e = ensure((void**)&B.dskip, B.skip, (size_t)gdf.x * gdf.y * nbk, P)) != cudaSuccess)
+    return cuda_fail(e, "far field scratch");
+  k_ff_df_skip<<<gdf, 256, 0, s>>>(B.dex, B.dxlo, n_ux, B.deg, B.dghi, (int)R, nbk, B.dskip);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "far-field skip flags");
+  B.skip_used = (size_t)gdf.x * gdf.y * nbk;
   {
     ProfScope ps(PF_FF_CONTRACT, s, 16.0 * ((double)n_ux * m + (double)R * m + (double)n_ux * R),
                  8.0 * (double)n_ux * (double)R * m);
     // exactly one of the two writes T (device-side range check on the spreads)
     k_ff_stage1_df<<<gdf, DF_NT, 0, s>>>(B.dxdf, B.dxsm, B.dex, n_ux, B.dgdf, B.dgsm, B.deg, (int)R, nbk, B.dspread,
-                                         B.dT);
+                                         B.dskip, B.dT);
     k_ff_stage1<<<g1, 256, 0, s>>>(B.dxt, n_ux, B.dg, (int)R, m, B.dT, B.dspread);
   }
   count_launch(2);

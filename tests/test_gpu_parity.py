@@ -374,3 +374,26 @@ def test_far_field_extended_range_k40(csff):
     for a in range(len(al)):
         d = Fg[a] * 2.0 ** float(eg[a] - e2[a]) - m[a]
         assert abs(d) <= 1e-12 * tn[a] + 1e-300
+
+
+def test_far_field_skips_negligible_blocks_within_the_bound(csff):
+    """k = 20 on [-20,20]^2 (257^2): most stage-1 blocks carry terms far below
+    the largest ones along the rotated contour and are skipped; the map still
+    meets the per-angle bound 1e-13 * sum_j |term_j| against the oracle."""
+    c = W.mixed_2d(20.0, n=257)
+    c["opts"].update(coarsest_n=9, rel_tol=1e-8)
+    plan = csff.Plan(c["problem"], c["opts"])
+    p = O.problem_from_dict(c["problem"])
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    plan.solve(c["eta"], u)
+    al = c["alphas"]
+    F = torch.zeros(len(al), dtype=torch.complex128, device="cuda")
+    E = torch.zeros(len(al), dtype=torch.int32, device="cuda")
+    plan.far_field(c["eta"], u, al, F, E)
+    work = plan.far_field_work()
+    assert 0.0 < work < 0.8
+    got = F.cpu().numpy() * 2.0 ** E.cpu().numpy().astype(np.float64)
+    mant, e2, tn = O.far_field(p, host(u, (p.m,) * 2), c["eta"][0], al, return_terms_norm=True)
+    ref = O.far_field_value(mant, e2)
+    assert np.all(np.abs(got - ref) <= 1e-13 * tn * 2.0 ** e2)
+    plan.close()
