@@ -411,20 +411,48 @@ constexpr int DF_BM = 16, DF_BN = 32, DF_NT = 128;
 // to both sides), far below the double-float rounding.  All-zero g blocks add
 // nothing and set no constraint.  One CTA per tile of k_ff_stage1_df.
 constexpr int DF_SKIP_MARGIN = 60;
+constexpr int DF_SKIP_NB_SMEM = 96;      // block counts up to this stage the exponents in shared memory
+__host__ __device__ constexpr size_t df_skip_smem(int nb) {
+  return (size_t)(2 * DF_BM + 2 * DF_BN) * (nb <= DF_SKIP_NB_SMEM ? nb : 0) * sizeof(int);
+}
 __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__ xlo, int M,
                              const int* __restrict__ eg, const int* __restrict__ ghi, int N, int nb,
                              unsigned char* __restrict__ skip) {
   __shared__ int Ls[DF_BM * DF_BN];
+  extern __shared__ int sexp[];          // the tile's rows of ex, xlo, eg, ghi when nb is small
   const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
   constexpr int OUTSIDE = -(1 << 30);    // pair outside the output range: no constraint
   constexpr int UNKNOWN = -(1 << 29);    // no lower bound for the pair: nothing may be skipped
+  const bool staged = nb <= DF_SKIP_NB_SMEM;
+  const int* sx = ex + (long long)m0 * nb;
+  const int* sxl = xlo + (long long)m0 * nb;
+  const int* sg = eg + (long long)n0 * nb;
+  const int* sgh = ghi + (long long)n0 * nb;
+  if (staged) {
+    int* t = sexp;
+    for (int i = threadIdx.x; i < DF_BM * nb; i += blockDim.x) {
+      const bool in = m0 + i / nb < M;
+      t[i] = in ? sx[i] : 0;
+      t[DF_BM * nb + i] = in ? sxl[i] : -100000;
+    }
+    for (int i = threadIdx.x; i < DF_BN * nb; i += blockDim.x) {
+      const bool in = n0 + i / nb < N;
+      t[2 * DF_BM * nb + i] = in ? sg[i] : 0;
+      t[2 * DF_BM * nb + DF_BN * nb + i] = in ? sgh[i] : -100000;
+    }
+    __syncthreads();
+    sx = t;
+    sxl = t + DF_BM * nb;
+    sg = t + 2 * DF_BM * nb;
+    sgh = t + 2 * DF_BM * nb + DF_BN * nb;
+  }
   for (int p = threadIdx.x; p < DF_BM * DF_BN; p += blockDim.x) {
-    const int k = m0 + p / DF_BN, r = n0 + p % DF_BN;
+    const int k = p / DF_BN, r = p % DF_BN;
     int L = OUTSIDE;
-    if (k < M && r < N) {
+    if (m0 + k < M && n0 + r < N) {
       L = UNKNOWN;
       for (int b = 0; b < nb; ++b) {
-        const int a = xlo[(long long)k * nb + b], g = ghi[(long long)r * nb + b];
+        const int a = sxl[k * nb + b], g = sgh[r * nb + b];
         if (a > -100000 && g > -100000) L = max(L, a + g - 2);
       }
     }
@@ -438,10 +466,10 @@ __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__
     for (int p = lane; p < DF_BM * DF_BN; p += 32) {
       const int L = Ls[p];
       if (L == OUTSIDE) continue;
-      const int k = m0 + p / DF_BN, r = n0 + p % DF_BN;
-      if (ghi[(long long)r * nb + b] <= -100000) continue;   // zero block of g: adds nothing
+      const int k = p / DF_BN, r = p % DF_BN;
+      if (sgh[r * nb + b] <= -100000) continue;        // zero block of g: adds nothing
       if (L == UNKNOWN) { worst = 1 << 20; continue; }
-      worst = max(worst, ex[(long long)k * nb + b] + eg[(long long)r * nb + b] + 6 - L);
+      worst = max(worst, sx[k * nb + b] + sg[r * nb + b] + 6 - L);
     }
     for (int o = 16; o > 0; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
     if (lane == 0) skip[tile * nb + b] = worst < -DF_SKIP_MARGIN ? 1 : 0;
@@ -1204,7 +1232,7 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   dim3 gdf((unsigned)((R + DF_BN - 1) / DF_BN), (n_ux + DF_BM - 1) / DF_BM);
   if ((e = ensure((void**)&B.dskip, B.skip, (size_t)gdf.x * gdf.y * nbk, P)) != cudaSuccess)
     return cuda_fail(e, "far field scratch");
-  k_ff_df_skip<<<gdf, 256, 0, s>>>(B.dex, B.dxlo, n_ux, B.deg, B.dghi, (int)R, nbk, B.dskip);
+  k_ff_df_skip<<<gdf, 256, df_skip_smem(nbk), s>>>(B.dex, B.dxlo, n_ux, B.deg, B.dghi, (int)R, nbk, B.dskip);
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "far-field skip flags");
   B.skip_used = (size_t)gdf.x * gdf.y * nbk;
