@@ -13,7 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcsff.so")
 SOURCES = ["csff_api.cu", "mg_kernels.cu", "mg_fused.cu", "farfield.cu", "batch.cu", "learned.cu", "noalloc.cu",
-           "gmres.cu", "partial_wave.cu"]
+           "gmres.cu", "partial_wave.cu", "refine_df.cu"]
 HEADERS = ["csff_internal.h", "mg_tiles.cuh", os.path.join("..", "..", "include", "csff.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

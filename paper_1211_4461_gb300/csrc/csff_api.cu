@@ -438,16 +438,17 @@ csff_status step_fp64(csff_plan* P, int eb) {
   return CSFF_OK;
 }
 
-csff_status step_mixed(csff_plan* P, int eb) {
+// One refinement step of the mixed solve: FP32 V-cycles on A e = r' (r' the
+// scaled residual, already the FP32 right-hand side), u' += e, the new r' in
+// double-float and its norm (refine_df.cu)
+csff_status step_mixed(csff_plan* P, int) {
   Level& L = P->lv[0];
   cudaStream_t s = P->stream;
-  int* ex = reinterpret_cast<int*>(P->red_out + 4);
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
-  CK(csff::launch_to32_scaled(L.r64, L.N, P->red_out, L.b32, ex, s), "scale");
   for (int c = 0; c < inner; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
-  CK(csff::launch_update64(L.u64, L.u32, L.N, ex, s), "update");
-  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
-  CS(norm64(P, L.r64, eb, 0));
+  CK(csff::launch_df_update(P->dfu, L.u32, L.N, s), "update");
+  CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, s), "residual");
+  CK(csff::launch_norm2<float>(L.b32, L.N, 0, P->red, P->red_blocks, P->red_out, s), "norm");
   CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s), "read norm");
   return CSFF_OK;
 }
@@ -505,7 +506,8 @@ csff_status solve_fp64(csff_plan* P, int eb, double nb, csff_info* info) {
   }
 }
 
-// FP64 residual, FP32 V-cycles on the scaled correction equation, FP64 update.
+// Mixed solve: FP32 V-cycles on the correction equation inside a refinement whose
+// residual and update run in double-float arithmetic (refine_df.cu).
 csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
   Level& L = P->lv[0];
   Tracker tr;
@@ -520,14 +522,23 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
   P->learned_off = P->net != nullptr;
   bool fell_back = false;
   double prev = 1.0, ref_factor = P->learned_guard;
-  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, P->stream), "residual");
-  CS(norm64(P, L.r64, eb, 0));
+  // b' = 2^-eb b, u' = 2^-eb u (guess or zero), q split once per coefficient set
+  cudaStream_t s = P->stream;
+  if (!P->dfq_ready) {
+    CK(csff::launch_df_split(L.q64, L.N, 0, P->dfq, s), "split q");
+    P->dfq_ready = true;
+  }
+  CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, s), "split b");
+  CK(csff::launch_df_split(L.u64, L.N, -eb, P->dfu, s), "split u");
+  CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, s), "residual");
+  const double nbs = std::ldexp(nb, -eb);           // ||b'||
+  csff_status result = CSFF_OK;
   for (;;) {
     const bool learned = P->net && !P->learned_off;
     CS(run_step(P, key0 + (learned ? (1ll << 38) : 0), step_mixed, eb));
     cycles += inner;
     ++refinements;
-    const double rel = P->red_host[0] / nb;
+    const double rel = P->red_host[0] / nbs;
     const double factor = rel / prev;
     if (P->net && refinements <= 2) {
       // two plain steps: the second one's factor is the reference
@@ -542,8 +553,14 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
     prev = rel;
     int st = tr.push(rel, cycles, refinements, P->opts.rel_tol, P->opts.max_cycles);
     if (info) info->flags = (P->net ? 1 : 0) | (fell_back ? 2 : 0);
-    if (st >= 0) return (csff_status)st;
+    if (st >= 0) {
+      result = (csff_status)st;
+      break;
+    }
   }
+  // u = 2^eb (hi + lo)
+  CK(csff::launch_df_to64(P->dfu, L.N, eb, L.u64, s), "assemble u");
+  return result;
 }
 
 csff_status check_level(const csff_plan* P, int level, int arith) {
@@ -629,7 +646,8 @@ void csff_plan_destroy(csff_plan* P) {
   if (P->red) cudaFree(P->red);
   if (P->red_out) cudaFree(P->red_out);
   if (P->red_host) cudaFreeHost(P->red_host);
-  for (void* p : {P->gm_v, (void*)P->gm_part, (void*)P->gm, (void*)P->sep_T})
+  for (void* p : {P->gm_v, (void*)P->gm_part, (void*)P->gm, (void*)P->sep_T, (void*)P->dfu, (void*)P->dfb,
+                  (void*)P->dfq})
     if (p) cudaFree(p);
   csff::free_ff_buffers(P);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
@@ -747,6 +765,10 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
       return fail(s);
     e = cudaMallocHost((void**)&P->red_host, 16 * sizeof(double));
     if (e != cudaSuccess) return fail(csff::cuda_fail(e, "pinned host buffer"));
+    if (P->opts.precision == CSFF_PREC_MIXED &&
+        ((s = dev_alloc(P, &P->dfu, (size_t)P->lv[0].N)) || (s = dev_alloc(P, &P->dfb, (size_t)P->lv[0].N)) ||
+         (s = dev_alloc(P, &P->dfq, (size_t)P->lv[0].N))))
+      return fail(s);
     if (P->opts.smoother == CSFF_SMOOTHER_GMRES) {
       double2* v = nullptr;
       if ((s = dev_alloc(P, &v, (size_t)(P->opts.krylov_m + 1) * P->lv[0].N)) ||
@@ -946,6 +968,7 @@ csff_status csff_plan_set_potential(csff_plan* P, const void* q_dev) {
   // the fused FP32 tiles form q from the Gaussian factors: per-level kernels from now on
   P->fused_lc = -1;
   P->user_q = true;
+  P->dfq_ready = false;
   if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
   return CSFF_OK;
 }

@@ -171,6 +171,10 @@ struct csff_plan {
   bool user_q = false;
   double2* sep_T = nullptr;
   size_t sep_cap = 0;
+  // mixed refinement in double-float (refine_df.cu): iterate, right-hand side
+  // and coefficients of the finest level as (re hi, re lo, im hi, im lo)
+  float4 *dfu = nullptr, *dfb = nullptr, *dfq = nullptr;
+  bool dfq_ready = false;
 };
 
 namespace csff {
@@ -218,11 +222,6 @@ cudaError_t launch_coefs(int dim, const Level& L, const double2* const* chi_tab,
                          double k2, cudaStream_t s);
 cudaError_t launch_rhs(int dim, int m, const double2* const* chi_tab, int n_gauss,
                        const double2* uinc_tab, double k2, double2* b, cudaStream_t s);
-// mixed precision helpers
-cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
-                               int* exp_out, cudaStream_t s);
-cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,
-                            cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
 
@@ -230,6 +229,15 @@ cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
 // each level's q64 (csff_plan_set_potential)
 cudaError_t launch_inject_q(int dim, const Level& F, const Level& C, cudaStream_t s);
 cudaError_t launch_coefs_from_q(int dim, const Level& L, cudaStream_t s);
+
+// ---- double-float refinement (refine_df.cu) -------------------------------------
+// out = 2^exp_scale v split into float pairs; r = b - A u in double-float, rounded
+// to FP32; u += e with TwoSum; out = 2^exp_scale (hi + lo)
+cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, cudaStream_t s);
+cudaError_t launch_df_residual(int dim, const Level& L, const float4* u, const float4* b, const float4* q,
+                               float2* r, cudaStream_t s);
+cudaError_t launch_df_update(float4* u, const float2* e, long long N, cudaStream_t s);
+cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2* out, cudaStream_t s);
 
 // ---- GMRES(m) smoothing step (gmres.cu) ----------------------------------------
 // u += V y for the GMRES(m) minimiser from u; V holds m+1 vectors of L.N

@@ -337,6 +337,28 @@ def test_mixed_refinement_solution_and_far_field(csff, k, n):
     assert cone.sum() >= 3 and err <= 1e-5
 
 
+@pytest.mark.parametrize("dim,n", [(2, 257), (3, 65)])
+def test_mixed_refinement_reaches_tight_tolerances(csff, dim, n):
+    """The refinement's residual and update carry pairs of FP32 words (about 48
+    significant bits; exact products for the 2D and 3D centre weights 4 and 6), so
+    a mixed solve asked for 1e-11 meets it under the oracle's FP64 operator."""
+    c = W.mixed_2d(10.0, n=n) if dim == 2 else W.big_3d(n=n, n_rhs=1)
+    c["opts"].update(precision="mixed", rel_tol=1e-11, max_cycles=400)
+    if dim == 2:
+        c["opts"]["coarsest_n"] = 9
+    plan = csff.Plan(c["problem"], c["opts"])
+    p = O.problem_from_dict(c["problem"])
+    eta = c["eta"]
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    st, info = plan.solve(eta[:1], u)
+    assert st == csff.OK and info[0]["rel_res"] <= 1e-11
+    ug = host(u, (p.m,) * dim)
+    b = O.rhs(p, eta[0])
+    lv = O.make_level(p, p.n)
+    assert O.norm2(O.residual(lv, ug, b)) <= 1.05e-11 * O.norm2(b)
+    plan.close()
+
+
 def test_fp64_far_field_matches_on_paper_window_variant(csff):
     """Same grid, k and smoother as the 1025^2 case at n=257, with w = 28/k^2
     (largest term below e^14): FP64 maps agree to the 1e-6 target over all
