@@ -56,10 +56,10 @@ FP64_PEAK_TFLOPS = 1.198
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 DF_INSTR_PER_FLOP = 36.0 / 8.0
 DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
-# DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload, from
-# the ncu capture summarised in profiles/ff_stage1_df_2d_n1025.md (None once
-# the kernel changes).
-FF_DF_DRAM_BYTES = None
+# DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload: the
+# mean over the four maps of the ncu capture summarised in
+# profiles/ff_stage1_df_2d_n1025.md (None once the kernel changes).
+FF_DF_DRAM_BYTES = 26.318144e6
 
 
 # FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of
@@ -69,12 +69,12 @@ FF_DF_DRAM_BYTES = None
 INNER_CYCLES = 6
 
 
-def _cases(precision, ks=None):
+def _cases(precision, ks=None, inner=INNER_CYCLES):
     out = []
     for k in (ks or KS):
         c = W.mixed_2d(k)
         c["opts"]["precision"] = precision
-        c["opts"]["inner_cycles"] = INNER_CYCLES
+        c["opts"]["inner_cycles"] = inner
         out.append(c)
     return out
 
@@ -82,7 +82,7 @@ def _cases(precision, ks=None):
 def _config(args, extra=None):
     cfg = {"workload": WORKLOAD, "maps_per_step": len(KS), "n": 1025, "levels": 8, "angles": 720,
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
-           "inner_cycles": INNER_CYCLES if args.precision == "mixed" else None,
+           "inner_cycles": args.inner_cycles if args.precision == "mixed" else None,
            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
            "concurrency": ("the maps of a step solved one after another" if args.sequential else
                            "the maps of a step solved concurrently: one host thread and one CUDA stream per map")}
@@ -195,7 +195,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     stream = torch.cuda.current_stream()
     ks = tuple(float(k) for k in args.ks.split(",")) if args.ks else KS
-    cases = _cases(args.precision, ks)
+    cases = _cases(args.precision, ks, args.inner_cycles)
     # one stream and one host thread per map: the four solves are independent
     # and each alone leaves most SMs idle on its coarse levels
     streams = [torch.cuda.Stream(device=dev) for _ in cases]
@@ -345,8 +345,10 @@ def run_ours(args, rank, world, local_rank):
     cycles = sum(infos[i]["cycles"] for i in infos)
     vc = {"fp32_kernels_ms": mg32["ms"], "fp32_alg_bytes": mg32["alg_bytes"],
           "fp32_achieved_gbs": mg32["alg_bytes"] / (mg32["ms"] * 1e-3) / 1e9 if mg32["ms"] else 0.0,
-          "fp64_kernels_ms": mg64["ms"],
-          "fp64_achieved_gbs": mg64["alg_bytes"] / (mg64["ms"] * 1e-3) / 1e9 if mg64["ms"] else 0.0,
+          # mixed: the double-float refinement kernels; fp64: the FP64 V-cycles
+          ("refine" if args.precision == "mixed" else "fp64") + "_kernels_ms": mg64["ms"],
+          ("refine" if args.precision == "mixed" else "fp64") + "_achieved_gbs":
+              mg64["alg_bytes"] / (mg64["ms"] * 1e-3) / 1e9 if mg64["ms"] else 0.0,
           "hbm_peak_gbs": hbm, "fp32_vcycles_per_step": cycles,
           "step_ms_profiled": breakdown_step_ms, "ff_contract_ms": breakdown["ff_contract"]["ms"]}
     vc["fp32_hbm_frac"] = vc["fp32_achieved_gbs"] / hbm
@@ -801,6 +803,8 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the plain-FP64 and batched comparison runs")
     ap.add_argument("--ks", default="", help="comma-separated subset of the wavenumbers (profiling runs)")
+    ap.add_argument("--inner-cycles", type=int, default=INNER_CYCLES,
+                    help="FP32 V-cycles per refinement step of the mixed solve")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the maps of a step one after another on one host thread (for profilers, "
                          "which serialise kernels anyway and do not follow several capturing threads)")

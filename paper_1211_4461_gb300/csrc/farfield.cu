@@ -412,8 +412,10 @@ constexpr int DF_BM = 16, DF_BN = 32, DF_NT = 128;
 // nothing and set no constraint.  One CTA per tile of k_ff_stage1_df.
 constexpr int DF_SKIP_MARGIN = 60;
 constexpr int DF_SKIP_NB_SMEM = 96;      // block counts up to this stage the exponents in shared memory
+// staged rows are (nb | 1) ints apart: lanes reading one column of 32 different
+// rows then hit 32 different banks
 __host__ __device__ constexpr size_t df_skip_smem(int nb) {
-  return (size_t)(2 * DF_BM + 2 * DF_BN) * (nb <= DF_SKIP_NB_SMEM ? nb : 0) * sizeof(int);
+  return (size_t)(2 * DF_BM + 2 * DF_BN) * (nb <= DF_SKIP_NB_SMEM ? (nb | 1) : 0) * sizeof(int);
 }
 __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__ xlo, int M,
                              const int* __restrict__ eg, const int* __restrict__ ghi, int N, int nb,
@@ -424,6 +426,7 @@ __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__
   constexpr int OUTSIDE = -(1 << 30);    // pair outside the output range: no constraint
   constexpr int UNKNOWN = -(1 << 29);    // no lower bound for the pair: nothing may be skipped
   const bool staged = nb <= DF_SKIP_NB_SMEM;
+  const int ps = staged ? (nb | 1) : nb;   // row pitch of sx, sxl, sg, sgh
   const int* sx = ex + (long long)m0 * nb;
   const int* sxl = xlo + (long long)m0 * nb;
   const int* sg = eg + (long long)n0 * nb;
@@ -431,20 +434,22 @@ __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__
   if (staged) {
     int* t = sexp;
     for (int i = threadIdx.x; i < DF_BM * nb; i += blockDim.x) {
-      const bool in = m0 + i / nb < M;
-      t[i] = in ? sx[i] : 0;
-      t[DF_BM * nb + i] = in ? sxl[i] : -100000;
+      const int row = i / nb, j = row * ps + i % nb;
+      const bool in = m0 + row < M;
+      t[j] = in ? sx[i] : 0;
+      t[DF_BM * ps + j] = in ? sxl[i] : -100000;
     }
     for (int i = threadIdx.x; i < DF_BN * nb; i += blockDim.x) {
-      const bool in = n0 + i / nb < N;
-      t[2 * DF_BM * nb + i] = in ? sg[i] : 0;
-      t[2 * DF_BM * nb + DF_BN * nb + i] = in ? sgh[i] : -100000;
+      const int row = i / nb, j = row * ps + i % nb;
+      const bool in = n0 + row < N;
+      t[2 * DF_BM * ps + j] = in ? sg[i] : 0;
+      t[2 * DF_BM * ps + DF_BN * ps + j] = in ? sgh[i] : -100000;
     }
     __syncthreads();
     sx = t;
-    sxl = t + DF_BM * nb;
-    sg = t + 2 * DF_BM * nb;
-    sgh = t + 2 * DF_BM * nb + DF_BN * nb;
+    sxl = t + DF_BM * ps;
+    sg = t + 2 * DF_BM * ps;
+    sgh = t + 2 * DF_BM * ps + DF_BN * ps;
   }
   for (int p = threadIdx.x; p < DF_BM * DF_BN; p += blockDim.x) {
     const int k = p / DF_BN, r = p % DF_BN;
@@ -452,7 +457,7 @@ __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__
     if (m0 + k < M && n0 + r < N) {
       L = UNKNOWN;
       for (int b = 0; b < nb; ++b) {
-        const int a = sxl[k * nb + b], g = sgh[r * nb + b];
+        const int a = sxl[k * ps + b], g = sgh[r * ps + b];
         if (a > -100000 && g > -100000) L = max(L, a + g - 2);
       }
     }
@@ -467,9 +472,9 @@ __global__ void k_ff_df_skip(const int* __restrict__ ex, const int* __restrict__
       const int L = Ls[p];
       if (L == OUTSIDE) continue;
       const int k = p / DF_BN, r = p % DF_BN;
-      if (sgh[r * nb + b] <= -100000) continue;        // zero block of g: adds nothing
+      if (sgh[r * ps + b] <= -100000) continue;        // zero block of g: adds nothing
       if (L == UNKNOWN) { worst = 1 << 20; continue; }
-      worst = max(worst, sx[k * nb + b] + sg[r * nb + b] + 6 - L);
+      worst = max(worst, sx[k * ps + b] + sg[r * ps + b] + 6 - L);
     }
     for (int o = 16; o > 0; o >>= 1) worst = max(worst, __shfl_xor_sync(0xffffffffu, worst, o));
     if (lane == 0) skip[tile * nb + b] = worst < -DF_SKIP_MARGIN ? 1 : 0;
