@@ -447,8 +447,7 @@ csff_status step_mixed(csff_plan* P, int) {
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
   for (int c = 0; c < inner; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
   CK(csff::launch_df_update(P->dfu, L.u32, L.N, s), "update");
-  CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, s), "residual");
-  CK(csff::launch_norm2<float>(L.b32, L.N, 0, P->red, P->red_blocks, P->red_out, s), "norm");
+  CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, P->dfpart, P->red_out, s), "residual");
   CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s), "read norm");
   return CSFF_OK;
 }
@@ -507,8 +506,10 @@ csff_status solve_fp64(csff_plan* P, int eb, double nb, csff_info* info) {
 }
 
 // Mixed solve: FP32 V-cycles on the correction equation inside a refinement whose
-// residual and update run in double-float arithmetic (refine_df.cu).
-csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
+// residual and update run in double-float arithmetic (refine_df.cu).  guess: the
+// initial iterate (nullptr: zero); the solution is written to u_out (which may be
+// the guess's buffer).
+csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const double2* guess, double2* u_out) {
   Level& L = P->lv[0];
   Tracker tr;
   tr.start(info);
@@ -525,12 +526,18 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
   // b' = 2^-eb b, u' = 2^-eb u (guess or zero), q split once per coefficient set
   cudaStream_t s = P->stream;
   if (!P->dfq_ready) {
-    CK(csff::launch_df_split(L.q64, L.N, 0, P->dfq, s), "split q");
+    CK(csff::launch_df_split(L.q64, L.N, 0, P->dfq, nullptr, s), "split q");
     P->dfq_ready = true;
   }
-  CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, s), "split b");
-  CK(csff::launch_df_split(L.u64, L.N, -eb, P->dfu, s), "split u");
-  CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, s), "residual");
+  if (guess) {
+    CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, nullptr, s), "split b");
+    CK(csff::launch_df_split(guess, L.N, -eb, P->dfu, nullptr, s), "split u");
+    CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, nullptr, nullptr, s), "residual");
+  } else {
+    // u' = 0: the first residual is b' itself, rounded to FP32 by the split
+    CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, L.b32, s), "split b");
+    CK(cudaMemsetAsync(P->dfu, 0, sizeof(float4) * (size_t)L.N, s), "zero u");
+  }
   const double nbs = std::ldexp(nb, -eb);           // ||b'||
   csff_status result = CSFF_OK;
   for (;;) {
@@ -559,7 +566,7 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info) {
     }
   }
   // u = 2^eb (hi + lo)
-  CK(csff::launch_df_to64(P->dfu, L.N, eb, L.u64, s), "assemble u");
+  CK(csff::launch_df_to64(P->dfu, L.N, eb, u_out, s), "assemble u");
   return result;
 }
 
@@ -647,7 +654,7 @@ void csff_plan_destroy(csff_plan* P) {
   if (P->red_out) cudaFree(P->red_out);
   if (P->red_host) cudaFreeHost(P->red_host);
   for (void* p : {P->gm_v, (void*)P->gm_part, (void*)P->gm, (void*)P->sep_T, (void*)P->dfu, (void*)P->dfb,
-                  (void*)P->dfq})
+                  (void*)P->dfq, (void*)P->dfpart})
     if (p) cudaFree(p);
   csff::free_ff_buffers(P);
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
@@ -767,7 +774,8 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
     if (e != cudaSuccess) return fail(csff::cuda_fail(e, "pinned host buffer"));
     if (P->opts.precision == CSFF_PREC_MIXED &&
         ((s = dev_alloc(P, &P->dfu, (size_t)P->lv[0].N)) || (s = dev_alloc(P, &P->dfb, (size_t)P->lv[0].N)) ||
-         (s = dev_alloc(P, &P->dfq, (size_t)P->lv[0].N))))
+         (s = dev_alloc(P, &P->dfq, (size_t)P->lv[0].N)) ||
+         (s = dev_alloc(P, &P->dfpart, (size_t)csff::df_residual_blocks(d, P->lv[0].m)))))
       return fail(s);
     if (P->opts.smoother == CSFF_SMOOTHER_GMRES) {
       double2* v = nullptr;
@@ -923,16 +931,20 @@ static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_in
     if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
     st = CSFF_OK;
   } else {
-    if (use_guess)
-      CK(cudaMemcpyAsync(L.u64, u, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
-    else
-      CK(csff::launch_zero<double>(L.u64, L.N, P->stream), "zero");
-    st = (P->opts.precision == CSFF_PREC_FP64) ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in);
-    if (P->net && P->opts.precision != CSFF_PREC_FP64) {
+    const bool fp64 = P->opts.precision == CSFF_PREC_FP64;
+    if (fp64) {
+      if (use_guess)
+        CK(cudaMemcpyAsync(L.u64, u, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
+      else
+        CK(csff::launch_zero<double>(L.u64, L.N, P->stream), "zero");
+    }
+    // the mixed solve reads the guess from u and writes the solution there itself
+    st = fp64 ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in, use_guess ? u : nullptr, u);
+    if (P->net && !fp64) {
       const csff_status nst = csff::net_check(P->net);
       if (nst != CSFF_OK) st = nst;
     }
-    if (st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)
+    if (fp64 && st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)
       CK(cudaMemcpyAsync(u, L.u64, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");
   }
   if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;

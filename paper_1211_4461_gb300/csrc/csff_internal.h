@@ -175,6 +175,8 @@ struct csff_plan {
   // and coefficients of the finest level as (re hi, re lo, im hi, im lo)
   float4 *dfu = nullptr, *dfb = nullptr, *dfq = nullptr;
   bool dfq_ready = false;
+  double* dfpart = nullptr;     // per-block partial sums of |r'|^2
+
 };
 
 namespace csff {
@@ -233,9 +235,13 @@ cudaError_t launch_coefs_from_q(int dim, const Level& L, cudaStream_t s);
 // ---- double-float refinement (refine_df.cu) -------------------------------------
 // out = 2^exp_scale v split into float pairs; r = b - A u in double-float, rounded
 // to FP32; u += e with TwoSum; out = 2^exp_scale (hi + lo)
-cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, cudaStream_t s);
+cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, float2* r32,
+                            cudaStream_t s);
+long long df_residual_blocks(int dim, int m);
+// r = b' - A u' rounded to FP32; with norm_out, also ||r|| (part: one double
+// per block of the residual kernel, df_residual_blocks of them)
 cudaError_t launch_df_residual(int dim, const Level& L, const float4* u, const float4* b, const float4* q,
-                               float2* r, cudaStream_t s);
+                               float2* r, double* part, double* norm_out, cudaStream_t s);
 cudaError_t launch_df_update(float4* u, const float2* e, long long N, cudaStream_t s);
 cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2* out, cudaStream_t s);
 

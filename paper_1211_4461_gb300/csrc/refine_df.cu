@@ -71,25 +71,27 @@ __device__ __forceinline__ cdf cmul(cdf a, cdf b) {
   return cdf{dadd(dmul(a.re, b.re), dneg(dmul(a.im, b.im))), dadd(dmul(a.re, b.im), dmul(a.im, b.re))};
 }
 
-// out = (re hi, re lo, im hi, im lo) of s v, s a power of two
-__global__ void k_df_split(const double2* __restrict__ v, long long N, double s, float4* __restrict__ out) {
+// out = (re hi, re lo, im hi, im lo) of s v, s a power of two; r32 (optional)
+// = s v rounded to FP32, i.e. the residual b' - A 0 when v is the right-hand side
+__global__ void k_df_split(const double2* __restrict__ v, long long N, double s, float4* __restrict__ out,
+                           float2* __restrict__ r32) {
   pdl_prologue();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double x = v[i].x * s, y = v[i].y * s;
     const float xh = __double2float_rn(x), yh = __double2float_rn(y);
     out[i] = make_float4(xh, __double2float_rn(x - (double)xh), yh, __double2float_rn(y - (double)yh));
+    if (r32) r32[i] = make_float2(xh, yh);
   }
 }
 
-// r' = b' - (c (2d u' - sum_nbr u') - q u'), rounded to FP32
+// r' = b' - (c (2d u' - sum_nbr u') - q u'), rounded to FP32.  part (optional):
+// per block, the sum of |r'|^2 over its points (FP32 squares and warp sums,
+// FP64 across warps): the squares of FP32 residual entries stay normal down to
+// entries of 1e-19, far below any tolerance relative to max |b'| in [1/2, 1).
 template <int D>
-__global__ void k_df_residual(const float4* __restrict__ u, const float4* __restrict__ b,
-                              const float4* __restrict__ q, float4 c4, int m, float2* __restrict__ r) {
-  pdl_prologue();
-  const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
-  const int iz = (D == 3) ? (int)blockIdx.z : 0;
-  if (ix >= m || iy >= m) return;
-  const long long idx = ((long long)iz * m + iy) * m + ix;
+__device__ __forceinline__ float2 df_residual_point(const float4* __restrict__ u, const float4* __restrict__ b,
+                                                   const float4* __restrict__ q, float4 c4, int m, int ix, int iy,
+                                                   int iz, long long idx) {
   const cdf zero{dff{0.f, 0.f}, dff{0.f, 0.f}};
   cdf s = zero;
   if (ix > 0) s = cadd(s, load(u, idx - 1));
@@ -109,7 +111,50 @@ __global__ void k_df_residual(const float4* __restrict__ u, const float4* __rest
   const cdf c{dff{c4.x, c4.y}, dff{c4.z, c4.w}};
   const cdf au = csub(cmul(c, t), cmul(load(q, idx), uj));
   const cdf rr = csub(load(b, idx), au);
-  r[idx] = make_float2(add(rr.re.hi, rr.re.lo), add(rr.im.hi, rr.im.lo));
+  return make_float2(add(rr.re.hi, rr.re.lo), add(rr.im.hi, rr.im.lo));
+}
+
+template <int D>
+__global__ void k_df_residual(const float4* __restrict__ u, const float4* __restrict__ b,
+                              const float4* __restrict__ q, float4 c4, int m, float2* __restrict__ r,
+                              double* __restrict__ part) {
+  pdl_prologue();
+  const int ix = blockIdx.x * BX + threadIdx.x, iy = blockIdx.y * BY + threadIdx.y;
+  const int iz = (D == 3) ? (int)blockIdx.z : 0;
+  float sq = 0.f;
+  if (ix < m && iy < m) {
+    const long long idx = ((long long)iz * m + iy) * m + ix;
+    const float2 v = df_residual_point<D>(u, b, q, c4, m, ix, iy, iz, idx);
+    r[idx] = v;
+    sq = fmaf(v.x, v.x, v.y * v.y);
+  }
+  if (!part) return;
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  __shared__ float ws[BX * BY / 32];
+  const int t = threadIdx.y * BX + threadIdx.x;
+  if ((t & 31) == 0) ws[t >> 5] = sq;
+  __syncthreads();
+  if (t == 0) {
+    double acc = 0.0;
+    for (int w = 0; w < BX * BY / 32; ++w) acc += (double)ws[w];
+    part[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+  }
+}
+
+// out = sqrt(sum of the n partial sums)
+__global__ void k_df_norm_finish(const double* __restrict__ part, long long n, double* __restrict__ out) {
+  pdl_prologue();
+  __shared__ double ws[32];
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    *out = sqrt(t);
+  }
 }
 
 // u' += e (TwoSum per component)
@@ -140,22 +185,33 @@ int flat(long long N) {
 
 }  // namespace
 
-cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, cudaStream_t s) {
-  const cudaError_t e = launch_pdl(k_df_split, dim3(flat(N)), dim3(256), 0, s, v, N, std::ldexp(1.0, exp_scale), out);
+cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, float2* r32, cudaStream_t s) {
+  const cudaError_t e =
+      launch_pdl(k_df_split, dim3(flat(N)), dim3(256), 0, s, v, N, std::ldexp(1.0, exp_scale), out, r32);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+long long df_residual_blocks(int dim, int m) {
+  return (long long)((m + BX - 1) / BX) * ((m + BY - 1) / BY) * (dim == 3 ? m : 1);
+}
+
 cudaError_t launch_df_residual(int dim, const Level& L, const float4* u, const float4* b, const float4* q,
-                               float2* r, cudaStream_t s) {
+                               float2* r, double* part, double* norm_out, cudaStream_t s) {
   // c = e^{-2 i gamma} / h^2 as two double-float parts
   const float cxh = (float)L.c.x, cyh = (float)L.c.y;
   const float4 c4 = make_float4(cxh, (float)(L.c.x - (double)cxh), cyh, (float)(L.c.y - (double)cyh));
   const dim3 g((L.m + BX - 1) / BX, (L.m + BY - 1) / BY, dim == 3 ? L.m : 1), blk(BX, BY);
+  if (norm_out && !part) return cudaErrorInvalidValue;
   ProfScope ps(PF_MG64, s, 56.0 * L.N, 0);
-  const cudaError_t e = (dim == 2) ? launch_pdl(k_df_residual<2>, g, blk, 0, s, u, b, q, c4, L.m, r)
-                                   : launch_pdl(k_df_residual<3>, g, blk, 0, s, u, b, q, c4, L.m, r);
+  cudaError_t e = (dim == 2) ? launch_pdl(k_df_residual<2>, g, blk, 0, s, u, b, q, c4, L.m, r, part)
+                             : launch_pdl(k_df_residual<3>, g, blk, 0, s, u, b, q, c4, L.m, r, part);
   count_launch();
+  if (e == cudaSuccess && norm_out) {
+    e = launch_pdl(k_df_norm_finish, dim3(1), dim3(512), 0, s, (const double*)part,
+                   df_residual_blocks(dim, L.m), norm_out);
+    count_launch();
+  }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
