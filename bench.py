@@ -60,6 +60,10 @@ DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 # mean over the four maps of the ncu capture summarised in
 # profiles/ff_stage1_df_2d_n1025.md (None once the kernel changes).
 FF_DF_DRAM_BYTES = 26.318144e6
+# DRAM bytes (read + write) per k_down2 / k_up2 launch on this workload, the
+# mean over 22 consecutive launches (two V-cycles) of the warm-cache ncu capture
+# summarised in profiles/vcycle_tiles_2d_n1025.md (None once the kernels change).
+TILES_DRAM_BYTES = 153274.0
 
 
 # FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of
@@ -277,11 +281,12 @@ def run_ours(args, rank, world, local_rank):
         total_ms = float(t.item())
     value = len(cases) * args.steps * world / (total_ms / 1e3)
 
-    # ---- the dominant kernel alone: one sequential step timing only the
+    # ---- the dominant kernels alone: one sequential step timing only the
+    # fused FP32 V(1,1) tile launches (the largest share of device time) and the
     # far-field contraction launches (CUDA events on each launch's stream) ----
     flush.zero_()
     torch.cuda.synchronize()
-    csff.prof_begin(csff.PROF_FF_CONTRACT)
+    csff.prof_begin(csff.PROF_TILES32 | csff.PROF_FF_CONTRACT)
     step(concurrent=False)
     torch.cuda.synchronize()
     prof_timed = csff.prof_end()
@@ -330,7 +335,21 @@ def run_ours(args, rank, world, local_rank):
     ff_flops_all = ff["alg_flops"] / max(1, ff["launches"])
     ff_flops = ff_flops_all * sum(ff_work) / max(1, len(ff_work))      # executed, per launch
     achieved_tf = ff_flops / (ff_avg_ms * 1e-3) / 1e12 if ff_avg_ms > 0 else 0.0
-    roofline = {"kernel": "k_ff_stage1_df (double-float far-field contraction)", "bound": "alu",
+    tl = prof_timed["tiles32"]
+    tl_avg_ms = tl["ms"] / max(1, tl["launches"])
+    tl_bytes = tl["alg_bytes"] / max(1, tl["launches"])
+    tl_gbs = tl_bytes / (tl_avg_ms * 1e-3) / 1e9 if tl_avg_ms > 0 else 0.0
+    roofline = {"kernel": "k_down2 / k_up2 (fused FP32 V(1,1) red-black tiles, every level above the "
+                          "one-CTA coarse block)",
+                "bound": "hbm", "achieved": tl_gbs, "peak": hbm, "unit": "GB/s", "frac": tl_gbs / hbm,
+                "traffic": TILES_DRAM_BYTES,
+                "peak_source": "measured HBM copy bandwidth of this GPU model",
+                "avg_launch_ms": tl_avg_ms, "launches": tl["launches"], "alg_bytes_per_launch": tl_bytes,
+                "note": "algorithmic bytes = 8 B x (3 fine-level points + 1 coarse point) per launch (iterate, "
+                        "right-hand side, output and coarse right-hand side); the 1025^2 V-cycle's arrays "
+                        "stay in L2, and the smaller levels' launches last one CTA's lifetime, so neither "
+                        "HBM nor issue bounds them"}
+    roofline_ff = {"kernel": "k_ff_stage1_df (double-float far-field contraction)", "bound": "alu",
                 "achieved": achieved_tf, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / DF_PEAK_TFLOPS, "traffic": FF_DF_DRAM_BYTES,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 4.5 FP32 instructions per "
@@ -356,7 +375,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if args.precision == "mixed" else "f64",
             "data": "synthetic", "config": _config(args, {"plan_ms": plan_ms}),
-            "roofline": roofline, "vcycle": vc,
+            "roofline": roofline, "roofline_ff_contraction": roofline_ff, "vcycle": vc,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk.result,

@@ -410,9 +410,10 @@ enum {
   CSFF_PROF_FF_CONTRACT = 1, /* far-field stage-1 contraction (FP64) */
   CSFF_PROF_MG32 = 2,        /* multigrid kernels in FP32 */
   CSFF_PROF_MG64 = 4,        /* multigrid kernels in FP64 (incl. refinement residuals) */
-  CSFF_PROF_FF_OTHER = 8     /* far-field tables, g field, stage 2 */
+  CSFF_PROF_FF_OTHER = 8,    /* far-field tables, g field, stage 2 */
+  CSFF_PROF_TILES32 = 16     /* the fused FP32 V(1,1) tile kernels alone (also counted in MG32) */
 };
-#define CSFF_PROF_FAMILIES 4
+#define CSFF_PROF_FAMILIES 5
 typedef struct csff_prof_stats {
   int launches;
   double ms;          /* summed event time of the launches */

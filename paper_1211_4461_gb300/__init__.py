@@ -77,9 +77,9 @@ class ProfStatsC(C.Structure):
     _fields_ = [("launches", C.c_int), ("ms", C.c_double), ("alg_bytes", C.c_double), ("alg_flops", C.c_double)]
 
 
-PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER = 1, 2, 4, 8
+PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER, PROF_TILES32 = 1, 2, 4, 8, 16
 FF_FP64, FF_TC_BF16X3 = 0, 1
-PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other")
+PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other", "tiles32")
 
 _vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
 _dp = C.POINTER(C.c_double)
@@ -168,10 +168,10 @@ def prof_begin(mask: int) -> None:
 
 
 def prof_end() -> dict:
-    out = (ProfStatsC * 4)()
+    out = (ProfStatsC * len(PROF_NAMES))()
     _check(_lib.csff_prof_end(out), "prof_end")
     return {PROF_NAMES[i]: {"launches": out[i].launches, "ms": out[i].ms, "alg_bytes": out[i].alg_bytes,
-                            "alg_flops": out[i].alg_flops} for i in range(4)}
+                            "alg_flops": out[i].alg_flops} for i in range(len(PROF_NAMES))}
 
 
 NOALLOC_MAX_N = 1 << 25

@@ -55,20 +55,28 @@ unsigned prof_mask() { return g_prof.mask; }
 // the record list is shared by every thread that launches while profiling is on
 std::mutex g_prof_mu;
 
-ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops) : stream(s) {
-  if (g_capturing || !(g_prof.mask & (1u << family))) return;
+ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops, int family2) : stream(s) {
+  if (g_capturing) return;
+  const bool on1 = (g_prof.mask & (1u << family)) != 0;
+  const bool on2 = family2 >= 0 && (g_prof.mask & (1u << family2)) != 0;
+  if (!on1 && !on2) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  ProfRec r{family, g_prof.get(), g_prof.get(), bytes, flops};
-  if (!r.a || !r.b) return;
-  cudaEventRecord(r.a, s);
-  slot = (int)g_prof.recs.size();
-  g_prof.recs.push_back(r);
+  auto add = [&](int f) {
+    ProfRec r{f, g_prof.get(), g_prof.get(), bytes, flops};
+    if (!r.a || !r.b) return -1;
+    cudaEventRecord(r.a, s);
+    g_prof.recs.push_back(r);
+    return (int)g_prof.recs.size() - 1;
+  };
+  if (on1) slot = add(family);
+  if (on2) slot2 = add(family2);
 }
 
 ProfScope::~ProfScope() {
-  if (slot < 0) return;
+  if (slot < 0 && slot2 < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  cudaEventRecord(g_prof.recs[slot].b, stream);
+  if (slot >= 0) cudaEventRecord(g_prof.recs[slot].b, stream);
+  if (slot2 >= 0) cudaEventRecord(g_prof.recs[slot2].b, stream);
 }
 
 }  // namespace csff
@@ -455,7 +463,7 @@ csff_status step_mixed(csff_plan* P, int) {
 // Run one step: replay the captured graph (capturing it first if the key
 // changed), or eagerly while kernel families of the solver are being timed.
 csff_status run_step(csff_plan* P, long long key, csff_status (*body)(csff_plan*, int), int eb) {
-  const unsigned mg_bits = CSFF_PROF_MG32 | CSFF_PROF_MG64;
+  const unsigned mg_bits = CSFF_PROF_MG32 | CSFF_PROF_MG64 | CSFF_PROF_TILES32;
   if (!P->use_graphs || !P->gstream || (csff::prof_mask() & mg_bits)) {
     CS(body(P, eb));
     CK(cudaStreamSynchronize(P->stream), "sync");
@@ -523,19 +531,15 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   P->learned_off = P->net != nullptr;
   bool fell_back = false;
   double prev = 1.0, ref_factor = P->learned_guard;
-  // b' = 2^-eb b, u' = 2^-eb u (guess or zero), q split once per coefficient set
+  // b' = 2^-eb b and q are split already (solve_loaded); u' = 2^-eb u (guess or
+  // zero)
   cudaStream_t s = P->stream;
-  if (!P->dfq_ready) {
-    CK(csff::launch_df_split(L.q64, L.N, 0, P->dfq, nullptr, s), "split q");
-    P->dfq_ready = true;
-  }
   if (guess) {
-    CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, nullptr, s), "split b");
-    CK(csff::launch_df_split(guess, L.N, -eb, P->dfu, nullptr, s), "split u");
+    CK(csff::launch_df_split(guess, L.N, -eb, P->dfu, nullptr, nullptr, nullptr, s), "split u");
     CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, nullptr, nullptr, s), "residual");
   } else {
-    // u' = 0: the first residual is b' itself, rounded to FP32 by the split
-    CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, L.b32, s), "split b");
+    // u' = 0: the first residual is b' itself, already in L.b32 (rounded to FP32
+    // by the split)
     CK(cudaMemsetAsync(P->dfu, 0, sizeof(float4) * (size_t)L.N, s), "zero u");
   }
   const double nbs = std::ldexp(nb, -eb);           // ||b'||
@@ -775,7 +779,8 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
     if (P->opts.precision == CSFF_PREC_MIXED &&
         ((s = dev_alloc(P, &P->dfu, (size_t)P->lv[0].N)) || (s = dev_alloc(P, &P->dfb, (size_t)P->lv[0].N)) ||
          (s = dev_alloc(P, &P->dfq, (size_t)P->lv[0].N)) ||
-         (s = dev_alloc(P, &P->dfpart, (size_t)csff::df_residual_blocks(d, P->lv[0].m)))))
+         (s = dev_alloc(P, &P->dfpart, (size_t)std::max(csff::df_residual_blocks(d, P->lv[0].m),
+                                                         csff::df_split_blocks(P->lv[0].N))))))
       return fail(s);
     if (P->opts.smoother == CSFF_SMOOTHER_GMRES) {
       double2* v = nullptr;
@@ -922,16 +927,27 @@ static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_in
     return CSFF_ERR_NONFINITE;
   }
   if (eb <= -2000) eb = 0;
-  CS(norm64(P, L.b64, eb, 1));
+  const bool fp64 = P->opts.precision == CSFF_PREC_FP64;
+  if (fp64) {
+    CS(norm64(P, L.b64, eb, 1));
+  } else {
+    // the mixed solve's operands: q (once per coefficient set) and b' = 2^-eb b as
+    // double-float pairs, b' rounded to FP32 (the first residual for a zero
+    // guess) and ||b'|| from the same pass
+    if (!P->dfq_ready) {
+      CK(csff::launch_df_split(L.q64, L.N, 0, P->dfq, nullptr, nullptr, nullptr, P->stream), "split q");
+      P->dfq_ready = true;
+    }
+    CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, L.b32, P->dfpart, P->red_out + 1, P->stream), "split b");
+  }
   CS(read_scalars(P, 2));
-  double nb = P->red_host[1];
+  const double nb = fp64 ? P->red_host[1] : std::ldexp(P->red_host[1], eb);
   csff_status st;
   if (nb == 0.0) {
     CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
     if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
     st = CSFF_OK;
   } else {
-    const bool fp64 = P->opts.precision == CSFF_PREC_FP64;
     if (fp64) {
       if (use_guess)
         CK(cudaMemcpyAsync(L.u64, u, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, P->stream), "copy");

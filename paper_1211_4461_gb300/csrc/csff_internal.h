@@ -188,11 +188,12 @@ extern std::atomic<uint64_t> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 // Event bracket around the launches of one kernel family (see csff_prof_begin).
-enum ProfFamily { PF_FF_CONTRACT = 0, PF_MG32 = 1, PF_MG64 = 2, PF_FF_OTHER = 3 };
+enum ProfFamily { PF_FF_CONTRACT = 0, PF_MG32 = 1, PF_MG64 = 2, PF_FF_OTHER = 3, PF_TILES32 = 4 };
+// events around one launch, counted in family and (when >= 0) in family2 as well
 struct ProfScope {
-  int slot = -1;
+  int slot = -1, slot2 = -1;
   cudaStream_t stream = nullptr;
-  ProfScope(int family, cudaStream_t s, double bytes, double flops);
+  ProfScope(int family, cudaStream_t s, double bytes, double flops, int family2 = -1);
   ~ProfScope();
 };
 template <typename T> constexpr int mg_family() { return sizeof(T) == 8 ? PF_MG64 : PF_MG32; }
@@ -235,8 +236,11 @@ cudaError_t launch_coefs_from_q(int dim, const Level& L, cudaStream_t s);
 // ---- double-float refinement (refine_df.cu) -------------------------------------
 // out = 2^exp_scale v split into float pairs; r = b - A u in double-float, rounded
 // to FP32; u += e with TwoSum; out = 2^exp_scale (hi + lo)
-cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, float2* r32,
-                            cudaStream_t s);
+// out = v 2^exp_scale as double-float pairs; r32 (optional): the same rounded to
+// FP32; norm_out (optional): ||r32||, with part holding df_split_blocks doubles
+cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, float2* r32, double* part,
+                            double* norm_out, cudaStream_t s);
+long long df_split_blocks(long long N);
 long long df_residual_blocks(int dim, int m);
 // r = b' - A u' rounded to FP32; with norm_out, also ||r|| (part: one double
 // per block of the residual kernel, df_residual_blocks of them)

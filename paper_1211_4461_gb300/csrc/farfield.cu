@@ -21,18 +21,21 @@
 #include <vector>
 
 #include "csff_internal.h"
+#include "df_bits.cuh"
 
 namespace csff {
 namespace {
 
-__device__ __forceinline__ int exp2_of(double a) {
-  if (a == 0.0) return -4000;
-  int e;
-  frexp(a, &e);
-  return e;
+// frexp's exponent of max(|re|, |im|), plus one, from the IEEE fields: -3999 for
+// zero; a non-finite component counts as exponent 0
+__device__ __forceinline__ int cexp2(double2 v) {
+  const bool nzx = ((unsigned long long)__double_as_longlong(v.x) & bits::ABS_MASK) != 0;
+  const bool nzy = ((unsigned long long)__double_as_longlong(v.y) & bits::ABS_MASK) != 0;
+  int e = -4000;
+  if (nzx) e = max(e, bits::exp_field(v.x) == 0x7ff ? 0 : bits::frexp_exp(v.x));
+  if (nzy) e = max(e, bits::exp_field(v.y) == 0x7ff ? 0 : bits::frexp_exp(v.y));
+  return e + 1;
 }
-
-__device__ __forceinline__ int cexp2(double2 v) { return exp2_of(fmax(fabs(v.x), fabs(v.y))) + 1; }
 
 // g = chi (u_in + u) at every interior node.
 struct Tabs8 { const double2* p[8]; };
@@ -40,20 +43,43 @@ struct Tabs8 { const double2* p[8]; };
 template <int D>
 __global__ void k_gfield(Tabs8 tabs, int n_gauss, const double2* __restrict__ uinc,
                          const double2* __restrict__ u, int m, double2* __restrict__ g) {
-  int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
-  int iz = (D == 3) ? (int)blockIdx.z : 0;
-  if (ix >= m || iy >= m) return;
-  long long idx = ((long long)iz * m + iy) * m + ix;
   // g = chi u_in + chi u; chi u_in with each axis' Gaussian factor paired with
-  // its incident-wave factor first (no partial product beyond the FP64 range)
+  // its incident-wave factor first (no partial product beyond the FP64 range).
+  // The per-axis factors and pairs of the block's 32 columns, 8 rows (and
+  // plane) are read and formed once per block.
+  __shared__ double2 ex[8][32], ey[8][8], px[8][32], py[8][8], ez[8], pz[8];
+  const int t = threadIdx.y * 32 + threadIdx.x;
+  for (int i = t; i < n_gauss * 41; i += 256) {
+    const int q = i / 41, r = i % 41;
+    const double2* E = tabs.p[q];
+    if (r < 32) {
+      const int x = blockIdx.x * 32 + r;
+      const double2 f = x < m ? E[x] : make_double2(0, 0);
+      ex[q][r] = f;
+      px[q][r] = x < m ? cmul(f, uinc[x]) : make_double2(0, 0);
+    } else if (r < 40) {
+      const int y = blockIdx.y * 8 + (r - 32);
+      const double2 f = y < m ? E[m + y] : make_double2(0, 0);
+      ey[q][r - 32] = f;
+      py[q][r - 32] = y < m ? cmul(f, uinc[m + y]) : make_double2(0, 0);
+    } else if (D == 3) {
+      const double2 f = E[2 * m + blockIdx.z];
+      ez[q] = f;
+      pz[q] = cmul(f, uinc[2 * m + blockIdx.z]);
+    }
+  }
+  __syncthreads();
+  const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
+  const int iz = (D == 3) ? (int)blockIdx.z : 0;
+  if (ix >= m || iy >= m) return;
+  const long long idx = ((long long)iz * m + iy) * m + ix;
   double2 chi = make_double2(0, 0), cu = make_double2(0, 0);
   for (int q = 0; q < n_gauss; ++q) {
-    const double2* t = tabs.p[q];
-    double2 v = cmul(t[ix], t[m + iy]);
-    double2 w = cmul(cmul(t[ix], uinc[ix]), cmul(t[m + iy], uinc[m + iy]));
+    double2 v = cmul(ex[q][threadIdx.x], ey[q][threadIdx.y]);
+    double2 w = cmul(px[q][threadIdx.x], py[q][threadIdx.y]);
     if (D == 3) {
-      v = cmul(v, t[2 * m + iz]);
-      w = cmul(w, cmul(t[2 * m + iz], uinc[2 * m + iz]));
+      v = cmul(v, ez[q]);
+      w = cmul(w, pz[q]);
     }
     chi = cadd(chi, v);
     cu = cadd(cu, w);
@@ -221,8 +247,9 @@ __global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict
   const double2* yr = ytab + (long long)a * m;
   const double2* zr = ztab + (long long)a * m;
   int emax = -4000;
-  for (long long r = threadIdx.x; r < R; r += blockDim.x) {
-    int iy = (int)(r % m), iz = (int)(r / m);
+  // R = m (2D) or m^2 (3D) stays well inside int
+  for (int r = threadIdx.x; r < (int)R; r += blockDim.x) {
+    const int iy = (D == 3) ? r % m : r, iz = (D == 3) ? r / m : 0;
     int e = cexp2(Tr[r]) + cexp2(yr[iy]) + ((D == 3) ? cexp2(zr[iz]) : 0);
     emax = e > emax ? e : emax;
   }
@@ -233,9 +260,9 @@ __global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict
   s2 = s2 > 0 ? s2 : 0;
   double sc = ldexp(1.0, -s2);
   double ax = 0, ay = 0;
-  for (long long r = threadIdx.x; r < R; r += blockDim.x) {
-    int iy = (int)(r % m), iz = (int)(r / m);
-    double2 w = cscale(yr[iy], sc);
+  for (int r = threadIdx.x; r < (int)R; r += blockDim.x) {
+    const int iy = (D == 3) ? r % m : r, iz = (D == 3) ? r / m : 0;
+    double2 w = s2 > 0 ? cscale(yr[iy], sc) : yr[iy];    // the scale is 1 unless the sum could overflow
     if (D == 3) w = cmul(w, zr[iz]);
     double2 t = Tr[r];
     ax = fma(w.x, t.x, fma(-w.y, t.y, ax));
@@ -273,11 +300,6 @@ constexpr int DKB = 32;
 struct df { float hi, lo; };
 
 // split x (|x| <= 2) into hi + lo
-__device__ __forceinline__ df df_of(double x) {
-  float h = (float)x;
-  return df{h, (float)(x - (double)h)};
-}
-
 // s += a * b  (double-float; s kept unnormalised: hi via TwoSum, lo collects errors)
 __device__ __forceinline__ void df_mac(df& s, df a, df b) {
   float p = a.hi * b.hi;
@@ -289,12 +311,6 @@ __device__ __forceinline__ void df_mac(df& s, df a, df b) {
   float err = (s.hi - (t - v)) + (p - v);
   s.hi = t;
   s.lo += err + e;
-}
-
-__device__ __forceinline__ int ilog2_up(double a) {   // exponent e with a < 2^e (a > 0)
-  int e;
-  frexp(a, &e);
-  return e;
 }
 
 // one warp per (row, block): block exponent of |v| (upper bound), scaled
@@ -312,16 +328,21 @@ __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, fl
   const int row = warp / nb, b = warp % nb;
   const int i = b * DKB + lane;
   double2 x = (i < m) ? v[(long long)row * m + i] : make_double2(0, 0);
-  double a = fmax(fabs(x.x), fabs(x.y));
-  int e = (a > 0.0 && isfinite(a)) ? ilog2_up(a) : -100000;
-  int emin = (a > 0.0 && isfinite(a)) ? e : 100000;
+  // exponent of max(|re|, |im|) from the IEEE fields: the larger of the two
+  // components' frexp exponents (a non-finite component marks the row bad)
+  const bool fin = bits::exp_field(x.x) != 0x7ff && bits::exp_field(x.y) != 0x7ff;
+  const bool nzx = ((unsigned long long)__double_as_longlong(x.x) & bits::ABS_MASK) != 0;
+  const bool nzy = ((unsigned long long)__double_as_longlong(x.y) & bits::ABS_MASK) != 0;
+  const bool pos = fin && (nzx || nzy);
+  int e = pos ? max(nzx ? bits::frexp_exp(x.x) : -100000, nzy ? bits::frexp_exp(x.y) : -100000) : -100000;
+  int emin = pos ? e : 100000;
   int elow = (i < m) ? e : 100000;               // -100000 for a zero entry; padding lanes ignored
   for (int o = 16; o > 0; o >>= 1) {
     e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
     emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
     elow = min(elow, __shfl_xor_sync(0xffffffffu, elow, o));
   }
-  const bool bad = __any_sync(0xffffffffu, !isfinite(a));   // non-finite: the FP64 kernel runs
+  const bool bad = __any_sync(0xffffffffu, !fin);   // non-finite: the FP64 kernel runs
   const int eb = (e == -100000 || bad) ? 0 : e;
   if (lane == 0) {
     ev[(long long)row * nb + b] = eb;
@@ -329,13 +350,20 @@ __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, fl
     int sp = bad ? DF_NONFINITE : ((e == -100000) ? 0 : e - emin);
     atomicMax(spread, sp);
   }
-  // ldexp on the value itself: 2^-eb alone overflows for subnormal blocks
+  // the scaled splits of re, im and re + im (Gauss's three-product complex
+  // multiply); the scale applies to the values themselves, since 2^-eb alone
+  // overflows for subnormal blocks
   const bool zero = e == -100000 || bad;
-  const double xr = zero ? 0.0 : ldexp(x.x, -eb), xi = zero ? 0.0 : ldexp(x.y, -eb);
-  df re = df_of(xr), im = df_of(xi), sm = df_of(xr + xi);
+  float2 re = make_float2(0.f, 0.f), im = re, sm = re;
+  if (!zero) {
+    re = bits::split_scaled(x.x, eb);
+    im = bits::split_scaled(x.y, eb);
+    sm = eb <= 1000 ? bits::split_scaled(x.x + x.y, eb)      // RN(x + y) 2^-eb = RN(x 2^-eb + y 2^-eb)
+                    : bits::split_scaled(ldexp(x.x, -eb) + ldexp(x.y, -eb), 0);
+  }
   const long long o = (long long)row * nb * DKB + b * DKB + lane;
-  vdf[o] = make_float4(re.hi, re.lo, im.hi, im.lo);
-  vsum[o] = make_float2(sm.hi, sm.lo);      // re + im for Gauss's three-product complex multiply
+  vdf[o] = make_float4(re.x, re.y, im.x, im.y);
+  vsum[o] = sm;
 }
 
 // 2^d as a float for d <= 0 (0 below the subnormal range): exact power of two

@@ -106,7 +106,8 @@ template <typename T>
 cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, bool zero_init, const cx<T>* b,
                          cx<T>* u_out, cx<T>* bc, cudaStream_t s) {
   cx<T> c = mk<cx<T>>((T)F.c.x, (T)F.c.y);
-  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0);
+  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0,
+               sizeof(T) == 4 ? PF_TILES32 : -1);
   const tiles::LevelCoef<T> K = level_coef<T>(F);
   const int ng = coef_ng<T>(F);
   cudaError_t e;
@@ -127,7 +128,8 @@ template <typename T>
 cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
                        cx<T>* u_out, cudaStream_t s) {
   cx<T> c = mk<cx<T>>((T)F.c.x, (T)F.c.y);
-  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0);
+  ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0,
+               sizeof(T) == 4 ? PF_TILES32 : -1);
   const tiles::LevelCoef<T> K = level_coef<T>(F);
   const int ng = coef_ng<T>(F);
   cudaError_t e;

@@ -7,6 +7,7 @@
 // nodes are not stored (homogeneous Dirichlet).  Grid mapping: block (32, 8)
 // over (x, y), blockIdx.z = z plane in 3D.
 #include "csff_internal.h"
+#include "df_bits.cuh"
 
 namespace csff {
 namespace {
@@ -207,21 +208,22 @@ __global__ void k_norm_finish(const double* __restrict__ partial, int nblk, doub
   if (threadIdx.x == 0) *out = sqrt(acc) * inv_scale;
 }
 
-__device__ __forceinline__ int exp_of(double a) {
-  if (a == 0.0) return -2000;
-  if (!isfinite(a)) return 4000;
-  int e;
-  frexp(a, &e);
-  return e;
-}
-
 __global__ void k_max_exp(const double2* __restrict__ v, long long N, int* __restrict__ out) {
   __shared__ int sh[32];
   int mx = -2000;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    double a = fmax(fabs(v[i].x), fabs(v[i].y));
-    int e = exp_of(a);
+    // frexp's exponent of max(|re|, |im|) from the IEEE fields: -2000 for zero,
+    // 4000 when a component is not finite
+    const double2 x = v[i];
+    const int Ex = bits::exp_field(x.x), Ey = bits::exp_field(x.y);
+    int e;
+    if (Ex == 0x7ff || Ey == 0x7ff) e = 4000;
+    else {
+      const bool nzx = ((unsigned long long)__double_as_longlong(x.x) & bits::ABS_MASK) != 0;
+      const bool nzy = ((unsigned long long)__double_as_longlong(x.y) & bits::ABS_MASK) != 0;
+      e = max(nzx ? bits::frexp_exp(x.x) : -2000, nzy ? bits::frexp_exp(x.y) : -2000);
+    }
     mx = e > mx ? e : mx;
   }
   mx = block_reduce(mx, MaxIOp(), sh, -2000);
@@ -289,16 +291,32 @@ __global__ void k_coefs_from_q(const double2* __restrict__ q64, int m, double2 c
 template <int D>
 __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uinc, int m, double k2,
                       double2* __restrict__ b) {
-  int ix, iy, iz; long long idx;
-  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
   // chi u_in = sum_g prod_c (E_{g,c} U_c): each axis' Gaussian factor is paired
   // with its incident-wave factor first, so no partial product leaves the
-  // FP64 range when chi u_in itself does not
+  // FP64 range when chi u_in itself does not.  The pairs for the block's 32
+  // columns, 8 rows (and plane) are formed once per block.
+  __shared__ double2 px[8][BX], py[8][BY], pz[8];
+  const int t = threadIdx.y * BX + threadIdx.x;
+  for (int i = t; i < n_gauss * (BX + BY + 1); i += BX * BY) {
+    const int g = i / (BX + BY + 1), r = i % (BX + BY + 1);
+    const double2* E = tabs.p[g];
+    if (r < BX) {
+      const int x = blockIdx.x * BX + r;
+      px[g][r] = x < m ? cmul(E[x], uinc[x]) : make_double2(0, 0);
+    } else if (r < BX + BY) {
+      const int y = blockIdx.y * BY + (r - BX);
+      py[g][r - BX] = y < m ? cmul(E[m + y], uinc[m + y]) : make_double2(0, 0);
+    } else if (D == 3) {
+      pz[g] = cmul(E[2 * m + blockIdx.z], uinc[2 * m + blockIdx.z]);
+    }
+  }
+  __syncthreads();
+  int ix, iy, iz; long long idx;
+  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
   double2 acc = make_double2(0, 0);
   for (int g = 0; g < n_gauss; ++g) {
-    const double2* t = tabs.p[g];
-    double2 v = cmul(cmul(t[ix], uinc[ix]), cmul(t[m + iy], uinc[m + iy]));
-    if (D == 3) v = cmul(v, cmul(t[2 * m + iz], uinc[2 * m + iz]));
+    double2 v = cmul(px[g][threadIdx.x], py[g][threadIdx.y]);
+    if (D == 3) v = cmul(v, pz[g]);
     acc = cadd(acc, v);
   }
   b[idx] = cscale(acc, k2);

@@ -13,11 +13,13 @@
 // magnitude under a 1e-8 residual.  The residual is written rounded to FP32 -
 // the accuracy the FP32 cycles use - straight into their right-hand side: the
 // V-cycle is linear and bias-free, so no further scaling is needed, and the
-// correction it returns is added to u' with TwoSum.  FP64 is touched once per
-// solve: to split b, q and the initial guess, and to assemble u = 2^e_b (hi + lo).
+// correction it returns is added to u' with TwoSum.  The splits of b, q and the
+// initial guess work on the IEEE fields (df_bits.cuh); FP64 arithmetic is left
+// only in assembling u = 2^e_b (hi + lo) once per solve.
 #include <cmath>
 
 #include "csff_internal.h"
+#include "df_bits.cuh"
 
 namespace csff {
 namespace {
@@ -71,16 +73,29 @@ __device__ __forceinline__ cdf cmul(cdf a, cdf b) {
   return cdf{dadd(dmul(a.re, b.re), dneg(dmul(a.im, b.im))), dadd(dmul(a.re, b.im), dmul(a.im, b.re))};
 }
 
-// out = (re hi, re lo, im hi, im lo) of s v, s a power of two; r32 (optional)
-// = s v rounded to FP32, i.e. the residual b' - A 0 when v is the right-hand side
-__global__ void k_df_split(const double2* __restrict__ v, long long N, double s, float4* __restrict__ out,
-                           float2* __restrict__ r32) {
+// out = (re hi, re lo, im hi, im lo) of v 2^-e; r32 (optional) = v 2^-e rounded
+// to FP32, i.e. the residual b' - A 0 when v is the right-hand side; part
+// (optional): per block, the sum of |r32|^2 (FP32 squares summed in FP64)
+__global__ void k_df_split(const double2* __restrict__ v, long long N, int e, float4* __restrict__ out,
+                           float2* __restrict__ r32, double* __restrict__ part) {
   pdl_prologue();
+  double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const double x = v[i].x * s, y = v[i].y * s;
-    const float xh = __double2float_rn(x), yh = __double2float_rn(y);
-    out[i] = make_float4(xh, __double2float_rn(x - (double)xh), yh, __double2float_rn(y - (double)yh));
-    if (r32) r32[i] = make_float2(xh, yh);
+    const double2 x = v[i];
+    const float2 re = bits::split_scaled(x.x, e), im = bits::split_scaled(x.y, e);
+    out[i] = make_float4(re.x, re.y, im.x, im.y);
+    if (r32) r32[i] = make_float2(re.x, im.x);
+    if (part) acc += (double)fmaf(re.x, re.x, im.x * im.x);
+  }
+  if (!part) return;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    part[blockIdx.x] = t;
   }
 }
 
@@ -169,12 +184,12 @@ __global__ void k_df_update(float4* __restrict__ u, const float2* __restrict__ e
   }
 }
 
-// out = s (hi + lo), s a power of two
-__global__ void k_df_to64(const float4* __restrict__ u, long long N, double s, double2* __restrict__ out) {
+// out = 2^e (hi + lo): the scale goes into the exponents of the widened words
+__global__ void k_df_to64(const float4* __restrict__ u, long long N, int e, double2* __restrict__ out) {
   pdl_prologue();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const float4 v = u[i];
-    out[i] = make_double2(((double)v.x + (double)v.y) * s, ((double)v.z + (double)v.w) * s);
+    out[i] = make_double2(bits::widen(v.x, e) + bits::widen(v.y, e), bits::widen(v.z, e) + bits::widen(v.w, e));
   }
 }
 
@@ -185,12 +200,20 @@ int flat(long long N) {
 
 }  // namespace
 
-cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, float2* r32, cudaStream_t s) {
-  const cudaError_t e =
-      launch_pdl(k_df_split, dim3(flat(N)), dim3(256), 0, s, v, N, std::ldexp(1.0, exp_scale), out, r32);
+cudaError_t launch_df_split(const double2* v, long long N, int exp_scale, float4* out, float2* r32, double* part,
+                            double* norm_out, cudaStream_t s) {
+  if (norm_out && !part) return cudaErrorInvalidValue;
+  cudaError_t e = launch_pdl(k_df_split, dim3(flat(N)), dim3(256), 0, s, v, N, -exp_scale, out, r32,
+                             norm_out ? part : nullptr);
   count_launch();
+  if (e == cudaSuccess && norm_out) {
+    e = launch_pdl(k_df_norm_finish, dim3(1), dim3(512), 0, s, (const double*)part, (long long)flat(N), norm_out);
+    count_launch();
+  }
   return e != cudaSuccess ? e : cudaGetLastError();
 }
+
+long long df_split_blocks(long long N) { return flat(N); }
 
 long long df_residual_blocks(int dim, int m) {
   return (long long)((m + BX - 1) / BX) * ((m + BY - 1) / BY) * (dim == 3 ? m : 1);
@@ -223,7 +246,7 @@ cudaError_t launch_df_update(float4* u, const float2* e, long long N, cudaStream
 }
 
 cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2* out, cudaStream_t s) {
-  const cudaError_t e = launch_pdl(k_df_to64, dim3(flat(N)), dim3(256), 0, s, u, N, std::ldexp(1.0, exp_scale), out);
+  const cudaError_t e = launch_pdl(k_df_to64, dim3(flat(N)), dim3(256), 0, s, u, N, exp_scale, out);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
