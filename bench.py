@@ -66,19 +66,22 @@ FF_DF_DRAM_BYTES = 26.318144e6
 TILES_DRAM_BYTES = 153274.0
 
 
-# FP32 V-cycles per FP64 refinement step on the headline workload.  A sweep of
-# 3, 4, 5, 6, 8 on the four 1025^2 solves gave 12.8, 11.8, 11.5, 10.9 and
-# 11.3 ms: each refinement step costs about as much as a V-cycle, and
-# stopping only after a step wastes about half a step's cycles on average.
+# FP32 V-cycles per refinement step on the headline workload (at most, with
+# the adaptive schedule).  With the double-float refinement a sweep of 3, 4, 5,
+# 6, 8 fixed cycles gave 522, 543, 530, 549, 533 maps/s: each step is a graph
+# launch and a host round trip for its norm, and a solve stops only after a
+# step.  Sizing each step from the previous step's reduction factor (the
+# default) gave 652 (at most 6) and 656 (at most 8) against 635 fixed, same box.
 INNER_CYCLES = 6
 
 
-def _cases(precision, ks=None, inner=INNER_CYCLES):
+def _cases(precision, ks=None, inner=INNER_CYCLES, adaptive=False):
     out = []
     for k in (ks or KS):
         c = W.mixed_2d(k)
         c["opts"]["precision"] = precision
         c["opts"]["inner_cycles"] = inner
+        c["opts"]["adaptive_inner"] = int(adaptive and precision == "mixed")
         out.append(c)
     return out
 
@@ -87,6 +90,7 @@ def _config(args, extra=None):
     cfg = {"workload": WORKLOAD, "maps_per_step": len(KS), "n": 1025, "levels": 8, "angles": 720,
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
            "inner_cycles": args.inner_cycles if args.precision == "mixed" else None,
+           "adaptive_inner": bool(args.adaptive_inner) if args.precision == "mixed" else None,
            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
            "concurrency": ("the maps of a step solved one after another" if args.sequential else
                            "the maps of a step solved concurrently: one host thread and one CUDA stream per map")}
@@ -199,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     stream = torch.cuda.current_stream()
     ks = tuple(float(k) for k in args.ks.split(",")) if args.ks else KS
-    cases = _cases(args.precision, ks, args.inner_cycles)
+    cases = _cases(args.precision, ks, args.inner_cycles, args.adaptive_inner)
     # one stream and one host thread per map: the four solves are independent
     # and each alone leaves most SMs idle on its coarse levels
     streams = [torch.cuda.Stream(device=dev) for _ in cases]
@@ -824,6 +828,10 @@ def main():
     ap.add_argument("--ks", default="", help="comma-separated subset of the wavenumbers (profiling runs)")
     ap.add_argument("--inner-cycles", type=int, default=INNER_CYCLES,
                     help="FP32 V-cycles per refinement step of the mixed solve")
+    ap.add_argument("--adaptive-inner", dest="adaptive_inner", action="store_true", default=True,
+                    help="size each refinement step from the previous step's reduction factor (default)")
+    ap.add_argument("--fixed-inner", dest="adaptive_inner", action="store_false",
+                    help="always inner-cycles FP32 V-cycles per refinement step")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the maps of a step one after another on one host thread (for profilers, "
                          "which serialise kernels anyway and do not follow several capturing threads)")

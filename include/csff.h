@@ -102,6 +102,11 @@ typedef struct csff_opts {
   int krylov_m;       /* GMRES smoother: Krylov dimension m of each GMRES(m)
                          smoothing step, 1..4 (0 selects 3); nu1 / nu2 count
                          GMRES(m) steps.  Ignored by the other smoothers. */
+  int adaptive_inner; /* MIXED without a learned smoother: 1 = after each
+                         refinement step, the next runs only the FP32 cycles
+                         that the step's per-cycle reduction factor predicts
+                         are needed to reach rel_tol (at most inner_cycles);
+                         0 = always inner_cycles.  Same stopping test either way. */
 } csff_opts;
 
 #define CSFF_MAX_HISTORY 256

@@ -446,55 +446,69 @@ csff_status step_fp64(csff_plan* P, int eb) {
   return CSFF_OK;
 }
 
-// One refinement step of the mixed solve: FP32 V-cycles on A e = r' (r' the
+// One refinement step of the mixed solve: n FP32 V-cycles on A e = r' (r' the
 // scaled residual, already the FP32 right-hand side), u' += e, the new r' in
 // double-float and its norm (refine_df.cu)
-csff_status step_mixed(csff_plan* P, int) {
+csff_status step_mixed(csff_plan* P, int n) {
   Level& L = P->lv[0];
   cudaStream_t s = P->stream;
-  const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
-  for (int c = 0; c < inner; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
+  for (int c = 0; c < n; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
   CK(csff::launch_df_update(P->dfu, L.u32, L.N, s), "update");
   CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, P->dfpart, P->red_out, s), "residual");
   CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s), "read norm");
   return CSFF_OK;
 }
 
+void destroy_graphs(csff_plan* P) {
+  for (auto& g : P->graphs)
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+}
+
 // Run one step: replay the captured graph (capturing it first if the key
 // changed), or eagerly while kernel families of the solver are being timed.
-csff_status run_step(csff_plan* P, long long key, csff_status (*body)(csff_plan*, int), int eb) {
+// arg: the body's parameter (FP64 step: the right-hand side's exponent; mixed
+// step: its FP32 cycle count), part of what the key identifies.
+csff_status run_step(csff_plan* P, long long key, csff_status (*body)(csff_plan*, int), int arg) {
   const unsigned mg_bits = CSFF_PROF_MG32 | CSFF_PROF_MG64 | CSFF_PROF_TILES32;
   if (!P->use_graphs || !P->gstream || (csff::prof_mask() & mg_bits)) {
-    CS(body(P, eb));
+    CS(body(P, arg));
     CK(cudaStreamSynchronize(P->stream), "sync");
     return CSFF_OK;
   }
-  if (!P->gexec || P->gkey != key) {
-    if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+  csff_plan::StepGraph* G = nullptr;
+  for (auto& g : P->graphs)
+    if (g.exec && g.key == key) G = &g;
+  if (!G) {
+    G = &P->graphs[P->graph_next];
+    P->graph_next = (P->graph_next + 1) % csff_plan::GRAPH_SLOTS;
+    if (G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
     CK(cudaStreamBeginCapture(P->gstream, cudaStreamCaptureModeThreadLocal), "begin capture");
     const uint64_t before = csff::g_launches.load();
     cudaStream_t saved = P->stream;
     P->stream = P->gstream;
     csff::g_capturing = true;
-    csff_status st = body(P, eb);
+    csff_status st = body(P, arg);
     csff::g_capturing = false;
     P->stream = saved;
     // kernels recorded in the graph: counted again on every replay below
-    P->gkernels = csff::g_launches.load() - before;
-    csff::g_launches.fetch_sub(P->gkernels);
+    G->kernels = csff::g_launches.load() - before;
+    csff::g_launches.fetch_sub(G->kernels);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(P->gstream, &graph);
     if (st != CSFF_OK) { if (graph) cudaGraphDestroy(graph); return st; }
     if (e != cudaSuccess) return csff::cuda_fail(e, "end capture");
-    e = cudaGraphInstantiate(&P->gexec, graph, 0);
+    e = cudaGraphInstantiate(&G->exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { P->gexec = nullptr; return csff::cuda_fail(e, "instantiate graph"); }
-    P->gkey = key;
+    if (e != cudaSuccess) { G->exec = nullptr; return csff::cuda_fail(e, "instantiate graph"); }
+    G->key = key;
   }
   CK(cudaEventRecord(P->gev, P->stream), "event");
   CK(cudaStreamWaitEvent(P->gstream, P->gev, 0), "wait event");
-  CK(cudaGraphLaunch(P->gexec, P->gstream), "graph launch");
-  csff::count_launch((int)P->gkernels);
+  CK(cudaGraphLaunch(G->exec, P->gstream), "graph launch");
+  csff::count_launch((int)G->kernels);
   CK(cudaStreamSynchronize(P->gstream), "sync");
   return CSFF_OK;
 }
@@ -523,7 +537,10 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   tr.start(info);
   int cycles = 0, refinements = 0;
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
-  const long long key0 = (2ll << 40) + (long long)(eb + 8192) * 64 + inner;
+  // the step's graph depends on its cycle count and on whether the learned step runs
+  const long long key0 = 2ll << 40;
+  const bool adaptive = P->opts.adaptive_inner != 0 && P->net == nullptr;
+  int n = inner;
   // with a learned smoother the first two refinement steps run plain
   // red-black sweeps and the second sets the reference factor; a later learned
   // step that reduces the residual less than min(reference, guard) hands the
@@ -546,8 +563,10 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   csff_status result = CSFF_OK;
   for (;;) {
     const bool learned = P->net && !P->learned_off;
-    CS(run_step(P, key0 + (learned ? (1ll << 38) : 0), step_mixed, eb));
-    cycles += inner;
+    const int n_step = n;
+    const double rel_before = prev;
+    CS(run_step(P, key0 + n_step + (learned ? (1ll << 38) : 0), step_mixed, n_step));
+    cycles += n_step;
     ++refinements;
     const double rel = P->red_host[0] / nbs;
     const double factor = rel / prev;
@@ -567,6 +586,15 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
     if (st >= 0) {
       result = (csff_status)st;
       break;
+    }
+    // adaptive: the next step runs the cycles that this step's per-cycle factor
+    // rho predicts for rel rho^n <= rel_tol (a guess makes the first step's
+    // starting residual unknown, so adapting starts after the second step)
+    n = inner;
+    if (adaptive && (!guess || refinements >= 2) && rel > 0.0 && rel < rel_before) {
+      const double rho = std::pow(rel / rel_before, 1.0 / n_step);
+      const double need = std::ceil(std::log(P->opts.rel_tol / rel) / std::log(rho));
+      if (need < inner) n = std::max(1, (int)need);
     }
   }
   // u = 2^eb (hi + lo)
@@ -661,7 +689,7 @@ void csff_plan_destroy(csff_plan* P) {
                   (void*)P->dfq, (void*)P->dfpart})
     if (p) cudaFree(p);
   csff::free_ff_buffers(P);
-  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  destroy_graphs(P);
   if (P->gstream) cudaStreamDestroy(P->gstream);
   if (P->gev) cudaEventDestroy(P->gev);
   delete P;
@@ -684,6 +712,7 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
     return invalid("unknown smoother");
   if (opts->smoother == CSFF_SMOOTHER_GMRES && (opts->krylov_m < 0 || opts->krylov_m > csff::GM_MAX))
     return invalid("krylov_m must be 0..4 (0 selects 3)");
+  if (opts->adaptive_inner != 0 && opts->adaptive_inner != 1) return invalid("adaptive_inner must be 0 or 1");
   if (opts->nu1 < 0 || opts->nu2 < 0 || opts->nu1 + opts->nu2 == 0) return invalid("need nu1 + nu2 > 0");
   if (opts->precision != CSFF_PREC_FP64 && opts->precision != CSFF_PREC_MIXED) return invalid("bad precision");
   if (!(opts->rel_tol > 0.0) || opts->max_cycles < 1) return invalid("need rel_tol > 0 and max_cycles >= 1");
@@ -843,7 +872,7 @@ csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, doubl
   P->net = net;
   P->learned_levels = net ? levels : 0;
   P->learned_guard = guard;
-  if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+  destroy_graphs(P);
   return CSFF_OK;
 }
 
@@ -997,7 +1026,7 @@ csff_status csff_plan_set_potential(csff_plan* P, const void* q_dev) {
   P->fused_lc = -1;
   P->user_q = true;
   P->dfq_ready = false;
-  if (P->gexec) { cudaGraphExecDestroy(P->gexec); P->gexec = nullptr; }
+  destroy_graphs(P);
   return CSFF_OK;
 }
 

@@ -147,13 +147,19 @@ struct csff_plan {
   double log_rhs_max = 0, log_ff_max = 0;
   // fused V(1,1) RB-GS path (2D): levels >= fused_lc run in one CTA; -1 = unfused
   int fused_lc = -1;
-  // CUDA graph of one solver step (FP64 cycle or mixed refinement step),
-  // captured on an internal stream; re-captured when its key changes
+  // CUDA graphs of solver steps (FP64 cycle, or mixed refinement step of a
+  // given cycle count), captured on an internal stream and kept by key; the
+  // oldest is replaced when all slots are taken
+  static constexpr int GRAPH_SLOTS = 8;
+  struct StepGraph {
+    long long key = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t kernels = 0;         // kernel nodes in the captured graph
+  };
+  StepGraph graphs[GRAPH_SLOTS];
+  int graph_next = 0;
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  long long gkey = 0;
-  uint64_t gkernels = 0;          // kernel nodes in the captured graph
   bool use_graphs = true;
   // learned smoother (csff_plan_set_learned): RB-GS sweep followed by
   // u += N(r) on levels < learned_levels of the FP32 cycles

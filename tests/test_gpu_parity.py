@@ -359,6 +359,35 @@ def test_mixed_refinement_reaches_tight_tolerances(csff, dim, n):
     plan.close()
 
 
+@pytest.mark.parametrize("k", [20.0, 40.0])
+def test_adaptive_refinement_meets_the_tolerance_in_fewer_cycles(csff, k):
+    """adaptive_inner sizes each refinement step from the previous step's
+    per-cycle reduction factor: the solve meets the same tolerance (re-checked
+    with the oracle's FP64 operator) in at most the cycles of the fixed
+    schedule, and a solve from a converged guess stops after one step."""
+    c = W.mixed_2d(k, n=513)
+    c["opts"].update(precision="mixed", inner_cycles=6, coarsest_n=9)
+    p = O.problem_from_dict(c["problem"])
+    eta = c["eta"][:1]
+    runs = {}
+    for adaptive in (0, 1):
+        plan = csff.Plan(c["problem"], dict(c["opts"], adaptive_inner=adaptive))
+        u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+        st, info = plan.solve(eta, u)
+        assert st == csff.OK and info[0]["rel_res"] <= 1e-8
+        runs[adaptive] = (plan, u, info[0])
+    assert runs[1][2]["cycles"] <= runs[0][2]["cycles"]
+    ug = host(runs[1][1], (p.m,) * 2)
+    b = O.rhs(p, eta[0])
+    lv = O.make_level(p, p.n)
+    assert O.norm2(O.residual(lv, ug, b)) <= 1.01e-8 * O.norm2(b)
+    plan, u, _ = runs[1]
+    st, info = plan.solve(eta, u, use_guess=True)
+    assert st == csff.OK and info[0]["refinements"] == 1
+    for pl, _, _ in runs.values():
+        pl.close()
+
+
 def test_fp64_far_field_matches_on_paper_window_variant(csff):
     """Same grid, k and smoother as the 1025^2 case at n=257, with w = 28/k^2
     (largest term below e^14): FP64 maps agree to the 1e-6 target over all
