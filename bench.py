@@ -508,7 +508,7 @@ def measure_variants(csff, torch, dev, stream, flush):
 
 def measure_3d(csff, torch, dev, stream, flush):
     """257^3 on [-15,15]^3, k = 4, 16 incident directions, 64 x 32 angles,
-    FP32-inner / FP64-refinement; the step with the FP64-class sum-factorised
+    FP32-inner / double-float refinement; the step with the FP64-class sum-factorised
     far field, then the far field alone in both modes (FP64 and the
     tensor-core z-contraction) and the relative L2 distance of their maps."""
     c = W.big_3d(n=257, n_rhs=16)

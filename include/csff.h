@@ -98,7 +98,8 @@ typedef struct csff_opts {
   double rel_tol;     /* stop when ||b - A u||_2 <= rel_tol ||b||_2 */
   int max_cycles;     /* FP64: V-cycles; MIXED: total FP32 V-cycles */
   int precision;      /* CSFF_PREC_FP64 or CSFF_PREC_MIXED */
-  int inner_cycles;   /* MIXED: FP32 V-cycles per FP64 refinement step (>= 1) */
+  int inner_cycles;   /* MIXED: FP32 V-cycles per refinement step (>= 1; the
+                         most per step with adaptive_inner) */
   int krylov_m;       /* GMRES smoother: Krylov dimension m of each GMRES(m)
                          smoothing step, 1..4 (0 selects 3); nu1 / nu2 count
                          GMRES(m) steps.  Ignored by the other smoothers. */
@@ -116,7 +117,7 @@ typedef struct csff_opts {
 typedef struct csff_info {
   int status;          /* csff_status of this right-hand side */
   int cycles;          /* finest-level V-cycles run (FP64 or FP32) */
-  int refinements;     /* FP64 refinement steps (MIXED), else 0 */
+  int refinements;     /* refinement steps (MIXED), else 0 */
   double rel_res;      /* final ||r|| / ||b|| */
   double conv_factor;  /* (||r_k|| / ||r_0||)^(1/k) per V-cycle */
   int n_hist;
@@ -165,11 +166,14 @@ csff_status csff_rhs(csff_plan* plan, int n_rhs, const double* eta_host, void* b
    n_rhs x m^d) is read as the initial guess if use_guess != 0, else taken as 0,
    and overwritten with the solution.  info_host: n_rhs reports or NULL.
    Returns the worst status over the right-hand sides (CSFF_OK if all met
-   rel_tol).  FP64: V-cycles in FP64.  MIXED: FP64 residual r = b - A u, FP32
-   V-cycles on the power-of-two-scaled correction equation, FP64 update
-   (iterative refinement).  The coarsest-grid inverse is formed in FP64 in
-   both; FP32 cycles apply its FP32 rounding in FP32, since their coarse
-   solution is stored in FP32 (an FP64 product would be rounded anyway). */
+   rel_tol).  FP64: V-cycles in FP64.  MIXED: iterative refinement with u, b
+   and the coefficients scaled by 2^-e (e the exponent of max |b|) and held as
+   double-float pairs (two FP32 words, about 48 bits): the residual
+   r = b - A u formed in double-float, FP32 V-cycles on the correction
+   equation A e = r, the update u += e in double-float; u is assembled in FP64
+   at the end.  The coarsest-grid inverse is formed in FP64 in both; FP32
+   cycles apply its FP32 rounding in FP32, since their coarse solution is
+   stored in FP32 (an FP64 product would be rounded anyway). */
 csff_status csff_solve(csff_plan* plan, int n_rhs, const double* eta_host, void* u_dev,
                        int use_guess, csff_info* info_host);
 
@@ -344,9 +348,10 @@ csff_status csff_plan_set_learned(csff_plan* plan, csff_net* net, int levels, do
 csff_status csff_plan_copy_coefficients(const csff_plan* plan, int level, void* q32_dev, double* c_host);
 
 /* ---- batched solve: many uneven 2D problems in one persistent launch ----
-   Each instance is solved as by csff_solve with CSFF_PREC_MIXED (FP64
-   residual, FP32 V(1,1) red-black cycles on the scaled correction, FP64
-   update; Sec. 4 with the refinement loop), but all instances advance inside
+   Each instance runs the refinement loop of CSFF_PREC_MIXED with the FP64
+   residual and update of its own kernel (FP32 V(1,1) red-black cycles on the
+   scaled correction; Sec. 4 with the refinement loop; the fixed schedule of
+   inner_cycles per step, adaptive_inner is ignored), but all instances advance inside
    one cooperative kernel whose phases are separated by grid barriers; the
    tiles of every active instance are shared out among the CTAs, convergence
    is decided per instance on the device.  The solve is captured once as a
@@ -414,7 +419,8 @@ csff_status csff_norm2_noalloc(int arith, const void* v_dev, long long n, int ex
 enum {
   CSFF_PROF_FF_CONTRACT = 1, /* far-field stage-1 contraction (FP64) */
   CSFF_PROF_MG32 = 2,        /* multigrid kernels in FP32 */
-  CSFF_PROF_MG64 = 4,        /* multigrid kernels in FP64 (incl. refinement residuals) */
+  CSFF_PROF_MG64 = 4,        /* multigrid kernels in FP64 and the mixed solve's
+                                double-float refinement kernels */
   CSFF_PROF_FF_OTHER = 8,    /* far-field tables, g field, stage 2 */
   CSFF_PROF_TILES32 = 16     /* the fused FP32 V(1,1) tile kernels alone (also counted in MG32) */
 };

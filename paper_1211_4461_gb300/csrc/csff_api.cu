@@ -1,5 +1,6 @@
 // C ABI of libcsff: plan construction, the multigrid solve drivers (FP64 and
-// FP32-inner / FP64-refinement), the far-field call and the per-step calls.
+// FP32-inner / double-float refinement), the far-field call and the per-step
+// calls.
 #include <cmath>
 #include <complex>
 #include <cstring>

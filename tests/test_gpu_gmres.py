@@ -3,7 +3,7 @@
 The smoothing step is compared element by element with the oracle's GMRES(m)
 cycle on the same inputs (FP64 to 1e-11 of the update, FP32 to 1e-4); the
 V(1,1)/GMRES(3) solve at 9.9 degrees is compared by residual history and
-solution, in 2D and 3D, plain FP64 and FP32-inner / FP64-refinement; and the
+solution, in 2D and 3D, plain FP64 and FP32-inner / double-float refinement; and the
 red-black cycle at the same angle is shown to fail on the GPU as well."""
 import math
 

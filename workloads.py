@@ -79,7 +79,7 @@ def small_2d(k=2.0, n=65):
 
 
 def mixed_2d(k, n=1025):
-    """2D FP32-inner / FP64-refinement case: 1025x1025 on [-20,20]^2, rotation
+    """2D FP32-inner / double-float refinement case: 1025x1025 on [-20,20]^2, rotation
     pi/6, chi = -exp(-|x|^2/4), red-black GS V(1,1), 8 levels (9x9 coarsest),
     720 outgoing angles, tolerance 1e-8."""
     coarsest = (n - 1) // 128 + 1 if n >= 1025 else 9
