@@ -440,6 +440,14 @@ csff_status csff_prof_end(csff_prof_stats* out_host);
 
 /* eq. (thetagamma): gamma = atan(sin theta / (2 + cos theta)). */
 double csff_gamma_from_ecs(double theta_ecs);
+/* The adaptive refinement schedule (csff_opts.adaptive_inner): after a step of
+   cycles_run FP32 V-cycles took the relative residual from rel_before to
+   rel_after, the next step runs n = ceil(log(rel_tol / rel_after) / log rho
+   - 1e-9) cycles, rho = (rel_after / rel_before)^(1 / cycles_run) the per-cycle
+   reduction factor, clamped to [1, max_cycles].  Without a reduction
+   (rel_after >= rel_before, or a non-positive or non-finite value) it returns
+   max_cycles; max_cycles < 1 counts as 1.  Host only. */
+int csff_refinement_cycles(double rel_before, double rel_after, int cycles_run, double rel_tol, int max_cycles);
 const char* csff_status_string(csff_status s);
 const char* csff_last_error(void);
 /* Number of CUDA kernel launches the library made in this process. */

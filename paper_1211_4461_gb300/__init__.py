@@ -102,6 +102,7 @@ _SIGS = {
     "csff_norm2": (_i, [_vp, _i, _i, _vp, _dp]),
     "csff_vcycle": (_i, [_vp, _i, _vp, _vp]),
     "csff_gamma_from_ecs": (_d, [_d]),
+    "csff_refinement_cycles": (_i, [_d, _d, _i, _d, _i]),
     "csff_status_string": (_cp, [_i]),
     "csff_last_error": (_cp, []),
     "csff_kernel_launches": (C.c_uint64, []),
@@ -157,6 +158,12 @@ def _check(st, where, ok=(OK,)):
 def gamma_from_ecs(theta: float) -> float:
     """eq. (thetagamma)."""
     return _lib.csff_gamma_from_ecs(theta)
+
+
+def refinement_cycles(rel_before: float, rel_after: float, cycles_run: int, rel_tol: float,
+                      max_cycles: int) -> int:
+    """The adaptive refinement schedule's next cycle count (csff_refinement_cycles)."""
+    return int(_lib.csff_refinement_cycles(rel_before, rel_after, cycles_run, rel_tol, max_cycles))
 
 
 def kernel_launches() -> int:

@@ -592,11 +592,8 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
     // rho predicts for rel rho^n <= rel_tol (a guess makes the first step's
     // starting residual unknown, so adapting starts after the second step)
     n = inner;
-    if (adaptive && (!guess || refinements >= 2) && rel > 0.0 && rel < rel_before) {
-      const double rho = std::pow(rel / rel_before, 1.0 / n_step);
-      const double need = std::ceil(std::log(P->opts.rel_tol / rel) / std::log(rho));
-      if (need < inner) n = std::max(1, (int)need);
-    }
+    if (adaptive && (!guess || refinements >= 2))
+      n = csff_refinement_cycles(rel_before, rel, n_step, P->opts.rel_tol, inner);
   }
   // u = 2^eb (hi + lo)
   CK(csff::launch_df_to64(P->dfu, L.N, eb, u_out, s), "assemble u");
@@ -623,6 +620,21 @@ int worse(int a, int b) {
 extern "C" {
 
 double csff_gamma_from_ecs(double theta) { return std::atan(std::sin(theta) / (2.0 + std::cos(theta))); }
+
+int csff_refinement_cycles(double rel_before, double rel_after, int cycles_run, double rel_tol, int max_cycles) {
+  const int cap = max_cycles > 1 ? max_cycles : 1;
+  if (!(rel_after > 0.0) || !(rel_before > rel_after) || !std::isfinite(rel_before) || !(rel_tol > 0.0) ||
+      cycles_run < 1)
+    return cap;
+  if (rel_after <= rel_tol) return 1;
+  const double rho = std::pow(rel_after / rel_before, 1.0 / cycles_run);
+  if (!(rho > 0.0) || !(rho < 1.0)) return cap;
+  // 1e-9 of slack keeps a ratio that is an integer up to rounding from taking one
+  // cycle more
+  const double need = std::ceil(std::log(rel_tol / rel_after) / std::log(rho) - 1e-9);
+  if (!(need < cap)) return cap;
+  return need < 1.0 ? 1 : (int)need;
+}
 
 const char* csff_status_string(csff_status s) {
   switch (s) {

@@ -49,6 +49,27 @@ def test_binding_covers_the_header(lib):
     assert set(_declared()) <= set(csff.EXPORTS)
 
 
+def test_adaptive_refinement_schedule_host_helper(lib):
+    import paper_1211_4461_gb300 as csff
+    f = csff.refinement_cycles
+    # rho = 0.5 per cycle: from 1e-6, 1e-8 needs log2(100) = 6.64 -> 7 cycles
+    assert f(1e-6 * 2 ** 6, 1e-6, 6, 1e-8, 10) == 7
+    assert f(1e-6 * 2 ** 6, 1e-6, 6, 1e-8, 6) == 6                 # clamped to the step size
+    assert f(1.0, 0.1 ** 6, 6, 1e-8, 6) == 2                        # rho = 0.1: 1e-6 -> 1e-8 in 2
+    assert f(1.0, 2e-8, 1, 1e-8, 6) == 1                            # one cycle is enough
+    assert f(1.0, 5e-9, 3, 1e-8, 6) == 1                            # already converged: at least 1
+    assert f(1e-3, 2e-3, 3, 1e-8, 6) == 6                           # no reduction: full step
+    assert f(1e-3, 0.0, 3, 1e-8, 6) == 6                            # degenerate inputs: full step
+    assert f(float("nan"), 1e-4, 3, 1e-8, 6) == 6
+    assert f(1.0, 0.999999, 1, 1e-8, 6) == 6                        # rho near 1: capped
+    assert f(1.0, 0.5, 1, 1e-8, 0) == 1                             # cap below 1 counts as 1
+    # the prediction reaches the tolerance: rho^n rel_after <= rel_tol
+    for rho in (0.2, 0.35, 0.5, 0.7):
+        for rel in (1e-3, 3e-5, 2e-7):
+            n = f(rel / rho ** 4, rel, 4, 1e-8, 1000)
+            assert rel * rho ** n <= 1e-8 * (1 + 1e-12) and rel * rho ** (n - 1) > 1e-8 * (1 - 1e-12)
+
+
 def test_gamma_from_ecs_host_helper(lib):
     import paper_1211_4461_gb300 as csff
     import math
