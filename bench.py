@@ -4,8 +4,8 @@
 Workload (one "step"): four far-field maps on [-20,20]^2, rotation pi/6,
 chi = -exp(-|x|^2/4), k in {5, 10, 20, 40}, eta = +x: for each k the
 scattered wave is solved to ||b - A u|| <= 1e-8 ||b|| (FP32 red-black
-Gauss-Seidel V(1,1) cycles inside FP64 iterative refinement, 8 levels, 9x9
-coarsest grid) and its far field evaluated at 720 equispaced outgoing angles.
+Gauss-Seidel V(1,1) cycles inside a double-float iterative refinement, 8
+levels, 9x9 coarsest grid) and its far field evaluated at 720 equispaced outgoing angles.
 Inputs are synthetic (analytic potential and plane waves).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
@@ -168,6 +168,22 @@ def oracle_sample(n_angles_sample=18):
     return per_map, {"solve_s": t1 - t0, "ff_sample_s": t2 - t1, "cycles": res.cycles}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units all ranks processed (each rank the same share) per second of the
+    slowest rank: the whole-job throughput of a weak-scaling run."""
+    return units_per_rank * world / seconds
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -278,12 +294,8 @@ def run_ours(args, rank, world, local_rank):
     launches = csff.kernel_launches() - launches0
     if dist:
         dist.barrier()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = len(cases) * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    value = whole_job_rate(len(cases) * args.steps, world, total_ms / 1e3)
 
     # ---- the dominant kernels alone: one sequential step timing only the
     # fused FP32 V(1,1) tile launches (the largest share of device time) and the
@@ -321,12 +333,8 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         step(e2e=True)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = len(cases) * args.steps * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_val = whole_job_rate(len(cases) * args.steps, world, e2e_s)
     h2d = sum(int(eta_h[i].numel() * 8 + al_h[i].numel() * 8) for i in range(len(cases)))
     d2h = sum(int(F_h[i].numel() * 16 + Fe_h[i].numel() * 4) for i in range(len(cases)))
 

@@ -1,0 +1,71 @@
+"""The multi-rank logic of bench.py on the CPU, without a GPU.
+
+The path shards by replicas only: every rank runs the same step on its own GPU
+with no data-path collective, and the ranks meet only to time the job.  Two
+gloo ranks on 127.0.0.1 (world size 2) check that the timed duration is the
+maximum over the ranks and that the reported value is the whole job's units
+per second of the slowest rank; the reference arm runs on rank 0 alone."""
+import argparse
+import json
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 + 3.0 * rank            # the ranks' own timed durations differ
+        dist.barrier()
+        total_ms = bench.max_over_ranks(local_ms, dist, "cpu")
+        rate = bench.whole_job_rate(4 * 5, world, total_ms / 1e3)   # 4 maps x 5 steps per rank
+        with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+            f.write(f"{total_ms!r} {rate!r}")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_the_whole_job_rate(tmp_path):
+    mp.start_processes(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    for r in range(2):
+        total_ms, rate = map(float, (tmp_path / f"rank{r}.txt").read_text().split())
+        assert total_ms == 13.0
+        assert rate == pytest.approx(4 * 5 * 2 / 0.013, rel=1e-12)
+
+
+def test_one_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(7.5, None, "cpu") == 7.5
+    assert bench.whole_job_rate(20, 1, 0.5) == 40.0
+
+
+def _reference_args():
+    return argparse.Namespace(warmup=3, steps=2, gpus=2, precision="mixed", inner_cycles=6, adaptive_inner=True,
+                              sequential=False)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import bench
+    calls = []
+    monkeypatch.setattr(bench, "oracle_sample", lambda: calls.append(1) or (0.5, {}))
+    bench.run_reference(_reference_args(), rank=1, world=2)
+    assert calls == [] and capsys.readouterr().out == ""
+    bench.run_reference(_reference_args(), rank=0, world=2)
+    assert len(calls) == 3 + 2                   # warm-up and timed samples
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(2.0)
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
