@@ -69,3 +69,19 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     line = json.loads(capsys.readouterr().out.strip())
     assert line["impl"] == "reference" and line["value"] == pytest.approx(2.0)
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_end_to_end_on_the_host():
+    """`bench.py --impl reference` (the oracle on the host cores, one bounded
+    sample of the workload) prints one JSON line with the contract's keys."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], check=True, capture_output=True, text=True, timeout=600).stdout
+    line = json.loads(out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "maps/s"
+    assert line["config"]["workload"].startswith("2D 1025x1025")
