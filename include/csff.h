@@ -108,6 +108,11 @@ typedef struct csff_opts {
                          that the step's per-cycle reduction factor predicts
                          are needed to reach rel_tol (at most inner_cycles);
                          0 = always inner_cycles.  Same stopping test either way. */
+  int refine_fp64;    /* MIXED: 0 = the outer residual and update in double-float
+                         (pairs of FP32 words, about 48 bits, on the FP32 pipes);
+                         1 = in FP64 (r = b - A u, 2^-e r rounded to FP32 for the
+                         cycles, u += 2^e e), as in the classical mixed-precision
+                         refinement.  Both meet the same stopping test. */
 } csff_opts;
 
 #define CSFF_MAX_HISTORY 256

@@ -54,7 +54,7 @@ class OptsC(C.Structure):
     _fields_ = [("smoother", C.c_int), ("omega", C.c_double), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("coarsest_n", C.c_int), ("rel_tol", C.c_double), ("max_cycles", C.c_int),
                 ("precision", C.c_int), ("inner_cycles", C.c_int), ("krylov_m", C.c_int),
-                ("adaptive_inner", C.c_int)]
+                ("adaptive_inner", C.c_int), ("refine_fp64", C.c_int)]
 
 
 class InfoC(C.Structure):
@@ -233,7 +233,8 @@ def _opts_c(o):
     return OptsC(SMOOTHER[o.get("smoother", "jacobi")], float(o.get("omega", 2.0 / 3.0)), int(o.get("nu1", 1)),
                  int(o.get("nu2", 1)), int(o.get("coarsest_n", 5)), float(o.get("rel_tol", 1e-8)),
                  int(o.get("max_cycles", 100)), PRECISION[o.get("precision", "fp64")],
-                 int(o.get("inner_cycles", 3)), int(o.get("krylov_m", 0)), int(bool(o.get("adaptive_inner", 0))))
+                 int(o.get("inner_cycles", 3)), int(o.get("krylov_m", 0)), int(bool(o.get("adaptive_inner", 0))),
+                 int(bool(o.get("refine_fp64", 0))))
 
 
 class Batch:

@@ -468,6 +468,22 @@ void destroy_graphs(csff_plan* P) {
     }
 }
 
+// One refinement step with the FP64 residual and update (option refine_fp64):
+// 2^-e r in FP32 (e the exponent of ||r||), n FP32 V-cycles, u += 2^e e in FP64,
+// the new FP64 residual and its norm
+csff_status step_mixed64(csff_plan* P, int n) {
+  Level& L = P->lv[0];
+  cudaStream_t s = P->stream;
+  int* ex = reinterpret_cast<int*>(P->red_out + 4);
+  CK(csff::launch_to32_scaled(L.r64, L.N, P->red_out, L.b32, ex, s), "scale");
+  for (int c = 0; c < n; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
+  CK(csff::launch_update64(L.u64, L.u32, L.N, ex, s), "update");
+  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
+  CS(norm64(P, L.r64, P->refine_eb, 0));
+  CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s), "read norm");
+  return CSFF_OK;
+}
+
 // Run one step: replay the captured graph (capturing it first if the key
 // changed), or eagerly while kernel families of the solver are being timed.
 // arg: the body's parameter (FP64 step: the right-hand side's exponent; mixed
@@ -538,8 +554,11 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   tr.start(info);
   int cycles = 0, refinements = 0;
   const int inner = P->opts.inner_cycles > 0 ? P->opts.inner_cycles : 1;
-  // the step's graph depends on its cycle count and on whether the learned step runs
-  const long long key0 = 2ll << 40;
+  const bool r64 = P->opts.refine_fp64 != 0;
+  // the step's graph depends on its cycle count, on whether the learned step
+  // runs and, with the FP64 refinement, on the right-hand side's exponent (the
+  // prescale of its norm)
+  const long long key0 = r64 ? (3ll << 40) + (long long)(eb + 8192) * 4096 : 2ll << 40;
   const bool adaptive = P->opts.adaptive_inner != 0 && P->net == nullptr;
   int n = inner;
   // with a learned smoother the first two refinement steps run plain
@@ -549,10 +568,18 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   P->learned_off = P->net != nullptr;
   bool fell_back = false;
   double prev = 1.0, ref_factor = P->learned_guard;
-  // b' = 2^-eb b and q are split already (solve_loaded); u' = 2^-eb u (guess or
-  // zero)
+  // double-float: b' = 2^-eb b and q are split already (solve_loaded); u' =
+  // 2^-eb u (guess or zero).  FP64: u in L.u64, its residual and norm.
   cudaStream_t s = P->stream;
-  if (guess) {
+  if (r64) {
+    P->refine_eb = eb;
+    if (guess)
+      CK(cudaMemcpyAsync(L.u64, guess, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, s), "copy guess");
+    else
+      CK(csff::launch_zero<double>(L.u64, L.N, s), "zero");
+    CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
+    CS(norm64(P, L.r64, eb, 0));
+  } else if (guess) {
     CK(csff::launch_df_split(guess, L.N, -eb, P->dfu, nullptr, nullptr, nullptr, s), "split u");
     CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, nullptr, nullptr, s), "residual");
   } else {
@@ -560,13 +587,13 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
     // by the split)
     CK(cudaMemsetAsync(P->dfu, 0, sizeof(float4) * (size_t)L.N, s), "zero u");
   }
-  const double nbs = std::ldexp(nb, -eb);           // ||b'||
+  const double nbs = r64 ? nb : std::ldexp(nb, -eb);   // ||b|| or ||b'||, the norms' scale
   csff_status result = CSFF_OK;
   for (;;) {
     const bool learned = P->net && !P->learned_off;
     const int n_step = n;
     const double rel_before = prev;
-    CS(run_step(P, key0 + n_step + (learned ? (1ll << 38) : 0), step_mixed, n_step));
+    CS(run_step(P, key0 + n_step + (learned ? (1ll << 38) : 0), r64 ? step_mixed64 : step_mixed, n_step));
     cycles += n_step;
     ++refinements;
     const double rel = P->red_host[0] / nbs;
@@ -595,8 +622,10 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
     if (adaptive && (!guess || refinements >= 2))
       n = csff_refinement_cycles(rel_before, rel, n_step, P->opts.rel_tol, inner);
   }
-  // u = 2^eb (hi + lo)
-  CK(csff::launch_df_to64(P->dfu, L.N, eb, u_out, s), "assemble u");
+  if (r64)
+    CK(cudaMemcpyAsync(u_out, L.u64, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, s), "copy");
+  else
+    CK(csff::launch_df_to64(P->dfu, L.N, eb, u_out, s), "assemble u");     // u = 2^eb (hi + lo)
   return result;
 }
 
@@ -726,6 +755,7 @@ csff_status csff_plan_create(const csff_problem* prob, const csff_opts* opts, vo
   if (opts->smoother == CSFF_SMOOTHER_GMRES && (opts->krylov_m < 0 || opts->krylov_m > csff::GM_MAX))
     return invalid("krylov_m must be 0..4 (0 selects 3)");
   if (opts->adaptive_inner != 0 && opts->adaptive_inner != 1) return invalid("adaptive_inner must be 0 or 1");
+  if (opts->refine_fp64 != 0 && opts->refine_fp64 != 1) return invalid("refine_fp64 must be 0 or 1");
   if (opts->nu1 < 0 || opts->nu2 < 0 || opts->nu1 + opts->nu2 == 0) return invalid("need nu1 + nu2 > 0");
   if (opts->precision != CSFF_PREC_FP64 && opts->precision != CSFF_PREC_MIXED) return invalid("bad precision");
   if (!(opts->rel_tol > 0.0) || opts->max_cycles < 1) return invalid("need rel_tol > 0 and max_cycles >= 1");
@@ -970,7 +1000,8 @@ static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_in
   }
   if (eb <= -2000) eb = 0;
   const bool fp64 = P->opts.precision == CSFF_PREC_FP64;
-  if (fp64) {
+  const bool df = !fp64 && P->opts.refine_fp64 == 0;
+  if (!df) {
     CS(norm64(P, L.b64, eb, 1));
   } else {
     // the mixed solve's operands: q (once per coefficient set) and b' = 2^-eb b as
@@ -983,7 +1014,7 @@ static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_in
     CK(csff::launch_df_split(L.b64, L.N, -eb, P->dfb, L.b32, P->dfpart, P->red_out + 1, P->stream), "split b");
   }
   CS(read_scalars(P, 2));
-  const double nb = fp64 ? P->red_host[1] : std::ldexp(P->red_host[1], eb);
+  const double nb = df ? std::ldexp(P->red_host[1], eb) : P->red_host[1];
   csff_status st;
   if (nb == 0.0) {
     CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");

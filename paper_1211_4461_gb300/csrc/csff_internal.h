@@ -182,6 +182,7 @@ struct csff_plan {
   float4 *dfu = nullptr, *dfb = nullptr, *dfq = nullptr;
   bool dfq_ready = false;
   double* dfpart = nullptr;     // per-block partial sums of |r'|^2
+  int refine_eb = 0;            // FP64 refinement: the right-hand side's exponent of this solve
 
 };
 
@@ -253,6 +254,11 @@ long long df_residual_blocks(int dim, int m);
 cudaError_t launch_df_residual(int dim, const Level& L, const float4* u, const float4* b, const float4* q,
                                float2* r, double* part, double* norm_out, cudaStream_t s);
 cudaError_t launch_df_update(float4* u, const float2* e, long long N, cudaStream_t s);
+// FP64 refinement (option refine_fp64): r32 = 2^-e r with e the exponent of
+// *norm_dev (written to *exp_out); u += 2^e e32
+cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
+                               int* exp_out, cudaStream_t s);
+cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in, cudaStream_t s);
 cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2* out, cudaStream_t s);
 
 // ---- GMRES(m) smoothing step (gmres.cu) ----------------------------------------

@@ -322,6 +322,62 @@ __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uin
   b[idx] = cscale(acc, k2);
 }
 
+// ---- FP64 refinement of the mixed solve (option refine_fp64) -------------------
+// r32 = r64 * 2^-e with e = exponent of ||r64||_2 (so |r32| < 1 elementwise).
+// The scaling and the rounding to FP32 (to nearest) work on the bit fields,
+// keeping the pass off the FP64 pipe (1/61 of the FP32 rate on this part);
+// values below FP32's normal range, 2^-126 ||r|| and less, become zero.
+__device__ __forceinline__ float d2f_pow2(double v, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const int E = (int)((hi >> 20) & 0x7FF);
+  const int Ef = E - e - 1023 + 127;
+  if (E == 0 || Ef <= 0) return 0.f;
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  unsigned int f = ((unsigned int)Ef << 23) + (unsigned int)(mant >> 29);
+  const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull), halfway = 0x10000000u;
+  f += (rem > halfway || (rem == halfway && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+__global__ void k_to32_scaled(const double2* __restrict__ r, long long N, const double* __restrict__ nrm,
+                              float2* __restrict__ r32, int* __restrict__ exp_out) {
+  pdl_prologue();
+  int e;
+  frexp(*nrm, &e);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = e;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = r[i];
+    r32[i] = make_float2(d2f_pow2(v.x, e), d2f_pow2(v.y, e));
+  }
+}
+
+// FP32 value times 2^s as a double, exactly, from the bit fields (zero,
+// subnormal input, or a result outside the normal FP64 range take ldexp)
+__device__ __forceinline__ double f2d_pow2(float v, int s) {
+  const unsigned int b = __float_as_uint(v);
+  const int E = (int)((b >> 23) & 0xFFu), Ed = E + 896 + s;
+  if (E == 0 || Ed < 1 || Ed > 2046) return ldexp((double)v, s);
+  const long long bits = ((long long)(b >> 31) << 63) | ((long long)Ed << 52) |
+                         ((long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double(bits);
+}
+
+__global__ void k_update64(double2* __restrict__ u, const float2* __restrict__ e, long long N,
+                           const int* __restrict__ exp_in) {
+  pdl_prologue();
+  const int s = *exp_in;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 c = e[i];
+    double2 v = u[i];
+    v.x += f2d_pow2(c.x, s);
+    v.y += f2d_pow2(c.y, s);
+    u[i] = v;
+  }
+}
+
 template <typename T>
 __global__ void k_zero(cx<T>* v, long long N) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -461,6 +517,22 @@ cudaError_t launch_rhs(int dim, int m, const double2* const* chi_tab, int n_gaus
   else k_rhs<3><<<g, blk, 0, s>>>(t, n_gauss, uinc_tab, m, k2, b);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
+                               int* exp_out, cudaStream_t s) {
+  ProfScope ps(PF_MG64, s, 24.0 * N, 0);
+  cudaError_t e = launch_pdl(k_to32_scaled, dim3(flat_blocks(N)), dim3(256), 0, s, r, N, norm_dev, r32, exp_out);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,
+                            cudaStream_t s) {
+  ProfScope ps(PF_MG64, s, 40.0 * N, 0);
+  cudaError_t err = launch_pdl(k_update64, dim3(flat_blocks(N)), dim3(256), 0, s, u, e, N, exp_in);
+  count_launch();
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 cudaError_t launch_inject_q(int dim, const Level& F, const Level& C, cudaStream_t s) {

@@ -313,11 +313,15 @@ def _cone_rel_err(Fg, Fo, tn, e2, eps_work, tol):
     return cone, np.linalg.norm(Fg[cone] - F_o[cone]) / np.linalg.norm(F_o[cone])
 
 
+@pytest.mark.parametrize("refine_fp64", [0, 1])
 @pytest.mark.parametrize("k,n", [(5.0, 129), (10.0, 257)])
-def test_mixed_refinement_solution_and_far_field(csff, k, n):
+def test_mixed_refinement_solution_and_far_field(csff, k, n, refine_fp64):
+    """FP32 V-cycles inside the refinement, its residual and update in
+    double-float (default) or in FP64 (refine_fp64)."""
     c = W.mixed_2d(k, n=n)
     c["opts"]["coarsest_n"] = 9
     c["opts"]["precision"] = "mixed"
+    c["opts"]["refine_fp64"] = refine_fp64
     plan = csff.Plan(c["problem"], c["opts"])
     p = O.problem_from_dict(c["problem"])
     eta = c["eta"]
@@ -337,13 +341,15 @@ def test_mixed_refinement_solution_and_far_field(csff, k, n):
     assert cone.sum() >= 3 and err <= 1e-5
 
 
+@pytest.mark.parametrize("refine_fp64", [0, 1])
 @pytest.mark.parametrize("dim,n", [(2, 257), (3, 65)])
-def test_mixed_refinement_reaches_tight_tolerances(csff, dim, n):
+def test_mixed_refinement_reaches_tight_tolerances(csff, dim, n, refine_fp64):
     """The refinement's residual and update carry pairs of FP32 words (about 48
-    significant bits; exact products for the 2D and 3D centre weights 4 and 6), so
-    a mixed solve asked for 1e-11 meets it under the oracle's FP64 operator."""
+    significant bits; exact products for the 2D and 3D centre weights 4 and 6),
+    or FP64 words with refine_fp64, so a mixed solve asked for 1e-11 meets it
+    under the oracle's FP64 operator."""
     c = W.mixed_2d(10.0, n=n) if dim == 2 else W.big_3d(n=n, n_rhs=1)
-    c["opts"].update(precision="mixed", rel_tol=1e-11, max_cycles=400)
+    c["opts"].update(precision="mixed", rel_tol=1e-11, max_cycles=400, refine_fp64=refine_fp64)
     if dim == 2:
         c["opts"]["coarsest_n"] = 9
     plan = csff.Plan(c["problem"], c["opts"])
