@@ -75,13 +75,14 @@ TILES_DRAM_BYTES = 153274.0
 INNER_CYCLES = 6
 
 
-def _cases(precision, ks=None, inner=INNER_CYCLES, adaptive=False):
+def _cases(precision, ks=None, inner=INNER_CYCLES, adaptive=False, refine_fp64=False):
     out = []
     for k in (ks or KS):
         c = W.mixed_2d(k)
         c["opts"]["precision"] = precision
         c["opts"]["inner_cycles"] = inner
         c["opts"]["adaptive_inner"] = int(adaptive and precision == "mixed")
+        c["opts"]["refine_fp64"] = int(refine_fp64 and precision == "mixed")
         out.append(c)
     return out
 
@@ -91,6 +92,7 @@ def _config(args, extra=None):
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
            "inner_cycles": args.inner_cycles if args.precision == "mixed" else None,
            "adaptive_inner": bool(args.adaptive_inner) if args.precision == "mixed" else None,
+           "refinement": ("fp64" if args.refine_fp64 else "double-float") if args.precision == "mixed" else None,
            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
            "concurrency": ("the maps of a step solved one after another" if args.sequential else
                            "the maps of a step solved concurrently: one host thread and one CUDA stream per map")}
@@ -219,7 +221,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     stream = torch.cuda.current_stream()
     ks = tuple(float(k) for k in args.ks.split(",")) if args.ks else KS
-    cases = _cases(args.precision, ks, args.inner_cycles, args.adaptive_inner)
+    cases = _cases(args.precision, ks, args.inner_cycles, args.adaptive_inner, args.refine_fp64)
     # one stream and one host thread per map: the four solves are independent
     # and each alone leaves most SMs idle on its coarse levels
     streams = [torch.cuda.Stream(device=dev) for _ in cases]
@@ -840,6 +842,8 @@ def main():
                     help="size each refinement step from the previous step's reduction factor (default)")
     ap.add_argument("--fixed-inner", dest="adaptive_inner", action="store_false",
                     help="always inner-cycles FP32 V-cycles per refinement step")
+    ap.add_argument("--refine-fp64", action="store_true",
+                    help="mixed solve with the FP64 outer residual and update instead of double-float")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the maps of a step one after another on one host thread (for profilers, "
                          "which serialise kernels anyway and do not follow several capturing threads)")

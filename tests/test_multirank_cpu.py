@@ -55,7 +55,7 @@ def test_one_rank_needs_no_process_group():
 
 def _reference_args():
     return argparse.Namespace(warmup=3, steps=2, gpus=2, precision="mixed", inner_cycles=6, adaptive_inner=True,
-                              sequential=False)
+                              refine_fp64=False, sequential=False)
 
 
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
