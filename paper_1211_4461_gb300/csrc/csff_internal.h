@@ -254,12 +254,13 @@ long long df_residual_blocks(int dim, int m);
 cudaError_t launch_df_residual(int dim, const Level& L, const float4* u, const float4* b, const float4* q,
                                float2* r, double* part, double* norm_out, cudaStream_t s);
 cudaError_t launch_df_update(float4* u, const float2* e, long long N, cudaStream_t s);
-// FP64 refinement (option refine_fp64): r32 = 2^-e r with e the exponent of
-// *norm_dev (written to *exp_out); u += 2^e e32
+cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2* out, cudaStream_t s);
+
+// ---- FP64 refinement of the mixed solve (option refine_fp64; mg_kernels.cu) ------
+// r32 = 2^-e r with e the exponent of *norm_dev (written to *exp_out); u += 2^e e32
 cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
                                int* exp_out, cudaStream_t s);
 cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in, cudaStream_t s);
-cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2* out, cudaStream_t s);
 
 // ---- GMRES(m) smoothing step (gmres.cu) ----------------------------------------
 // u += V y for the GMRES(m) minimiser from u; V holds m+1 vectors of L.N

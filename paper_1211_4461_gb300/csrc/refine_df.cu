@@ -15,7 +15,9 @@
 // V-cycle is linear and bias-free, so no further scaling is needed, and the
 // correction it returns is added to u' with TwoSum.  The splits of b, q and the
 // initial guess work on the IEEE fields (df_bits.cuh); FP64 arithmetic is left
-// only in assembling u = 2^e_b (hi + lo) once per solve.
+// only in assembling u = 2^e_b (hi + lo) once per solve.  The classical form,
+// with the residual and update in FP64, stays available as the option
+// refine_fp64 (mg_kernels.cu).
 #include <cmath>
 
 #include "csff_internal.h"
