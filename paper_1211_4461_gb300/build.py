@@ -14,7 +14,9 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcsff.so")
 SOURCES = ["csff_api.cu", "mg_kernels.cu", "mg_fused.cu", "farfield.cu", "batch.cu", "learned.cu", "noalloc.cu",
            "gmres.cu", "partial_wave.cu", "refine_df.cu"]
-HEADERS = ["csff_internal.h", "mg_tiles.cuh", os.path.join("..", "..", "include", "csff.h")]
+# every header under csrc/ and the public one: an edit to any of them rebuilds every object
+HEADERS = sorted(f for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))) + [
+    os.path.join("..", "..", "include", "csff.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wno-unused-function"]
