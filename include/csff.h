@@ -410,8 +410,12 @@ csff_status csff_batch_debug_barrier(csff_batch* batch, int extra_arrivals, long
    whose work overlaps on the GPU (different streams, or different host
    threads on one device) race and give wrong results; serialise them.
    The first call on each device looks up the array's device address
-   (cudaGetSymbolAddress, with that device current); make that first call
-   before any stream capture. */
+   (cudaGetSymbolAddress, with that device current) and keeps it with the id
+   of the device's current CUDA context; a call that finds another context
+   there (after cudaDeviceReset, say) looks the address up again.  Make the
+   first call on a device, and the first after such a reset, before any
+   stream capture.  v_dev and out_dev must be addresses in the calling
+   thread's current context. */
 csff_status csff_norm2_noalloc(int arith, const void* v_dev, long long n, int exp_scale, double* out_dev,
                                void* stream);
 

@@ -187,8 +187,16 @@ NOALLOC_MAX_N = 1 << 25
 
 def norm2_noalloc(v, out, exp_scale=0, stream=None) -> None:
     """csff_norm2_noalloc: ||v||_2 into the device double `out` without any
-    device allocation (fixed scratch inside the library; see include/csff.h)."""
+    device allocation (fixed scratch inside the library; see include/csff.h).
+    v: contiguous complex128 or complex64 CUDA tensor; out: CUDA float64
+    tensor with at least one element (the result goes to its first)."""
     import torch
+    if not isinstance(v, torch.Tensor) or v.dtype not in (torch.complex128, torch.complex64):
+        raise TypeError("v must be a complex128 or complex64 CUDA tensor")
+    _require(v, v.dtype, v.numel(), "v")
+    _require(out, torch.float64, 1, "out")
+    if out.device != v.device:
+        raise ValueError("v and out must be on the same device")
     arith = ARITH_FP64 if v.dtype == torch.complex128 else ARITH_FP32
     _check(_lib.csff_norm2_noalloc(arith, _ptr(v), v.numel(), int(exp_scale), _ptr(out), _stream_handle(stream)),
            "norm2_noalloc")

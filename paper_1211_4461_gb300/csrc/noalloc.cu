@@ -9,7 +9,12 @@
 //
 // The host cannot use the array's name as a device address, so the first call
 // on each device looks the address up with cudaGetSymbolAddress (that device
-// current) and caches it; later calls on that device reuse it.
+// current) and caches it together with the id of the CUDA context it belongs
+// to; later calls on that device reuse it while the context is the same.  A
+// new context on the device (after cudaDeviceReset, for instance) holds a new
+// copy of the array, so the address is looked up again.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "csff_internal.h"
@@ -68,19 +73,48 @@ __global__ void k_na_finish(const double* __restrict__ partial, int nblk, double
 
 std::mutex g_na_mutex;
 double* g_na_addr[NA_MAX_DEVICES] = {nullptr};
+unsigned long long g_na_ctx[NA_MAX_DEVICES] = {0};
 
-// Device address of the partials array on the current device (set-up on first use).
+// Id of the calling thread's current CUDA context (0 if none is current or the
+// driver cannot tell).  The two driver calls are fetched through the runtime,
+// so the library does not link against the driver library.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    looked_up = true;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, nullptr) == cudaSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the partials array on the current device: looked up on
+// the first call on the device and again whenever its context has changed.
 cudaError_t partials_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_na_addr[dev] || ctx == 0 || ctx != g_na_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);   // makes the device's context current if needed
     if (e != cudaSuccess) return e;
     g_na_addr[dev] = static_cast<double*>(p);
+    g_na_ctx[dev] = current_context_id();
   }
   *out = g_na_addr[dev];
   return cudaSuccess;

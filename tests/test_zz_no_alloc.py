@@ -71,3 +71,37 @@ def test_noalloc_norm_prescale_and_limits(csff):
                                       0, C.c_void_p(out.data_ptr()), None)
     assert st == csff.ERR_INVALID_ARG
     assert b"scratch limit" in csff._lib.csff_last_error()
+
+
+def test_noalloc_norm_at_the_size_limit_through_the_wrapper(csff):
+    """The largest allowed n (2^25 complex64 values: every one of the 4096
+    partial slots in use), called through the Python wrapper, against a torch
+    FP64 reference; further calls leave the device's free memory unchanged."""
+    n = csff.NOALLOC_MAX_N
+    g = torch.Generator(device="cuda").manual_seed(61)
+    v = torch.randn(n, dtype=torch.complex64, device="cuda", generator=g)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    csff.norm2_noalloc(v, out)       # warm-up: the scratch address is looked up here
+    torch.cuda.synchronize()
+    ref = torch.sqrt(torch.sum(torch.view_as_real(v).double() ** 2)).item()
+    assert abs(out.item() - ref) <= 1e-12 * ref
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        csff.norm2_noalloc(v, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert abs(out.item() - ref) <= 1e-12 * ref
+
+
+def test_noalloc_wrapper_rejects_wrong_tensors(csff):
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        csff.norm2_noalloc(torch.zeros(16, dtype=torch.float32, device="cuda"), out)
+    v = torch.zeros(32, dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError):
+        csff.norm2_noalloc(v[::2], out)                   # strided view
+    with pytest.raises(ValueError):
+        csff.norm2_noalloc(v, torch.zeros(1, dtype=torch.float32, device="cuda"))
+    with pytest.raises(TypeError):
+        csff.norm2_noalloc(v, torch.zeros(1, dtype=torch.float64))   # host tensor
