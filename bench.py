@@ -781,13 +781,13 @@ def measure_partial_wave(csff, torch, dev, stream, flush):
         c = W.partial_wave(E, n=n)
         c["opts"].update(rel_tol=1e-10, max_cycles=100)
         plan = csff.Plan(c["problem"], c["opts"], stream=stream)
-        q, b, f, w = (torch.from_numpy(np.ascontiguousarray(x).ravel()).to(dev) for x in (c["q"], c["b"], c["f"], c["w"]))
+        V, f, w = (torch.from_numpy(np.ascontiguousarray(x).ravel()).to(dev) for x in (c["V"], c["f"], c["w"]))
         u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
         res = {}
 
         def run():
-            plan.set_potential(q)
-            st, info = plan.solve_rhs(b, u, ok=(csff.OK, csff.ERR_DIVERGED, csff.ERR_NOT_CONVERGED))
+            plan.set_schroedinger(E, V)
+            st, info = plan.solve_schroedinger(f, u, ok=(csff.OK, csff.ERR_DIVERGED, csff.ERR_NOT_CONVERGED))
             g = c["gamma"]
             lam, phi0 = csff.contour_bound_state(c["v1"], c["h"], g, -1.0)
             kn = math.sqrt(2.0 * (E - lam.real))

@@ -246,6 +246,21 @@ csff_status csff_plan_set_potential(csff_plan* plan, const void* q_dev);
    reported with u holding the last iterate). */
 csff_status csff_solve_rhs(csff_plan* plan, const void* b_dev, void* u_dev, int use_guess, csff_info* info);
 
+/* The partial-wave Schroedinger problem of Sec. 5.2, eq. (partialwave2d),
+   (-1/2 Delta + V - E) u = phi on the rotated contour, multiplied by 2: the
+   plan's operator with q = 2E - 2V and the right-hand side 2 phi.
+   csff_plan_set_schroedinger forms q on the device from the samples V_dev
+   (device, complex128, m^d values at the finest level's interior nodes, x
+   fastest: V = V1 + V2 + V12 at z; read during the call) and then proceeds as
+   csff_plan_set_potential.  csff_solve_schroedinger forms b = 2 phi from
+   phi_dev (device, complex128, m^d, read only) and proceeds as
+   csff_solve_rhs.  Errors: CSFF_ERR_INVALID_ARG (NULL arguments, E not
+   finite, singular coarsest operator), CSFF_ERR_CUDA; solve statuses as for
+   csff_solve_rhs. */
+csff_status csff_plan_set_schroedinger(csff_plan* plan, double E, const void* V_dev);
+csff_status csff_solve_schroedinger(csff_plan* plan, const void* phi_dev, void* u_dev, int use_guess,
+                                    csff_info* info);
+
 /* One-dimensional functions along the contour z_i = i h e^{i gamma},
    i = 1 .. m (zero at i = 0 and i = m + 1), with the three-point stencil of
    -1/2 d^2/dz^2; v (host, 2m doubles, interleaved re/im) holds V(z_i).

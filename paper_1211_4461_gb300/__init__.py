@@ -130,6 +130,8 @@ _SIGS = {
     "csff_plan_set_potential": (_i, [_vp, _vp]),
     "csff_far_field_work": (_i, [_vp, _dp]),
     "csff_solve_rhs": (_i, [_vp, _vp, _vp, _i, C.POINTER(InfoC)]),
+    "csff_plan_set_schroedinger": (_i, [_vp, _d, _vp]),
+    "csff_solve_schroedinger": (_i, [_vp, _vp, _vp, _i, C.POINTER(InfoC)]),
     "csff_contour_bound_state": (_i, [_i, _d, _d, _dp, _d, _dp, _dp]),
     "csff_contour_regular_solution": (_i, [_i, _d, _d, _dp, _d, _d, _dp]),
     "csff_separable_sum": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -536,6 +538,24 @@ class Plan:
         import torch
         _require(q, torch.complex128, self.N, "q")
         _check(_lib.csff_plan_set_potential(self._h, _ptr(q)), "plan_set_potential")
+
+    def set_schroedinger(self, E, V):
+        """q = 2E - 2V on the device from the potential samples V (complex128
+        CUDA tensor of m^d; csff_plan_set_schroedinger)."""
+        import torch
+        _require(V, torch.complex128, self.N, "V")
+        _check(_lib.csff_plan_set_schroedinger(self._h, float(E), _ptr(V)), "plan_set_schroedinger")
+
+    def solve_schroedinger(self, phi, u, use_guess=False, ok=(OK,)):
+        """Solve the doubled Schroedinger problem A u = 2 phi (complex128 CUDA
+        tensors of m^d; csff_solve_schroedinger); returns (status, info)."""
+        import torch
+        _require(phi, torch.complex128, self.N, "phi")
+        _require(u, torch.complex128, self.N, "u")
+        info = InfoC()
+        st = _lib.csff_solve_schroedinger(self._h, _ptr(phi), _ptr(u), int(bool(use_guess)), C.byref(info))
+        _check(st, "solve_schroedinger", ok)
+        return st, info.as_dict()
 
     def solve_rhs(self, b, u, use_guess=False, ok=(OK,)):
         """Solve A u = b (complex128 CUDA tensors of m^d); returns (status, info)."""

@@ -1048,11 +1048,10 @@ csff_status csff_solve_rhs(csff_plan* P, const void* b_dev, void* u_dev, int use
   return solve_loaded(P, (double2*)u_dev, use_guess, info);
 }
 
-csff_status csff_plan_set_potential(csff_plan* P, const void* q_dev) {
-  if (!P || !q_dev) return invalid("bad potential arguments");
+// The coefficients of every level from the finest level's q64 (already set):
+// injection to the coarse levels, 1/d and FP32 copies, the coarsest inverse.
+static csff_status user_q_levels(csff_plan* P) {
   cudaStream_t s = P->stream;
-  CK(cudaMemcpyAsync(P->lv[0].q64, q_dev, sizeof(double2) * (size_t)P->lv[0].N, cudaMemcpyDeviceToDevice, s),
-     "copy potential");
   for (size_t l = 1; l < P->lv.size(); ++l) CK(csff::launch_inject_q(P->dim, P->lv[l - 1], P->lv[l], s), "inject q");
   for (const Level& L : P->lv) CK(csff::launch_coefs_from_q(P->dim, L, s), "coefficients");
   const Level& Lc = P->lv.back();
@@ -1072,6 +1071,28 @@ csff_status csff_plan_set_potential(csff_plan* P, const void* q_dev) {
   P->dfq_ready = false;
   destroy_graphs(P);
   return CSFF_OK;
+}
+
+csff_status csff_plan_set_potential(csff_plan* P, const void* q_dev) {
+  if (!P || !q_dev) return invalid("bad potential arguments");
+  CK(cudaMemcpyAsync(P->lv[0].q64, q_dev, sizeof(double2) * (size_t)P->lv[0].N, cudaMemcpyDeviceToDevice,
+                     P->stream),
+     "copy potential");
+  return user_q_levels(P);
+}
+
+csff_status csff_plan_set_schroedinger(csff_plan* P, double E, const void* V_dev) {
+  if (!P || !V_dev || !std::isfinite(E)) return invalid("bad Schroedinger potential arguments");
+  Level& L = P->lv[0];
+  CK(csff::launch_affine((const double2*)V_dev, L.N, 2.0 * E, -2.0, L.q64, P->stream), "q = 2E - 2V");
+  return user_q_levels(P);
+}
+
+csff_status csff_solve_schroedinger(csff_plan* P, const void* phi_dev, void* u_dev, int use_guess, csff_info* info) {
+  if (!P || !phi_dev || !u_dev) return invalid("bad solve arguments");
+  Level& L = P->lv[0];
+  CK(csff::launch_affine((const double2*)phi_dev, L.N, 0.0, 2.0, L.b64, P->stream), "b = 2 phi");
+  return solve_loaded(P, (double2*)u_dev, use_guess, info);
 }
 
 csff_status csff_far_field(csff_plan* P, int n_rhs, const double* eta, const void* u_dev, int n_ang,

@@ -239,6 +239,9 @@ cudaError_t launch_zero(cx<T>* v, long long N, cudaStream_t s);
 // each level's q64 (csff_plan_set_potential)
 cudaError_t launch_inject_q(int dim, const Level& F, const Level& C, cudaStream_t s);
 cudaError_t launch_coefs_from_q(int dim, const Level& L, cudaStream_t s);
+// out = a + s v (complex v, real a and s) over N values (partial_wave.cu: the
+// Schroedinger coefficients q = 2E - 2V and right-hand side 2 phi)
+cudaError_t launch_affine(const double2* v, long long N, double a, double s, double2* out, cudaStream_t st);
 
 // ---- double-float refinement (refine_df.cu) -------------------------------------
 // out = 2^exp_scale v split into float pairs; r = b - A u in double-float, rounded

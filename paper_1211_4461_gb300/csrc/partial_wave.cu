@@ -128,6 +128,26 @@ cd bilinear_rq(const std::vector<cd>& dg, cd off, const std::vector<cd>& y) {
 }
 
 }  // namespace
+
+// Sec. 5.2: (-1/2 Delta + V - E) u = phi times 2 is the plan's A u = c (2d u -
+// sum_nbr u) - q u = b with q = 2E - 2V and b = 2 phi; out = a + s v per point
+// (a = 2E, s = -2 for q; a = 0, s = 2 for b).  Both scalings are exact.
+__global__ void k_affine(const double2* __restrict__ v, long long N, double a, double s, double2* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double2 x = v[i];
+    out[i] = make_double2(fma(s, x.x, a), s * x.y);
+  }
+}
+
+cudaError_t launch_affine(const double2* v, long long N, double a, double s, double2* out, cudaStream_t st) {
+  const int blk = 256;
+  const long long want = (N + blk - 1) / blk;
+  const int grid = (int)(want < 152 * 8 ? (want > 0 ? want : 1) : 152 * 8);
+  k_affine<<<grid, blk, 0, st>>>(v, N, a, s, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace csff
 
 using csff::cd;

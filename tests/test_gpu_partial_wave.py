@@ -29,7 +29,7 @@ def dev(a):
 
 def _plan(csff, c):
     plan = csff.Plan(c["problem"], c["opts"])
-    plan.set_potential(dev(c["q"]))
+    plan.set_schroedinger(c["E"], dev(c["V"]))
     return plan
 
 
@@ -38,7 +38,7 @@ def test_solve_with_user_potential_matches_direct_solve(csff, E):
     c = W.partial_wave(E, n=129)
     plan = _plan(csff, c)
     u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
-    st, info = plan.solve_rhs(dev(c["b"]), u)
+    st, info = plan.solve_schroedinger(dev(c["f"]), u)
     assert st == csff.OK and info["rel_res"] <= 1e-10
     ref = PW.solve(E, 129)
     got = u.cpu().numpy().reshape(ref.shape)
@@ -46,12 +46,36 @@ def test_solve_with_user_potential_matches_direct_solve(csff, E):
     plan.close()
 
 
+def test_sampled_coefficients_through_set_potential(csff):
+    """The same problem given as coefficient samples (the oracle's q = 2E - 2V
+    and 2 phi) through csff_plan_set_potential / csff_solve_rhs: the solution
+    matches the direct solve and the device-formed path."""
+    E, n = 1.0, 129
+    c = W.partial_wave(E, n=n)
+    _, _, ph = PW.fields(n)
+    plan = csff.Plan(c["problem"], c["opts"])
+    plan.set_potential(dev(PW.q_of(E, n)))
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    st, info = plan.solve_rhs(dev(2.0 * ph), u)
+    assert st == csff.OK and info["rel_res"] <= 1e-10
+    ref = PW.solve(E, n)
+    got = u.cpu().numpy().reshape(ref.shape)
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+    plan2 = _plan(csff, c)
+    u2 = torch.zeros(plan2.N, dtype=torch.complex128, device="cuda")
+    st2, info2 = plan2.solve_schroedinger(dev(c["f"]), u2)
+    assert st2 == csff.OK and info2["cycles"] == info["cycles"]
+    assert np.linalg.norm(u2.cpu().numpy().reshape(ref.shape) - got) <= 1e-12 * np.linalg.norm(got)
+    plan.close()
+    plan2.close()
+
+
 def test_mixed_precision_solve_with_user_potential(csff):
     c = W.partial_wave(2.0, n=257)
     c["opts"].update(precision="mixed", inner_cycles=2, rel_tol=1e-9)
     plan = _plan(csff, c)
     u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
-    st, info = plan.solve_rhs(dev(c["b"]), u)
+    st, info = plan.solve_schroedinger(dev(c["f"]), u)
     assert st == csff.OK and info["rel_res"] <= 1e-9
     ref = PW.solve(2.0, 257)
     got = u.cpu().numpy().reshape(ref.shape)
@@ -64,7 +88,7 @@ def test_vcycle_history_matches_oracle(csff):
     c = W.partial_wave(1.5, n=129)
     plan = _plan(csff, c)
     u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
-    st, info = plan.solve_rhs(dev(c["b"]), u)
+    st, info = plan.solve_schroedinger(dev(c["f"]), u)
     o = O.MGOptions(smoother="gmres", nu1=1, nu2=1, coarsest_n=5, rel_tol=1e-10, max_cycles=200, krylov_m=3)
     r = PW.mg_solve(1.5, 129, o)
     assert info["cycles"] == r.cycles
@@ -111,7 +135,7 @@ def test_cross_sections_end_to_end(csff):
     c = W.partial_wave(E, n=n)
     plan = _plan(csff, c)
     u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
-    st, _ = plan.solve_rhs(dev(c["b"]), u)
+    st, _ = plan.solve_schroedinger(dev(c["f"]), u)
     assert st == csff.OK
     g = c["gamma"]
     lam, phi0 = csff.contour_bound_state(c["v1"], c["h"], g, -1.0)

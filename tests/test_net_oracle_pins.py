@@ -63,3 +63,41 @@ def test_gradient_matches_central_differences(seed):
         tm = theta.copy(); tm[i] -= eps
         fd = (N.loss_and_grad(tp, r, q, c, 2)[0] - N.loss_and_grad(tm, r, q, c, 2)[0]) / (2 * eps)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-9, (i, fd, g[i])
+
+
+def _patch_operator_agrees_with_level_operator(apply_patch):
+    """The loss's patch operator, given the level's coefficients in units of
+    h^2, must equal h^2 times the multigrid oracle's operator (eq. csg with the
+    Sec. 5.2 stencil, built by the other oracle module) applied to a field that
+    vanishes outside the patch, on every point of the patch."""
+    import oracle.csff_oracle as O
+    p = O.Problem(2, 33, -6.0, 6.0, np.pi / 6, 3.0, [O.Gaussian(-0.8 + 0.1j, 2.0, (0.5, -0.4, 0.0))])
+    lv = O.make_level(p, p.n)
+    y = W.rand_complex((9, 11), 17)
+    Y = np.zeros((lv.m, lv.m), complex)
+    i0, j0 = 7, 12
+    Y[i0:i0 + 9, j0:j0 + 11] = y
+    ref = lv.h ** 2 * O.apply_A(lv, Y)[i0:i0 + 9, j0:j0 + 11]
+    got = apply_patch(lv.h ** 2 * lv.c, lv.h ** 2 * lv.q[i0:i0 + 9, j0:j0 + 11], y)
+    return np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_loss_operator_is_the_level_operator_in_units_of_h2():
+    assert _patch_operator_agrees_with_level_operator(N.apply_A_patch)
+
+
+def test_planted_mistakes_in_the_loss_operator_fail_its_pin():
+    def sign_on_c(c, q, y):
+        return N.apply_A_patch(-c, q, y)                     # c (nb - 4 y) - q y
+
+    def missing_q(c, q, y):
+        return N.apply_A_patch(c, 0 * q, y)
+
+    def conj_c(c, q, y):
+        return N.apply_A_patch(np.conj(c), q, y)
+
+    def diagonal_2(c, q, y):
+        return N.apply_A_patch(c, q, y) - 2 * c * y           # 2 y in place of 4 y
+
+    for bad in (sign_on_c, missing_q, conj_c, diagonal_2):
+        assert not _patch_operator_agrees_with_level_operator(bad), bad.__name__

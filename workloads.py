@@ -182,9 +182,11 @@ def partial_wave(E, n=257, R=15.0, gamma=8.5 * PI / 180):
     """Sec. 5.2-5.3 partial-wave model along the rotated contour: V1(x) =
     -4.5 e^{-x^2}, V2(y) = -4.5 e^{-y^2}, V12 = 2 e^{-(x+y)^2}, phi =
     e^{-3(x+y)^2} on [0, R]^2 (R = 15), rotation 8.5 degrees, energy E.
-    Samples at the interior nodes z = i h e^{i gamma} (x fastest): q = 2E -
-    2(V1 + V2 + V12), the right-hand side 2 phi, phi, V12 and V1 along one
-    axis; plan options for V(1,1) cycles with GMRES(3) smoothing."""
+    Samples at the interior nodes z = i h e^{i gamma} (x fastest): the
+    potential V = V1 + V2 + V12, the source phi, V12 and V1 along one axis;
+    plan options for V(1,1) cycles with GMRES(3) smoothing.  The problem's
+    coefficients (q = 2E - 2V, right-hand side 2 phi) are formed by whoever
+    solves it, not here."""
     h = R / (n - 1)
     z = np.arange(1, n - 1) * h * np.exp(1j * gamma)
     zy, zx = np.meshgrid(z, z, indexing="ij")
@@ -198,7 +200,7 @@ def partial_wave(E, n=257, R=15.0, gamma=8.5 * PI / 180):
         "opts": {"smoother": "gmres", "krylov_m": 3, "nu1": 1, "nu2": 1, "coarsest_n": 5,
                  "rel_tol": 1e-10, "max_cycles": 200},
         "h": h, "gamma": gamma, "E": E,
-        "q": 2.0 * E - 2.0 * V, "b": 2.0 * ph, "f": ph, "w": w12, "v1": v_one,
+        "V": V, "f": ph, "w": w12, "v1": v_one,
     }
 
 
