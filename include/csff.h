@@ -402,6 +402,12 @@ csff_status csff_batch_far_field(csff_batch* batch, const double* eta_host, cons
    levels (16 or 8 coarse points per tile side) and each CTA count per SM the
    occupancy allows, keeps the fastest; chosen values returned if non-NULL. */
 csff_status csff_batch_autotune(csff_batch* batch, const double* eta_host, int* tc_big_out, int* ctas_per_sm_out);
+/* Fix the tile choice by hand instead: tc_big = 16 or 8 coarse points per
+   tile side on the levels with at least 64 coarse points per side (16 is the
+   choice before any autotune), ctas_per_sm = CTAs per SM of the persistent
+   launch (0 = the occupancy maximum, larger values are clamped to it).
+   Errors: CSFF_ERR_INVALID_ARG. */
+csff_status csff_batch_set_tiles(csff_batch* batch, int tc_big, int ctas_per_sm);
 
 /* Test hook for the bounded barrier: extra_arrivals = 1 makes every grid
    barrier of the next solves wait for one CTA that does not exist, so each

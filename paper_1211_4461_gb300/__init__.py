@@ -115,6 +115,7 @@ _SIGS = {
     "csff_batch_far_field": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_dp), C.POINTER(_vp), C.POINTER(_vp)]),
     "csff_batch_autotune": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_i)]),
     "csff_batch_debug_barrier": (_i, [_vp, _i, C.c_longlong]),
+    "csff_batch_set_tiles": (_i, [_vp, _i, _i]),
     "csff_net_num_params": (_i, []),
     "csff_net_create": (_i, [_fp, C.POINTER(_vp)]),
     "csff_net_destroy": (None, [_vp]),
@@ -300,6 +301,10 @@ class Batch:
         tc, per = C.c_int(), C.c_int()
         _check(_lib.csff_batch_autotune(self._h, ep, C.byref(tc), C.byref(per)), "batch_autotune")
         return tc.value, per.value
+
+    def set_tiles(self, tc_big, ctas_per_sm=0):
+        """Fix the large levels' tile size (16 or 8) and the CTAs per SM."""
+        _check(_lib.csff_batch_set_tiles(self._h, int(tc_big), int(ctas_per_sm)), "batch_set_tiles")
 
     def debug_barrier(self, extra_arrivals, spin_limit=0):
         _check(_lib.csff_batch_debug_barrier(self._h, int(extra_arrivals), int(spin_limit)), "batch_debug_barrier")

@@ -763,6 +763,16 @@ csff_status csff_batch_debug_barrier(csff_batch* B, int extra_arrivals, long lon
   return CSFF_OK;
 }
 
+csff_status csff_batch_set_tiles(csff_batch* B, int tc_big, int ctas_per_sm) {
+  if (!B) return binvalid("NULL batch");
+  if (tc_big != 8 && tc_big != 16) return binvalid("tile size must be 8 or 16 coarse points");
+  if (ctas_per_sm < 0) return binvalid("ctas_per_sm must be >= 0");
+  B->tc_big = tc_big;
+  B->ctas_per_sm = ctas_per_sm;
+  if (B->gexec) { cudaGraphExecDestroy(B->gexec); B->gexec = nullptr; }   // parameters are baked into the graph
+  return upload_descriptors(B);
+}
+
 csff_status csff_batch_autotune(csff_batch* B, const double* eta, int* tc_big_out, int* ctas_per_sm_out) {
   if (!B || !eta) return binvalid("NULL argument");
   int dev = 0, sms = 0, occ = 0;

@@ -262,6 +262,11 @@ template <typename T> cx<T>* rbuf(Level& L);
 template <> double2* rbuf<double>(Level& L) { return L.r64; }
 template <> float2* rbuf<float>(Level& L) { return L.r32; }
 
+// The mixed solve with the FP64 refinement applies the coarsest inverse in
+// FP64 inside its FP32 cycles: FP64 for the outer residual, the update and the
+// coarsest-grid solve, FP32 for the rest of the cycle.
+bool coarse_fp64(const csff_plan* P) { return P->opts.precision == CSFF_PREC_MIXED && P->opts.refine_fp64 != 0; }
+
 template <typename T>
 csff_status smooth(csff_plan* P, int l, cx<T>* u, const cx<T>* b, int sweeps) {
   Level& L = P->lv[l];
@@ -301,6 +306,12 @@ csff_status vcycle(csff_plan* P, int l, cx<T>* u, const cx<T>* b) {
   const int nl = (int)P->lv.size();
   cudaStream_t s = P->stream;
   if (l == nl - 1) {
+    if constexpr (sizeof(T) == 4) {
+      if (coarse_fp64(P)) {
+        CK(csff::launch_coarse_solve_f64(P->coarse_inv, P->coarse_N, b, u, s), "coarse solve");
+        return CSFF_OK;
+      }
+    }
     CK(csff::launch_coarse_solve<T>(cinv<T>(P), P->coarse_N, b, u, s), "coarse solve");
     return CSFF_OK;
   }
@@ -376,7 +387,8 @@ csff_status run_fused_from(csff_plan* P, int l0, cx<T>* u, const cx<T>* b, bool 
     const cx<T>* bl = (l == l0) ? b : bbuf<T>(F);
     CK(csff::launch_down2<T>(F, C, in, zero_init || l > l0, bl, tbuf<T>(F), bbuf<T>(C), s), "fused down");
   }
-  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, cinv<T>(P), bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
+  CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, cinv<T>(P), coarse_fp64(P) ? P->coarse_inv : nullptr,
+                                   bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
      "coarse levels");
   for (int l = lc - 1; l >= l0; --l) {
     Level& F = P->lv[l];

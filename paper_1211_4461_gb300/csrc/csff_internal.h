@@ -222,6 +222,8 @@ cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx
                                cudaStream_t s);
 template <typename T>
 cudaError_t launch_coarse_solve(const cx<T>* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s);
+// FP32 vectors, FP64 inverse and product, one rounding of the result to FP32
+cudaError_t launch_coarse_solve_f64(const double2* inv, int N, const float2* b, float2* u, cudaStream_t s);
 // ||v||_2 * 2^{-e_scale}... computed as sqrt(sum |v 2^-e|^2) * 2^e; result to out (device)
 template <typename T>
 cudaError_t launch_norm2(const cx<T>* v, long long N, int exp_scale, double* partial, int nblk,
@@ -280,9 +282,11 @@ cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, boo
 template <typename T>
 cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
                        cx<T>* u_out, cudaStream_t s);
+// inv64 (FP32 cycles only, may be null): the FP64 inverse, applied in FP64
+// to the coarsest right-hand side in place of inv
 template <typename T>
-cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const cx<T>* inv, const cx<T>* b,
-                                 cx<T>* u, cudaStream_t s);
+cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const cx<T>* inv,
+                                 const double2* inv64, const cx<T>* b, cx<T>* u, cudaStream_t s);
 // dynamic shared-memory opt-in of the fused kernels on the current device
 cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc);
 // true while a graph is being captured (profiling brackets are suppressed)

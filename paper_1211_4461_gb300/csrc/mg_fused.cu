@@ -45,12 +45,12 @@ __global__ void __launch_bounds__(NT, tile_min_ctas<T, TC>()) k_up2(const cx<T>*
   tiles::up_tile<T, TC, false, G1>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, K, c, m, mc, u_out, smem_raw);
 }
 
-template <typename T, int D>
+template <typename T, int D, typename TI = T>
 __global__ void __launch_bounds__(1024) k_coarse_levels(CoarseLevels L, const cx<T>* __restrict__ b_top,
-                                                        cx<T>* __restrict__ u_top, const cx<T>* __restrict__ inv) {
+                                                        cx<T>* __restrict__ u_top, const cx<TI>* __restrict__ inv) {
   extern __shared__ unsigned char smem_raw[];
   pdl_prologue();
-  tiles::coarse_levels_block<T, D, false>(L, b_top, u_top, inv, smem_raw);
+  tiles::coarse_levels_block<T, D, false, TI>(L, b_top, u_top, inv, smem_raw);
 }
 
 template <typename T> const cx<T>* qt(const Level& L);
@@ -149,8 +149,8 @@ size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int rea
 }
 
 template <typename T>
-cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const cx<T>* inv, const cx<T>* b,
-                                 cx<T>* u, cudaStream_t s) {
+cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, const cx<T>* inv,
+                                 const double2* inv64, const cx<T>* b, cx<T>* u, cudaStream_t s) {
   CoarseLevels L{};
   L.nl = (int)lv.size() - lc;
   if (L.nl > 8 || L.nl < 1) return cudaErrorInvalidValue;
@@ -164,8 +164,13 @@ cudaError_t launch_coarse_levels(int dim, const std::vector<Level>& lv, int lc, 
   }
   size_t sm = coarse_levels_smem(dim, lv, lc, sizeof(T));
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * 2.0 * lv[lc].N, 0);
-  cudaError_t e = (dim == 2) ? launch_pdl(k_coarse_levels<T, 2>, dim3(1), dim3(1024), sm, s, L, b, u, inv)
-                             : launch_pdl(k_coarse_levels<T, 3>, dim3(1), dim3(1024), sm, s, L, b, u, inv);
+  cudaError_t e;
+  if (sizeof(T) == 4 && inv64)
+    e = (dim == 2) ? launch_pdl(k_coarse_levels<T, 2, double>, dim3(1), dim3(1024), sm, s, L, b, u, inv64)
+                   : launch_pdl(k_coarse_levels<T, 3, double>, dim3(1), dim3(1024), sm, s, L, b, u, inv64);
+  else
+    e = (dim == 2) ? launch_pdl(k_coarse_levels<T, 2>, dim3(1), dim3(1024), sm, s, L, b, u, inv)
+                   : launch_pdl(k_coarse_levels<T, 3>, dim3(1), dim3(1024), sm, s, L, b, u, inv);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -192,10 +197,14 @@ cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc) {
   if (s8 > (size_t)kMax) return cudaErrorInvalidValue;
   if (dim == 2) {
     if ((e = cudaFuncSetAttribute(k_coarse_levels<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)) ||
+        (e = cudaFuncSetAttribute(k_coarse_levels<float, 2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMax)) ||
         (e = cudaFuncSetAttribute(k_coarse_levels<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)))
       return e;
   } else {
     if ((e = cudaFuncSetAttribute(k_coarse_levels<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)) ||
+        (e = cudaFuncSetAttribute(k_coarse_levels<float, 3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMax)) ||
         (e = cudaFuncSetAttribute(k_coarse_levels<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMax)))
       return e;
   }
@@ -208,7 +217,7 @@ cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc) {
   template cudaError_t launch_up2<T>(const Level&, const Level&, const cx<T>*, const cx<T>*, const cx<T>*,   \
                                      cx<T>*, cudaStream_t);                                                \
   template cudaError_t launch_coarse_levels<T>(int, const std::vector<Level>&, int, const cx<T>*,           \
-                                               const cx<T>*, cx<T>*, cudaStream_t);
+                                               const double2*, const cx<T>*, cx<T>*, cudaStream_t);
 CSFF_FUSED_INST(double)
 CSFF_FUSED_INST(float)
 

@@ -162,6 +162,27 @@ __global__ void k_coarse_solve(const cx<T>* __restrict__ inv, int N, const cx<T>
   }
 }
 
+// The FP64 inverse applied in FP64 to an FP32 right-hand side; the product is
+// rounded once to FP32 (the mixed solve with its coarsest solve in FP64).
+__global__ void k_coarse_solve_f64(const double2* __restrict__ inv, int N, const float2* __restrict__ b,
+                                   float2* __restrict__ u) {
+  extern __shared__ unsigned char sb_raw[];
+  double2* sb = reinterpret_cast<double2*>(sb_raw);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = make_double2(b[j].x, b[j].y);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < N; i += nw) {
+    double2 acc = make_double2(0.0, 0.0);
+    const double2* row = inv + (long long)i * N;
+    for (int j = lane; j < N; j += 32) acc = cadd(acc, cmul(row[j], sb[j]));
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) u[i] = make_float2(__double2float_rn(acc.x), __double2float_rn(acc.y));
+  }
+}
+
 // ---- reductions ------------------------------------------------------------
 // Block-wide reduction; the result is valid in thread 0.
 template <typename V, typename Op>
@@ -469,6 +490,13 @@ template <typename T>
 cudaError_t launch_coarse_solve(const cx<T>* inv, int N, const cx<T>* b, cx<T>* u, cudaStream_t s) {
   ProfScope ps(mg_family<T>(), s, sizeof(cx<T>) * (2.0 * N + (double)N * N), 8.0 * N * N);
   k_coarse_solve<T><<<1, 256, (size_t)N * sizeof(cx<T>), s>>>(inv, N, b, u);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve_f64(const double2* inv, int N, const float2* b, float2* u, cudaStream_t s) {
+  ProfScope ps(mg_family<float>(), s, sizeof(float2) * 2.0 * N + sizeof(double2) * (double)N * N, 8.0 * N * N);
+  k_coarse_solve_f64<<<1, 256, (size_t)N * sizeof(double2), s>>>(inv, N, b, u);
   count_launch();
   return cudaGetLastError();
 }

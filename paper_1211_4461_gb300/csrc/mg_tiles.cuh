@@ -476,9 +476,20 @@ inline size_t coarse_levels_elems(const std::vector<Level>& lv, int lc) {
   return n;
 }
 
-template <typename T, int D, bool COH>
+template <typename T> __device__ __forceinline__ cx<T> to_cx(double2 v);
+template <> __device__ __forceinline__ double2 to_cx<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_cx<float>(double2 v) {
+  return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+}
+template <typename TI, typename T> __device__ __forceinline__ cx<TI> widen(cx<T> v) {
+  return mk<cx<TI>>((TI)v.x, (TI)v.y);
+}
+
+// TI: the arithmetic of the coarsest product (T, or double for FP32 cycles
+// whose coarsest solve runs in FP64; the product is then rounded to T once)
+template <typename T, int D, bool COH, typename TI = T>
 __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, cx<T>* u_top,
-                                    const cx<T>* __restrict__ inv, unsigned char* smem_raw) {
+                                    const cx<TI>* __restrict__ inv, unsigned char* smem_raw) {
   using C = cx<T>;
   C* base = reinterpret_cast<C*>(smem_raw);
   C* U[8];
@@ -571,14 +582,17 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
     const int n = N[last];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = warp; i < n; i += nw) {
-      C acc = zero_c<T>();
-      const C* row = inv + (long long)i * n;
-      for (int j = lane; j < n; j += 32) acc = xadd(acc, xmul(row[j], B[last][j]));
+      cx<TI> acc = zero_c<TI>();
+      const cx<TI>* row = inv + (long long)i * n;
+      for (int j = lane; j < n; j += 32) acc = xadd(acc, xmul(row[j], widen<TI, T>(B[last][j])));
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
-      if (lane == 0) U[last][i] = acc;
+      if (lane == 0) {
+        if constexpr (sizeof(TI) == sizeof(T)) U[last][i] = acc;
+        else U[last][i] = to_cx<T>(make_double2(acc.x, acc.y));
+      }
     }
     __syncthreads();
   }
