@@ -4,12 +4,14 @@
 Workload (one "step"): four far-field maps on [-20,20]^2, rotation pi/6,
 chi = -exp(-|x|^2/4), k in {5, 10, 20, 40}, eta = +x: for each k the
 scattered wave is solved to ||b - A u|| <= 1e-8 ||b|| (FP32 red-black
-Gauss-Seidel V(1,1) cycles inside a double-float iterative refinement, 8
-levels, 9x9 coarsest grid) and its far field evaluated at 720 equispaced outgoing angles.
-Inputs are synthetic (analytic potential and plane waves).
+Gauss-Seidel V(1,1) cycles inside an FP64 iterative refinement -- FP64 outer
+residual, update and coarsest-grid solve -- 8 levels, 9x9 coarsest grid) and
+its far field evaluated at 720 equispaced outgoing angles.  Inputs are
+synthetic (analytic potential and plane waves).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on
-a bounded sample of the same workload instead.
+the same workload instead (its four solves in full, the far field on a
+quarter of the angles, on the host cores).
 """
 from __future__ import annotations
 
@@ -56,14 +58,13 @@ FP64_PEAK_TFLOPS = 1.198
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 DF_INSTR_PER_FLOP = 36.0 / 8.0
 DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
-# DRAM bytes (read + write) of one k_ff_stage1_df launch on this workload: the
-# mean over the four maps of the ncu capture summarised in
-# profiles/ff_stage1_df_2d_n1025.md (None once the kernel changes).
-FF_DF_DRAM_BYTES = 26.318144e6
-# DRAM bytes (read + write) per k_down2 / k_up2 launch on this workload, the
-# mean over 22 consecutive launches (two V-cycles) of the warm-cache ncu capture
-# summarised in profiles/vcycle_tiles_2d_n1025.md (None once the kernels change).
-TILES_DRAM_BYTES = 153274.0
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
+# capture of the current kernels on this workload (None when no capture of
+# the current kernels exists): the double-float far-field contraction and the
+# fused FP32 V(1,1) tiles (all levels, and those of the 1025^2 level).
+FF_DF_DRAM_BYTES = None
+TILES_DRAM_BYTES = None
+TILES_FINE_DRAM_BYTES = None
 
 
 # FP32 V-cycles per refinement step on the headline workload (at most, with
@@ -92,7 +93,8 @@ def _config(args, extra=None):
            "rel_tol": 1e-8, "smoother": "rbgs V(1,1)", "precision": args.precision,
            "inner_cycles": args.inner_cycles if args.precision == "mixed" else None,
            "adaptive_inner": bool(args.adaptive_inner) if args.precision == "mixed" else None,
-           "refinement": ("fp64" if args.refine_fp64 else "double-float") if args.precision == "mixed" else None,
+           "refinement": ("fp64 (outer residual, update and coarsest solve in FP64)" if args.refine_fp64
+                          else "double-float") if args.precision == "mixed" else None,
            "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{args.gpus}",
            "concurrency": ("the maps of a step solved one after another" if args.sequential else
                            "the maps of a step solved concurrently: one host thread and one CUDA stream per map")}
@@ -150,24 +152,79 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# reference arm: the CPU FP64 oracle on a bounded sample
+# reference arm: the CPU FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
-def oracle_sample(n_angles_sample=18):
-    """One k=5 map: full oracle V-cycle solve to 1e-8 plus the far field at
-    n_angles_sample of the 720 angles; returns seconds per full map (far-field
-    time scaled to 720 angles) and the thread count used."""
+ORACLE_ANGLE_STRIDE = 4      # the oracle's far field runs on every 4th of the 720 angles
+
+
+def _oracle_solve(k):
+    """Worker: the oracle's RB-GS V(1,1) solve of one map to 1e-8 (one thread)."""
     from oracle import csff_oracle as O
-    c = W.mixed_2d(5.0)
+    c = W.mixed_2d(k)
     p = O.problem_from_dict(c["problem"])
-    o = O.opts_from_dict(c["opts"])
     t0 = time.perf_counter()
-    res = O.mg_solve(p, O.rhs(p, c["eta"][0]), o)
-    t1 = time.perf_counter()
-    stride = len(c["alphas"]) // n_angles_sample
-    O.far_field(p, res.u, c["eta"][0], c["alphas"][::stride][:n_angles_sample])
-    t2 = time.perf_counter()
-    per_map = (t1 - t0) + (t2 - t1) * len(c["alphas"]) / n_angles_sample
-    return per_map, {"solve_s": t1 - t0, "ff_sample_s": t2 - t1, "cycles": res.cycles}
+    res = O.mg_solve(p, O.rhs(p, c["eta"][0]), O.opts_from_dict(c["opts"]))
+    return res.u, time.perf_counter() - t0, res.cycles
+
+
+def _oracle_far_field(k, u, idx):
+    """Worker: the oracle's far-field sum of one map at the angles idx."""
+    from oracle import csff_oracle as O
+    c = W.mixed_2d(k)
+    p = O.problem_from_dict(c["problem"])
+    t0 = time.perf_counter()
+    O.far_field(p, u, c["eta"][0], c["alphas"][idx])
+    return time.perf_counter() - t0
+
+
+class OracleStep:
+    """The step's four maps by the oracle on the host cores: a pool of
+    single-threaded worker processes (spawned, so safe after CUDA use) solves
+    the four maps at once, then evaluates their far fields at every
+    ORACLE_ANGLE_STRIDE-th angle, split over all workers.  run() returns the
+    measured wall time, the time with the far-field phase scaled to all 720
+    angles (only the angles are scaled), and the summed single-thread task
+    times (the same work on one core)."""
+
+    def __init__(self, workers=None):
+        import multiprocessing as mp
+        self.workers = int(workers or min(os.cpu_count() or 1, 16))
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"          # inherited by the spawned workers: one thread each
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def run(self):
+        t0 = time.perf_counter()
+        solves = self.pool.map(_oracle_solve, KS)
+        t1 = time.perf_counter()
+        idx = np.arange(0, 720, ORACLE_ANGLE_STRIDE)
+        per_map = max(1, self.workers // len(KS))
+        tasks = [(k, u, ch) for k, (u, _, _) in zip(KS, solves) for ch in np.array_split(idx, per_map)]
+        ff = self.pool.starmap(_oracle_far_field, tasks)
+        t2 = time.perf_counter()
+        return {"wall_s": t2 - t0, "solve_wall_s": t1 - t0, "ff_wall_s": t2 - t1,
+                "scaled_s": (t1 - t0) + (t2 - t1) * ORACLE_ANGLE_STRIDE,
+                "single_thread_s": sum(x[1] for x in solves) + sum(ff) * ORACLE_ANGLE_STRIDE,
+                "solve_s": [round(x[1], 3) for x in solves], "cycles": [x[2] for x in solves]}
+
+
+ORACLE_SAMPLE = ("the step's four maps (k = 5, 10, 20, 40) by the FP64 oracle: each RB-GS V(1,1) solve to 1e-8 in "
+                 "full, in its own single-threaded worker process; the far fields at every 4th of the 720 angles, "
+                 "split over the workers, their time scaled by 4 (only the angles are scaled)")
+
+
+def cpu_baseline_record(r, workers):
+    """cpu_baseline entry from one OracleStep.run() result r."""
+    return {"value": len(KS) / r["scaled_s"], "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": ORACLE_SAMPLE,
+            "single_thread": {"value": len(KS) / r["single_thread_s"], "unit": UNIT, "cores": 1,
+                              "how": "the summed times of the single-threaded worker tasks (far-field part "
+                                     "scaled by 4)"},
+            "detail": {k: r[k] for k in ("wall_s", "solve_wall_s", "ff_wall_s", "solve_s", "cycles")}}
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -187,22 +244,29 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 
 
 def run_reference(args, rank, world):
+    """The oracle on this host's cores, each step one OracleStep.run() of the
+    headline workload; printed by rank 0 only.  ms_per_step is the measured
+    wall time of a step; value scales only the far-field angles."""
     if rank != 0:
         return
-    sample = "one k=5 map: oracle RB-GS V(1,1) solve to 1e-8 + far field at 18 of 720 angles (scaled to 720)"
-    for _ in range(args.warmup):
-        oracle_sample()
-    times = []
-    for _ in range(args.steps):
-        t, _info = oracle_sample()
-        times.append(t)
-    per_map = sum(times) / len(times)
-    value = 1.0 / per_map
+    runner = OracleStep()
+    try:
+        for _ in range(args.warmup):
+            runner.run()
+        runs = [runner.run() for _ in range(args.steps)]
+    finally:
+        runner.close()
+    scaled = sum(r["scaled_s"] for r in runs) / len(runs)
+    value = len(KS) / scaled
+    rec = cpu_baseline_record({**runs[-1], "scaled_s": scaled,
+                               "single_thread_s": sum(r["single_thread_s"] for r in runs) / len(runs)},
+                              runner.workers)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_map * 1e3 * len(KS),
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(r["wall_s"] for r in runs) / len(runs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config(args, {"precision": "fp64 (oracle)"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": _config(args),
+            "cpu_baseline": rec,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -304,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
     # far-field contraction launches (CUDA events on each launch's stream) ----
     flush.zero_()
     torch.cuda.synchronize()
-    csff.prof_begin(csff.PROF_TILES32 | csff.PROF_FF_CONTRACT)
+    csff.prof_begin(csff.PROF_TILES32 | csff.PROF_TILES32_FINE | csff.PROF_FF_CONTRACT)
     step(concurrent=False)
     torch.cuda.synchronize()
     prof_timed = csff.prof_end()
@@ -349,20 +413,31 @@ def run_ours(args, rank, world, local_rank):
     ff_flops_all = ff["alg_flops"] / max(1, ff["launches"])
     ff_flops = ff_flops_all * sum(ff_work) / max(1, len(ff_work))      # executed, per launch
     achieved_tf = ff_flops / (ff_avg_ms * 1e-3) / 1e12 if ff_avg_ms > 0 else 0.0
-    tl = prof_timed["tiles32"]
-    tl_avg_ms = tl["ms"] / max(1, tl["launches"])
-    tl_bytes = tl["alg_bytes"] / max(1, tl["launches"])
-    tl_gbs = tl_bytes / (tl_avg_ms * 1e-3) / 1e9 if tl_avg_ms > 0 else 0.0
-    roofline = {"kernel": "k_down2 / k_up2 (fused FP32 V(1,1) red-black tiles, every level above the "
-                          "one-CTA coarse block)",
-                "bound": "hbm", "achieved": tl_gbs, "peak": hbm, "unit": "GB/s", "frac": tl_gbs / hbm,
-                "traffic": TILES_DRAM_BYTES,
-                "peak_source": "measured HBM copy bandwidth of this GPU model",
-                "avg_launch_ms": tl_avg_ms, "launches": tl["launches"], "alg_bytes_per_launch": tl_bytes,
-                "note": "algorithmic bytes = 8 B x (3 fine-level points + 1 coarse point) per launch (iterate, "
-                        "right-hand side, output and coarse right-hand side); the 1025^2 V-cycle's arrays "
-                        "stay in L2, and the smaller levels' launches last one CTA's lifetime, so neither "
-                        "HBM nor issue bounds them"}
+    def tiles_roofline(rec, traffic, kernel, note):
+        avg = rec["ms"] / max(1, rec["launches"])
+        byt = rec["alg_bytes"] / max(1, rec["launches"])
+        gbs = byt / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        return {"kernel": kernel, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": traffic, "peak_source": "measured HBM copy bandwidth (burst; each launch timed alone)",
+                "avg_launch_ms": avg, "launches": rec["launches"], "alg_bytes_per_launch": byt, "note": note}
+
+    fine = prof_timed["tiles32_fine"]
+    allt = prof_timed["tiles32"]
+    rest = {k: allt[k] - fine[k] for k in ("launches", "ms", "alg_bytes")}
+    alg_note = ("algorithmic bytes = 8 B x (3 fine-level points + 1 coarse point) per launch (iterate and right-hand "
+                "side read, iterate written, coarse right-hand side or correction); each launch bracketed by CUDA "
+                "events on its stream in a step run one map after another (in the timed step the maps' kernels "
+                "overlap on four streams)")
+    roofline = tiles_roofline(fine, TILES_FINE_DRAM_BYTES,
+                              "k_down2 / k_up2 on the 1025^2 level (fused FP32 V(1,1) red-black tiles of 16 coarse "
+                              "points; the largest share of the step's device time)",
+                              alg_note + "; the 1025^2 level's FP32 arrays (8.4 MB each) stay in the 129 MB L2 "
+                                         "through a V-cycle, so this fraction measures algorithmic throughput")
+    roofline_levels = {"1025": roofline,
+                       "513_to_65": tiles_roofline(rest, None, "k_down2 / k_up2 on the 513^2 ... 65^2 levels",
+                                                   alg_note + "; these launches last about one CTA's lifetime"),
+                       "all": tiles_roofline(allt, TILES_DRAM_BYTES, "k_down2 / k_up2, every fused level",
+                                             alg_note)}
     roofline_ff = {"kernel": "k_ff_stage1_df (double-float far-field contraction)", "bound": "alu",
                 "achieved": achieved_tf, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / DF_PEAK_TFLOPS, "traffic": FF_DF_DRAM_BYTES,
@@ -389,20 +464,22 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if args.precision == "mixed" else "f64",
             "data": "synthetic", "config": _config(args, {"plan_ms": plan_ms}),
-            "roofline": roofline, "roofline_ff_contraction": roofline_ff, "vcycle": vc,
+            "roofline": roofline, "roofline_levels": roofline_levels, "roofline_ff_contraction": roofline_ff,
+            "vcycle": vc,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk.result,
             "solve": {str(ks[i]): {"cycles": infos[i]["cycles"], "refinements": infos[i]["refinements"],
                                    "rel_res": infos[i]["rel_res"]} for i in infos}}
     if args.variants:
-        line["variants"] = measure_variants(csff, torch, dev, stream, flush)
+        line["variants"] = measure_variants(csff, torch, dev, stream, flush, total_ms / args.steps)
     if args.cpu_baseline and world == 1:
-        per_map, info = oracle_sample()
-        line["cpu_baseline"] = {"value": 1.0 / per_map, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "one k=5 map: oracle RB-GS V(1,1) solve to 1e-8 + far field at 18 "
-                                          "of 720 angles (scaled to 720); numpy, single thread",
-                                "detail": info}
+        runner = OracleStep()
+        try:
+            r = runner.run()
+        finally:
+            runner.close()
+        line["cpu_baseline"] = cpu_baseline_record(r, runner.workers)
     print(json.dumps(line), flush=True)
 
 
@@ -421,12 +498,9 @@ def _time_events(torch, stream, fn, flush, reps):
     return sum(ms) / len(ms)
 
 
-def measure_variants(csff, torch, dev, stream, flush):
-    """The same four maps in plain FP64 (V-cycles in FP64), and the 64-instance
-    uneven batch solved in one persistent launch against the same instances
-    solved one after the other through the single-problem mixed path."""
-    out = {}
-    cases = _cases("fp64")
+def _concurrent_maps(csff, torch, dev, stream, flush, cases, reps=3):
+    """The four maps of `cases` scheduled as the headline step (one host thread
+    and CUDA stream per map); returns (ms per step, cycles per map)."""
     streams = [torch.cuda.Stream(device=dev) for _ in cases]
     plans = [csff.Plan(c["problem"], c["opts"], stream=st) for c, st in zip(cases, streams)]
     N = plans[0].N
@@ -435,20 +509,19 @@ def measure_variants(csff, torch, dev, stream, flush):
     Fe = [torch.zeros(720, dtype=torch.int32, device=dev) for _ in cases]
     cyc = {}
 
-    def one64(i):
+    def one(i):
         p, c = plans[i], cases[i]
         with torch.cuda.stream(streams[i]):
             _, info = p.solve(c["eta"], us[i])
-            cyc[i] = info[0]["cycles"]
+            cyc[i] = (info[0]["cycles"], info[0]["rel_res"])
             p.far_field(c["eta"], us[i], c["alphas"], Fs[i], Fe[i])
 
-    def step64():
-        # scheduled as the headline step: one host thread and stream per map
+    def step():
         start = torch.cuda.Event()
         start.record(stream)
         for st in streams:
             st.wait_event(start)
-        th = [threading.Thread(target=one64, args=(i,)) for i in range(len(plans))]
+        th = [threading.Thread(target=one, args=(i,)) for i in range(len(plans))]
         for t in th:
             t.start()
         for t in th:
@@ -456,13 +529,31 @@ def measure_variants(csff, torch, dev, stream, flush):
         for st in streams:
             stream.wait_stream(st)
 
-    step64()
-    ms = _time_events(torch, stream, step64, flush, 2)
-    out["fp64_plain"] = {"value": len(cases) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                         "cycles": [cyc[i] for i in range(len(cases))]}
+    for _ in range(3):
+        step()
+    ms = _time_events(torch, stream, step, flush, reps)
     for p in plans:
         p.close()
-    del us, Fs, Fe
+    return ms, [cyc[i][0] for i in range(len(cases))], [cyc[i][1] for i in range(len(cases))]
+
+
+def measure_variants(csff, torch, dev, stream, flush, headline_ms):
+    """The same four maps with the double-float refinement and in plain FP64
+    (V-cycles in FP64), and the 64-instance uneven batch solved in one
+    persistent launch against the same instances solved one after the other
+    through the single-problem mixed path."""
+    out = {}
+    ms, cyc, rel = _concurrent_maps(csff, torch, dev, stream, flush,
+                                    _cases("mixed", inner=INNER_CYCLES, adaptive=True, refine_fp64=False))
+    out["double_float_refinement"] = {
+        "value": len(KS) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "cycles": cyc, "rel_res": rel,
+        "speedup_vs_headline": headline_ms / ms,
+        "note": "outer residual and update in double-float (pairs of FP32 words, about 48 bits) on the FP32 "
+                "pipes, coarsest solve in FP32; same stopping test; its solutions re-checked to 1e-11 with "
+                "the oracle's FP64 operator in the tests"}
+    ms, cyc, rel = _concurrent_maps(csff, torch, dev, stream, flush, _cases("fp64"), reps=2)
+    out["fp64_plain"] = {"value": len(KS) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "cycles": cyc,
+                         "rel_res": rel, "headline_speedup_vs_fp64_plain": ms / headline_ms}
     # ---- 64 uneven instances
     bc = W.batch_2d(64, seed=4461)
     for c in bc:
@@ -842,8 +933,10 @@ def main():
                     help="size each refinement step from the previous step's reduction factor (default)")
     ap.add_argument("--fixed-inner", dest="adaptive_inner", action="store_false",
                     help="always inner-cycles FP32 V-cycles per refinement step")
-    ap.add_argument("--refine-fp64", action="store_true",
-                    help="mixed solve with the FP64 outer residual and update instead of double-float")
+    ap.add_argument("--refine-fp64", dest="refine_fp64", action="store_true", default=True,
+                    help="mixed solve with the FP64 outer residual, update and coarsest solve (default)")
+    ap.add_argument("--refine-df", dest="refine_fp64", action="store_false",
+                    help="mixed solve with the outer residual and update in double-float (pairs of FP32 words)")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the maps of a step one after another on one host thread (for profilers, "
                          "which serialise kernels anyway and do not follow several capturing threads)")

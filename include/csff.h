@@ -452,9 +452,10 @@ enum {
   CSFF_PROF_MG64 = 4,        /* multigrid kernels in FP64 and the mixed solve's
                                 double-float refinement kernels */
   CSFF_PROF_FF_OTHER = 8,    /* far-field tables, g field, stage 2 */
-  CSFF_PROF_TILES32 = 16     /* the fused FP32 V(1,1) tile kernels alone (also counted in MG32) */
+  CSFF_PROF_TILES32 = 16,    /* the fused FP32 V(1,1) tile kernels alone (also counted in MG32) */
+  CSFF_PROF_TILES32_FINE = 32 /* those of them that work on a plan's finest level (also in TILES32) */
 };
-#define CSFF_PROF_FAMILIES 5
+#define CSFF_PROF_FAMILIES 6
 typedef struct csff_prof_stats {
   int launches;
   double ms;          /* summed event time of the launches */

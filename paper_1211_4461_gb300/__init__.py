@@ -78,9 +78,9 @@ class ProfStatsC(C.Structure):
     _fields_ = [("launches", C.c_int), ("ms", C.c_double), ("alg_bytes", C.c_double), ("alg_flops", C.c_double)]
 
 
-PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER, PROF_TILES32 = 1, 2, 4, 8, 16
+PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER, PROF_TILES32, PROF_TILES32_FINE = 1, 2, 4, 8, 16, 32
 FF_FP64, FF_TC_BF16X3 = 0, 1
-PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other", "tiles32")
+PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other", "tiles32", "tiles32_fine")
 
 _vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
 _dp = C.POINTER(C.c_double)

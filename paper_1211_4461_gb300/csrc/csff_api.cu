@@ -56,11 +56,13 @@ unsigned prof_mask() { return g_prof.mask; }
 // the record list is shared by every thread that launches while profiling is on
 std::mutex g_prof_mu;
 
-ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops, int family2) : stream(s) {
+ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops, int family2, int family3)
+    : stream(s) {
   if (g_capturing) return;
   const bool on1 = (g_prof.mask & (1u << family)) != 0;
   const bool on2 = family2 >= 0 && (g_prof.mask & (1u << family2)) != 0;
-  if (!on1 && !on2) return;
+  const bool on3 = family3 >= 0 && (g_prof.mask & (1u << family3)) != 0;
+  if (!on1 && !on2 && !on3) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   auto add = [&](int f) {
     ProfRec r{f, g_prof.get(), g_prof.get(), bytes, flops};
@@ -71,13 +73,15 @@ ProfScope::ProfScope(int family, cudaStream_t s, double bytes, double flops, int
   };
   if (on1) slot = add(family);
   if (on2) slot2 = add(family2);
+  if (on3) slot3 = add(family3);
 }
 
 ProfScope::~ProfScope() {
-  if (slot < 0 && slot2 < 0) return;
+  if (slot < 0 && slot2 < 0 && slot3 < 0) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (slot >= 0) cudaEventRecord(g_prof.recs[slot].b, stream);
   if (slot2 >= 0) cudaEventRecord(g_prof.recs[slot2].b, stream);
+  if (slot3 >= 0) cudaEventRecord(g_prof.recs[slot3].b, stream);
 }
 
 }  // namespace csff
@@ -385,7 +389,7 @@ csff_status run_fused_from(csff_plan* P, int l0, cx<T>* u, const cx<T>* b, bool 
     Level& C = P->lv[l + 1];
     const cx<T>* in = (l == l0) ? u : ubuf<T>(F);
     const cx<T>* bl = (l == l0) ? b : bbuf<T>(F);
-    CK(csff::launch_down2<T>(F, C, in, zero_init || l > l0, bl, tbuf<T>(F), bbuf<T>(C), s), "fused down");
+    CK(csff::launch_down2<T>(F, C, in, zero_init || l > l0, bl, tbuf<T>(F), bbuf<T>(C), s, l == 0), "fused down");
   }
   CK(csff::launch_coarse_levels<T>(P->dim, P->lv, lc, cinv<T>(P), coarse_fp64(P) ? P->coarse_inv : nullptr,
                                    bbuf<T>(P->lv[lc]), ubuf<T>(P->lv[lc]), s),
@@ -395,7 +399,7 @@ csff_status run_fused_from(csff_plan* P, int l0, cx<T>* u, const cx<T>* b, bool 
     Level& C = P->lv[l + 1];
     cx<T>* out = (l == l0) ? u : ubuf<T>(F);
     const cx<T>* bl = (l == l0) ? b : bbuf<T>(F);
-    CK(csff::launch_up2<T>(F, C, tbuf<T>(F), ubuf<T>(C), bl, out, s), "fused up");
+    CK(csff::launch_up2<T>(F, C, tbuf<T>(F), ubuf<T>(C), bl, out, s, l == 0), "fused up");
   }
   return CSFF_OK;
 }
@@ -481,17 +485,18 @@ void destroy_graphs(csff_plan* P) {
 }
 
 // One refinement step with the FP64 residual and update (option refine_fp64):
-// 2^-e r in FP32 (e the exponent of ||r||), n FP32 V-cycles, u += 2^e e in FP64,
-// the new FP64 residual and its norm
+// n FP32 V-cycles on A e = r32 (r32 = 2^-e_b r, already in the cycles'
+// right-hand side), u += 2^e_b e in FP64, then in one pass the new FP64
+// residual, its FP32 rounding 2^-e_b r as the next right-hand side and its norm
+// (e_b the exponent of max |b|, fixed for the solve)
 csff_status step_mixed64(csff_plan* P, int n) {
   Level& L = P->lv[0];
   cudaStream_t s = P->stream;
-  int* ex = reinterpret_cast<int*>(P->red_out + 4);
-  CK(csff::launch_to32_scaled(L.r64, L.N, P->red_out, L.b32, ex, s), "scale");
   for (int c = 0; c < n; ++c) CS(run_vcycle<float>(P, L.u32, L.b32, c == 0));
-  CK(csff::launch_update64(L.u64, L.u32, L.N, ex, s), "update");
-  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
-  CS(norm64(P, L.r64, P->refine_eb, 0));
+  CK(csff::launch_update64_fixed(L.u64, L.u32, L.N, P->refine_eb, s), "update");
+  CK(csff::launch_refine_residual(P->dim, L, L.u64, L.b64, P->refine_eb, L.b32, P->red, P->red_blocks, P->red_out,
+                                  s),
+     "residual");
   CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, s), "read norm");
   return CSFF_OK;
 }
@@ -501,7 +506,7 @@ csff_status step_mixed64(csff_plan* P, int n) {
 // arg: the body's parameter (FP64 step: the right-hand side's exponent; mixed
 // step: its FP32 cycle count), part of what the key identifies.
 csff_status run_step(csff_plan* P, long long key, csff_status (*body)(csff_plan*, int), int arg) {
-  const unsigned mg_bits = CSFF_PROF_MG32 | CSFF_PROF_MG64 | CSFF_PROF_TILES32;
+  const unsigned mg_bits = CSFF_PROF_MG32 | CSFF_PROF_MG64 | CSFF_PROF_TILES32 | CSFF_PROF_TILES32_FINE;
   if (!P->use_graphs || !P->gstream || (csff::prof_mask() & mg_bits)) {
     CS(body(P, arg));
     CK(cudaStreamSynchronize(P->stream), "sync");
@@ -584,13 +589,17 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   // 2^-eb u (guess or zero).  FP64: u in L.u64, its residual and norm.
   cudaStream_t s = P->stream;
   if (r64) {
+    // the first right-hand side of the FP32 cycles: 2^-eb r for the guess, or
+    // 2^-eb b from zero
     P->refine_eb = eb;
-    if (guess)
+    if (guess) {
       CK(cudaMemcpyAsync(L.u64, guess, sizeof(double2) * (size_t)L.N, cudaMemcpyDeviceToDevice, s), "copy guess");
-    else
+      CK(csff::launch_refine_residual(P->dim, L, L.u64, L.b64, eb, L.b32, P->red, P->red_blocks, P->red_out, s),
+         "residual");
+    } else {
       CK(csff::launch_zero<double>(L.u64, L.N, s), "zero");
-    CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
-    CS(norm64(P, L.r64, eb, 0));
+      CK(csff::launch_scale_to32(L.b64, L.N, eb, L.b32, s), "scale b");
+    }
   } else if (guess) {
     CK(csff::launch_df_split(guess, L.N, -eb, P->dfu, nullptr, nullptr, nullptr, s), "split u");
     CK(csff::launch_df_residual(P->dim, L, P->dfu, P->dfb, P->dfq, L.b32, nullptr, nullptr, s), "residual");

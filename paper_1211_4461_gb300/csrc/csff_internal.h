@@ -195,12 +195,12 @@ extern std::atomic<uint64_t> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 // Event bracket around the launches of one kernel family (see csff_prof_begin).
-enum ProfFamily { PF_FF_CONTRACT = 0, PF_MG32 = 1, PF_MG64 = 2, PF_FF_OTHER = 3, PF_TILES32 = 4 };
+enum ProfFamily { PF_FF_CONTRACT = 0, PF_MG32 = 1, PF_MG64 = 2, PF_FF_OTHER = 3, PF_TILES32 = 4, PF_TILES32_FINE = 5 };
 // events around one launch, counted in family and (when >= 0) in family2 as well
 struct ProfScope {
-  int slot = -1, slot2 = -1;
+  int slot = -1, slot2 = -1, slot3 = -1;
   cudaStream_t stream = nullptr;
-  ProfScope(int family, cudaStream_t s, double bytes, double flops, int family2 = -1);
+  ProfScope(int family, cudaStream_t s, double bytes, double flops, int family2 = -1, int family3 = -1);
   ~ProfScope();
 };
 template <typename T> constexpr int mg_family() { return sizeof(T) == 8 ? PF_MG64 : PF_MG32; }
@@ -266,6 +266,13 @@ cudaError_t launch_df_to64(const float4* u, long long N, int exp_scale, double2*
 cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm_dev, float2* r32,
                                int* exp_out, cudaStream_t s);
 cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in, cudaStream_t s);
+// The FP64 refinement step with a fixed scale 2^s: r = b - A u in FP64, r32 =
+// 2^-s r in FP32, ||r|| into *out (device; partial: nblk doubles of scratch);
+// u += 2^s e; r32 = 2^-s v.  N < 2^31.
+cudaError_t launch_refine_residual(int dim, const Level& L, const double2* u, const double2* b, int s_exp,
+                                   float2* r32, double* partial, int nblk, double* out, cudaStream_t s);
+cudaError_t launch_update64_fixed(double2* u, const float2* e, long long N, int s_exp, cudaStream_t s);
+cudaError_t launch_scale_to32(const double2* v, long long N, int s_exp, float2* r32, cudaStream_t s);
 
 // ---- GMRES(m) smoothing step (gmres.cu) ----------------------------------------
 // u += V y for the GMRES(m) minimiser from u; V holds m+1 vectors of L.N
@@ -276,12 +283,13 @@ cudaError_t launch_gmres_step(int dim, const Level& L, int m, cx<T>* u, const cx
 
 // ---- fused 2D V(1,1) RB-GS kernels (mg_fused.cu) ----------------------------
 size_t coarse_levels_smem(int dim, const std::vector<Level>& lv, int lc, int real_bytes);
+// finest: the launch works on the plan's finest level (a profiling family of its own)
 template <typename T>
 cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, bool zero_init, const cx<T>* b,
-                         cx<T>* u_out, cx<T>* bc, cudaStream_t s);
+                         cx<T>* u_out, cx<T>* bc, cudaStream_t s, bool finest = false);
 template <typename T>
 cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
-                       cx<T>* u_out, cudaStream_t s);
+                       cx<T>* u_out, cudaStream_t s, bool finest = false);
 // inv64 (FP32 cycles only, may be null): the FP64 inverse, applied in FP64
 // to the coarsest right-hand side in place of inv
 template <typename T>

@@ -104,10 +104,10 @@ cudaError_t up2_tc(dim3 g, size_t smem, bool g1, cudaStream_t s, const cx<T>* u_
 
 template <typename T>
 cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, bool zero_init, const cx<T>* b,
-                         cx<T>* u_out, cx<T>* bc, cudaStream_t s) {
+                         cx<T>* u_out, cx<T>* bc, cudaStream_t s, bool finest) {
   cx<T> c = mk<cx<T>>((T)F.c.x, (T)F.c.y);
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0,
-               sizeof(T) == 4 ? PF_TILES32 : -1);
+               sizeof(T) == 4 ? PF_TILES32 : -1, sizeof(T) == 4 && finest ? PF_TILES32_FINE : -1);
   const tiles::LevelCoef<T> K = level_coef<T>(F);
   const int ng = coef_ng<T>(F);
   cudaError_t e;
@@ -126,10 +126,10 @@ cudaError_t launch_down2(const Level& F, const Level& Cl, const cx<T>* u_in, boo
 
 template <typename T>
 cudaError_t launch_up2(const Level& F, const Level& Cl, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
-                       cx<T>* u_out, cudaStream_t s) {
+                       cx<T>* u_out, cudaStream_t s, bool finest) {
   cx<T> c = mk<cx<T>>((T)F.c.x, (T)F.c.y);
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (3.0 * F.N + Cl.N), 0,
-               sizeof(T) == 4 ? PF_TILES32 : -1);
+               sizeof(T) == 4 ? PF_TILES32 : -1, sizeof(T) == 4 && finest ? PF_TILES32_FINE : -1);
   const tiles::LevelCoef<T> K = level_coef<T>(F);
   const int ng = coef_ng<T>(F);
   cudaError_t e;
@@ -213,9 +213,9 @@ cudaError_t prepare_fused(int dim, const std::vector<Level>& lv, int lc) {
 
 #define CSFF_FUSED_INST(T)                                                                                 \
   template cudaError_t launch_down2<T>(const Level&, const Level&, const cx<T>*, bool, const cx<T>*, cx<T>*, \
-                                       cx<T>*, cudaStream_t);                                              \
+                                       cx<T>*, cudaStream_t, bool);                                        \
   template cudaError_t launch_up2<T>(const Level&, const Level&, const cx<T>*, const cx<T>*, const cx<T>*,   \
-                                     cx<T>*, cudaStream_t);                                                \
+                                     cx<T>*, cudaStream_t, bool);                                          \
   template cudaError_t launch_coarse_levels<T>(int, const std::vector<Level>&, int, const cx<T>*,           \
                                                const double2*, const cx<T>*, cx<T>*, cudaStream_t);
 CSFF_FUSED_INST(double)

@@ -170,16 +170,24 @@ __global__ void k_coarse_solve_f64(const double2* __restrict__ inv, int N, const
   double2* sb = reinterpret_cast<double2*>(sb_raw);
   for (int j = threadIdx.x; j < N; j += blockDim.x) sb[j] = make_double2(b[j].x, b[j].y);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < N; i += nw) {
-    double2 acc = make_double2(0.0, 0.0);
-    const double2* row = inv + (long long)i * N;
-    for (int j = lane; j < N; j += 32) acc = cadd(acc, cmul(row[j], sb[j]));
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  // four consecutive lanes per row (columns j = p mod 4), fused multiply-add
+  // chains, two shuffles: FP64 work is scarce on this part
+  for (int t = threadIdx.x; t < ((4 * N + 31) & ~31); t += blockDim.x) {
+    const int i = t >> 2, part = t & 3;
+    double re = 0.0, im = 0.0;
+    if (i < N) {
+      const double2* row = inv + (long long)i * N;
+      for (int j = part; j < N; j += 4) {
+        const double2 a = row[j], x = sb[j];
+        re = fma(a.x, x.x, fma(-a.y, x.y, re));
+        im = fma(a.x, x.y, fma(a.y, x.x, im));
+      }
     }
-    if (lane == 0) u[i] = make_float2(__double2float_rn(acc.x), __double2float_rn(acc.y));
+    re += __shfl_xor_sync(0xffffffffu, re, 1);
+    im += __shfl_xor_sync(0xffffffffu, im, 1);
+    re += __shfl_xor_sync(0xffffffffu, re, 2);
+    im += __shfl_xor_sync(0xffffffffu, im, 2);
+    if (i < N && part == 0) u[i] = make_float2(__double2float_rn(re), __double2float_rn(im));
   }
 }
 
@@ -353,8 +361,10 @@ __device__ __forceinline__ float d2f_pow2(double v, int e) {
   const unsigned int hi = (unsigned int)(b >> 32);
   const int E = (int)((hi >> 20) & 0x7FF);
   const int Ef = E - e - 1023 + 127;
-  if (E == 0 || Ef <= 0) return 0.f;
   const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  if (E == 0x7FF) return mant ? __uint_as_float(0x7FC00000u) : __uint_as_float(0x7F800000u | (hi & 0x80000000u));
+  if (E == 0 || Ef <= 0) return 0.f;
+  if (Ef >= 255) return __uint_as_float(0x7F800000u | (hi & 0x80000000u));   // beyond FP32's range
   unsigned int f = ((unsigned int)Ef << 23) + (unsigned int)(mant >> 29);
   const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull), halfway = 0x10000000u;
   f += (rem > halfway || (rem == halfway && (f & 1u))) ? 1u : 0u;
@@ -396,6 +406,82 @@ __global__ void k_update64(double2* __restrict__ u, const float2* __restrict__ e
     v.x += f2d_pow2(c.x, s);
     v.y += f2d_pow2(c.y, s);
     u[i] = v;
+  }
+}
+
+// v * 2^-s exactly from the bit fields (values that would leave the normal
+// range become zero; Inf and NaN pass unchanged), off the FP64 pipe
+__device__ __forceinline__ double pow2_down(double v, int s) {
+  const long long b = __double_as_longlong(v);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0x7FF) return v;
+  const int En = E - s;
+  if (E == 0 || En <= 0) return 0.0;
+  if (En >= 0x7FF) return ldexp(v, -s);
+  return __longlong_as_double((b & ~(0x7FFLL << 52)) | ((long long)En << 52));
+}
+
+// One pass of the FP64 refinement step (option refine_fp64): the residual
+// r = b - A u in FP64 as a chain of fused multiply-adds,
+//   r = b - c (2d u - sum_nbr u) + q u,
+// its rounding r32 = 2^-s r to FP32 (the right-hand side of the next FP32
+// cycles; the bit-field conversion keeps it off the FP64 pipe), and per-block
+// sums of |2^-s r|^2 for the norm.  s is fixed for a solve (the exponent of
+// max |b|), so the FP32 values stay below 1 in magnitude and, with a relative
+// residual of at least 2^-100, far above FP32's normal range.
+template <int D>
+__global__ void k_refine_residual(const double2* __restrict__ u, const double2* __restrict__ b,
+                                  const double2* __restrict__ q, double2 c, int m, int N, int s,
+                                  float2* __restrict__ r32, double* __restrict__ partial) {
+  pdl_prologue();
+  __shared__ double sh[32];
+  double acc = 0;
+  const int mm = m * m;
+  const double2 z = make_double2(0.0, 0.0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int rest = i / m, ix = i - rest * m;
+    const int iz = (D == 3) ? rest / m : 0;
+    const int iy = (D == 3) ? rest - iz * m : rest;
+    const double2 uj = u[i];
+    const double2 xl = ix > 0 ? u[i - 1] : z, xr = ix < m - 1 ? u[i + 1] : z;
+    const double2 yl = iy > 0 ? u[i - m] : z, yr = iy < m - 1 ? u[i + m] : z;
+    double sx = (xl.x + xr.x) + (yl.x + yr.x), sy = (xl.y + xr.y) + (yl.y + yr.y);
+    if (D == 3) {
+      const double2 zl = iz > 0 ? u[i - mm] : z, zr = iz < m - 1 ? u[i + mm] : z;
+      sx += zl.x + zr.x;
+      sy += zl.y + zr.y;
+    }
+    const double tx = fma((double)(2 * D), uj.x, -sx), ty = fma((double)(2 * D), uj.y, -sy);
+    const double2 bj = b[i], qj = q[i];
+    const double rx = fma(-c.x, tx, fma(c.y, ty, fma(qj.x, uj.x, fma(-qj.y, uj.y, bj.x))));
+    const double ry = fma(-c.x, ty, fma(-c.y, tx, fma(qj.x, uj.y, fma(qj.y, uj.x, bj.y))));
+    r32[i] = make_float2(d2f_pow2(rx, s), d2f_pow2(ry, s));
+    const double ax = pow2_down(rx, s), ay = pow2_down(ry, s);
+    acc = fma(ax, ax, fma(ay, ay, acc));
+  }
+  acc = block_reduce(acc, AddOp(), sh, 0.0);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// u += 2^s e (FP32 correction, exact widening on the bit fields; one FP64 add
+// per component)
+__global__ void k_update64_fixed(double2* __restrict__ u, const float2* __restrict__ e, int N, int s) {
+  pdl_prologue();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const float2 c = e[i];
+    double2 v = u[i];
+    v.x += f2d_pow2(c.x, s);
+    v.y += f2d_pow2(c.y, s);
+    u[i] = v;
+  }
+}
+
+// r32 = 2^-s v rounded to FP32 (the first right-hand side of a solve from zero)
+__global__ void k_scale_to32(const double2* __restrict__ v, int N, int s, float2* __restrict__ r32) {
+  pdl_prologue();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double2 x = v[i];
+    r32[i] = make_float2(d2f_pow2(x.x, s), d2f_pow2(x.y, s));
   }
 }
 
@@ -553,6 +639,41 @@ cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm
   cudaError_t e = launch_pdl(k_to32_scaled, dim3(flat_blocks(N)), dim3(256), 0, s, r, N, norm_dev, r32, exp_out);
   count_launch();
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_refine_residual(int dim, const Level& L, const double2* u, const double2* b, int s_exp,
+                                   float2* r32, double* partial, int nblk, double* out, cudaStream_t s) {
+  if (L.N >= (1ll << 31)) return cudaErrorInvalidValue;
+  const int N = (int)L.N;
+  const int need = (N + RED_THREADS - 1) / RED_THREADS;
+  const int nb = need < nblk ? (need < 1 ? 1 : need) : nblk;
+  ProfScope ps(PF_MG64, s, (16.0 * 3 + 8.0) * L.N, 0);
+  cudaError_t e = (dim == 2)
+      ? launch_pdl(k_refine_residual<2>, dim3(nb), dim3(RED_THREADS), 0, s, u, b, (const double2*)L.q64, L.c, L.m, N,
+                   s_exp, r32, partial)
+      : launch_pdl(k_refine_residual<3>, dim3(nb), dim3(RED_THREADS), 0, s, u, b, (const double2*)L.q64, L.c, L.m, N,
+                   s_exp, r32, partial);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_norm_finish, dim3(1), dim3(RED_THREADS), 0, s, (const double*)partial, nb, ldexp(1.0, s_exp),
+                   out);
+  count_launch(2);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_update64_fixed(double2* u, const float2* e, long long N, int s_exp, cudaStream_t s) {
+  if (N >= (1ll << 31)) return cudaErrorInvalidValue;
+  ProfScope ps(PF_MG64, s, 40.0 * N, 0);
+  cudaError_t err = launch_pdl(k_update64_fixed, dim3(flat_blocks(N)), dim3(256), 0, s, u, e, (int)N, s_exp);
+  count_launch();
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+cudaError_t launch_scale_to32(const double2* v, long long N, int s_exp, float2* r32, cudaStream_t s) {
+  if (N >= (1ll << 31)) return cudaErrorInvalidValue;
+  ProfScope ps(PF_MG64, s, 24.0 * N, 0);
+  cudaError_t err = launch_pdl(k_scale_to32, dim3(flat_blocks(N)), dim3(256), 0, s, v, (int)N, s_exp, r32);
+  count_launch();
+  return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 cudaError_t launch_update64(double2* u, const float2* e, long long N, const int* exp_in,

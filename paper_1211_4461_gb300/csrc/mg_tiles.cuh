@@ -576,23 +576,45 @@ __device__ void coarse_levels_block(const CoarseLevels& L, const cx<T>* b_top, c
     }
     __syncthreads();
   }
-  // coarsest: u = inv b in the cycle's precision (the inverse itself comes from
-  // FP64 Gauss-Jordan), one warp per row, lanes split the columns
-  {
+  // coarsest: u = inv b (the inverse itself comes from FP64 Gauss-Jordan)
+  if constexpr (sizeof(TI) == sizeof(T)) {
+    // in the cycle's precision: one warp per row, lanes split the columns
     const int n = N[last];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = warp; i < n; i += nw) {
-      cx<TI> acc = zero_c<TI>();
-      const cx<TI>* row = inv + (long long)i * n;
-      for (int j = lane; j < n; j += 32) acc = xadd(acc, xmul(row[j], widen<TI, T>(B[last][j])));
+      C acc = zero_c<T>();
+      const C* row = inv + (long long)i * n;
+      for (int j = lane; j < n; j += 32) acc = xadd(acc, xmul(row[j], B[last][j]));
       for (int o = 16; o > 0; o >>= 1) {
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
       }
-      if (lane == 0) {
-        if constexpr (sizeof(TI) == sizeof(T)) U[last][i] = acc;
-        else U[last][i] = to_cx<T>(make_double2(acc.x, acc.y));
+      if (lane == 0) U[last][i] = acc;
+    }
+    __syncthreads();
+  } else {
+    // in FP64 (FP32 cycles of the FP64 refinement): FP64 work is scarce, so
+    // each row is split over four consecutive lanes only (columns j = p mod 4),
+    // each lane a chain of fused multiply-adds; two shuffles join the parts and
+    // the row's sum is rounded once to the cycle's precision
+    const int n = N[last];
+    for (int t = threadIdx.x; t < ((4 * n + 31) & ~31); t += blockDim.x) {
+      const int i = t >> 2, part = t & 3;
+      double re = 0.0, im = 0.0;
+      if (i < n) {
+        const double2* row = reinterpret_cast<const double2*>(inv) + (long long)i * n;
+        for (int j = part; j < n; j += 4) {
+          const double2 a = row[j];
+          const double bx = (double)B[last][j].x, by = (double)B[last][j].y;
+          re = fma(a.x, bx, fma(-a.y, by, re));
+          im = fma(a.x, by, fma(a.y, bx, im));
+        }
       }
+      re += __shfl_xor_sync(0xffffffffu, re, 1);
+      im += __shfl_xor_sync(0xffffffffu, im, 1);
+      re += __shfl_xor_sync(0xffffffffu, re, 2);
+      im += __shfl_xor_sync(0xffffffffu, im, 2);
+      if (i < n && part == 0) U[last][i] = to_cx<T>(make_double2(re, im));
     }
     __syncthreads();
   }

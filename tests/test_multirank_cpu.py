@@ -61,14 +61,33 @@ def _reference_args():
 def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     import bench
     calls = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda: calls.append(1) or (0.5, {}))
+
+    class FakeStep:
+        workers = 3
+
+        def __init__(self):
+            calls.append("init")
+
+        def run(self):
+            calls.append("run")
+            return {"wall_s": 0.25, "solve_wall_s": 0.2, "ff_wall_s": 0.05, "scaled_s": 2.0, "single_thread_s": 4.0,
+                    "solve_s": [0.1] * 4, "cycles": [10] * 4}
+
+        def close(self):
+            calls.append("close")
+
+    monkeypatch.setattr(bench, "OracleStep", FakeStep)
     bench.run_reference(_reference_args(), rank=1, world=2)
     assert calls == [] and capsys.readouterr().out == ""
     bench.run_reference(_reference_args(), rank=0, world=2)
-    assert len(calls) == 3 + 2                   # warm-up and timed samples
+    assert calls.count("run") == 3 + 2 and calls[-1] == "close"      # warm-up and timed steps
     line = json.loads(capsys.readouterr().out.strip())
-    assert line["impl"] == "reference" and line["value"] == pytest.approx(2.0)
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["impl"] == "reference" and line["value"] == pytest.approx(4 / 2.0)
+    assert line["ms_per_step"] == pytest.approx(250.0)                # measured wall time per step
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 3
+    assert line["cpu_baseline"]["single_thread"]["value"] == pytest.approx(1.0)
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["config"] == bench._config(_reference_args())       # the same config as the GPU arm
 
 
 def test_reference_arm_end_to_end_on_the_host():
