@@ -815,18 +815,28 @@ def measure_gmres_table2(csff, torch, dev, stream, flush):
     64^3, 128^3 and 256^3 grids for k0 = 1/4 ... 4: V-cycles, average
     convergence factor and time per solve, beside the values Table 2 prints
     (tests/golden/table2_vcycle_gmres3.txt).  At this angle the red-black
-    V-cycle diverges (checked in the tests)."""
+    V-cycle diverges (checked in the tests).  The same problems by full
+    multigrid (nested iteration, 1e-6 on every level): V-cycles per level, time
+    per solve against the V-cycles from zero, and the finest-level count Table 3
+    prints (tests/golden/table3_fmg_gmres3.txt)."""
     gold = {}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "table2_vcycle_gmres3.txt")
     for line in open(path):
         if line.strip() and not line.startswith("#"):
             k, pts, cyc, fac = line.split()
             gold[(float(k), int(pts))] = (int(cyc), float(fac))
+    # Table 3 (FMG cycle, same setting): V-cycles on the designated finest grid
+    fmg_gold = {}
+    for line in open(os.path.join(os.path.dirname(path), "table3_fmg_gmres3.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, pts, cyc = line.split()[:3]
+            fmg_gold[(float(k), int(pts))] = int(cyc)
     out = {}
     for pts in (64, 128, 256):
         rows = []
         for k in (0.25, 0.5, 1.0, 2.0, 4.0):
             c = W.paper_gmres(dim=3, k=k, n=pts + 1)
+            c["opts"]["precision"] = "fp64"
             plan = csff.Plan(c["problem"], c["opts"], stream=stream)
             u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
             info = {}
@@ -839,9 +849,21 @@ def measure_gmres_table2(csff, torch, dev, stream, flush):
             ms = _time_events(torch, stream, solve, flush, 2)
             i = info["i"]
             pc, pf = gold[(k, pts)]
+
+            def solve_fmg():
+                _, inf, cyc = plan.solve_fmg(c["eta"], u)
+                info["f"] = (inf[0], cyc[0])
+
+            solve_fmg()
+            ms_f = _time_events(torch, stream, solve_fmg, flush, 2)
+            fi, fc = info["f"]
             rows.append({"k0": k, "cycles": i["cycles"], "conv_factor": round(i["conv_factor"], 3),
                          "paper_cycles": pc, "paper_factor": pf, "ms_per_solve": ms,
-                         "converged": i["rel_res"] <= c["opts"]["rel_tol"]})
+                         "converged": i["rel_res"] <= c["opts"]["rel_tol"],
+                         "fmg": {"level_cycles_coarse_to_fine": fc, "finest_cycles": fi["cycles"],
+                                 "paper_finest_cycles": fmg_gold[(k, pts)], "ms_per_solve": ms_f,
+                                 "speedup_vs_vcycles_from_zero": ms / ms_f,
+                                 "converged": fi["status"] == csff.OK}})
             plan.close()
             del u
         out[f"{pts}^3"] = rows

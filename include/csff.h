@@ -182,6 +182,21 @@ csff_status csff_rhs(csff_plan* plan, int n_rhs, const double* eta_host, void* b
 csff_status csff_solve(csff_plan* plan, int n_rhs, const double* eta_host, void* u_dev,
                        int use_guess, csff_info* info_host);
 
+/* Full multigrid (Sec. 4, the FMG paragraph, and Table 3): for each incident
+   direction, b = k^2 chi u_in is carried to every coarser level by full
+   weighting, the coarsest level is solved directly, and on each finer level
+   the bi/trilinear interpolation of the coarser solution starts V(nu1, nu2)
+   cycles run until ||b_l - A_l u_l|| <= rel_tol ||b_l|| (the same tolerance
+   on every level, at most max_cycles per level).  u_dev (c128, n_rhs x m^d)
+   receives the finest level's iterate.  level_cycles (host, n_rhs x
+   (n_levels - 1) ints, or NULL) receives the V-cycles run on each level above
+   the coarsest, coarsest first; info_host (n_rhs reports or NULL) the finest
+   level's: history[0] is the relative residual of the interpolated guess.
+   FP64 plans only (CSFF_ERR_UNSUPPORTED otherwise).  Returns the worst status
+   over the levels and right-hand sides. */
+csff_status csff_solve_fmg(csff_plan* plan, int n_rhs, const double* eta_host, void* u_dev, int* level_cycles,
+                           csff_info* info_host);
+
 /* Far-field map, eq. (FFmap) over the contour (eq. I2complex), for each
    right-hand side r and outgoing direction a:
      F[r*n_ang + a] = k^2 e^{i d gamma} h^d sum_j e^{-i k z_j.alpha_a}

@@ -469,6 +469,59 @@ def mg_solve(prob: Problem, b: np.ndarray, opts: MGOptions, u0=None) -> SolveRes
     return SolveResult(u, hist, cycles, hist[-1] <= opts.rel_tol)
 
 
+@dataclass
+class FMGResult:
+    u: np.ndarray
+    level_cycles: list          # V-cycles on each level above the coarsest, coarse to fine
+    level_history: list         # per level: ||r_k|| / ||b_l||, k = 0 (interpolated guess), 1, ...
+    converged: bool
+
+    @property
+    def cycles(self) -> int:
+        """V-cycles on the finest level."""
+        return self.level_cycles[-1] if self.level_cycles else 0
+
+    @property
+    def history(self) -> list:
+        return self.level_history[-1] if self.level_history else [0.0]
+
+
+def fmg_solve(prob: Problem, b: np.ndarray, opts: MGOptions) -> FMGResult:
+    """Full multigrid (Sec. 4, the FMG paragraph with Table 3): a nested
+    iteration of V-cycles.  The right-hand side is carried to every coarser
+    level by full weighting, b_{l+1} = FW(b_l); the coarsest level is solved
+    directly; then on each finer level, from the second coarsest up to the
+    finest, the bi/trilinear interpolation of the coarser level's solution is
+    the initial guess of V(nu1, nu2)-cycles on A_l u_l = b_l, run until
+    ||b_l - A_l u_l|| <= rel_tol ||b_l|| (the same tolerance on every level)
+    or max_cycles.  The paper does not say how the coarse right-hand sides are
+    formed or what the tolerance is relative to; these are the readings taken."""
+    levels = make_hierarchy(prob, opts.coarsest_n)
+    lu = coarse_factor(levels[-1])
+    bs = [b]
+    for _ in levels[1:]:
+        bs.append(restrict_fw(bs[-1]))
+    u = coarse_solve(lu, bs[-1])
+    counts, hists = [], []
+    converged = True
+    for l in range(len(levels) - 2, -1, -1):
+        u = prolong(u)
+        lv = levels[l]
+        nb = norm2(bs[l])
+        hist = [norm2(residual(lv, u, bs[l])) / nb] if nb > 0 else [0.0]
+        c = 0
+        while hist[-1] > opts.rel_tol and c < opts.max_cycles:
+            u = vcycle(levels[l:], lu, 0, u, bs[l], opts)
+            c += 1
+            hist.append(norm2(residual(lv, u, bs[l])) / nb)
+            if not np.isfinite(hist[-1]):
+                break
+        counts.append(c)
+        hists.append(hist)
+        converged = converged and hist[-1] <= opts.rel_tol
+    return FMGResult(u, counts, hists, converged)
+
+
 # ---------------------------------------------------------------------------
 # Far field (eq. FFmap over the contour, eq. I2complex)
 # ---------------------------------------------------------------------------

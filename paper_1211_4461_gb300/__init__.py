@@ -92,6 +92,7 @@ _SIGS = {
     "csff_plan_describe": (_i, [_vp, C.POINTER(DescC)]),
     "csff_rhs": (_i, [_vp, _i, _dp, _vp]),
     "csff_solve": (_i, [_vp, _i, _dp, _vp, _i, C.POINTER(InfoC)]),
+    "csff_solve_fmg": (_i, [_vp, _i, _dp, _vp, C.POINTER(_i), C.POINTER(InfoC)]),
     "csff_far_field": (_i, [_vp, _i, _dp, _vp, _i, _dp, _vp, _vp]),
     "csff_plan_set_far_field_mode": (_i, [_vp, _i]),
     "csff_residual": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
@@ -485,6 +486,21 @@ class Plan:
         st = _lib.csff_solve(self._h, nr, ep, _ptr(u), int(bool(use_guess)), infos)
         _check(st, "solve", ok)
         return st, [infos[i].as_dict() for i in range(nr)]
+
+    def solve_fmg(self, eta, u, ok=(OK,)):
+        """Full multigrid (csff_solve_fmg) for each incident direction; returns
+        (status, [info dicts], level cycles per right-hand side, coarsest first)."""
+        import torch
+        eta, ep = _dbl(eta)
+        nr = eta.shape[0]
+        _require(u, torch.complex128, nr * self.N, "u")
+        nl = len(self.describe()["levels"])
+        cyc = (_i * max(1, nr * (nl - 1)))()
+        infos = (InfoC * max(1, nr))()
+        st = _lib.csff_solve_fmg(self._h, nr, ep, _ptr(u), cyc, infos)
+        _check(st, "solve_fmg", ok)
+        return st, [infos[i].as_dict() for i in range(nr)], \
+            [list(cyc[r * (nl - 1):(r + 1) * (nl - 1)]) for r in range(nr)]
 
     def far_field(self, eta, u, alphas, F, F_exp=None, ok=(OK, WARN_ILL_CONDITIONED)):
         import torch

@@ -547,6 +547,22 @@ csff_status run_step(csff_plan* P, long long key, csff_status (*body)(csff_plan*
   return CSFF_OK;
 }
 
+// One FP64 V-cycle on level l of the full-multigrid iteration (iterate and
+// right-hand side in that level's u64 and b64; the levels below serve as the
+// cycle's work space), then the level's residual norm into red_host[0].  The
+// level travels in the step argument: l * 8192 + (e + 4096), e the prescale
+// exponent of the norms.
+csff_status step_fmg_level(csff_plan* P, int arg) {
+  const int l = arg / 8192, e = arg % 8192 - 4096;
+  Level& L = P->lv[l];
+  if (P->fused_lc > l) CS(run_fused_from<double>(P, l, L.u64, L.b64, false));
+  else CS(vcycle<double>(P, l, L.u64, L.b64));
+  CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, P->stream), "residual");
+  CK(csff::launch_norm2<double>(L.r64, L.N, e, P->red, P->red_blocks, P->red_out, P->stream), "norm");
+  CK(cudaMemcpyAsync(P->red_host, P->red_out, sizeof(double), cudaMemcpyDeviceToHost, P->stream), "read norm");
+  return CSFF_OK;
+}
+
 // FP64 V-cycles on the finest level (iterate in the plan's u64, rhs in b64).
 csff_status solve_fp64(csff_plan* P, int eb, double nb, csff_info* info) {
   Tracker tr;
@@ -1005,6 +1021,69 @@ csff_status csff_solve(csff_plan* P, int n_rhs, const double* eta, void* u_dev, 
 
 // Solve A u = b for the right-hand side already in level 0's b64; u (the
 // caller's buffer) holds the guess when use_guess and receives the solution.
+// Full multigrid (Sec. 4, FMG paragraph; Table 3) for the right-hand side in
+// level 0's b64: b_{l+1} = FW(b_l) down to the coarsest level, its direct
+// solve, then on each finer level the interpolated coarser solution as the
+// initial guess of FP64 V-cycles to rel_tol ||b_l||.
+static csff_status fmg_loaded(csff_plan* P, double2* u_out, int* level_cycles, csff_info* in) {
+  const int nl = (int)P->lv.size();
+  cudaStream_t s = P->stream;
+  Level& L0 = P->lv[0];
+  int* ex = reinterpret_cast<int*>(P->red_out + 4);
+  CK(csff::launch_max_exp(L0.b64, L0.N, ex, s), "max exponent");
+  int eb = 0;
+  CK(cudaMemcpyAsync(&eb, ex, sizeof(int), cudaMemcpyDeviceToHost, s), "read exponent");
+  CK(cudaStreamSynchronize(s), "sync");
+  if (in) { std::memset(in, 0, sizeof(*in)); in->n_hist = 1; }
+  if (eb >= 4000) {
+    csff::set_error("right-hand side is not finite");
+    if (in) in->status = CSFF_ERR_NONFINITE;
+    return CSFF_ERR_NONFINITE;
+  }
+  if (eb <= -2000) eb = 0;
+  for (int l = 1; l < nl; ++l)
+    CK(csff::launch_restrict<double>(P->dim, P->lv[l - 1], P->lv[l], P->lv[l - 1].b64, P->lv[l].b64, s), "restrict");
+  CK(csff::launch_coarse_solve<double>(P->coarse_inv, P->coarse_N, P->lv[nl - 1].b64, P->lv[nl - 1].u64, s),
+     "coarse solve");
+  csff_status result = CSFF_OK;
+  for (int l = nl - 2; l >= 0; --l) {
+    Level& L = P->lv[l];
+    CK(csff::launch_zero<double>(L.u64, L.N, s), "zero");
+    CK(csff::launch_prolong_add<double>(P->dim, L, P->lv[l + 1], P->lv[l + 1].u64, L.u64, s), "interpolate");
+    CK(csff::launch_norm2<double>(L.b64, L.N, eb, P->red, P->red_blocks, P->red_out + 1, s), "norm b");
+    CK(csff::launch_residual<double>(P->dim, L, L.u64, L.b64, L.r64, s), "residual");
+    CK(csff::launch_norm2<double>(L.r64, L.N, eb, P->red, P->red_blocks, P->red_out, s), "norm");
+    CS(read_scalars(P, 2));
+    const double nb = P->red_host[1];
+    int cycles = 0;
+    csff_status st = CSFF_OK;
+    if (nb > 0.0) {
+      Tracker tr;
+      tr.start(l == 0 ? in : nullptr);
+      double rel = P->red_host[0] / nb;
+      if (l == 0 && in) in->history[0] = rel;
+      tr.prev = rel;
+      if (rel > P->opts.rel_tol) {
+        const long long key = (5ll << 40) + (long long)l * 8192 + (eb + 4096);
+        for (;;) {
+          CS(run_step(P, key, step_fmg_level, l * 8192 + (eb + 4096)));
+          ++cycles;
+          rel = P->red_host[0] / nb;
+          const int t = tr.push(rel, cycles, 0, P->opts.rel_tol, P->opts.max_cycles);
+          if (t >= 0) { st = (csff_status)t; break; }
+        }
+      } else if (l == 0 && in) {
+        in->rel_res = rel;
+      }
+    }
+    if (level_cycles) level_cycles[nl - 2 - l] = cycles;
+    result = (csff_status)worse(result, st);
+  }
+  CK(cudaMemcpyAsync(u_out, L0.u64, sizeof(double2) * (size_t)L0.N, cudaMemcpyDeviceToDevice, s), "copy");
+  if (in) in->status = result;
+  return result;
+}
+
 static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_info* in) {
   Level& L = P->lv[0];
   if (!use_guess) CK(csff::launch_zero<double>(u, L.N, P->stream), "zero");
@@ -1060,6 +1139,27 @@ static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_in
   if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;
   if (in) in->status = st;
   return st;
+}
+
+csff_status csff_solve_fmg(csff_plan* P, int n_rhs, const double* eta, void* u_dev, int* level_cycles,
+                           csff_info* info) {
+  if (!P || !eta || !u_dev || n_rhs < 0) return invalid("bad solve arguments");
+  if (P->opts.precision != CSFF_PREC_FP64) {
+    csff::set_error("full multigrid runs FP64 V-cycles: the plan's precision must be CSFF_PREC_FP64");
+    return CSFF_ERR_UNSUPPORTED;
+  }
+  Level& L = P->lv[0];
+  const int nl = (int)P->lv.size();
+  int worst = CSFF_OK;
+  for (int r = 0; r < n_rhs; ++r) {
+    CS(csff_rhs(P, 1, eta + (size_t)r * P->dim, L.b64));
+    const csff_status st = fmg_loaded(P, (double2*)u_dev + (size_t)r * L.N,
+                                      level_cycles ? level_cycles + (size_t)r * (nl - 1) : nullptr,
+                                      info ? info + r : nullptr);
+    if (st == CSFF_ERR_CUDA || st == CSFF_ERR_OOM || st == CSFF_ERR_INVALID_ARG) return st;
+    worst = worse(worst, st);
+  }
+  return (csff_status)worst;
 }
 
 csff_status csff_solve_rhs(csff_plan* P, const void* b_dev, void* u_dev, int use_guess, csff_info* info) {

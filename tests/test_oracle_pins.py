@@ -6,6 +6,7 @@ import os
 import numpy as np
 import pytest
 import scipy.fft as sfft
+import scipy.sparse.linalg as spla
 
 import oracle.csff_oracle as O
 import workloads as W
@@ -479,3 +480,79 @@ def test_gmres_vcycle_reproduces_table2(pts):
         assert r.converged
         assert abs(r.cycles - cyc) <= 2, (k, n, r.cycles, cyc)
         assert abs(r.conv_factor - fac) <= 0.07, (k, n, r.conv_factor, fac)
+
+
+# ---------------------------------------------------------------------------
+# Full multigrid (Sec. 4, FMG paragraph; Table 3)
+# ---------------------------------------------------------------------------
+def _fmg_case(dim, n, k=2.0):
+    if dim == 2:
+        c = W.small_2d(n=n)
+        c["problem"]["k"] = k
+        c["opts"].update(smoother="rbgs", nu1=1, nu2=1, coarsest_n=5, rel_tol=1e-9, max_cycles=60)
+    else:
+        c = W.paper_gmres(dim=3, k=1.0, n=n)
+        c["opts"].update(rel_tol=1e-8, max_cycles=60)
+    p = O.problem_from_dict(c["problem"])
+    return p, O.opts_from_dict(c["opts"]), O.rhs(p, c["eta"][0])
+
+
+@pytest.mark.parametrize("dim,n", [(2, 33), (2, 65), (3, 17)])
+def test_fmg_reaches_the_direct_solution(dim, n):
+    """Every level meets the tolerance and the finest iterate agrees with a
+    sparse direct solve to within the tolerance's error bound."""
+    p, o, b = _fmg_case(dim, n)
+    res = O.fmg_solve(p, b, o)
+    assert res.converged and len(res.level_cycles) == len(O.make_hierarchy(p, o.coarsest_n)) - 1
+    assert all(h[-1] <= o.rel_tol for h in res.level_history)
+    ud = O.direct_solve(p, b)
+    A = O.assemble_matrix(O.make_level(p, p.n))
+    # ||u - u*|| <= ||A^-1|| ||r||: bound ||A^-1|| by a few inverse-power steps
+    x = W.rand_complex(A.shape[0], 5)
+    lu = spla.splu(A.tocsc())
+    for _ in range(30):
+        x = lu.solve(x)
+        nrm = np.linalg.norm(x)
+        x /= nrm
+    err = np.linalg.norm(res.u - ud) / np.linalg.norm(ud)
+    assert err <= 2.0 * nrm * o.rel_tol * np.linalg.norm(b) / np.linalg.norm(ud)
+
+
+def test_fmg_without_cycles_is_the_interpolated_coarse_solution():
+    """With no V-cycles the two-level FMG returns P A_c^{-1} FW(b): the coarse
+    problem solved by an independent sparse direct solve, then interpolated."""
+    p, o, b = _fmg_case(2, 9)
+    o.max_cycles = 0
+    res = O.fmg_solve(p, b, o)
+    pc = O.Problem(2, 5, p.lo, p.hi, p.gamma, p.k, p.gaussians)
+    uc = spla.spsolve(O.assemble_matrix(O.make_level(pc, 5)).tocsc(), O.restrict_fw(b).ravel()).reshape(3, 3)
+    ref = O.prolong(uc)
+    assert res.level_cycles == [0]
+    assert np.abs(res.u - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_fmg_on_a_single_level_is_the_direct_solve():
+    p, o, b = _fmg_case(2, 5)
+    res = O.fmg_solve(p, b, o)
+    assert res.level_cycles == []
+    ref = spla.spsolve(O.assemble_matrix(O.make_level(p, 5)).tocsc(), b.ravel()).reshape(b.shape)
+    assert np.abs(res.u - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("pts", [16, 32])
+def test_fmg_finest_level_needs_no_more_cycles_than_vcycles_from_zero(pts):
+    """Table 3's setting (eq. chi3D, 9.9 degrees, V(1,1)/GMRES(3), 1e-6): the
+    nested iteration's finest level needs at most the V-cycles the iteration
+    from zero needs (Table 2's setting).  Table 3 prints 2-4 fewer finest-level
+    cycles than Table 2 on these grids; this reading of the FMG saves at most
+    one (the paper does not give its coarse right-hand sides or the reference
+    of its per-level tolerance), so the printed counts are context, not a pin."""
+    for k in (0.25, 0.5, 1.0, 2.0, 4.0):
+        c = W.paper_gmres(dim=3, k=k, n=pts + 1)
+        p = O.problem_from_dict(c["problem"])
+        o = O.opts_from_dict(c["opts"])
+        b = O.rhs(p, c["eta"][0])
+        f = O.fmg_solve(p, b, o)
+        v = O.mg_solve(p, b, o)
+        assert f.converged and v.converged
+        assert f.cycles <= v.cycles, (k, f.level_cycles, v.cycles)
