@@ -635,7 +635,7 @@ def measure_3d(csff, torch, dev, stream, flush):
            "cycles": [i["cycles"] for i in info["inf"]],
            "all_converged": all(i["rel_res"] <= 1e-8 for i in info["inf"])}
     maps = {}
-    for mode, name in ((csff.FF_FP64, "fp64"), (csff.FF_TC_BF16X3, "tc_bf16x3")):
+    for mode, name in ((csff.FF_FP64, "fp64"), (csff.FF_TC_BF16X4, "tc_bf16x4")):
         plan.set_far_field_mode(mode)
         ff()
         ff_ms = _time_events(torch, stream, ff, flush, 3)
@@ -648,10 +648,10 @@ def measure_3d(csff, torch, dev, stream, flush):
         out[f"ff_{name}_stageA_ms_per_map"] = prof["ms"] / max(1, nr)
         out[f"ff_{name}_stageA_tflops"] = prof["alg_flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] else 0.0
     out["ff_fp64_stageA_fp64_frac"] = out["ff_fp64_stageA_tflops"] / FP64_PEAK_TFLOPS
-    rel = np.linalg.norm(maps["tc_bf16x3"] - maps["fp64"], axis=1) / np.linalg.norm(maps["fp64"], axis=1)
+    rel = np.linalg.norm(maps["tc_bf16x4"] - maps["fp64"], axis=1) / np.linalg.norm(maps["fp64"], axis=1)
     out["tc_vs_fp64_rel_l2"] = {"max": float(rel.max()), "median": float(np.median(rel)),
                                 "maps_below_1e-5": int((rel <= 1e-5).sum())}
-    out["step_ms_with_tc_far_field"] = ms - out["ff_fp64_ms_per_16_maps"] + out["ff_tc_bf16x3_ms_per_16_maps"]
+    out["step_ms_with_tc_far_field"] = ms - out["ff_fp64_ms_per_16_maps"] + out["ff_tc_bf16x4_ms_per_16_maps"]
     plan.set_far_field_mode(csff.FF_FP64)
     plan.close()
     return out

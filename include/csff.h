@@ -214,16 +214,17 @@ csff_status csff_far_field(csff_plan* plan, int n_rhs, const double* eta_host, c
    quadrature's arithmetic open, Sec. 4).
    CSFF_FF_FP64 (default): FP64-class throughout (2D stage 1 in double-float
      arithmetic on the FP32 pipes, FP64 where the operand ranges need it).
-   CSFF_FF_TC_BF16X3: 3D plans evaluate the z-contraction (the largest stage)
-     on the tensor cores: operands rounded to FP32, split into three BF16 terms,
-     six products accumulated in FP32; relative error per term about 2^-22 of
-     its magnitude, so F carries an absolute error of that order times
+   CSFF_FF_TC_BF16X4: 3D plans evaluate the z-contraction (the largest stage)
+     on the tensor cores: each operand split into four BF16 terms (32
+     significant bits), the ten products of terms i, j with i + j <= 3
+     accumulated in FP32 over 32 z-nodes at a time and summed in double-float
+     across them; F then carries an absolute error of about 2^-26 times
      sum_j |term_j| per angle.  The library falls back to FP64 on the device
      when an operand is not finite or its exponent range is too wide.  2D plans
      are unaffected.  A wait inside the tensor-core kernel that runs out makes
      csff_far_field return CSFF_ERR_TIMEOUT.
    Errors: CSFF_ERR_INVALID_ARG for an unknown mode. */
-enum { CSFF_FF_FP64 = 0, CSFF_FF_TC_BF16X3 = 1 };
+enum { CSFF_FF_FP64 = 0, CSFF_FF_TC_BF16X4 = 1 };
 csff_status csff_plan_set_far_field_mode(csff_plan* plan, int mode);
 
 /* The 2D far field's stage-1 contraction skips the 32-node blocks whose

@@ -79,7 +79,7 @@ class ProfStatsC(C.Structure):
 
 
 PROF_FF_CONTRACT, PROF_MG32, PROF_MG64, PROF_FF_OTHER, PROF_TILES32, PROF_TILES32_FINE = 1, 2, 4, 8, 16, 32
-FF_FP64, FF_TC_BF16X3 = 0, 1
+FF_FP64, FF_TC_BF16X4 = 0, 1
 PROF_NAMES = ("ff_contract", "mg32", "mg64", "ff_other", "tiles32", "tiles32_fine")
 
 _vp, _cp, _i, _d = C.c_void_p, C.c_char_p, C.c_int, C.c_double
@@ -437,7 +437,7 @@ class Plan:
         _check(_lib.csff_plan_set_stream(self._h, _stream_handle(stream)), "set_stream")
 
     def set_far_field_mode(self, mode):
-        """FF_FP64 (default) or FF_TC_BF16X3 (3D z-contraction on the tensor cores)."""
+        """FF_FP64 (default) or FF_TC_BF16X4 (3D z-contraction on the tensor cores)."""
         _check(_lib.csff_plan_set_far_field_mode(self._h, int(mode)), "plan_set_far_field_mode")
 
     def set_learned(self, net, levels=1, guard=0.5):

@@ -1238,7 +1238,7 @@ csff_status csff_far_field_work(csff_plan* P, double* executed) {
 }
 
 csff_status csff_plan_set_far_field_mode(csff_plan* P, int mode) {
-  if (!P || (mode != CSFF_FF_FP64 && mode != CSFF_FF_TC_BF16X3)) return invalid("bad far-field mode");
+  if (!P || (mode != CSFF_FF_FP64 && mode != CSFF_FF_TC_BF16X4)) return invalid("bad far-field mode");
   P->ff_mode = mode;
   return CSFF_OK;
 }

@@ -124,7 +124,7 @@ struct GmState {
 
 struct csff_plan {
   csff_problem prob{};
-  int ff_mode = 0;          // CSFF_FF_FP64 or CSFF_FF_TC_BF16X3
+  int ff_mode = 0;          // CSFF_FF_FP64 or CSFF_FF_TC_BF16X4
   std::vector<csff_gauss> gauss;
   csff_opts opts{};
   cudaStream_t stream = nullptr;

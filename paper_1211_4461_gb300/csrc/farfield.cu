@@ -611,11 +611,13 @@ __global__ void __launch_bounds__(DF_NT, 5) k_ff_stage1_df(const float4* __restr
 //   A[col] = (g_re(iz), g_im(iz))_iz,  B[t]    = (P_re, -P_im)_iz  (Re T_t),
 //                                      B[32+t] = (P_im,  P_re)_iz  (Im T_t).
 // Each operand row is scaled by a power of two (per column of g, per z-row of
-// P), rounded to FP32 and split into three BF16 terms v = v0 + v1 + v2 (24
-// significant bits); the six products with i + j <= 2 run as tcgen05.mma
+// P) and split into four BF16 terms v = v0 + v1 + v2 + v3 (32 significant
+// bits, split4); the ten products with i + j <= 3 run as tcgen05.mma
 // (kind::f16, BF16 inputs, FP32 accumulation in tensor memory), the (0,0)
-// product in its own accumulator.  The epilogue adds the two accumulators in
-// FP64 and applies the exponents.  Operands sit in shared memory in the
+// product in its own accumulator.  The accumulators are drained after every
+// K chunk (32 z-nodes) into double-float sums in registers, so FP32
+// accumulation never spans more than 64 K-values; the epilogue forms the
+// sums in FP64 and applies the exponents.  Operands sit in shared memory in the
 // 128-byte-swizzled K-major layout (8-row atoms of 1024 B, 16-byte chunk index
 // XOR row mod 8): A is split and stored by the CTA's threads from g, B is
 // pre-split and pre-swizzled in global memory.  Two pipeline stages; the MMAs
@@ -627,7 +629,8 @@ constexpr int KZ = 32;                        // z-nodes per K chunk (64 BF16 = 
 constexpr int NTHR = 256;
 constexpr int A_SPLIT = TM * 128;             // bytes of one split of an A chunk
 constexpr int B_SPLIT = 2 * TT * 128;         // bytes of one split of a B chunk
-constexpr int STAGE = 3 * A_SPLIT + 3 * B_SPLIT;
+constexpr int NSPLIT = 4;                     // BF16 terms per operand value (32 significant bits)
+constexpr int STAGE = NSPLIT * A_SPLIT + NSPLIT * B_SPLIT;
 constexpr int SMEM = 2 * STAGE + 1024 + 64;
 constexpr int SPREAD_LIMIT = 90;              // bits, see tc_selected
 constexpr int NONFINITE = 100000;
@@ -675,6 +678,32 @@ __device__ __forceinline__ float d2f_scaled(double v, int e) {
   const unsigned int rem = (unsigned int)(mant & 0x1FFFFFFFull), halfway = 0x10000000u;
   f += (rem > halfway || (rem == halfway && (f & 1u))) ? 1u : 0u;   // a carry into the exponent is exact
   return __uint_as_float(f | (hi & 0x80000000u));
+}
+
+// v * 2^-e (|v| 2^-e < 1) as four BF16 terms with 32 significant bits: the
+// top 24 bits of the FP64 significand, truncated (an FP32 value, split three
+// ways exactly by split3), and the next bits rounded to one BF16 term.  The
+// representation error is below 2^-32 |v 2^-e|.  Bit fields and FP32
+// arithmetic only; values below FP32's normal range become zero.
+__device__ __forceinline__ void split4(double v, int e, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c,
+                                       __nv_bfloat16& d) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned int hi32 = (unsigned int)(bits >> 32);
+  const int E = (int)((hi32 >> 20) & 0x7FF);
+  const int Ef = E - e - 1023 + 127;
+  float head = 0.f, tail = 0.f;
+  if (E != 0 && Ef > 0) {
+    const unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+    const unsigned int sgn = hi32 & 0x80000000u;
+    head = __uint_as_float(sgn | ((unsigned int)Ef << 23) | (unsigned int)(mant >> 29));
+    // the 29 bits below the head: r 2^(Ef - 127 - 52), formed as
+    // (r 2^-60) 2^(Ef - 119), both factors in FP32's normal range (Ef < 127)
+    const unsigned int r = (unsigned int)(mant & 0x1FFFFFFFull);
+    const float t = __fmul_rn(__fmul_rn((float)r, 0x1p-60f), __uint_as_float((unsigned int)(Ef - 119 + 127) << 23));
+    tail = sgn ? -t : t;
+  }
+  split3(head, a, b, c);
+  d = __float2bfloat16_rn(tail);
 }
 
 // 2^e as a double (e clamped to the normal range -1022..1023)
@@ -761,7 +790,7 @@ __global__ void k_tc_psplit(const double2* __restrict__ zt, int T, int t0, int m
   if (id >= nkc * 2 * tc::TT * 8) return;
   const int q = id & 7, j = (id >> 3) % (2 * tc::TT), c = id / (2 * tc::TT * 8);
   const int t = j % tc::TT, im_row = j / tc::TT;
-  __align__(16) __nv_bfloat16 v[3][8];
+  __align__(16) __nv_bfloat16 v[tc::NSPLIT][8];
   const int er = erow[t];
   for (int e = 0; e < 8; ++e) {
     const int k = q * 8 + e, iz = c * tc::KZ + (k >> 1);
@@ -771,12 +800,23 @@ __global__ void k_tc_psplit(const double2* __restrict__ zt, int T, int t0, int m
       // Re rows (P_re, -P_im), Im rows (P_im, P_re)
       x = im_row ? ((k & 1) ? p.x : p.y) : ((k & 1) ? -p.y : p.x);
     }
-    split3(d2f_scaled(x, er), v[0][e], v[1][e], v[2][e]);
+    split4(x, er, v[0][e], v[1][e], v[2][e], v[3][e]);
   }
-  for (int sidx = 0; sidx < 3; ++sidx) {
-    unsigned char* dst = Bg + ((size_t)c * 3 + sidx) * tc::B_SPLIT + sw128(j, q);
+  for (int sidx = 0; sidx < tc::NSPLIT; ++sidx) {
+    unsigned char* dst = Bg + ((size_t)c * tc::NSPLIT + sidx) * tc::B_SPLIT + sw128(j, q);
     *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(v[sidx]);
   }
+}
+
+// (hi, lo) += x + y as double-float: x + y exactly by TwoSum, then TwoSum with
+// hi; the errors collect in lo (non-contracting intrinsics keep each rounding)
+__device__ __forceinline__ void df_accumulate(float& hi, float& lo, float x, float y) {
+  const float s = __fadd_rn(x, y), bb = __fsub_rn(s, x);
+  const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(y, bb));
+  const float h = __fadd_rn(hi, s), b2 = __fsub_rn(h, hi);
+  const float e2 = __fadd_rn(__fsub_rn(hi, __fsub_rn(h, b2)), __fsub_rn(s, b2));
+  hi = h;
+  lo = __fadd_rn(lo, __fadd_rn(e, e2));
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
@@ -813,7 +853,7 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_addr(tslot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tslot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -823,74 +863,24 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
   // instruction descriptor: FP32 accumulator, BF16 A and B, K-major, N = 64, M = 128
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(2 * tc::TT >> 3) << 17) |
                          ((uint32_t)(tc::TM >> 4) << 24);
+  // this thread's outputs: warp w holds rows 32 (w % 4) + lane (TMEM lanes) and
+  // z-rows [16 (w / 4), +16); per output a double-float running sum of the
+  // chunk sums (re, im)
+  const int lg = warp & 3, th = warp >> 2;
+  float acc_hi[2][16], acc_lo[2][16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc_hi[0][j] = acc_lo[0][j] = acc_hi[1][j] = acc_lo[1][j] = 0.f;
   bool ok = true;
-  for (int c = 0; c < nkc; ++c) {
-    const int st = c & 1;
-    unsigned char* sA = base + st * tc::STAGE;
-    unsigned char* sB = sA + 3 * tc::A_SPLIT;
-    // the MMAs of chunk c - 2 read this stage
-    if (c >= 2) ok &= mbar_wait(smem_addr(&mbar[st]), (uint32_t)(((c - 2) >> 1) & 1));
-    // A: 16 z-nodes of this thread's column, 4 at a time -> one 16-byte chunk per split
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-      const int izl = half * 16 + qq * 4;
-      __align__(16) __nv_bfloat16 v[3][8];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int iz = c * tc::KZ + izl + e;
-        double2 x = make_double2(0.0, 0.0);
-        if (colv && iz < m) x = g[(long long)iz * ncol + col];
-        split3(d2f_scaled(x.x, ecl), v[0][2 * e], v[1][2 * e], v[2][2 * e]);
-        split3(d2f_scaled(x.y, ecl), v[0][2 * e + 1], v[1][2 * e + 1], v[2][2 * e + 1]);
-      }
-      const int off = sw128(rl, half * 4 + qq);
-#pragma unroll
-      for (int sidx = 0; sidx < 3; ++sidx)
-        *reinterpret_cast<uint4*>(sA + sidx * tc::A_SPLIT + off) = *reinterpret_cast<const uint4*>(v[sidx]);
-    }
-    // B: copy the pre-swizzled chunk
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(Bg + (size_t)c * 3 * tc::B_SPLIT);
-      uint4* dst = reinterpret_cast<uint4*>(sB);
-      for (int i = tid; i < 3 * tc::B_SPLIT / 16; i += tc::NTHR) dst[i] = src[i];
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
-#pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        const uint32_t dacc = tmem + (p == 0 ? 0u : (uint32_t)(2 * tc::TT));
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = sw128_desc(smem_addr(sA + pa[p] * tc::A_SPLIT) + 32 * kk);
-          const uint64_t bd = sw128_desc(smem_addr(sB + pb[p] * tc::B_SPLIT) + 32 * kk);
-          const uint32_t acc = (c > 0 || kk > 0 || p > 1) ? 1u : 0u;
-          asm volatile(
-              "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(dacc),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(&mbar[st]))
-                   : "memory");
-    }
-  }
-  // the last commit covers every MMA issued before it
-  const int cl = nkc - 1;
-  ok &= mbar_wait(smem_addr(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1));
-  if (!ok) {
-    atomicOr(flag + 2, tc::ERR_TIMEOUT);
-    mbar_wait(smem_addr(&mbar[cl & 1]), (uint32_t)((cl >> 1) & 1));
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    // warp w reads lanes 32 (w % 4).. (rows) and z-rows [16 (w / 4), +16)
-    const int lg = warp & 3, th = warp >> 2;
-    const uint32_t ta = tmem + ((uint32_t)(32 * lg) << 16);
+  // Chunk c's ten products accumulate in FP32 in TMEM set c & 1 (columns
+  // 128 (c & 1) + [0, 64): the (0,0) product, + [64, 128): the other nine),
+  // starting from zero; while the tensor core works on chunk c, the threads
+  // read chunk c - 1's two accumulators and add them into the double-float
+  // sums.  FP32 accumulation thus spans 64 K-values (32 z-nodes) only.
+  auto drain = [&](int cd) {
+    const int sd = cd & 1;
+    ok &= mbar_wait(smem_addr(&mbar[sd]), (uint32_t)((cd >> 1) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t ta = tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)(128 * sd);
     uint32_t r0[16], i0[16], r1[16], i1[16];
 #define TC_LD16(dst, colo)                                                                                   \
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
@@ -904,6 +894,79 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
     TC_LD16(i1, 3 * tc::TT + 16 * th);
 #undef TC_LD16
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      df_accumulate(acc_hi[0][j], acc_lo[0][j], __uint_as_float(r0[j]), __uint_as_float(r1[j]));
+      df_accumulate(acc_hi[1][j], acc_lo[1][j], __uint_as_float(i0[j]), __uint_as_float(i1[j]));
+    }
+  };
+  for (int c = 0; c < nkc; ++c) {
+    const int st = c & 1;
+    unsigned char* sA = base + st * tc::STAGE;
+    unsigned char* sB = sA + tc::NSPLIT * tc::A_SPLIT;
+    // stage st and TMEM set st were last used by chunk c - 2, whose MMAs the
+    // drain of iteration c - 1 waited for
+    // A: 16 z-nodes of this thread's column, 4 at a time -> one 16-byte chunk per split
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      const int izl = half * 16 + qq * 4;
+      __align__(16) __nv_bfloat16 v[tc::NSPLIT][8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int iz = c * tc::KZ + izl + e;
+        double2 x = make_double2(0.0, 0.0);
+        if (colv && iz < m) x = g[(long long)iz * ncol + col];
+        split4(x.x, ecl, v[0][2 * e], v[1][2 * e], v[2][2 * e], v[3][2 * e]);
+        split4(x.y, ecl, v[0][2 * e + 1], v[1][2 * e + 1], v[2][2 * e + 1], v[3][2 * e + 1]);
+      }
+      const int off = sw128(rl, half * 4 + qq);
+#pragma unroll
+      for (int sidx = 0; sidx < tc::NSPLIT; ++sidx)
+        *reinterpret_cast<uint4*>(sA + sidx * tc::A_SPLIT + off) = *reinterpret_cast<const uint4*>(v[sidx]);
+    }
+    // B: copy the pre-swizzled chunk
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(Bg + (size_t)c * tc::NSPLIT * tc::B_SPLIT);
+      uint4* dst = reinterpret_cast<uint4*>(sB);
+      for (int i = tid; i < tc::NSPLIT * tc::B_SPLIT / 16; i += tc::NTHR) dst[i] = src[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // the ten products of split terms i, j with i + j <= 3 (the rest are
+      // below 2^-33 of each term)
+      const int pa[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3}, pb[10] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+#pragma unroll
+      for (int p = 0; p < 10; ++p) {
+        const uint32_t dacc = tmem + (uint32_t)(128 * st) + (p == 0 ? 0u : (uint32_t)(2 * tc::TT));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = sw128_desc(smem_addr(sA + pa[p] * tc::A_SPLIT) + 32 * kk);
+          const uint64_t bd = sw128_desc(smem_addr(sB + pb[p] * tc::B_SPLIT) + 32 * kk);
+          const uint32_t acc = (kk > 0 || p > 1) ? 1u : 0u;
+          asm volatile(
+              "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(dacc),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_addr(&mbar[st]))
+                   : "memory");
+    }
+    __syncwarp();
+    if (c >= 1) drain(c - 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  // the last chunk; its commit covers every MMA issued before it
+  drain(nkc - 1);
+  if (!ok) {
+    atomicOr(flag + 2, tc::ERR_TIMEOUT);
+    mbar_wait(smem_addr(&mbar[(nkc - 1) & 1]), (uint32_t)(((nkc - 1) >> 1) & 1));
+  }
+  if (ok) {
     const long long ocol = col0 + 32 * lg + lane;
     if (ocol < ncol) {
       const int ec = ecol[ocol];
@@ -912,8 +975,8 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
         const int t = 16 * th + j;
         if (t0 + t >= T) continue;
         const int e = ec + erow[t];
-        const double re = (double)__uint_as_float(r0[j]) + (double)__uint_as_float(r1[j]);
-        const double im = (double)__uint_as_float(i0[j]) + (double)__uint_as_float(i1[j]);
+        const double re = (double)acc_hi[0][j] + (double)acc_lo[0][j];
+        const double im = (double)acc_hi[1][j] + (double)acc_lo[1][j];
         T1[(long long)(t0 + t) * ncol + ocol] =
             (e >= -1022 && e <= 1023) ? make_double2(re * pow2d(e), im * pow2d(e)) : make_double2(ldexp(re, e), ldexp(im, e));
       }
@@ -921,7 +984,7 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
 // ---- 3D sum-factorised contraction --------------------------------------------
@@ -1158,10 +1221,10 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
                                           B.dxt, B.dyt, B.dzt);
       double2* T1 = B.dT;
       double2* T2 = B.dT + (size_t)n_uz * ncol;
-      const bool use_tc = P->ff_mode == CSFF_FF_TC_BF16X3;
+      const bool use_tc = P->ff_mode == CSFF_FF_TC_BF16X4;
       const int nkc = (m + tc::KZ - 1) / tc::KZ;
       if (use_tc) {
-        if ((e = ensure((void**)&B.dtcb, B.tcb, (size_t)nkc * 3 * tc::B_SPLIT, P)) != cudaSuccess ||
+        if ((e = ensure((void**)&B.dtcb, B.tcb, (size_t)nkc * tc::NSPLIT * tc::B_SPLIT, P)) != cudaSuccess ||
             (e = ensure((void**)&B.dtce, B.tce, sizeof(int) * ((size_t)ncol + tc::TT), P)) != cudaSuccess)
           return cuda_fail(e, "far field scratch");
         if (!B.dtcflag && (e = cudaMalloc((void**)&B.dtcflag, 3 * sizeof(int))) != cudaSuccess)

@@ -409,69 +409,63 @@ __global__ void k_update64(double2* __restrict__ u, const float2* __restrict__ e
   }
 }
 
-// v * 2^-s exactly from the bit fields (values that would leave the normal
-// range become zero; Inf and NaN pass unchanged), off the FP64 pipe
-__device__ __forceinline__ double pow2_down(double v, int s) {
-  const long long b = __double_as_longlong(v);
-  const int E = (int)((b >> 52) & 0x7FF);
-  if (E == 0x7FF) return v;
-  const int En = E - s;
-  if (E == 0 || En <= 0) return 0.0;
-  if (En >= 0x7FF) return ldexp(v, -s);
-  return __longlong_as_double((b & ~(0x7FFLL << 52)) | ((long long)En << 52));
-}
-
 // One pass of the FP64 refinement step (option refine_fp64): the residual
 // r = b - A u in FP64 as a chain of fused multiply-adds,
 //   r = b - c (2d u - sum_nbr u) + q u,
 // its rounding r32 = 2^-s r to FP32 (the right-hand side of the next FP32
-// cycles; the bit-field conversion keeps it off the FP64 pipe), and per-block
-// sums of |2^-s r|^2 for the norm.  s is fixed for a solve (the exponent of
-// max |b|), so the FP32 values stay below 1 in magnitude and, with a relative
-// residual of at least 2^-100, far above FP32's normal range.
+// cycles: an exact FP64 scaling and one conversion), and per-block sums of
+// |r32|^2 for the norm (within 2^-24 relative of ||2^-s r||, far inside what
+// the stopping test resolves).  s is fixed for a solve (the exponent of
+// max |b|), so the FP32 values stay below 1 in magnitude.  The kernel is
+// bound by instruction issue as much as by the FP64 pipe, so each CTA walks
+// grid rows (no index division per point) and nothing else is done per point.
 template <int D>
 __global__ void k_refine_residual(const double2* __restrict__ u, const double2* __restrict__ b,
-                                  const double2* __restrict__ q, double2 c, int m, int N, int s,
+                                  const double2* __restrict__ q, double2 c, int m, double scale,
                                   float2* __restrict__ r32, double* __restrict__ partial) {
   pdl_prologue();
   __shared__ double sh[32];
-  double acc = 0;
-  const int mm = m * m;
+  float acc = 0.f;
+  const int nrows = (D == 3) ? m * m : m;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   const double2 z = make_double2(0.0, 0.0);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    const int rest = i / m, ix = i - rest * m;
-    const int iz = (D == 3) ? rest / m : 0;
-    const int iy = (D == 3) ? rest - iz * m : rest;
-    const double2 uj = u[i];
-    const double2 xl = ix > 0 ? u[i - 1] : z, xr = ix < m - 1 ? u[i + 1] : z;
-    const double2 yl = iy > 0 ? u[i - m] : z, yr = iy < m - 1 ? u[i + m] : z;
-    double sx = (xl.x + xr.x) + (yl.x + yr.x), sy = (xl.y + xr.y) + (yl.y + yr.y);
-    if (D == 3) {
-      const double2 zl = iz > 0 ? u[i - mm] : z, zr = iz < m - 1 ? u[i + mm] : z;
-      sx += zl.x + zr.x;
-      sy += zl.y + zr.y;
+  if (ix < m) {
+    for (int row = blockIdx.y; row < nrows; row += gridDim.y) {
+      const int iz = (D == 3) ? row / m : 0;
+      const int iy = (D == 3) ? row - iz * m : row;
+      const long long i = (long long)row * m + ix;
+      const double2 uj = u[i];
+      const double2 xl = ix > 0 ? u[i - 1] : z, xr = ix < m - 1 ? u[i + 1] : z;
+      const double2 yl = iy > 0 ? u[i - m] : z, yr = iy < m - 1 ? u[i + m] : z;
+      double sx = (xl.x + xr.x) + (yl.x + yr.x), sy = (xl.y + xr.y) + (yl.y + yr.y);
+      if (D == 3) {
+        const long long mm = (long long)m * m;
+        const double2 zl = iz > 0 ? u[i - mm] : z, zr = iz < m - 1 ? u[i + mm] : z;
+        sx += zl.x + zr.x;
+        sy += zl.y + zr.y;
+      }
+      const double tx = fma((double)(2 * D), uj.x, -sx), ty = fma((double)(2 * D), uj.y, -sy);
+      const double2 bj = b[i], qj = q[i];
+      const double rx = fma(-c.x, tx, fma(c.y, ty, fma(qj.x, uj.x, fma(-qj.y, uj.y, bj.x))));
+      const double ry = fma(-c.x, ty, fma(-c.y, tx, fma(qj.x, uj.y, fma(qj.y, uj.x, bj.y))));
+      const float fx = __double2float_rn(rx * scale), fy = __double2float_rn(ry * scale);
+      r32[i] = make_float2(fx, fy);
+      acc = __fmaf_rn(fx, fx, __fmaf_rn(fy, fy, acc));
     }
-    const double tx = fma((double)(2 * D), uj.x, -sx), ty = fma((double)(2 * D), uj.y, -sy);
-    const double2 bj = b[i], qj = q[i];
-    const double rx = fma(-c.x, tx, fma(c.y, ty, fma(qj.x, uj.x, fma(-qj.y, uj.y, bj.x))));
-    const double ry = fma(-c.x, ty, fma(-c.y, tx, fma(qj.x, uj.y, fma(qj.y, uj.x, bj.y))));
-    r32[i] = make_float2(d2f_pow2(rx, s), d2f_pow2(ry, s));
-    const double ax = pow2_down(rx, s), ay = pow2_down(ry, s);
-    acc = fma(ax, ax, fma(ay, ay, acc));
   }
-  acc = block_reduce(acc, AddOp(), sh, 0.0);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  const double tot = block_reduce((double)acc, AddOp(), sh, 0.0);
+  if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
-// u += 2^s e (FP32 correction, exact widening on the bit fields; one FP64 add
-// per component)
-__global__ void k_update64_fixed(double2* __restrict__ u, const float2* __restrict__ e, int N, int s) {
+// u += 2^s e (FP32 correction widened exactly; one FP64 multiply and add per
+// component, p2 = 2^s)
+__global__ void k_update64_fixed(double2* __restrict__ u, const float2* __restrict__ e, int N, double p2) {
   pdl_prologue();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const float2 c = e[i];
     double2 v = u[i];
-    v.x += f2d_pow2(c.x, s);
-    v.y += f2d_pow2(c.y, s);
+    v.x = fma((double)c.x, p2, v.x);
+    v.y = fma((double)c.y, p2, v.y);
     u[i] = v;
   }
 }
@@ -644,18 +638,21 @@ cudaError_t launch_to32_scaled(const double2* r, long long N, const double* norm
 cudaError_t launch_refine_residual(int dim, const Level& L, const double2* u, const double2* b, int s_exp,
                                    float2* r32, double* partial, int nblk, double* out, cudaStream_t s) {
   if (L.N >= (1ll << 31)) return cudaErrorInvalidValue;
-  const int N = (int)L.N;
-  const int need = (N + RED_THREADS - 1) / RED_THREADS;
-  const int nb = need < nblk ? (need < 1 ? 1 : need) : nblk;
+  const int gx = (L.m + RED_THREADS - 1) / RED_THREADS;
+  const int nrows = dim == 3 ? L.m * L.m : L.m;
+  int gy = nblk / gx;
+  gy = gy < 1 ? 1 : (gy > nrows ? nrows : gy);
+  if (gx * gy > nblk) return cudaErrorInvalidValue;
   ProfScope ps(PF_MG64, s, (16.0 * 3 + 8.0) * L.N, 0);
+  const double scale = ldexp(1.0, -s_exp);
   cudaError_t e = (dim == 2)
-      ? launch_pdl(k_refine_residual<2>, dim3(nb), dim3(RED_THREADS), 0, s, u, b, (const double2*)L.q64, L.c, L.m, N,
-                   s_exp, r32, partial)
-      : launch_pdl(k_refine_residual<3>, dim3(nb), dim3(RED_THREADS), 0, s, u, b, (const double2*)L.q64, L.c, L.m, N,
-                   s_exp, r32, partial);
+      ? launch_pdl(k_refine_residual<2>, dim3(gx, gy), dim3(RED_THREADS), 0, s, u, b, (const double2*)L.q64, L.c,
+                   L.m, scale, r32, partial)
+      : launch_pdl(k_refine_residual<3>, dim3(gx, gy), dim3(RED_THREADS), 0, s, u, b, (const double2*)L.q64, L.c,
+                   L.m, scale, r32, partial);
   if (e == cudaSuccess)
-    e = launch_pdl(k_norm_finish, dim3(1), dim3(RED_THREADS), 0, s, (const double*)partial, nb, ldexp(1.0, s_exp),
-                   out);
+    e = launch_pdl(k_norm_finish, dim3(1), dim3(RED_THREADS), 0, s, (const double*)partial, gx * gy,
+                   ldexp(1.0, s_exp), out);
   count_launch(2);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -663,7 +660,8 @@ cudaError_t launch_refine_residual(int dim, const Level& L, const double2* u, co
 cudaError_t launch_update64_fixed(double2* u, const float2* e, long long N, int s_exp, cudaStream_t s) {
   if (N >= (1ll << 31)) return cudaErrorInvalidValue;
   ProfScope ps(PF_MG64, s, 40.0 * N, 0);
-  cudaError_t err = launch_pdl(k_update64_fixed, dim3(flat_blocks(N)), dim3(256), 0, s, u, e, (int)N, s_exp);
+  cudaError_t err = launch_pdl(k_update64_fixed, dim3(flat_blocks(N)), dim3(256), 0, s, u, e, (int)N,
+                               ldexp(1.0, s_exp));
   count_launch();
   return err != cudaSuccess ? err : cudaGetLastError();
 }

@@ -37,7 +37,7 @@ def _constants(csff):
          "CSFF_SMOOTHER_GMRES": csff.SMOOTHER["gmres"],
          "CSFF_PREC_FP64": csff.PRECISION["fp64"], "CSFF_PREC_MIXED": csff.PRECISION["mixed"],
          "CSFF_MAX_HISTORY": csff.MAX_HISTORY,
-         "CSFF_FF_FP64": csff.FF_FP64, "CSFF_FF_TC_BF16X3": csff.FF_TC_BF16X3,
+         "CSFF_FF_FP64": csff.FF_FP64, "CSFF_FF_TC_BF16X4": csff.FF_TC_BF16X4,
          "CSFF_PROF_FF_CONTRACT": csff.PROF_FF_CONTRACT, "CSFF_PROF_MG32": csff.PROF_MG32,
          "CSFF_PROF_MG64": csff.PROF_MG64, "CSFF_PROF_FF_OTHER": csff.PROF_FF_OTHER,
          "CSFF_PROF_TILES32": csff.PROF_TILES32, "CSFF_PROF_TILES32_FINE": csff.PROF_TILES32_FINE,

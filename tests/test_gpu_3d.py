@@ -95,23 +95,23 @@ def _maps(csff, plan, c, u, mode):
 
 
 def test_3d_tensor_core_far_field_against_oracle(csff):
-    """Tensor-core z-contraction (three-way BF16 split, FP32 accumulation):
-    per angle within 2^-20 sum|terms| of the oracle on the same solution (each
-    rounding is 2^-24 relative: FP32 operands, the split, and FP32 accumulation
-    growing like sqrt(K/16)), and within the 1e-5 relative L2 target over the
-    64 x 32 map."""
+    """Tensor-core z-contraction (four-way BF16 split of each operand, ten
+    products, FP32 accumulation over 32 z-nodes, double-float sums across
+    them): per angle within 2^-24 sum|terms| of the oracle on the same
+    solution (2^-25.5 measured), and within the 1e-5 relative L2 target over
+    the 64 x 32 map."""
     c = W.big_3d(n=65, n_rhs=2)
     c["opts"]["precision"] = "mixed"
     plan = csff.Plan(c["problem"], c["opts"])
     p = O.problem_from_dict(c["problem"])
     u = torch.zeros(2 * plan.N, dtype=torch.complex128, device="cuda")
     plan.solve(c["eta"], u)
-    Ft = _maps(csff, plan, c, u, csff.FF_TC_BF16X3)
+    Ft = _maps(csff, plan, c, u, csff.FF_TC_BF16X4)
     for r in range(2):
         ug = u[r * plan.N:(r + 1) * plan.N].cpu().numpy().reshape((p.m,) * 3)
         m, e2, tn = O.far_field(p, ug, c["eta"][r], c["alphas"], return_terms_norm=True)
         Fo = O.far_field_value(m, e2)
-        assert np.all(np.abs(Ft[r] - Fo) <= 2.0 ** -20 * tn * 2.0 ** e2)
+        assert np.all(np.abs(Ft[r] - Fo) <= 2.0 ** -24 * tn * 2.0 ** e2)
         assert np.linalg.norm(Ft[r] - Fo) <= 1e-5 * np.linalg.norm(Fo)
     plan.close()
 
@@ -126,24 +126,24 @@ def test_3d_tensor_core_falls_back_when_the_range_is_too_wide(csff):
     plan = csff.Plan(c["problem"], c["opts"])
     u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")      # g = chi u_in
     F64 = _maps(csff, plan, c, u, csff.FF_FP64)
-    Ft = _maps(csff, plan, c, u, csff.FF_TC_BF16X3)
+    Ft = _maps(csff, plan, c, u, csff.FF_TC_BF16X4)
     assert np.array_equal(F64, Ft)
     plan.close()
 
 
 def test_3d_full_size_tensor_core_maps(csff):
     """257^3, 16 directions: the tensor-core maps against the FP64 maps of the
-    same solutions.  Relative L2 per map is about 2^-24 times the map's
-    condition number: 2.2e-6 to 2.5e-6 for half the directions, about 2.2e-5
-    for the directions with the largest terms (the FP32 accumulation floor);
-    asserted below 5e-5, and below 1e-5 for at least 8 of the 16 maps."""
+    same solutions.  Relative L2 per map is about 2^-26 times the map's
+    condition number (four-term splits, FP32 accumulation over 32 z-nodes,
+    double-float across chunks): 1.1e-6 to 5.7e-6 measured; every map within
+    the 1e-5 target."""
     c = W.big_3d(n=257, n_rhs=16)
     c["opts"]["precision"] = "mixed"
     plan = csff.Plan(c["problem"], c["opts"])
     u = torch.zeros(16 * plan.N, dtype=torch.complex128, device="cuda")
     plan.solve(c["eta"], u)
     F64 = _maps(csff, plan, c, u, csff.FF_FP64)
-    Ft = _maps(csff, plan, c, u, csff.FF_TC_BF16X3)
+    Ft = _maps(csff, plan, c, u, csff.FF_TC_BF16X4)
     rel = np.linalg.norm(Ft - F64, axis=1) / np.linalg.norm(F64, axis=1)
-    assert rel.max() <= 5e-5 and (rel <= 1e-5).sum() >= 8
+    assert rel.max() <= 1e-5
     plan.close()
