@@ -583,22 +583,35 @@ def measure_variants(csff, torch, dev, stream, flush, headline_ms):
                          "all_converged": all(x["rel_res"] <= 1e-8 for x in binfo["inf"]),
                          "cycles_total": int(sum(x["cycles"] for x in binfo["inf"]))}
     b.close()
-    # the same instances, one plan at a time (single-problem mixed path)
-    sp = [csff.Plan(c["problem"], c["opts"], stream=stream) for c in bc]
-    su = [torch.zeros(p.N, dtype=torch.complex128, device=dev) for p in sp]
+    # the same instances, one plan at a time: the single-problem mixed path
+    # with the batch's iteration (FP64 refinement, fixed schedule), then the
+    # plain FP64 V-cycles (the plain GPU form) to the same tolerance
+    def one_at_a_time(opts_update):
+        sp = [csff.Plan(c["problem"], dict(c["opts"], **opts_update), stream=stream) for c in bc]
+        su = [torch.zeros(p.N, dtype=torch.complex128, device=dev) for p in sp]
+        cyc = {}
 
-    def seq_step():
-        for i, (p, c) in enumerate(zip(sp, bc)):
-            p.solve(c["eta"], su[i])
-            p.far_field(c["eta"], su[i], c["alphas"], Fb[i], Eb[i])
+        def seq_step():
+            for i, (p, c) in enumerate(zip(sp, bc)):
+                _, inf = p.solve(c["eta"], su[i])
+                cyc[i] = inf[0]["cycles"]
+                p.far_field(c["eta"], su[i], c["alphas"], Fb[i], Eb[i])
 
-    seq_step()
-    ms_s = _time_events(torch, stream, seq_step, flush, 2)
-    out["sequential_64"] = {"value": len(bc) / (ms_s / 1e3), "unit": UNIT, "ms_per_step": ms_s}
+        seq_step()
+        ms = _time_events(torch, stream, seq_step, flush, 2)
+        for p in sp:
+            p.close()
+        return ms, int(sum(cyc.values()))
+
+    ms_s, cyc_s = one_at_a_time({"refine_fp64": 1, "adaptive_inner": 0})
+    out["sequential_64"] = {"value": len(bc) / (ms_s / 1e3), "unit": UNIT, "ms_per_step": ms_s,
+                            "cycles_total": cyc_s}
     out["batched_speedup_vs_sequential"] = ms_s / ms_b
-    for p in sp:
-        p.close()
-    del su
+    ms_p, cyc_p = one_at_a_time({"precision": "fp64"})
+    out["plain_fp64_64"] = {"value": len(bc) / (ms_p / 1e3), "unit": UNIT, "ms_per_step": ms_p,
+                            "cycles_total": cyc_p,
+                            "note": "the same 64 instances by plain FP64 V-cycles to 1e-8, one after another"}
+    out["batched_mixed_speedup_vs_plain_fp64"] = ms_p / ms_b
     out["3d_257_16dirs"] = measure_3d(csff, torch, dev, stream, flush)
     out["vcycle_4097"] = measure_vcycle_bandwidth(csff, torch, dev, stream, flush)
     out["learned_2049"] = measure_learned(csff, torch, dev, stream, flush)

@@ -2,7 +2,8 @@
 //
 // Every instance runs the FP32-inner / FP64-refinement iteration of the
 // single-problem path (FP64 residual, power-of-two scaled FP32 V(1,1) RB-GS
-// cycles on the correction equation, FP64 update), but all instances advance
+// cycles on the correction equation with the coarsest solve in FP64, FP64
+// update), but all instances advance
 // together inside ONE cooperative kernel: the iteration is a fixed sequence of
 // phases (rhs, norms, scale to FP32, per-level down tiles, coarse block,
 // per-level up tiles, update + residual, convergence), separated by grid
@@ -40,7 +41,7 @@ struct BInst {
   long long N;
   BLevel L[MAXL];
   tiles::CoarseLevels cl;
-  const float2* inv;
+  const double2* inv64;             // coarsest inverse, applied in FP64 to the FP32 right-hand side
   double2 c64;
   const double2* q64;
   double2* u64[2];                  // current iterate alternates between these
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
       for (int i = blockIdx.x; i < n; i += gridDim.x) {
         if (inst_done(A.st, i)) continue;
         const BInst& I = A.inst[i];
-        tiles::coarse_levels_block<float, 2, true>(I.cl, I.L[I.lc].b, I.L[I.lc].u, I.inv, smem);
+        tiles::coarse_levels_block<float, 2, true, double>(I.cl, I.L[I.lc].b, I.L[I.lc].u, I.inv64, smem);
       }
       if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
       for (int l = A.LC - 1; l >= 0; --l) {
@@ -475,7 +476,7 @@ csff_status upload_descriptors(csff_batch* B) {
       I.cl.c[l] = L.c;
       I.cl.c32[l] = make_float2((float)L.c.x, (float)L.c.y);
     }
-    I.inv = P->coarse_inv32;
+    I.inv64 = P->coarse_inv;
     I.c64 = P->lv[0].c;
     I.q64 = P->lv[0].q64;
     I.u64[0] = P->lv[0].u64;

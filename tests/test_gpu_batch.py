@@ -21,7 +21,7 @@ def csff():
 def _cases(n=8, sizes=(65, 129, 257)):
     cs = W.batch_2d(n, seed=4461, sizes=sizes)
     for c in cs:
-        c["opts"].update(precision="mixed", inner_cycles=3)
+        c["opts"].update(precision="mixed", inner_cycles=3, refine_fp64=1)
     return cs
 
 

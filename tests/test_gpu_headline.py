@@ -111,7 +111,7 @@ def test_batch_with_1025_instances_on_16_point_tiles(csff):
     cs = W.batch_2d(5, seed=77, sizes=(257, 513, 1025))
     assert any(c["problem"]["n"] == 1025 for c in cs)
     for c in cs:
-        c["opts"].update(precision="mixed", inner_cycles=3)
+        c["opts"].update(precision="mixed", inner_cycles=3, refine_fp64=1)
     b = csff.Batch([c["problem"] for c in cs], cs[0]["opts"])
     b.set_tiles(16)
     eta = np.vstack([c["eta"] for c in cs])
