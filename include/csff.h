@@ -378,6 +378,13 @@ csff_status csff_net_train_step(csff_net* net, int B, int H, int W, const void* 
    rest of that solve (csff_info.flags bit 1).  The plan keeps a pointer to
    the net; the net must outlive the attachment. */
 csff_status csff_plan_set_learned(csff_plan* plan, csff_net* net, int levels, double guard);
+/* Use net (NULL: the plan's network again) for the learned step on one level
+   0 <= level < levels of the last csff_plan_set_learned.  In units of h^2 a
+   level's operator depends on k h, which doubles from one level to the next,
+   so a coarser level is served by a network trained at its own k h.
+   csff_plan_set_learned clears these replacements.  Errors:
+   CSFF_ERR_INVALID_ARG (no learned step on that level), CSFF_ERR_OOM. */
+csff_status csff_plan_set_learned_level(csff_plan* plan, int level, csff_net* net);
 /* FP32 copy of a level's q = k^2(1 + chi) (c64, m_l^d, device) and its
    constant c = e^{-2i gamma}/h_l^2 (2 doubles, host): the operator the learned
    step is trained against. */

@@ -126,6 +126,7 @@ _SIGS = {
     "csff_net_loss_grad": (_i, [_vp, _i, _i, _i, _vp, _vp, _dp, _i, _fp, _fp, _vp]),
     "csff_net_train_step": (_i, [_vp, _i, _i, _i, _vp, _vp, _dp, _i, C.c_float, _fp, _vp]),
     "csff_plan_set_learned": (_i, [_vp, _vp, _i, _d]),
+    "csff_plan_set_learned_level": (_i, [_vp, _i, _vp]),
     "csff_plan_copy_coefficients": (_i, [_vp, _i, _vp, _dp]),
     "csff_prof_begin": (_i, [C.c_uint]),
     "csff_prof_end": (_i, [C.POINTER(ProfStatsC)]),
@@ -445,6 +446,13 @@ class Plan:
         _check(_lib.csff_plan_set_learned(self._h, net._h if net is not None else None, int(levels), float(guard)),
                "plan_set_learned")
         self._net = net
+
+    def set_learned_level(self, level, net):
+        """Use net (None: the plan's network) for the learned step on one level."""
+        _check(_lib.csff_plan_set_learned_level(self._h, int(level), net._h if net is not None else None),
+               "plan_set_learned_level")
+        self._level_nets = getattr(self, "_level_nets", {})
+        self._level_nets[int(level)] = net
 
     def coefficients(self, level):
         """(q, c): FP32 q = k^2(1+chi) of a level (complex64 CUDA tensor) and c."""

@@ -286,7 +286,7 @@ csff_status smooth(csff_plan* P, int l, cx<T>* u, const cx<T>* b, int sweeps) {
     for (int i = 0; i < sweeps; ++i) {
       CK(csff::launch_rbgs<T>(P->dim, L, u, b, s), "rbgs");
       if constexpr (sizeof(T) == 4) {
-        if (P->net && !P->learned_off && l < P->learned_levels) CS(csff::learned_step(P, P->dim, L, u, b, s));
+        if (P->net && !P->learned_off && l < P->learned_levels) CS(csff::learned_step(P, l, P->dim, L, u, b, s));
       }
     }
     return CSFF_OK;
@@ -952,6 +952,16 @@ csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, doubl
   P->net = net;
   P->learned_levels = net ? levels : 0;
   P->learned_guard = guard;
+  for (auto& n : P->level_net) n = nullptr;
+  destroy_graphs(P);
+  return CSFF_OK;
+}
+
+csff_status csff_plan_set_learned_level(csff_plan* P, int level, csff_net* net) {
+  if (!P) return invalid("plan is NULL");
+  if (!P->net || level < 0 || level >= P->learned_levels) return invalid("level carries no learned step");
+  if (net) CS(csff::net_reserve(net, P->lv[level].N));
+  P->level_net[level] = net;
   destroy_graphs(P);
   return CSFF_OK;
 }
@@ -1130,7 +1140,9 @@ static csff_status solve_loaded(csff_plan* P, double2* u, int use_guess, csff_in
     // the mixed solve reads the guess from u and writes the solution there itself
     st = fp64 ? solve_fp64(P, eb, nb, in) : solve_mixed(P, eb, nb, in, use_guess ? u : nullptr, u);
     if (P->net && !fp64) {
-      const csff_status nst = csff::net_check(P->net);
+      csff_status nst = csff::net_check(P->net);
+      for (int l = 0; l < P->learned_levels && l < 16; ++l)
+        if (nst == CSFF_OK && P->level_net[l]) nst = csff::net_check(P->level_net[l]);
       if (nst != CSFF_OK) st = nst;
     }
     if (fp64 && st != CSFF_ERR_CUDA && st != CSFF_ERR_OOM && st != CSFF_ERR_INVALID_ARG)

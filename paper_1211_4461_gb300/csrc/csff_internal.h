@@ -164,6 +164,7 @@ struct csff_plan {
   // learned smoother (csff_plan_set_learned): RB-GS sweep followed by
   // u += N(r) on levels < learned_levels of the FP32 cycles
   csff_net* net = nullptr;
+  csff_net* level_net[16] = {};   // per-level replacements of net (csff_plan_set_learned_level)
   int learned_levels = 0;
   double learned_guard = 0.5;
   bool learned_off = false;       // per-solve fallback to plain RB-GS
@@ -303,7 +304,7 @@ extern thread_local bool g_capturing;
 unsigned prof_mask();
 
 // ---- learned smoother (learned.cu) ------------------------------------------
-csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s);
+csff_status learned_step(csff_plan* P, int level, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s);
 csff_status net_reserve(csff_net* N, long long npix);
 csff_status net_check(csff_net* N);
 

@@ -713,8 +713,8 @@ csff_status net_check(csff_net* N) {
   return CSFF_OK;
 }
 
-csff_status learned_step(csff_plan* P, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s) {
-  csff_net* N = P->net;
+csff_status learned_step(csff_plan* P, int level, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s) {
+  csff_net* N = (level >= 0 && level < 16 && P->level_net[level]) ? P->level_net[level] : P->net;
   Geom g{1, L.m, L.m};
   csff_status st = ensure_scratch(N, g.npix(), 1, false);
   if (st != CSFF_OK) return st;
