@@ -55,11 +55,17 @@ __device__ __forceinline__ long long nbr(const Geom& g, long long p, int a, int 
   return nbr_at(g, pix_of(g, p), p, a, b);
 }
 
-// layer 1: x0 = bf16(r) (2 channels) -> h1 = bf16(relu(conv)) (16 channels)
+// layer 1: x0 = bf16(r) (2 channels) -> h1 = bf16(relu(conv)) (16 channels).
+// The weights sit in shared memory as [tap][in][out] so that the 16 output
+// weights of one (tap, input channel) are four 16-byte broadcast loads for 16
+// fused multiply-adds.
 __global__ void k_conv1(Geom g, const float2* __restrict__ r, const __nv_bfloat16* __restrict__ w1,
                         __nv_bfloat16* __restrict__ h1) {
-  __shared__ float ws[NP1];
-  for (int i = threadIdx.x; i < NP1; i += blockDim.x) ws[i] = __bfloat162float(w1[i]);
+  __shared__ __align__(16) float ws[9][2][16];
+  for (int i = threadIdx.x; i < NP1; i += blockDim.x) {
+    const int o = i / 18, c = (i / 9) % 2, t = i % 9;      // w1 index (o * 2 + c) * 9 + t
+    ws[t][c][o] = __bfloat162float(w1[i]);
+  }
   __syncthreads();
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= g.npix()) return;
@@ -73,11 +79,20 @@ __global__ void k_conv1(Geom g, const float2* __restrict__ r, const __nv_bfloat1
     for (int b = 0; b < 3; ++b) {
       long long q = nbr_at(g, pc, p, a, b);
       if (q < 0) continue;
-      float2 v = r[q];
-      float x0 = bf(v.x), x1 = bf(v.y);
+      const float2 v = r[q];
+      const float x[2] = {bf(v.x), bf(v.y)};
 #pragma unroll
-      for (int o = 0; o < 16; ++o)
-        acc[o] = fmaf(ws[(o * 2 + 0) * 9 + a * 3 + b], x0, fmaf(ws[(o * 2 + 1) * 9 + a * 3 + b], x1, acc[o]));
+      for (int c = 1; c >= 0; --c) {          // channel 1 first: the order of the per-output chains
+        const float4* wv = reinterpret_cast<const float4*>(&ws[a * 3 + b][c][0]);
+#pragma unroll
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const float4 w = wv[q4];
+          acc[4 * q4 + 0] = fmaf(w.x, x[c], acc[4 * q4 + 0]);
+          acc[4 * q4 + 1] = fmaf(w.y, x[c], acc[4 * q4 + 1]);
+          acc[4 * q4 + 2] = fmaf(w.z, x[c], acc[4 * q4 + 2]);
+          acc[4 * q4 + 3] = fmaf(w.w, x[c], acc[4 * q4 + 3]);
+        }
+      }
     }
   __align__(16) __nv_bfloat16 hv[16];
 #pragma unroll
