@@ -146,9 +146,68 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
                                             cx<T>* X) {
   constexpr int HS = RB<W>::HS, PL = RB<W>::PLANE, WI = W - 2;
   const bool inner = ox >= 0 && oy >= 0 && ox + W <= m && oy + W <= m;
-  // per-level kernels: every copy of this thread in flight at once (one round
-  // trip per tile); the persistent kernel reads data written by other CTAs of
-  // the same launch through L2
+  if constexpr (!COH) {
+    // Per-level kernels: each thread owns one window column of each array and
+    // walks the window rows an even stride apart, so a row's colour plane and
+    // slot stay fixed and the shared and global addresses advance by
+    // constants; every copy of the thread is in flight at once (one round trip
+    // per tile).  Points outside the interior read as zero.
+    const int t = threadIdx.x;
+    {
+      // black plane: wx = 2 jj + (~wy & 1)
+      constexpr int RS = (NT / HS) & ~1;
+      const int r0 = t / HS, jj = t - r0 * HS;
+      const int wx = 2 * jj + ((r0 & 1) ^ 1);
+      if (r0 < RS && wx < W) {
+        const int fx = ox + wx;
+        const bool xin = !zero_u && fx >= 0 && fx < m;
+        cx<T>* dst = U + PL + r0 * HS + jj;
+        const cx<T>* src = u_in + (long long)(oy + r0) * m + fx;
+        const long long step = (long long)RS * m;
+#pragma unroll
+        for (int k = 0; k < (W + RS - 1) / RS; ++k) {
+          const int wy = r0 + k * RS;
+          if (wy < W) {
+            const int fy = oy + wy;
+            const bool in = xin && (inner || (fy >= 0 && fy < m));
+            cp_async_zfill<sizeof(cx<T>)>(dst, in ? src : u_in, in);
+          }
+          dst += RS * HS;
+          src += step;
+        }
+      }
+    }
+    if (!inner)
+      for (int i = t; i < W * HS; i += NT) {                 // red plane: zero outside the domain
+        const int wy = i / HS, j = i - wy * HS;
+        const int fx = ox + 2 * j + (wy & 1), fy = oy + wy;
+        if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[i] = zero_c<T>();
+      }
+    {
+      // right-hand side (FP64: and 1/d) on window [1, W-2]^2
+      constexpr int RS = (NT / WI) & ~1;
+      const int r1 = t / WI, c1 = t - r1 * WI;
+      if (r1 < RS) {
+        const int wx = 1 + c1, wy0 = 1 + r1;
+        const int fx = ox + wx;
+        const bool xin = fx >= 0 && fx < m;
+        int d = rbi<W>(wx, wy0);
+        const long long g0 = (long long)(oy + wy0) * m + fx, step = (long long)RS * m;
+#pragma unroll
+        for (int k = 0; k < (WI + RS - 1) / RS; ++k) {
+          const int wy = wy0 + k * RS;
+          if (wy <= WI) {
+            const int fy = oy + wy;
+            const bool in = xin && (inner || (fy >= 0 && fy < m));
+            const long long g = in ? g0 + k * step : 0;
+            cp_async_zfill<sizeof(cx<T>)>(B + d, b + g, in);
+            if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + d, K.dinv + g, in);
+          }
+          d += RS * HS;
+        }
+      }
+    }
+  } else
   for (int i = threadIdx.x; i < W * HS; i += NT) {         // black plane: wx = 2 j + (~wy & 1)
     const int wy = i / HS, j = i - wy * HS;
     const int wx = 2 * j + ((wy & 1) ^ 1);
@@ -159,6 +218,7 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
     if constexpr (COH) U[PL + i] = in ? ld<COH>(u_in + g) : zero_c<T>();
     else cp_async_zfill<sizeof(cx<T>)>(U + PL + i, u_in + g, in);
   }
+  if constexpr (COH) {
   if (!inner)
     for (int i = threadIdx.x; i < W * HS; i += NT) {       // red plane: wx = 2 j + (wy & 1)
       const int wy = i / HS, j = i - wy * HS;
@@ -179,6 +239,7 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
       cp_async_zfill<sizeof(cx<T>)>(B + d, b + g, in);
       if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + d, K.dinv + g, in);
     }
+  }
   }
   if constexpr (formed_coef<T>()) {
     constexpr int FW = RB<W>::FACTOR;
@@ -316,11 +377,22 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
     constexpr int PL = RB<DW>::PLANE;
     const int ex = (P0x + TC >= mc) ? m : 2 * P0x + FT;
     const int ey = (P0y + TC >= mc) ? m : 2 * P0y + FT;
-    for (int i = threadIdx.x; i < (FT + 1) * HS; i += NT) {
-      const int ly = i / HS, j = i - ly * HS;
-      const int wy = ly + 3, wx = 2 * j + ((wy & 1) ^ 1);
-      const int fx = ox + wx, fy = oy + wy;
-      if (wx >= 3 && fx < ex && fy < ey && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[PL + wy * HS + j];
+    // each thread one slot column, rows an even stride apart (fixed colour,
+    // constant address steps)
+    constexpr int RS = (NT / HS) & ~1;
+    const int r0 = threadIdx.x / HS, j = threadIdx.x - r0 * HS;
+    const int wx = 2 * j + (((r0 + 3) & 1) ^ 1);
+    const int fx = ox + wx;
+    if (r0 < RS && wx >= 3 && fx < ex && fx < m) {
+      const C* src = U + PL + (r0 + 3) * HS + j;
+      cx<T>* dst = u_out + (long long)(oy + r0 + 3) * m + fx;
+#pragma unroll
+      for (int k = 0; k < (FT + 1 + RS - 1) / RS; ++k) {
+        const int ly = r0 + k * RS, fy = oy + ly + 3;
+        if (ly <= FT && fy < ey && fy < m) *dst = *src;
+        src += RS * HS;
+        dst += (long long)RS * m;
+      }
     }
   }
   // residual at the red points of [2P0, 2P0+FT]^2 (window [3, 3+FT]).  At the
@@ -406,10 +478,23 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
   __syncthreads();
   const int exx = (P0x + TC >= mc) ? m : 2 * P0x + FT;
   const int eyy = (P0y + TC >= mc) ? m : 2 * P0y + FT;
-  for (int i = threadIdx.x; i < (FT + 1) * (FT + 1); i += NT) {
-    int ly = i / (FT + 1), lx = i - ly * (FT + 1);
-    int fx = 2 * P0x + lx, fy = 2 * P0y + ly;
-    if (fx < exx && fy < eyy && fx < m && fy < m) u_out[(long long)fy * m + fx] = U[rbi<UW>(lx + 2, ly + 2)];
+  {
+    // each thread one column, rows an even stride apart (fixed colour,
+    // constant address steps)
+    constexpr int RS = (NT / (FT + 1)) & ~1;
+    const int r0 = threadIdx.x / (FT + 1), lx = threadIdx.x - r0 * (FT + 1);
+    const int fx = 2 * P0x + lx;
+    if (r0 < RS && fx < exx && fx < m) {
+      const C* src = U + rbi<UW>(lx + 2, r0 + 2);
+      cx<T>* dst = u_out + (long long)(2 * P0y + r0) * m + fx;
+#pragma unroll
+      for (int k = 0; k < (FT + 1 + RS - 1) / RS; ++k) {
+        const int ly = r0 + k * RS, fy = 2 * P0y + ly;
+        if (ly <= FT && fy < eyy && fy < m) *dst = *src;
+        src += RS * RB<UW>::HS;
+        dst += (long long)RS * m;
+      }
+    }
   }
   __syncthreads();
 }
