@@ -723,64 +723,104 @@ def measure_vcycle_bandwidth(csff, torch, dev, stream, flush):
     return out
 
 
-def measure_learned(csff, torch, dev, stream, flush):
-    """2049^2 on [-20,20]^2, k = 60 (k h = 1.17 on the finest level): plain
-    red-black V(1,1) cycles against red-black + learned step u += N(h^2 r) on
-    the finest level.  The network is trained on the GPU on residual patches
-    from 257^2 problems with the same k h (k = 7.5), chi drawn from the batch
-    ranges; in units of h^2 the operator is the same on both grids."""
-    from paper_1211_4461_gb300 import learned as LR
+def _learned_problems(n_solves, k, n=257):
+    """Training problems for the learned smoother: seeds 0 .. n_solves-1, chi
+    and the incident angle drawn from the batch ranges, k fixed (so that k h
+    matches the level the network serves)."""
     import math as _m
-    opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
-            "max_cycles": 400, "inner_cycles": 3}
-    probs = []
-    rng = np.random.Generator(np.random.PCG64(5))
-    for i in range(32):
-        n = 257
+    out = []
+    for seed in range(n_solves):
+        rng = np.random.Generator(np.random.PCG64(seed))
         amp = float(rng.uniform(-2.0, -0.2))
         w = float(rng.uniform(1.0, 6.0))
         t = float(rng.uniform(0, 2 * _m.pi))
-        probs.append((W.problem(2, n, 20.0, _m.pi / 6, 7.5, [W.gauss(amp, w)]), np.array([_m.cos(t), _m.sin(t)])))
-    t0 = time.perf_counter()
-    data = LR.collect_patches(probs, opts, n_cycles=5, patch=64, per_field=6, seed=1)
-    net = csff.Net(LR.init_weights(7))
-    hist = LR.train(net, data, steps=1000, batch=32, lr=2e-3, margin=4, seed=2)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
+        out.append((W.problem(2, n, 20.0, _m.pi / 6, k, [W.gauss(amp, w)]), np.array([_m.cos(t), _m.sin(t)])))
+    return out
+
+
+def measure_learned(csff, torch, dev, stream, flush):
+    """2049^2 on [-20,20]^2, k = 60 (k h = 1.17 on the finest level): plain
+    red-black V(1,1) cycles against red-black + learned step u += N(h^2 r) on
+    the finest level, both inside the FP64 refinement.  The networks are
+    trained on the GPU on residual patches from 257^2 problems with the same
+    k h (k = 7.5), chi drawn from the batch ranges: on 8, 32 and 2,000 seeded
+    solves (the last is the reported network); in units of h^2 the operator is
+    the same on both grids.  A second network trained at level 1's k h (257^2,
+    k = 15) serves level 1 in the levels-0-1 variant."""
+    from paper_1211_4461_gb300 import learned as LR
+    opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
+            "max_cycles": 400, "inner_cycles": 3}
+
+    def train(n_solves, k, steps):
+        t0 = time.perf_counter()
+        data = LR.collect_patches(_learned_problems(n_solves, k), opts, n_cycles=5, patch=64,
+                                  per_field=6 if n_solves <= 32 else 1, seed=1)
+        net = csff.Net(LR.init_weights(7))
+        hist = LR.train(net, data, steps=steps, batch=32, lr=2e-3, margin=4, seed=2)
+        torch.cuda.synchronize()
+        return net, {"solves": n_solves, "patches": int(data[0].shape[0]), "steps": steps,
+                     "train_s": time.perf_counter() - t0, "loss_first": float(np.mean(hist[:5])),
+                     "loss_last": float(np.mean(hist[-20:]))}
+
     case = W.mixed_2d(60.0, n=2049)
-    case["opts"].update(precision="mixed", inner_cycles=3, max_cycles=400)
+    case["opts"].update(precision="mixed", inner_cycles=3, max_cycles=400, refine_fp64=1)
     plan = csff.Plan(case["problem"], case["opts"], stream=stream)
     u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
     F = torch.zeros(720, dtype=torch.complex128, device=dev)
     Fe = torch.zeros(720, dtype=torch.int32, device=dev)
-    out = {"train_s": train_s, "train_patches": int(data[0].shape[0]),
-           "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:]))}
-    maps = {}
-    for name, levels in (("classical", 0), ("learned", 1)):
-        plan.set_learned(net if levels else None, levels=max(levels, 1))
-        info = {}
+    info = {}
 
-        def step():
-            _, inf = plan.solve(case["eta"], u)
-            info["inf"] = inf[0]
-            plan.far_field(case["eta"], u, case["alphas"], F, Fe)
+    def step():
+        _, inf = plan.solve(case["eta"], u)
+        info["inf"] = inf[0]
+        plan.far_field(case["eta"], u, case["alphas"], F, Fe)
 
+    def run(name):
         step()
         ms = _time_events(torch, stream, step, flush, 2)
-        maps[name] = (F.cpu().numpy(), Fe.cpu().numpy().astype(np.int64))
-        out[name] = {"value": 1.0 / (ms / 1e3), "unit": UNIT, "ms_per_map": ms, "cycles": info["inf"]["cycles"],
-                     "rel_res": info["inf"]["rel_res"], "flags": info["inf"]["flags"]}
-    # both solves reach 1e-8; the learned map against the classical one, angle
-    # by angle (mantissa and power-of-two exponent, since the map's terms pass
-    # the FP64 range at this k; the oracle is pinned to this far-field path on
-    # smaller grids)
-    (f0, e0), (f1, e1) = maps["classical"], maps["learned"]
+        return {"value": 1.0 / (ms / 1e3), "unit": UNIT, "ms_per_map": ms, "cycles": info["inf"]["cycles"],
+                "rel_res": info["inf"]["rel_res"], "flags": info["inf"]["flags"]}, \
+            (F.cpu().numpy(), Fe.cpu().numpy().astype(np.int64))
+
+    out = {}
+    plan.set_learned(None)
+    out["classical"], map_c = run("classical")
+    curve = []
+    nets = []
+    for n_solves, steps in ((8, 1000), (32, 1000), (2000, 3000)):
+        net, tinfo = train(n_solves, 7.5, steps)
+        nets.append(net)
+        plan.set_learned(net, levels=1)
+        res, map_l = run("learned")
+        curve.append(dict(tinfo, cycles=res["cycles"], ms_per_map=res["ms_per_map"]))
+    out["training_curve"] = curve
+    out["learned"] = res
+    out["train"] = curve[-1]
+    # the learned map against the classical one, angle by angle (mantissa and
+    # power-of-two exponent: the map's terms pass the FP64 range at this k).
+    # Both solutions meet 1e-8; the per-angle check against the oracle on the
+    # well-conditioned cone runs in the tests (513^2).
+    (f0, e0), (f1, e1) = map_c, map_l
     d = np.abs(f1 * 2.0 ** (e1 - e0).astype(np.float64) - f0) / np.abs(f0)
-    out["far_field_learned_vs_classical"] = {"median_rel_diff": float(np.median(d)), "max_rel_diff": float(d.max())}
+    out["far_field_learned_vs_classical"] = {"median_rel_diff": float(np.median(d)),
+                                             "p90_rel_diff": float(np.quantile(d, 0.9)),
+                                             "max_rel_diff": float(d.max())}
     out["cycle_ratio_learned_vs_classical"] = out["learned"]["cycles"] / max(1, out["classical"]["cycles"])
     out["speedup_learned_vs_classical"] = out["classical"]["ms_per_map"] / out["learned"]["ms_per_map"]
+    net1, t1 = train(32, 15.0, 1000)
+    plan.set_learned(nets[-1], levels=2)
+    plan.set_learned_level(1, net1)
+    out["learned_levels_0_1"], _ = run("learned01")
+    out["learned_levels_0_1"]["level1_train"] = t1
     plan.close()
-    net.close()
+    for n in nets + [net1]:
+        n.close()
+    # the network forward alone on the 2049^2 finest level (4.2 M pixels)
+    y = torch.empty((1, 2047, 2047), dtype=torch.complex64, device=dev)
+    r = torch.randn((1, 2047, 2047), dtype=torch.complex64, device=dev)
+    netf = csff.Net(LR.init_weights(7))
+    out["forward_ms_2047sq"] = _time_events(torch, stream, lambda: netf.forward(r, y, stream=stream), flush, 5)
+    netf.close()
     out["small_grid_129"] = measure_learned_small(csff, torch, dev, stream)
     return out
 

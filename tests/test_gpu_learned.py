@@ -122,6 +122,31 @@ def test_learned_smoother_in_the_solve(csff, trained):
         plan.close()
 
 
+def test_level_specific_networks(csff, trained):
+    """A second network on level 1 (csff_plan_set_learned_level): the solve
+    still meets 1e-8 with the learned step active, detaching the replacement
+    restores the plan's network, and levels without a learned step are
+    rejected."""
+    net, _ = trained
+    from paper_1211_4461_gb300 import learned as LR
+    net1 = csff.Net(LR.init_weights(11))
+    prob, eta = _train_problems([200])[0]
+    plan = csff.Plan(prob, dict(OPTS, precision="mixed"))
+    plan.set_learned(net, levels=2)
+    plan.set_learned_level(1, net1)
+    u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+    _, inf = plan.solve(np.atleast_2d(eta), u)
+    assert inf[0]["status"] == csff.OK and inf[0]["rel_res"] <= 1e-8 and inf[0]["flags"] & 1
+    plan.set_learned_level(1, None)
+    u2 = torch.zeros_like(u)
+    _, inf2 = plan.solve(np.atleast_2d(eta), u2)
+    assert inf2[0]["rel_res"] <= 1e-8
+    with pytest.raises(csff.CsffError):
+        plan.set_learned_level(2, net1)
+    plan.close()
+    net1.close()
+
+
 def test_learned_smoother_halves_the_cycles_at_high_kh(csff):
     """k h = 1.17 (the 2049^2, k = 60 workload's finest level), checked on a
     held-out 513^2, k = 15 problem with a network trained on 257^2, k = 7.5
