@@ -394,8 +394,9 @@ csff_status csff_plan_copy_coefficients(const csff_plan* plan, int level, void* 
    Each instance runs the refinement loop of CSFF_PREC_MIXED with the FP64
    residual and update of its own kernel (FP32 V(1,1) red-black cycles on the
    scaled correction with the coarsest solve in FP64; Sec. 4 with the
-   refinement loop; the fixed schedule of inner_cycles per step,
-   adaptive_inner and refine_fp64 are ignored), but all instances advance inside
+   refinement loop; inner_cycles per step, or with adaptive_inner each
+   instance's steps sized from its previous step's reduction factor as in the
+   single-plan solve; refine_fp64 is ignored), but all instances advance inside
    one cooperative kernel whose phases are separated by grid barriers; the
    tiles of every active instance are shared out among the CTAs, convergence
    is decided per instance on the device.  The solve is captured once as a

@@ -53,6 +53,7 @@ struct BInst {
 
 struct BState {
   int done, status, cycles, refinements, e, eb, cur, rises, n_hist;
+  int n_step;                       // FP32 cycles of the current refinement step
   double prev, nb, rel;
   double hist[CSFF_MAX_HISTORY];
 };
@@ -64,7 +65,8 @@ struct BArgs {
   const int* off_pts;               // [n_inst + 1]
   const int* off_lvl;               // [LC][n_inst + 1] down/up tiles per level
   int LC;
-  int inner;
+  int inner;                        // cycles per refinement step (at most, when adaptive)
+  int adaptive;                     // size each step from the previous step's reduction factor
   double rel_tol;
   int max_cycles;
   double* partials;                 // per FP64 tile
@@ -113,6 +115,11 @@ __device__ bool grid_barrier(unsigned* bar, int* err, int extra, long long limit
 
 __device__ __forceinline__ bool inst_done(const BState* st, int i) {
   return __ldcg(&st[i].done) != 0;
+}
+
+// instance i still runs FP32 cycle c of the current refinement step
+__device__ __forceinline__ bool in_cycle(const BState* st, int i, int c) {
+  return !inst_done(st, i) && c < __ldcg(&st[i].n_step);
 }
 
 template <typename V>
@@ -243,10 +250,13 @@ __device__ void ph_finish(const BArgs& A, int i, bool initial, double* shd) {
       S.rel = 0.0;
     }
     S.e = frexp_e(nrm);
+    S.n_step = A.inner;
     return;
   }
   const double rel = nrm / S.nb;
-  S.cycles += A.inner;
+  const double rel_before = S.rel;
+  const int ran = S.n_step;
+  S.cycles += ran;
   S.refinements += 1;
   S.rel = rel;
   if (S.n_hist < CSFF_MAX_HISTORY) S.hist[S.n_hist++] = rel;
@@ -264,6 +274,8 @@ __device__ void ph_finish(const BArgs& A, int i, bool initial, double* shd) {
   if (status >= 0) {
     S.status = status;
     S.done = 1;
+  } else if (A.adaptive) {
+    S.n_step = refinement_cycles(rel_before, rel, ran, A.rel_tol, A.inner);
   }
 }
 
@@ -329,16 +341,21 @@ __global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
     }
     if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
     for (int c = 0; c < A.inner; ++c) {
+      // instances whose step is shorter sit out its remaining cycles (every
+      // CTA reads the same state, so all leave the loop together)
+      bool busy = false;
+      for (int i = 0; i < n; ++i) busy |= in_cycle(A.st, i, c);
+      if (!busy) break;
       for (int l = 0; l < A.LC; ++l) {
         const int* off = A.off_lvl + (size_t)l * (n + 1);
         for (int it = blockIdx.x; it < off[n]; it += gridDim.x) {
           int i = find_inst(off, n, it);
-          if (!inst_done(A.st, i)) ph_down(A.inst[i], l, it - off[i], c == 0, smem);
+          if (in_cycle(A.st, i, c)) ph_down(A.inst[i], l, it - off[i], c == 0, smem);
         }
         if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
       }
       for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        if (inst_done(A.st, i)) continue;
+        if (!in_cycle(A.st, i, c)) continue;
         const BInst& I = A.inst[i];
         tiles::coarse_levels_block<float, 2, true, double>(I.cl, I.L[I.lc].b, I.L[I.lc].u, I.inv64, smem);
       }
@@ -347,7 +364,7 @@ __global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
         const int* off = A.off_lvl + (size_t)l * (n + 1);
         for (int it = blockIdx.x; it < off[n]; it += gridDim.x) {
           int i = find_inst(off, n, it);
-          if (!inst_done(A.st, i)) ph_up(A.inst[i], l, it - off[i], smem);
+          if (in_cycle(A.st, i, c)) ph_up(A.inst[i], l, it - off[i], smem);
         }
         if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
       }
@@ -369,7 +386,7 @@ __global__ void k_batch_init(BState* st, int n, unsigned* bar, int* err) {
   if (i >= n) return;
   BState& S = st[i];
   S.done = 0; S.status = 0; S.cycles = 0; S.refinements = 0; S.e = 0; S.eb = -2000; S.cur = 0;
-  S.rises = 0; S.n_hist = 0; S.prev = 1.0; S.nb = 0.0; S.rel = 1.0;
+  S.rises = 0; S.n_hist = 0; S.prev = 1.0; S.nb = 0.0; S.rel = 1.0; S.n_step = 1;
 }
 
 size_t batch_smem(const std::vector<csff_plan*>& plans) {
@@ -525,6 +542,7 @@ csff_status launch_batch(csff_batch* B, cudaStream_t s) {
   A.off_lvl = B->d_off + (n + 1);
   A.LC = B->LC;
   A.inner = B->opts.inner_cycles > 0 ? B->opts.inner_cycles : 1;
+  A.adaptive = B->opts.adaptive_inner != 0 ? 1 : 0;
   A.rel_tol = B->opts.rel_tol;
   A.max_cycles = B->opts.max_cycles;
   A.partials = B->d_partials;

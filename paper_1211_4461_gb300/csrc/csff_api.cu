@@ -688,18 +688,7 @@ extern "C" {
 double csff_gamma_from_ecs(double theta) { return std::atan(std::sin(theta) / (2.0 + std::cos(theta))); }
 
 int csff_refinement_cycles(double rel_before, double rel_after, int cycles_run, double rel_tol, int max_cycles) {
-  const int cap = max_cycles > 1 ? max_cycles : 1;
-  if (!(rel_after > 0.0) || !(rel_before > rel_after) || !std::isfinite(rel_before) || !(rel_tol > 0.0) ||
-      cycles_run < 1)
-    return cap;
-  if (rel_after <= rel_tol) return 1;
-  const double rho = std::pow(rel_after / rel_before, 1.0 / cycles_run);
-  if (!(rho > 0.0) || !(rho < 1.0)) return cap;
-  // 1e-9 of slack keeps a ratio that is an integer up to rounding from taking one
-  // cycle more
-  const double need = std::ceil(std::log(rel_tol / rel_after) / std::log(rho) - 1e-9);
-  if (!(need < cap)) return cap;
-  return need < 1.0 ? 1 : (int)need;
+  return csff::refinement_cycles(rel_before, rel_after, cycles_run, rel_tol, max_cycles);
 }
 
 const char* csff_status_string(csff_status s) {

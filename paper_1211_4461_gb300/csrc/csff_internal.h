@@ -198,6 +198,27 @@ inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::mem
 // Event bracket around the launches of one kernel family (see csff_prof_begin).
 enum ProfFamily { PF_FF_CONTRACT = 0, PF_MG32 = 1, PF_MG64 = 2, PF_FF_OTHER = 3, PF_TILES32 = 4, PF_TILES32_FINE = 5 };
 // events around one launch, counted in family and (when >= 0) in family2 as well
+// The adaptive refinement schedule (csff_refinement_cycles), shared by the
+// host (single plans) and the batched kernel: after a step of cycles_run FP32
+// V-cycles took the relative residual from rel_before to rel_after, the next
+// step runs ceil(log(rel_tol / rel_after) / log rho) cycles, rho the step's
+// per-cycle factor, clamped to [1, max_cycles]; max_cycles without a reduction.
+__host__ __device__ inline int refinement_cycles(double rel_before, double rel_after, int cycles_run,
+                                                 double rel_tol, int max_cycles) {
+  const int cap = max_cycles > 1 ? max_cycles : 1;
+  if (!(rel_after > 0.0) || !(rel_before > rel_after) || !isfinite(rel_before) || !(rel_tol > 0.0) ||
+      cycles_run < 1)
+    return cap;
+  if (rel_after <= rel_tol) return 1;
+  const double rho = pow(rel_after / rel_before, 1.0 / cycles_run);
+  if (!(rho > 0.0) || !(rho < 1.0)) return cap;
+  // 1e-9 of slack keeps a ratio that is an integer up to rounding from taking one
+  // cycle more
+  const double need = ceil(log(rel_tol / rel_after) / log(rho) - 1e-9);
+  if (!(need < cap)) return cap;
+  return need < 1.0 ? 1 : (int)need;
+}
+
 struct ProfScope {
   int slot = -1, slot2 = -1, slot3 = -1;
   cudaStream_t stream = nullptr;

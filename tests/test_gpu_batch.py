@@ -109,3 +109,34 @@ def test_bounded_barrier_reports_timeout_and_context_survives(csff):
     st, infos = b.solve(eta)
     assert st == csff.OK and all(x["rel_res"] <= 1e-8 for x in infos)
     b.close()
+
+
+def test_batch_adaptive_schedule_matches_single_plans(csff):
+    """With adaptive_inner each instance sizes its refinement steps from the
+    previous step's reduction factor inside the persistent kernel: the same
+    cycle counts and histories as the single-plan FP64-refinement solves with
+    the same schedule, no more cycles than the fixed schedule, and every
+    solution meets 1e-8 under the oracle's operator."""
+    cs = _cases(6, sizes=(65, 129, 257))
+    for c in cs:
+        c["opts"].update(inner_cycles=6, adaptive_inner=1)
+    eta = np.vstack([c["eta"] for c in cs])
+    b = csff.Batch([c["problem"] for c in cs], cs[0]["opts"])
+    st, infos = b.solve(eta)
+    assert st == csff.OK
+    bf = csff.Batch([c["problem"] for c in cs], dict(cs[0]["opts"], adaptive_inner=0))
+    _, fixed = bf.solve(eta)
+    assert sum(x["cycles"] for x in infos) <= sum(x["cycles"] for x in fixed)
+    for i, c in enumerate(cs):
+        p = O.problem_from_dict(c["problem"])
+        rhs = O.rhs(p, c["eta"][0])
+        u = b.solution(i).cpu().numpy().reshape((p.m, p.m))
+        assert O.norm2(O.residual(O.make_level(p, p.n), u, rhs)) <= 1.01e-8 * O.norm2(rhs)
+        plan = csff.Plan(c["problem"], c["opts"])
+        us = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+        _, inf1 = plan.solve(c["eta"], us)
+        assert inf1[0]["cycles"] == infos[i]["cycles"]
+        assert np.allclose(inf1[0]["history"], infos[i]["history"], rtol=1e-5, atol=1e-14)
+        plan.close()
+    b.close()
+    bf.close()
