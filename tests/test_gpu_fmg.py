@@ -55,3 +55,30 @@ def test_fmg_needs_an_fp64_plan(csff):
     with pytest.raises(csff.CsffError):
         plan.solve_fmg(c["eta"], u)
     plan.close()
+
+
+def test_fmg_finest_cycles_against_table3_on_256(csff):
+    """Table 3's setting on the 256^3 grid (every k0 resolved there, k0 h <
+    0.625): the nested iteration's finest level needs within two V-cycles of
+    the counts Table 3 prints, and fewer than the V-cycles from zero for the
+    smaller k0 (tests/golden/table3_fmg_gmres3.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table3_fmg_gmres3.txt")
+    gold = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            k, pts, cyc = line.split()[:3]
+            gold[(float(k), int(pts))] = int(cyc)
+    for k in (0.25, 0.5, 1.0, 2.0, 4.0):
+        c = W.paper_gmres(dim=3, k=k, n=257)
+        c["opts"]["precision"] = "fp64"
+        plan = csff.Plan(c["problem"], c["opts"])
+        u = torch.zeros(plan.N, dtype=torch.complex128, device="cuda")
+        st, info, cyc = plan.solve_fmg(c["eta"], u)
+        assert st == csff.OK and info[0]["rel_res"] <= 1e-6
+        assert abs(cyc[0][-1] - gold[(k, 256)]) <= 2, (k, cyc[0], gold[(k, 256)])
+        if k <= 0.5:
+            u0 = torch.zeros_like(u)
+            _, inf0 = plan.solve(c["eta"], u0)
+            assert cyc[0][-1] < inf0[0]["cycles"]
+        plan.close()
