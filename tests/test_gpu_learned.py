@@ -58,6 +58,35 @@ def test_forward_matches_oracle(csff):
         assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
 
 
+def test_fused_forward_over_several_ragged_tiles(csff):
+    """Inference runs the three layers fused per output tile of 32 x 16 pixels
+    (activations in shared memory): patches of 37 x 70 pixels span three tile
+    rows and three tile columns with ragged last ones, so the per-layer zero
+    padding at the patch edges, the tile seams and the ragged tails all enter.
+    Each output pixel is compared with the oracle on the BF16-rounded weights
+    and input; the relative bound per pixel allows the BF16 rounding of the
+    two hidden layers."""
+    theta = NO.init_params(11)
+    net = csff.Net(theta)
+    r = W.rand_complex((2, 37, 70), 12)
+    y = torch.empty(r.shape, dtype=torch.complex64, device="cuda")
+    net.forward(_dev(r), y)
+    tb = _bf16(theta)
+    for b in range(r.shape[0]):
+        rb = _bf16(r[b].real) + 1j * _bf16(r[b].imag)
+        ref, _ = NO.forward(tb, rb)
+        got = y[b].cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 5e-2 * scale
+    # the network has no bias: a patch of zeros gives zeros
+    z = torch.zeros((1, 19, 33), dtype=torch.complex64, device="cuda")
+    y0 = torch.empty_like(z)
+    net.forward(z, y0)
+    assert torch.count_nonzero(y0).item() == 0
+    net.close()
+
+
 def test_loss_and_gradient_match_oracle(csff):
     theta = NO.init_params(6)
     net = csff.Net(theta)
