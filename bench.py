@@ -612,11 +612,75 @@ def measure_variants(csff, torch, dev, stream, flush, headline_ms):
                             "cycles_total": cyc_p,
                             "note": "the same 64 instances by plain FP64 V-cycles to 1e-8, one after another"}
     out["batched_mixed_speedup_vs_plain_fp64"] = ms_p / ms_b
+    out["batched_learned"] = measure_batched_learned(csff, torch, dev, stream, flush, bc, ms_p, ms_b)
     out["3d_257_16dirs"] = measure_3d(csff, torch, dev, stream, flush)
     out["vcycle_4097"] = measure_vcycle_bandwidth(csff, torch, dev, stream, flush)
     out["learned_2049"] = measure_learned(csff, torch, dev, stream, flush)
     out["gmres3_table2"] = measure_gmres_table2(csff, torch, dev, stream, flush)
     out["partial_wave_fig8"] = measure_partial_wave(csff, torch, dev, stream, flush)
+    return out
+
+
+def measure_batched_learned(csff, torch, dev, stream, flush, bc, ms_plain, ms_batched):
+    """The combined form: the 64 uneven instances in one persistent launch
+    with FP32 cycles inside the FP64 refinement and the learned step ending
+    every cycle on each instance's finest level (the network trained on the GPU
+    on residual patches of 257^2 problems at k h = 1.17, 32 seeded solves),
+    against the plain FP64 V-cycles one instance after another (ms_plain) and
+    the classical batched form (ms_batched), maps with far fields, all at 1e-8.
+    Instances far from the network's k h hand themselves back to plain cycles
+    (the fallback); a second batch of 16 instances at the network's k h
+    (n in {257, 513, 1025}, k = 7.5 (n-1)/256) shows the cycle saving where the
+    network applies."""
+    from paper_1211_4461_gb300 import learned as LR
+    opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
+            "max_cycles": 400, "inner_cycles": 3}
+    data = LR.collect_patches(_learned_problems(32, 7.5), opts, n_cycles=5, patch=64, per_field=6, seed=1)
+    net = csff.Net(LR.init_weights(7))
+    LR.train(net, data, steps=1000, batch=32, lr=2e-3, margin=4, seed=2)
+    out = {}
+
+    def run(cases, learned, far_field):
+        eta = np.vstack([c["eta"] for c in cases])
+        b = csff.Batch([c["problem"] for c in cases], cases[0]["opts"], stream=stream)
+        if learned:
+            b.set_learned(net)
+        tc, per = b.autotune(eta)
+        Fs = [torch.zeros(720, dtype=torch.complex128, device=dev) for _ in cases]
+        Es = [torch.zeros(720, dtype=torch.int32, device=dev) for _ in cases]
+        info = {}
+
+        def step():
+            _, inf = b.solve(eta)
+            info["inf"] = inf
+            if far_field:
+                b.far_field(eta, [c["alphas"] for c in cases], Fs, Es)
+
+        step()
+        ms = _time_events(torch, stream, step, flush, 3)
+        inf = info["inf"]
+        b.close()
+        return {"value": len(cases) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                "autotuned": {"tile_coarse_points": tc, "ctas_per_sm": per},
+                "all_converged": all(x["rel_res"] <= 1e-8 for x in inf),
+                "cycles_total": int(sum(x["cycles"] for x in inf)),
+                "fell_back": int(sum(1 for x in inf if x["flags"] & 2))}
+
+    out["config4_64"] = run(bc, True, True)
+    out["config4_64"]["speedup_vs_plain_fp64"] = ms_plain / out["config4_64"]["ms_per_step"]
+    out["config4_64"]["speedup_vs_batched_classical"] = ms_batched / out["config4_64"]["ms_per_step"]
+    kh = W.batch_2d(16, seed=11, sizes=(257, 513, 1025))
+    for c in kh:
+        c["problem"]["k"] = 7.5 * (c["problem"]["n"] - 1) / 256
+        c["opts"].update(precision="mixed", inner_cycles=3, coarsest_n=5, refine_fp64=1)
+    out["kh117_16_classical"] = run(kh, False, False)
+    out["kh117_16_learned"] = run(kh, True, False)
+    out["kh117_16_learned"]["speedup_vs_classical"] = (out["kh117_16_classical"]["ms_per_step"] /
+                                                       out["kh117_16_learned"]["ms_per_step"])
+    out["note"] = ("solve and far field per step for config4_64, solve only for the k h = 1.17 batch (fixed "
+                   "three cycles a refinement step in both of its forms); the learned step costs a residual "
+                   "pass, the network pass and two grid barriers per cycle")
+    net.close()
     return out
 
 

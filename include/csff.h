@@ -433,6 +433,19 @@ csff_status csff_batch_autotune(csff_batch* batch, const double* eta_host, int* 
    launch (0 = the occupancy maximum, larger values are clamped to it).
    Errors: CSFF_ERR_INVALID_ARG. */
 csff_status csff_batch_set_tiles(csff_batch* batch, int tc_big, int ctas_per_sm);
+/* Learned smoother in the batched solve (an addition to the paper's method,
+   like csff_plan_set_learned): every FP32 V-cycle of an instance ends with
+   u <- u + N(h^2 (b - A u)) on its finest level, N the network (not owned; it
+   must outlive the solves that use it, and its weights are read at each
+   solve).  The first two refinement steps of an instance run without it; the
+   second's reduction factor, capped at guard, is the reference; an instance
+   whose learned step reduces the residual less than the reference runs plain
+   cycles for the rest of its solve (info.flags bit 1; bit 0 = a network was
+   set).  With a network the cycles per step stay at inner_cycles (the
+   adaptive schedule is off, as in the single-problem solve).  net = NULL
+   removes it.  Errors: CSFF_ERR_INVALID_ARG (guard <= 0, or the network's
+   shared memory does not fit beside the tiles'). */
+csff_status csff_batch_set_learned(csff_batch* batch, csff_net* net, double guard);
 
 /* Test hook for the bounded barrier: extra_arrivals = 1 makes every grid
    barrier of the next solves wait for one CTA that does not exist, so each

@@ -117,6 +117,7 @@ _SIGS = {
     "csff_batch_autotune": (_i, [_vp, _dp, C.POINTER(_i), C.POINTER(_i)]),
     "csff_batch_debug_barrier": (_i, [_vp, _i, C.c_longlong]),
     "csff_batch_set_tiles": (_i, [_vp, _i, _i]),
+    "csff_batch_set_learned": (_i, [_vp, _vp, _d]),
     "csff_net_num_params": (_i, []),
     "csff_net_create": (_i, [_fp, C.POINTER(_vp)]),
     "csff_net_destroy": (None, [_vp]),
@@ -307,6 +308,13 @@ class Batch:
     def set_tiles(self, tc_big, ctas_per_sm=0):
         """Fix the large levels' tile size (16 or 8) and the CTAs per SM."""
         _check(_lib.csff_batch_set_tiles(self._h, int(tc_big), int(ctas_per_sm)), "batch_set_tiles")
+
+    def set_learned(self, net, guard=0.5):
+        """Attach (net) or detach (None) the learned step on every instance's
+        finest level."""
+        _check(_lib.csff_batch_set_learned(self._h, net._h if net is not None else None, float(guard)),
+               "batch_set_learned")
+        self._net = net
 
     def debug_barrier(self, extra_arrivals, spin_limit=0):
         _check(_lib.csff_batch_debug_barrier(self._h, int(extra_arrivals), int(spin_limit)), "batch_debug_barrier")

@@ -12,8 +12,18 @@
 // Convergence, divergence and non-finite checks are taken per instance on the
 // device; converged instances drop out of the following phases.
 //
+// With a learned smoother (csff_batch_set_learned) every FP32 cycle of an
+// instance ends with the learned step on its finest level, u <- u + N(h^2 r)
+// with r = b - A u: a residual phase, then the network phase, whose work items
+// are the 32 x 16 output tiles of the fused three-layer network (net_tile.cuh)
+// of every instance that takes the step.  As in the single-problem solve the
+// first two refinement steps of an instance run without it, the second sets
+// the reference reduction factor (at most the guard), and an instance whose
+// learned step reduces less than the reference runs plain cycles from then on.
+//
 // Every barrier wait is bounded: after BAR_SPIN_LIMIT polls a CTA raises the
-// error word and all CTAs leave the kernel (status CSFF_ERR_TIMEOUT).
+// error word and all CTAs leave the kernel (status CSFF_ERR_TIMEOUT); so is
+// every wait for the network's MMAs.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -21,6 +31,7 @@
 #include <vector>
 
 #include "mg_tiles.cuh"
+#include "net_tile.cuh"
 
 namespace csff {
 namespace {
@@ -49,11 +60,14 @@ struct BInst {
   const double2* chi;               // [n_gauss][2][m]
   const double2* uinc;              // [2][m]
   double k2;
+  float h2;                         // h^2 of the finest level (the learned step's input scale)
 };
 
 struct BState {
   int done, status, cycles, refinements, e, eb, cur, rises, n_hist;
   int n_step;                       // FP32 cycles of the current refinement step
+  int lrn, lflags;                  // learned step on; bit 0 a network is set, bit 1 it was switched off
+  double lref;                      // reference reduction factor of the learned steps
   double prev, nb, rel;
   double hist[CSFF_MAX_HISTORY];
 };
@@ -74,6 +88,10 @@ struct BArgs {
   int* err;
   int extra_arrivals;               // test hook: arrivals that never come (0 in use)
   long long spin_limit;             // polls before a barrier wait gives up
+  const __nv_bfloat16* net_wb;      // learned smoother's BF16 weights, or null
+  double guard;                     // largest reference factor of the learned steps
+  const int* off_net;               // [n_inst + 1] network tiles per instance
+  int net_off;                      // byte offset of the network's weight region in shared memory
 };
 
 __device__ __forceinline__ int find_inst(const int* off, int n, int item) {
@@ -120,6 +138,11 @@ __device__ __forceinline__ bool inst_done(const BState* st, int i) {
 // instance i still runs FP32 cycle c of the current refinement step
 __device__ __forceinline__ bool in_cycle(const BState* st, int i, int c) {
   return !inst_done(st, i) && c < __ldcg(&st[i].n_step);
+}
+
+// ... and ends it with the learned step
+__device__ __forceinline__ bool learned_now(const BState* st, int i, int c) {
+  return in_cycle(st, i, c) && __ldcg(&st[i].lrn) != 0;
 }
 
 template <typename V>
@@ -251,6 +274,9 @@ __device__ void ph_finish(const BArgs& A, int i, bool initial, double* shd) {
     }
     S.e = frexp_e(nrm);
     S.n_step = A.inner;
+    S.lrn = 0;
+    S.lflags = A.net_wb ? 1 : 0;
+    S.lref = A.guard;
     return;
   }
   const double rel = nrm / S.nb;
@@ -271,12 +297,99 @@ __device__ void ph_finish(const BArgs& A, int i, bool initial, double* shd) {
     if (S.rises >= 3) status = CSFF_ERR_DIVERGED;
     else if (S.cycles >= A.max_cycles) status = CSFF_ERR_NOT_CONVERGED;
   }
+  if (A.net_wb) {
+    // the learned step: off for the first two refinement steps, the second's
+    // factor is the reference; a learned step that reduces less turns it off
+    const double factor = rel / rel_before;
+    if (S.refinements <= 2) {
+      if (S.refinements == 2) {
+        S.lref = fmin(factor, A.guard);
+        S.lrn = 1;
+      }
+    } else if (S.lrn && factor > S.lref) {
+      S.lrn = 0;
+      S.lflags |= 2;
+    }
+  }
   if (status >= 0) {
     S.status = status;
     S.done = 1;
-  } else if (A.adaptive) {
+  } else if (A.adaptive && !A.net_wb) {
     S.n_step = refinement_cycles(rel_before, rel, ran, A.rel_tol, A.inner);
   }
+}
+
+// r = b - A u on the finest level in FP32 (the learned step's input), with the
+// coefficients formed from the separable factors as in the tiles:
+// A u = d u - c sum_nbr u, d = 4c - k^2 - sum_g X_g Y_g
+__device__ void ph_resid0(const BInst& I, int t) {
+  const BLevel& F = I.L[0];
+  const int m = F.m;
+  const long long N = (long long)m * m;
+  const float2 c = F.c;
+  const float2 D0 = make_float2(__fmaf_rn(4.f, c.x, -F.K.k2), __fmul_rn(4.f, c.y));
+  for (int k = 0; k < PT / 256; ++k) {
+    const long long j = (long long)t * PT + k * 256 + threadIdx.x;
+    if (j >= N) return;
+    const int iy = (int)(j / m), ix = (int)(j - (long long)iy * m);
+    float2 d = D0;
+    for (int g = 0; g < F.K.ng; ++g) {
+      const float2* f = F.K.fac + (size_t)g * 2 * m;
+      d = tiles::xfms(d, f[ix], f[m + iy]);
+    }
+    const float2 uj = F.u[j];
+    float2 sn = make_float2(0.f, 0.f);
+    if (ix > 0) sn = tiles::xadd(sn, F.u[j - 1]);
+    if (ix < m - 1) sn = tiles::xadd(sn, F.u[j + 1]);
+    if (iy > 0) sn = tiles::xadd(sn, F.u[j - m]);
+    if (iy < m - 1) sn = tiles::xadd(sn, F.u[j + m]);
+    F.t[j] = tiles::xfma(tiles::xfms(F.b[j], d, uj), c, sn);          // b - d u + c s
+  }
+}
+
+// the first network work item at or after `from` (in steps of the grid) whose
+// instance takes the learned step in cycle c, or the total
+__device__ int next_net_item(const BArgs& A, int c, int from) {
+  const int n = A.n_inst, total = A.off_net[n];
+  for (int it = from; it < total; it += gridDim.x)
+    if (learned_now(A.st, find_inst(A.off_net, n, it), c)) return it;
+  return total;
+}
+
+// network work item it: an output tile of its instance's finest level, input
+// r in the level's t buffer, output u
+__device__ nettile::Tile net_item(const BArgs& A, int it, float* scale) {
+  const int i = find_inst(A.off_net, A.n_inst, it);
+  const BInst& I = A.inst[i];
+  const int t = it - A.off_net[i], tiles_x = (I.m + nettile::TW - 1) / nettile::TW;
+  *scale = I.h2;
+  return nettile::Tile{I.L[0].t, I.L[0].u, I.m, I.m, (t % tiles_x) * nettile::TW - 3,
+                       (t / tiles_x) * nettile::TH - 3};
+}
+
+// the network phase of cycle c: every output tile of every instance that takes
+// the learned step, u += N(h^2 r); the next tile's input is loaded while the
+// current tile's MMAs run.  Kept out of line: the kernel body stays small
+// enough for every host build of the compiler.
+__device__ __noinline__ bool ph_net(const BArgs& A, int c, nettile::Ctx& nc) {
+  const int total = A.off_net[A.n_inst];
+  int it = next_net_item(A, c, blockIdx.x);
+  if (it >= total) return true;
+  nettile::zero_planes(nc);
+  __syncthreads();
+  float2 xr[nettile::SPT];
+  float scale = 1.f, next_scale = 1.f;
+  nettile::Tile cur = net_item(A, it, &scale);
+  nettile::load_x(cur, xr);
+  while (it < total) {
+    const int nxt = next_net_item(A, c, it + gridDim.x);
+    const nettile::Tile next = net_item(A, nxt < total ? nxt : it, &next_scale);
+    if (!nettile::run_tile(nc, cur, xr, scale, 1, A.err, nxt < total ? &next : nullptr)) return false;
+    cur = next;
+    scale = next_scale;
+    it = nxt;
+  }
+  return true;
 }
 
 // ---- FP32 V-cycle phases --------------------------------------------------------
@@ -310,11 +423,8 @@ __device__ void ph_up(const BInst& I, int l, int t, unsigned char* smem) {
   }
 }
 
-// at most 85 registers a thread, so that three CTAs fit on an SM (the
-// autotuner picks between one and the occupancy maximum)
-__global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double shd[8];
+template <bool LEARNED>
+__device__ __forceinline__ void batch_body(const BArgs& A, unsigned char* smem, double* shd, nettile::Ctx& nc) {
   const int n = A.n_inst;
   const int npts = A.off_pts[n];
   // ---- initial residual r = b (u = 0) and its norm
@@ -368,6 +478,19 @@ __global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
         }
         if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
       }
+      if constexpr (LEARNED) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) any |= learned_now(A.st, i, c);
+        if (any) {
+          for (int it = blockIdx.x; it < npts; it += gridDim.x) {
+            int i = find_inst(A.off_pts, n, it);
+            if (learned_now(A.st, i, c)) ph_resid0(A.inst[i], it - A.off_pts[i]);
+          }
+          if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
+          if (!ph_net(A, c, nc)) return;
+          if (!grid_barrier(A.bar, A.err, A.extra_arrivals, A.spin_limit)) return;
+        }
+      }
     }
     for (int it = blockIdx.x; it < npts; it += gridDim.x) {
       int i = find_inst(A.off_pts, n, it);
@@ -380,6 +503,24 @@ __global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
   }
 }
 
+// at most 85 registers a thread, so that three CTAs fit on an SM (the
+// autotuner picks between one and the occupancy maximum).  LEARNED: the
+// learned step ends every cycle; each CTA holds the network's weight operands
+// and 128 columns of tensor memory for the whole launch, and the activation
+// planes share the tiles' shared memory.  The two forms are separate kernels:
+// the occupancy calculation, which bounds a cooperative launch, admits one CTA
+// per SM for any kernel with tensor-memory instructions, so the classical form
+// carries none.
+template <bool LEARNED>
+__global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double shd[8];
+  nettile::Ctx nc;
+  if constexpr (LEARNED) nettile::setup(nc, smem, smem + A.net_off, A.net_wb);
+  batch_body<LEARNED>(A, smem, shd, nc);
+  if constexpr (LEARNED) nettile::teardown(nc);
+}
+
 __global__ void k_batch_init(BState* st, int n, unsigned* bar, int* err) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) { bar[0] = 0; bar[1] = 0; *err = 0; }
@@ -387,6 +528,7 @@ __global__ void k_batch_init(BState* st, int n, unsigned* bar, int* err) {
   BState& S = st[i];
   S.done = 0; S.status = 0; S.cycles = 0; S.refinements = 0; S.e = 0; S.eb = -2000; S.cur = 0;
   S.rises = 0; S.n_hist = 0; S.prev = 1.0; S.nb = 0.0; S.rel = 1.0; S.n_step = 1;
+  S.lrn = 0; S.lflags = 0; S.lref = 1.0;
 }
 
 size_t batch_smem(const std::vector<csff_plan*>& plans) {
@@ -436,6 +578,10 @@ struct csff_batch {
   int grid = 0;
   bool tuned = false;
   std::vector<int> off_host;
+  csff_net* net = nullptr;        // learned smoother (csff_batch_set_learned), not owned
+  double guard = 0.5;
+  size_t smem_tiles = 0;          // shared memory of the tile phases
+  int net_off = 0;
 };
 
 namespace {
@@ -451,6 +597,11 @@ csff_status binvalid(const char* s) {
   return CSFF_ERR_INVALID_ARG;
 }
 
+// the persistent kernel of the batch's form
+const void* batch_kernel(const csff_batch* B) {
+  return B->net ? (const void*)csff::k_batch_solve<true> : (const void*)csff::k_batch_solve<false>;
+}
+
 // device descriptors of every instance for the current tile choice
 csff_status upload_descriptors(csff_batch* B) {
   const int n = B->n;
@@ -458,7 +609,7 @@ csff_status upload_descriptors(csff_batch* B) {
   int LC = 0;
   for (int i = 0; i < n; ++i) LC = std::max(LC, B->plans[i]->fused_lc);
   B->LC = LC;
-  std::vector<int> off_pts(n + 1, 0), off_lvl((size_t)LC * (n + 1), 0);
+  std::vector<int> off_pts(n + 1, 0), off_lvl((size_t)LC * (n + 1), 0), off_net(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     csff_plan* P = B->plans[i];
     BInst& I = hi[i];
@@ -503,7 +654,10 @@ csff_status upload_descriptors(csff_batch* B) {
     I.chi = P->chi_tab[0];
     I.uinc = P->uinc_tab;
     I.k2 = P->prob.k * P->prob.k;
+    I.h2 = (float)(P->lv[0].h * P->lv[0].h);
     off_pts[i + 1] = off_pts[i] + (int)((I.N + csff::PT - 1) / csff::PT);
+    off_net[i + 1] = off_net[i] + ((I.m + csff::nettile::TW - 1) / csff::nettile::TW) *
+                                      ((I.m + csff::nettile::TH - 1) / csff::nettile::TH);
     for (int l = 0; l < LC; ++l) {
       int t = (l < I.lc) ? I.L[l].ntx * I.L[l].ntx : 0;
       off_lvl[(size_t)l * (n + 1) + i + 1] = off_lvl[(size_t)l * (n + 1) + i] + t;
@@ -511,6 +665,7 @@ csff_status upload_descriptors(csff_batch* B) {
   }
   B->off_host = off_pts;
   B->off_host.insert(B->off_host.end(), off_lvl.begin(), off_lvl.end());
+  B->off_host.insert(B->off_host.end(), off_net.begin(), off_net.end());
   BK(cudaMemcpy(B->d_inst, hi.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice), "upload batch descriptors");
   if (B->d_off) cudaFree(B->d_off);
   BK(cudaMalloc((void**)&B->d_off, sizeof(int) * B->off_host.size()), "batch tables");
@@ -526,9 +681,9 @@ csff_status launch_batch(csff_batch* B, cudaStream_t s) {
   int dev = 0, sms = 0, occ = 0;
   BK(cudaGetDevice(&dev), "device");
   BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-  BK(cudaFuncSetAttribute(csff::k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem),
-     "batch smem");
-  BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csff::k_batch_solve, 256, B->smem), "occupancy");
+  const void* kern = batch_kernel(B);
+  BK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem), "batch smem");
+  BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, B->smem), "occupancy");
   if (occ < 1) return binvalid("batch kernel does not fit on an SM");
   int per = B->ctas_per_sm > 0 ? std::min(B->ctas_per_sm, occ) : occ;
   B->grid = per * sms;
@@ -550,11 +705,14 @@ csff_status launch_batch(csff_batch* B, cudaStream_t s) {
   A.err = B->d_err;
   A.extra_arrivals = B->dbg_extra;
   A.spin_limit = B->dbg_spin > 0 ? B->dbg_spin : csff::BAR_SPIN_LIMIT;
+  A.net_wb = B->net ? (const __nv_bfloat16*)csff::net_weights_bf16(B->net) : nullptr;
+  A.guard = B->guard;
+  A.off_net = B->d_off + (size_t)(n + 1) * (1 + B->LC);
+  A.net_off = B->net_off;
   void* args[] = {&A};
   {
     csff::ProfScope ps(csff::PF_MG32, s, 0, 0);
-    BK(cudaLaunchCooperativeKernel((const void*)csff::k_batch_solve, dim3(B->grid), dim3(256), args, B->smem, s),
-       "cooperative batch launch");
+    BK(cudaLaunchCooperativeKernel(kern, dim3(B->grid), dim3(256), args, B->smem, s), "cooperative batch launch");
   }
   csff::count_launch();
   return CSFF_OK;
@@ -638,7 +796,7 @@ csff_status collect(csff_batch* B, csff_info* infos, int* worst) {
   const int err = *B->h_err_p;
   *worst = CSFF_OK;
   if (err) {
-    csff::set_error("batch kernel: a grid barrier wait ran out");
+    csff::set_error("batch kernel: a grid barrier or tensor-core wait ran out");
     *worst = CSFF_ERR_TIMEOUT;
   }
   for (int i = 0; i < B->n; ++i) {
@@ -654,6 +812,7 @@ csff_status collect(csff_batch* B, csff_info* infos, int* worst) {
       in.rel_res = S.rel;
       in.conv_factor = S.cycles > 0 ? std::pow(S.rel, 1.0 / S.cycles) : 0.0;
       in.n_hist = S.n_hist;
+      in.flags = S.lflags;
       for (int h = 0; h < S.n_hist && h < CSFF_MAX_HISTORY; ++h) in.history[h] = S.hist[h];
     }
   }
@@ -720,7 +879,7 @@ csff_status csff_batch_create(int n_inst, const csff_problem* probs, const csff_
       (e = cudaStreamCreateWithFlags(&B->gstream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&B->gev, cudaEventDisableTiming)) != cudaSuccess)
     return fail(csff::cuda_fail(e, "batch allocation"));
-  B->smem = csff::batch_smem(B->plans);
+  B->smem = B->smem_tiles = csff::batch_smem(B->plans);
   if (B->smem > 227 * 1024) return fail(binvalid("batched solve: coarse levels exceed shared memory"));
   csff_status s = upload_descriptors(B);
   if (s != CSFF_OK) return fail(s);
@@ -782,6 +941,30 @@ csff_status csff_batch_debug_barrier(csff_batch* B, int extra_arrivals, long lon
   return CSFF_OK;
 }
 
+csff_status csff_batch_set_learned(csff_batch* B, csff_net* net, double guard) {
+  if (!B) return binvalid("NULL batch");
+  if (net && !(guard > 0.0)) return binvalid("guard must be positive");
+  B->net = net;
+  B->guard = guard;
+  if (net) {
+    // the network's activation planes share the tiles' shared memory; its
+    // weight operands, mbarrier and tensor-memory slot follow
+    const size_t planes = std::max<size_t>((B->smem_tiles + 127) / 128 * 128, csff::nettile::PLANES_BYTES);
+    B->net_off = (int)planes;
+    B->smem = planes + csff::nettile::WREG_BYTES;
+    if (B->smem > 227 * 1024) {
+      B->net = nullptr;
+      B->smem = B->smem_tiles;
+      return binvalid("batched solve: the learned step does not fit in shared memory");
+    }
+  } else {
+    B->net_off = 0;
+    B->smem = B->smem_tiles;
+  }
+  if (B->gexec) { cudaGraphExecDestroy(B->gexec); B->gexec = nullptr; }   // parameters are baked into the graph
+  return CSFF_OK;
+}
+
 csff_status csff_batch_set_tiles(csff_batch* B, int tc_big, int ctas_per_sm) {
   if (!B) return binvalid("NULL batch");
   if (tc_big != 8 && tc_big != 16) return binvalid("tile size must be 8 or 16 coarse points");
@@ -797,9 +980,9 @@ csff_status csff_batch_autotune(csff_batch* B, const double* eta, int* tc_big_ou
   int dev = 0, sms = 0, occ = 0;
   BK(cudaGetDevice(&dev), "device");
   BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-  BK(cudaFuncSetAttribute(csff::k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem),
-     "batch smem");
-  BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, csff::k_batch_solve, 256, B->smem), "occupancy");
+  const void* kern = batch_kernel(B);
+  BK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem), "batch smem");
+  BK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, B->smem), "occupancy");
   cudaEvent_t e0, e1;
   BK(cudaEventCreate(&e0), "event");
   BK(cudaEventCreate(&e1), "event");

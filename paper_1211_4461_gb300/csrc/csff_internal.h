@@ -328,6 +328,7 @@ unsigned prof_mask();
 csff_status learned_step(csff_plan* P, int level, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s);
 csff_status net_reserve(csff_net* N, long long npix);
 csff_status net_check(csff_net* N);
+const void* net_weights_bf16(const csff_net* N);   // the network's BF16 weights on the device
 
 // ---- far field (farfield.cu) -----------------------------------------------
 void free_ff_buffers(csff_plan* P);

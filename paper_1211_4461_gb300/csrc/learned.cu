@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "csff_internal.h"
+#include "net_tile.cuh"
 
 namespace csff {
 namespace {
@@ -465,328 +466,44 @@ __global__ void k_adam(float* w, float* m, float* v, const float* gr, __nv_bfloa
   wb[i] = __float2bfloat16(wi);
 }
 
-// ---- Inference with the three layers fused in shared memory.
-// An output tile of TW x TH pixels needs layer-2 activations on a one-pixel
-// ring around it, layer-1 activations on a two-pixel ring and the input on a
-// three-pixel ring: a region of RW x RH = (TW + 6) x (TH + 6) pixels, its
-// pixels numbered row-major (region row p = y RW + x).  Layer L is computed on
-// the run of region rows from (L, L) to (RW-1-L, RH-1-L), in blocks of 128
-// consecutive rows, as tcgen05 GEMMs M128 N16 K16 (BF16 operands, FP32
-// accumulators in tensor memory):
-//   layer 1: the input entry E[p] = (x(p-1), x(p), x(p+1)) of both channels
-//     (six values and two zeros: one 16-byte K group) is one filter row of
-//     the 3x3 stencil, so two MMAs cover it, with the K groups (E[p-RW], E[p])
-//     and (E[p+RW], E[p+2RW]) (the last with zero weights);
-//   layers 2 and 3: nine MMAs, one per tap (a, b), each reading the
-//     activation planes shifted by (a-1) RW + (b-1) rows.
-// A shift by whole rows is a start-address offset: activations are kept as
-// two planes (channels 0-7 and 8-15) of 16-byte rows, the no-swizzle K-major
-// operand layout (8-row core matrices 128 bytes apart, the two K groups one
-// plane apart).  Pixels outside the patch are zero in every layer (zero
-// padding per layer, as in the layer-by-layer kernels).  A row whose
-// neighbourhood leaves the region at its depth holds a value that only rows of
-// the same kind read; every row the MMAs read lies inside the planes and is
-// finite (the planes are zeroed once, the input rows past the region are
-// rewritten as zeros for every tile).  Persistent CTAs walk the tiles; each
-// layer's MMAs complete on an mbarrier (bounded wait).
-namespace fus {
-constexpr int TW = 32, TH = 16, RW = TW + 6, RH = TH + 6, R = RW * RH;
-constexpr int first_row(int L) { return L * RW + L; }
-constexpr int n_rows(int L) { return (RH - 2 * L) * RW - 2 * L; }
-constexpr int n_blocks(int L) { return (n_rows(L) + 127) / 128; }
-constexpr int PR = 896;                          // rows per plane
-constexpr int PLANE = PR * 16;
-// h1 in planes 0-1, h2 in planes 2-3; plane 2 holds the input entries until
-// layer 1's MMAs have completed
-constexpr int OFF_H1 = 0, OFF_H2 = 2 * PLANE, OFF_E = OFF_H2;
-constexpr int OFF_STAGE = 3 * PLANE;             // staged input of a tile, (RW + 2) x RH FP32 complex
-constexpr int SW = RW + 2, SR = SW * RH;
-constexpr int OFF_B = 4 * PLANE;                 // 20 weight operands of 16 x 16 (layer 1: 2, layers 2-3: 9 each)
-constexpr int OFF_BAR = OFF_B + 20 * 512;
-constexpr int SMEM = OFF_BAR + 64 + 128;
-constexpr int NT = 256;
-constexpr int CTAS_PER_SM = 3;
-constexpr int SPT = (SR + NT - 1) / NT;          // staged input values per thread
-constexpr int TMEM_COLS = 128;
-constexpr long long WAIT_LIMIT = 1ll << 26;
-static_assert(R <= PR, "region rows");
-static_assert(first_row(1) - RW >= 0, "input entries read before the plane");
-static_assert(first_row(1) + n_blocks(1) * 128 - 1 + 2 * RW < PR, "input entries read past the plane");
-static_assert(first_row(2) - RW - 1 >= 0 && first_row(3) - RW - 1 >= 0, "activations read before the plane");
-static_assert(first_row(2) + n_blocks(2) * 128 - 1 + RW + 1 < PR, "h1 read past the plane");
-static_assert(first_row(3) + n_blocks(3) * 128 - 1 + RW + 1 < PR, "h2 read past the plane");
-static_assert(first_row(1) + n_blocks(1) * 128 <= PR && first_row(2) + n_blocks(2) * 128 <= PR, "writes");
-static_assert(n_blocks(1) * 16 <= TMEM_COLS && n_blocks(2) * 16 <= TMEM_COLS && n_blocks(3) * 16 <= TMEM_COLS,
-              "tensor memory");
-static_assert(CTAS_PER_SM * TMEM_COLS <= 512, "tensor memory per SM");
-static_assert(SR * 8 <= PLANE, "staged input");
-static_assert((n_blocks(3) + 1) / 2 <= 3, "output pixels per thread");
-}  // namespace fus
+// ---- Inference: the three layers fused per output tile (net_tile.cuh).
+// Persistent CTAs walk the tiles of B patches; each loads the next tile's
+// input while the current tile's MMAs run.
+constexpr int NET_CTAS_PER_SM = 3;
+constexpr int NET_SMEM = nettile::PLANES_BYTES + nettile::WREG_BYTES + 128;
+static_assert(NET_CTAS_PER_SM * nettile::TMEM_COLS <= 512, "tensor memory per SM");
 
-// no-swizzle K-major descriptor: 16-byte rows, 8-row core matrices 128 bytes
-// apart, K groups lbo bytes apart
-__device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, uint32_t lbo) {
-  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)(128 >> 4) << 32) | ((uint64_t)1 << 46);
-}
-
-// two FP32 values to packed BF16 (lo in the low half), round to nearest even;
-// with ReLU folded into the conversion
-__device__ __forceinline__ uint32_t bf2_relu_free(float lo, float hi) {
-  uint32_t d;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
-}
-__device__ __forceinline__ uint32_t bf2_relu(uint32_t lo, uint32_t hi) {
-  uint32_t d;
-  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(__uint_as_float(hi)), "f"(__uint_as_float(lo)));
-  return d;
-}
-
-__device__ __forceinline__ void f_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred q;\nsetp.ne.b32 q, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ bool f_wait(uint32_t bar, uint32_t phase) {
-  for (long long it = 0; it < fus::WAIT_LIMIT; ++it) {
-    uint32_t d;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(d)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    if (d) return true;
-  }
-  return false;
+// tile t of B patches of H x W (tiles row-major within a patch)
+__device__ __forceinline__ nettile::Tile net_tile_of(const Geom& g, const float2* x, float2* y, int tiles_x,
+                                                     int tiles_y, long long t) {
+  const int tx = (int)(t % tiles_x);
+  const long long t2 = t / tiles_x;
+  const long long off = (t2 / tiles_y) * g.H * g.W;
+  return nettile::Tile{x + off, y + off, g.H, g.W, tx * nettile::TW - 3, (int)(t2 % tiles_y) * nettile::TH - 3};
 }
 
 // y = N(scale x) (accumulate: y += N(scale x)) over B patches of H x W
-__global__ void __launch_bounds__(fus::NT, fus::CTAS_PER_SM)
+__global__ void __launch_bounds__(nettile::NT, NET_CTAS_PER_SM)
     k_net_fused(Geom g, const float2* __restrict__ x, float scale, const __nv_bfloat16* __restrict__ wb,
                 float2* __restrict__ y, int accumulate, int* __restrict__ err) {
-  using namespace fus;
+  using namespace nettile;
   extern __shared__ __align__(128) unsigned char fsm_raw[];
-  unsigned char* base = fsm_raw + ((128 - (c_saddr(fsm_raw) & 127)) & 127);
-  const uint32_t sbase = c_saddr(base);
-  const uint32_t bar = sbase + OFF_BAR;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(base + OFF_BAR + 16);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quarter = warp & 3, half = warp >> 2;      // tensor-memory lanes 32 quarter.., blocks of parity half
+  unsigned char* base = fsm_raw + ((128 - (saddr(fsm_raw) & 127)) & 127);
+  Ctx c;
+  setup(c, base, base + PLANES_BYTES, wb);
+  zero_planes(c);
   const int tiles_x = (g.W + TW - 1) / TW, tiles_y = (g.H + TH - 1) / TH;
   const long long ntiles = (long long)g.B * tiles_x * tiles_y;
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(c_saddr(tslot)),
-                 "n"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  for (int i = tid; i < 4 * PLANE / 16; i += NT) reinterpret_cast<uint4*>(base)[i] = make_uint4(0, 0, 0, 0);
-  // weight operands: element (n, k) of operand t at (k / 8) 256 + (n / 8) 128 + (n % 8) 16 + (k % 8) 2
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int i = tid; i < 20 * 256; i += NT) {
-    const int t = i >> 8, n = (i >> 4) & 15, k = i & 15;
-    __nv_bfloat16 v = zero;
-    if (t < 2) {
-      // layer 1, K group (k / 8) of MMA t: filter row dy, entry e = 2 (dx + 1) + channel
-      const int grp = k >> 3, e = k & 7;
-      const int dy = (t == 0) ? grp - 1 : grp + 1;
-      if (e < 6 && dy <= 1) v = wb[(n * 2 + (e & 1)) * 9 + (dy + 1) * 3 + (e >> 1)];
-    } else if (t < 11) {
-      v = wb[NP1 + (n * 16 + k) * 9 + (t - 2)];
-    } else if (n < 2) {
-      v = wb[NP1 + NP2 + (n * 16 + k) * 9 + (t - 11)];
-    }
-    *reinterpret_cast<__nv_bfloat16*>(base + OFF_B + t * 512 + (k >> 3) * 256 + (n >> 3) * 128 + (n & 7) * 16 +
-                                      (k & 7) * 2) = v;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-  const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16);
-  uint32_t phase = 0;
-  bool ok = true;
-  // waits for the MMAs just committed; on a timeout the CTA records it, waits
-  // once more (bounded) for MMAs still in flight and leaves the tile loop
-  auto layer_done = [&]() -> bool {
-    const bool d = f_wait(bar, phase);
-    if (!__syncthreads_and(d ? 1 : 0)) {
-      if (tid == 0) atomicExch(err, 1);
-      f_wait(bar, phase);
-      return false;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return true;
-  };
-  auto commit = [&]() {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-  };
-  auto to_async = [&]() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-  };
-  // The input of a tile, x on the region widened by one column on each side
-  // ((RW + 2) x RH pixels, zero outside the patch), is loaded into registers
-  // one tile ahead and staged through plane 3 (free until layer 2's
-  // epilogue); the pixels this thread adds its output to are loaded when the
-  // tile starts.
   float2 xr[SPT];
-  auto tile_origin = [&](long long tile, int& bb, int& gx0, int& gy0) {
-    const int tx = (int)(tile % tiles_x);
-    const long long t2 = tile / tiles_x;
-    bb = (int)(t2 / tiles_y);
-    gx0 = tx * TW - 3;
-    gy0 = (int)(t2 % tiles_y) * TH - 3;
-  };
-  auto load_x = [&](long long tile) {
-    if (tile >= ntiles) return;
-    int bb, gx0, gy0;
-    tile_origin(tile, bb, gx0, gy0);
-    const float2* xb = x + (long long)bb * g.H * g.W;
-#pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-      const int i = tid + k * NT;
-      const int sy = i / SW, sx = i - sy * SW;
-      const int gy = gy0 + sy, gx = gx0 - 1 + sx;
-      xr[k] = (i < SR && gy >= 0 && gy < g.H && gx >= 0 && gx < g.W) ? xb[(long long)gy * g.W + gx]
-                                                                     : make_float2(0.f, 0.f);
-    }
-  };
-  float2 yv[3];
-  load_x(blockIdx.x);
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    int b, gx0, gy0;
-    tile_origin(tile, b, gx0, gy0);
-    float2* stage = reinterpret_cast<float2*>(base + OFF_STAGE);
-#pragma unroll
-    for (int k = 0; k < SPT; ++k)
-      if (tid + k * NT < SR) stage[tid + k * NT] = xr[k];
-    __syncthreads();
-    // input entries (zero past the region)
-    for (int p = tid; p < PR; p += NT) {
-      uint4 ev = make_uint4(0, 0, 0, 0);
-      if (p < R) {
-        const int ry = p / RW, rx = p - ry * RW;
-        const float2* sp = stage + ry * SW + rx;       // x(p - 1), x(p), x(p + 1)
-        ev.x = bf2_relu_free(sp[0].x * scale, sp[0].y * scale);
-        ev.y = bf2_relu_free(sp[1].x * scale, sp[1].y * scale);
-        ev.z = bf2_relu_free(sp[2].x * scale, sp[2].y * scale);
-      }
-      *reinterpret_cast<uint4*>(base + OFF_E + p * 16) = ev;
-    }
-    // this thread's output pixels, and the next tile's input
-    if (accumulate) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const int j = half + 2 * i;
-        const int p = first_row(3) + j * 128 + 32 * quarter + lane;
-        const int ry = p / RW, rx = p - ry * RW;
-        const int gy = gy0 + ry, gx = gx0 + rx;
-        yv[i] = (j < n_blocks(3) && rx >= 3 && rx < RW - 3 && ry >= 3 && ry < RH - 3 && gx < g.W && gy < g.H)
-                    ? y[((long long)b * g.H + gy) * g.W + gx]
-                    : make_float2(0.f, 0.f);
-      }
-    }
-    load_x(tile + gridDim.x);
-    to_async();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t bd = ns_desc(sbase + OFF_B, 256);
-      for (int j = 0; j < n_blocks(1); ++j) {
-        const uint64_t ad = ns_desc(sbase + OFF_E + (first_row(1) + j * 128 - RW) * 16, RW * 16);
-        f_mma(tmem + j * 16, ad, bd, idesc, 0);
-        f_mma(tmem + j * 16, ad + 2 * RW, bd + 32, idesc, 1);     // rows + 2 RW, weights + 512 bytes
-      }
-      commit();
-    }
-    if (!(ok = layer_done())) break;
-    // hidden layers' epilogue: ReLU and BF16 rounding in one conversion, zero
-    // outside the patch, into the two planes
-    auto hidden = [&](int L, int nb, int off) {
-      for (int j = half; j < nb; j += 2) {
-        uint32_t v[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tl + (uint32_t)(j * 16)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int p = first_row(L) + j * 128 + 32 * quarter + lane;
-        const int ry = p / RW, rx = p - ry * RW;
-        const int gy = gy0 + ry, gx = gx0 + rx;
-        const bool in = ry < RH && gy >= 0 && gy < g.H && gx >= 0 && gx < g.W;
-        uint4 lo = make_uint4(0, 0, 0, 0), hi = make_uint4(0, 0, 0, 0);
-        if (in) {
-          lo = make_uint4(bf2_relu(v[0], v[1]), bf2_relu(v[2], v[3]), bf2_relu(v[4], v[5]), bf2_relu(v[6], v[7]));
-          hi = make_uint4(bf2_relu(v[8], v[9]), bf2_relu(v[10], v[11]), bf2_relu(v[12], v[13]),
-                          bf2_relu(v[14], v[15]));
-        }
-        *reinterpret_cast<uint4*>(base + off + p * 16) = lo;
-        *reinterpret_cast<uint4*>(base + off + PLANE + p * 16) = hi;
-      }
-    };
-    // nine taps: the A descriptor of tap (a, b) is the block's by (a-1) RW + (b-1)
-    // rows (one unit of the 16-byte address field per row)
-    auto taps = [&](int L, int in_off, int b_off) {
-      const uint64_t bd0 = ns_desc(sbase + OFF_B + b_off, 256);
-      for (int j = 0; j < n_blocks(L); ++j) {
-        const uint64_t ad0 = ns_desc(sbase + in_off + (first_row(L) + j * 128 - RW - 1) * 16, PLANE);
-#pragma unroll
-        for (int t = 0; t < 9; ++t)
-          f_mma(tmem + j * 16, ad0 + (uint64_t)((t / 3) * RW + (t % 3)), bd0 + (uint64_t)(t * 32), idesc,
-                t > 0 ? 1u : 0u);
-      }
-      commit();
-    };
-    hidden(1, n_blocks(1), OFF_H1);
-    to_async();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      taps(2, OFF_H1, 2 * 512);
-    }
-    if (!(ok = layer_done())) break;
-    hidden(2, n_blocks(2), OFF_H2);
-    to_async();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      taps(3, OFF_H2, 11 * 512);
-    }
-    if (!(ok = layer_done())) break;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const int j = half + 2 * i;
-      if (j >= n_blocks(3)) break;
-      uint32_t v0, v1;
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-                   : "=r"(v0), "=r"(v1)
-                   : "r"(tl + (uint32_t)(j * 16)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int p = first_row(3) + j * 128 + 32 * quarter + lane;
-      const int ry = p / RW, rx = p - ry * RW;
-      const int gy = gy0 + ry, gx = gx0 + rx;
-      if (rx >= 3 && rx < RW - 3 && ry >= 3 && ry < RH - 3 && gx < g.W && gy < g.H) {
-        const long long idx = ((long long)b * g.H + gy) * g.W + gx;
-        const float a0 = __uint_as_float(v0), a1 = __uint_as_float(v1);
-        y[idx] = accumulate ? make_float2(yv[i].x + a0, yv[i].y + a1) : make_float2(a0, a1);
-      }
-    }
-    // tensor memory and the planes are reused by the next tile
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  Tile cur = net_tile_of(g, x, y, tiles_x, tiles_y, blockIdx.x);
+  if (blockIdx.x < ntiles) load_x(cur, xr);
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long nt = t + gridDim.x;
+    const Tile next = net_tile_of(g, x, y, tiles_x, tiles_y, nt < ntiles ? nt : t);
+    if (!run_tile(c, cur, xr, scale, accumulate, err, nt < ntiles ? &next : nullptr)) break;
+    cur = next;
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
+  teardown(c);
 }
 
 __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
@@ -889,12 +606,13 @@ csff_status forward(csff_net* N, csff::Geom g, const float2* r, float scale, flo
                     cudaStream_t s) {
   using namespace csff;
   const long long np = g.npix();
-  const long long ntiles = (long long)g.B * ((g.W + fus::TW - 1) / fus::TW) * ((g.H + fus::TH - 1) / fus::TH);
-  NK(cudaFuncSetAttribute(k_net_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, fus::SMEM), "net attribute");
-  const unsigned grid = (unsigned)std::min<long long>(ntiles, 152 * fus::CTAS_PER_SM);
+  const long long ntiles =
+      (long long)g.B * ((g.W + nettile::TW - 1) / nettile::TW) * ((g.H + nettile::TH - 1) / nettile::TH);
+  NK(cudaFuncSetAttribute(k_net_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, NET_SMEM), "net attribute");
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, 152 * NET_CTAS_PER_SM);
   {
     ProfScope ps(PF_MG32, s, (accumulate ? 24.0 : 16.0) * np, 2.0 * 9 * (2 * 16 + 16 * 16 + 16 * 2) * np);
-    k_net_fused<<<grid, fus::NT, fus::SMEM, s>>>(g, r, scale, N->wb, y, accumulate, N->tcerr);
+    k_net_fused<<<grid, nettile::NT, NET_SMEM, s>>>(g, r, scale, N->wb, y, accumulate, N->tcerr);
   }
   count_launch();
   NK(cudaGetLastError(), "net forward");
@@ -1047,6 +765,8 @@ csff_status csff_net_train_step(csff_net* N, int B, int H, int W, const void* r_
 namespace csff {
 
 // scratch for a single patch of npix pixels (reserved before graph capture)
+const void* net_weights_bf16(const csff_net* N) { return N->wb; }
+
 // inference keeps its activations in shared memory: nothing to allocate, only
 // the pixel limit of the kernels' 32-bit patch indexing to check
 csff_status net_reserve(csff_net* N, long long npix) {
