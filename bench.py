@@ -886,6 +886,65 @@ def measure_learned(csff, torch, dev, stream, flush):
     out["forward_ms_2047sq"] = _time_events(torch, stream, lambda: netf.forward(r, y, stream=stream), flush, 5)
     netf.close()
     out["small_grid_129"] = measure_learned_small(csff, torch, dev, stream)
+    out["3d_257_k6"] = measure_learned_3d(csff, torch, dev, stream, flush)
+    return out
+
+
+def measure_learned_3d(csff, torch, dev, stream, flush):
+    """The 3D learned smoother on the 257^3 grid of the 3D workload at k = 6
+    (k h = 0.70 on the finest level), both solves inside the FP64 refinement
+    with three FP32 cycles a step: plain red-black V(1,1) against red-black +
+    learned step u += N(h^2 r) (3x3x3 network on the CUDA cores) on the finest
+    level.  The network is trained on the GPU on residual windows (16^3, at
+    least a fifth of their energy inside the loss's 12^3 core) of 65^3 problems
+    with the same grid spacing and wavenumber (box [-3.75, 3.75]^3, k = 6),
+    chi and the incident direction drawn from the batch ranges, 32 seeded
+    solves."""
+    from paper_1211_4461_gb300 import learned as LR
+    import math as _m
+    opts = {"smoother": "rbgs", "omega": 1.0, "nu1": 1, "nu2": 1, "coarsest_n": 5, "rel_tol": 1e-8,
+            "max_cycles": 400, "inner_cycles": 3}
+    probs = []
+    for seed in range(32):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        amp = float(rng.uniform(-2.0, -0.2))
+        w = float(rng.uniform(1.0, 6.0))
+        th, ph = float(rng.uniform(0, _m.pi)), float(rng.uniform(0, 2 * _m.pi))
+        probs.append((W.problem(3, 65, 3.75, _m.pi / 6, 6.0, [W.gauss(amp, w)]),
+                      np.array([_m.sin(th) * _m.cos(ph), _m.sin(th) * _m.sin(ph), _m.cos(th)])))
+    t0 = time.perf_counter()
+    data = LR.collect_patches(probs, opts, n_cycles=4, patch=16, per_field=8, seed=1, core_margin=2, min_core=0.2)
+    net = csff.Net(LR.init_weights(7, dim=3), dim=3)
+    hist = LR.train(net, data, steps=600, batch=8, lr=3e-4, margin=2, seed=2)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    c = W.big_3d(n=257, n_rhs=1)
+    c["problem"]["k"] = 6.0
+    plan = csff.Plan(c["problem"], dict(c["opts"], precision="mixed", refine_fp64=1, inner_cycles=3),
+                     stream=stream)
+    u = torch.zeros(plan.N, dtype=torch.complex128, device=dev)
+    info = {}
+
+    def step():
+        _, inf = plan.solve(c["eta"], u)
+        info["inf"] = inf[0]
+
+    out = {"train": {"solves": 32, "patches": int(data[0].shape[0]), "steps": 600, "train_s": train_s,
+                     "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:]))}}
+    for name, learned in (("classical", False), ("learned", True)):
+        plan.set_learned(net if learned else None, levels=1)
+        step()
+        ms = _time_events(torch, stream, step, flush, 1)
+        out[name] = {"value": 1.0 / (ms / 1e3), "unit": UNIT, "ms_per_solve": ms, "cycles": info["inf"]["cycles"],
+                     "rel_res": info["inf"]["rel_res"], "flags": info["inf"]["flags"]}
+    r = torch.randn(plan.N, dtype=torch.complex64, device=dev).view(1, 255, 255, 255)
+    y = torch.empty_like(r)
+    out["forward_ms_255cube"] = _time_events(torch, stream, lambda: net.forward(r, y, stream=stream), flush, 2)
+    out["speedup_learned_vs_classical"] = out["classical"]["ms_per_solve"] / out["learned"]["ms_per_solve"]
+    out["note"] = ("solve only (the far field is the same for both); the 3x3x3 network's forward pass runs "
+                   "on the CUDA cores")
+    plan.close()
+    net.close()
     return out
 
 

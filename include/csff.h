@@ -344,8 +344,8 @@ csff_status csff_vcycle(csff_plan* plan, int arith, void* u_dev, const void* b_d
 /* ---- learned smoother --------------------------------------------------
    Not in the paper: a bias-free 3x3 convolutional network N (2 -> 16 -> 16 ->
    2 channels, ReLU between layers) on the two real channels of a residual,
-   used as u <- u + N(b - A u) after each red-black sweep of the FP32 cycles on
-   the finest levels.  Weights and activations BF16, FP32 accumulation, FP32
+   used as u <- u + N(h^2 (b - A u)) after each red-black sweep of the FP32
+   cycles on the finest levels.  Weights and activations BF16, FP32 accumulation, FP32
    master weights.  Weight layout: flat (out, in, a, b) per layer, layers 1, 2,
    3 (288 + 2304 + 288 = 2880 values).  Convolutions are 3x3
    cross-correlations with zero padding.  Training (all on the GPU): loss
@@ -368,10 +368,26 @@ csff_status csff_net_loss_grad(csff_net* net, int B, int H, int W, const void* r
 /* One Adam step on a batch (loss before the step in *loss_host if non-NULL). */
 csff_status csff_net_train_step(csff_net* net, int B, int H, int W, const void* r_dev, const void* q_dev,
                                 const double* c_host, int margin, float lr, float* loss_host, void* stream);
+/* The 3D network: the same three layers with 3x3x3 cross-correlations
+   (out[o][z][y][x] = sum_c sum_{a,b,e} w[o][c][a][b][e] x[c][z+a-1][y+b-1][x+e-1],
+   zero padding), weights flat (out, in, a, b, e): 864 + 6912 + 864 = 8640
+   values; its loss takes the 7-point operator A y = c (6 y - sum_nbr y) - q y.
+   Patches [B][Z][H][W], c64.  Same precision and training as the 2D network;
+   csff_net_set_weights, _get_weights and _destroy serve both.  A network of
+   one dimension is refused (CSFF_ERR_INVALID_ARG) by the other dimension's
+   calls and by plans of the other dimension. */
+int csff_net_num_params3(void);
+csff_status csff_net_create3(const float* w_host, csff_net** out);
+csff_status csff_net_forward3(csff_net* net, int B, int Z, int H, int W, const void* r_dev, void* y_dev, void* stream);
+csff_status csff_net_loss_grad3(csff_net* net, int B, int Z, int H, int W, const void* r_dev, const void* q_dev,
+                                const double* c_host, int margin, float* loss_host, float* grad_host, void* stream);
+csff_status csff_net_train_step3(csff_net* net, int B, int Z, int H, int W, const void* r_dev, const void* q_dev,
+                                 const double* c_host, int margin, float lr, float* loss_host, void* stream);
 /* Attach (net != NULL) or detach the learned step on levels 0..levels-1 of a
-   red-black plan's FP32 cycles (mixed-precision solves): after the red-black
-   pre-sweep, u <- u + N(h_l^2 r) with r the level's residual (so the network
-   sees the operator in units of h^2, O(1) on every grid).  The first two
+   red-black plan's FP32 cycles (mixed-precision solves): after each red-black
+   sweep, u <- u + N(h_l^2 r) with r the level's residual (so the network sees
+   the operator in units of h^2, O(1) on every grid); 2D plans take a 2D
+   network, 3D plans a 3D one.  The first two
    refinement steps of each solve run plain red-black sweeps; the second sets
    the reference reduction factor f = min(its factor, guard); a later learned step
    that reduces the residual by less than f turns the learned step off for the

@@ -118,6 +118,11 @@ _SIGS = {
     "csff_batch_debug_barrier": (_i, [_vp, _i, C.c_longlong]),
     "csff_batch_set_tiles": (_i, [_vp, _i, _i]),
     "csff_batch_set_learned": (_i, [_vp, _vp, _d]),
+    "csff_net_num_params3": (_i, []),
+    "csff_net_create3": (_i, [_fp, C.POINTER(_vp)]),
+    "csff_net_forward3": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "csff_net_loss_grad3": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _dp, _i, _fp, _fp, _vp]),
+    "csff_net_train_step3": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _dp, _i, C.c_float, _fp, _vp]),
     "csff_net_num_params": (_i, []),
     "csff_net_create": (_i, [_fp, C.POINTER(_vp)]),
     "csff_net_destroy": (None, [_vp]),
@@ -322,15 +327,23 @@ class Batch:
 
 class Net:
     """The learned smoother's network on the GPU (csff_net_*).  Weights are a
-    flat FP32 vector of 2880 values, (out, in, a, b) per layer."""
+    flat FP32 vector, (out, in, taps) per layer: 2880 values for the 2D
+    network (dim=2, 3x3), 8640 for the 3D one (dim=3, 3x3x3)."""
 
-    def __init__(self, weights):
+    def __init__(self, weights, dim=2):
+        if dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        self.dim = dim
         w = np.ascontiguousarray(weights, dtype=np.float32)
-        if w.size != _lib.csff_net_num_params():
-            raise ValueError("need %d weights" % _lib.csff_net_num_params())
+        if w.size != self._n_params():
+            raise ValueError("need %d weights" % self._n_params())
         h = C.c_void_p()
-        _check(_lib.csff_net_create(w.ctypes.data_as(_fp), C.byref(h)), "net_create")
+        create = _lib.csff_net_create if dim == 2 else _lib.csff_net_create3
+        _check(create(w.ctypes.data_as(_fp), C.byref(h)), "net_create")
         self._h = h
+
+    def _n_params(self):
+        return _lib.csff_net_num_params() if self.dim == 2 else _lib.csff_net_num_params3()
 
     def close(self):
         if getattr(self, "_h", None):
@@ -345,7 +358,7 @@ class Net:
 
     @property
     def weights(self):
-        w = np.empty(_lib.csff_net_num_params(), np.float32)
+        w = np.empty(self._n_params(), np.float32)
         _check(_lib.csff_net_get_weights(self._h, w.ctypes.data_as(_fp)), "net_get_weights")
         return w
 
@@ -354,25 +367,40 @@ class Net:
         _check(_lib.csff_net_set_weights(self._h, w.ctypes.data_as(_fp)), "net_set_weights")
 
     def forward(self, r, y, stream=None):
-        """r, y: complex64 CUDA tensors of shape (B, H, W)."""
-        B, H, W = r.shape
-        _check(_lib.csff_net_forward(self._h, B, H, W, _ptr(r), _ptr(y), _stream_handle(stream)), "net_forward")
+        """r, y: complex64 CUDA tensors of shape (B, H, W) (2D) or (B, Z, H, W) (3D)."""
+        if self.dim == 2:
+            B, H, W = r.shape
+            _check(_lib.csff_net_forward(self._h, B, H, W, _ptr(r), _ptr(y), _stream_handle(stream)), "net_forward")
+        else:
+            B, Z, H, W = r.shape
+            _check(_lib.csff_net_forward3(self._h, B, Z, H, W, _ptr(r), _ptr(y), _stream_handle(stream)),
+                   "net_forward3")
 
     def loss_grad(self, r, q, c, margin=4, stream=None):
-        B, H, W = r.shape
         cc, cp = _dbl(np.stack([np.real(c), np.imag(c)], axis=1).ravel())
         loss = C.c_float()
-        g = np.empty(_lib.csff_net_num_params(), np.float32)
-        _check(_lib.csff_net_loss_grad(self._h, B, H, W, _ptr(r), _ptr(q), cp, int(margin), C.byref(loss),
-                                       g.ctypes.data_as(_fp), _stream_handle(stream)), "net_loss_grad")
+        g = np.empty(self._n_params(), np.float32)
+        if self.dim == 2:
+            B, H, W = r.shape
+            _check(_lib.csff_net_loss_grad(self._h, B, H, W, _ptr(r), _ptr(q), cp, int(margin), C.byref(loss),
+                                           g.ctypes.data_as(_fp), _stream_handle(stream)), "net_loss_grad")
+        else:
+            B, Z, H, W = r.shape
+            _check(_lib.csff_net_loss_grad3(self._h, B, Z, H, W, _ptr(r), _ptr(q), cp, int(margin), C.byref(loss),
+                                            g.ctypes.data_as(_fp), _stream_handle(stream)), "net_loss_grad3")
         return loss.value, g
 
     def train_step(self, r, q, c, lr, margin=4, stream=None):
-        B, H, W = r.shape
         cc, cp = _dbl(np.stack([np.real(c), np.imag(c)], axis=1).ravel())
         loss = C.c_float()
-        _check(_lib.csff_net_train_step(self._h, B, H, W, _ptr(r), _ptr(q), cp, int(margin), float(lr),
-                                        C.byref(loss), _stream_handle(stream)), "net_train_step")
+        if self.dim == 2:
+            B, H, W = r.shape
+            _check(_lib.csff_net_train_step(self._h, B, H, W, _ptr(r), _ptr(q), cp, int(margin), float(lr),
+                                            C.byref(loss), _stream_handle(stream)), "net_train_step")
+        else:
+            B, Z, H, W = r.shape
+            _check(_lib.csff_net_train_step3(self._h, B, Z, H, W, _ptr(r), _ptr(q), cp, int(margin), float(lr),
+                                             C.byref(loss), _stream_handle(stream)), "net_train_step3")
         return loss.value
 
 

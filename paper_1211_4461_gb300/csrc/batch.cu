@@ -944,6 +944,7 @@ csff_status csff_batch_debug_barrier(csff_batch* B, int extra_arrivals, long lon
 csff_status csff_batch_set_learned(csff_batch* B, csff_net* net, double guard) {
   if (!B) return binvalid("NULL batch");
   if (net && !(guard > 0.0)) return binvalid("guard must be positive");
+  if (net && csff::net_dim(net) != 2) return binvalid("batched solve: needs a 2D network");
   B->net = net;
   B->guard = guard;
   if (net) {

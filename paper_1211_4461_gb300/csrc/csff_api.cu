@@ -937,6 +937,7 @@ csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, doubl
     csff::set_error("the learned step follows red-black sweeps");
     return CSFF_ERR_UNSUPPORTED;
   }
+  if (net && csff::net_dim(net) != P->dim) return invalid("the network's dimension is not the plan's");
   if (net) CS(csff::net_reserve(net, P->lv[0].N));
   P->net = net;
   P->learned_levels = net ? levels : 0;
@@ -949,6 +950,7 @@ csff_status csff_plan_set_learned(csff_plan* P, csff_net* net, int levels, doubl
 csff_status csff_plan_set_learned_level(csff_plan* P, int level, csff_net* net) {
   if (!P) return invalid("plan is NULL");
   if (!P->net || level < 0 || level >= P->learned_levels) return invalid("level carries no learned step");
+  if (net && csff::net_dim(net) != P->dim) return invalid("the network's dimension is not the plan's");
   if (net) CS(csff::net_reserve(net, P->lv[level].N));
   P->level_net[level] = net;
   destroy_graphs(P);

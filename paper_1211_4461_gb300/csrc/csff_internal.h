@@ -329,6 +329,7 @@ csff_status learned_step(csff_plan* P, int level, int dim, const Level& L, float
 csff_status net_reserve(csff_net* N, long long npix);
 csff_status net_check(csff_net* N);
 const void* net_weights_bf16(const csff_net* N);   // the network's BF16 weights on the device
+int net_dim(const csff_net* N);                    // 2 or 3
 
 // ---- far field (farfield.cu) -----------------------------------------------
 void free_ff_buffers(csff_plan* P);

@@ -506,6 +506,337 @@ __global__ void __launch_bounds__(nettile::NT, NET_CTAS_PER_SM)
   teardown(c);
 }
 
+
+// ---- The 3D network: 3x3x3 cross-correlations, the same channels (2 -> 16 ->
+// 16 -> 2), on the CUDA cores with the 2D network's precision (BF16 weights and
+// activations, FP32 accumulation).  Patches [B][Z][H][W]; weights (out, in, a,
+// b, e), tap t = 9 a + 3 b + e reading x[z + a - 1][y + b - 1][x + e - 1].
+constexpr int T3 = 27;
+constexpr int NP31 = 16 * 2 * T3, NP32 = 16 * 16 * T3, NP33 = 2 * 16 * T3;
+constexpr int NPARAM3 = NP31 + NP32 + NP33;
+
+struct Geom3 {
+  int B, Z, H, W;
+  __host__ __device__ __forceinline__ long long npix() const { return (long long)B * Z * H * W; }
+};
+struct Vox { int z, y, x; };
+// coordinates of voxel p inside its patch (32-bit: B Z H W < 2^31)
+__device__ __forceinline__ Vox vox_of(const Geom3& g, long long p) {
+  const int q = (int)p;
+  const int t = q / g.W, x = q - t * g.W;
+  const int t2 = t / g.H, y = t - t2 * g.H;
+  return Vox{t2 % g.Z, y, x};
+}
+// neighbour (z + a - 1, y + b - 1, x + e - 1) of voxel p (at v), or -1
+__device__ __forceinline__ long long nbr3(const Geom3& g, Vox v, long long p, int a, int b, int e) {
+  const int zz = v.z + a - 1, yy = v.y + b - 1, xx = v.x + e - 1;
+  if (zz < 0 || zz >= g.Z || yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) return -1;
+  return p + ((long long)(a - 1) * g.H + (b - 1)) * g.W + (e - 1);
+}
+
+__device__ __forceinline__ void unpack16(const __nv_bfloat16* src, float* x) {
+  const uint4 a = reinterpret_cast<const uint4*>(src)[0], b = reinterpret_cast<const uint4*>(src)[1];
+  const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&a);
+  const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&b);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 fa = __bfloat1622float2(pa[i]), fb = __bfloat1622float2(pb[i]);
+    x[2 * i] = fa.x;
+    x[2 * i + 1] = fa.y;
+    x[8 + 2 * i] = fb.x;
+    x[8 + 2 * i + 1] = fb.y;
+  }
+}
+__device__ __forceinline__ void store16_relu(__nv_bfloat16* dst, const float* acc) {
+  __align__(16) __nv_bfloat16 hv[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) hv[o] = __float2bfloat16(fmaxf(acc[o], 0.f));
+  reinterpret_cast<uint4*>(dst)[0] = *reinterpret_cast<const uint4*>(hv);
+  reinterpret_cast<uint4*>(dst)[1] = *reinterpret_cast<const uint4*>(hv + 8);
+}
+
+// layer 1: x0 = bf16(scale r) -> h1 = bf16(relu(conv)); weights in shared
+// memory as [tap][in][out]
+__global__ void k3_conv1(Geom3 g, const float2* __restrict__ r, float scale, const __nv_bfloat16* __restrict__ w1,
+                         __nv_bfloat16* __restrict__ h1) {
+  __shared__ __align__(16) float ws[T3][2][16];
+  for (int i = threadIdx.x; i < NP31; i += blockDim.x) {
+    const int o = i / (2 * T3), c = (i / T3) % 2, t = i % T3;
+    ws[t][c][o] = __bfloat162float(w1[i]);
+  }
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const Vox v = vox_of(g, p);
+  float acc[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) acc[o] = 0.f;
+  for (int t = 0; t < T3; ++t) {
+    const long long q = nbr3(g, v, p, t / 9, (t / 3) % 3, t % 3);
+    if (q < 0) continue;
+    const float2 rv = r[q];
+    const float x[2] = {bf(rv.x * scale), bf(rv.y * scale)};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float4* wv = reinterpret_cast<const float4*>(&ws[t][c][0]);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 w = wv[q4];
+        acc[4 * q4 + 0] = fmaf(w.x, x[c], acc[4 * q4 + 0]);
+        acc[4 * q4 + 1] = fmaf(w.y, x[c], acc[4 * q4 + 1]);
+        acc[4 * q4 + 2] = fmaf(w.z, x[c], acc[4 * q4 + 2]);
+        acc[4 * q4 + 3] = fmaf(w.w, x[c], acc[4 * q4 + 3]);
+      }
+    }
+  }
+  store16_relu(h1 + p * 16, acc);
+}
+
+// layer 2: h1 -> h2 = bf16(relu(conv)); weights [tap][in][out] (27.6 KB)
+__global__ void k3_conv2(Geom3 g, const __nv_bfloat16* __restrict__ h1, const __nv_bfloat16* __restrict__ w2,
+                         __nv_bfloat16* __restrict__ h2) {
+  __shared__ __align__(16) float ws[T3][16][16];
+  for (int i = threadIdx.x; i < NP32; i += blockDim.x) {
+    const int o = i / (16 * T3), c = (i / T3) % 16, t = i % T3;
+    ws[t][c][o] = __bfloat162float(w2[i]);
+  }
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const Vox v = vox_of(g, p);
+  float acc[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) acc[o] = 0.f;
+  for (int t = 0; t < T3; ++t) {
+    const long long q = nbr3(g, v, p, t / 9, (t / 3) % 3, t % 3);
+    if (q < 0) continue;
+    float x[16];
+    unpack16(h1 + q * 16, x);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float4* wv = reinterpret_cast<const float4*>(&ws[t][c][0]);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 w = wv[q4];
+        acc[4 * q4 + 0] = fmaf(w.x, x[c], acc[4 * q4 + 0]);
+        acc[4 * q4 + 1] = fmaf(w.y, x[c], acc[4 * q4 + 1]);
+        acc[4 * q4 + 2] = fmaf(w.z, x[c], acc[4 * q4 + 2]);
+        acc[4 * q4 + 3] = fmaf(w.w, x[c], acc[4 * q4 + 3]);
+      }
+    }
+  }
+  store16_relu(h2 + p * 16, acc);
+}
+
+// layer 3: h2 -> y (2 channels, FP32; accumulate: y += conv); weights [tap][in][out]
+__global__ void k3_conv3(Geom3 g, const __nv_bfloat16* __restrict__ h2, const __nv_bfloat16* __restrict__ w3,
+                         float2* __restrict__ y, int accumulate) {
+  __shared__ __align__(16) float2 ws[T3][16];
+  for (int i = threadIdx.x; i < NP33; i += blockDim.x) {
+    const int o = i / (16 * T3), c = (i / T3) % 16, t = i % T3;
+    float* wf = reinterpret_cast<float*>(&ws[t][c]);
+    wf[o] = __bfloat162float(w3[i]);
+  }
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const Vox v = vox_of(g, p);
+  float a0 = 0.f, a1 = 0.f;
+  for (int t = 0; t < T3; ++t) {
+    const long long q = nbr3(g, v, p, t / 9, (t / 3) % 3, t % 3);
+    if (q < 0) continue;
+    float x[16];
+    unpack16(h2 + q * 16, x);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float2 w = ws[t][c];
+      a0 = fmaf(w.x, x[c], a0);
+      a1 = fmaf(w.y, x[c], a1);
+    }
+  }
+  if (accumulate) {
+    const float2 u = y[p];
+    y[p] = make_float2(u.x + a0, u.y + a1);
+  } else {
+    y[p] = make_float2(a0, a1);
+  }
+}
+
+// ---- 3D loss: E = mask (r - A y) with the 7-point operator
+__device__ __forceinline__ bool in_mask3(const Geom3& g, Vox v, int margin) {
+  return v.z >= margin && v.z < g.Z - margin && v.y >= margin && v.y < g.H - margin && v.x >= margin &&
+         v.x < g.W - margin;
+}
+
+__device__ __forceinline__ float2 apply_A3(const Geom3& g, const float2* f, long long p, float2 q, float2 c,
+                                           bool conj_in) {
+  const Vox v = vox_of(g, p);
+  auto ld = [&](long long k) {
+    const float2 x = f[k];
+    return conj_in ? make_float2(x.x, -x.y) : x;
+  };
+  float2 sn = make_float2(0.f, 0.f);
+  const int ax[6][3] = {{0, 1, 1}, {2, 1, 1}, {1, 0, 1}, {1, 2, 1}, {1, 1, 0}, {1, 1, 2}};
+#pragma unroll
+  for (int n = 0; n < 6; ++n) {
+    const long long k = nbr3(g, v, p, ax[n][0], ax[n][1], ax[n][2]);
+    if (k >= 0) sn = cadd(sn, ld(k));
+  }
+  const float2 vj = ld(p);
+  return csub(cmul(c, csub(cscale(vj, 6.f), sn)), cmul(q, vj));
+}
+
+__global__ void k3_loss1(Geom3 g, const float2* __restrict__ y, const float2* __restrict__ r,
+                         const float2* __restrict__ q, const float2* __restrict__ cpatch, int margin,
+                         float2* __restrict__ E, double* __restrict__ sums) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const int bpatch = (int)(p / ((long long)g.Z * g.H * g.W));
+  float2 e = make_float2(0.f, 0.f);
+  if (in_mask3(g, vox_of(g, p), margin)) {
+    const float2 rv = r[p];
+    e = csub(rv, apply_A3(g, y, p, q[p], cpatch[bpatch], false));
+    atomicAdd(&sums[2 * bpatch + 0], (double)e.x * e.x + (double)e.y * e.y);
+    atomicAdd(&sums[2 * bpatch + 1], (double)rv.x * rv.x + (double)rv.y * rv.y);
+  }
+  E[p] = e;
+}
+
+// dy = -conj(A conj(G)), G = 2 E / (S_r B)
+__global__ void k3_loss2(Geom3 g, const float2* __restrict__ E, const double* __restrict__ sums,
+                         const float2* __restrict__ q, const float2* __restrict__ cpatch, float2* __restrict__ G,
+                         float2* __restrict__ dy, int phase) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const int bpatch = (int)(p / ((long long)g.Z * g.H * g.W));
+  if (phase == 0) {
+    const double sr = sums[2 * bpatch + 1];
+    const float sc = sr > 0 ? (float)(2.0 / (sr * g.B)) : 0.f;
+    G[p] = cscale(E[p], sc);
+  } else {
+    const float2 a = apply_A3(g, G, p, q[p], cpatch[bpatch], true);
+    dy[p] = make_float2(-a.x, a.y);
+  }
+}
+
+// input gradients: dh2[c] = sum_o sum_t w3[o][c][t] dy[o](p - (t - 1)) masked by
+// h2 > 0; dh1 likewise from dh2 and w2, masked by h1 > 0
+__global__ void k3_bwd3(Geom3 g, const float2* __restrict__ dy, const __nv_bfloat16* __restrict__ w3,
+                        const __nv_bfloat16* __restrict__ h2, float* __restrict__ dh2) {
+  __shared__ float ws[NP33];
+  for (int i = threadIdx.x; i < NP33; i += blockDim.x) ws[i] = __bfloat162float(w3[i]);
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const Vox v = vox_of(g, p);
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+  for (int t = 0; t < T3; ++t) {
+    const long long q = nbr3(g, v, p, 2 - t / 9, 2 - (t / 3) % 3, 2 - t % 3);
+    if (q < 0) continue;
+    const float2 d = dy[q];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = fmaf(ws[(0 * 16 + c) * T3 + t], d.x, fmaf(ws[(1 * 16 + c) * T3 + t], d.y, acc[c]));
+  }
+  float hv[16];
+  unpack16(h2 + p * 16, hv);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) dh2[p * 16 + c] = hv[c] > 0.f ? acc[c] : 0.f;
+}
+
+__global__ void k3_bwd2(Geom3 g, const float* __restrict__ dh2, const __nv_bfloat16* __restrict__ w2,
+                        const __nv_bfloat16* __restrict__ h1, float* __restrict__ dh1) {
+  __shared__ __align__(16) float ws[T3][16][16];      // [tap][out][in]
+  for (int i = threadIdx.x; i < NP32; i += blockDim.x) {
+    const int o = i / (16 * T3), c = (i / T3) % 16, t = i % T3;
+    ws[t][o][c] = __bfloat162float(w2[i]);
+  }
+  __syncthreads();
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= g.npix()) return;
+  const Vox v = vox_of(g, p);
+  float acc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+  for (int t = 0; t < T3; ++t) {
+    const long long q = nbr3(g, v, p, 2 - t / 9, 2 - (t / 3) % 3, 2 - t % 3);
+    if (q < 0) continue;
+    const float4* d4 = reinterpret_cast<const float4*>(dh2 + q * 16);
+    float d[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 x = d4[i];
+      d[4 * i] = x.x; d[4 * i + 1] = x.y; d[4 * i + 2] = x.z; d[4 * i + 3] = x.w;
+    }
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+      const float4* wv = reinterpret_cast<const float4*>(&ws[t][o][0]);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const float4 w = wv[q4];
+        acc[4 * q4 + 0] = fmaf(w.x, d[o], acc[4 * q4 + 0]);
+        acc[4 * q4 + 1] = fmaf(w.y, d[o], acc[4 * q4 + 1]);
+        acc[4 * q4 + 2] = fmaf(w.z, d[o], acc[4 * q4 + 2]);
+        acc[4 * q4 + 3] = fmaf(w.w, d[o], acc[4 * q4 + 3]);
+      }
+    }
+  }
+  float hv[16];
+  unpack16(h1 + p * 16, hv);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) dh1[p * 16 + c] = hv[c] > 0.f ? acc[c] : 0.f;
+}
+
+// weight gradient: dw[o][c][t] += sum_p dout[p][o] in[c](p + (t - 1)).
+// INKIND 0: input is bf16(scale r) (2 channels from float2); 1: bf16
+// activations.  DKIND 0: dout is float2; 1: float[16].  A block takes 128
+// voxels, their coordinates and dout staged in shared memory.
+template <int CIN, int COUT, int INKIND, int DKIND>
+__global__ void k3_wgrad(Geom3 g, const void* __restrict__ in, const void* __restrict__ dout, float* __restrict__ dw) {
+  constexpr int NPAR = COUT * CIN * T3;
+  constexpr int TP = 128;
+  __shared__ float sd[TP * COUT];
+  __shared__ Vox sv[TP];
+  const long long p0 = (long long)blockIdx.x * TP;
+  for (int i = threadIdx.x; i < TP * COUT; i += blockDim.x) {
+    const long long p = p0 + i / COUT;
+    const int o = i % COUT;
+    float v = 0.f;
+    if (p < g.npix()) {
+      if (DKIND == 0) {
+        const float2 d = reinterpret_cast<const float2*>(dout)[p];
+        v = (o == 0) ? d.x : d.y;
+      } else {
+        v = reinterpret_cast<const float*>(dout)[p * COUT + o];
+      }
+    }
+    sd[i] = v;
+  }
+  for (int i = threadIdx.x; i < TP; i += blockDim.x)
+    if (p0 + i < g.npix()) sv[i] = vox_of(g, p0 + i);
+  __syncthreads();
+  const int np = (int)min((long long)TP, g.npix() - p0);
+  for (int par = threadIdx.x; par < NPAR; par += blockDim.x) {
+    const int o = par / (CIN * T3), rem = par % (CIN * T3), c = rem / T3, t = rem % T3;
+    const int a = t / 9, b = (t / 3) % 3, e = t % 3;
+    float acc = 0.f;
+    for (int k = 0; k < np; ++k) {
+      const long long q = nbr3(g, sv[k], p0 + k, a, b, e);
+      if (q < 0) continue;
+      float x;
+      if (INKIND == 0) {
+        const float2 v = reinterpret_cast<const float2*>(in)[q];
+        x = bf(c == 0 ? v.x : v.y);
+      } else {
+        x = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(in)[q * CIN + c]);
+      }
+      acc = fmaf(sd[k * COUT + o], x, acc);
+    }
+    atomicAdd(&dw[par], acc);
+  }
+}
+
 __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) wb[i] = __float2bfloat16(w[i]);
@@ -517,7 +848,9 @@ inline int nblk(long long n) { return (int)((n + NTH - 1) / NTH); }
 }  // namespace csff
 
 struct csff_net {
-  float* w = nullptr;            // FP32 master [NPARAM]
+  int dim = 2;                   // 2: 3x3 network, 3: 3x3x3 network
+  int nparam = csff::NPARAM;
+  float* w = nullptr;            // FP32 master [nparam]
   float* m = nullptr;            // Adam moments
   float* v = nullptr;
   float* grad = nullptr;
@@ -619,6 +952,75 @@ csff_status forward(csff_net* N, csff::Geom g, const float2* r, float scale, flo
   return CSFF_OK;
 }
 
+// the 3D network layer by layer, the activations kept in the scratch:
+// y = N(scale r) (accumulate: y += N(scale r))
+csff_status forward3(csff_net* N, csff::Geom3 g, const float2* r, float scale, float2* y, int accumulate,
+                     cudaStream_t s) {
+  using namespace csff;
+  const long long np = g.npix();
+  csff_status st = ensure_scratch(N, np, g.B, false);
+  if (st != CSFF_OK) return st;
+  {
+    ProfScope ps(PF_MG32, s, 8.0 * np + 64.0 * np + (accumulate ? 16.0 : 8.0) * np,
+                 2.0 * T3 * (2 * 16 + 16 * 16 + 16 * 2) * np);
+    k3_conv1<<<nblk(np), NTH, 0, s>>>(g, r, scale, N->wb, N->h1);
+    k3_conv2<<<nblk(np), NTH, 0, s>>>(g, N->h1, N->wb + NP31, N->h2);
+    k3_conv3<<<nblk(np), NTH, 0, s>>>(g, N->h2, N->wb + NP31 + NP32, y, accumulate);
+  }
+  count_launch(3);
+  NK(cudaGetLastError(), "3D net forward");
+  return CSFF_OK;
+}
+
+csff_status loss_grad3(csff_net* N, csff::Geom3 g, const float2* r, const float2* q, const double* c_host, int margin,
+                       float* loss_host, cudaStream_t s) {
+  using namespace csff;
+  const long long np = g.npix();
+  csff_status st = ensure_scratch(N, np, g.B, true);
+  if (st != CSFF_OK) return st;
+  std::vector<float2> cp(g.B);
+  for (int b = 0; b < g.B; ++b) cp[b] = make_float2((float)c_host[2 * b], (float)c_host[2 * b + 1]);
+  NK(cudaMemcpyAsync(N->cpatch, cp.data(), sizeof(float2) * g.B, cudaMemcpyHostToDevice, s), "patch constants");
+  NK(cudaMemsetAsync(N->sums, 0, sizeof(double) * 2 * g.B, s), "sums");
+  NK(cudaMemsetAsync(N->grad, 0, sizeof(float) * NPARAM3, s), "grad");
+  st = forward3(N, g, r, 1.f, N->y, 0, s);
+  if (st != CSFF_OK) return st;
+  const __nv_bfloat16* w2 = N->wb + NP31;
+  const __nv_bfloat16* w3 = N->wb + NP31 + NP32;
+  k3_loss1<<<nblk(np), NTH, 0, s>>>(g, N->y, r, q, N->cpatch, margin, N->E, N->sums);
+  k3_loss2<<<nblk(np), NTH, 0, s>>>(g, N->E, N->sums, q, N->cpatch, N->G, N->dy, 0);
+  k3_loss2<<<nblk(np), NTH, 0, s>>>(g, N->E, N->sums, q, N->cpatch, N->G, N->dy, 1);
+  k3_bwd3<<<nblk(np), NTH, 0, s>>>(g, N->dy, w3, N->h2, N->dh2);
+  k3_bwd2<<<nblk(np), NTH, 0, s>>>(g, N->dh2, w2, N->h1, N->dh1);
+  const int wb_blocks = (int)((np + 127) / 128);
+  k3_wgrad<16, 2, 1, 0><<<wb_blocks, NTH, 0, s>>>(g, N->h2, N->dy, N->grad + NP31 + NP32);
+  k3_wgrad<16, 16, 1, 1><<<wb_blocks, NTH, 0, s>>>(g, N->h1, N->dh2, N->grad + NP31);
+  k3_wgrad<2, 16, 0, 1><<<wb_blocks, NTH, 0, s>>>(g, r, N->dh1, N->grad);
+  count_launch(8);
+  NK(cudaGetLastError(), "3D net backward");
+  if (loss_host) {
+    std::vector<double> sums(2 * g.B);
+    NK(cudaMemcpyAsync(sums.data(), N->sums, sizeof(double) * 2 * g.B, cudaMemcpyDeviceToHost, s), "loss");
+    NK(cudaStreamSynchronize(s), "sync");
+    double L = 0;
+    for (int b = 0; b < g.B; ++b) L += sums[2 * b + 1] > 0 ? sums[2 * b] / sums[2 * b + 1] : 0.0;
+    *loss_host = (float)(L / g.B);
+  }
+  return CSFF_OK;
+}
+
+// one Adam step on N->grad
+csff_status adam_step(csff_net* N, float lr, cudaStream_t s) {
+  N->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)N->step), c2 = 1.f - std::pow(b2, (float)N->step);
+  csff::k_adam<<<(N->nparam + 255) / 256, 256, 0, s>>>(N->w, N->m, N->v, N->grad, N->wb, N->nparam, lr, b1, b2,
+                                                       1e-8f, c1, c2);
+  csff::count_launch();
+  NK(cudaGetLastError(), "adam");
+  return CSFF_OK;
+}
+
 // loss and weight gradient (into N->grad) for a batch of patches
 csff_status loss_grad(csff_net* N, csff::Geom g, const float2* r, const float2* q, const double* c_host, int margin,
                       float* loss_host, cudaStream_t s) {
@@ -661,24 +1063,27 @@ csff_status loss_grad(csff_net* N, csff::Geom g, const float2* r, const float2* 
 
 extern "C" {
 
-csff_status csff_net_create(const float* w_host, csff_net** out) {
+static csff_status net_create(int dim, const float* w_host, csff_net** out) {
   if (!out) return ninvalid("out is NULL");
   *out = nullptr;
   csff_net* N = new csff_net();
+  N->dim = dim;
+  N->nparam = dim == 3 ? csff::NPARAM3 : csff::NPARAM;
   auto fail = [&](csff_status s) {
     csff_net_destroy(N);
     return s;
   };
   cudaError_t e;
-  if ((e = cudaMalloc((void**)&N->w, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&N->m, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&N->v, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&N->grad, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
-      (e = cudaMalloc((void**)&N->wb, sizeof(__nv_bfloat16) * csff::NPARAM)) != cudaSuccess ||
+  const size_t np = (size_t)N->nparam;
+  if ((e = cudaMalloc((void**)&N->w, sizeof(float) * np)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->m, sizeof(float) * np)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->v, sizeof(float) * np)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->grad, sizeof(float) * np)) != cudaSuccess ||
+      (e = cudaMalloc((void**)&N->wb, sizeof(__nv_bfloat16) * np)) != cudaSuccess ||
       (e = cudaMalloc((void**)&N->tcerr, sizeof(int))) != cudaSuccess ||
       (e = cudaMemset(N->tcerr, 0, sizeof(int))) != cudaSuccess ||
-      (e = cudaMemset(N->m, 0, sizeof(float) * csff::NPARAM)) != cudaSuccess ||
-      (e = cudaMemset(N->v, 0, sizeof(float) * csff::NPARAM)) != cudaSuccess)
+      (e = cudaMemset(N->m, 0, sizeof(float) * np)) != cudaSuccess ||
+      (e = cudaMemset(N->v, 0, sizeof(float) * np)) != cudaSuccess)
     return fail(csff::cuda_fail(e, "net allocation"));
   csff_status s = csff_net_set_weights(N, w_host);
   if (s != CSFF_OK) return fail(s);
@@ -695,19 +1100,24 @@ void csff_net_destroy(csff_net* N) {
   delete N;
 }
 
+csff_status csff_net_create(const float* w_host, csff_net** out) { return net_create(2, w_host, out); }
+csff_status csff_net_create3(const float* w_host, csff_net** out) { return net_create(3, w_host, out); }
+
 int csff_net_num_params(void) { return csff::NPARAM; }
+int csff_net_num_params3(void) { return csff::NPARAM3; }
 
 
 
 csff_status csff_net_set_weights(csff_net* N, const float* w_host) {
   if (!N || !w_host) return ninvalid("NULL argument");
-  for (int i = 0; i < csff::NPARAM; ++i)
+  const int np = N->nparam;
+  for (int i = 0; i < np; ++i)
     if (!std::isfinite(w_host[i])) return ninvalid("non-finite weight");
-  NK(cudaMemcpy(N->w, w_host, sizeof(float) * csff::NPARAM, cudaMemcpyHostToDevice), "set weights");
-  csff::k_to_bf16<<<(csff::NPARAM + 255) / 256, 256>>>(N->w, N->wb, csff::NPARAM);
+  NK(cudaMemcpy(N->w, w_host, sizeof(float) * np, cudaMemcpyHostToDevice), "set weights");
+  csff::k_to_bf16<<<(np + 255) / 256, 256>>>(N->w, N->wb, np);
   csff::count_launch();
-  NK(cudaMemset(N->m, 0, sizeof(float) * csff::NPARAM), "reset moments");
-  NK(cudaMemset(N->v, 0, sizeof(float) * csff::NPARAM), "reset moments");
+  NK(cudaMemset(N->m, 0, sizeof(float) * np), "reset moments");
+  NK(cudaMemset(N->v, 0, sizeof(float) * np), "reset moments");
   N->step = 0;
   NK(cudaDeviceSynchronize(), "set weights");
   return CSFF_OK;
@@ -715,12 +1125,13 @@ csff_status csff_net_set_weights(csff_net* N, const float* w_host) {
 
 csff_status csff_net_get_weights(const csff_net* N, float* w_host) {
   if (!N || !w_host) return ninvalid("NULL argument");
-  NK(cudaMemcpy(w_host, N->w, sizeof(float) * csff::NPARAM, cudaMemcpyDeviceToHost), "get weights");
+  NK(cudaMemcpy(w_host, N->w, sizeof(float) * N->nparam, cudaMemcpyDeviceToHost), "get weights");
   return CSFF_OK;
 }
 
 csff_status csff_net_forward(csff_net* N, int B, int H, int W, const void* r_dev, void* y_dev, void* stream) {
   if (!N || !r_dev || !y_dev || B < 1 || H < 1 || W < 1) return ninvalid("bad forward arguments");
+  if (N->dim != 2) return ninvalid("a 3D network: csff_net_forward3");
   csff::Geom g{B, H, W};
   if (g.npix() >= (1ll << 31)) return ninvalid("more than 2^31 pixels");
   csff_status s = forward(N, g, (const float2*)r_dev, 1.f, (float2*)y_dev, 0, (cudaStream_t)stream);
@@ -733,6 +1144,8 @@ csff_status csff_net_loss_grad(csff_net* N, int B, int H, int W, const void* r_d
                                const double* c_host, int margin, float* loss_host, float* grad_host, void* stream) {
   if (!N || !r_dev || !q_dev || !c_host || B < 1 || H < 2 * margin + 1 || W < 2 * margin + 1 || margin < 0)
     return ninvalid("bad loss arguments");
+  if (N->dim != 2) return ninvalid("a 3D network: csff_net_loss_grad3");
+  if ((long long)B * H * W >= (1ll << 31)) return ninvalid("more than 2^31 pixels");
   cudaStream_t s = (cudaStream_t)stream;
   csff_status st = loss_grad(N, csff::Geom{B, H, W}, (const float2*)r_dev, (const float2*)q_dev, c_host, margin,
                              loss_host, s);
@@ -750,32 +1163,62 @@ csff_status csff_net_train_step(csff_net* N, int B, int H, int W, const void* r_
   cudaStream_t s = (cudaStream_t)stream;
   csff_status st = csff_net_loss_grad(N, B, H, W, r_dev, q_dev, c_host, margin, loss_host, nullptr, stream);
   if (st != CSFF_OK) return st;
-  N->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  float c1 = 1.f - std::pow(b1, (float)N->step), c2 = 1.f - std::pow(b2, (float)N->step);
-  csff::k_adam<<<(csff::NPARAM + 255) / 256, 256, 0, s>>>(N->w, N->m, N->v, N->grad, N->wb, csff::NPARAM, lr, b1,
-                                                          b2, 1e-8f, c1, c2);
-  csff::count_launch();
-  NK(cudaGetLastError(), "adam");
+  return adam_step(N, lr, s);
+}
+
+csff_status csff_net_forward3(csff_net* N, int B, int Z, int H, int W, const void* r_dev, void* y_dev, void* stream) {
+  if (!N || !r_dev || !y_dev || B < 1 || Z < 1 || H < 1 || W < 1) return ninvalid("bad forward arguments");
+  if (N->dim != 3) return ninvalid("a 2D network: csff_net_forward");
+  const csff::Geom3 g{B, Z, H, W};
+  if (g.npix() >= (1ll << 31)) return ninvalid("more than 2^31 voxels");
+  csff_status s = forward3(N, g, (const float2*)r_dev, 1.f, (float2*)y_dev, 0, (cudaStream_t)stream);
+  if (s != CSFF_OK) return s;
+  NK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
   return CSFF_OK;
+}
+
+csff_status csff_net_loss_grad3(csff_net* N, int B, int Z, int H, int W, const void* r_dev, const void* q_dev,
+                                const double* c_host, int margin, float* loss_host, float* grad_host, void* stream) {
+  if (!N || !r_dev || !q_dev || !c_host || B < 1 || margin < 0 || Z < 2 * margin + 1 || H < 2 * margin + 1 ||
+      W < 2 * margin + 1)
+    return ninvalid("bad loss arguments");
+  if (N->dim != 3) return ninvalid("a 2D network: csff_net_loss_grad");
+  const csff::Geom3 g{B, Z, H, W};
+  if (g.npix() >= (1ll << 31)) return ninvalid("more than 2^31 voxels");
+  cudaStream_t s = (cudaStream_t)stream;
+  csff_status st = loss_grad3(N, g, (const float2*)r_dev, (const float2*)q_dev, c_host, margin, loss_host, s);
+  if (st != CSFF_OK) return st;
+  if (grad_host) {
+    NK(cudaMemcpyAsync(grad_host, N->grad, sizeof(float) * csff::NPARAM3, cudaMemcpyDeviceToHost, s), "grad");
+    NK(cudaStreamSynchronize(s), "sync");
+  }
+  return CSFF_OK;
+}
+
+csff_status csff_net_train_step3(csff_net* N, int B, int Z, int H, int W, const void* r_dev, const void* q_dev,
+                                 const double* c_host, int margin, float lr, float* loss_host, void* stream) {
+  if (!(lr > 0.f)) return ninvalid("learning rate must be positive");
+  csff_status st = csff_net_loss_grad3(N, B, Z, H, W, r_dev, q_dev, c_host, margin, loss_host, nullptr, stream);
+  if (st != CSFF_OK) return st;
+  return adam_step(N, lr, (cudaStream_t)stream);
 }
 
 }  // extern "C"
 
 namespace csff {
 
-// scratch for a single patch of npix pixels (reserved before graph capture)
 const void* net_weights_bf16(const csff_net* N) { return N->wb; }
+int net_dim(const csff_net* N) { return N->dim; }
 
-// inference keeps its activations in shared memory: nothing to allocate, only
-// the pixel limit of the kernels' 32-bit patch indexing to check
+// Before graph capture: the 2D network's inference keeps its activations in
+// shared memory (only the 32-bit indexing limit to check); the 3D network's
+// layers need their scratch for npix voxels.
 csff_status net_reserve(csff_net* N, long long npix) {
-  (void)N;
-  return npix < (1ll << 31) ? CSFF_OK : ninvalid("more than 2^31 pixels");
+  if (npix >= (1ll << 31)) return ninvalid("more than 2^31 pixels");
+  return N->dim == 3 ? ensure_scratch(N, npix, 1, false) : CSFF_OK;
 }
 
-// u <- u + N(b - A u) on level L (FP32), the learned step of the smoother
-// status of the tensor-core layer since the last check (synchronises)
+// status of the tensor-core layers since the last check (synchronises)
 csff_status net_check(csff_net* N) {
   int err = 0;
   cudaError_t e = cudaMemcpy(&err, N->tcerr, sizeof(int), cudaMemcpyDeviceToHost);
@@ -790,9 +1233,10 @@ csff_status net_check(csff_net* N) {
 
 csff_status learned_step(csff_plan* P, int level, int dim, const Level& L, float2* u, const float2* b, cudaStream_t s) {
   csff_net* N = (level >= 0 && level < 16 && P->level_net[level]) ? P->level_net[level] : P->net;
-  Geom g{1, L.m, L.m};
   cudaError_t e = launch_residual<float>(dim, L, u, b, L.r32, s);
   if (e != cudaSuccess) return cuda_fail(e, "learned step residual");
+  if (dim == 3) return forward3(N, Geom3{1, L.m, L.m, L.m}, L.r32, (float)(L.h * L.h), u, 1, s);
+  Geom g{1, L.m, L.m};
   // u += N(h^2 r) = h^2 N(r) (the scaling applied as the input is read): the
   // network is positively homogeneous, and in units of h^2 the level's
   // operator e^{-2i gamma}(4 - shift) - (kh)^2 (1 + chi) is O(1) on every

@@ -11,24 +11,29 @@ import torch
 from . import Net, Plan
 
 
-def init_weights(seed: int) -> np.ndarray:
-    """He-normal weights (last layer scaled by 0.1), layout (out, in, a, b)."""
+def init_weights(seed: int, dim: int = 2) -> np.ndarray:
+    """He-normal weights (last layer scaled by 0.1), layout (out, in, taps):
+    3^dim taps per input channel."""
+    taps = 3 ** dim
     rng = np.random.Generator(np.random.PCG64(seed))
     parts = []
     for l, (o, i) in enumerate(((16, 2), (16, 16), (2, 16))):
-        std = np.sqrt(2.0 / (9 * i)) * (0.1 if l == 2 else 1.0)
-        parts.append(rng.standard_normal(o * i * 9) * std)
+        std = np.sqrt(2.0 / (taps * i)) * (0.1 if l == 2 else 1.0)
+        parts.append(rng.standard_normal(o * i * taps) * std)
     return np.concatenate(parts).astype(np.float32)
 
 
-def collect_patches(problems, opts, n_cycles=5, patch=64, per_field=4, seed=0):
+def collect_patches(problems, opts, n_cycles=5, patch=64, per_field=4, seed=0, core_margin=0, min_core=0.0):
     """Residual patches as the learned step sees them: in FP32 from u = 0 on
     A u = b (b the scaled right-hand side), after each red-black sweep that
-    starts a V-cycle.  Returns (r, q, c): complex64 CUDA tensors (B, P, P) of
-    residuals normalised to unit RMS, the matching windows of h^2 q =
-    (kh)^2(1+chi), and the per-patch constants h^2 c = e^{-2i gamma}: the
+    starts a V-cycle.  Returns (r, q, c): complex64 CUDA tensors (B, P, P)
+    (3D problems: (B, P, P, P)) of residuals normalised to unit RMS, the
+    matching windows of h^2 q = (kh)^2(1+chi), and the per-patch constants
+    h^2 c = e^{-2i gamma}: the
     operator in the units in which the plan applies the network,
-    u <- u + N(h^2 r)."""
+    u <- u + N(h^2 r).  With min_core > 0 a window is kept only if at least
+    that fraction of its residual energy lies inside its core (the window
+    less core_margin on every side, the part the loss weighs)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     rs, qs, cs = [], [], []
     for prob, eta in problems:
@@ -42,19 +47,26 @@ def collect_patches(problems, opts, n_cycles=5, patch=64, per_field=4, seed=0):
         q, c = plan.coefficients(0)
         h2 = plan.describe()["h"][0] ** 2
         q, c = q * h2, c * h2
+        d = int(prob["dim"])
         for _ in range(n_cycles):
             plan.smooth(0, u, b, 1)
             plan.residual(0, u, b, r)
-            R = r.view(m, m)
-            Q = q.view(m, m)
+            R = r.view((m,) * d)
+            Q = q.view((m,) * d)
             for _ in range(per_field):
-                i, j = rng.integers(0, m - patch + 1, size=2)
-                rp = R[i:i + patch, j:j + patch]
-                s = rp.abs().square().mean().sqrt()
+                o = rng.integers(0, m - patch + 1, size=d)
+                win = tuple(slice(int(a), int(a) + patch) for a in o)
+                rp = R[win]
+                e2 = rp.abs().square()
+                s = e2.mean().sqrt()
                 if not torch.isfinite(s) or s.item() == 0.0:
                     continue
+                if min_core > 0.0:
+                    core = tuple(slice(core_margin, patch - core_margin) for _ in range(d))
+                    if e2[core].sum().item() < min_core * e2.sum().item():
+                        continue
                 rs.append(rp / s)
-                qs.append(Q[i:i + patch, j:j + patch])
+                qs.append(Q[win])
                 cs.append(c)
             plan.vcycle(u, b)
         plan.close()
