@@ -80,9 +80,12 @@ __device__ __forceinline__ cx<T> zero_c() { return mk<cx<T>>((T)0, (T)0); }
 // nearest intrinsics are never contracted or reassociated by the compiler), so
 // the per-level kernels and the persistent batched kernel, which inline the
 // same tile bodies into different code, produce identical bits.
-__device__ __forceinline__ float2 xadd(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+// The FP32 element-wise forms use the packed two-lane instructions (one
+// instruction for both parts, the same rounding per part); a - b is
+// fma(b, -1, a), exact product and one rounding.
+__device__ __forceinline__ float2 xadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ double2 xadd(double2 a, double2 b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
-__device__ __forceinline__ float2 xsub(float2 a, float2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 xsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ double2 xsub(double2 a, double2 b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
 __device__ __forceinline__ float2 xmul(float2 a, float2 b) {
   return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
@@ -90,7 +93,7 @@ __device__ __forceinline__ float2 xmul(float2 a, float2 b) {
 __device__ __forceinline__ double2 xmul(double2 a, double2 b) {
   return make_double2(__fma_rn(a.x, b.x, -__dmul_rn(a.y, b.y)), __fma_rn(a.x, b.y, __dmul_rn(a.y, b.x)));
 }
-__device__ __forceinline__ float2 xscale(float2 a, float s) { return make_float2(__fmul_rn(a.x, s), __fmul_rn(a.y, s)); }
+__device__ __forceinline__ float2 xscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 __device__ __forceinline__ double2 xscale(double2 a, double s) { return make_double2(__dmul_rn(a.x, s), __dmul_rn(a.y, s)); }
 // a + b c and a - b c as chains of fused multiply-adds (one rounding each)
 __device__ __forceinline__ float2 xfma(float2 a, float2 b, float2 c) {
