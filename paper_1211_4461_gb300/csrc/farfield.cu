@@ -37,54 +37,76 @@ __device__ __forceinline__ int cexp2(double2 v) {
   return e + 1;
 }
 
-// g = chi (u_in + u) at every interior node.
+// g = chi (u_in + u) at every interior node, and the largest frexp exponent of
+// max(|Re g|, |Im g|) over the field (atomicMax into *emax, which the caller
+// sets to -2000; 4000 when a component is not finite, -2000 for zero).
 struct Tabs8 { const double2* p[8]; };
+
+__global__ void k_fill_int(int* p, int v) { *p = v; }
+
+__device__ __forceinline__ int value_exp(double2 x) {
+  const int Ex = bits::exp_field(x.x), Ey = bits::exp_field(x.y);
+  if (Ex == 0x7ff || Ey == 0x7ff) return 4000;
+  const bool nzx = ((unsigned long long)__double_as_longlong(x.x) & bits::ABS_MASK) != 0;
+  const bool nzy = ((unsigned long long)__double_as_longlong(x.y) & bits::ABS_MASK) != 0;
+  return max(nzx ? bits::frexp_exp(x.x) : -2000, nzy ? bits::frexp_exp(x.y) : -2000);
+}
 
 template <int D>
 __global__ void k_gfield(Tabs8 tabs, int n_gauss, const double2* __restrict__ uinc,
-                         const double2* __restrict__ u, int m, double2* __restrict__ g) {
+                         const double2* __restrict__ u, int m, double2* __restrict__ g, int* __restrict__ emax) {
   // g = chi u_in + chi u; chi u_in with each axis' Gaussian factor paired with
   // its incident-wave factor first (no partial product beyond the FP64 range).
-  // The per-axis factors and pairs of the block's 32 columns, 8 rows (and
-  // plane) are read and formed once per block.
-  __shared__ double2 ex[8][32], ey[8][8], px[8][32], py[8][8], ez[8], pz[8];
+  // The per-axis factors and pairs of the block's 32 columns are read and
+  // formed once per block, those of its 8 rows (times the plane's, in 3D)
+  // likewise, so a node costs two complex products per Gaussian.
+  __shared__ double2 ex[8][32], eyz[8][8], px[8][32], pyz[8][8];
+  __shared__ int wmax[8];
   const int t = threadIdx.y * 32 + threadIdx.x;
-  for (int i = t; i < n_gauss * 41; i += 256) {
-    const int q = i / 41, r = i % 41;
+  for (int i = t; i < n_gauss * 40; i += 256) {
+    const int q = i / 40, r = i % 40;
     const double2* E = tabs.p[q];
     if (r < 32) {
       const int x = blockIdx.x * 32 + r;
       const double2 f = x < m ? E[x] : make_double2(0, 0);
       ex[q][r] = f;
       px[q][r] = x < m ? cmul(f, uinc[x]) : make_double2(0, 0);
-    } else if (r < 40) {
+    } else {
       const int y = blockIdx.y * 8 + (r - 32);
-      const double2 f = y < m ? E[m + y] : make_double2(0, 0);
-      ey[q][r - 32] = f;
-      py[q][r - 32] = y < m ? cmul(f, uinc[m + y]) : make_double2(0, 0);
-    } else if (D == 3) {
-      const double2 f = E[2 * m + blockIdx.z];
-      ez[q] = f;
-      pz[q] = cmul(f, uinc[2 * m + blockIdx.z]);
+      double2 f = y < m ? E[m + y] : make_double2(0, 0);
+      double2 pf = y < m ? cmul(f, uinc[m + y]) : make_double2(0, 0);
+      if (D == 3) {
+        const double2 fz = E[2 * m + blockIdx.z];
+        f = cmul(f, fz);
+        pf = cmul(pf, cmul(fz, uinc[2 * m + blockIdx.z]));
+      }
+      eyz[q][r - 32] = f;
+      pyz[q][r - 32] = pf;
     }
   }
   __syncthreads();
   const int ix = blockIdx.x * 32 + threadIdx.x, iy = blockIdx.y * 8 + threadIdx.y;
   const int iz = (D == 3) ? (int)blockIdx.z : 0;
-  if (ix >= m || iy >= m) return;
-  const long long idx = ((long long)iz * m + iy) * m + ix;
-  double2 chi = make_double2(0, 0), cu = make_double2(0, 0);
-  for (int q = 0; q < n_gauss; ++q) {
-    double2 v = cmul(ex[q][threadIdx.x], ey[q][threadIdx.y]);
-    double2 w = cmul(px[q][threadIdx.x], py[q][threadIdx.y]);
-    if (D == 3) {
-      v = cmul(v, ez[q]);
-      w = cmul(w, pz[q]);
+  int e = -2000;
+  if (ix < m && iy < m) {
+    const long long idx = ((long long)iz * m + iy) * m + ix;
+    double2 chi = make_double2(0, 0), cu = make_double2(0, 0);
+    for (int q = 0; q < n_gauss; ++q) {
+      chi = cadd(chi, cmul(ex[q][threadIdx.x], eyz[q][threadIdx.y]));
+      cu = cadd(cu, cmul(px[q][threadIdx.x], pyz[q][threadIdx.y]));
     }
-    chi = cadd(chi, v);
-    cu = cadd(cu, w);
+    const double2 v = cadd(cu, cmul(chi, u[idx]));
+    g[idx] = v;
+    e = value_exp(v);
   }
-  g[idx] = cadd(cu, cmul(chi, u[idx]));
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (threadIdx.x == 0) wmax[threadIdx.y] = e;
+  __syncthreads();
+  if (t == 0) {
+    int b = wmax[0];
+    for (int w = 1; w < 8; ++w) b = max(b, wmax[w]);
+    atomicMax(emax, b);
+  }
 }
 
 // Phase tables P(a, x_i) = exp(-i k e^{i gamma} a x_i) = exp(k a x_i (sin g - i cos g)):
@@ -1175,10 +1197,12 @@ csff_status far_field_one(csff_plan* P, const double* eta_host, const double2* u
   Tabs8 t{};
   for (int q = 0; q < P->prob.n_gauss; ++q) t.p[q] = P->chi_tab[0] + (size_t)q * d * m;   // finest level
   dim3 gg((m + 31) / 32, (m + 7) / 8, d == 3 ? m : 1), gb(32, 8);
-  if (d == 2) k_gfield<2><<<gg, gb, 0, s>>>(t, P->prob.n_gauss, P->uinc_tab, u, m, B.dg);
-  else k_gfield<3><<<gg, gb, 0, s>>>(t, P->prob.n_gauss, P->uinc_tab, u, m, B.dg);
+  k_fill_int<<<1, 1, 0, s>>>(B.dmisc, -2000);
   count_launch();
-  if ((e = launch_max_exp(B.dg, L.N, B.dmisc, s)) != cudaSuccess) return cuda_fail(e, "max exponent");
+  if (d == 2) k_gfield<2><<<gg, gb, 0, s>>>(t, P->prob.n_gauss, P->uinc_tab, u, m, B.dg, B.dmisc);
+  else k_gfield<3><<<gg, gb, 0, s>>>(t, P->prob.n_gauss, P->uinc_tab, u, m, B.dg, B.dmisc);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "g field");
   const double sg = std::sin(P->prob.gamma), cg = std::cos(P->prob.gamma);
   if (d == 3) {
     // sum-factorised path when no intermediate can leave the FP64 range:

@@ -66,13 +66,16 @@ __global__ void k_jacobi(const cx<T>* __restrict__ u, const cx<T>* __restrict__ 
 }
 
 // One colour of red-black Gauss-Seidel, in place.  colour 0 (red) = even sum
-// of node indices (interior index + 1 per axis).
+// of node indices (interior index + 1 per axis).  One thread per point of the
+// colour: x thread t of a row takes ix = 2 t + (colour + iy + iz + D) mod 2.
 template <typename T, int D>
 __global__ void k_rbgs(cx<T>* u, const cx<T>* __restrict__ b, const cx<T>* __restrict__ q,
                        const cx<T>* __restrict__ dinv, cx<T> c, int m, int colour) {
-  int ix, iy, iz; long long idx;
-  if (!thread_point<D>(m, ix, iy, iz, idx)) return;
-  if (((ix + iy + iz + D) & 1) != colour) return;
+  const int iy = blockIdx.y * BY + threadIdx.y;
+  const int iz = (D == 3) ? (int)blockIdx.z : 0;
+  const int ix = 2 * (int)(blockIdx.x * BX + threadIdx.x) + ((colour + iy + iz + D) & 1);
+  if (ix >= m || iy >= m) return;
+  const long long idx = ((long long)iz * m + iy) * m + ix;
   cx<T> uj = u[idx];
   cx<T> rj = csub(b[idx], apply_point<T, D>(u, uj, q[idx], c, m, ix, iy, iz, idx));
   u[idx] = cadd(uj, cmul(dinv[idx], rj));
@@ -538,6 +541,7 @@ cudaError_t launch_jacobi(int dim, const Level& L, double omega, const cx<T>* u,
 template <typename T>
 cudaError_t launch_rbgs(int dim, const Level& L, cx<T>* u, const cx<T>* b, cudaStream_t s) {
   dim3 g = grid_of(dim, L.m), blk(BX, BY);
+  g.x = ((L.m + 1) / 2 + BX - 1) / BX;          // one thread per point of a colour along x
   cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
   ProfScope ps(mg_family<T>(), s, 3.0 * sizeof(cx<T>) * L.N, 0);
   CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 0);
