@@ -686,13 +686,14 @@ def measure_batched_learned(csff, torch, dev, stream, flush, bc, ms_plain, ms_ba
 
 def measure_3d(csff, torch, dev, stream, flush):
     """257^3 on [-15,15]^3, k = 4, 16 incident directions, 64 x 32 angles,
-    FP32-inner / FP64 refinement.  The step as the workload states it: the
+    FP32-inner / FP64 refinement (at most six cycles a step, adaptive, as in the
+    2D headline).  The step as the workload states it: the
     far field's z-contraction on the tensor cores (four-term BF16 splits, FP32
     accumulation in tensor memory); the same step with the FP64-class
     sum-factorised far field beside it; then the far field alone in both modes
     and the relative L2 distance of their maps."""
     c = W.big_3d(n=257, n_rhs=16)
-    c["opts"].update(precision="mixed", refine_fp64=1)
+    c["opts"].update(precision="mixed", refine_fp64=1, inner_cycles=INNER_CYCLES, adaptive_inner=1)
     plan = csff.Plan(c["problem"], c["opts"], stream=stream)
     nr, na = c["eta"].shape[0], c["alphas"].shape[0]
     u = torch.zeros(nr * plan.N, dtype=torch.complex128, device=dev)

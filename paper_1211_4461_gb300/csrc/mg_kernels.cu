@@ -124,6 +124,64 @@ __device__ __forceinline__ int interp_1d(int p, int mc, int* ci, T* w) {
   return n;
 }
 
+// u_f += P e by coarse cells: cell (Nx, Ny, Nz), N in [0, mc] per axis, spans
+// coarse nodes N and N + 1 (node 0 and mc + 1 on the boundary, value zero)
+// and holds the fine nodes 2N + 1 (the midpoint: weight 1/2 on each end) and
+// 2N + 2 (coarse node N + 1: weight 1), interior indices 2N and 2N + 1 (the
+// latter only for N < mc).  The bilinear/trilinear weights are products of
+// these per axis, applied axis by axis; one thread per cell, its two x points
+// adjacent in memory.
+template <typename T, int D>
+__global__ void k_prolong_cells(const cx<T>* __restrict__ ec, int mc, cx<T>* __restrict__ uf, int mf) {
+  using C = cx<T>;
+  const int Nx = blockIdx.x * BX + threadIdx.x, Ny = blockIdx.y * BY + threadIdx.y;
+  const int Nz = (D == 3) ? (int)blockIdx.z : 0;
+  if (Nx > mc || Ny > mc) return;
+  const T h = (T)0.5;
+  // coarse values at the cell's corners: node K -> e[K - 1] inside [1, mc]
+  auto ev = [&](int kx, int ky, int kz) -> C {
+    const int X = Nx + kx, Y = Ny + ky, Z = Nz + kz;
+    if (X < 1 || X > mc || Y < 1 || Y > mc || (D == 3 && (Z < 1 || Z > mc))) return mk<C>(0, 0);
+    return ec[((long long)(D == 3 ? Z - 1 : 0) * mc + (Y - 1)) * mc + (X - 1)];
+  };
+  // along x for each (y, z) corner: mid and coincident values
+  C xm[2][2], xc[2][2];
+#pragma unroll
+  for (int kz = 0; kz < (D == 3 ? 2 : 1); ++kz)
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky) {
+      const C a = ev(0, ky, kz), b = ev(1, ky, kz);
+      xm[kz][ky] = cscale(cadd(a, b), h);
+      xc[kz][ky] = b;
+    }
+  const bool x1 = Nx < mc, y1 = Ny < mc, z1 = (D == 3) ? Nz < mc : false;
+  const long long f0 = ((long long)(D == 3 ? 2 * Nz : 0) * mf + 2 * Ny) * mf + 2 * Nx;
+#pragma unroll
+  for (int sz = 0; sz < (D == 3 ? 2 : 1); ++sz) {        // fine z: 0 mid, 1 coincident
+    if (sz == 1 && !z1) continue;
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy) {                      // fine y: 0 mid, 1 coincident
+      if (sy == 1 && !y1) continue;
+      // along z, then y
+      C vm, vc;
+      if (D == 3) {
+        C ym_m = sz ? xm[1][0] : cscale(cadd(xm[0][0], xm[1][0]), h);
+        C ym_c = sz ? xc[1][0] : cscale(cadd(xc[0][0], xc[1][0]), h);
+        C yc_m = sz ? xm[1][1] : cscale(cadd(xm[0][1], xm[1][1]), h);
+        C yc_c = sz ? xc[1][1] : cscale(cadd(xc[0][1], xc[1][1]), h);
+        vm = sy ? yc_m : cscale(cadd(ym_m, yc_m), h);
+        vc = sy ? yc_c : cscale(cadd(ym_c, yc_c), h);
+      } else {
+        vm = sy ? xm[0][1] : cscale(cadd(xm[0][0], xm[0][1]), h);
+        vc = sy ? xc[0][1] : cscale(cadd(xc[0][0], xc[0][1]), h);
+      }
+      const long long f = f0 + ((long long)sz * mf + sy) * mf;
+      uf[f] = cadd(uf[f], vm);
+      if (x1) uf[f + 1] = cadd(uf[f + 1], vc);
+    }
+  }
+}
+
 template <typename T, int D>
 __global__ void k_prolong_add(const cx<T>* __restrict__ ec, int mc, cx<T>* __restrict__ uf, int mf) {
   int ix, iy, iz; long long idx;
@@ -565,7 +623,8 @@ cudaError_t launch_prolong_add(int dim, const Level& F, const Level& C, const cx
                                cudaStream_t s) {
   dim3 g = grid_of(dim, F.m), blk(BX, BY);
   ProfScope ps(mg_family<T>(), s, (double)sizeof(cx<T>) * (2.0 * F.N + C.N), 0);
-  CSFF_DIM_DISPATCH(dim, k_prolong_add, ec, C.m, u, F.m);
+  g = dim3((C.m + 1 + BX - 1) / BX, (C.m + 1 + BY - 1) / BY, dim == 3 ? C.m + 1 : 1);   // coarse cells
+  CSFF_DIM_DISPATCH(dim, k_prolong_cells, ec, C.m, u, F.m);
   count_launch();
   return cudaGetLastError();
 }
