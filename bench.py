@@ -687,52 +687,95 @@ def measure_batched_learned(csff, torch, dev, stream, flush, bc, ms_plain, ms_ba
 def measure_3d(csff, torch, dev, stream, flush):
     """257^3 on [-15,15]^3, k = 4, 16 incident directions, 64 x 32 angles,
     FP32-inner / FP64 refinement (at most six cycles a step, adaptive, as in the
-    2D headline).  The step as the workload states it: the
-    far field's z-contraction on the tensor cores (four-term BF16 splits, FP32
-    accumulation in tensor memory); the same step with the FP64-class
-    sum-factorised far field beside it; then the far field alone in both modes
-    and the relative L2 distance of their maps."""
+    2D headline).  The step as the workload states it: the far field's
+    z-contraction on the tensor cores (four-term BF16 splits, FP32 accumulation
+    in tensor memory).  Scheduled like the 2D headline: four plans of four
+    directions each, every plan on its own CUDA stream and host thread (the
+    small levels' launches of one plan hide under another's fine-level work);
+    one plan solving the sixteen directions in turn beside it, and the
+    concurrent step with the FP64-class sum-factorised far field; then the far
+    field alone in both modes and the relative L2 distance of their maps."""
     c = W.big_3d(n=257, n_rhs=16)
     c["opts"].update(precision="mixed", refine_fp64=1, inner_cycles=INNER_CYCLES, adaptive_inner=1)
-    plan = csff.Plan(c["problem"], c["opts"], stream=stream)
     nr, na = c["eta"].shape[0], c["alphas"].shape[0]
-    u = torch.zeros(nr * plan.N, dtype=torch.complex128, device=dev)
-    F = torch.zeros(nr * na, dtype=torch.complex128, device=dev)
-    Fe = torch.zeros(nr * na, dtype=torch.int32, device=dev)
+    G = 4
+    streams = [torch.cuda.Stream(device=dev) for _ in range(G)]
+    plans = [csff.Plan(c["problem"], c["opts"], stream=st) for st in streams]
+    N = plans[0].N
+    per = nr // G
+    us = [torch.zeros(per * N, dtype=torch.complex128, device=dev) for _ in range(G)]
+    Fs = [torch.zeros(per * na, dtype=torch.complex128, device=dev) for _ in range(G)]
+    Es = [torch.zeros(per * na, dtype=torch.int32, device=dev) for _ in range(G)]
     info = {}
 
+    def group(i):
+        eta = c["eta"][i * per:(i + 1) * per]
+        with torch.cuda.stream(streams[i]):
+            _, inf = plans[i].solve(eta, us[i])
+            info[i] = inf
+            plans[i].far_field(eta, us[i], c["alphas"], Fs[i], Es[i])
+
     def step():
-        _, inf = plan.solve(c["eta"], u)
-        info["inf"] = inf
+        start = torch.cuda.Event()
+        start.record(stream)
+        for st in streams:
+            st.wait_event(start)
+        th = [threading.Thread(target=group, args=(i,)) for i in range(G)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for st in streams:
+            stream.wait_stream(st)
+
+    def set_mode(mode):
+        for p in plans:
+            p.set_far_field_mode(mode)
+
+    set_mode(csff.FF_TC_BF16X4)
+    step()
+    ms = _time_events(torch, stream, step, flush, 2)
+    infs = [x for i in range(G) for x in info[i]]
+    out = {"value": nr / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "maps_per_step": nr,
+           "far_field": "tensor cores (z-contraction, four-term BF16 splits, FP32 accumulation)",
+           "concurrency": "four plans of four directions, each on its own stream and host thread",
+           "cycles": [x["cycles"] for x in infs], "all_converged": all(x["rel_res"] <= 1e-8 for x in infs)}
+    set_mode(csff.FF_FP64)
+    step()
+    ms64 = _time_events(torch, stream, step, flush, 2)
+    out["fp64_far_field"] = {"value": nr / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
+    for p in plans[1:]:
+        p.close()
+    plan = plans[0]
+    u = torch.zeros(nr * N, dtype=torch.complex128, device=dev)
+    F = torch.zeros(nr * na, dtype=torch.complex128, device=dev)
+    Fe = torch.zeros(nr * na, dtype=torch.int32, device=dev)
+
+    def seq_step():
+        plan.solve(c["eta"], u)
         plan.far_field(c["eta"], u, c["alphas"], F, Fe)
 
     def ff():
         plan.far_field(c["eta"], u, c["alphas"], F, Fe)
 
     plan.set_far_field_mode(csff.FF_TC_BF16X4)
-    step()
-    ms = _time_events(torch, stream, step, flush, 2)
-    out = {"value": nr / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "maps_per_step": nr,
-           "far_field": "tensor cores (z-contraction, four-term BF16 splits, FP32 accumulation)",
-           "cycles": [i["cycles"] for i in info["inf"]],
-           "all_converged": all(i["rel_res"] <= 1e-8 for i in info["inf"])}
-    plan.set_far_field_mode(csff.FF_FP64)
-    step()
-    ms64 = _time_events(torch, stream, step, flush, 2)
-    out["fp64_far_field"] = {"value": nr / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64}
-    maps = {}
-    for mode, name in ((csff.FF_FP64, "fp64"), (csff.FF_TC_BF16X4, "tc_bf16x4")):
-        plan.set_far_field_mode(mode)
-        ff()
-        ff_ms = _time_events(torch, stream, ff, flush, 3)
-        csff.prof_begin(csff.PROF_FF_CONTRACT)
-        ff()
-        torch.cuda.synchronize()
-        prof = csff.prof_end()["ff_contract"]
-        maps[name] = (F.cpu().numpy() * 2.0 ** Fe.cpu().numpy().astype(np.float64)).reshape(nr, na)
-        out[f"ff_{name}_ms_per_16_maps"] = ff_ms
-        out[f"ff_{name}_stageA_ms_per_map"] = prof["ms"] / max(1, nr)
-        out[f"ff_{name}_stageA_tflops"] = prof["alg_flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] else 0.0
+    with torch.cuda.stream(streams[0]):
+        seq_step()
+        mss = _time_events(torch, streams[0], seq_step, flush, 1)
+        out["one_plan_in_turn"] = {"value": nr / (mss / 1e3), "unit": UNIT, "ms_per_step": mss}
+        maps = {}
+        for mode, name in ((csff.FF_FP64, "fp64"), (csff.FF_TC_BF16X4, "tc_bf16x4")):
+            plan.set_far_field_mode(mode)
+            ff()
+            ff_ms = _time_events(torch, streams[0], ff, flush, 3)
+            csff.prof_begin(csff.PROF_FF_CONTRACT)
+            ff()
+            torch.cuda.synchronize()
+            prof = csff.prof_end()["ff_contract"]
+            maps[name] = (F.cpu().numpy() * 2.0 ** Fe.cpu().numpy().astype(np.float64)).reshape(nr, na)
+            out[f"ff_{name}_ms_per_16_maps"] = ff_ms
+            out[f"ff_{name}_stageA_ms_per_map"] = prof["ms"] / max(1, nr)
+            out[f"ff_{name}_stageA_tflops"] = prof["alg_flops"] / (prof["ms"] * 1e-3) / 1e12 if prof["ms"] else 0.0
     out["ff_fp64_stageA_fp64_frac"] = out["ff_fp64_stageA_tflops"] / FP64_PEAK_TFLOPS
     rel = np.linalg.norm(maps["tc_bf16x4"] - maps["fp64"], axis=1) / np.linalg.norm(maps["fp64"], axis=1)
     out["tc_vs_fp64_rel_l2"] = {"max": float(rel.max()), "median": float(np.median(rel)),
