@@ -335,6 +335,22 @@ __device__ __forceinline__ void df_mac(df& s, df a, df b) {
   s.lo += err + e;
 }
 
+// Two df_mac at once on the packed two-lane FP32 instructions: lane j holds
+// the running sum of output j; the same operations in the same order, each
+// rounded per lane as the scalar form rounds it.
+__device__ __forceinline__ void df_mac2(float2& sh, float2& sl, float2 ah, float2 al, float2 bh, float2 bl) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 p = __fmul2_rn(ah, bh);
+  float2 e = __ffma2_rn(ah, bh, __fmul2_rn(p, m1));     // exact error of the leading product
+  e = __ffma2_rn(ah, bl, e);
+  e = __ffma2_rn(al, bh, e);
+  const float2 t = __fadd2_rn(sh, p);                   // TwoSum(s.hi, p)
+  const float2 v = __ffma2_rn(sh, m1, t);               // t - s.hi
+  const float2 err = __fadd2_rn(__ffma2_rn(__ffma2_rn(v, m1, t), m1, sh), __ffma2_rn(v, m1, p));
+  sh = t;
+  sl = __fadd2_rn(sl, __fadd2_rn(err, e));
+}
+
 // one warp per (row, block): block exponent of |v| (upper bound), scaled
 // double-float split, and the row-block spread (max - min exponent) into *spread.
 // elo (block bounds for skipping negligible blocks, see k_ff_df_skip):
@@ -541,8 +557,9 @@ __global__ void __launch_bounds__(DF_NT, 5) k_ff_stage1_df(const float4* __restr
   if (!df_selected(spread)) return;      // the FP64 kernel takes this launch
   __shared__ float4 As[DF_BM][DKB + 1];
   __shared__ float2 As2[DF_BM][DKB + 1];
-  __shared__ float4 Bs[DF_BN][DKB + 1];
-  __shared__ float2 Bs2[DF_BN][DKB + 1];
+  // g rows tx and tx + 16 side by side (the two outputs j of a thread), per
+  // node: (re.hi, re.hi'), (re.lo, re.lo'), (im.hi, ..), (im.lo, ..), (sum.hi, ..), (sum.lo, ..)
+  __shared__ float4 Bp[DF_BN / 2][DKB + 1][3];
   __shared__ int eA[DF_BM], eB[DF_BN];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // ty: 0..7, rows 2 ty and 2 ty + 1
   const int m0 = blockIdx.y * DF_BM, n0 = blockIdx.x * DF_BN;
@@ -567,41 +584,50 @@ __global__ void __launch_bounds__(DF_NT, 5) k_ff_stage1_df(const float4* __restr
     for (int i = tid; i < DF_BN * DKB; i += DF_NT) {
       int r = i / DKB, kk = i % DKB, gn = n0 + r;
       const long long o = ((long long)gn * nb + b) * DKB + kk;
-      Bs[r][kk] = (gn < N) ? G[o] : make_float4(0, 0, 0, 0);
-      Bs2[r][kk] = (gn < N) ? Gs[o] : make_float2(0, 0);
+      const float4 gv = (gn < N) ? G[o] : make_float4(0, 0, 0, 0);
+      const float2 gs = (gn < N) ? Gs[o] : make_float2(0, 0);
+      float* d = reinterpret_cast<float*>(&Bp[r & 15][kk][0]);
+      const int ln = r >> 4;
+      d[ln] = gv.x;
+      d[2 + ln] = gv.y;
+      d[4 + ln] = gv.z;
+      d[6 + ln] = gv.w;
+      d[8 + ln] = gs.x;
+      d[10 + ln] = gs.y;
     }
     if (tid < DF_BM) eA[tid] = (m0 + tid < M) ? ex[(long long)(m0 + tid) * nb + b] : 0;
     if (tid >= 64 && tid < 64 + DF_BN) eB[tid - 64] = (n0 + tid - 64 < N) ? eg[(long long)(n0 + tid - 64) * nb + b] : 0;
     __syncthreads();
-    df s1[2][2], s2[2][2], s3[2][2];
+    // block sums of the thread's outputs (i, j): lane j of the pairs
+    float2 h1[2], l1[2], h2[2], l2[2], h3[2], l3[2];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) { s1[i][j] = df{0.f, 0.f}; s2[i][j] = df{0.f, 0.f}; s3[i][j] = df{0.f, 0.f}; }
+    for (int i = 0; i < 2; ++i) {
+      h1[i] = l1[i] = h2[i] = l2[i] = h3[i] = l3[i] = make_float2(0.f, 0.f);
+    }
 #pragma unroll 4
     for (int kk = 0; kk < DKB; ++kk) {
-      df ar[2], ai[2], as[2], br[2], bi[2], bs[2];
+      const float4 b0 = Bp[tx][kk][0], b1 = Bp[tx][kk][1], b2 = Bp[tx][kk][2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const float4 a = As[2 * ty + i][kk];
         const float2 a2 = As2[2 * ty + i][kk];
-        ar[i] = df{a.x, a.y};
-        ai[i] = df{a.z, a.w};
-        as[i] = df{a2.x, a2.y};
-        const float4 bb = Bs[tx + 16 * i][kk];
-        const float2 b2 = Bs2[tx + 16 * i][kk];
-        br[i] = df{bb.x, bb.y};
-        bi[i] = df{bb.z, bb.w};
-        bs[i] = df{b2.x, b2.y};
+        df_mac2(h1[i], l1[i], make_float2(a.x, a.x), make_float2(a.y, a.y), make_float2(b0.x, b0.y),
+                make_float2(b0.z, b0.w));
+        df_mac2(h2[i], l2[i], make_float2(a.z, a.z), make_float2(a.w, a.w), make_float2(b1.x, b1.y),
+                make_float2(b1.z, b1.w));
+        df_mac2(h3[i], l3[i], make_float2(a2.x, a2.x), make_float2(a2.y, a2.y), make_float2(b2.x, b2.y),
+                make_float2(b2.z, b2.w));
       }
+    }
+    df s1[2][2], s2[2][2], s3[2][2];
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          df_mac(s1[i][j], ar[i], br[j]);
-          df_mac(s2[i][j], ai[i], bi[j]);
-          df_mac(s3[i][j], as[i], bs[j]);
-        }
+    for (int i = 0; i < 2; ++i) {
+      s1[i][0] = df{h1[i].x, l1[i].x};
+      s1[i][1] = df{h1[i].y, l1[i].y};
+      s2[i][0] = df{h2[i].x, l2[i].x};
+      s2[i][1] = df{h2[i].y, l2[i].y};
+      s3[i][0] = df{h3[i].x, l3[i].x};
+      s3[i][1] = df{h3[i].y, l3[i].y};
     }
 #pragma unroll
     for (int i = 0; i < 2; ++i)
