@@ -73,7 +73,10 @@ TILES_FINE_DRAM_BYTES = 0.785e6
 # launch and a host round trip for its norm, and a solve stops only after a
 # step.  Sizing each step from the previous step's reduction factor (the
 # default) gave 652 (at most 6) and 656 (at most 8) against 635 fixed, same box.
-INNER_CYCLES = 6
+# With the FP64 refinement each step also costs an FP64-bound residual pass:
+# caps of 6, 8, 10, 12 gave 648, 664, 682, 682 maps/s with the same cycle
+# counts (18, 24, 28, 27) and fewer steps.
+INNER_CYCLES = 10
 
 
 def _cases(precision, ks=None, inner=INNER_CYCLES, adaptive=False, refine_fp64=False):
@@ -686,8 +689,8 @@ def measure_batched_learned(csff, torch, dev, stream, flush, bc, ms_plain, ms_ba
 
 def measure_3d(csff, torch, dev, stream, flush):
     """257^3 on [-15,15]^3, k = 4, 16 incident directions, 64 x 32 angles,
-    FP32-inner / FP64 refinement (at most six cycles a step, adaptive, as in the
-    2D headline).  The step as the workload states it: the far field's
+    FP32-inner / FP64 refinement (the 2D headline's adaptive schedule of at
+    most INNER_CYCLES cycles a step).  The step as the workload states it: the far field's
     z-contraction on the tensor cores (four-term BF16 splits, FP32 accumulation
     in tensor memory).  Scheduled like the 2D headline: four plans of four
     directions each, every plan on its own CUDA stream and host thread (the
