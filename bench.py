@@ -77,6 +77,8 @@ TILES_FINE_DRAM_BYTES = 0.731e6
 # caps of 6, 8, 10, 12 gave 648, 664, 682, 682 maps/s with the same cycle
 # counts (18, 24, 28, 27) and fewer steps.
 INNER_CYCLES = 10
+# concurrent plans (streams and host threads) sharing the 3D step's directions
+GROUPS_3D = 4
 
 
 def _cases(precision, ks=None, inner=INNER_CYCLES, adaptive=False, refine_fp64=False):
@@ -701,7 +703,7 @@ def measure_3d(csff, torch, dev, stream, flush):
     c = W.big_3d(n=257, n_rhs=16)
     c["opts"].update(precision="mixed", refine_fp64=1, inner_cycles=INNER_CYCLES, adaptive_inner=1)
     nr, na = c["eta"].shape[0], c["alphas"].shape[0]
-    G = 4
+    G = GROUPS_3D
     streams = [torch.cuda.Stream(device=dev) for _ in range(G)]
     plans = [csff.Plan(c["problem"], c["opts"], stream=st) for st in streams]
     N = plans[0].N
