@@ -321,23 +321,11 @@ constexpr int DKB = 32;
 
 struct df { float hi, lo; };
 
-// split x (|x| <= 2) into hi + lo
-// s += a * b  (double-float; s kept unnormalised: hi via TwoSum, lo collects errors)
-__device__ __forceinline__ void df_mac(df& s, df a, df b) {
-  float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);          // exact error of the leading product
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  float t = s.hi + p;                      // TwoSum(s.hi, p)
-  float v = t - s.hi;
-  float err = (s.hi - (t - v)) + (p - v);
-  s.hi = t;
-  s.lo += err + e;
-}
-
-// Two df_mac at once on the packed two-lane FP32 instructions: lane j holds
-// the running sum of output j; the same operations in the same order, each
-// rounded per lane as the scalar form rounds it.
+// s += a * b in double-float for two sums at once (lane j of every pair holds
+// sum j; one packed two-lane FP32 instruction per step, rounded per lane):
+// the leading product p = a.hi b.hi and its exact error by FMA plus the cross
+// terms a.hi b.lo + a.lo b.hi; s.hi + p by TwoSum (Knuth), whose error and the
+// product's error collect in s.lo (s kept unnormalised).
 __device__ __forceinline__ void df_mac2(float2& sh, float2& sl, float2 ah, float2 al, float2 bh, float2 bl) {
   const float2 m1 = make_float2(-1.f, -1.f);
   const float2 p = __fmul2_rn(ah, bh);
