@@ -103,11 +103,13 @@ typedef struct csff_opts {
   int krylov_m;       /* GMRES smoother: Krylov dimension m of each GMRES(m)
                          smoothing step, 1..4 (0 selects 3); nu1 / nu2 count
                          GMRES(m) steps.  Ignored by the other smoothers. */
-  int adaptive_inner; /* MIXED without a learned smoother: 1 = after each
-                         refinement step, the next runs only the FP32 cycles
-                         that the step's per-cycle reduction factor predicts
-                         are needed to reach rel_tol (at most inner_cycles);
-                         0 = always inner_cycles.  Same stopping test either way. */
+  int adaptive_inner; /* MIXED: 1 = after each refinement step, the next runs
+                         only the FP32 cycles that the step's per-cycle
+                         reduction factor predicts are needed to reach rel_tol
+                         (at most inner_cycles); 0 = always inner_cycles.  Same
+                         stopping test either way.  A learned smoother's
+                         fallback then compares factors per inner_cycles
+                         cycles. */
   int refine_fp64;    /* MIXED: 0 = the outer residual and update in double-float
                          (pairs of FP32 words, about 48 bits, on the FP32 pipes);
                          1 = in FP64 (r = b - A u, 2^-e r rounded to FP32 for the
@@ -391,8 +393,10 @@ csff_status csff_net_train_step3(csff_net* net, int B, int Z, int H, int W, cons
    refinement steps of each solve run plain red-black sweeps; the second sets
    the reference reduction factor f = min(its factor, guard); a later learned step
    that reduces the residual by less than f turns the learned step off for the
-   rest of that solve (csff_info.flags bit 1).  The plan keeps a pointer to
-   the net; the net must outlive the attachment. */
+   rest of that solve (csff_info.flags bit 1); with adaptive_inner the
+   factors are taken per inner_cycles cycles, f^(inner_cycles / cycles of the
+   step).  The plan keeps a pointer to the net; the net must outlive the
+   attachment. */
 csff_status csff_plan_set_learned(csff_plan* plan, csff_net* net, int levels, double guard);
 /* Use net (NULL: the plan's network again) for the learned step on one level
    0 <= level < levels of the last csff_plan_set_learned.  In units of h^2 a
@@ -457,9 +461,8 @@ csff_status csff_batch_set_tiles(csff_batch* batch, int tc_big, int ctas_per_sm)
    second's reduction factor, capped at guard, is the reference; an instance
    whose learned step reduces the residual less than the reference runs plain
    cycles for the rest of its solve (info.flags bit 1; bit 0 = a network was
-   set).  With a network the cycles per step stay at inner_cycles (the
-   adaptive schedule is off, as in the single-problem solve).  net = NULL
-   removes it.  Errors: CSFF_ERR_INVALID_ARG (guard <= 0, or the network's
+   set); with adaptive_inner the factors are taken per inner_cycles cycles, as
+   in the single-problem solve.  net = NULL removes it.  Errors: CSFF_ERR_INVALID_ARG (guard <= 0, or the network's
    shared memory does not fit beside the tiles'). */
 csff_status csff_batch_set_learned(csff_batch* batch, csff_net* net, double guard);
 

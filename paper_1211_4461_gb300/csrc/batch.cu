@@ -300,7 +300,8 @@ __device__ void ph_finish(const BArgs& A, int i, bool initial, double* shd) {
   if (A.net_wb) {
     // the learned step: off for the first two refinement steps, the second's
     // factor is the reference; a learned step that reduces less turns it off
-    const double factor = rel / rel_before;
+    // (factors of steps of inner cycles: the adaptive schedule's steps differ)
+    const double factor = ran == A.inner ? rel / rel_before : pow(rel / rel_before, (double)A.inner / ran);
     if (S.refinements <= 2) {
       if (S.refinements == 2) {
         S.lref = fmin(factor, A.guard);
@@ -314,7 +315,7 @@ __device__ void ph_finish(const BArgs& A, int i, bool initial, double* shd) {
   if (status >= 0) {
     S.status = status;
     S.done = 1;
-  } else if (A.adaptive && !A.net_wb) {
+  } else if (A.adaptive) {
     S.n_step = refinement_cycles(rel_before, rel, ran, A.rel_tol, A.inner);
   }
 }

@@ -592,7 +592,7 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
   // runs and, with the FP64 refinement, on the right-hand side's exponent (the
   // prescale of its norm)
   const long long key0 = r64 ? (3ll << 40) + (long long)(eb + 8192) * 4096 : 2ll << 40;
-  const bool adaptive = P->opts.adaptive_inner != 0 && P->net == nullptr;
+  const bool adaptive = P->opts.adaptive_inner != 0;
   int n = inner;
   // with a learned smoother the first two refinement steps run plain
   // red-black sweeps and the second sets the reference factor; a later learned
@@ -634,7 +634,9 @@ csff_status solve_mixed(csff_plan* P, int eb, double nb, csff_info* info, const 
     cycles += n_step;
     ++refinements;
     const double rel = P->red_host[0] / nbs;
-    const double factor = rel / prev;
+    // the learned step's comparisons use the reduction of a step of inner
+    // cycles (steps of the adaptive schedule differ in length)
+    const double factor = n_step == inner ? rel / prev : std::pow(rel / prev, (double)inner / n_step);
     if (P->net && refinements <= 2) {
       // two plain steps: the second one's factor is the reference
       if (refinements == 2) {

@@ -149,6 +149,13 @@ def test_learned_smoother_in_the_solve(csff, trained):
         assert lrn[0]["flags"] & 1
         assert lrn[0]["cycles"] <= base[0]["cycles"] + 3
         plan.close()
+        # the adaptive schedule with the learned step
+        pa = csff.Plan(prob, dict(OPTS, precision="mixed", inner_cycles=6, adaptive_inner=1, refine_fp64=1))
+        pa.set_learned(net, levels=1)
+        ua = torch.zeros_like(u)
+        st, la = pa.solve(np.atleast_2d(eta), ua)
+        assert st == csff.OK and la[0]["rel_res"] <= 1e-8 and la[0]["flags"] & 1
+        pa.close()
 
 
 def test_batched_learned_solve(csff, trained):
@@ -192,6 +199,19 @@ def test_batched_learned_solve(csff, trained):
     assert all(x["flags"] == 0 for x in again)
     bad.close()
     b.close()
+    # with the adaptive schedule (steps of up to six cycles sized from the last
+    # step's factor; the fallback compares factors per six cycles)
+    ba = csff.Batch([p for p, _ in probs], dict(opts, inner_cycles=6, adaptive_inner=1))
+    ba.set_learned(net)
+    st, ad = ba.solve(eta)
+    assert st == csff.OK
+    for i, (pr, e) in enumerate(probs):
+        assert ad[i]["rel_res"] <= 1e-8 and ad[i]["flags"] & 1
+        p = O.problem_from_dict(pr)
+        rhs = O.rhs(p, e)
+        u = ba.solution(i).cpu().numpy().reshape((p.m, p.m))
+        assert O.norm2(O.residual(O.make_level(p, p.n), u, rhs)) <= 1.01e-8 * O.norm2(rhs)
+    ba.close()
 
 
 def test_level_specific_networks(csff, trained):
