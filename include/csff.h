@@ -363,6 +363,10 @@ csff_status csff_net_set_weights(csff_net* net, const float* w_host);   /* reset
 csff_status csff_net_get_weights(const csff_net* net, float* w_host);
 /* y_dev = N(r_dev) for B patches of H x W (c64 each, device). */
 csff_status csff_net_forward(csff_net* net, int B, int H, int W, const void* r_dev, void* y_dev, void* stream);
+/* The same forward pass over the warp-level MMA tile (mma.sync, no tensor
+   memory), the form the batched persistent kernel runs; results agree with
+   csff_net_forward to the accumulation order. */
+csff_status csff_net_forward_mma(csff_net* net, int B, int H, int W, const void* r_dev, void* y_dev, void* stream);
 /* Loss and FP32 weight gradient of a batch: r_dev, q_dev c64 [B][H][W];
    c_host: B complex constants (re, im); grad_host: 2880 floats or NULL. */
 csff_status csff_net_loss_grad(csff_net* net, int B, int H, int W, const void* r_dev, const void* q_dev,

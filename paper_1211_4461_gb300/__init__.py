@@ -129,6 +129,7 @@ _SIGS = {
     "csff_net_set_weights": (_i, [_vp, _fp]),
     "csff_net_get_weights": (_i, [_vp, _fp]),
     "csff_net_forward": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
+    "csff_net_forward_mma": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
     "csff_net_loss_grad": (_i, [_vp, _i, _i, _i, _vp, _vp, _dp, _i, _fp, _fp, _vp]),
     "csff_net_train_step": (_i, [_vp, _i, _i, _i, _vp, _vp, _dp, _i, C.c_float, _fp, _vp]),
     "csff_plan_set_learned": (_i, [_vp, _vp, _i, _d]),
@@ -375,6 +376,13 @@ class Net:
             B, Z, H, W = r.shape
             _check(_lib.csff_net_forward3(self._h, B, Z, H, W, _ptr(r), _ptr(y), _stream_handle(stream)),
                    "net_forward3")
+
+    def forward_mma(self, r, y, stream=None):
+        """The 2D forward pass over the warp-level MMA tile (the batched
+        kernel's form); r, y: complex64 CUDA tensors of shape (B, H, W)."""
+        B, H, W = r.shape
+        _check(_lib.csff_net_forward_mma(self._h, B, H, W, _ptr(r), _ptr(y), _stream_handle(stream)),
+               "net_forward_mma")
 
     def loss_grad(self, r, q, c, margin=4, stream=None):
         cc, cp = _dbl(np.stack([np.real(c), np.imag(c)], axis=1).ravel())

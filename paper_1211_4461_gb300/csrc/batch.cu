@@ -372,11 +372,12 @@ __device__ nettile::Tile net_item(const BArgs& A, int it, float* scale) {
 // the learned step, u += N(h^2 r); the next tile's input is loaded while the
 // current tile's MMAs run.  Kept out of line: the kernel body stays small
 // enough for every host build of the compiler.
-__device__ __noinline__ bool ph_net(const BArgs& A, int c, nettile::Ctx& nc) {
+__device__ __noinline__ bool ph_net(const BArgs& A, int c, nettile::mmat::Ctx& nc) {
   const int total = A.off_net[A.n_inst];
   int it = next_net_item(A, c, blockIdx.x);
   if (it >= total) return true;
-  nettile::zero_planes(nc);
+  for (int i = threadIdx.x; i < nettile::PLANES_BYTES / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(nc.planes)[i] = make_uint4(0, 0, 0, 0);
   __syncthreads();
   float2 xr[nettile::SPT];
   float scale = 1.f, next_scale = 1.f;
@@ -385,7 +386,7 @@ __device__ __noinline__ bool ph_net(const BArgs& A, int c, nettile::Ctx& nc) {
   while (it < total) {
     const int nxt = next_net_item(A, c, it + gridDim.x);
     const nettile::Tile next = net_item(A, nxt < total ? nxt : it, &next_scale);
-    if (!nettile::run_tile(nc, cur, xr, scale, 1, A.err, nxt < total ? &next : nullptr)) return false;
+    if (!nettile::mmat::run_tile(nc, cur, xr, scale, 1, nxt < total ? &next : nullptr)) return false;
     cur = next;
     scale = next_scale;
     it = nxt;
@@ -425,7 +426,7 @@ __device__ void ph_up(const BInst& I, int l, int t, unsigned char* smem) {
 }
 
 template <bool LEARNED>
-__device__ __forceinline__ void batch_body(const BArgs& A, unsigned char* smem, double* shd, nettile::Ctx& nc) {
+__device__ __forceinline__ void batch_body(const BArgs& A, unsigned char* smem, double* shd, nettile::mmat::Ctx& nc) {
   const int n = A.n_inst;
   const int npts = A.off_pts[n];
   // ---- initial residual r = b (u = 0) and its norm
@@ -507,19 +508,17 @@ __device__ __forceinline__ void batch_body(const BArgs& A, unsigned char* smem, 
 // at most 85 registers a thread, so that three CTAs fit on an SM (the
 // autotuner picks between one and the occupancy maximum).  LEARNED: the
 // learned step ends every cycle; each CTA holds the network's weight operands
-// and 128 columns of tensor memory for the whole launch, and the activation
-// planes share the tiles' shared memory.  The two forms are separate kernels:
-// the occupancy calculation, which bounds a cooperative launch, admits one CTA
-// per SM for any kernel with tensor-memory instructions, so the classical form
-// carries none.
+// for the whole launch, and the activation planes share the tiles' shared
+// memory.  The network runs on the warp-level MMA instructions: the occupancy
+// calculation, which bounds a cooperative launch, admits one CTA per SM for any
+// kernel with tensor-memory instructions.
 template <bool LEARNED>
 __global__ void __launch_bounds__(256, 3) k_batch_solve(BArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double shd[8];
-  nettile::Ctx nc;
-  if constexpr (LEARNED) nettile::setup(nc, smem, smem + A.net_off, A.net_wb);
+  nettile::mmat::Ctx nc;
+  if constexpr (LEARNED) nettile::mmat::setup(nc, smem, smem + A.net_off, A.net_wb);
   batch_body<LEARNED>(A, smem, shd, nc);
-  if constexpr (LEARNED) nettile::teardown(nc);
 }
 
 __global__ void k_batch_init(BState* st, int n, unsigned* bar, int* err) {

@@ -837,6 +837,30 @@ __global__ void k3_wgrad(Geom3 g, const void* __restrict__ in, const void* __res
   }
 }
 
+// the same over the warp-level MMA tile (the variant the batched kernel runs)
+__global__ void __launch_bounds__(nettile::NT, NET_CTAS_PER_SM)
+    k_net_fused_mma(Geom g, const float2* __restrict__ x, float scale, const __nv_bfloat16* __restrict__ wb,
+                    float2* __restrict__ y, int accumulate) {
+  using namespace nettile;
+  extern __shared__ __align__(128) unsigned char fsm_raw[];
+  unsigned char* base = fsm_raw + ((128 - (saddr(fsm_raw) & 127)) & 127);
+  mmat::Ctx c;
+  mmat::setup(c, base, base + PLANES_BYTES, wb);
+  for (int i = threadIdx.x; i < PLANES_BYTES / 16; i += blockDim.x) reinterpret_cast<uint4*>(base)[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  const int tiles_x = (g.W + TW - 1) / TW, tiles_y = (g.H + TH - 1) / TH;
+  const long long ntiles = (long long)g.B * tiles_x * tiles_y;
+  float2 xr[SPT];
+  Tile cur = net_tile_of(g, x, y, tiles_x, tiles_y, blockIdx.x);
+  if (blockIdx.x < ntiles) load_x(cur, xr);
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long nt = t + gridDim.x;
+    const Tile next = net_tile_of(g, x, y, tiles_x, tiles_y, nt < ntiles ? nt : t);
+    mmat::run_tile(c, cur, xr, scale, accumulate, nt < ntiles ? &next : nullptr);
+    cur = next;
+  }
+}
+
 __global__ void k_to_bf16(const float* w, __nv_bfloat16* wb, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) wb[i] = __float2bfloat16(w[i]);
@@ -1021,6 +1045,23 @@ csff_status adam_step(csff_net* N, float lr, cudaStream_t s) {
   return CSFF_OK;
 }
 
+// the same with the warp-level MMA tile
+csff_status forward_mma(csff_net* N, csff::Geom g, const float2* r, float2* y, cudaStream_t s) {
+  using namespace csff;
+  const long long np = g.npix();
+  const long long ntiles =
+      (long long)g.B * ((g.W + nettile::TW - 1) / nettile::TW) * ((g.H + nettile::TH - 1) / nettile::TH);
+  NK(cudaFuncSetAttribute(k_net_fused_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, NET_SMEM), "net attribute");
+  const unsigned grid = (unsigned)std::min<long long>(ntiles, 152 * NET_CTAS_PER_SM);
+  {
+    ProfScope ps(PF_MG32, s, 16.0 * np, 2.0 * 9 * (2 * 16 + 16 * 16 + 16 * 2) * np);
+    k_net_fused_mma<<<grid, nettile::NT, NET_SMEM, s>>>(g, r, 1.f, N->wb, y, 0);
+  }
+  count_launch();
+  NK(cudaGetLastError(), "net forward");
+  return CSFF_OK;
+}
+
 // loss and weight gradient (into N->grad) for a batch of patches
 csff_status loss_grad(csff_net* N, csff::Geom g, const float2* r, const float2* q, const double* c_host, int margin,
                       float* loss_host, cudaStream_t s) {
@@ -1138,6 +1179,17 @@ csff_status csff_net_forward(csff_net* N, int B, int H, int W, const void* r_dev
   if (s != CSFF_OK) return s;
   NK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
   return csff::net_check(N);
+}
+
+csff_status csff_net_forward_mma(csff_net* N, int B, int H, int W, const void* r_dev, void* y_dev, void* stream) {
+  if (!N || !r_dev || !y_dev || B < 1 || H < 1 || W < 1) return ninvalid("bad forward arguments");
+  if (N->dim != 2) return ninvalid("a 3D network has no warp-level MMA variant");
+  csff::Geom g{B, H, W};
+  if (g.npix() >= (1ll << 31)) return ninvalid("more than 2^31 pixels");
+  csff_status s = forward_mma(N, g, (const float2*)r_dev, (float2*)y_dev, (cudaStream_t)stream);
+  if (s != CSFF_OK) return s;
+  NK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
+  return CSFF_OK;
 }
 
 csff_status csff_net_loss_grad(csff_net* N, int B, int H, int W, const void* r_dev, const void* q_dev,

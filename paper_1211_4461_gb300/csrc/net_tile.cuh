@@ -1,7 +1,8 @@
 // The learned smoother's network (bias-free 3x3 convolutions 2 -> 16 -> 16 -> 2,
 // ReLU between layers, BF16 weights and activations, FP32 accumulation) for
 // inference, its three layers fused per output tile in shared memory on the
-// tensor cores.  Used by the stand-alone inference kernel and by the batched
+// tensor cores.  run_tile (tcgen05, tensor memory) serves the stand-alone
+// inference kernel; mmat::run_tile (warp-level mma.sync) the batched
 // persistent solve.
 //
 // An output tile of TW x TH pixels needs layer-2 activations on a one-pixel
@@ -358,5 +359,179 @@ static __device__ __forceinline__ bool run_tile(Ctx& c, const Tile& T, float2 (&
   return true;
 }
 
+// ---- The same tile on the warp-level tensor-core instructions (mma.sync) -----
+// For kernels that must not contain tensor-memory instructions: a cooperative
+// launch is sized by an occupancy calculation that admits one CTA per SM for
+// any kernel with them (the batched persistent kernel).  Same planes, input
+// entries, regions and results as run_tile (accumulation order aside); the
+// weight operands sit in shared memory as [operand][n][k] rows of 32 bytes.
+// Warp w computes rows 16 w .. 16 w + 15 of every 128-row block with
+// m16n8k16 BF16 MMAs: the A fragment of a tap is read by ldmatrix from the
+// shifted rows of the two planes (16-byte rows, any row offset), the B
+// fragment from the weight rows; accumulators stay in registers and the
+// epilogues store from them.  No asynchronous proxy and no waits are involved.
+namespace mmat {
+
+__device__ __forceinline__ void ldm_x4(uint32_t addr, uint32_t (&a)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldm_x2(uint32_t addr, uint32_t (&b)[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(b[0]), "=r"(b[1]) : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+struct Ctx {
+  unsigned char* planes;
+  uint32_t splanes, sw;
+};
+
+// all threads: the weight operands in wreg ([operand t][n][k], 512 bytes each,
+// the same 20 operands as the tensor-memory path)
+__device__ inline void setup(Ctx& c, unsigned char* planes, unsigned char* wreg, const __nv_bfloat16* __restrict__ wb) {
+  c.planes = planes;
+  c.splanes = saddr(planes);
+  c.sw = saddr(wreg);
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int i = threadIdx.x; i < 20 * 256; i += blockDim.x) {
+    const int t = i >> 8, n = (i >> 4) & 15, k = i & 15;
+    __nv_bfloat16 v = zero;
+    if (t < 2) {
+      const int grp = k >> 3, e = k & 7;
+      const int dy = (t == 0) ? grp - 1 : grp + 1;
+      if (e < 6 && dy <= 1) v = wb[(n * 2 + (e & 1)) * 9 + (dy + 1) * 3 + (e >> 1)];
+    } else if (t < 11) {
+      v = wb[NW1 + (n * 16 + k) * 9 + (t - 2)];
+    } else if (n < 2) {
+      v = wb[NW1 + NW2 + (n * 16 + k) * 9 + (t - 11)];
+    }
+    *reinterpret_cast<__nv_bfloat16*>(wreg + t * 512 + n * 32 + k * 2) = v;
+  }
+  __syncthreads();
+}
+
+// B fragment of operand t, n-half h (lanes 0-15 give the row addresses)
+__device__ __forceinline__ void load_b(const Ctx& c, int t, int h, int lane, uint32_t (&b)[2]) {
+  ldm_x2(c.sw + t * 512 + (8 * h + (lane & 7)) * 32 + ((lane >> 3) & 1) * 16, b);
+}
+
+// hidden layer's epilogue from the accumulators of rows r0, r0 + 8 (n-halves h)
+__device__ __forceinline__ void hidden_store(const Ctx& c, const Tile& T, int r0, int lane, const float (&acc)[2][4],
+                                             int off) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int p = r0 + 8 * s;
+    const int ry = p / RW, rx = p - ry * RW;
+    const int gy = T.gy0 + ry, gx = T.gx0 + rx;
+    const bool in = ry < RH && gy >= 0 && gy < T.H && gx >= 0 && gx < T.W;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t v = in ? bf2_relu(__float_as_uint(acc[h][2 * s]), __float_as_uint(acc[h][2 * s + 1])) : 0u;
+      *reinterpret_cast<uint32_t*>(c.planes + off + h * PLANE + p * 16 + 4 * (lane & 3)) = v;
+    }
+  }
+}
+
+// One tile, all threads (see run_tile); returns true.
+static __device__ __forceinline__ bool run_tile(const Ctx& c, const Tile& T, float2 (&xr)[SPT], float scale,
+                                               int accumulate, const Tile* next) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* stage = reinterpret_cast<float2*>(c.planes + OFF_STAGE);
+#pragma unroll
+  for (int k = 0; k < SPT; ++k)
+    if (tid + k * NT < SR) stage[tid + k * NT] = xr[k];
+  __syncthreads();
+  for (int p = tid; p < PR; p += NT) {
+    uint4 ev = make_uint4(0, 0, 0, 0);
+    if (p < R) {
+      const int ry = p / RW, rx = p - ry * RW;
+      const float2* sp = stage + ry * SW + rx;
+      ev.x = bf2(sp[0].x * scale, sp[0].y * scale);
+      ev.y = bf2(sp[1].x * scale, sp[1].y * scale);
+      ev.z = bf2(sp[2].x * scale, sp[2].y * scale);
+    }
+    *reinterpret_cast<uint4*>(c.planes + OFF_E + p * 16) = ev;
+  }
+  if (next) load_x(*next, xr);
+  __syncthreads();
+  const int lrow = lane & 15, lk = lane >= 16 ? 1 : 0;
+  // layer 1: two K16 steps, K groups (E[p - RW], E[p]) and (E[p + RW], E[p + 2 RW])
+  for (int j = 0; j < n_blocks(1); ++j) {
+    const int r0 = first_row(1) + j * 128 + 16 * warp;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      uint32_t a[4];
+      ldm_x4(c.splanes + OFF_E + (r0 + lrow + (m == 0 ? -RW : RW) + lk * RW) * 16, a);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t b[2];
+        load_b(c, m, h, lane, b);
+        mma16816(acc[h], a, b);
+      }
+    }
+    hidden_store(c, T, r0 + (lane >> 2), lane, acc, OFF_H1);
+  }
+  __syncthreads();
+  // layer 2: nine taps from the h1 planes
+  for (int j = 0; j < n_blocks(2); ++j) {
+    const int r0 = first_row(2) + j * 128 + 16 * warp;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      uint32_t a[4];
+      ldm_x4(c.splanes + OFF_H1 + lk * PLANE + (r0 + lrow + (t / 3 - 1) * RW + (t % 3 - 1)) * 16, a);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t b[2];
+        load_b(c, 2 + t, h, lane, b);
+        mma16816(acc[h], a, b);
+      }
+    }
+    hidden_store(c, T, r0 + (lane >> 2), lane, acc, OFF_H2);
+  }
+  __syncthreads();
+  // layer 3: nine taps from the h2 planes, outputs 0 and 1 of the first n-half
+  for (int j = 0; j < n_blocks(3); ++j) {
+    const int r0 = first_row(3) + j * 128 + 16 * warp;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      uint32_t a[4], b[2];
+      ldm_x4(c.splanes + OFF_H2 + lk * PLANE + (r0 + lrow + (t / 3 - 1) * RW + (t % 3 - 1)) * 16, a);
+      load_b(c, 11 + t, 0, lane, b);
+      mma16816(acc, a, b);
+    }
+    if ((lane & 3) == 0) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int p = r0 + (lane >> 2) + 8 * s;
+        const int ry = p / RW, rx = p - ry * RW;
+        const int gy = T.gy0 + ry, gx = T.gx0 + rx;
+        if (rx >= 3 && rx < RW - 3 && ry >= 3 && ry < RH - 3 && gx < T.W && gy < T.H) {
+          const long long idx = (long long)gy * T.W + gx;
+          const float a0 = acc[2 * s], a1 = acc[2 * s + 1];
+          if (accumulate) {
+            const float2 u = T.y[idx];
+            T.y[idx] = make_float2(u.x + a0, u.y + a1);
+          } else {
+            T.y[idx] = make_float2(a0, a1);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();        // the planes are reused by the next tile
+  return true;
+}
+
+}  // namespace mmat
 }  // namespace nettile
 }  // namespace csff

@@ -79,6 +79,16 @@ def test_fused_forward_over_several_ragged_tiles(csff):
         assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
         scale = np.abs(ref).max()
         assert np.abs(got - ref).max() <= 5e-2 * scale
+    # the warp-level MMA tile (the batched kernel's form) over the same patches
+    ym = torch.empty_like(y)
+    net.forward_mma(_dev(r), ym)
+    for b in range(r.shape[0]):
+        rb = _bf16(r[b].real) + 1j * _bf16(r[b].imag)
+        ref, _ = NO.forward(tb, rb)
+        got = ym[b].cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
+        assert np.abs(got - ref).max() <= 5e-2 * np.abs(ref).max()
+    assert torch.linalg.norm(ym - y).item() <= 1e-2 * torch.linalg.norm(y).item()
     # the network has no bias: a patch of zeros gives zeros
     z = torch.zeros((1, 19, 33), dtype=torch.complex64, device="cuda")
     y0 = torch.empty_like(z)
