@@ -68,17 +68,29 @@ __global__ void k_jacobi(const cx<T>* __restrict__ u, const cx<T>* __restrict__ 
 // One colour of red-black Gauss-Seidel, in place.  colour 0 (red) = even sum
 // of node indices (interior index + 1 per axis).  One thread per point of the
 // colour: x thread t of a row takes ix = 2 t + (colour + iy + iz + D) mod 2.
+// With d = 2 D c - q the point's equation (A u)_j = d u_j - c sum_nbr u = b_j
+// solved for u_j: u_j <- d^{-1} (b_j + c sum_nbr u), which reads neither q nor
+// the point's old value.
 template <typename T, int D>
-__global__ void k_rbgs(cx<T>* u, const cx<T>* __restrict__ b, const cx<T>* __restrict__ q,
-                       const cx<T>* __restrict__ dinv, cx<T> c, int m, int colour) {
+__global__ void k_rbgs(cx<T>* u, const cx<T>* __restrict__ b, const cx<T>* __restrict__ dinv, cx<T> c, int m,
+                       int colour) {
   const int iy = blockIdx.y * BY + threadIdx.y;
   const int iz = (D == 3) ? (int)blockIdx.z : 0;
   const int ix = 2 * (int)(blockIdx.x * BX + threadIdx.x) + ((colour + iy + iz + D) & 1);
   if (ix >= m || iy >= m) return;
   const long long idx = ((long long)iz * m + iy) * m + ix;
-  cx<T> uj = u[idx];
-  cx<T> rj = csub(b[idx], apply_point<T, D>(u, uj, q[idx], c, m, ix, iy, iz, idx));
-  u[idx] = cadd(uj, cmul(dinv[idx], rj));
+  using C = cx<T>;
+  C s = mk<C>(0, 0);
+  if (ix > 0) s = cadd(s, u[idx - 1]);
+  if (ix < m - 1) s = cadd(s, u[idx + 1]);
+  if (iy > 0) s = cadd(s, u[idx - m]);
+  if (iy < m - 1) s = cadd(s, u[idx + m]);
+  if (D == 3) {
+    const long long p = (long long)m * m;
+    if (iz > 0) s = cadd(s, u[idx - p]);
+    if (iz < m - 1) s = cadd(s, u[idx + p]);
+  }
+  u[idx] = cmul(dinv[idx], cadd(b[idx], cmul(c, s)));
 }
 
 // Full weighting: coarse interior P <- sum over offsets o in {-1,0,1}^d of
@@ -602,8 +614,8 @@ cudaError_t launch_rbgs(int dim, const Level& L, cx<T>* u, const cx<T>* b, cudaS
   g.x = ((L.m + 1) / 2 + BX - 1) / BX;          // one thread per point of a colour along x
   cx<T> c = mk<cx<T>>((T)L.c.x, (T)L.c.y);
   ProfScope ps(mg_family<T>(), s, 3.0 * sizeof(cx<T>) * L.N, 0);
-  CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 0);
-  CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, qtab<T>(L), dtab<T>(L), c, L.m, 1);
+  CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, dtab<T>(L), c, L.m, 0);
+  CSFF_DIM_DISPATCH(dim, k_rbgs, u, b, dtab<T>(L), c, L.m, 1);
   count_launch(2);
   return cudaGetLastError();
 }
