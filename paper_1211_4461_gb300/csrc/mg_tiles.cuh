@@ -95,6 +95,11 @@ __device__ __forceinline__ double2 xmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ float2 xscale(float2 a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 __device__ __forceinline__ double2 xscale(double2 a, double s) { return make_double2(__dmul_rn(a.x, s), __dmul_rn(a.y, s)); }
+// a + s b for a real s, one rounding per part
+__device__ __forceinline__ float2 xfma_r(float2 a, float2 b, float s) { return __ffma2_rn(b, make_float2(s, s), a); }
+__device__ __forceinline__ double2 xfma_r(double2 a, double2 b, double s) {
+  return make_double2(__fma_rn(b.x, s, a.x), __fma_rn(b.y, s, a.y));
+}
 // a + b c and a - b c as chains of fused multiply-adds (one rounding each)
 __device__ __forceinline__ float2 xfma(float2 a, float2 b, float2 c) {
   return make_float2(__fmaf_rn(b.x, c.x, __fmaf_rn(-b.y, c.y, a.x)), __fmaf_rn(b.x, c.y, __fmaf_rn(b.y, c.x, a.y)));
@@ -134,6 +139,20 @@ __device__ __forceinline__ void cp_async_zfill(void* smem_dst, const void* gsrc,
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// the same with the shared destination as a 32-bit shared-window address
+// (formed once per loop, then advanced by constants), unconditional or
+// zero-filled when !valid
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async_s(uint32_t dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(gsrc), "n"(BYTES) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_sz(uint32_t dst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(gsrc), "n"(BYTES),
+               "r"(valid ? BYTES : 0)
+               : "memory");
+}
 
 // Window of W x W fine points with origin (ox, oy) in the colour-split layout.
 //  - Iterate: the black points (window colour 1) only.  A red-black sweep
@@ -154,29 +173,37 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
     // walks the window rows an even stride apart, so a row's colour plane and
     // slot stay fixed and the shared and global addresses advance by
     // constants; every copy of the thread is in flight at once (one round trip
-    // per tile).  Points outside the interior read as zero.
+    // per tile).  Points outside the interior read as zero.  Element offsets
+    // are 32-bit: a 2D plan has at most 15 levels, so m <= 32767 and every
+    // offset (m + W) m stays below 2^31.  A tile whose window lies inside the
+    // domain copies without any per-element test.
+    constexpr int E = (int)sizeof(cx<T>);
     const int t = threadIdx.x;
     {
       // black plane: wx = 2 jj + (~wy & 1)
-      constexpr int RS = (NT / HS) & ~1;
+      constexpr int RS = (NT / HS) & ~1, NK = (W + RS - 1) / RS;
+      constexpr uint32_t DSTEP = RS * HS * E;
       const int r0 = t / HS, jj = t - r0 * HS;
       const int wx = 2 * jj + ((r0 & 1) ^ 1);
       if (r0 < RS && wx < W) {
-        const int fx = ox + wx;
-        const bool xin = !zero_u && fx >= 0 && fx < m;
-        cx<T>* dst = U + PL + r0 * HS + jj;
-        const cx<T>* src = u_in + (long long)(oy + r0) * m + fx;
-        const long long step = (long long)RS * m;
+        const int fx = ox + wx, gstep = RS * m;
+        const uint32_t dst = smem_addr(U + PL + r0 * HS + jj);
+        const int g = (oy + r0) * m + fx;
+        if (inner && !zero_u) {
 #pragma unroll
-        for (int k = 0; k < (W + RS - 1) / RS; ++k) {
-          const int wy = r0 + k * RS;
-          if (wy < W) {
-            const int fy = oy + wy;
-            const bool in = xin && (inner || (fy >= 0 && fy < m));
-            cp_async_zfill<sizeof(cx<T>)>(dst, in ? src : u_in, in);
+          for (int k = 0; k < NK; ++k)
+            if (r0 + k * RS < W) cp_async_s<E>(dst + k * DSTEP, u_in + (g + k * gstep));
+        } else {
+          const bool xin = !zero_u && fx >= 0 && fx < m;
+#pragma unroll
+          for (int k = 0; k < NK; ++k) {
+            const int wy = r0 + k * RS;
+            if (wy < W) {
+              const int fy = oy + wy;
+              const bool in = xin && fy >= 0 && fy < m;
+              cp_async_sz<E>(dst + k * DSTEP, u_in + (in ? g + k * gstep : 0), in);
+            }
           }
-          dst += RS * HS;
-          src += step;
         }
       }
     }
@@ -188,26 +215,56 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
       }
     {
       // right-hand side (FP64: and 1/d) on window [1, W-2]^2
-      constexpr int RS = (NT / WI) & ~1;
+      constexpr int RS = (NT / WI) & ~1, NK = (WI + RS - 1) / RS;
+      constexpr uint32_t DSTEP = RS * HS * E;
       const int r1 = t / WI, c1 = t - r1 * WI;
       if (r1 < RS) {
         const int wx = 1 + c1, wy0 = 1 + r1;
-        const int fx = ox + wx;
-        const bool xin = fx >= 0 && fx < m;
-        int d = rbi<W>(wx, wy0);
-        const long long g0 = (long long)(oy + wy0) * m + fx, step = (long long)RS * m;
+        const int fx = ox + wx, gstep = RS * m;
+        const int d = rbi<W>(wx, wy0);
+        const uint32_t dB = smem_addr(B + d), dX = smem_addr(X + d);
+        const int g = (oy + wy0) * m + fx;
+        if (inner) {
 #pragma unroll
-        for (int k = 0; k < (WI + RS - 1) / RS; ++k) {
-          const int wy = wy0 + k * RS;
-          if (wy <= WI) {
-            const int fy = oy + wy;
-            const bool in = xin && (inner || (fy >= 0 && fy < m));
-            const long long g = in ? g0 + k * step : 0;
-            cp_async_zfill<sizeof(cx<T>)>(B + d, b + g, in);
-            if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + d, K.dinv + g, in);
+          for (int k = 0; k < NK; ++k)
+            if (wy0 + k * RS <= WI) {
+              cp_async_s<E>(dB + k * DSTEP, b + (g + k * gstep));
+              if constexpr (!formed_coef<T>()) cp_async_s<E>(dX + k * DSTEP, K.dinv + (g + k * gstep));
+            }
+        } else {
+          const bool xin = fx >= 0 && fx < m;
+#pragma unroll
+          for (int k = 0; k < NK; ++k) {
+            const int wy = wy0 + k * RS;
+            if (wy <= WI) {
+              const int fy = oy + wy;
+              const bool in = xin && fy >= 0 && fy < m;
+              const int gk = in ? g + k * gstep : 0;
+              cp_async_sz<E>(dB + k * DSTEP, b + gk, in);
+              if constexpr (!formed_coef<T>()) cp_async_sz<E>(dX + k * DSTEP, K.dinv + gk, in);
+            }
           }
-          d += RS * HS;
         }
+      }
+    }
+    if constexpr (formed_coef<T>()) {
+      // factor windows: X_g at wx = 2 j + o in slot o HS + j, then Y_g along wy
+      constexpr int FW = RB<W>::FACTOR;
+      for (int i = t; i < K.ng * FW; i += NT) {
+        const int gg = i / FW, r = i - gg * FW;
+        int f;
+        bool in;
+        if (r < 2 * HS) {
+          const int o = r >= HS ? 1 : 0;
+          const int fx = ox + 2 * (r - o * HS) + o;
+          in = fx >= 0 && fx < m;
+          f = (gg * 2) * m + fx;
+        } else {
+          const int fy = oy + r - 2 * HS;
+          in = fy >= 0 && fy < m;
+          f = (gg * 2 + 1) * m + fy;
+        }
+        cp_async_sz<E>(smem_addr(X + i), K.fac + (in ? f : 0), in);
       }
     }
   } else
@@ -244,7 +301,7 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
     }
   }
   }
-  if constexpr (formed_coef<T>()) {
+  if constexpr (COH && formed_coef<T>()) {
     constexpr int FW = RB<W>::FACTOR;
     for (int i = threadIdx.x; i < K.ng * FW; i += NT) {
       const int g = i / FW, r = i - g * FW;
@@ -454,7 +511,9 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
   for (int i = threadIdx.x; i < EW * EW; i += NT) {
     int wy = i / EW, wx = i - wy * EW;
     int cxp = ex0 + wx, cyp = ey0 + wy;
-    E[i] = (cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc) ? ld<COH>(ec + (long long)cyp * mc + cxp) : zero_c<T>();
+    const bool in = cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc;
+    if constexpr (COH) E[i] = in ? ld<COH>(ec + (long long)cyp * mc + cxp) : zero_c<T>();
+    else cp_async_sz<(int)sizeof(C)>(smem_addr(E + i), ec + (in ? cyp * mc + cxp : 0), in);   // waited for by load_window
   }
   load_window<T, UW, COH>(ox, oy, m, u_in, false, b, K, U, B, X);
   __syncthreads();
@@ -464,14 +523,27 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
   // between coarse-window columns j and j+1 of row (wy+1)/2, in even rows (iy
   // odd) between rows wy/2 and wy/2+1 of column j+1.  The coarse window is
   // zero outside the coarse interior, so points outside the domain stay zero.
+  // Each thread takes slot column j of the black plane and rows an even
+  // stride apart, so the row parity, the coarse neighbours' layout and every
+  // address step are fixed for the thread.  u + (e0 + e1)/2 as one fused
+  // multiply-add: the halving is exact, so this rounds like u + e0/2 + e1/2
+  // summed as (e0/2 + e1/2) first.
   {
     constexpr int HS = RB<UW>::HS, PL = RB<UW>::PLANE;
-    for (int i = threadIdx.x; i < UW * HS; i += NT) {
-      const int wy = i / HS, j = i - wy * HS;
-      if (2 * j + ((wy & 1) ^ 1) >= UW) continue;
-      const C* e = (wy & 1) ? E + ((wy + 1) >> 1) * EW + j : E + (wy >> 1) * EW + j + 1;
-      const C e1 = (wy & 1) ? e[1] : e[EW];
-      U[PL + i] = xadd(U[PL + i], xadd(xscale(e[0], (T)0.5), xscale(e1, (T)0.5)));
+    constexpr int RS = (NT / HS) & ~1, NK = (UW + RS - 1) / RS;
+    const int r0 = threadIdx.x / HS, j = threadIdx.x - r0 * HS;
+    const bool odd = r0 & 1;
+    if (r0 < RS && 2 * j + (odd ? 0 : 1) < UW) {
+      const C* e = odd ? E + ((r0 + 1) >> 1) * EW + j : E + (r0 >> 1) * EW + j + 1;
+      const int e1 = odd ? 1 : EW;
+      C* uu = U + PL + r0 * HS + j;
+#pragma unroll
+      for (int k = 0; k < NK; ++k) {
+        if (r0 + k * RS < UW) {
+          const C* ek = e + k * (RS / 2) * EW;
+          uu[k * RS * HS] = xfma_r(uu[k * RS * HS], xadd(ek[0], ek[e1]), (T)0.5);
+        }
+      }
     }
   }
   __syncthreads();
