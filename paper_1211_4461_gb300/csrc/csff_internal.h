@@ -34,15 +34,21 @@ template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C
 
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch: a kernel launched with launch_pdl is set up
-// while its predecessor in the stream runs, and starts as the predecessor's
-// CTAs retire (each CTA triggers its dependents implicitly when it exits; an
-// explicit trigger at kernel start measured slower on the 1025^2 solves).
-// Every such kernel begins with pdl_prologue(), which waits
-// until the predecessor has completed and its writes are visible; launched
-// the ordinary way, the wait is a no-op.
+// while its predecessor in the stream runs, and starts once every CTA of the
+// predecessor has triggered its dependents (pdl_trigger) or exited.  The
+// fused tiles trigger as they enter their last phase, so the next kernel's
+// CTAs take the slots of retiring tiles; an explicit trigger at kernel start
+// measured slower on the 1025^2 solves (early CTAs hold slots the
+// predecessor's later waves need).  Every such kernel calls pdl_prologue(),
+// which waits until the predecessor has completed and its writes are
+// visible, before it touches anything the predecessor writes (the up tile
+// first copies its iterate, right-hand side and factor windows, written by
+// kernels that completed before the predecessor passed its own wait);
+// launched the ordinary way, both are no-ops.
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_prologue() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 #endif
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(NT, tile_min_ctas<T, TC>()) k_up2(const cx<T>*
                                             const cx<T>* __restrict__ b, const tiles::LevelCoef<T> K, cx<T> c,
                                             int m, int mc, cx<T>* __restrict__ u_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_prologue();
+  // the tile waits for its predecessor itself, after its window copies
   tiles::up_tile<T, TC, false, G1>(blockIdx.x * TC, blockIdx.y * TC, u_in, ec, b, K, c, m, mc, u_out, smem_raw);
 }
 

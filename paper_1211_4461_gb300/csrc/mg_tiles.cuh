@@ -162,7 +162,7 @@ __device__ __forceinline__ void cp_async_sz(uint32_t dst, const void* gsrc, bool
 //  - RHS (FP64: and 1/d) on window [1, W-2]^2, the points the sweeps update.
 //  - FP32: per Gaussian X_g at wx = 2 j + o in slot o HS + j, then Y_g along wy.
 // Points outside the interior read as zero.
-template <typename T, int W, bool COH>
+template <typename T, int W, bool COH, bool WAIT = true>
 __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* u_in, bool zero_u,
                                             const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
                                             cx<T>* X) {
@@ -317,7 +317,7 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
       X[i] = v;
     }
   }
-  if constexpr (!COH) cp_async_wait_all();
+  if constexpr (!COH && WAIT) cp_async_wait_all();
 }
 
 // d = 4c - q = D0 - sum_g X_g Y_g (D0 = 4c - k^2) at the point in slot j
@@ -460,6 +460,7 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
   // equations with the final red values.
   rb_pass<T, DW, 0, 3, 3 + FT, true, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
+  if constexpr (!COH) pdl_trigger();
   // full weighting: coarse P has its centre fine point 2P+1 at window
   // (2p+4, 2p+4) and corners at (2p+3 | 2p+5, 2p+3 | 2p+5), all red (slots
   // p+2 and p+1, p+2); the four edge points are black, with zero residual
@@ -508,14 +509,21 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
   C* X = E + EW * EW;                    // coefficient windows
   const int ox = 2 * P0x - 2, oy = 2 * P0y - 2;
   const int ex0 = P0x - 2, ey0 = P0y - 2;
+  // per-level kernels: the window copies go out before the wait for the
+  // predecessor, which writes only the coarse correction
+  if constexpr (!COH) {
+    load_window<T, UW, COH, false>(ox, oy, m, u_in, false, b, K, U, B, X);
+    pdl_prologue();
+  }
   for (int i = threadIdx.x; i < EW * EW; i += NT) {
     int wy = i / EW, wx = i - wy * EW;
     int cxp = ex0 + wx, cyp = ey0 + wy;
     const bool in = cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc;
     if constexpr (COH) E[i] = in ? ld<COH>(ec + (long long)cyp * mc + cxp) : zero_c<T>();
-    else cp_async_sz<(int)sizeof(C)>(smem_addr(E + i), ec + (in ? cyp * mc + cxp : 0), in);   // waited for by load_window
+    else cp_async_sz<(int)sizeof(C)>(smem_addr(E + i), ec + (in ? cyp * mc + cxp : 0), in);
   }
-  load_window<T, UW, COH>(ox, oy, m, u_in, false, b, K, U, B, X);
+  if constexpr (COH) load_window<T, UW, COH>(ox, oy, m, u_in, false, b, K, U, B, X);
+  else cp_async_wait_all();
   __syncthreads();
   // prolongation at the black points only: the red half sweep overwrites the
   // red ones without reading them.  With node index i = f + 1, a black fine
@@ -551,6 +559,7 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
   __syncthreads();
   rb_pass<T, UW, 1, 2, UW - 3, false, G1>(ox, oy, m, K, c, U, B, X);
   __syncthreads();
+  if constexpr (!COH) pdl_trigger();
   const int exx = (P0x + TC >= mc) ? m : 2 * P0x + FT;
   const int eyy = (P0y + TC >= mc) ? m : 2 * P0y + FT;
   {
