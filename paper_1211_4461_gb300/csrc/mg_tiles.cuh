@@ -267,55 +267,91 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
         cp_async_sz<E>(smem_addr(X + i), K.fac + (in ? f : 0), in);
       }
     }
-  } else
-  for (int i = threadIdx.x; i < W * HS; i += NT) {         // black plane: wx = 2 j + (~wy & 1)
-    const int wy = i / HS, j = i - wy * HS;
-    const int wx = 2 * j + ((wy & 1) ^ 1);
-    if (wx >= W) continue;
-    const int fx = ox + wx, fy = oy + wy;
-    const bool in = !zero_u && (inner || (fx >= 0 && fx < m && fy >= 0 && fy < m));
-    const long long g = in ? (long long)fy * m + fx : 0;
-    if constexpr (COH) U[PL + i] = in ? ld<COH>(u_in + g) : zero_c<T>();
-    else cp_async_zfill<sizeof(cx<T>)>(U + PL + i, u_in + g, in);
-  }
-  if constexpr (COH) {
-  if (!inner)
-    for (int i = threadIdx.x; i < W * HS; i += NT) {       // red plane: wx = 2 j + (wy & 1)
-      const int wy = i / HS, j = i - wy * HS;
-      const int fx = ox + 2 * j + (wy & 1), fy = oy + wy;
-      if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[i] = zero_c<T>();
-    }
-  for (int i = threadIdx.x; i < WI * WI; i += NT) {
-    const int r = i / WI;
-    const int wy = 1 + r, wx = 1 + i - r * WI;
-    const int fx = ox + wx, fy = oy + wy;
-    const bool in = inner || (fx >= 0 && fx < m && fy >= 0 && fy < m);
-    const int d = rbi<W>(wx, wy);
-    const long long g = in ? (long long)fy * m + fx : 0;
-    if constexpr (COH) {
-      B[d] = in ? ld<COH>(b + g) : zero_c<T>();
-      if constexpr (!formed_coef<T>()) X[d] = in ? K.dinv[g] : zero_c<T>();
-    } else {
-      cp_async_zfill<sizeof(cx<T>)>(B + d, b + g, in);
-      if constexpr (!formed_coef<T>()) cp_async_zfill<sizeof(cx<T>)>(X + d, K.dinv + g, in);
-    }
-  }
-  }
-  if constexpr (COH && formed_coef<T>()) {
-    constexpr int FW = RB<W>::FACTOR;
-    for (int i = threadIdx.x; i < K.ng * FW; i += NT) {
-      const int g = i / FW, r = i - g * FW;
-      cx<T> v = zero_c<T>();
-      if (r < 2 * HS) {
-        const int o = r >= HS ? 1 : 0;
-        const int fx = ox + 2 * (r - o * HS) + o;
-        if (fx >= 0 && fx < m) v = K.fac[((size_t)g * 2) * m + fx];
-      } else {
-        const int fy = oy + r - 2 * HS;
-        if (fy >= 0 && fy < m) v = K.fac[((size_t)g * 2 + 1) * m + fy];
+  } else {
+    // The persistent kernel reads data other CTAs of the same launch wrote,
+    // through L2 (ld.cg).  The same column-per-thread walk as above; each
+    // thread issues all its loads into registers before it stores any, so a
+    // window costs one round trip, not one per element.
+    const int t = threadIdx.x;
+    constexpr int RSU = (NT / HS) & ~1, NKU = (W + RSU - 1) / RSU;
+    constexpr int RSB = (NT / WI) & ~1, NKB = (WI + RSB - 1) / RSB;
+    constexpr int FW = RB<W>::FACTOR, NKF = formed_coef<T>() ? (8 * FW + NT - 1) / NT : 0;
+    const int r0 = t / HS, jj = t - r0 * HS;
+    const int wxu = 2 * jj + ((r0 & 1) ^ 1);
+    const bool uact = r0 < RSU && wxu < W;
+    const int r1 = t / WI, c1 = t - r1 * WI;
+    const bool bact = r1 < RSB;
+    cx<T> vu[NKU], vb[NKB], vx[NKB], vf[NKF > 0 ? NKF : 1];
+    {
+      const int fx = ox + wxu;
+      const bool xin = uact && !zero_u && fx >= 0 && fx < m;
+      const int g = (oy + r0) * m + fx;
+#pragma unroll
+      for (int k = 0; k < NKU; ++k) {
+        const int wy = r0 + k * RSU, fy = oy + wy;
+        const bool in = xin && wy < W && (inner || (fy >= 0 && fy < m));
+        vu[k] = in ? ld<COH>(u_in + (g + k * RSU * m)) : zero_c<T>();
       }
-      X[i] = v;
     }
+    {
+      const int wx = 1 + c1, fx = ox + wx;
+      const bool xin = bact && fx >= 0 && fx < m;
+      const int g = (oy + 1 + r1) * m + fx;
+#pragma unroll
+      for (int k = 0; k < NKB; ++k) {
+        const int wy = 1 + r1 + k * RSB, fy = oy + wy;
+        const bool in = xin && wy <= WI && (inner || (fy >= 0 && fy < m));
+        vb[k] = in ? ld<COH>(b + (g + k * RSB * m)) : zero_c<T>();
+        if constexpr (!formed_coef<T>()) vx[k] = in ? ld<COH>(K.dinv + (g + k * RSB * m)) : zero_c<T>();
+      }
+    }
+    if constexpr (formed_coef<T>()) {
+      // factor windows (at most 8 Gaussians): X_g at wx = 2 j + o in slot
+      // o HS + j, then Y_g along wy
+#pragma unroll
+      for (int k = 0; k < NKF; ++k) {
+        const int i = t + k * NT;
+        const int gg = i / FW, r = i - gg * FW;
+        int f = 0;
+        bool in = i < K.ng * FW;
+        if (r < 2 * HS) {
+          const int o = r >= HS ? 1 : 0;
+          const int fx = ox + 2 * (r - o * HS) + o;
+          in = in && fx >= 0 && fx < m;
+          f = (gg * 2) * m + fx;
+        } else {
+          const int fy = oy + r - 2 * HS;
+          in = in && fy >= 0 && fy < m;
+          f = (gg * 2 + 1) * m + fy;
+        }
+        vf[k] = in ? ld<COH>(K.fac + f) : zero_c<T>();
+      }
+    }
+    if (uact) {
+#pragma unroll
+      for (int k = 0; k < NKU; ++k)
+        if (r0 + k * RSU < W) U[PL + (r0 + k * RSU) * HS + jj] = vu[k];
+    }
+    if (bact) {
+      const int d0 = rbi<W>(1 + c1, 1 + r1);
+#pragma unroll
+      for (int k = 0; k < NKB; ++k)
+        if (1 + r1 + k * RSB <= WI) {
+          B[d0 + k * RSB * HS] = vb[k];
+          if constexpr (!formed_coef<T>()) X[d0 + k * RSB * HS] = vx[k];
+        }
+    }
+    if constexpr (formed_coef<T>()) {
+#pragma unroll
+      for (int k = 0; k < NKF; ++k)
+        if (t + k * NT < K.ng * FW) X[t + k * NT] = vf[k];
+    }
+    if (!inner)
+      for (int i = t; i < W * HS; i += NT) {               // red plane: zero outside the domain
+        const int wy = i / HS, j = i - wy * HS;
+        const int fx = ox + 2 * j + (wy & 1), fy = oy + wy;
+        if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[i] = zero_c<T>();
+      }
   }
   if constexpr (!COH && WAIT) cp_async_wait_all();
 }
