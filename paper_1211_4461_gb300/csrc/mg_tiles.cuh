@@ -551,15 +551,27 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
     load_window<T, UW, COH, false>(ox, oy, m, u_in, false, b, K, U, B, X);
     pdl_prologue();
   }
-  for (int i = threadIdx.x; i < EW * EW; i += NT) {
-    int wy = i / EW, wx = i - wy * EW;
-    int cxp = ex0 + wx, cyp = ey0 + wy;
-    const bool in = cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc;
-    if constexpr (COH) E[i] = in ? ld<COH>(ec + (long long)cyp * mc + cxp) : zero_c<T>();
-    else cp_async_sz<(int)sizeof(C)>(smem_addr(E + i), ec + (in ? cyp * mc + cxp : 0), in);
+  // coarse window: asynchronous copies (per-level kernels) or loads held in
+  // registers across the fine window's loads (persistent kernel)
+  constexpr int NKE = (EW * EW + NT - 1) / NT;
+  C ev[NKE];
+#pragma unroll
+  for (int k = 0; k < NKE; ++k) {
+    const int i = threadIdx.x + k * NT;
+    const int wy = i / EW, wx = i - wy * EW;
+    const int cxp = ex0 + wx, cyp = ey0 + wy;
+    const bool in = i < EW * EW && cxp >= 0 && cxp < mc && cyp >= 0 && cyp < mc;
+    if constexpr (COH) ev[k] = in ? ld<COH>(ec + (cyp * mc + cxp)) : zero_c<T>();
+    else if (i < EW * EW) cp_async_sz<(int)sizeof(C)>(smem_addr(E + i), ec + (in ? cyp * mc + cxp : 0), in);
   }
-  if constexpr (COH) load_window<T, UW, COH>(ox, oy, m, u_in, false, b, K, U, B, X);
-  else cp_async_wait_all();
+  if constexpr (COH) {
+    load_window<T, UW, COH>(ox, oy, m, u_in, false, b, K, U, B, X);
+#pragma unroll
+    for (int k = 0; k < NKE; ++k)
+      if (threadIdx.x + k * NT < EW * EW) E[threadIdx.x + k * NT] = ev[k];
+  } else {
+    cp_async_wait_all();
+  }
   __syncthreads();
   // prolongation at the black points only: the red half sweep overwrites the
   // red ones without reading them.  With node index i = f + 1, a black fine
