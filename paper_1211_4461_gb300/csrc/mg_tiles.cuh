@@ -46,30 +46,48 @@ template <typename T> constexpr bool formed_coef() { return sizeof(T) == 4; }
 
 // Shared-memory windows are stored split by colour: window point (wx, wy)
 // sits in plane (wx + wy) & 1, row wy, slot wx >> 1, with HS = (W + 1) / 2
-// slots a row.  A point in slot j of its row (wx = 2 j + o) finds its four
-// neighbours in the other plane: slots j + o - 1 and j + o of the same row and
-// slot j of the rows above and below, so a warp working along a row touches
-// consecutive words.
-template <int W> struct RB {
+// slots a row, rows P elements apart and planes PLANE apart.  A point in slot
+// j of its row (wx = 2 j + o) finds its four neighbours in the other plane:
+// slots j + o - 1 and j + o of the same row and slot j of the rows above and
+// below, so a warp working along a row touches consecutive words.
+//
+// Row pitch of the FP32 down windows (ES = 8-byte elements): with P = HS the
+// thread segments of a pass, which start an even number of rows apart, land
+// on the same banks; a bank model of every pass of the tiles (each warp
+// access costs as many wavefronts as the busiest bank pair has distinct
+// words) gives 22-23 % fewer wavefronts with P = 21 for the 39-wide window
+// and P = 14 with planes one element further apart for the 23-wide one.  The
+// up windows gain nothing, and the FP64 windows stay unpadded, which keeps
+// their CTAs per SM.
+template <int W, int ES> struct RBPad {
+  static constexpr int P = (ES == 8 && W == 39) ? 21 : (ES == 8 && W == 23) ? 14 : (W + 1) / 2;
+  static constexpr int GAP = (ES == 8 && W == 23) ? 1 : 0;
+};
+template <int W, int ES = 8> struct RB {
   static constexpr int HS = (W + 1) / 2;
-  static constexpr int PLANE = W * HS;
+  static constexpr int P = RBPad<W, ES>::P;
+  static constexpr int PLANE = W * P + RBPad<W, ES>::GAP;
   static constexpr int ELEMS = 2 * PLANE;
   // factor windows of one Gaussian: X_g split by the parity of wx (2 HS), Y_g (W)
   static constexpr int FACTOR = 2 * HS + W;
 };
-template <int W> __device__ __forceinline__ int rbi(int wx, int wy) {
-  return (((wx + wy) & 1) * W + wy) * RB<W>::HS + (wx >> 1);
+template <int W, int ES> __device__ __forceinline__ int rbi(int wx, int wy) {
+  return ((wx + wy) & 1) * RB<W, ES>::PLANE + wy * RB<W, ES>::P + (wx >> 1);
 }
 
-template <int TC> __host__ __device__ constexpr int down_window() { return RB<Geo<TC>::DW>::ELEMS; }
-template <int TC> __host__ __device__ constexpr int up_window() { return RB<Geo<TC>::UW>::ELEMS; }
+template <int TC> __host__ __device__ constexpr int down_window(bool fp64) {
+  return fp64 ? RB<Geo<TC>::DW, 16>::ELEMS : RB<Geo<TC>::DW, 8>::ELEMS;
+}
+template <int TC> __host__ __device__ constexpr int up_window(bool fp64) {
+  return fp64 ? RB<Geo<TC>::UW, 16>::ELEMS : RB<Geo<TC>::UW, 8>::ELEMS;
+}
 // shared-memory elements (complex values) of one tile: iterate and RHS
 // windows, then FP32 factor windows (ng Gaussians) or the FP64 1/d window
 template <int TC> __host__ __device__ constexpr size_t down_smem_elems(int ng, bool fp64) {
-  return (size_t)(fp64 ? 3 : 2) * down_window<TC>() + (fp64 ? 0 : (size_t)ng * RB<Geo<TC>::DW>::FACTOR);
+  return (size_t)(fp64 ? 3 : 2) * down_window<TC>(fp64) + (fp64 ? 0 : (size_t)ng * RB<Geo<TC>::DW>::FACTOR);
 }
 template <int TC> __host__ __device__ constexpr size_t up_smem_elems(int ng, bool fp64) {
-  return (size_t)(fp64 ? 3 : 2) * up_window<TC>() + Geo<TC>::EW * Geo<TC>::EW +
+  return (size_t)(fp64 ? 3 : 2) * up_window<TC>(fp64) + Geo<TC>::EW * Geo<TC>::EW +
          (fp64 ? 0 : (size_t)ng * RB<Geo<TC>::UW>::FACTOR);
 }
 
@@ -166,7 +184,8 @@ template <typename T, int W, bool COH, bool WAIT = true>
 __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* u_in, bool zero_u,
                                             const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
                                             cx<T>* X) {
-  constexpr int HS = RB<W>::HS, PL = RB<W>::PLANE, WI = W - 2;
+  using L = RB<W, (int)sizeof(cx<T>)>;
+  constexpr int HS = L::HS, P = L::P, PL = L::PLANE, WI = W - 2;
   const bool inner = ox >= 0 && oy >= 0 && ox + W <= m && oy + W <= m;
   if constexpr (!COH) {
     // Per-level kernels: each thread owns one window column of each array and
@@ -182,12 +201,12 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
     {
       // black plane: wx = 2 jj + (~wy & 1)
       constexpr int RS = (NT / HS) & ~1, NK = (W + RS - 1) / RS;
-      constexpr uint32_t DSTEP = RS * HS * E;
+      constexpr uint32_t DSTEP = RS * P * E;
       const int r0 = t / HS, jj = t - r0 * HS;
       const int wx = 2 * jj + ((r0 & 1) ^ 1);
       if (r0 < RS && wx < W) {
         const int fx = ox + wx, gstep = RS * m;
-        const uint32_t dst = smem_addr(U + PL + r0 * HS + jj);
+        const uint32_t dst = smem_addr(U + PL + r0 * P + jj);
         const int g = (oy + r0) * m + fx;
         if (inner && !zero_u) {
 #pragma unroll
@@ -211,17 +230,17 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
       for (int i = t; i < W * HS; i += NT) {                 // red plane: zero outside the domain
         const int wy = i / HS, j = i - wy * HS;
         const int fx = ox + 2 * j + (wy & 1), fy = oy + wy;
-        if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[i] = zero_c<T>();
+        if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[wy * P + j] = zero_c<T>();
       }
     {
       // right-hand side (FP64: and 1/d) on window [1, W-2]^2
       constexpr int RS = (NT / WI) & ~1, NK = (WI + RS - 1) / RS;
-      constexpr uint32_t DSTEP = RS * HS * E;
+      constexpr uint32_t DSTEP = RS * P * E;
       const int r1 = t / WI, c1 = t - r1 * WI;
       if (r1 < RS) {
         const int wx = 1 + c1, wy0 = 1 + r1;
         const int fx = ox + wx, gstep = RS * m;
-        const int d = rbi<W>(wx, wy0);
+        const int d = rbi<W, E>(wx, wy0);
         const uint32_t dB = smem_addr(B + d), dX = smem_addr(X + d);
         const int g = (oy + wy0) * m + fx;
         if (inner) {
@@ -330,15 +349,15 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
     if (uact) {
 #pragma unroll
       for (int k = 0; k < NKU; ++k)
-        if (r0 + k * RSU < W) U[PL + (r0 + k * RSU) * HS + jj] = vu[k];
+        if (r0 + k * RSU < W) U[PL + (r0 + k * RSU) * P + jj] = vu[k];
     }
     if (bact) {
-      const int d0 = rbi<W>(1 + c1, 1 + r1);
+      const int d0 = rbi<W, (int)sizeof(cx<T>)>(1 + c1, 1 + r1);
 #pragma unroll
       for (int k = 0; k < NKB; ++k)
         if (1 + r1 + k * RSB <= WI) {
-          B[d0 + k * RSB * HS] = vb[k];
-          if constexpr (!formed_coef<T>()) X[d0 + k * RSB * HS] = vx[k];
+          B[d0 + k * RSB * P] = vb[k];
+          if constexpr (!formed_coef<T>()) X[d0 + k * RSB * P] = vx[k];
         }
     }
     if constexpr (formed_coef<T>()) {
@@ -350,7 +369,7 @@ __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* 
       for (int i = t; i < W * HS; i += NT) {               // red plane: zero outside the domain
         const int wy = i / HS, j = i - wy * HS;
         const int fx = ox + 2 * j + (wy & 1), fy = oy + wy;
-        if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[i] = zero_c<T>();
+        if (!(fx >= 0 && fx < m && fy >= 0 && fy < m)) U[wy * P + j] = zero_c<T>();
       }
   }
   if constexpr (!COH && WAIT) cp_async_wait_all();
@@ -394,7 +413,8 @@ __device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T
                                         cx<T>* B, const cx<T>* X) {
   using C = cx<T>;
   using S = Seg<W, HI - LO + 1>;
-  constexpr int HS = S::HS, PL = RB<W>::PLANE, RS = S::RS;
+  constexpr int HS = S::HS, RS = S::RS;
+  constexpr int P = RB<W, (int)sizeof(C)>::P, PL = RB<W, (int)sizeof(C)>::PLANE;
   constexpr int OA = (COLOUR ^ LO) & 1;          // slot parity of the segment's even rows
   static_assert(LO >= 1 && HI <= W - 2, "neighbours inside the window");
   const int t = threadIdx.x;
@@ -406,9 +426,9 @@ __device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T
   const bool okA = wxA >= LO && wxA <= HI && ox + wxA >= 0 && ox + wxA < m;
   const bool okB = wxB >= LO && wxB <= HI && ox + wxB >= 0 && ox + wxB < m;
   const bool rows_in = oy + y0 >= 0 && oy + y0 + nrows <= m;
-  const C* po = U + (1 - COLOUR) * PL + y0 * HS + j;
-  C* pc = U + COLOUR * PL + y0 * HS + j;
-  C* pb = B + COLOUR * PL + y0 * HS + j;
+  const C* po = U + (1 - COLOUR) * PL + y0 * P + j;
+  C* pc = U + COLOUR * PL + y0 * P + j;
+  C* pb = B + COLOUR * PL + y0 * P + j;
   C xA = zero_c<T>(), xB = zero_c<T>();
   if constexpr (G1 && formed_coef<T>()) {
     xA = X[OA * HS + j];
@@ -417,16 +437,16 @@ __device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T
   // formed diagonal: D0 = 4c - k^2
   C D0 = zero_c<T>();
   if constexpr (formed_coef<T>()) D0 = make_float2(__fmaf_rn(4.f, c.x, -K.k2), __fmul_rn(4.f, c.y));
-  C up = po[-HS], mid = po[0];
+  C up = po[-P], mid = po[0];
 #pragma unroll
   for (int r = 0; r < RS; ++r) {
     if (r >= nrows) break;
-    const C dn = po[(r + 1) * HS];
+    const C dn = po[(r + 1) * P];
     const int o = OA ^ (r & 1);
     bool ok = (r & 1) ? okB : okA;
     if (!rows_in) ok = ok && oy + y0 + r >= 0 && oy + y0 + r < m;
     if (ok) {
-      const C side = po[r * HS + 2 * o - 1];
+      const C side = po[r * P + 2 * o - 1];
       const C s = xadd(xadd(xadd(o ? mid : side, o ? side : mid), up), dn);
       C d;
       if constexpr (formed_coef<T>()) {
@@ -435,12 +455,12 @@ __device__ __forceinline__ void rb_pass(int ox, int oy, int m, const LevelCoef<T
       }
       if constexpr (RESID) {
         if constexpr (!formed_coef<T>()) d = xsub(xscale(c, (T)4), K.q[(long long)(oy + y0 + r) * m + ox + 2 * j + o]);
-        pb[r * HS] = xfma(xfms(pb[r * HS], d, pc[r * HS]), c, s);       // b - d u + c s
+        pb[r * P] = xfma(xfms(pb[r * P], d, pc[r * P]), c, s);          // b - d u + c s
       } else {
         C di;
         if constexpr (formed_coef<T>()) di = crecip(d);
-        else di = X[COLOUR * PL + (y0 + r) * HS + j];
-        pc[r * HS] = xmul(di, xfma(pb[r * HS], c, s));                  // d^{-1} (b + c s)
+        else di = X[COLOUR * PL + (y0 + r) * P + j];
+        pc[r * P] = xmul(di, xfma(pb[r * P], c, s));                    // d^{-1} (b + c s)
       }
     }
     up = mid;
@@ -455,7 +475,8 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
                           const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, cx<T>* bc,
                           unsigned char* smem_raw) {
   using C = cx<T>;
-  constexpr int FT = Geo<TC>::FT, DW = Geo<TC>::DW, HS = RB<DW>::HS, NW = RB<DW>::ELEMS;
+  using L = RB<Geo<TC>::DW, (int)sizeof(C)>;
+  constexpr int FT = Geo<TC>::FT, DW = Geo<TC>::DW, HS = L::HS, P = L::P, NW = L::ELEMS;
   C* U = reinterpret_cast<C*>(smem_raw);
   C* B = U + NW;                              // RHS, then the red residual in place
   C* X = B + NW;                              // coefficient windows
@@ -470,7 +491,7 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
   // owned fine points [2P0, 2P0+FT) per axis (the last tile also the final
   // index), the black ones only: the up tile of this level reads no red value
   {
-    constexpr int PL = RB<DW>::PLANE;
+    constexpr int PL = L::PLANE;
     const int ex = (P0x + TC >= mc) ? m : 2 * P0x + FT;
     const int ey = (P0y + TC >= mc) ? m : 2 * P0y + FT;
     // each thread one slot column, rows an even stride apart (fixed colour,
@@ -480,13 +501,13 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
     const int wx = 2 * j + (((r0 + 3) & 1) ^ 1);
     const int fx = ox + wx;
     if (r0 < RS && wx >= 3 && fx < ex && fx < m) {
-      const C* src = U + PL + (r0 + 3) * HS + j;
+      const C* src = U + PL + (r0 + 3) * P + j;
       cx<T>* dst = u_out + (long long)(oy + r0 + 3) * m + fx;
 #pragma unroll
       for (int k = 0; k < (FT + 1 + RS - 1) / RS; ++k) {
         const int ly = r0 + k * RS, fy = oy + ly + 3;
         if (ly <= FT && fy < ey && fy < m) *dst = *src;
-        src += RS * HS;
+        src += RS * P;
         dst += (long long)RS * m;
       }
     }
@@ -505,9 +526,9 @@ __device__ void down_tile(int P0x, int P0y, const cx<T>* u_in, int zero_init, co
     const int py = i / TC, px = i - py * TC;
     const int Px = P0x + px, Py = P0y + py;
     if (Px >= mc || Py >= mc) continue;
-    const C* r3 = R0 + (2 * py + 3) * HS + px;
-    const C* r4 = r3 + HS;
-    const C* r5 = r4 + HS;
+    const C* r3 = R0 + (2 * py + 3) * P + px;
+    const C* r4 = r3 + P;
+    const C* r5 = r4 + P;
     const C top = xadd(xscale(r3[1], (T)0.25), xscale(r3[2], (T)0.25));
     const C cen = xscale(r4[2], (T)0.5);
     const C bot = xadd(xscale(r5[1], (T)0.25), xscale(r5[2], (T)0.25));
@@ -538,7 +559,8 @@ template <typename T, int TC, bool COH, bool G1>
 __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
                         const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, unsigned char* smem_raw) {
   using C = cx<T>;
-  constexpr int FT = Geo<TC>::FT, UW = Geo<TC>::UW, EW = Geo<TC>::EW, NW = RB<UW>::ELEMS;
+  using L = RB<Geo<TC>::UW, (int)sizeof(C)>;
+  constexpr int FT = Geo<TC>::FT, UW = Geo<TC>::UW, EW = Geo<TC>::EW, NW = L::ELEMS;
   C* U = reinterpret_cast<C*>(smem_raw);
   C* B = U + NW;
   C* E = B + NW;                         // EW x EW coarse window
@@ -585,19 +607,19 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
   // multiply-add: the halving is exact, so this rounds like u + e0/2 + e1/2
   // summed as (e0/2 + e1/2) first.
   {
-    constexpr int HS = RB<UW>::HS, PL = RB<UW>::PLANE;
+    constexpr int HS = L::HS, P = L::P, PL = L::PLANE;
     constexpr int RS = (NT / HS) & ~1, NK = (UW + RS - 1) / RS;
     const int r0 = threadIdx.x / HS, j = threadIdx.x - r0 * HS;
     const bool odd = r0 & 1;
     if (r0 < RS && 2 * j + (odd ? 0 : 1) < UW) {
       const C* e = odd ? E + ((r0 + 1) >> 1) * EW + j : E + (r0 >> 1) * EW + j + 1;
       const int e1 = odd ? 1 : EW;
-      C* uu = U + PL + r0 * HS + j;
+      C* uu = U + PL + r0 * P + j;
 #pragma unroll
       for (int k = 0; k < NK; ++k) {
         if (r0 + k * RS < UW) {
           const C* ek = e + k * (RS / 2) * EW;
-          uu[k * RS * HS] = xfma_r(uu[k * RS * HS], xadd(ek[0], ek[e1]), (T)0.5);
+          uu[k * RS * P] = xfma_r(uu[k * RS * P], xadd(ek[0], ek[e1]), (T)0.5);
         }
       }
     }
@@ -617,13 +639,13 @@ __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, co
     const int r0 = threadIdx.x / (FT + 1), lx = threadIdx.x - r0 * (FT + 1);
     const int fx = 2 * P0x + lx;
     if (r0 < RS && fx < exx && fx < m) {
-      const C* src = U + rbi<UW>(lx + 2, r0 + 2);
+      const C* src = U + rbi<UW, (int)sizeof(C)>(lx + 2, r0 + 2);
       cx<T>* dst = u_out + (long long)(2 * P0y + r0) * m + fx;
 #pragma unroll
       for (int k = 0; k < (FT + 1 + RS - 1) / RS; ++k) {
         const int ly = r0 + k * RS, fy = 2 * P0y + ly;
         if (ly <= FT && fy < eyy && fy < m) *dst = *src;
-        src += RS * RB<UW>::HS;
+        src += RS * L::P;
         dst += (long long)RS * m;
       }
     }
