@@ -62,9 +62,9 @@ DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 # capture of the current kernels on this workload (None when no capture of
 # the current kernels exists): the double-float far-field contraction and the
 # fused FP32 V(1,1) tiles (all levels, and those of the 1025^2 level).
-FF_DF_DRAM_BYTES = None
-TILES_DRAM_BYTES = 0.2165e6
-TILES_FINE_DRAM_BYTES = 0.731e6
+FF_DF_DRAM_BYTES = 10.67e6
+TILES_DRAM_BYTES = 0.241e6
+TILES_FINE_DRAM_BYTES = 0.793e6
 
 
 # FP32 V-cycles per refinement step on the headline workload (at most, with
