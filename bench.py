@@ -699,7 +699,8 @@ def measure_3d(csff, torch, dev, stream, flush):
     small levels' launches of one plan hide under another's fine-level work);
     one plan solving the sixteen directions in turn beside it, and the
     concurrent step with the FP64-class sum-factorised far field; then the far
-    field alone in both modes and the relative L2 distance of their maps."""
+    field alone in both modes and the relative L2 distance of their maps; last
+    the concurrent step with the double-float refinement."""
     c = W.big_3d(n=257, n_rhs=16)
     c["opts"].update(precision="mixed", refine_fp64=1, inner_cycles=INNER_CYCLES, adaptive_inner=1)
     nr, na = c["eta"].shape[0], c["alphas"].shape[0]
@@ -787,6 +788,20 @@ def measure_3d(csff, torch, dev, stream, flush):
                                 "maps_below_1e-5": int((rel <= 1e-5).sum())}
     plan.set_far_field_mode(csff.FF_FP64)
     plan.close()
+    # beside the stated FP64 refinement: the double-float one (outer residual
+    # and update as FP32 pairs on the FP32 pipes, coarsest solve in FP32), the
+    # same concurrent step and tensor-core far field on four new plans
+    opts_df = dict(c["opts"], refine_fp64=0)
+    plans[:] = [csff.Plan(c["problem"], opts_df, stream=st) for st in streams]
+    set_mode(csff.FF_TC_BF16X4)
+    step()
+    msdf = _time_events(torch, stream, step, flush, 2)
+    infs = [x for i in range(G) for x in info[i]]
+    out["double_float_refinement"] = {"value": nr / (msdf / 1e3), "unit": UNIT, "ms_per_step": msdf,
+                                      "cycles": [x["cycles"] for x in infs],
+                                      "all_converged": all(x["rel_res"] <= 1e-8 for x in infs)}
+    for p in plans:
+        p.close()
     return out
 
 
