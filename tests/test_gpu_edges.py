@@ -69,6 +69,34 @@ def test_fp32_vcycle_on_the_largest_grid(csff):
     plan.close()
 
 
+def test_vcycles_on_the_headline_grid_with_the_rhs_changed_in_between(csff):
+    """1025^2 (16-point tiles on the finest level): three FP32 V-cycles in a
+    row on the plan's stream with the right-hand side doubled in place by a
+    torch kernel before each, every cycle against the oracle's from the GPU's
+    previous iterate."""
+    c = W.mixed_2d(20.0)
+    c["opts"]["precision"] = "mixed"
+    plan = csff.Plan(c["problem"], c["opts"])
+    p = O.problem_from_dict(c["problem"])
+    levels = O.make_hierarchy(p, c["opts"]["coarsest_n"])
+    lu = O.coarse_factor(levels[-1])
+    oo = O.opts_from_dict(c["opts"])
+    shp = (p.m, p.m)
+    prev = W.rand_complex(shp, 906).astype(np.complex64).astype(np.complex128)
+    b = W.rand_complex(shp, 907, scale=20.0).astype(np.complex64).astype(np.complex128)
+    ut = dev(prev, torch.complex64)
+    bt = dev(b, torch.complex64)
+    for _ in range(3):
+        bt.mul_(2.0)
+        b = 2.0 * b
+        plan.vcycle(ut, bt)
+        ref = O.vcycle(levels, lu, 0, prev, b, oo)
+        got = ut.cpu().numpy().astype(np.complex128).reshape(shp)
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+        prev = got
+    plan.close()
+
+
 def test_batch_of_one_and_with_a_vanishing_source(csff):
     """A batch of one instance runs the single-plan iteration; in a batch whose
     second instance has chi = 0 (so b = 0) that instance ends at once with

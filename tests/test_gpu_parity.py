@@ -186,6 +186,31 @@ def test_vcycle_fp32(setup):
     assert np.abs(host(ut, shp) - ref).max() <= 1e-4 * np.abs(ref).max()
 
 
+def test_vcycles_with_the_rhs_changed_in_between(setup):
+    """Three FP32 V-cycles in a row on the plan's stream, the right-hand side
+    doubled in place by a torch kernel on that stream just before each (the
+    fused up tiles copy their fine windows before they wait for the kernel
+    before them): each cycle against the oracle's cycle from the GPU's
+    previous iterate and the doubled right-hand side."""
+    c, plan, p, levels = setup
+    oo = O.opts_from_dict(c["opts"])
+    lu = O.coarse_factor(levels[-1])
+    shp = (levels[0].m,) * p.dim
+    u0 = W.rand_complex(shp, 904).astype(np.complex64).astype(np.complex128)
+    b = W.rand_complex(shp, 905, scale=20.0).astype(np.complex64).astype(np.complex128)
+    ut = dev(u0, torch.complex64)
+    bt = dev(b, torch.complex64)
+    prev = u0
+    for _ in range(3):
+        bt.mul_(2.0)
+        b = 2.0 * b
+        plan.vcycle(ut, bt)
+        ref = O.vcycle(levels, lu, 0, prev, b, oo)
+        got = host(ut, shp).astype(np.complex128)
+        assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+        prev = got
+
+
 def test_solve_fp64_history_and_far_field(setup):
     """Per-cycle residual history, cycle count, solution and far-field map."""
     c, plan, p, levels = setup
