@@ -179,7 +179,9 @@ __device__ __forceinline__ void cp_async_sz(uint32_t dst, const void* gsrc, bool
 //    they lie outside the domain (Dirichlet neighbours of black edge points).
 //  - RHS (FP64: and 1/d) on window [1, W-2]^2, the points the sweeps update.
 //  - FP32: per Gaussian X_g at wx = 2 j + o in slot o HS + j, then Y_g along wy.
-// Points outside the interior read as zero.
+// Points outside the interior read as zero.  Per-level kernels copy
+// asynchronously and, with WAIT, wait for their copies before returning;
+// without it the caller waits (after issuing more copies of its own).
 template <typename T, int W, bool COH, bool WAIT = true>
 __device__ __forceinline__ void load_window(int ox, int oy, int m, const cx<T>* u_in, bool zero_u,
                                             const cx<T>* b, const LevelCoef<T>& K, cx<T>* U, cx<T>* B,
@@ -554,7 +556,9 @@ __device__ __forceinline__ int interp_w(int p, int e0, int mc, int* ci, T* w) {
 }
 
 // up tile: u = u_in + P e_c, one RB-GS sweep, write owned points.  Window
-// colour 0 is red (ox + oy even).
+// colour 0 is red (ox + oy even).  In the per-level kernel the tile itself
+// waits for the kernel before it (which writes only e_c), after issuing the
+// copies of its fine window; the persistent kernel's grid barrier orders it.
 template <typename T, int TC, bool COH, bool G1>
 __device__ void up_tile(int P0x, int P0y, const cx<T>* u_in, const cx<T>* ec, const cx<T>* b,
                         const LevelCoef<T>& K, cx<T> c, int m, int mc, cx<T>* u_out, unsigned char* smem_raw) {
