@@ -348,12 +348,17 @@ __device__ __forceinline__ void df_mac2(float2& sh, float2& sl, float2 ah, float
 __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, float4* __restrict__ vdf,
                              float2* __restrict__ vsum, int* __restrict__ ev, int* __restrict__ spread,
                              int* __restrict__ elo, int lo_min) {
+  // the spread is reduced over the CTA before one atomic (a per-warp atomic on
+  // the one counter serialises in L2)
+  __shared__ int wsp[8];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nb = (m + DKB - 1) / DKB;
-  if (warp >= nrows * nb) return;
-  const int row = warp / nb, b = warp % nb;
+  if (threadIdx.x < 8) wsp[threadIdx.x] = 0;
+  __syncthreads();
+  const bool active = warp < nrows * nb;        // warp-uniform
+  const int row = active ? warp / nb : 0, b = active ? warp % nb : 0;
   const int i = b * DKB + lane;
-  double2 x = (i < m) ? v[(long long)row * m + i] : make_double2(0, 0);
+  double2 x = (active && i < m) ? v[(long long)row * m + i] : make_double2(0, 0);
   // exponent of max(|re|, |im|) from the IEEE fields: the larger of the two
   // components' frexp exponents (a non-finite component marks the row bad)
   const bool fin = bits::exp_field(x.x) != 0x7ff && bits::exp_field(x.y) != 0x7ff;
@@ -370,11 +375,16 @@ __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, fl
   }
   const bool bad = __any_sync(0xffffffffu, !fin);   // non-finite: the FP64 kernel runs
   const int eb = (e == -100000 || bad) ? 0 : e;
-  if (lane == 0) {
+  if (active && lane == 0) {
     ev[(long long)row * nb + b] = eb;
     if (elo) elo[(long long)row * nb + b] = lo_min ? elow : e;
-    int sp = bad ? DF_NONFINITE : ((e == -100000) ? 0 : e - emin);
-    atomicMax(spread, sp);
+    wsp[threadIdx.x >> 5] = bad ? DF_NONFINITE : ((e == -100000) ? 0 : e - emin);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sp = 0;
+    for (int w = 0; w < 8; ++w) sp = max(sp, wsp[w]);
+    if (sp > 0) atomicMax(spread, sp);
   }
   // the scaled splits of re, im and re + im (Gauss's three-product complex
   // multiply); the scale applies to the values themselves, since 2^-eb alone
@@ -387,9 +397,11 @@ __global__ void k_split_rows(const double2* __restrict__ v, int m, int nrows, fl
     sm = eb <= 1000 ? bits::split_scaled(x.x + x.y, eb)      // RN(x + y) 2^-eb = RN(x 2^-eb + y 2^-eb)
                     : bits::split_scaled(ldexp(x.x, -eb) + ldexp(x.y, -eb), 0);
   }
-  const long long o = (long long)row * nb * DKB + b * DKB + lane;
-  vdf[o] = make_float4(re.x, re.y, im.x, im.y);
-  vsum[o] = sm;
+  if (active) {
+    const long long o = (long long)row * nb * DKB + b * DKB + lane;
+    vdf[o] = make_float4(re.x, re.y, im.x, im.y);
+    vsum[o] = sm;
+  }
 }
 
 // 2^d as a float for d <= 0 (0 below the subnormal range): exact power of two
