@@ -250,8 +250,26 @@ __device__ __forceinline__ V bred(V v, Op op, V* sh) {
   for (int j = 1; j < (int)(blockDim.x >> 5); ++j) v = op(v, sh[j]);
   return v;
 }
+// (x, y) summed over the block in the order bred uses, the result in thread
+// 0 only: one pass for both components and no FP64 work for the other threads
+__device__ __forceinline__ double2 bsum2_to0(double x, double y, double2* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_double2(x, y);
+  __syncthreads();
+  double2 v = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) {
+    v = sh[0];
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j) {
+      v.x = v.x + sh[j].x;
+      v.y = v.y + sh[j].y;
+    }
+  }
+  return v;
+}
 struct MaxI { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
-struct AddD { __device__ double operator()(double a, double b) const { return a + b; } };
 
 // Stage 2: one block per angle.
 template <int D>
@@ -261,7 +279,7 @@ __global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict
                             double2* __restrict__ F, int* __restrict__ Fexp, int write_exp,
                             int* __restrict__ flag) {
   __shared__ int shi[32];
-  __shared__ double shd[32];
+  __shared__ double2 shd[32];
   const int a = blockIdx.x;
   const int kx = xrow[a];
   const long long R = (D == 3) ? (long long)m * m : m;
@@ -290,10 +308,9 @@ __global__ void k_ff_stage2(const double2* __restrict__ T, const int* __restrict
     ax = fma(w.x, t.x, fma(-w.y, t.y, ax));
     ay = fma(w.x, t.y, fma(w.y, t.x, ay));
   }
-  ax = bred(ax, AddD(), shd);
-  ay = bred(ay, AddD(), shd);
+  const double2 axy = bsum2_to0(ax, ay, shd);
   if (threadIdx.x == 0) {
-    double2 f = cmul(pref, make_double2(ax, ay));
+    double2 f = cmul(pref, axy);
     int e = s1[kx] + s2;
     if (s2 > 0) atomicOr(flag, 1);
     if (write_exp) {
