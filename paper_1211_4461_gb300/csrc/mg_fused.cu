@@ -81,9 +81,11 @@ template <typename T> int coef_ng(const Level& L) { return tiles::formed_coef<T>
 
 template <int TC> size_t down_smem(int rb, int ng) { return tiles::down_smem_elems<TC>(ng, rb == 8) * 2 * rb; }
 template <int TC> size_t up_smem(int rb, int ng) { return tiles::up_smem_elems<TC>(ng, rb == 8) * 2 * rb; }
-// tiles of 16 coarse points unless that leaves fewer than two CTAs per SM (the
-// 513^2 level then runs 1024 tiles of 8 instead of 256 of 16: 3-5 % faster)
-static bool small_tiles(int mc) { return ((mc + 15) / 16) * ((mc + 15) / 16) < 2 * 152; }
+// tiles of 16 coarse points on levels with at least 128 of them (the 513^2
+// level too: its 256 tiles of 16 do less halo work than 1024 tiles of 8 and
+// leave most of the GPU to the other maps of a concurrent step, 2-3 % faster
+// there; one map alone ran 3-5 % slower that way), tiles of 8 below
+static bool small_tiles(int mc) { return ((mc + 15) / 16) * ((mc + 15) / 16) < 128; }
 
 // the down and up kernels for a tile size, specialised for a single Gaussian
 // in FP32 (its x factors then stay in registers)

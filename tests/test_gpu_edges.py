@@ -51,7 +51,7 @@ def test_single_level_plan_is_the_direct_solve(csff, precision):
 
 def test_fp32_vcycle_on_the_largest_grid(csff):
     """4097^2 (134 MB per FP32 array, beyond the L2 cache; 16-point tiles on
-    the 4097^2, 2049^2 and 1025^2 levels): one FP32 V-cycle against the
+    the 4097^2 to 513^2 levels): one FP32 V-cycle against the
     oracle's cycle from the same FP32-rounded inputs, element by element."""
     c = W.mixed_2d(40.0, n=4097)
     c["opts"].update(coarsest_n=9, precision="mixed")
@@ -70,7 +70,7 @@ def test_fp32_vcycle_on_the_largest_grid(csff):
 
 
 def test_vcycles_on_the_headline_grid_with_the_rhs_changed_in_between(csff):
-    """1025^2 (16-point tiles on the finest level): three FP32 V-cycles in a
+    """1025^2 (16-point tiles on the 1025^2 and 513^2 levels): three FP32 V-cycles in a
     row on the plan's stream with the right-hand side doubled in place by a
     torch kernel before each, every cycle against the oracle's from the GPU's
     previous iterate."""

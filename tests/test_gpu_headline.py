@@ -1,7 +1,7 @@
 """Parity on the 1025^2 workload itself (box [-20,20]^2, rotation pi/6,
 chi = -exp(-|x|^2/4), RB-GS V(1,1), 8 levels, 9^2 coarsest grid): the kernels
 that run only at this size -- the fused tiles of 16 coarse points on the
-1025^2 level, in FP32 and in FP64 -- against the oracle's V-cycle element by
+1025^2 and 513^2 levels, in FP32 and in FP64 -- against the oracle's V-cycle element by
 element, full mixed solves re-checked with the oracle's FP64 operator, their
 far fields against the oracle's sum on the same solution, and the batched
 kernel with 1025^2 instances on 16-point tiles.  GPU only."""
@@ -43,8 +43,8 @@ def headline(request):
 
 @pytest.mark.parametrize("refine_fp64", [0, 1], ids=["df", "fp64"])
 def test_fp32_vcycle_at_1025_matches_oracle(csff, headline, refine_fp64):
-    """One FP32 V-cycle through the 16-point tiles of the 1025^2 level (and the
-    8-point tiles and coarse-level block below), against the FP64 oracle cycle
+    """One FP32 V-cycle through the 16-point tiles of the 1025^2 and 513^2
+    levels (and the 8-point tiles and coarse-level block below), against the FP64 oracle cycle
     from the same FP32-rounded inputs.  With refine_fp64 the coarsest solve
     runs in FP64."""
     c, p, levels, lu = headline
@@ -60,8 +60,8 @@ def test_fp32_vcycle_at_1025_matches_oracle(csff, headline, refine_fp64):
 
 
 def test_fp64_vcycle_at_1025_matches_oracle(csff, headline):
-    """One FP64 V-cycle (FP64 16-point tiles on the 1025^2 level) against the
-    oracle cycle."""
+    """One FP64 V-cycle (FP64 16-point tiles on the 1025^2 and 513^2 levels)
+    against the oracle cycle."""
     c, p, levels, lu = headline
     plan = csff.Plan(c["problem"], dict(c["opts"], precision="fp64"))
     shp = (p.m, p.m)
