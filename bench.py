@@ -63,8 +63,8 @@ DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
 # the current kernels exists): the double-float far-field contraction and the
 # fused FP32 V(1,1) tiles (all levels, and those of the 1025^2 level).
 FF_DF_DRAM_BYTES = 10.67e6
-TILES_DRAM_BYTES = 0.241e6
-TILES_FINE_DRAM_BYTES = 0.793e6
+TILES_DRAM_BYTES = 0.223e6
+TILES_FINE_DRAM_BYTES = 0.771e6
 
 
 # FP32 V-cycles per refinement step on the headline workload (at most, with
