@@ -49,12 +49,12 @@ def _peaks():
 # FP64 FMA throughput of this part, measured with an FMA-loop kernel
 # (0.599e12 DFMA/s over 152 SMs; 2 flops per FMA).
 FP64_PEAK_TFLOPS = 1.198
-# FP32 instruction rate derived from unit counts and clock: 152 SMs x 128 FP32
-# lanes x 2.07 GHz.  The double-float contraction spends 36 FP32 instructions
-# (three double-float multiply-adds of 12, Gauss's complex product) per complex
-# multiply-add, i.e. 4.5 per FP64-equivalent flop (8 per complex
-# multiply-add), so its arithmetic ceiling in FP64-equivalent flops is that
-# rate / 4.5.
+# FP32 operation rate derived from unit counts and clock: 152 SMs x 128 FP32
+# lanes x 2.07 GHz (a packed two-lane instruction counts two operations).  The
+# double-float contraction spends 36 FP32 operations (three double-float
+# multiply-adds of 12, Gauss's complex product) per complex multiply-add, i.e.
+# 4.5 per FP64-equivalent flop (8 per complex multiply-add), so its arithmetic
+# ceiling in FP64-equivalent flops is that rate / 4.5.
 FP32_INSTR_PER_S = 152 * 128 * 2.07e9
 DF_INSTR_PER_FLOP = 36.0 / 8.0
 DF_PEAK_TFLOPS = FP32_INSTR_PER_S / DF_INSTR_PER_FLOP / 1e12
@@ -446,9 +446,9 @@ def run_ours(args, rank, world, local_rank):
     roofline_ff = {"kernel": "k_ff_stage1_df (double-float far-field contraction)", "bound": "alu",
                 "achieved": achieved_tf, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / DF_PEAK_TFLOPS, "traffic": FF_DF_DRAM_BYTES,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 4.5 FP32 instructions per "
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 4.5 FP32 operations per "
                                "FP64-equivalent flop (36 per complex multiply-add: three double-float "
-                               "multiply-adds, Gauss's product)",
+                               "multiply-adds, Gauss's product; a packed two-lane instruction counts two)",
                 "avg_launch_ms": ff_avg_ms, "launches": ff["launches"],
                 "alg_flops_per_launch": ff_flops_all, "executed_flops_per_launch": ff_flops,
                 "executed_fraction_per_map": ff_work,
