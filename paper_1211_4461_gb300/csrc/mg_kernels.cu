@@ -168,6 +168,18 @@ __global__ void k_prolong_cells(const cx<T>* __restrict__ ec, int mc, cx<T>* __r
     }
   const bool x1 = Nx < mc, y1 = Ny < mc, z1 = (D == 3) ? Nz < mc : false;
   const long long f0 = ((long long)(D == 3 ? 2 * Nz : 0) * mf + 2 * Ny) * mf + 2 * Nx;
+  // the cell's fine values first, all in flight together (a load after a
+  // store through the same pointer would wait for it)
+  C u0[2][2], u1[2][2];
+#pragma unroll
+  for (int sz = 0; sz < (D == 3 ? 2 : 1); ++sz)
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy) {
+      const bool in = (sz == 0 || z1) && (sy == 0 || y1);
+      const long long f = f0 + ((long long)sz * mf + sy) * mf;
+      u0[sz][sy] = in ? uf[f] : mk<C>(0, 0);
+      u1[sz][sy] = (in && x1) ? uf[f + 1] : mk<C>(0, 0);
+    }
 #pragma unroll
   for (int sz = 0; sz < (D == 3 ? 2 : 1); ++sz) {        // fine z: 0 mid, 1 coincident
     if (sz == 1 && !z1) continue;
@@ -188,8 +200,8 @@ __global__ void k_prolong_cells(const cx<T>* __restrict__ ec, int mc, cx<T>* __r
         vc = sy ? xc[0][1] : cscale(cadd(xc[0][0], xc[0][1]), h);
       }
       const long long f = f0 + ((long long)sz * mf + sy) * mf;
-      uf[f] = cadd(uf[f], vm);
-      if (x1) uf[f + 1] = cadd(uf[f + 1], vc);
+      uf[f] = cadd(u0[sz][sy], vm);
+      if (x1) uf[f + 1] = cadd(u1[sz][sy], vc);
     }
   }
 }
