@@ -408,7 +408,9 @@ __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uin
   // chi u_in = sum_g prod_c (E_{g,c} U_c): each axis' Gaussian factor is paired
   // with its incident-wave factor first, so no partial product leaves the
   // FP64 range when chi u_in itself does not.  The pairs for the block's 32
-  // columns, 8 rows (and plane) are formed once per block.
+  // columns, 8 rows (and plane) are formed once per block, and so are the
+  // row factors k^2 (E_y U_y)(E_z U_z): a node costs one complex product per
+  // Gaussian (this pass runs on the FP64 pipe, 1/61 of the FP32 rate here).
   __shared__ double2 px[8][BX], py[8][BY], pz[8];
   const int t = threadIdx.y * BX + threadIdx.x;
   for (int i = t; i < n_gauss * (BX + BY + 1); i += BX * BY) {
@@ -425,15 +427,17 @@ __global__ void k_rhs(TabPtrs tabs, int n_gauss, const double2* __restrict__ uin
     }
   }
   __syncthreads();
+  for (int i = t; i < n_gauss * BY; i += BX * BY) {
+    const int g = i / BY, r = i % BY;
+    const double2 v = (D == 3) ? cmul(py[g][r], pz[g]) : py[g][r];
+    py[g][r] = cscale(v, k2);
+  }
+  __syncthreads();
   int ix, iy, iz; long long idx;
   if (!thread_point<D>(m, ix, iy, iz, idx)) return;
-  double2 acc = make_double2(0, 0);
-  for (int g = 0; g < n_gauss; ++g) {
-    double2 v = cmul(px[g][threadIdx.x], py[g][threadIdx.y]);
-    if (D == 3) v = cmul(v, pz[g]);
-    acc = cadd(acc, v);
-  }
-  b[idx] = cscale(acc, k2);
+  double2 acc = n_gauss > 0 ? cmul(px[0][threadIdx.x], py[0][threadIdx.y]) : make_double2(0, 0);
+  for (int g = 1; g < n_gauss; ++g) acc = cadd(acc, cmul(px[g][threadIdx.x], py[g][threadIdx.y]));
+  b[idx] = acc;
 }
 
 // ---- FP64 refinement of the mixed solve (option refine_fp64) -------------------
