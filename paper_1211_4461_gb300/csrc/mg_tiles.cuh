@@ -146,20 +146,12 @@ __device__ __forceinline__ float2 crecip(float2 d) {
   return make_float2(__fmul_rn(d.x, r), -__fmul_rn(d.y, r));
 }
 
-// Asynchronous global -> shared copy of BYTES (4, 8 or 16), zero-filled when
-// !valid (no bytes are read then).  Per-level kernels only: data written by
-// other CTAs of the same launch (the persistent kernel) is read through L2.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_zfill(void* smem_dst, const void* gsrc, bool valid) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(gsrc), "n"(BYTES),
-               "r"(valid ? BYTES : 0)
-               : "memory");
-}
+// Asynchronous global -> shared copies of BYTES (4, 8 or 16) to a 32-bit
+// shared-window address (formed once per loop, then advanced by constants),
+// unconditional or zero-filled when !valid (no bytes are read then).
+// Per-level kernels only: data written by other CTAs of the same launch (the
+// persistent kernel) is read through L2.
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-// the same with the shared destination as a 32-bit shared-window address
-// (formed once per loop, then advanced by constants), unconditional or
-// zero-filled when !valid
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 template <int BYTES>
 __device__ __forceinline__ void cp_async_s(uint32_t dst, const void* gsrc) {
