@@ -108,14 +108,86 @@ def _config(args, extra=None):
     return cfg
 
 
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+class _Nvml:
+    """The read-only NVML calls the clock sampler needs, through ctypes (the
+    driver's libnvidia-ml; no Python package needed): the SM clock, its
+    maximum and the clock-event (throttle) reason bits of one device."""
+    SM = 1                                   # NVML_CLOCK_SM
+    REASONS = ((0x8, "hw_slowdown"), (0x40, "hw_thermal_slowdown"), (0x20, "sw_thermal_slowdown"),
+               (0x4, "sw_power_cap"))
 
-    def __init__(self, index):
+    def __init__(self, index, pci_bus_id=None):
+        import ctypes
+        self.ct = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        rc = 1
+        if pci_bus_id:
+            rc = lib.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(), ctypes.byref(h))
+        if rc != 0:
+            rc = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h))
+        if rc != 0:
+            lib.nvmlShutdown()
+            raise OSError("no NVML handle for the device")
+        self.lib, self.h = lib, h
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        mx = ctypes.c_uint()
+        self.max_mhz = mx.value if lib.nvmlDeviceGetMaxClockInfo(h, self.SM, ctypes.byref(mx)) == 0 else None
+
+    def sample(self):
+        c, r = self.ct.c_uint(), self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.ct.byref(c)) != 0:
+            return None
+        bits = r.value if self.reasons_fn(self.h, self.ct.byref(r)) == 0 else 0
+        return c.value, [n for b, n in self.REASONS if bits & b]
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
+def _pci_bus_id(dev_index):
+    """NVML's bus-id string of a CUDA device, from torch's properties (None
+    where this torch does not report them)."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev_index)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """SM clocks and throttle reasons sampled during the timed region: NVML
+    every 10 ms from a thread (ctypes releases the GIL during the calls), or
+    nvidia-smi every 200 ms where NVML cannot be loaded."""
+
+    def __init__(self, index, dev_index=None):
         self.index = index
+        self.dev_index = index if dev_index is None else dev_index
         self.p = None
+        self.nvml = None
+
+    def _poll(self):
+        while not self.stop.is_set():
+            x = self.nvml.sample()
+            if x is not None:
+                self.samples.append(x)
+            self.stop.wait(0.01)
 
     def __enter__(self):
+        try:
+            self.nvml = _Nvml(self.index, _pci_bus_id(self.dev_index))
+        except Exception:
+            self.nvml = None
+        if self.nvml is not None:
+            self.samples = []
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
         q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -128,6 +200,17 @@ class ClockSampler:
 
     def __exit__(self, *a):
         self.result = None
+        if self.nvml is not None:
+            self.stop.set()
+            self.thread.join()
+            self.nvml.close()
+            if self.samples:
+                sm = [x[0] for x in self.samples]
+                self.result = {"sm_mhz": statistics.median(sm),
+                               "sm_max_mhz": self.nvml.max_mhz if self.nvml.max_mhz else max(sm),
+                               "samples": len(sm), "reasons": sorted({n for x in self.samples for n in x[1]}),
+                               "source": "NVML every 10 ms during the timed steps"}
+            return
         if self.p is None:
             return
         time.sleep(0.25)
@@ -153,7 +236,7 @@ class ClockSampler:
                     reasons.add(n)
         if sm:
             self.result = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                           "reasons": sorted(reasons)}
+                           "reasons": sorted(reasons), "source": "nvidia-smi every 200 ms"}
 
 
 # ---------------------------------------------------------------------------
